@@ -1,0 +1,122 @@
+/*
+ * ORACLE for the implicit high-order gas-kinetic scheme (HGKS) on tetrahedra.
+ *
+ * TEST INFRASTRUCTURE ONLY. This is a plain, slow, FP64 CPU restatement of the
+ * paper's method, written to check the CUDA library against. Only tests/,
+ * __graft_entry__.smoke() and bench.py's cpu_baseline / reference arm may load
+ * it. It shares no code with the CUDA library, and the library never calls it.
+ *
+ * Every routine names the passage it follows: Eq. (bgk), (semi), (finite),
+ * (flux), (polys), (compact-big-1/2), (point), (derivative), (weno),
+ * (impEuler), (impsystem), (A-system-1/2), (deri-matrix), (precond), the
+ * algorithm "preconditioned GMRES" (Algorithm 1), and Sec. 5's collision time
+ * and characteristic-variable reconstruction. Where the paper is silent the
+ * oracle takes the readings listed in DESIGN.md ("Readings of the paper").
+ *
+ * Data layout is the natural one for a reader: cell arrays are [cell][5] in the
+ * caller's cell order, gradients [cell][5][3] (component, then direction).
+ */
+#ifndef HGKS_ORACLE_H
+#define HGKS_ORACLE_H
+#include <stdint.h>
+
+#define ORC_MAXSTEN 16   /* non-compact big stencil, excluding the target cell */
+#define ORC_MAXSUB 8     /* cells of one sub-stencil, excluding the target cell */
+
+typedef struct {
+  int32_t scheme;        /* 0: non-compact WENO, 1: compact HWENO           */
+  int32_t weights;       /* 0: nonlinear weights, 1: linear weights (omega = gamma) */
+  int32_t viscous;       /* 0: Euler collision time, 1: Navier-Stokes        */
+  int32_t characteristic;/* 1: reconstruct characteristic variables (Sec. 5) */
+  int32_t krylov_dim, restarts, jacobi_sweeps;
+  int32_t tstar_end;     /* compact point value at t = dt (1) or t = 0 (0)  */
+  double gamma, Pr, mu, cfl, flux_cfl; /* flux_cfl: CFL of the time step used inside the flux */
+  double tau_eps, tau_C, lin_weight, weno_eps;
+  double flux_dt;        /* > 0: fixed time step inside the flux (tests)     */
+  double rho_inf, u_inf[3], p_inf; /* far-field state                        */
+  double wall_T, lid_speed;        /* isothermal wall temperature p/rho; lid speed along +x */
+} orc_params;
+
+typedef struct { int64_t cell; double shift[3]; } orc_sref;
+
+typedef struct {
+  /* non-compact (WENO) */
+  int n_big;                    orc_sref big[ORC_MAXSTEN];
+  double X0[9][ORC_MAXSTEN];    /* a_d = sum_k X0[d][k] (Q_k - Q_0)           */
+  int n_sub[4];                 orc_sref sub[4][ORC_MAXSUB];
+  double Xm[4][3][ORC_MAXSUB];  /* b_j^m = sum_k Xm[m][j][k] (Q_k - Q_0)      */
+  int sub_valid[4];
+  /* compact (HWENO): data = (Q_k - Q_0 for face neighbours k, then gradients) */
+  int n_nb;                     orc_sref nb[4]; int nb_slot[4];
+  double H0[9][4 + 15];         /* a_d = sum H0[d][col] data[col]              */
+  double Hm[4][3][1 + 6];       /* b^m from (Q_m - Q_0, G_0 (3), G_m (3))      */
+  int hsub_has_nb[4];
+  int ready_weno, ready_hweno;
+} orc_fit;
+
+typedef struct {
+  int64_t nv, nc, nf;
+  double *xyz;                 /* [nv][3] */
+  int64_t *tet;                /* [nc][4] */
+  double *vol, *cen, *h;       /* [nc], [nc][3], [nc] */
+  int64_t *cface;              /* [nc][4] face across local face p (opposite vertex p) */
+  int64_t *cnb;                /* [nc][4] neighbour cell, -1 on a boundary */
+  double *cshift;              /* [nc][4][3] add to the neighbour's coordinates to bring it next to this cell */
+  int32_t *cside;              /* [nc][4] 0: this cell is the face's left cell, 1: right */
+  int64_t *fl, *fr;            /* [nf] left/right cell (fr = -1 on a boundary) */
+  int32_t *flp, *frp, *ftag;   /* local face index in left/right; boundary tag (0 interior) */
+  double *farea, *fnrm;        /* [nf], [nf][3] unit normal from left to right */
+  double *fgp;                 /* [nf][3][3] Gauss points, left cell's frame */
+  double *fshift;              /* [nf][3] x(left frame) = x(right frame) + shift */
+  double *fcen;                /* [nf][3] face centroid, left frame */
+  orc_fit *fit;                /* [nc], filled on demand */
+} orc_mesh;
+
+/* ---- mesh (orc_mesh.c) ---- */
+orc_mesh *orc_mesh_create(const double *xyz, int64_t nv, const int64_t *tet, int64_t nc,
+                          const int64_t *bface, const int32_t *btag, int64_t nb,
+                          const double *pshift, int32_t npshift, char *err, int errlen);
+void orc_mesh_destroy(orc_mesh *m);
+int orc_fit_cell(orc_mesh *m, int64_t i, int scheme);   /* 0 ok, <0 error */
+
+/* ---- small dense linear algebra (orc_linalg.c) ---- */
+int orc_lu_solve(int n, const double *A, const double *b, double *x);  /* A row-major n x n */
+int orc_inverse(int n, const double *A, double *Ainv);
+int orc_lsq_pinv(int rows, int cols, const double *A, double *X);    /* X = (cols x rows) least-squares map */
+double orc_sv_ratio(int rows, int cols, const double *A);            /* sigma_min / sigma_max of A */
+
+/* ---- gas-kinetic flux (orc_gks.c) ---- */
+void orc_uvw_moments(double rho, double U, double V, double W, double lam, double K, int range,
+                     double *mu, double *mv, double *mw, double *mxi);
+double orc_monomial_moment(const double *prim, double K, int range, int iu, int iv, int iw, int ixi);
+int orc_slope(const double *prim, double K, const double *dQ, double *a);
+void orc_gks_flux(const orc_params *p, const double *Wl, const double *dWl, const double *Wr,
+                  const double *dWr, double dt, double *F, double *Qpt);
+void orc_boundary_state(const orc_params *p, int tag, const double *nrm_frame /*3x3 rows n,t1,t2*/,
+                        const double *Wl, const double *dWl, double *Wr, double *dWr);
+void orc_primitive(const double *Q, double gamma, double *prim /*rho,U,V,W,lambda*/);
+
+/* ---- reconstruction (orc_recon.c) ---- */
+void orc_face_frame(const double *n, double *T /*3x3 rows*/);
+void orc_char_eigen(const double *Qloc, double gamma, double *R, double *L);
+int orc_recon_side(orc_mesh *m, const orc_params *p, const double *Q, const double *G,
+                   int64_t cell, int slot, double *Wloc /*[3][5]*/, double *dWloc /*[3][3][5]*/,
+                   double *Wglob /*[3][5] or NULL*/, double *gradglob /*[3][5][3] or NULL*/);
+
+/* ---- residual and implicit solver (orc_solver.c) ---- */
+void orc_euler_jacobian(const double *Q, const double *n, double gamma, double *J);
+int orc_local_dt(orc_mesh *m, const orc_params *p, const double *Q, double *dt);
+int orc_residual(orc_mesh *m, const orc_params *p, const double *Q, const double *G,
+                 double *R, double *Gnew, const int64_t *cells, int64_t ncells);
+int orc_jacobian(orc_mesh *m, const orc_params *p, const double *Q, const double *dt,
+                 double *diag /*[nc][25]*/, double *off /*[nc][4][25]*/);
+void orc_apply_A(const orc_mesh *m, const double *diag, const double *off, const double *x, double *y);
+int orc_precondition(const orc_mesh *m, const double *diag, const double *off, int sweeps,
+                     const double *b, double *x);
+int orc_gmres(const orc_mesh *m, const double *diag, const double *off, const orc_params *p,
+              const double *rhs, double *dx, double *hist);
+int orc_gmres_step(orc_mesh *m, const orc_params *p, double *Q, double *G, double *res,
+                   double *dQ_out);
+int orc_solve_steady(orc_mesh *m, const orc_params *p, double *Q, double *G, double drop,
+                     int max_steps, double *hist, int *steps_out);
+#endif

@@ -1,0 +1,240 @@
+"""GB300-native implicit high-order gas-kinetic scheme (HGKS) hot path.
+
+Python binding of libhgks (include/hgks.h): the same entry points, argument
+marshalling only. Every step of the residual and of the GMRES step runs in the
+library's CUDA kernels; PyTorch provides device memory and streams. If the
+library is missing or no CUDA device is present the calls raise; nothing
+falls back to a CPU path.
+
+Device state arrays are torch tensors in the library's internal cell order and
+component-major layout: Q [5, N], G [15, N] (row 3*c + d), R [5, N].
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _native
+
+HGKS_OK = 0
+HGKS_ERR_NOT_CONVERGED = 7
+HGKS_WENO, HGKS_HWENO = 0, 1
+HGKS_NONLINEAR, HGKS_LINEAR = 0, 1
+HGKS_FP64, HGKS_MIXED = 0, 1
+
+
+class hgks_params(C.Structure):
+    _fields_ = [("scheme", C.c_int32), ("weights", C.c_int32), ("viscous", C.c_int32),
+                ("characteristic", C.c_int32), ("precision", C.c_int32), ("jv_mode", C.c_int32),
+                ("krylov_dim", C.c_int32), ("restarts", C.c_int32), ("jacobi_sweeps", C.c_int32),
+                ("tstar_end", C.c_int32),
+                ("gamma", C.c_double), ("Pr", C.c_double), ("mu", C.c_double), ("cfl", C.c_double),
+                ("flux_cfl", C.c_double), ("tau_eps", C.c_double), ("tau_C", C.c_double),
+                ("lin_weight", C.c_double), ("weno_eps", C.c_double), ("flux_dt", C.c_double),
+                ("rho_inf", C.c_double), ("u_inf", C.c_double * 3), ("p_inf", C.c_double),
+                ("wall_T", C.c_double), ("lid_speed", C.c_double)]
+
+
+class hgks_mesh_info_t(C.Structure):
+    _fields_ = [("n_cells", C.c_int64), ("n_faces", C.c_int64), ("n_boundary_faces", C.c_int64),
+                ("device_bytes", C.c_int64), ("device", C.c_int32), ("schemes", C.c_int32)]
+
+
+class hgks_step_info(C.Structure):
+    _fields_ = [("res_l1", C.c_double), ("lin_res", C.c_double * 2), ("krylov_iters", C.c_int32),
+                ("nonphysical", C.c_int32)]
+
+
+class hgks_solve_info(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("converged", C.c_int32), ("res_ref", C.c_double),
+                ("res_final", C.c_double)]
+
+
+class HGKSError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"hgks status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = _native.load()
+        vp, i64, i32, dp = C.c_void_p, C.c_int64, C.c_int32, C.c_void_p
+        P = C.POINTER(hgks_params)
+        sig = {
+            "hgks_default_params": [P],
+            "hgks_mesh_create": [dp, i64, dp, i64, dp, dp, i64, dp, i32, i32, i32, C.POINTER(vp), dp],
+            "hgks_mesh_destroy": [vp],
+            "hgks_mesh_info": [vp, C.POINTER(hgks_mesh_info_t)],
+            "hgks_mesh_volumes": [vp, dp],
+            "hgks_residual": [vp, P, dp, dp, dp, dp, vp],
+            "hgks_local_dt": [vp, P, dp, dp, vp],
+            "hgks_assemble": [vp, P, dp, dp, dp, dp, vp],
+            "hgks_apply_jacobian": [vp, dp, dp, vp],
+            "hgks_precondition": [vp, i32, dp, dp, vp],
+            "hgks_gmres_step": [vp, P, dp, dp, dp, C.POINTER(hgks_step_info), vp],
+            "hgks_solve_steady": [vp, P, dp, dp, C.c_double, i32, dp, C.POINTER(hgks_solve_info), vp],
+            "hgks_residual_host": [vp, P, dp, dp, dp, dp, vp],
+            "hgks_gmres_step_host": [vp, P, dp, dp, C.POINTER(hgks_step_info), vp],
+            "hgks_sync": [vp],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.hgks_last_error.restype = C.c_char_p
+        L.hgks_launch_count.restype = C.c_int64
+        L.hgks_launch_count.argtypes = [i32]
+        _lib = L
+    return _lib
+
+
+def _check(st, allow=()):
+    if st != HGKS_OK and st not in allow:
+        raise HGKSError(st, lib().hgks_last_error().decode())
+    return st
+
+
+def _ptr(t):
+    """Device (torch) or host (numpy) data pointer, or None."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def hgks_default_params(**overrides) -> hgks_params:
+    p = hgks_params()
+    _check(lib().hgks_default_params(C.byref(p)))
+    for k, v in overrides.items():
+        if k == "u_inf":
+            p.u_inf[:] = list(v)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+class hgks_mesh:
+    """A mesh handle; .perm[internal] = caller cell index."""
+
+    def __init__(self, handle, perm, n_cells):
+        self.handle = C.c_void_p(handle)
+        self.perm = perm
+        self.inv = np.empty_like(perm)
+        self.inv[perm] = np.arange(len(perm))
+        self.n_cells = n_cells
+
+    def __del__(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            try:
+                lib().hgks_mesh_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = C.c_void_p(0)
+
+    # marshalling between caller order [n, k] and internal component-major [k, n]
+    def to_internal(self, A, device="cuda"):
+        import torch
+        a = np.ascontiguousarray(np.asarray(A, dtype=np.float64)[self.perm].T)
+        return torch.from_numpy(a).to(device)
+
+    def to_caller(self, T):
+        a = T.detach().cpu().numpy() if hasattr(T, "detach") else np.asarray(T)
+        return np.ascontiguousarray(a.T[self.inv])
+
+
+def hgks_mesh_create(mesh, scheme_mask=3, device=0) -> hgks_mesh:
+    """Build a library mesh from an inputs.Mesh (host arrays, caller order)."""
+    xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
+    tet = np.ascontiguousarray(mesh.tet4, dtype=np.int64)
+    bf = np.ascontiguousarray(mesh.bface3, dtype=np.int64).reshape(-1, 3)
+    bt = np.ascontiguousarray(mesh.btag, dtype=np.int32)
+    ps = mesh.periodic_shift
+    psa = np.ascontiguousarray(ps if ps is not None else np.zeros((0, 3)), dtype=np.float64)
+    perm = np.zeros(max(1, tet.shape[0]), dtype=np.int64)
+    h = C.c_void_p()
+    _check(lib().hgks_mesh_create(_ptr(xyz), xyz.shape[0], _ptr(tet), tet.shape[0], _ptr(bf) if len(bf) else None,
+                                  _ptr(bt) if len(bt) else None, bf.shape[0], _ptr(psa) if len(psa) else None,
+                                  psa.shape[0], scheme_mask, device, C.byref(h), _ptr(perm)))
+    return hgks_mesh(h.value, perm[: tet.shape[0]], tet.shape[0])
+
+
+def hgks_mesh_info(mesh: hgks_mesh) -> hgks_mesh_info_t:
+    info = hgks_mesh_info_t()
+    _check(lib().hgks_mesh_info(mesh.handle, C.byref(info)))
+    return info
+
+
+def hgks_mesh_volumes(mesh: hgks_mesh) -> np.ndarray:
+    v = np.zeros(mesh.n_cells)
+    _check(lib().hgks_mesh_volumes(mesh.handle, _ptr(v)))
+    return v
+
+
+def hgks_residual(mesh, params, Q, G, R, G_new, stream=None):
+    _check(lib().hgks_residual(mesh.handle, C.byref(params), _ptr(Q), _ptr(G), _ptr(R), _ptr(G_new), _stream(stream)))
+
+
+def hgks_local_dt(mesh, params, Q, dt, stream=None):
+    _check(lib().hgks_local_dt(mesh.handle, C.byref(params), _ptr(Q), _ptr(dt), _stream(stream)))
+
+
+def hgks_assemble(mesh, params, Q, dt, diag_out=None, off_out=None, stream=None):
+    _check(lib().hgks_assemble(mesh.handle, C.byref(params), _ptr(Q), _ptr(dt), _ptr(diag_out), _ptr(off_out),
+                               _stream(stream)))
+
+
+def hgks_apply_jacobian(mesh, x, y, stream=None):
+    _check(lib().hgks_apply_jacobian(mesh.handle, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def hgks_precondition(mesh, sweeps, b, x, stream=None):
+    _check(lib().hgks_precondition(mesh.handle, sweeps, _ptr(b), _ptr(x), _stream(stream)))
+
+
+def hgks_gmres_step(mesh, params, Q, G=None, dQ_out=None, stream=None) -> hgks_step_info:
+    info = hgks_step_info()
+    _check(lib().hgks_gmres_step(mesh.handle, C.byref(params), _ptr(Q), _ptr(G), _ptr(dQ_out), C.byref(info),
+                                 _stream(stream)))
+    return info
+
+
+def hgks_solve_steady(mesh, params, Q, G=None, drop_tol=1e-8, max_steps=1000, stream=None):
+    hist = np.zeros(max_steps + 1)
+    info = hgks_solve_info()
+    st = _check(lib().hgks_solve_steady(mesh.handle, C.byref(params), _ptr(Q), _ptr(G), drop_tol, max_steps,
+                                        _ptr(hist), C.byref(info), _stream(stream)), allow=(HGKS_ERR_NOT_CONVERGED,))
+    return info, hist[: info.steps + 1], st == HGKS_OK
+
+
+def hgks_residual_host(mesh, params, Q_host, G_host, R_host, G_new_host, stream=None):
+    _check(lib().hgks_residual_host(mesh.handle, C.byref(params), _ptr(Q_host), _ptr(G_host), _ptr(R_host),
+                                    _ptr(G_new_host), _stream(stream)))
+
+
+def hgks_gmres_step_host(mesh, params, Q_host, G_host=None, stream=None) -> hgks_step_info:
+    info = hgks_step_info()
+    _check(lib().hgks_gmres_step_host(mesh.handle, C.byref(params), _ptr(Q_host), _ptr(G_host), C.byref(info),
+                                      _stream(stream)))
+    return info
+
+
+def hgks_sync(stream=None):
+    _check(lib().hgks_sync(_stream(stream)))
+
+
+def hgks_launch_count(reset=False) -> int:
+    return int(lib().hgks_launch_count(1 if reset else 0))

@@ -1,0 +1,329 @@
+"""Seeded synthetic inputs: tetrahedral meshes and flow states.
+
+This module is shared by the CUDA path's tests/benchmark and by the oracle's
+tests. It holds no arithmetic of the method (no geometry of cells or faces, no
+reconstruction, no flux): it only lays vertices out, connects them into
+tetrahedra, tags boundary triangles and draws seeded states.
+
+Meshes stand in for the paper's workloads (Sec. 5.1 lid-driven cavity on
+tetrahedra split from hexahedra; Sec. 5.2 flow past a sphere). The paper's own
+meshes are not available; these generators reproduce their kind and size.
+
+Boundary tags (shared vocabulary with include/hgks.h):
+  1 isothermal no-slip wall at rest, 2 isothermal no-slip wall moving with the
+  lid speed along +x, 3 adiabatic slip wall, 4 adiabatic no-slip wall,
+  5 far field.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+BC_WALL_ISO = 1
+BC_WALL_LID = 2
+BC_SLIP = 3
+BC_NOSLIP_ADIA = 4
+BC_FARFIELD = 5
+
+BASE_SEED = 2304_09485
+
+
+@dataclass
+class Mesh:
+    """A tetrahedral mesh as plain arrays (caller order)."""
+    xyz: np.ndarray            # [n_vert, 3] float64
+    tet4: np.ndarray           # [n_tet, 4] int64
+    bface3: np.ndarray         # [n_bface, 3] int64
+    btag: np.ndarray           # [n_bface] int32
+    periodic_shift: np.ndarray | None = None   # [k, 3] translations, or None
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_tet(self) -> int:
+        return int(self.tet4.shape[0])
+
+
+def _kuhn_tets(idx):
+    """Six tetrahedra of each hexahedron, all around the main diagonal.
+
+    idx(a, b, c) returns the vertex index array of corner (a, b, c) in {0,1}^3 of
+    every hexahedron. All hexahedra use the same diagonal, so neighbouring
+    splits agree on every shared quadrilateral.
+    """
+    v0 = idx(0, 0, 0)
+    v7 = idx(1, 1, 1)
+    perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+    tets = []
+    for p in perms:
+        c1 = [0, 0, 0]
+        c1[p[0]] = 1
+        c2 = list(c1)
+        c2[p[1]] = 1
+        tets.append(np.stack([v0, idx(*c1), idx(*c2), v7], axis=-1))
+    return np.concatenate([t.reshape(-1, 4) for t in tets], axis=0)
+
+
+def _signed_volume6(xyz, tet):
+    a = xyz[tet[:, 0]]
+    b = xyz[tet[:, 1]] - a
+    c = xyz[tet[:, 2]] - a
+    d = xyz[tet[:, 3]] - a
+    return np.einsum("ij,ij->i", b, np.cross(c, d))
+
+
+def _orient_positive(xyz, tet):
+    """Swap two vertices of every negatively oriented tetrahedron."""
+    s = _signed_volume6(xyz, tet)
+    tet = tet.copy()
+    neg = s < 0
+    tet[neg, 2], tet[neg, 3] = tet[neg, 3].copy(), tet[neg, 2].copy()
+    return tet
+
+
+def cavity_mesh(n: int = 8, jitter: float = 0.1, seed: int = BASE_SEED + 0,
+                permute: bool = True, lid_tag: int = BC_WALL_LID,
+                wall_tag: int = BC_WALL_ISO) -> Mesh:
+    """Unit cube, n^3 hexahedra, each split into 6 tetrahedra (6 n^3 cells).
+
+    Interior vertices are moved by U(-jitter*h, +jitter*h) per axis; the order of
+    the cells is randomly permuted. The lid is the face y = 1 (Sec. 5.1).
+    """
+    rng = np.random.default_rng(seed)
+    h = 1.0 / n
+    g = np.arange(n + 1)
+    I, J, K = np.meshgrid(g, g, g, indexing="ij")
+    lat = np.stack([I, J, K], axis=-1).reshape(-1, 3)
+    xyz = lat.astype(np.float64) * h
+    interior = np.all((lat > 0) & (lat < n), axis=1)
+    d = rng.uniform(-jitter * h, jitter * h, size=xyz.shape)
+    xyz[interior] += d[interior]
+
+    def vid(i, j, k):
+        return (i * (n + 1) + j) * (n + 1) + k
+
+    hi, hj, hk = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    hi, hj, hk = hi.ravel(), hj.ravel(), hk.ravel()
+    tet = _kuhn_tets(lambda a, b, c: vid(hi + a, hj + b, hk + c))
+    tet = _orient_positive(xyz, tet)
+    if permute:
+        tet = tet[rng.permutation(tet.shape[0])]
+
+    # boundary triangles: faces whose three vertices lie on one cube face
+    faces = np.concatenate([tet[:, [1, 2, 3]], tet[:, [0, 2, 3]],
+                            tet[:, [0, 1, 3]], tet[:, [0, 1, 2]]], axis=0)
+    fl = lat[faces]                                   # [nf, 3, 3] lattice coords
+    bf, bt = [], []
+    for axis in range(3):
+        for side in (0, n):
+            on = np.all(fl[:, :, axis] == side, axis=1)
+            bf.append(faces[on])
+            tag = lid_tag if (axis == 1 and side == n) else wall_tag
+            bt.append(np.full(on.sum(), tag, dtype=np.int32))
+    bface = np.concatenate(bf).astype(np.int64)
+    btag = np.concatenate(bt)
+    return Mesh(xyz, tet.astype(np.int64), bface, btag, None,
+                name=f"cavity{n}", meta=dict(n=n, jitter=jitter, seed=seed))
+
+
+def periodic_cube_mesh(n: int = 6, jitter: float = 0.1, seed: int = BASE_SEED + 100,
+                       permute: bool = True, length: float = 1.0) -> Mesh:
+    """Periodic cube [0,L]^3 of n^3 Kuhn-split hexahedra, every vertex jittered.
+
+    Periodic images of a vertex get the same jitter, so faces on opposite sides
+    of the box coincide after a translation by L along one axis.
+    """
+    rng = np.random.default_rng(seed)
+    h = length / n
+    g = np.arange(n + 1)
+    I, J, K = np.meshgrid(g, g, g, indexing="ij")
+    lat = np.stack([I, J, K], axis=-1).reshape(-1, 3)
+    base = rng.uniform(-jitter * h, jitter * h, size=(n, n, n, 3))
+    d = base[lat[:, 0] % n, lat[:, 1] % n, lat[:, 2] % n]
+    xyz = lat.astype(np.float64) * h + d
+
+    def vid(i, j, k):
+        return (i * (n + 1) + j) * (n + 1) + k
+
+    hi, hj, hk = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    hi, hj, hk = hi.ravel(), hj.ravel(), hk.ravel()
+    tet = _kuhn_tets(lambda a, b, c: vid(hi + a, hj + b, hk + c))
+    tet = _orient_positive(xyz, tet)
+    if permute:
+        tet = tet[rng.permutation(tet.shape[0])]
+    return Mesh(xyz, tet.astype(np.int64), np.zeros((0, 3), np.int64),
+                np.zeros(0, np.int32), np.eye(3) * length,
+                name=f"periodic{n}", meta=dict(n=n, jitter=jitter, seed=seed, length=length))
+
+
+def sphere_radii(layers: int, r_in: float, r_out: float, stretch: float) -> np.ndarray:
+    """Radii of a geometric O-grid: first spacing dr1, ratio `stretch`, r_out reached."""
+    if stretch == 1.0:
+        return np.linspace(r_in, r_out, layers + 1)
+    dr1 = (r_out - r_in) * (stretch - 1.0) / (stretch ** layers - 1.0)
+    l = np.arange(layers + 1, dtype=np.float64)
+    return r_in + dr1 * (stretch ** l - 1.0) / (stretch - 1.0)
+
+
+def sphere_mesh(n: int = 32, layers: int = 64, r_in: float = 0.5, r_out: float = 10.0,
+                stretch: float = 1.08, wall_tag: int = BC_SLIP, seed: int = BASE_SEED + 1,
+                permute: bool = True) -> Mesh:
+    """Cubed-sphere O-grid around a sphere, split into tetrahedra.
+
+    Six n x n patches (equiangular) on the sphere, `layers` radial layers. Each
+    surface quadrilateral is cut along the diagonal through its lowest-index
+    vertex; each triangle is extruded into prisms, and each prism is cut into 3
+    tetrahedra by the lowest-vertex-index rule. That rule makes every shared
+    quadrilateral get the same diagonal from both sides, so the mesh is
+    conforming across the patch seams. Cell count = 6 n^2 layers * 6, the same as
+    6 tetrahedra per hexahedron.
+    """
+    rng = np.random.default_rng(seed)
+    # surface lattice points of the cube [0,n]^3
+    g = np.arange(n + 1)
+    I, J, K = np.meshgrid(g, g, g, indexing="ij")
+    lat = np.stack([I, J, K], axis=-1).reshape(-1, 3)
+    on_surf = np.any((lat == 0) | (lat == n), axis=1)
+    surf = lat[on_surf]
+    ns = surf.shape[0]
+    sid = -np.ones((n + 1) ** 3, dtype=np.int64)
+    lin = (surf[:, 0] * (n + 1) + surf[:, 1]) * (n + 1) + surf[:, 2]
+    sid[lin] = np.arange(ns)
+
+    def S(i, j, k):
+        return sid[(i * (n + 1) + j) * (n + 1) + k]
+
+    t = np.tan((surf.astype(np.float64) / n - 0.5) * (math.pi / 2.0))
+    unit = t / np.linalg.norm(t, axis=1, keepdims=True)
+
+    # quadrilaterals of the 6 cube faces
+    a, b = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    a, b = a.ravel(), b.ravel()
+    quads = []
+    for axis in range(3):
+        for side in (0, n):
+            o1, o2 = [x for x in range(3) if x != axis]
+
+            def P(u, v):
+                c = [None, None, None]
+                c[axis] = np.full_like(u, side)
+                c[o1] = u
+                c[o2] = v
+                return S(c[0], c[1], c[2])
+            quads.append(np.stack([P(a, b), P(a + 1, b), P(a + 1, b + 1), P(a, b + 1)], axis=1))
+    quads = np.concatenate(quads, axis=0)
+    # split each quad along the diagonal through its minimum-index vertex
+    m = np.argmin(quads, axis=1)
+    r = np.arange(quads.shape[0])
+    q0 = quads[r, m]
+    q1 = quads[r, (m + 1) % 4]
+    q2 = quads[r, (m + 2) % 4]
+    q3 = quads[r, (m + 3) % 4]
+    tris = np.concatenate([np.stack([q0, q1, q2], 1), np.stack([q0, q2, q3], 1)], axis=0)
+    tris = np.sort(tris, axis=1)                       # a < b < c (surface indices)
+
+    radii = sphere_radii(layers, r_in, r_out, stretch)
+    xyz = (unit[None, :, :] * radii[:, None, None]).reshape(-1, 3)
+    L = np.arange(layers)[:, None]
+    A = (L * ns + tris[None, :, 0]).ravel()
+    B = (L * ns + tris[None, :, 1]).ravel()
+    C = (L * ns + tris[None, :, 2]).ravel()
+    A2, B2, C2 = A + ns, B + ns, C + ns
+    # prism (a,b,c | a',b',c') with a<b<c: the minimum vertex is a, the lateral
+    # quad (b,c,c',b') has minimum b, so the diagonals are a-b', a-c', b-c'.
+    tet = np.concatenate([np.stack([A, B, C, C2], 1),
+                          np.stack([A, B, B2, C2], 1),
+                          np.stack([A, A2, B2, C2], 1)], axis=0)
+    tet = _orient_positive(xyz, tet)
+    if permute:
+        tet = tet[rng.permutation(tet.shape[0])]
+    inner = tris.astype(np.int64)
+    outer = tris.astype(np.int64) + layers * ns
+    bface = np.concatenate([inner, outer], axis=0)
+    btag = np.concatenate([np.full(inner.shape[0], wall_tag, np.int32),
+                           np.full(outer.shape[0], BC_FARFIELD, np.int32)])
+    return Mesh(xyz, tet.astype(np.int64), bface, btag, None,
+                name=f"sphere{n}x{layers}",
+                meta=dict(n=n, layers=layers, r_in=r_in, r_out=r_out, stretch=stretch))
+
+
+# ----------------------------------------------------------------------------
+# states
+# ----------------------------------------------------------------------------
+
+def conservative(rho, u, v, w, p, gamma=1.4):
+    """(rho, rho U, rho V, rho W, rho E) from primitive variables (Sec. 2)."""
+    rho = np.asarray(rho, dtype=np.float64)
+    E = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w)
+    return np.stack(np.broadcast_arrays(rho, rho * u, rho * v, rho * w, E), axis=-1)
+
+
+def vertex_mean(mesh: Mesh) -> np.ndarray:
+    """Mean of the four vertices of every tetrahedron (a sampling point for states)."""
+    return mesh.xyz[mesh.tet4].mean(axis=1)
+
+
+def uniform_state(n: int, rho=1.0, u=0.3, v=0.0, w=0.0, p=1.0 / 1.4, gamma=1.4) -> np.ndarray:
+    """[n, 5] copies of one conservative state (free stream, Sec. 5.2)."""
+    q = conservative(rho, u, v, w, p, gamma)
+    return np.tile(q, (n, 1))
+
+
+def smooth_state(mesh: Mesh, seed: int = BASE_SEED + 7, amp: float = 0.05, gamma=1.4,
+                 base=(1.0, 0.3, 0.1, -0.05, 1.0 / 1.4), wavenumber: float = 2.0):
+    """Smooth random perturbation of a base state, sampled at vertex means.
+
+    Returns (Q [n,5], G [n,15]) where G holds the exact Cartesian gradients of
+    the sampled conservative field (component-major: G[:, 3*c + d] = dQ_c/dx_d),
+    a plausible input for the compact scheme's cell-averaged gradients.
+    """
+    rng = np.random.default_rng(seed)
+    x = vertex_mean(mesh)
+    k = rng.normal(size=(5, 3)) * wavenumber
+    ph = rng.uniform(0, 2 * math.pi, size=5)
+    s = np.sin(x @ k.T + ph)                       # [n,5]
+    c = np.cos(x @ k.T + ph)
+    prim = np.array(base)[None, :] * (1.0 + amp * s)
+    dprim = (np.array(base)[None, :, None] * amp * c[:, :, None] * k[None, :, :])
+    rho, u, v, w, p = (prim[:, i] for i in range(5))
+    Q = conservative(rho, u, v, w, p, gamma)
+    drho, du, dv, dw, dp = (dprim[:, i, :] for i in range(5))
+    G = np.zeros((x.shape[0], 5, 3))
+    G[:, 0] = drho
+    G[:, 1] = drho * u[:, None] + rho[:, None] * du
+    G[:, 2] = drho * v[:, None] + rho[:, None] * dv
+    G[:, 3] = drho * w[:, None] + rho[:, None] * dw
+    G[:, 4] = dp / (gamma - 1.0) + 0.5 * drho * (u * u + v * v + w * w)[:, None] \
+        + rho[:, None] * (u[:, None] * du + v[:, None] * dv + w[:, None] * dw)
+    return Q, G.reshape(-1, 15)
+
+
+# ----------------------------------------------------------------------------
+# flow conditions (Sec. 5.1, 5.2): plain parameter values for a problem
+# ----------------------------------------------------------------------------
+
+def cavity_conditions(Mach: float = 0.15, Re: float = 100.0, gamma: float = 1.4, lid_speed: float = 1.0):
+    """Lid-driven cavity: rho = 1, lid speed U, sound speed U/Mach, isothermal walls
+    at the initial temperature, mu = rho U L / Re with L = 1."""
+    p = 1.0 / (gamma * Mach * Mach) * lid_speed ** 2
+    return dict(viscous=1, mu=lid_speed / Re, rho_inf=1.0, u_inf=(0.0, 0.0, 0.0), p_inf=p,
+                wall_T=p / 1.0, lid_speed=lid_speed, gamma=gamma)
+
+
+def sphere_conditions(Mach: float = 0.3, Re: float | None = None, aoa_deg: float = 0.0, gamma: float = 1.4):
+    """Flow past a unit-diameter sphere: free stream (1, Ma, 0, 0, 1/gamma), rotated by
+    the angle of attack in the x-y plane; mu = rho U D / Re (D = 1) when viscous."""
+    a = math.radians(aoa_deg)
+    u = (Mach * math.cos(a), Mach * math.sin(a), 0.0)
+    d = dict(viscous=0 if Re is None else 1, mu=0.0 if Re is None else Mach / Re, rho_inf=1.0,
+             u_inf=u, p_inf=1.0 / gamma, wall_T=1.0 / gamma, lid_speed=0.0, gamma=gamma)
+    return d
+
+
+def state_from_conditions(n: int, cond: dict) -> np.ndarray:
+    """Uniform initial state of a problem: the free stream (the cavity starts at rest)."""
+    u = cond["u_inf"]
+    return uniform_state(n, rho=cond["rho_inf"], u=u[0], v=u[1], w=u[2], p=cond["p_inf"],
+                         gamma=cond.get("gamma", 1.4))

@@ -1,0 +1,568 @@
+"""Pins of the oracle against facts the paper and the mathematics fix.
+
+None of these retypes an oracle formula: the expected values come from
+numerical quadrature of the Maxwellian, the Euler and Navier-Stokes equations
+(Chapman-Enskog limit of the BGK model, Sec. 2), symmetry, exactness of the
+reconstruction on polynomials (Sec. 3), discrete conservation of Eq. (finite),
+finite differences of the Euler flux, and dense linear algebra (Sec. 4).
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+import oracle as O
+from paper_2304_09485_gb300 import inputs as I
+
+GAMMA = 1.4
+K = (5 - 3 * GAMMA) / (GAMMA - 1)        # internal degrees of freedom (Sec. 2): 2
+
+
+def prim_of(Q, g=GAMMA):
+    rho = Q[0]; u = Q[1:4] / rho
+    p = (g - 1) * (Q[4] - 0.5 * rho * u @ u)
+    return rho, u, p
+
+
+def euler_flux(Q, n, g=GAMMA):
+    rho, u, p = prim_of(Q, g)
+    un = u @ n
+    return np.array([rho * un, *(rho * u * un + p * n), (Q[4] + p) * un])
+
+
+# ---------------------------------------------------------------------------
+# Maxwellian moments vs numerical quadrature
+# ---------------------------------------------------------------------------
+
+def gauss_hermite_moment(U, lam, k):
+    """<u^k> of the 1-D Maxwellian (lam/pi)^(1/2) exp(-lam (u-U)^2), Gauss-Hermite."""
+    x, w = np.polynomial.hermite.hermgauss(40)
+    u = U + x / math.sqrt(lam)
+    return float(np.sum(w * u ** k) / math.sqrt(math.pi))
+
+
+def half_moment(U, lam, k, sign):
+    f = lambda u: u ** k * math.sqrt(lam / math.pi) * math.exp(-lam * (u - U) ** 2)
+    if sign > 0:
+        v, _ = integrate.quad(f, 0, np.inf, epsabs=1e-15, epsrel=1e-14, limit=200)
+    else:
+        v, _ = integrate.quad(f, -np.inf, 0, epsabs=1e-15, epsrel=1e-14, limit=200)
+    return v
+
+
+@pytest.mark.parametrize("U,lam", [(0.3, 0.7), (-1.2, 2.5), (0.0, 1.0), (2.0, 0.4)])
+def test_moments_vs_quadrature(U, lam):
+    prim = np.array([1.3, U, 0.2, -0.4, lam])
+    for k in range(7):
+        full = O.monomial_moment(prim, K, 0, k, 0, 0, 0) / 1.3
+        assert full == pytest.approx(gauss_hermite_moment(U, lam, k), rel=1e-12, abs=1e-13)
+        for s in (+1, -1):
+            hm = O.monomial_moment(prim, K, s, k, 0, 0, 0) / 1.3
+            assert hm == pytest.approx(half_moment(U, lam, k, s), rel=1e-10, abs=1e-13)
+    for k in range(6):   # v and w moments
+        assert O.monomial_moment(prim, K, 0, 0, k, 0, 0) / 1.3 == pytest.approx(gauss_hermite_moment(0.2, lam, k), rel=1e-12, abs=1e-13)
+        assert O.monomial_moment(prim, K, 0, 0, 0, k, 0) / 1.3 == pytest.approx(gauss_hermite_moment(-0.4, lam, k), rel=1e-12, abs=1e-13)
+
+
+@pytest.mark.parametrize("Kdof", [2.0, 3.0])
+def test_internal_dof_moments(Kdof):
+    """<xi^2>, <xi^4> of K Gaussian internal variables, by a K-dim Gauss-Hermite product."""
+    lam = 0.8
+    x, w = np.polynomial.hermite.hermgauss(20)
+    grids = np.meshgrid(*([x] * int(Kdof)), indexing="ij")
+    wts = np.ones_like(grids[0])
+    for gi, wi in zip(grids, np.meshgrid(*([w] * int(Kdof)), indexing="ij")):
+        wts = wts * wi
+    xi2 = sum(gi ** 2 for gi in grids) / lam
+    norm = math.pi ** (Kdof / 2)
+    prim = np.array([1.0, 0.0, 0.0, 0.0, lam])
+    assert O.monomial_moment(prim, Kdof, 0, 0, 0, 0, 1) == pytest.approx(np.sum(wts * xi2) / norm, rel=1e-12)
+    assert O.monomial_moment(prim, Kdof, 0, 0, 0, 0, 2) == pytest.approx(np.sum(wts * xi2 ** 2) / norm, rel=1e-12)
+
+
+def maxwell_quadrature(prim, poly, npts=10):
+    """int g poly(u,v,w,xi^2) dXi by tensor Gauss-Hermite in (u, v, w, xi_1, xi_2)."""
+    rho, U, V, W, lam = prim
+    x, w = np.polynomial.hermite.hermgauss(npts)
+    s = 1 / math.sqrt(lam)
+    u, v, ww, a, b = np.meshgrid(U + s * x, V + s * x, W + s * x, s * x, s * x, indexing="ij")
+    wt = np.einsum("i,j,k,l,m->ijklm", w, w, w, w, w) / math.pi ** 2.5
+    return rho * np.sum(wt * poly(u, v, ww, a * a + b * b))
+
+
+def psi(u, v, w, xi2):
+    return [np.ones_like(u), u, v, w, 0.5 * (u * u + v * v + w * w + xi2)]
+
+
+def test_slope_moment_identity():
+    """<a> = int g (a . psi) psi dXi reproduces the derivative it was solved from."""
+    rng = np.random.default_rng(3)
+    for _ in range(3):
+        prim = np.array([rng.uniform(0.5, 2), *rng.normal(size=3) * 0.5, rng.uniform(0.4, 2)])
+        dQ = rng.normal(size=5)
+        a = O.slope(prim, K, dQ)
+        got = [maxwell_quadrature(prim, lambda u, v, w, x2, k=k: sum(a[j] * psi(u, v, w, x2)[j] for j in range(5)) * psi(u, v, w, x2)[k])
+               for k in range(5)]
+        np.testing.assert_allclose(got, dQ, rtol=1e-10, atol=1e-11)
+
+
+# ---------------------------------------------------------------------------
+# the BGK flux
+# ---------------------------------------------------------------------------
+
+def rand_state(rng, g=GAMMA):
+    rho = rng.uniform(0.6, 1.6); u = rng.normal(size=3) * 0.4; p = rng.uniform(0.4, 1.4)
+    return np.array([rho, *(rho * u), p / (g - 1) + 0.5 * rho * u @ u])
+
+
+def test_uniform_flux_is_euler_flux():
+    rng = np.random.default_rng(5)
+    p = O.make_params(viscous=0)
+    for _ in range(5):
+        W = rand_state(rng)
+        F, Qp = O.gks_flux(p, W, np.zeros((3, 5)), W, np.zeros((3, 5)), 0.01)
+        np.testing.assert_allclose(F, euler_flux(W, np.array([1.0, 0, 0])), rtol=1e-13, atol=1e-14)
+        np.testing.assert_allclose(Qp, W, rtol=1e-13, atol=1e-14)
+
+
+def test_two_state_flux_time_integral():
+    """Zero slopes, W_l != W_r: f(t) = (1 - e^{-t/tau}) g0 + e^{-t/tau} (g_l H(u) + g_r (1 - H(u)))
+    (Eq. (flux)); its flux averaged over [0, dt] by numerical integration in u and t."""
+    rng = np.random.default_rng(7)
+    p = O.make_params(viscous=0, tau_eps=0.1, tau_C=1.0)
+    Wl, Wr = rand_state(rng), rand_state(rng)
+    dt = 0.05
+    F, _ = O.gks_flux(p, Wl, np.zeros((3, 5)), Wr, np.zeros((3, 5)), dt)
+
+    def prim(W):
+        rho, u, pr = prim_of(W)
+        return rho, u, rho / (2 * pr)
+
+    def flux_half(W, sign):
+        """int_{u sign 0} u psi g dXi: numerical in u, Gaussian moments in v, w, xi."""
+        rho, (U, V, Wv), lam = prim(W)
+        g1 = lambda u: math.sqrt(lam / math.pi) * math.exp(-lam * (u - U) ** 2)
+        lo, hi = (0, np.inf) if sign > 0 else (-np.inf, 0)
+        m = [integrate.quad(lambda u: u ** (k + 1) * g1(u), lo, hi, epsabs=1e-15, epsrel=1e-13)[0] for k in range(4)]
+        ev2 = V * V + 0.5 / lam; ew2 = Wv * Wv + 0.5 / lam; exi = K * 0.5 / lam
+        return rho * np.array([m[0], m[1], V * m[0], Wv * m[0], 0.5 * (m[2] + (ev2 + ew2 + exi) * m[0])])
+
+    def dens_half(W, sign):
+        rho, (U, V, Wv), lam = prim(W)
+        g1 = lambda u: math.sqrt(lam / math.pi) * math.exp(-lam * (u - U) ** 2)
+        lo, hi = (0, np.inf) if sign > 0 else (-np.inf, 0)
+        m = [integrate.quad(lambda u: u ** k * g1(u), lo, hi, epsabs=1e-15, epsrel=1e-13)[0] for k in range(3)]
+        ev2 = V * V + 0.5 / lam; ew2 = Wv * Wv + 0.5 / lam; exi = K * 0.5 / lam
+        return rho * np.array([m[0], m[1], V * m[0], Wv * m[0], 0.5 * (m[2] + (ev2 + ew2 + exi) * m[0])])
+
+    Q0 = dens_half(Wl, +1) + dens_half(Wr, -1)
+    Feq = euler_flux(Q0, np.array([1.0, 0, 0]))
+    Fkin = flux_half(Wl, +1) + flux_half(Wr, -1)
+    pl, pr = prim_of(Wl)[2], prim_of(Wr)[2]
+    tau = 0.1 * dt + abs((pl - pr) / (pl + pr)) * dt     # Sec. 5, inviscid
+    avg = lambda fn: integrate.quad(fn, 0, dt, epsabs=1e-16, epsrel=1e-13)[0] / dt
+    expect = avg(lambda t: 1 - math.exp(-t / tau)) * Feq + avg(lambda t: math.exp(-t / tau)) * Fkin
+    np.testing.assert_allclose(F, expect, rtol=1e-10, atol=1e-12)
+
+
+def ns_reference(W, dW, tau, dt, g=GAMMA):
+    """Euler flux + (dt/2) d/dt F_Euler + Navier-Stokes flux with mu = tau p, Pr = 1 and the
+    BGK bulk term 2/(K+3) (the Chapman-Enskog limit of Eq. (bgk), Sec. 2), along x."""
+    rho, u, p = prim_of(W, g)
+    n = np.eye(3)
+
+    def flux(Q, d):
+        return euler_flux(Q, n[d], g)
+    drho = dW[:, 0]
+    du = (dW[:, 1:4] - np.outer(drho, u)) / rho                 # du[d, i] = d u_i / d x_d
+    dp = (g - 1) * (dW[:, 4] - 0.5 * drho * (u @ u) - rho * du @ u)
+    # dQ/dt = -sum_d J_d dQ/dx_d (Euler equations), J_d by central differences
+    def dflux(d):
+        e = 1e-7
+        J = np.zeros((5, 5))
+        for k in range(5):
+            dq = np.zeros(5); dq[k] = e * max(1.0, abs(W[k]))
+            J[:, k] = (flux(W + dq, d) - flux(W - dq, d)) / (2 * dq[k])
+        return J
+    Jx = dflux(0)
+    dQdt = -sum(dflux(d) @ dW[d] for d in range(3))
+    mu = tau * p
+    divu = du[0, 0] + du[1, 1] + du[2, 2]
+    sig = np.array([mu * (du[0, i] + du[i, 0]) for i in range(3)])
+    sig[0] -= mu * 2.0 / (K + 3) * divu
+    T = p / rho
+    dT = (dp - T * drho) / rho
+    kappa = mu * (K + 5) / 2                                     # Pr = 1: kappa = c_p mu
+    visc = np.array([0.0, *(-sig), -(u @ sig) - kappa * dT[0]])
+    return flux(W, 0) + 0.5 * dt * (Jx @ dQdt) + visc
+
+
+def test_chapman_enskog_limit():
+    """Continuous data (W_l = W_r, equal slopes): Eq. (flux) averaged over dt is exactly the
+    Euler flux, plus dt/2 times its Euler time derivative, plus the NS viscous flux with
+    mu = tau p (the e^{-t/tau} terms cancel). Pins slopes, time slopes and time weights."""
+    rng = np.random.default_rng(11)
+    mu, dt = 2e-3, 0.02
+    p = O.make_params(viscous=1, mu=mu, tau_C=1.0)
+    for _ in range(3):
+        W = rand_state(rng)
+        dW = rng.normal(size=(3, 5)) * 0.3
+        F, Qp = O.gks_flux(p, W, dW, W, dW, dt)
+        _, _, pr = prim_of(W)
+        tau = mu / pr
+        ref = ns_reference(W, dW, tau, dt)
+        np.testing.assert_allclose(F, ref, rtol=1e-6, atol=1e-8)   # FD Jacobian in the reference
+        # point value at t* = dt is W + dt dW/dt (Eq. (point)); its mass component follows
+        # the continuity equation
+        drho_dt = -(dW[0, 1] + dW[1, 2] + dW[2, 3])
+        assert Qp[0] == pytest.approx(W[0] + dt * drho_dt, rel=1e-12, abs=1e-12)
+
+
+def mirror(W, dW):
+    """Reflection x -> -x of a face-frame state and its (n, t1, t2) derivatives."""
+    S = np.array([1, -1, 1, 1, 1.0])
+    dWm = dW * S[None, :]
+    dWm[0] = -dWm[0]
+    return W * S, dWm
+
+
+def test_flux_reflection_antisymmetry():
+    """Swapping the sides and reflecting x reverses the flux: F(mirror(r), mirror(l)) = -S F(l, r)."""
+    rng = np.random.default_rng(13)
+    for visc in (0, 1):
+        p = O.make_params(viscous=visc, mu=3e-3)
+        Wl, Wr = rand_state(rng), rand_state(rng)
+        dWl, dWr = rng.normal(size=(3, 5)) * 0.2, rng.normal(size=(3, 5)) * 0.2
+        F, _ = O.gks_flux(p, Wl, dWl, Wr, dWr, 0.03)
+        ml, mdl = mirror(Wr, dWr)
+        mr, mdr = mirror(Wl, dWl)
+        F2, _ = O.gks_flux(p, ml, mdl, mr, mdr, 0.03)
+        S = np.array([1, -1, 1, 1, 1.0])
+        np.testing.assert_allclose(F2, -S * F, rtol=1e-12, atol=1e-14)
+
+
+def test_flux_tangential_rotation():
+    """Rotating the tangential frame by an angle rotates (V, W) flux components alike."""
+    rng = np.random.default_rng(17)
+    p = O.make_params(viscous=1, mu=2e-3)
+    Wl, Wr = rand_state(rng), rand_state(rng)
+    dWl, dWr = rng.normal(size=(3, 5)) * 0.2, rng.normal(size=(3, 5)) * 0.2
+    F, _ = O.gks_flux(p, Wl, dWl, Wr, dWr, 0.02)
+    th = 0.7
+    Rt = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+
+    def rot(W, dW):
+        W2 = W.copy(); W2[2:4] = Rt @ W[2:4]
+        dW2 = dW.copy(); dW2[:, 2:4] = dW[:, 2:4] @ Rt.T
+        dW2[1:3] = Rt @ dW2[1:3]
+        return W2, dW2
+    a, da = rot(Wl, dWl)
+    b, db = rot(Wr, dWr)
+    F2, _ = O.gks_flux(p, a, da, b, db, 0.02)
+    Fr = F.copy(); Fr[2:4] = Rt @ F[2:4]
+    np.testing.assert_allclose(F2, Fr, rtol=1e-12, atol=1e-14)
+
+
+def test_boundary_states():
+    """Walls: a state at rest at the wall temperature is its own image (pressure-only wall flux);
+    every wall image is an involution; the far field returns the free stream."""
+    rng = np.random.default_rng(19)
+    T3 = O.face_frame(np.array([0.3, -0.5, 0.81]) / np.linalg.norm([0.3, -0.5, 0.81]))
+    p = O.make_params(wall_T=0.9, lid_speed=0.0, rho_inf=1.1, u_inf=(0.2, 0.1, 0.0), p_inf=0.8)
+    W = np.array([1.0, 0, 0, 0, 0.9 / (GAMMA - 1)])
+    for tag in (1, 2, 3, 4):
+        Wr, dWr = O.boundary_state(p, tag, T3, W, np.zeros((3, 5)))
+        np.testing.assert_allclose(Wr, W, rtol=1e-14, atol=1e-14)
+        F, _ = O.gks_flux(O.make_params(viscous=1, mu=1e-3), W, np.zeros((3, 5)), Wr, dWr, 0.01)
+        np.testing.assert_allclose(F, [0, 0.9, 0, 0, 0], atol=1e-13)
+    for tag in (1, 3, 4):
+        W = rand_state(rng); dW = rng.normal(size=(3, 5)) * 0.1
+        Wr, dWr = O.boundary_state(p, tag, T3, W, dW)
+        W2, dW2 = O.boundary_state(p, tag, T3, Wr, dWr)
+        np.testing.assert_allclose(W2, W, rtol=1e-12)
+        np.testing.assert_allclose(dW2, dW, rtol=1e-10, atol=1e-12)
+    Wr, dWr = O.boundary_state(p, 5, T3, W, dW)
+    u = T3 @ np.array([0.2, 0.1, 0.0])
+    np.testing.assert_allclose(Wr, [1.1, *(1.1 * u), 0.8 / (GAMMA - 1) + 0.55 * u @ u], rtol=1e-14)
+    assert np.all(dWr == 0)
+
+
+# ---------------------------------------------------------------------------
+# reconstruction (Sec. 3)
+# ---------------------------------------------------------------------------
+
+def tet_average_quadratic(xyz, tet, f):
+    """Exact cell average of a quadratic f over each tetrahedron from the quadratic
+    Lagrange element: -1/20 sum f(vertices) + 1/5 sum f(edge midpoints)."""
+    V = xyz[tet]
+    vs = sum(f(V[:, a]) for a in range(4))
+    es = sum(f(0.5 * (V[:, a] + V[:, b])) for a in range(4) for b in range(a + 1, 4))
+    return -vs / 20 + es / 5
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_linear_fields_reproduced(scheme):
+    """Any linear field is reproduced exactly at the Gauss points, with nonlinear weights
+    and characteristic variables (all sub-polynomials agree, so the weights are linear)."""
+    m = I.cavity_mesh(4)
+    om = O.OracleMesh(m)
+    rng = np.random.default_rng(23)
+    A = rng.normal(size=(5, 3)) * 0.1
+    b = np.array([1.0, 0.2, -0.1, 0.05, 2.5])
+    f = lambda X: X @ A.T + b
+    Q = tet_average_quadratic(m.xyz, m.tet4, f)
+    G = np.repeat(A.reshape(1, 15), m.n_tet, axis=0)
+    p = O.make_params(scheme=scheme, weights=0)
+    for cell in rng.choice(m.n_tet, 25, replace=False):
+        for slot in range(4):
+            _, _, Wg, gg = om.recon_side(p, Q, G, int(cell), slot)
+            gp = om.face_gauss_points(int(cell), slot)
+            np.testing.assert_allclose(Wg, f(gp), rtol=1e-12, atol=1e-13)
+            np.testing.assert_allclose(gg, np.repeat(A[None], 3, axis=0), rtol=1e-10, atol=1e-11)
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_quadratic_fields_reproduced_linear_weights(scheme):
+    """With linear weights Eq. (weno) returns P0, which reproduces any quadratic."""
+    m = I.periodic_cube_mesh(5)
+    om = O.OracleMesh(m)
+    rng = np.random.default_rng(29)
+    Hq = rng.normal(size=(5, 3, 3)) * 0.2
+    Hq = Hq + Hq.transpose(0, 2, 1)
+    A = rng.normal(size=(5, 3)) * 0.3
+    b = np.array([1.0, 0.2, -0.1, 0.05, 2.5])
+    cellc = m.xyz[m.tet4].mean(axis=1)
+
+    def f(X):
+        return X @ A.T + 0.5 * np.einsum("...i,cij,...j->...c", X, Hq, X) + b
+    Q = tet_average_quadratic(m.xyz, m.tet4, f)
+    G = np.einsum("cij,nj->nci", Hq, cellc) + A[None]       # gradient of a quadratic at the centroid
+    G = G.reshape(-1, 15)
+    p = O.make_params(scheme=scheme, weights=1)
+    # cells whose stencils do not cross the periodic seam
+    inner = np.where(np.all((cellc > 0.35) & (cellc < 0.65), axis=1))[0]
+    for cell in inner[:20]:
+        for slot in range(4):
+            _, _, Wg, gg = om.recon_side(p, Q, G, int(cell), slot)
+            gp = om.face_gauss_points(int(cell), slot)
+            np.testing.assert_allclose(Wg, f(gp), rtol=1e-11, atol=1e-12)
+            grad = np.einsum("cij,gj->gci", Hq, gp) + A[None]
+            np.testing.assert_allclose(gg, grad, rtol=1e-9, atol=1e-10)
+
+
+def test_gauss_points_on_faces():
+    m = I.cavity_mesh(3)
+    om = O.OracleMesh(m)
+    for cell in range(0, m.n_tet, 17):
+        for slot in range(4):
+            gp = om.face_gauss_points(cell, slot)
+            V = m.xyz[np.delete(m.tet4[cell], slot)]
+            # barycentric (2/3, 1/6, 1/6) and permutations: the centroid of the 3 points is the face centroid
+            np.testing.assert_allclose(gp.mean(0), V.mean(0), rtol=1e-13, atol=1e-14)
+            for g in gp:
+                lam = np.linalg.lstsq(np.vstack([V.T, np.ones(3)]), np.append(g, 1), rcond=None)[0]
+                assert sorted(np.round(lam, 12)) == pytest.approx([1 / 6, 1 / 6, 2 / 3])
+
+
+# ---------------------------------------------------------------------------
+# residual (Eq. (finite))
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_free_stream_preservation(scheme):
+    m = I.periodic_cube_mesh(5)
+    om = O.OracleMesh(m)
+    Q = I.uniform_state(m.n_tet, rho=1.1, u=0.3, v=-0.2, w=0.1, p=0.9)
+    G = np.zeros((m.n_tet, 15))
+    p = O.make_params(scheme=scheme)
+    out = om.residual(p, Q, G)
+    R = out[0] if scheme == 1 else out
+    assert np.abs(R).max() <= 1e-13
+    if scheme == 1:
+        assert np.abs(out[1]).max() <= 1e-12
+
+
+def test_rest_state_in_closed_cavity():
+    """Fluid at rest at the wall temperature inside isothermal walls at rest: R = 0."""
+    m = I.cavity_mesh(4, lid_tag=I.BC_WALL_ISO)
+    om = O.OracleMesh(m)
+    c = I.cavity_conditions()
+    Q = I.state_from_conditions(m.n_tet, c)
+    for scheme in (0, 1):
+        p = O.make_params(scheme=scheme, Pr=0.72, **c)
+        out = om.residual(p, Q, np.zeros((m.n_tet, 15)))
+        R = out[0] if scheme else out
+        assert np.abs(R).max() <= 1e-12 * c["p_inf"]
+
+
+@pytest.mark.parametrize("scheme,visc", [(0, 0), (1, 0), (1, 1)])
+def test_discrete_conservation(scheme, visc):
+    m = I.periodic_cube_mesh(5)
+    om = O.OracleMesh(m)
+    Q, G = I.smooth_state(m, amp=0.08)
+    p = O.make_params(scheme=scheme, viscous=visc, mu=0.01, Pr=0.72 if visc else 1.0)
+    out = om.residual(p, Q, G)
+    R = out[0] if scheme else out
+    scale = np.abs(R).sum(0) + 1e-3
+    assert np.all(np.abs(R.sum(0)) <= 1e-13 * scale + 1e-16)
+    if scheme == 1:
+        tot = (out[1] * om.vol[:, None]).sum(0)
+        assert np.abs(tot).max() <= 1e-13
+
+
+def test_design_order_density_wave():
+    """rho = 1 + 0.2 sin(2 pi (x+y+z)), U = (1,1,1)/2, p = 1 solves the Euler equations;
+    R/|Omega| must approach -(1/|Omega|) sum_faces F_Euler(Q_exact).n S (7-point faces)."""
+    u0 = 0.5
+    def Qx(X):
+        rho = 1 + 0.2 * np.sin(2 * np.pi * X.sum(-1))
+        return np.stack([rho, rho * u0, rho * u0, rho * u0, 1 / (GAMMA - 1) + 0.5 * rho * 3 * u0 * u0], -1)
+    # degree-5 triangle rule (7 points), barycentric
+    a1, b1 = 0.797426985353087, 0.101286507323456
+    a2, b2 = 0.059715871789770, 0.470142064105115
+    w0, w1, w2 = 0.225, 0.125939180544827, 0.132394152788506
+    bary = [(1 / 3, 1 / 3, 1 / 3, w0)] + [(a1, b1, b1, w1), (b1, a1, b1, w1), (b1, b1, a1, w1)] + \
+           [(a2, b2, b2, w2), (b2, a2, b2, w2), (b2, b2, a2, w2)]
+    errs, hs = [], []
+    for n in (4, 8, 16):
+        m = I.periodic_cube_mesh(n, jitter=0.1)
+        om = O.OracleMesh(m)
+        V = m.xyz[m.tet4]
+        Q = cell_average(V, Qx)
+        p = O.make_params(scheme=0, weights=0, flux_dt=1e-8, characteristic=1)
+        R = om.residual(p, Q)
+        vol = om.vol
+        ex = np.zeros_like(Q)
+        for f_ in range(4):
+            F3 = V[:, [k for k in range(4) if k != f_]]
+            opp = V[:, f_]
+            nrm = np.cross(F3[:, 1] - F3[:, 0], F3[:, 2] - F3[:, 0])
+            sgn = np.sign(np.einsum("ij,ij->i", nrm, F3[:, 0] - opp))
+            nrm = nrm * sgn[:, None]
+            area = 0.5 * np.linalg.norm(nrm, axis=1)
+            nu = nrm / np.linalg.norm(nrm, axis=1)[:, None]
+            for (l1, l2, l3, w) in bary:
+                X = l1 * F3[:, 0] + l2 * F3[:, 1] + l3 * F3[:, 2]
+                q = Qx(X)
+                rho = q[:, 0]; un = u0 * nu.sum(1); pr = 1.0
+                Fx = np.stack([rho * un, rho * u0 * un + pr * nu[:, 0], rho * u0 * un + pr * nu[:, 1],
+                               rho * u0 * un + pr * nu[:, 2], (q[:, 4] + pr) * un], -1)
+                ex -= w * area[:, None] * Fx
+        err = np.abs(R[:, 0] / vol - ex[:, 0] / vol)
+        errs.append(np.sqrt(np.mean(err ** 2)))
+        hs.append(1.0 / n)
+    rates = np.log(np.array(errs[:-1]) / np.array(errs[1:])) / np.log(2)
+    assert np.all(rates >= 1.8), (errs, rates)
+
+
+def cell_average(V, f):
+    """Cell averages by a degree-3 rule (Keast 5-point) on each tetrahedron."""
+    rule = [((0.25, 0.25, 0.25, 0.25), -0.8)]
+    for k in range(4):
+        lam = [1 / 6] * 4
+        lam[k] = 0.5
+        rule.append((tuple(lam), 0.45))
+    out = 0
+    for lam, w in rule:
+        X = sum(lam[a] * V[:, a] for a in range(4))
+        out = out + w * f(X)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# implicit system (Sec. 4)
+# ---------------------------------------------------------------------------
+
+def test_euler_jacobian_vs_finite_differences():
+    rng = np.random.default_rng(31)
+    for _ in range(4):
+        Q = rand_state(rng)
+        n = rng.normal(size=3); n /= np.linalg.norm(n)
+        J = O.euler_jacobian(Q, n)
+        Jfd = np.zeros((5, 5))
+        for k in range(5):
+            h = 1e-6 * max(1, abs(Q[k]))
+            e = np.zeros(5); e[k] = h
+            Jfd[:, k] = (euler_flux(Q + e, n) - euler_flux(Q - e, n)) / (2 * h)
+        np.testing.assert_allclose(J, Jfd, rtol=1e-7, atol=1e-8)
+
+
+def test_characteristic_eigensystem():
+    rng = np.random.default_rng(37)
+    Q = rand_state(rng)
+    R, L = O.char_eigen(Q)
+    J = O.euler_jacobian(Q, np.array([1.0, 0, 0]))
+    np.testing.assert_allclose(L @ R, np.eye(5), atol=1e-13)
+    rho, u, p = prim_of(Q)
+    a = math.sqrt(GAMMA * p / rho)
+    np.testing.assert_allclose(L @ J @ R, np.diag([u[0] - a, u[0], u[0], u[0], u[0] + a]), atol=1e-12)
+
+
+def dense_A(om, diag, off):
+    n = om.nc
+    A = np.zeros((5 * n, 5 * n))
+    nb = om.neighbours
+    for i in range(n):
+        A[5 * i:5 * i + 5, 5 * i:5 * i + 5] = diag[i]
+        for q in range(4):
+            j = nb[i, q]
+            if j >= 0:
+                A[5 * i:5 * i + 5, 5 * j:5 * j + 5] += off[i, q]
+    return A
+
+
+def small_problem():
+    m = I.periodic_cube_mesh(3)          # 162 cells
+    om = O.OracleMesh(m)
+    Q, G = I.smooth_state(m, amp=0.1)
+    p = O.make_params(scheme=0, cfl=5.0)
+    return m, om, Q, G, p
+
+
+def test_jacobi_matches_dense_recursion():
+    m, om, Q, G, p = small_problem()
+    diag, off = om.jacobian(p, Q)
+    A = dense_A(om, diag, off)
+    D = np.zeros_like(A)
+    for i in range(om.nc):
+        D[5 * i:5 * i + 5, 5 * i:5 * i + 5] = diag[i]
+    b = np.random.default_rng(41).normal(size=(om.nc, 5))
+    x = np.linalg.solve(D, b.ravel())
+    for _ in range(2):
+        x = np.linalg.solve(D, b.ravel() - (A - D) @ x)
+    np.testing.assert_allclose(om.precondition(diag, off, 2, b).ravel(), x, rtol=1e-12, atol=1e-14)
+
+
+def test_full_gmres_equals_lu():
+    """GMRES with a Krylov space of the full dimension solves A x = b exactly (Sec. 4.1)."""
+    m, om, Q, G, p = small_problem()
+    diag, off = om.jacobian(p, Q)
+    A = dense_A(om, diag, off)
+    b = np.random.default_rng(43).normal(size=(om.nc, 5))
+    q = O.make_params(scheme=0, krylov_dim=5 * om.nc, restarts=1, jacobi_sweeps=2)
+    dx, _ = om.gmres(q, diag, off, b)
+    np.testing.assert_allclose(dx.ravel(), np.linalg.solve(A, b.ravel()), rtol=1e-8, atol=1e-10)
+
+
+def test_restarted_gmres_monotone():
+    m, om, Q, G, p = small_problem()
+    diag, off = om.jacobian(p, Q)
+    b = np.random.default_rng(47).normal(size=(om.nc, 5))
+    q = O.make_params(scheme=0, krylov_dim=10, restarts=4)
+    dx, hist = om.gmres(q, diag, off, b)
+    assert np.all(np.diff(hist) <= 1e-12 * hist[0])
+    assert hist[-1] < hist[0]
+
+
+def test_local_time_step_invariants():
+    """dt is linear in the CFL number and scales with the mesh size at fixed state."""
+    m1 = I.periodic_cube_mesh(4, length=1.0)
+    m2 = I.periodic_cube_mesh(4, length=2.0)
+    o1, o2 = O.OracleMesh(m1), O.OracleMesh(m2)
+    Q = I.uniform_state(m1.n_tet, u=0.2)
+    d1 = o1.local_dt(O.make_params(cfl=1.0), Q)
+    d3 = o1.local_dt(O.make_params(cfl=3.0), Q)
+    d2 = o2.local_dt(O.make_params(cfl=1.0), Q)
+    np.testing.assert_allclose(d3, 3 * d1, rtol=1e-14)
+    np.testing.assert_allclose(d2, 2 * d1, rtol=1e-12)
