@@ -1,0 +1,217 @@
+/*
+ * hgks.h -- C ABI of libhgks: the residual R(U) and the Jacobi-preconditioned
+ * restarted GMRES step of the implicit high-order gas-kinetic scheme (HGKS)
+ * on 3-D tetrahedral meshes (Yang, Pan, Xu, "Implicit high-order gas-kinetic
+ * schemes for compressible flows on three-dimensional unstructured meshes I:
+ * steady flows"), on one NVIDIA GB300 (sm_103a).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every function returns an hgks_status; 0 (HGKS_OK) is success. No
+ *    function throws, aborts or exits. hgks_last_error() returns a
+ *    thread-local, NUL-terminated description of the last failure.
+ *  - Argument errors are reported synchronously. Device-side failures are
+ *    reported by the first later call that synchronises (hgks_gmres_step,
+ *    hgks_solve_steady, the *_host variants, hgks_sync).
+ *  - A mesh handle owns all device memory it needs (geometry, stencils,
+ *    reconstruction matrices, Jacobian blocks, Krylov basis, scratch). The
+ *    caller owns the state arrays Q, G, R, G_new: device pointers unless the
+ *    name ends in _host.
+ *  - Cells are held in the library's internal order (a space-filling curve on
+ *    the cell centroids). hgks_mesh_create() returns perm_out[internal] =
+ *    caller cell index; every device array passed to the library is in the
+ *    internal order.
+ *  - Device state layouts are component-major ("structure of arrays"):
+ *      Q, R  : double[5][N]  conservative (rho, rho U, rho V, rho W, rho E)
+ *      G     : double[15][N] cell-averaged Cartesian gradients,
+ *              G[3*c + d][i] = d Q_c / d x_d  (compact scheme only)
+ *  - R is L(Q) of Eq. (semi)/(finite): |Omega_i| dQ_i/dt, NOT divided by the
+ *    cell volume; the face flux is the time average of Sec. 4.1.
+ *  - Work is enqueued on the caller's CUDA stream (cudaStream_t passed as
+ *    void*; NULL is the legacy default stream). Calls on one mesh handle must
+ *    not overlap: the handle's scratch is shared.
+ */
+#ifndef HGKS_H
+#define HGKS_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HGKS_OK = 0,
+  HGKS_ERR_ARG = 1,          /* invalid argument (NULL, size, parameter)          */
+  HGKS_ERR_MESH = 2,         /* degenerate tet, unmatched or over-shared face,
+                                singular reconstruction stencil                  */
+  HGKS_ERR_CUDA = 3,         /* a CUDA call failed                                 */
+  HGKS_ERR_OOM = 4,          /* device allocation failed                           */
+  HGKS_ERR_NONPHYSICAL = 5,  /* non-finite residual or non-positive cell state     */
+  HGKS_ERR_BREAKDOWN = 6,    /* reserved                                           */
+  HGKS_ERR_NOT_CONVERGED = 7,/* hgks_solve_steady reached max_steps                */
+  HGKS_ERR_TIMEOUT = 8       /* reserved                                           */
+} hgks_status;
+
+/* boundary tags of hgks_mesh_create (paper Sec. 5.1, 5.2) */
+enum {
+  HGKS_BC_WALL_ISO = 1,       /* isothermal no-slip wall at rest                   */
+  HGKS_BC_WALL_LID = 2,       /* isothermal no-slip wall moving with lid_speed +x   */
+  HGKS_BC_SLIP = 3,           /* adiabatic slip wall                                */
+  HGKS_BC_NOSLIP_ADIA = 4,    /* adiabatic no-slip wall                             */
+  HGKS_BC_FARFIELD = 5        /* far field (free stream)                            */
+};
+
+enum { HGKS_WENO = 0, HGKS_HWENO = 1 };           /* non-compact / compact (Sec. 3.2, 3.3) */
+enum { HGKS_NONLINEAR = 0, HGKS_LINEAR = 1 };     /* weights of Eq. (weno)                 */
+enum { HGKS_FP64 = 0, HGKS_MIXED = 1 };           /* Krylov arithmetic                     */
+
+typedef struct hgks_mesh_s *hgks_mesh;            /* opaque */
+
+/* Plain-old-data parameters, copied by every call. Defaults (paper Sec. 3.4,
+ * Sec. 4, Sec. 5): scheme WENO, nonlinear weights, characteristic variables,
+ * Krylov 10, 3 restarts, 2 Jacobi sweeps, gamma 1.4, Pr 1, CFL 10,
+ * tau_eps 0.1, tau_C 1, lin_weight 0.025; see hgks_default_params(). */
+typedef struct {
+  int32_t scheme;          /* HGKS_WENO | HGKS_HWENO                                  */
+  int32_t weights;         /* HGKS_NONLINEAR | HGKS_LINEAR                            */
+  int32_t viscous;         /* 0: tau = eps dt + C|dp|dt, 1: tau = mu/p + C|dp|dt (Sec. 5) */
+  int32_t characteristic;  /* 1: reconstruct characteristic variables (Sec. 5), 0: conservative */
+  int32_t precision;       /* HGKS_FP64 | HGKS_MIXED (FP32 Krylov basis, Arnoldi, Jacobi) */
+  int32_t jv_mode;         /* 0: assembled approximate Jacobian (Eq. (deri-matrix))    */
+  int32_t krylov_dim;      /* Arnoldi steps per restart, 1..64                        */
+  int32_t restarts;        /* GMRES cycles per implicit step                          */
+  int32_t jacobi_sweeps;   /* k_max of Eq. (precond)                                  */
+  int32_t tstar_end;       /* compact gradients from f at t = dt_flux (1) or t = 0 (0) */
+  double gamma;            /* specific heat ratio                                     */
+  double Pr;               /* Prandtl number (energy-flux fix; 1 = plain BGK)         */
+  double mu;               /* dynamic viscosity (constant)                            */
+  double cfl;              /* CFL of the implicit pseudo-time step                    */
+  double flux_cfl;         /* CFL of the time step used inside the gas-kinetic flux   */
+  double tau_eps, tau_C;   /* collision time constants of Sec. 5                      */
+  double lin_weight;       /* linear weight gamma_m of every sub-stencil              */
+  double weno_eps;         /* epsilon of the nonlinear weights                        */
+  double flux_dt;          /* > 0: fixed time step inside the flux (overrides flux_cfl) */
+  double rho_inf, u_inf[3], p_inf;  /* free stream (far field)                        */
+  double wall_T;           /* isothermal wall temperature p/rho                       */
+  double lid_speed;        /* speed of HGKS_BC_WALL_LID walls along +x                */
+} hgks_params;
+
+typedef struct {
+  int64_t n_cells, n_faces, n_boundary_faces;
+  int64_t device_bytes;      /* device memory held by the handle */
+  int32_t device;
+  int32_t schemes;           /* bit 0: WENO data present, bit 1: HWENO data present */
+} hgks_mesh_info_t;
+
+typedef struct {
+  double res_l1;             /* L1 norm of the density residual of the input state (Sec. 5) */
+  double lin_res[2];         /* preconditioned linear residual before/after GMRES          */
+  int32_t krylov_iters;      /* Arnoldi steps performed                                     */
+  int32_t nonphysical;       /* count of Gauss-point states that fell back to cell averages */
+} hgks_step_info;
+
+typedef struct {
+  int32_t steps;             /* implicit steps taken                                       */
+  int32_t converged;         /* 1 if res/res_ref <= drop_tol                                */
+  double res_ref;            /* largest density residual seen (the drop reference)         */
+  double res_final;
+} hgks_solve_info;
+
+/* Fill *p with the defaults listed above. */
+hgks_status hgks_default_params(hgks_params *p);
+
+/* Build a mesh on `device` (paper Sec. 3.1, 4.3: cells, faces, stencils and the
+ * per-cell reconstruction matrices of Eq. (polys), (compact-big-1/2)).
+ *  xyz[n_vert][3]      vertex coordinates (host, copied)
+ *  tet4[n_tet][4]      vertex indices of every tetrahedron (host, copied);
+ *                      local face p is the triangle opposite local vertex p
+ *  bface3[n_bface][3], btag[n_bface]  boundary triangles and their HGKS_BC_* tags
+ *  periodic_shift[n_periodic][3]      translations pairing the remaining faces
+ *                      (NULL / 0 if none)
+ *  scheme_mask         bit 0: build WENO data, bit 1: build HWENO data
+ *  perm_out[n_tet]     (host, may be NULL) internal index -> caller index
+ * Errors: HGKS_ERR_ARG (n_tet <= 0, NULL arrays), HGKS_ERR_MESH (degenerate or
+ * non-conforming mesh, singular stencil), HGKS_ERR_CUDA/OOM. */
+hgks_status hgks_mesh_create(const double *xyz, int64_t n_vert, const int64_t *tet4, int64_t n_tet,
+                             const int64_t *bface3, const int32_t *btag, int64_t n_bface,
+                             const double *periodic_shift, int32_t n_periodic, int32_t scheme_mask,
+                             int32_t device, hgks_mesh *out, int64_t *perm_out);
+hgks_status hgks_mesh_destroy(hgks_mesh mesh);
+hgks_status hgks_mesh_info(hgks_mesh mesh, hgks_mesh_info_t *info);
+/* Cell volumes in internal order, into a host array of n_cells doubles. */
+hgks_status hgks_mesh_volumes(hgks_mesh mesh, double *vol_host);
+
+/* Residual R = L(Q) (Eq. (finite) with the time-averaged flux of Sec. 4.1):
+ * reconstruction (Sec. 3.2/3.3 in characteristic variables, Sec. 5), the BGK
+ * flux of Eq. (flux) at 3 Gauss points per face, face-to-cell accumulation;
+ * compact scheme: G_new = cell-averaged gradients from the point values of
+ * Eq. (point) by Eq. (derivative). G and G_new are NULL for WENO.
+ * All pointers are device pointers in internal order. */
+hgks_status hgks_residual(hgks_mesh mesh, const hgks_params *p, const double *Q, const double *G,
+                          double *R, double *G_new, void *cuda_stream);
+
+/* Local time step dt[N] (device) at CFL p->cfl: dt_i = CFL |Omega_i| /
+ * sum_p S_p (|U_i.n_p| + a_i + 2 gamma mu/(Pr rho_i h_i)) (the paper gives no
+ * formula; this is the reading the library takes). */
+hgks_status hgks_local_dt(hgks_mesh mesh, const hgks_params *p, const double *Q, double *dt,
+                          void *cuda_stream);
+
+/* Assemble A of Eq. (A-system-2) with Eq. (deri-matrix) at state Q and
+ * time step dt (device arrays), into the handle. If diag_out / off_out are not
+ * NULL they receive the blocks (device, double[25][N] and double[4][25][N],
+ * row-major 5x5, off block p multiplies the neighbour across local face p;
+ * zero on boundary faces). */
+hgks_status hgks_assemble(hgks_mesh mesh, const hgks_params *p, const double *Q, const double *dt,
+                          double *diag_out, double *off_out, void *cuda_stream);
+/* y = A x with the assembled A (device double[5][N]). */
+hgks_status hgks_apply_jacobian(hgks_mesh mesh, const double *x, double *y, void *cuda_stream);
+/* x = P^{-1} b, Jacobi iteration of Eq. (precond) with `sweeps` sweeps. */
+hgks_status hgks_precondition(hgks_mesh mesh, int32_t sweeps, const double *b, double *x,
+                              void *cuda_stream);
+
+/* One pass of Algorithm 1's outer loop: time step, R(Q) (and G_new), A,
+ * `restarts` cycles of left-preconditioned GMRES(krylov_dim) with modified
+ * Gram-Schmidt, Q += dQ, and G = G_new for the compact scheme. Q, G are device
+ * arrays updated in place; dQ_out (device, may be NULL) receives the update.
+ * Synchronises the stream (to return info->res_l1). */
+hgks_status hgks_gmres_step(hgks_mesh mesh, const hgks_params *p, double *Q, double *G,
+                            double *dQ_out, hgks_step_info *info, void *cuda_stream);
+
+/* Algorithm 1 until res/res_ref <= drop_tol (res_ref = largest density
+ * residual seen) or max_steps steps. hist_host (may be NULL) receives
+ * max_steps + 1 residuals. Returns HGKS_ERR_NOT_CONVERGED if the limit was hit. */
+hgks_status hgks_solve_steady(hgks_mesh mesh, const hgks_params *p, double *Q, double *G,
+                              double drop_tol, int32_t max_steps, double *hist_host,
+                              hgks_solve_info *info, void *cuda_stream);
+
+/* Host-buffer variants: Q, G (and R, G_new) are host arrays in internal order
+ * and layout above; the copies to and from the device happen inside the call
+ * on the given stream, which is synchronised before return. */
+hgks_status hgks_residual_host(hgks_mesh mesh, const hgks_params *p, const double *Q_host,
+                               const double *G_host, double *R_host, double *G_new_host,
+                               void *cuda_stream);
+hgks_status hgks_gmres_step_host(hgks_mesh mesh, const hgks_params *p, double *Q_host,
+                                 double *G_host, hgks_step_info *info, void *cuda_stream);
+
+/* Wait for the stream and report any deferred device-side error. */
+hgks_status hgks_sync(void *cuda_stream);
+
+/* Per-kernel timing with CUDA events recorded on the launching stream around
+ * every kernel the library enqueues between hgks_profile_begin() and
+ * hgks_profile_end(). end() waits for the events and fills, for up to
+ * max_kernels kernels that ran: names (32 bytes each, NUL-terminated),
+ * total_ms and launches; *n_out = number of distinct kernels. Host state is
+ * per process; profile one stream at a time. */
+hgks_status hgks_profile_begin(void);
+hgks_status hgks_profile_end(int32_t max_kernels, char *names, double *total_ms, int64_t *launches,
+                             int32_t *n_out);
+
+/* Kernel launches made by this thread since the last reset (profiling aid). */
+int64_t hgks_launch_count(int32_t reset);
+
+const char *hgks_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

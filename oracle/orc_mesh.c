@@ -358,7 +358,9 @@ int orc_fit_cell(orc_mesh *m, int64_t i, int scheme) {
       double s[3]; int64_t j = nb_of(m, &self, p, s);
       if (j >= 0) { F->nb[F->n_nb].cell = j; for (int d = 0; d < 3; d++) F->nb[F->n_nb].shift[d] = s[d]; F->nb_slot[F->n_nb] = p; F->n_nb++; }
     }
-    int ne = F->n_nb, nls = 3 * (1 + F->n_nb), n = 9 + ne;
+    /* with fewer than 3 face neighbours (an edge of the domain) the quadratic
+     * system is singular: P0 keeps its linear terms only (nu = 3 unknowns) */
+    int ne = F->n_nb, nls = 3 * (1 + F->n_nb), nu = ne >= 3 ? 9 : 3, n = nu + ne;
     double C[4][9], B[15][9], av[9];
     for (int r = 0; r < ne; r++) {
       avg_monomials(m, i, F->nb[r].cell, F->nb[r].shift, av);
@@ -374,25 +376,25 @@ int orc_fit_cell(orc_mesh *m, int64_t i, int scheme) {
     }
     double K[(9 + 4) * (9 + 4)];
     memset(K, 0, sizeof(K));
-    for (int a = 0; a < 9; a++)
-      for (int b = 0; b < 9; b++) { double s = 0; for (int r = 0; r < nls; r++) s += B[r][a] * B[r][b]; K[a * n + b] = s; }
-    for (int r = 0; r < ne; r++) for (int d = 0; d < 9; d++) { K[d * n + 9 + r] = C[r][d]; K[(9 + r) * n + d] = C[r][d]; }
+    for (int a = 0; a < nu; a++)
+      for (int b = 0; b < nu; b++) { double s = 0; for (int r = 0; r < nls; r++) s += B[r][a] * B[r][b]; K[a * n + b] = s; }
+    for (int r = 0; r < ne; r++) for (int d = 0; d < nu; d++) { K[d * n + nu + r] = C[r][d]; K[(nu + r) * n + d] = C[r][d]; }
     memset(F->H0, 0, sizeof(F->H0));
     /* the map from data to coefficients, one data unit vector at a time */
     for (int col = 0; col < 4 + 15; col++) {
       double rhs[13] = {0}, sol[13];
       if (col < 4) {
         if (col >= ne) continue;
-        rhs[9 + col] = 1.0;
+        rhs[nu + col] = 1.0;
       } else {
         int k = (col - 4) / 3, j = (col - 4) % 3;
         if (k > ne) continue;
         const orc_sref *rk = k == 0 ? &self : &F->nb[k - 1];
         double dval = m->h[rk->cell];        /* d_row = h_k * G_kj */
-        for (int a = 0; a < 9; a++) rhs[a] = B[3 * k + j][a] * dval;
+        for (int a = 0; a < nu; a++) rhs[a] = B[3 * k + j][a] * dval;
       }
       if (orc_lu_solve(n, K, rhs, sol)) return -3;
-      for (int d = 0; d < 9; d++) F->H0[d][col] = sol[d];
+      for (int d = 0; d < nu; d++) F->H0[d][col] = sol[d];
     }
     /* compact sub-stencils {target, one face neighbour}, Eq. (compact-big-2) */
     for (int mm = 0; mm < 4; mm++) {

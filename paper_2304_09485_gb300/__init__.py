@@ -82,6 +82,8 @@ def lib():
             "hgks_residual_host": [vp, P, dp, dp, dp, dp, vp],
             "hgks_gmres_step_host": [vp, P, dp, dp, C.POINTER(hgks_step_info), vp],
             "hgks_sync": [vp],
+            "hgks_profile_begin": [],
+            "hgks_profile_end": [i32, dp, dp, dp, C.POINTER(C.c_int32)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -184,7 +186,7 @@ def hgks_mesh_volumes(mesh: hgks_mesh) -> np.ndarray:
     return v
 
 
-def hgks_residual(mesh, params, Q, G, R, G_new, stream=None):
+def hgks_residual(mesh, params, Q, G, R, G_new=None, stream=None):
     _check(lib().hgks_residual(mesh.handle, C.byref(params), _ptr(Q), _ptr(G), _ptr(R), _ptr(G_new), _stream(stream)))
 
 
@@ -234,6 +236,24 @@ def hgks_gmres_step_host(mesh, params, Q_host, G_host=None, stream=None) -> hgks
 
 def hgks_sync(stream=None):
     _check(lib().hgks_sync(_stream(stream)))
+
+
+def hgks_profile_begin():
+    _check(lib().hgks_profile_begin())
+
+
+def hgks_profile_end(max_kernels=32):
+    """{kernel name: (total ms, launches)} of the kernels timed since hgks_profile_begin()."""
+    names = C.create_string_buffer(32 * max_kernels)
+    ms = np.zeros(max_kernels)
+    cnt = np.zeros(max_kernels, dtype=np.int64)
+    n = C.c_int32(0)
+    _check(lib().hgks_profile_end(max_kernels, C.addressof(names), _ptr(ms), _ptr(cnt), C.byref(n)))
+    out = {}
+    for k in range(min(n.value, max_kernels)):
+        nm = names.raw[32 * k:32 * k + 32].split(b"\0")[0].decode()
+        out[nm] = (float(ms[k]), int(cnt[k]))
+    return out
 
 
 def hgks_launch_count(reset=False) -> int:

@@ -1,0 +1,489 @@
+// C ABI of libhgks (include/hgks.h): argument checks, device memory of a mesh
+// handle, and the orchestration of the kernels in residual.cu / implicit.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include "hgks_internal.h"
+
+using namespace hgks;
+
+struct hgks_mesh_s {
+  Mesh m;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+hgks_status fail(hgks_status st, const std::string &msg) {
+  g_err = msg;
+  return st;
+}
+hgks_status cuda_fail(cudaError_t e, const char *where) {
+  g_err = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? HGKS_ERR_OOM : HGKS_ERR_CUDA;
+}
+#define HGKS_CUDA(call)                                   \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+  } while (0)
+
+template <typename T>
+hgks_status dalloc(Mesh &m, T **p, size_t n) {
+  *p = nullptr;
+  if (n == 0) return HGKS_OK;
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, n * sizeof(T));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  m.allocs.push_back(q);
+  m.bytes += n * sizeof(T);
+  *p = (T *)q;
+  return HGKS_OK;
+}
+template <typename T>
+hgks_status upload(Mesh &m, T **p, const std::vector<T> &v) {
+  hgks_status st = dalloc(m, p, v.size());
+  if (st) return st;
+  if (!v.empty()) HGKS_CUDA(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return HGKS_OK;
+}
+
+void free_all(Mesh &m) {
+  for (void *p : m.allocs) cudaFree(p);
+  m.allocs.clear();
+}
+
+hgks_status check_params(const Mesh &m, const hgks_params *p) {
+  if (!p) return fail(HGKS_ERR_ARG, "params is NULL");
+  if (p->scheme != HGKS_WENO && p->scheme != HGKS_HWENO) return fail(HGKS_ERR_ARG, "unknown scheme");
+  if (!(m.schemes & (p->scheme == HGKS_WENO ? 1 : 2))) return fail(HGKS_ERR_ARG, "mesh was built without data for this scheme");
+  if (p->krylov_dim < 1 || p->krylov_dim > 64) return fail(HGKS_ERR_ARG, "krylov_dim must be in 1..64");
+  if (p->restarts < 0 || p->jacobi_sweeps < 0) return fail(HGKS_ERR_ARG, "negative restarts or sweeps");
+  if (!(p->gamma > 1.0) || !(p->cfl > 0.0) || !(p->flux_cfl > 0.0) || !(p->Pr > 0.0)) return fail(HGKS_ERR_ARG, "gamma, cfl, flux_cfl, Pr out of range");
+  if (p->viscous && !(p->mu > 0.0)) return fail(HGKS_ERR_ARG, "viscous flow needs mu > 0");
+  if (!p->viscous && !(p->tau_eps > 0.0)) return fail(HGKS_ERR_ARG, "inviscid flow needs tau_eps > 0");
+  if (p->precision != HGKS_FP64 && p->precision != HGKS_MIXED) return fail(HGKS_ERR_ARG, "unknown precision");
+  if (p->jv_mode != 0) return fail(HGKS_ERR_ARG, "only the assembled Jacobian is available");
+  return HGKS_OK;
+}
+
+// Scratch of the residual (always) and of the implicit solve (lazily, per Krylov size)
+hgks_status ensure_scratch(Mesh &m, int kdim, bool implicit) {
+  Scratch &s = m.s;
+  const size_t N = m.N, F = m.F;
+  if (!s.coef) {
+    hgks_status st;
+    if ((st = dalloc(m, &s.coef, (size_t)kCoef * N))) return st;
+    if ((st = dalloc(m, &s.dt, N))) return st;
+    if ((st = dalloc(m, &s.wface, (size_t)2 * 3 * kFaceState * F))) return st;
+    if ((st = dalloc(m, &s.fflux, (size_t)15 * F))) return st;
+    if ((st = dalloc(m, &s.fpt, (size_t)15 * F))) return st;
+    if ((st = dalloc(m, &s.flags, 8))) return st;
+    if ((st = dalloc(m, &s.red, 1024))) return st;
+    if ((st = dalloc(m, &s.red_count, 4))) return st;
+    HGKS_CUDA(cudaMemset(s.flags, 0, 8 * sizeof(int)));
+    HGKS_CUDA(cudaMemset(s.red_count, 0, 4 * sizeof(unsigned)));
+    HGKS_CUDA(cudaMemset(s.wface, 0, sizeof(double) * 2 * 3 * kFaceState * F));
+  }
+  if (implicit && !s.off) {
+    hgks_status st;
+    if ((st = dalloc(m, &s.off, (size_t)2 * 25 * F))) return st;
+    if ((st = dalloc(m, &s.dval, N))) return st;
+    if ((st = dalloc(m, &s.dinv, N))) return st;
+    if ((st = dalloc(m, &s.R, 5 * N))) return st;
+    if ((st = dalloc(m, &s.Gnew, 15 * N))) return st;
+    if ((st = dalloc(m, &s.dQ, 5 * N))) return st;
+    if ((st = dalloc(m, &s.w, 5 * N))) return st;
+    if ((st = dalloc(m, &s.t, 5 * N))) return st;
+    if ((st = dalloc(m, &s.t2, 5 * N))) return st;
+    if ((st = dalloc(m, &s.hs, 65 * 64 + 256))) return st;
+    HGKS_CUDA(cudaMemset(s.off, 0, sizeof(double) * 2 * 25 * F));
+  }
+  if (implicit && kdim > s.kdim) {
+    if (s.V) {
+      cudaFree(s.V);
+      for (auto &p : m.allocs) if (p == s.V) p = nullptr;
+      m.bytes -= sizeof(double) * (size_t)(s.kdim + 1) * 5 * N;
+      s.V = nullptr;
+    }
+    hgks_status st;
+    if ((st = dalloc(m, &s.V, (size_t)(kdim + 1) * 5 * N))) return st;
+    s.kdim = kdim;
+  }
+  return HGKS_OK;
+}
+
+hgks_status set_device(const Mesh &m) {
+  HGKS_CUDA(cudaSetDevice(m.device));
+  return HGKS_OK;
+}
+
+hgks_status last_launch() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return HGKS_OK;
+}
+
+}  // namespace
+
+namespace hgks {
+bool g_prof_on = false;
+namespace {
+struct ProfRec { int kid; cudaEvent_t a, b; };
+std::vector<ProfRec> g_prof_recs;
+std::vector<cudaEvent_t> g_prof_pool;
+int g_prof_open = -1;
+const char *kKernelNames[K_COUNT] = {"local_dt", "coef", "recon", "flux", "gather", "assemble", "spmv", "jacobi",
+                                     "diag_scale", "axpy_dot", "scale", "givens", "combine", "update", "density_l1"};
+cudaEvent_t prof_event() {
+  if (!g_prof_pool.empty()) { cudaEvent_t e = g_prof_pool.back(); g_prof_pool.pop_back(); return e; }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+}  // namespace
+void prof_mark(int kid, cudaStream_t st, bool begin) {
+  if (begin) {
+    ProfRec r{kid, prof_event(), prof_event()};
+    cudaEventRecord(r.a, st);
+    g_prof_recs.push_back(r);
+    g_prof_open = (int)g_prof_recs.size() - 1;
+  } else if (g_prof_open >= 0) {
+    cudaEventRecord(g_prof_recs[g_prof_open].b, st);
+    g_prof_open = -1;
+  }
+}
+}  // namespace hgks
+
+extern "C" {
+
+hgks_status hgks_profile_begin(void) {
+  for (auto &r : g_prof_recs) { g_prof_pool.push_back(r.a); g_prof_pool.push_back(r.b); }
+  g_prof_recs.clear();
+  g_prof_on = true;
+  return HGKS_OK;
+}
+
+hgks_status hgks_profile_end(int32_t max_kernels, char *names, double *total_ms, int64_t *launches, int32_t *n_out) {
+  g_prof_on = false;
+  if (!n_out) return fail(HGKS_ERR_ARG, "n_out is NULL");
+  double tot[K_COUNT] = {0};
+  int64_t cnt[K_COUNT] = {0};
+  for (auto &r : g_prof_recs) {
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    tot[r.kid] += ms;
+    cnt[r.kid]++;
+  }
+  int n = 0;
+  for (int k = 0; k < K_COUNT; k++) {
+    if (!cnt[k]) continue;
+    if (n < max_kernels) {
+      if (names) { std::strncpy(names + 32 * n, kKernelNames[k], 31); names[32 * n + 31] = 0; }
+      if (total_ms) total_ms[n] = tot[k];
+      if (launches) launches[n] = cnt[k];
+    }
+    n++;
+  }
+  *n_out = n;
+  return HGKS_OK;
+}
+
+
+const char *hgks_last_error(void) { return g_err.c_str(); }
+
+int64_t hgks_launch_count(int32_t reset) {
+  int64_t v = g_launches;
+  if (reset) g_launches = 0;
+  return v;
+}
+
+hgks_status hgks_default_params(hgks_params *p) {
+  if (!p) return fail(HGKS_ERR_ARG, "params is NULL");
+  std::memset(p, 0, sizeof(*p));
+  p->scheme = HGKS_WENO; p->weights = HGKS_NONLINEAR; p->viscous = 0; p->characteristic = 1;
+  p->precision = HGKS_FP64; p->jv_mode = 0; p->krylov_dim = 10; p->restarts = 3; p->jacobi_sweeps = 2;
+  p->tstar_end = 1; p->gamma = 1.4; p->Pr = 1.0; p->mu = 0.0; p->cfl = 10.0; p->flux_cfl = 1.0;
+  p->tau_eps = 0.1; p->tau_C = 1.0; p->lin_weight = 0.025; p->weno_eps = 1e-8; p->flux_dt = 0.0;
+  p->rho_inf = 1.0; p->u_inf[0] = 0.3; p->p_inf = 1.0 / 1.4; p->wall_T = 1.0 / 1.4; p->lid_speed = 0.0;
+  return HGKS_OK;
+}
+
+hgks_status hgks_mesh_create(const double *xyz, int64_t n_vert, const int64_t *tet4, int64_t n_tet,
+                             const int64_t *bface3, const int32_t *btag, int64_t n_bface,
+                             const double *periodic_shift, int32_t n_periodic, int32_t scheme_mask,
+                             int32_t device, hgks_mesh *out, int64_t *perm_out) {
+  if (!out) return fail(HGKS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if ((scheme_mask & 3) == 0) return fail(HGKS_ERR_ARG, "scheme_mask selects no scheme");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) return fail(HGKS_ERR_CUDA, "no CUDA device");
+  if (device < 0 || device >= ndev) return fail(HGKS_ERR_ARG, "device index out of range");
+  HostMesh hm;
+  std::string err;
+  hgks_status st = build_host_mesh(xyz, n_vert, tet4, n_tet, bface3, btag, n_bface, periodic_shift, n_periodic,
+                                   scheme_mask & 3, hm, err);
+  if (st) return fail(st, err);
+  hgks_mesh_s *h = new (std::nothrow) hgks_mesh_s;
+  if (!h) return fail(HGKS_ERR_OOM, "host allocation");
+  Mesh &m = h->m;
+  m.device = device;
+  m.N = hm.N; m.F = hm.F; m.Fb = hm.Fb; m.schemes = scheme_mask & 3;
+  auto bail = [&](hgks_status s2) { free_all(m); delete h; return s2; };
+  if ((st = set_device(m))) return bail(st);
+  DevMesh &d = m.d;
+  d.N = (int)hm.N; d.F = (int)hm.F;
+  std::vector<double> inv_vol(hm.N);
+  for (int64_t i = 0; i < hm.N; i++) inv_vol[i] = 1.0 / hm.vol[i];
+  if ((st = upload(m, &d.vol, hm.vol)) || (st = upload(m, &d.inv_vol, inv_vol)) || (st = upload(m, &d.h, hm.h)) ||
+      (st = upload(m, &d.m2, hm.m2)) || (st = upload(m, &d.cnb, hm.cnb)) || (st = upload(m, &d.cface, hm.cface)) ||
+      (st = upload(m, &d.xg, hm.xg)) || (st = upload(m, &d.sten, hm.sten)) || (st = upload(m, &d.X0, hm.X0)) ||
+      (st = upload(m, &d.Xm, hm.Xm)) || (st = upload(m, &d.subvalid, hm.subvalid)) || (st = upload(m, &d.H0, hm.H0)) ||
+      (st = upload(m, &d.Hm, hm.Hm)) || (st = upload(m, &d.fl, hm.fl)) || (st = upload(m, &d.fr, hm.fr)) ||
+      (st = upload(m, &d.ftag, hm.ftag)) || (st = upload(m, &d.fT, hm.fT)) || (st = upload(m, &d.fS, hm.fS)) ||
+      (st = upload(m, &d.fdist, hm.fdist)))
+    return bail(st);
+  if ((st = ensure_scratch(m, 0, false))) return bail(st);
+  m.vol_host = hm.vol;
+  if (perm_out) std::memcpy(perm_out, hm.perm.data(), sizeof(int64_t) * hm.N);
+  *out = h;
+  return HGKS_OK;
+}
+
+hgks_status hgks_mesh_destroy(hgks_mesh mesh) {
+  if (!mesh) return fail(HGKS_ERR_ARG, "mesh is NULL");
+  cudaSetDevice(mesh->m.device);
+  free_all(mesh->m);
+  delete mesh;
+  return HGKS_OK;
+}
+
+hgks_status hgks_mesh_info(hgks_mesh mesh, hgks_mesh_info_t *info) {
+  if (!mesh || !info) return fail(HGKS_ERR_ARG, "NULL argument");
+  info->n_cells = mesh->m.N; info->n_faces = mesh->m.F; info->n_boundary_faces = mesh->m.Fb;
+  info->device_bytes = (int64_t)mesh->m.bytes; info->device = mesh->m.device; info->schemes = mesh->m.schemes;
+  return HGKS_OK;
+}
+
+hgks_status hgks_mesh_volumes(hgks_mesh mesh, double *vol_host) {
+  if (!mesh || !vol_host) return fail(HGKS_ERR_ARG, "NULL argument");
+  std::memcpy(vol_host, mesh->m.vol_host.data(), sizeof(double) * mesh->m.N);
+  return HGKS_OK;
+}
+
+hgks_status hgks_residual(hgks_mesh mesh, const hgks_params *p, const double *Q, const double *G, double *R,
+                          double *G_new, void *cuda_stream) {
+  if (!mesh) return fail(HGKS_ERR_ARG, "mesh is NULL");
+  Mesh &m = mesh->m;
+  hgks_status st = check_params(m, p);
+  if (st) return st;
+  if (!Q || !R) return fail(HGKS_ERR_ARG, "Q or R is NULL");
+  if (p->scheme == HGKS_HWENO && (!G || !G_new)) return fail(HGKS_ERR_ARG, "compact scheme needs G and G_new");
+  if ((st = set_device(m))) return st;
+  if ((st = ensure_scratch(m, 0, false))) return st;
+  launch_residual(m.d, m.s, *p, Q, G, R, G_new, (cudaStream_t)cuda_stream);
+  return last_launch();
+}
+
+hgks_status hgks_local_dt(hgks_mesh mesh, const hgks_params *p, const double *Q, double *dt, void *cuda_stream) {
+  if (!mesh) return fail(HGKS_ERR_ARG, "mesh is NULL");
+  Mesh &m = mesh->m;
+  hgks_status st = check_params(m, p);
+  if (st) return st;
+  if (!Q || !dt) return fail(HGKS_ERR_ARG, "Q or dt is NULL");
+  if ((st = set_device(m))) return st;
+  launch_local_dt(m.d, *p, Q, dt, (cudaStream_t)cuda_stream);
+  return last_launch();
+}
+
+hgks_status hgks_assemble(hgks_mesh mesh, const hgks_params *p, const double *Q, const double *dt, double *diag_out,
+                          double *off_out, void *cuda_stream) {
+  if (!mesh) return fail(HGKS_ERR_ARG, "mesh is NULL");
+  Mesh &m = mesh->m;
+  hgks_status st = check_params(m, p);
+  if (st) return st;
+  if (!Q || !dt) return fail(HGKS_ERR_ARG, "Q or dt is NULL");
+  if ((st = set_device(m))) return st;
+  if ((st = ensure_scratch(m, p->krylov_dim, true))) return st;
+  launch_assemble(m.d, m.s, *p, Q, dt, diag_out, off_out, (cudaStream_t)cuda_stream);
+  return last_launch();
+}
+
+hgks_status hgks_apply_jacobian(hgks_mesh mesh, const double *x, double *y, void *cuda_stream) {
+  if (!mesh || !x || !y) return fail(HGKS_ERR_ARG, "NULL argument");
+  Mesh &m = mesh->m;
+  if (!m.s.off) return fail(HGKS_ERR_ARG, "hgks_assemble has not been called");
+  hgks_status st;
+  if ((st = set_device(m))) return st;
+  launch_apply_A(m.d, m.s, x, y, (cudaStream_t)cuda_stream);
+  return last_launch();
+}
+
+hgks_status hgks_precondition(hgks_mesh mesh, int32_t sweeps, const double *b, double *x, void *cuda_stream) {
+  if (!mesh || !b || !x) return fail(HGKS_ERR_ARG, "NULL argument");
+  if (b == x) return fail(HGKS_ERR_ARG, "b and x must not alias");
+  if (sweeps < 0) return fail(HGKS_ERR_ARG, "negative sweeps");
+  Mesh &m = mesh->m;
+  if (!m.s.off) return fail(HGKS_ERR_ARG, "hgks_assemble has not been called");
+  hgks_status st;
+  if ((st = set_device(m))) return st;
+  launch_precondition(m.d, m.s, sweeps, b, x, (cudaStream_t)cuda_stream);
+  return last_launch();
+}
+
+static hgks_status gmres_step_impl(Mesh &m, const hgks_params *p, double *Q, double *G, double *dQ_out,
+                                   hgks_step_info *info, cudaStream_t st_) {
+  const DevMesh &d = m.d;
+  Scratch &s = m.s;
+  launch_residual(d, s, *p, Q, G, s.R, p->scheme == HGKS_HWENO ? s.Gnew : nullptr, st_);
+  double *res_dev = s.hs + 65 * 64 + 200;
+  launch_density_l1(d, s, s.R, res_dev, st_);
+  launch_assemble(d, s, *p, Q, s.dt, nullptr, nullptr, st_);
+  hgks_status st = gmres_solve(d, s, *p, s.R, s.dQ, info, st_);
+  if (st) return st;
+  if (dQ_out) HGKS_CUDA(cudaMemcpyAsync(dQ_out, s.dQ, sizeof(double) * 5 * m.N, cudaMemcpyDeviceToDevice, st_));
+  launch_update(d, Q, s.dQ, G, s.Gnew, p->scheme == HGKS_HWENO ? 15 : 0, st_);
+  if ((st = last_launch())) return st;
+  double host[3];
+  const int mk = p->krylov_dim;
+  HGKS_CUDA(cudaMemcpyAsync(host, res_dev, sizeof(double), cudaMemcpyDeviceToHost, st_));
+  HGKS_CUDA(cudaMemcpyAsync(host + 1, s.hs + (mk + 1) * mk + 1 + mk, 2 * sizeof(double), cudaMemcpyDeviceToHost, st_));
+  int nonphys = 0;
+  HGKS_CUDA(cudaMemcpyAsync(&nonphys, s.flags, sizeof(int), cudaMemcpyDeviceToHost, st_));
+  HGKS_CUDA(cudaMemsetAsync(s.flags, 0, sizeof(int), st_));
+  HGKS_CUDA(cudaStreamSynchronize(st_));
+  const double res = host[0] / (double)m.N;
+  if (info) {
+    info->res_l1 = res;
+    info->lin_res[0] = host[1];
+    info->lin_res[1] = host[2];
+    info->nonphysical = nonphys;
+  }
+  if (!std::isfinite(res)) return fail(HGKS_ERR_NONPHYSICAL, "non-finite residual");
+  return HGKS_OK;
+}
+
+hgks_status hgks_gmres_step(hgks_mesh mesh, const hgks_params *p, double *Q, double *G, double *dQ_out,
+                            hgks_step_info *info, void *cuda_stream) {
+  if (!mesh) return fail(HGKS_ERR_ARG, "mesh is NULL");
+  Mesh &m = mesh->m;
+  hgks_status st = check_params(m, p);
+  if (st) return st;
+  if (!Q) return fail(HGKS_ERR_ARG, "Q is NULL");
+  if (p->scheme == HGKS_HWENO && !G) return fail(HGKS_ERR_ARG, "compact scheme needs G");
+  if ((st = set_device(m))) return st;
+  if ((st = ensure_scratch(m, p->krylov_dim, true))) return st;
+  if (info) std::memset(info, 0, sizeof(*info));
+  return gmres_step_impl(m, p, Q, G, dQ_out, info, (cudaStream_t)cuda_stream);
+}
+
+hgks_status hgks_solve_steady(hgks_mesh mesh, const hgks_params *p, double *Q, double *G, double drop_tol,
+                              int32_t max_steps, double *hist_host, hgks_solve_info *info, void *cuda_stream) {
+  if (!mesh) return fail(HGKS_ERR_ARG, "mesh is NULL");
+  Mesh &m = mesh->m;
+  hgks_status st = check_params(m, p);
+  if (st) return st;
+  if (!Q || (p->scheme == HGKS_HWENO && !G)) return fail(HGKS_ERR_ARG, "Q (or G) is NULL");
+  if (!(drop_tol > 0.0) || max_steps < 0) return fail(HGKS_ERR_ARG, "drop_tol must be > 0 and max_steps >= 0");
+  if ((st = set_device(m))) return st;
+  if ((st = ensure_scratch(m, p->krylov_dim, true))) return st;
+  cudaStream_t s_ = (cudaStream_t)cuda_stream;
+  double ref = 0.0, res = 0.0;
+  int k = 0;
+  bool conv = false;
+  for (;; k++) {
+    // the residual of the current state decides; the step then updates it
+    launch_residual(m.d, m.s, *p, Q, G, m.s.R, p->scheme == HGKS_HWENO ? m.s.Gnew : nullptr, s_);
+    double *res_dev = m.s.hs + 65 * 64 + 200;
+    launch_density_l1(m.d, m.s, m.s.R, res_dev, s_);
+    double h = 0.0;
+    HGKS_CUDA(cudaMemcpyAsync(&h, res_dev, sizeof(double), cudaMemcpyDeviceToHost, s_));
+    HGKS_CUDA(cudaStreamSynchronize(s_));
+    res = h / (double)m.N;
+    if (!std::isfinite(res)) { st = fail(HGKS_ERR_NONPHYSICAL, "non-finite residual"); break; }
+    if (hist_host) hist_host[k] = res;
+    if (res > ref) ref = res;
+    if (res <= drop_tol * ref) { conv = true; break; }
+    if (k >= max_steps) break;
+    hgks_step_info si;
+    if ((st = gmres_step_impl(m, p, Q, G, nullptr, &si, s_))) break;
+  }
+  if (info) { info->steps = k; info->converged = conv; info->res_ref = ref; info->res_final = res; }
+  if (st) return st;
+  if (!conv) return fail(HGKS_ERR_NOT_CONVERGED, "max_steps reached");
+  return HGKS_OK;
+}
+
+// device copies of host-side state for the *_host entry points: Q, G, R, G_new
+static hgks_status host_state_buffer(Mesh &m, double **buf) {
+  if (!m.s.hostbuf) {
+    hgks_status st = dalloc(m, &m.s.hostbuf, 40 * (size_t)m.N);
+    if (st) return st;
+  }
+  *buf = m.s.hostbuf;
+  return HGKS_OK;
+}
+
+hgks_status hgks_residual_host(hgks_mesh mesh, const hgks_params *p, const double *Q_host, const double *G_host,
+                               double *R_host, double *G_new_host, void *cuda_stream) {
+  if (!mesh) return fail(HGKS_ERR_ARG, "mesh is NULL");
+  Mesh &m = mesh->m;
+  hgks_status st = check_params(m, p);
+  if (st) return st;
+  const bool compact = p->scheme == HGKS_HWENO;
+  if (!Q_host || !R_host || (compact && (!G_host || !G_new_host))) return fail(HGKS_ERR_ARG, "NULL host array");
+  if ((st = set_device(m))) return st;
+  if ((st = ensure_scratch(m, 0, false))) return st;
+  double *buf;
+  if ((st = host_state_buffer(m, &buf))) return st;
+  const size_t N = m.N;
+  double *Qd = buf, *Gd = buf + 5 * N, *Rd = buf + 20 * N, *Gn = buf + 25 * N;
+  cudaStream_t s_ = (cudaStream_t)cuda_stream;
+  HGKS_CUDA(cudaMemcpyAsync(Qd, Q_host, 5 * N * sizeof(double), cudaMemcpyHostToDevice, s_));
+  if (compact) HGKS_CUDA(cudaMemcpyAsync(Gd, G_host, 15 * N * sizeof(double), cudaMemcpyHostToDevice, s_));
+  launch_residual(m.d, m.s, *p, Qd, compact ? Gd : nullptr, Rd, compact ? Gn : nullptr, s_);
+  if ((st = last_launch())) return st;
+  HGKS_CUDA(cudaMemcpyAsync(R_host, Rd, 5 * N * sizeof(double), cudaMemcpyDeviceToHost, s_));
+  if (compact) HGKS_CUDA(cudaMemcpyAsync(G_new_host, Gn, 15 * N * sizeof(double), cudaMemcpyDeviceToHost, s_));
+  HGKS_CUDA(cudaStreamSynchronize(s_));
+  return HGKS_OK;
+}
+
+hgks_status hgks_gmres_step_host(hgks_mesh mesh, const hgks_params *p, double *Q_host, double *G_host,
+                                 hgks_step_info *info, void *cuda_stream) {
+  if (!mesh) return fail(HGKS_ERR_ARG, "mesh is NULL");
+  Mesh &m = mesh->m;
+  hgks_status st = check_params(m, p);
+  if (st) return st;
+  const bool compact = p->scheme == HGKS_HWENO;
+  if (!Q_host || (compact && !G_host)) return fail(HGKS_ERR_ARG, "NULL host array");
+  if ((st = set_device(m))) return st;
+  if ((st = ensure_scratch(m, p->krylov_dim, true))) return st;
+  double *buf;
+  if ((st = host_state_buffer(m, &buf))) return st;
+  const size_t N = m.N;
+  double *Qd = buf, *Gd = buf + 5 * N;
+  cudaStream_t s_ = (cudaStream_t)cuda_stream;
+  HGKS_CUDA(cudaMemcpyAsync(Qd, Q_host, 5 * N * sizeof(double), cudaMemcpyHostToDevice, s_));
+  if (compact) HGKS_CUDA(cudaMemcpyAsync(Gd, G_host, 15 * N * sizeof(double), cudaMemcpyHostToDevice, s_));
+  if (info) std::memset(info, 0, sizeof(*info));
+  if ((st = gmres_step_impl(m, p, Qd, compact ? Gd : nullptr, nullptr, info, s_))) return st;
+  HGKS_CUDA(cudaMemcpyAsync(Q_host, Qd, 5 * N * sizeof(double), cudaMemcpyDeviceToHost, s_));
+  if (compact) HGKS_CUDA(cudaMemcpyAsync(G_host, Gd, 15 * N * sizeof(double), cudaMemcpyDeviceToHost, s_));
+  HGKS_CUDA(cudaStreamSynchronize(s_));
+  return HGKS_OK;
+}
+
+hgks_status hgks_sync(void *cuda_stream) {
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  return HGKS_OK;
+}
+
+}  // extern "C"

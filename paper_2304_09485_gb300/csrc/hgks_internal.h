@@ -1,0 +1,130 @@
+// Internal declarations of libhgks (not part of the C ABI).
+//
+// Device data of one mesh, in the library's internal (space-filling-curve)
+// cell order, component-major ("structure of arrays") so that a warp of
+// consecutive cells reads consecutive addresses:
+//   per cell  (N): volume, 1/volume, h = vol^(1/3), second moments, neighbours,
+//                  faces, Gauss points in the cell's scaled frame, fits
+//   per face  (F): left/right cell, boundary tag, frame (n, t1, t2), area
+#pragma once
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+#include <cuda_runtime.h>
+#include "../../include/hgks.h"
+
+namespace hgks {
+
+constexpr int kBig = 16;        // non-compact big stencil size (excluding the target)
+constexpr int kSub = 4;         // sub-stencils per tetrahedron
+constexpr int kCoefA = 45;      // quadratic coefficients: 9 x 5
+constexpr int kCoef = 105;      // + 4 linear sub-polynomials: 4 x 3 x 5
+constexpr int kFaceState = 20;  // W[5] + dW[3][5] at one Gauss point, face frame
+
+struct DevMesh {
+  int N = 0, F = 0;
+  // cells
+  double *vol = nullptr, *inv_vol = nullptr, *h = nullptr;
+  double *m2 = nullptr;          // [6][N] avg over the cell of xh_a xh_b: xx,yy,zz,xy,xz,yz
+  int *cnb = nullptr;            // [4][N] neighbour across local face p, -1 on a boundary
+  int *cface = nullptr;          // [4][N] 2*face + side (side 0: the cell is the face's left)
+  double *xg = nullptr;          // [36][N] Gauss points of face slot p: (p*3+g)*3+d, scaled frame
+  // non-compact (WENO)
+  int *sten = nullptr;           // [16][N] big stencil, -1 padded
+  double *X0 = nullptr;          // [9*16][N] a_d = sum_k X0[d*16+k] (Q_k - Q_i)
+  double *Xm = nullptr;          // [4*3*16][N] b_j^m = sum_k Xm[(m*3+j)*16+k] (Q_k - Q_i)
+  unsigned char *subvalid = nullptr;  // [N] bit m: sub-stencil m used
+  // compact (HWENO)
+  double *H0 = nullptr;          // [9*19][N] a_d from (dQ of slots 0..3, G_i, G of slots 0..3)
+  double *Hm = nullptr;          // [4*3*7][N] b^m from (dQ_m, G_i, G_m)
+  // faces
+  int *fl = nullptr, *fr = nullptr;   // [F] left/right cell, fr = -1 on a boundary
+  signed char *ftag = nullptr;        // [F] boundary tag, 0 inside
+  double *fT = nullptr;          // [9][F] rows n, t1, t2 (n from left to right)
+  double *fS = nullptr;          // [F] area
+  double *fdist = nullptr;       // [F] |x_L - x_R| (or twice the wall distance on a boundary)
+};
+
+struct Scratch {
+  double *coef = nullptr;        // [105][N]
+  double *dt = nullptr;          // [N]
+  double *wface = nullptr;       // [2][3][20][F] reconstructed states at Gauss points
+  double *fflux = nullptr;       // [3][5][F] global-frame flux * area / 3
+  double *fpt = nullptr;         // [3][5][F] global-frame point values * area / 3
+  // implicit
+  double *dinv = nullptr, *dval = nullptr;  // [N] the diagonal block is (|Omega|/dt + sum lambda S/2) I
+  double *off = nullptr;         // [2][25][F]: side s = row cell, block multiplies the other cell
+  float *off32 = nullptr;        // [2][25][F] FP32 copy (mixed precision)
+  float *dinv32 = nullptr;
+  double *R = nullptr, *Gnew = nullptr, *dQ = nullptr;   // [5][N], [15][N], [5][N]
+  double *V = nullptr;           // [(m+1)][5N] Krylov basis (FP64)
+  float *V32 = nullptr;          // [(m+1)][5N] Krylov basis (FP32)
+  double *w = nullptr, *t = nullptr, *t2 = nullptr;      // [5N]
+  float *w32 = nullptr, *t32 = nullptr, *t232 = nullptr;
+  double *red = nullptr;         // reduction partials
+  unsigned int *red_count = nullptr;
+  double *hs = nullptr;          // small device scalars: H, beta, y, norms
+  int *flags = nullptr;          // [8] device flags (nonphysical count, breakdown)
+  double *hostbuf = nullptr;     // [40][N] device state of the *_host entry points
+  int kdim = 0;
+  size_t bytes = 0;
+};
+
+struct Mesh {
+  int device = 0;
+  int64_t N = 0, F = 0, Fb = 0;
+  int schemes = 0;
+  DevMesh d;
+  Scratch s;
+  std::vector<double> vol_host;
+  size_t bytes = 0;
+  std::vector<void *> allocs;
+};
+
+// ---- host mesh construction (mesh_setup.cpp) ----
+struct HostMesh {
+  int64_t N = 0, F = 0, Fb = 0;
+  std::vector<int64_t> perm;             // internal -> caller
+  std::vector<double> vol, h, m2, xg;    // SoA-ready, internal order
+  std::vector<int> cnb, cface, sten, fl, fr;
+  std::vector<signed char> ftag;
+  std::vector<unsigned char> subvalid;
+  std::vector<double> X0, Xm, H0, Hm, fT, fS, fdist;
+};
+hgks_status build_host_mesh(const double *xyz, int64_t nv, const int64_t *tet, int64_t nt,
+                            const int64_t *bface, const int32_t *btag, int64_t nb,
+                            const double *pshift, int32_t nps, int scheme_mask, HostMesh &hm,
+                            std::string &err);
+
+// ---- kernels (residual.cu, implicit.cu) ----
+void launch_local_dt(const DevMesh &m, const hgks_params &p, const double *Q, double *dt, cudaStream_t st);
+void launch_residual(const DevMesh &m, Scratch &s, const hgks_params &p, const double *Q, const double *G,
+                     double *R, double *Gnew, cudaStream_t st);
+void launch_assemble(const DevMesh &m, Scratch &s, const hgks_params &p, const double *Q, const double *dt,
+                     double *diag_out, double *off_out, cudaStream_t st);
+void launch_apply_A(const DevMesh &m, const Scratch &s, const double *x, double *y, cudaStream_t st);
+void launch_precondition(const DevMesh &m, Scratch &s, int sweeps, const double *b, double *x, cudaStream_t st);
+hgks_status gmres_solve(const DevMesh &m, Scratch &s, const hgks_params &p, const double *rhs, double *dx,
+                        hgks_step_info *info, cudaStream_t st);
+void launch_density_l1(const DevMesh &m, Scratch &s, const double *R, double *out_dev, cudaStream_t st);
+void launch_update(const DevMesh &m, double *Q, const double *dQ, double *G, const double *Gnew, int ncomp_g,
+                   cudaStream_t st);
+
+extern thread_local int64_t g_launches;
+inline void count_launch() { ++g_launches; }
+
+// Optional per-kernel timing with CUDA events on the launching stream
+// (hgks_profile_begin / hgks_profile_end). Off by default: one branch per launch.
+enum KernelId { K_DT, K_COEF, K_RECON, K_FLUX, K_GATHER, K_ASSEMBLE, K_SPMV, K_JACOBI, K_DIAG, K_DOT, K_SCALE,
+                K_GIVENS, K_COMBINE, K_UPDATE, K_NORM, K_COUNT };
+extern bool g_prof_on;
+void prof_mark(int kid, cudaStream_t st, bool begin);
+#define HGKS_PROF_BEGIN(kid, st) do { if (hgks::g_prof_on) hgks::prof_mark((kid), (st), true); } while (0)
+#define HGKS_PROF_END(kid, st) do { if (hgks::g_prof_on) hgks::prof_mark((kid), (st), false); hgks::count_launch(); } while (0)
+inline unsigned grid_for(int64_t n, int block) {
+  int64_t g = (n + block - 1) / block;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+}  // namespace hgks

@@ -1,0 +1,731 @@
+// Residual R(U) of the implicit HGKS (paper Eq. (finite), Sec. 4.1), FP64.
+//
+// Four kernels per evaluation, all on the caller's stream:
+//  1. k_coef    one thread per (cell, conservative component): polynomial
+//               coefficients of Eq. (polys) = per-cell fit matrix x stencil data
+//               (non-compact: Q_k - Q_i over the big stencil; compact: Q_k - Q_i
+//               of the face neighbours and the cell-averaged gradients).
+//  2. k_recon   one thread per (cell, local face): characteristic projection at
+//               Q* (Sec. 5), smoothness indicators and nonlinear weights of
+//               Eq. (weno), values and directional derivatives at the face's 3
+//               Gauss points, written in characteristic variables.
+//  3. k_flux    one thread per (face, Gauss point): back-projection with the
+//               face's R* (shared by both sides), positivity fallback, boundary
+//               state, the BGK flux of Eq. (flux) averaged over [0, dt] and, for
+//               the compact scheme, the point value of Eq. (point).
+//  4. k_gather  one thread per cell: R_i = -sum of its faces' fluxes (signed),
+//               compact G_new_i = sum of point values * n * S / |Omega_i|
+//               (Eq. (derivative)). Gather, not scatter: no atomics, and the
+//               summation order is fixed (deterministic results).
+// Arrays are component-major with the cell or face index fastest, so
+// consecutive threads touch consecutive addresses.
+#include <cmath>
+#include "hgks_internal.h"
+
+namespace hgks {
+
+thread_local int64_t g_launches = 0;
+
+namespace {
+
+constexpr int kBlock = 128;
+
+struct Prim { double rho, U, V, W, lam; };
+
+__device__ __forceinline__ Prim to_prim(const double *Q, double gamma) {
+  Prim p;
+  p.rho = Q[0];
+  double ir = 1.0 / Q[0];
+  p.U = Q[1] * ir; p.V = Q[2] * ir; p.W = Q[3] * ir;
+  double pr = (gamma - 1.0) * (Q[4] - 0.5 * Q[0] * (p.U * p.U + p.V * p.V + p.W * p.W));
+  p.lam = 0.5 * Q[0] / pr;
+  return p;
+}
+
+// rotate momentum into the face frame (rows of T: n, t1, t2) and back
+__device__ __forceinline__ void rot_in(const double *T, const double *in, double *out) {
+  out[0] = in[0]; out[4] = in[4];
+#pragma unroll
+  for (int r = 0; r < 3; r++) out[1 + r] = T[3 * r] * in[1] + T[3 * r + 1] * in[2] + T[3 * r + 2] * in[3];
+}
+__device__ __forceinline__ void rot_out(const double *T, const double *in, double *out) {
+  out[0] = in[0]; out[4] = in[4];
+#pragma unroll
+  for (int d = 0; d < 3; d++) out[1 + d] = T[d] * in[1] + T[3 + d] * in[2] + T[6 + d] * in[3];
+}
+
+// Euler eigen-system along x of a face-frame state: scalars from which the
+// rows of R^{-1} (left) and columns of R (right) are formed.
+struct Eig { double u, v, w, a, H, q2, b1, b2, ia; };
+__device__ __forceinline__ Eig eig_of(const double *Q, double gamma) {
+  Eig e;
+  double ir = 1.0 / Q[0];
+  e.u = Q[1] * ir; e.v = Q[2] * ir; e.w = Q[3] * ir;
+  e.q2 = e.u * e.u + e.v * e.v + e.w * e.w;
+  double p = (gamma - 1.0) * (Q[4] - 0.5 * Q[0] * e.q2);
+  e.a = sqrt(gamma * p * ir);
+  e.ia = 1.0 / e.a;
+  e.H = (Q[4] + p) * ir;
+  e.b1 = (gamma - 1.0) * e.ia * e.ia;
+  e.b2 = 0.5 * e.b1 * e.q2;
+  return e;
+}
+// row c of R^{-1}
+__device__ __forceinline__ void left_row(const Eig &e, int c, double *l) {
+  switch (c) {
+    case 0: l[0] = 0.5 * (e.b2 + e.u * e.ia); l[1] = -0.5 * (e.b1 * e.u + e.ia); l[2] = -0.5 * e.b1 * e.v; l[3] = -0.5 * e.b1 * e.w; l[4] = 0.5 * e.b1; break;
+    case 1: l[0] = 1.0 - e.b2; l[1] = e.b1 * e.u; l[2] = e.b1 * e.v; l[3] = e.b1 * e.w; l[4] = -e.b1; break;
+    case 2: l[0] = -e.v; l[1] = 0.0; l[2] = 1.0; l[3] = 0.0; l[4] = 0.0; break;
+    case 3: l[0] = -e.w; l[1] = 0.0; l[2] = 0.0; l[3] = 1.0; l[4] = 0.0; break;
+    default: l[0] = 0.5 * (e.b2 - e.u * e.ia); l[1] = -0.5 * (e.b1 * e.u - e.ia); l[2] = -0.5 * e.b1 * e.v; l[3] = -0.5 * e.b1 * e.w; l[4] = 0.5 * e.b1;
+  }
+}
+// out = R q (characteristic -> conservative, face frame)
+__device__ __forceinline__ void right_apply(const Eig &e, const double *q, double *out) {
+  double s = q[0] + q[1] + q[4];
+  out[0] = s;
+  out[1] = e.u * s + e.a * (q[4] - q[0]);
+  out[2] = e.v * s + q[2];
+  out[3] = e.w * s + q[3];
+  out[4] = e.H * (q[0] + q[4]) + e.u * e.a * (q[4] - q[0]) + 0.5 * e.q2 * q[1] + e.v * q[2] + e.w * q[3];
+}
+
+// ------------------------------------------------------------------------
+// 1. polynomial coefficients
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_coef_weno(DevMesh m, const double *__restrict__ Q, double *__restrict__ coef) {
+  const int N = m.N;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 5 * N) return;
+  const int c = t / N, i = t - c * N;
+  const double qi = Q[(size_t)c * N + i];
+  double a[9], b[12];
+#pragma unroll
+  for (int d = 0; d < 9; d++) a[d] = 0.0;
+#pragma unroll
+  for (int d = 0; d < 12; d++) b[d] = 0.0;
+#pragma unroll
+  for (int k = 0; k < kBig; k++) {
+    int j = m.sten[(size_t)k * N + i];
+    if (j < 0) break;
+    double dq = Q[(size_t)c * N + j] - qi;
+#pragma unroll
+    for (int d = 0; d < 9; d++) a[d] = fma(m.X0[(size_t)(d * kBig + k) * N + i], dq, a[d]);
+#pragma unroll
+    for (int d = 0; d < 12; d++) b[d] = fma(m.Xm[(size_t)(d * kBig + k) * N + i], dq, b[d]);
+  }
+#pragma unroll
+  for (int d = 0; d < 9; d++) coef[(size_t)(d * 5 + c) * N + i] = a[d];
+#pragma unroll
+  for (int d = 0; d < 12; d++) coef[(size_t)(kCoefA + d * 5 + c) * N + i] = b[d];
+}
+
+__global__ void __launch_bounds__(kBlock) k_coef_hweno(DevMesh m, const double *__restrict__ Q, const double *__restrict__ G,
+                                                        double *__restrict__ coef) {
+  const int N = m.N;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 5 * N) return;
+  const int c = t / N, i = t - c * N;
+  const double qi = Q[(size_t)c * N + i];
+  double data[19];
+  int nb[4];
+#pragma unroll
+  for (int p = 0; p < 4; p++) {
+    nb[p] = m.cnb[(size_t)p * N + i];
+    data[p] = nb[p] >= 0 ? Q[(size_t)c * N + nb[p]] - qi : 0.0;
+  }
+#pragma unroll
+  for (int j = 0; j < 3; j++) data[4 + j] = G[(size_t)(3 * c + j) * N + i];
+#pragma unroll
+  for (int p = 0; p < 4; p++)
+#pragma unroll
+    for (int j = 0; j < 3; j++) data[7 + 3 * p + j] = nb[p] >= 0 ? G[(size_t)(3 * c + j) * N + nb[p]] : 0.0;
+#pragma unroll
+  for (int d = 0; d < 9; d++) {
+    double s = 0.0;
+#pragma unroll
+    for (int col = 0; col < 19; col++) s = fma(m.H0[(size_t)(d * 19 + col) * N + i], data[col], s);
+    coef[(size_t)(d * 5 + c) * N + i] = s;
+  }
+#pragma unroll
+  for (int mm = 0; mm < 4; mm++) {
+    double dm[7] = {data[mm], data[4], data[5], data[6], data[7 + 3 * mm], data[8 + 3 * mm], data[9 + 3 * mm]};
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+      double s = 0.0;
+#pragma unroll
+      for (int col = 0; col < 7; col++) s = fma(m.Hm[(size_t)((mm * 3 + j) * 7 + col) * N + i], dm[col], s);
+      coef[(size_t)(kCoefA + (mm * 3 + j) * 5 + c) * N + i] = s;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------
+// 2. reconstruction at the Gauss points of one face, one side
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_recon(DevMesh m, hgks_params P, const double *__restrict__ Q,
+                                                   const double *__restrict__ coef, double *__restrict__ wface) {
+  const int N = m.N, F = m.F;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 4 * N) return;
+  const int slot = t / N, i = t - slot * N;
+  const int cf = m.cface[(size_t)slot * N + i];
+  const int f = cf >> 1, side = cf & 1;
+  double T[9];
+#pragma unroll
+  for (int k = 0; k < 9; k++) T[k] = m.fT[(size_t)k * F + f];
+  const int L = m.fl[f], R = m.fr[f];
+  double Qi[5], Qs[5], Qsl[5];
+#pragma unroll
+  for (int c = 0; c < 5; c++) {
+    Qi[c] = Q[(size_t)c * N + i];
+    Qs[c] = R >= 0 ? 0.5 * (Q[(size_t)c * N + L] + Q[(size_t)c * N + R]) : Qi[c];
+  }
+  rot_in(T, Qs, Qsl);
+  const Eig e = eig_of(Qsl, P.gamma);
+  const double ih = 1.0 / m.h[i];
+  double m2[6], xg[9];
+#pragma unroll
+  for (int k = 0; k < 6; k++) m2[k] = m.m2[(size_t)k * N + i];
+#pragma unroll
+  for (int k = 0; k < 9; k++) xg[k] = m.xg[(size_t)(slot * 9 + k) * N + i];
+  // weights of the sub-stencils
+  unsigned valid = P.scheme == HGKS_WENO ? m.subvalid[i] : 0xFu;
+  const int M = __popc(valid);
+  const double gm = P.lin_weight, g0 = M ? 1.0 - gm * M : 1.0;
+  const double ig0 = 1.0 / g0;
+  double *out = wface + (size_t)side * 3 * kFaceState * F + f;
+  for (int c = 0; c < 5; c++) {
+    double mr[5];
+    if (P.characteristic) {
+      double l[5];
+      left_row(e, c, l);
+      mr[0] = l[0]; mr[4] = l[4];
+#pragma unroll
+      for (int j = 0; j < 3; j++) mr[1 + j] = l[1] * T[j] + l[2] * T[3 + j] + l[3] * T[6 + j];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 5; k++) mr[k] = k == c ? 1.0 : 0.0;
+    }
+    double q0 = 0.0;
+#pragma unroll
+    for (int k = 0; k < 5; k++) q0 = fma(mr[k], Qi[k], q0);
+    double ac[9], bc[12];
+#pragma unroll
+    for (int d = 0; d < 9; d++) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < 5; k++) s = fma(mr[k], coef[(size_t)(d * 5 + k) * N + i], s);
+      ac[d] = s;
+    }
+#pragma unroll
+    for (int d = 0; d < 12; d++) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < 5; k++) s = fma(mr[k], coef[(size_t)(kCoefA + d * 5 + k) * N + i], s);
+      bc[d] = s;
+    }
+    // smoothness indicators in the scaled frame: beta_0 = avg |grad P0|^2 + sum of squared second derivatives
+    const double H00 = 2.0 * ac[3], H11 = 2.0 * ac[4], H22 = 2.0 * ac[5], H01 = ac[6], H02 = ac[7], H12 = ac[8];
+    double beta0 = ac[0] * ac[0] + ac[1] * ac[1] + ac[2] * ac[2];
+    {
+      const double Hr[3][3] = {{H00, H01, H02}, {H01, H11, H12}, {H02, H12, H22}};
+#pragma unroll
+      for (int j = 0; j < 3; j++) {
+        double y0 = m2[0] * Hr[j][0] + m2[3] * Hr[j][1] + m2[4] * Hr[j][2];
+        double y1 = m2[3] * Hr[j][0] + m2[1] * Hr[j][1] + m2[5] * Hr[j][2];
+        double y2 = m2[4] * Hr[j][0] + m2[5] * Hr[j][1] + m2[2] * Hr[j][2];
+        beta0 += Hr[j][0] * y0 + Hr[j][1] * y1 + Hr[j][2] * y2;
+      }
+    }
+    beta0 += H00 * H00 + H11 * H11 + H22 * H22 + H01 * H01 + H02 * H02 + H12 * H12;
+    double kap0, kap[4];
+    if (P.weights == HGKS_LINEAR || M == 0) {
+      kap0 = 1.0;
+#pragma unroll
+      for (int mm = 0; mm < 4; mm++) kap[mm] = 0.0;
+    } else {
+      double beta[4], tz = 0.0;
+#pragma unroll
+      for (int mm = 0; mm < 4; mm++) {
+        beta[mm] = bc[3 * mm] * bc[3 * mm] + bc[3 * mm + 1] * bc[3 * mm + 1] + bc[3 * mm + 2] * bc[3 * mm + 2];
+        if (valid >> mm & 1) tz += fabs(beta0 - beta[mm]);
+      }
+      tz /= M;
+      double w0 = g0 * (1.0 + tz / (beta0 + P.weno_eps)), w[4], sum = w0;
+#pragma unroll
+      for (int mm = 0; mm < 4; mm++) {
+        w[mm] = (valid >> mm & 1) ? gm * (1.0 + tz / (beta[mm] + P.weno_eps)) : 0.0;
+        sum += w[mm];
+      }
+      double is = 1.0 / sum;
+      double wb0 = w0 * is;
+      kap0 = wb0 * ig0;
+#pragma unroll
+      for (int mm = 0; mm < 4; mm++) kap[mm] = (valid >> mm & 1) ? w[mm] * is - wb0 * gm * ig0 : 0.0;
+    }
+    // combined polynomial: Q = kap0 P0 + sum kap_m P_m (kap0 + sum kap_m = 1)
+    double lin[3];
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+      double s = kap0 * ac[j];
+#pragma unroll
+      for (int mm = 0; mm < 4; mm++) s = fma(kap[mm], bc[3 * mm + j], s);
+      lin[j] = s;
+    }
+    double qd[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) qd[k] = kap0 * ac[3 + k];
+#pragma unroll
+    for (int g = 0; g < 3; g++) {
+      const double x = xg[3 * g], y = xg[3 * g + 1], z = xg[3 * g + 2];
+      double val = q0 + lin[0] * x + lin[1] * y + lin[2] * z + qd[0] * (x * x - m2[0]) + qd[1] * (y * y - m2[1]) +
+                   qd[2] * (z * z - m2[2]) + qd[3] * (x * y - m2[3]) + qd[4] * (x * z - m2[4]) + qd[5] * (y * z - m2[5]);
+      double gx = lin[0] + 2.0 * qd[0] * x + qd[3] * y + qd[4] * z;
+      double gy = lin[1] + 2.0 * qd[1] * y + qd[3] * x + qd[5] * z;
+      double gz = lin[2] + 2.0 * qd[2] * z + qd[4] * x + qd[5] * y;
+      double *o = out + (size_t)g * kFaceState * F;
+      o[(size_t)c * F] = val;
+#pragma unroll
+      for (int k = 0; k < 3; k++) o[(size_t)(5 + 5 * k + c) * F] = ih * (T[3 * k] * gx + T[3 * k + 1] * gy + T[3 * k + 2] * gz);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------
+// 3. gas-kinetic flux
+// ------------------------------------------------------------------------
+// moments of the normalised Maxwellian: u (full or half range) up to u^6,
+// v and w up to the 5th power, xi^2 and xi^4
+struct Mom { double u[7], v[6], w[6], xi2, xi4; };
+
+__device__ __forceinline__ void mom_vw(const Prim &p, double K, Mom &m) {
+  const double il = 0.5 / p.lam;   // 1/(2 lambda)
+  m.v[0] = 1.0; m.v[1] = p.V; m.w[0] = 1.0; m.w[1] = p.W;
+#pragma unroll
+  for (int n = 0; n < 4; n++) {
+    m.v[n + 2] = p.V * m.v[n + 1] + (n + 1) * il * m.v[n];
+    m.w[n + 2] = p.W * m.w[n + 1] + (n + 1) * il * m.w[n];
+  }
+  m.xi2 = K * il;
+  m.xi4 = (K * K + 2.0 * K) * il * il;
+}
+__device__ __forceinline__ void mom_u_full(const Prim &p, double *u) {
+  const double il = 0.5 / p.lam;
+  u[0] = 1.0; u[1] = p.U;
+#pragma unroll
+  for (int n = 0; n < 5; n++) u[n + 2] = p.U * u[n + 1] + (n + 1) * il * u[n];
+}
+// sgn = +1: u > 0, sgn = -1: u < 0
+__device__ __forceinline__ void mom_u_half(const Prim &p, double sgn, double *u) {
+  const double il = 0.5 / p.lam, sl = sqrt(p.lam);
+  u[0] = 0.5 * erfc(-sgn * sl * p.U);
+  u[1] = p.U * u[0] + sgn * 0.5 * exp(-p.lam * p.U * p.U) / (sl * 1.7724538509055160273);   // sqrt(pi)
+#pragma unroll
+  for (int n = 0; n < 5; n++) u[n + 2] = p.U * u[n + 1] + (n + 1) * il * u[n];
+}
+
+// out += s <u^A v^B w^C psi>
+template <int A, int B, int C>
+__device__ __forceinline__ void acc_psi(const double *mu, const double *mv, const double *mw, double xi2, double s, double *out) {
+  const double vw = mv[B] * mw[C];
+  const double g = mu[A] * vw;
+  out[0] = fma(s, g, out[0]);
+  out[1] = fma(s, mu[A + 1] * vw, out[1]);
+  out[2] = fma(s, mu[A] * mv[B + 1] * mw[C], out[2]);
+  out[3] = fma(s, mu[A] * mv[B] * mw[C + 1], out[3]);
+  out[4] = fma(0.5 * s, mu[A + 2] * vw + mu[A] * (mv[B + 2] * mw[C] + mv[B] * mw[C + 2]) + xi2 * g, out[4]);
+}
+// out += s <u^A v^B w^C xi^2 psi>
+template <int A, int B, int C>
+__device__ __forceinline__ void acc_psi_xi(const double *mu, const double *mv, const double *mw, double xi2, double xi4, double s,
+                                           double *out) {
+  const double vw = mv[B] * mw[C];
+  const double g = mu[A] * vw;
+  const double sx = s * xi2;
+  out[0] = fma(sx, g, out[0]);
+  out[1] = fma(sx, mu[A + 1] * vw, out[1]);
+  out[2] = fma(sx, mu[A] * mv[B + 1] * mw[C], out[2]);
+  out[3] = fma(sx, mu[A] * mv[B] * mw[C + 1], out[3]);
+  out[4] = fma(0.5 * s, xi2 * (mu[A + 2] * vw + mu[A] * (mv[B + 2] * mw[C] + mv[B] * mw[C + 2])) + xi4 * g, out[4]);
+}
+// out += s <u^A v^B w^C (a.psi) psi>
+template <int A, int B, int C>
+__device__ __forceinline__ void acc_apsi(const double *mu, const Mom &m, const double *a, double s, double *out) {
+  acc_psi<A, B, C>(mu, m.v, m.w, m.xi2, s * a[0], out);
+  acc_psi<A + 1, B, C>(mu, m.v, m.w, m.xi2, s * a[1], out);
+  acc_psi<A, B + 1, C>(mu, m.v, m.w, m.xi2, s * a[2], out);
+  acc_psi<A, B, C + 1>(mu, m.v, m.w, m.xi2, s * a[3], out);
+  const double h = 0.5 * s * a[4];
+  acc_psi<A + 2, B, C>(mu, m.v, m.w, m.xi2, h, out);
+  acc_psi<A, B + 2, C>(mu, m.v, m.w, m.xi2, h, out);
+  acc_psi<A, B, C + 2>(mu, m.v, m.w, m.xi2, h, out);
+  acc_psi_xi<A, B, C>(mu, m.v, m.w, m.xi2, m.xi4, h, out);
+}
+// out += s * sum_d <u_d (a_d.psi) psi> (u_d = u, v, w): the moment of (a . u_vec) psi
+__device__ __forceinline__ void acc_slope_u(const double *mu, const Mom &m, const double (*a)[5], double s, double *out) {
+  acc_apsi<1, 0, 0>(mu, m, a[0], s, out);
+  acc_apsi<0, 1, 0>(mu, m, a[1], s, out);
+  acc_apsi<0, 0, 1>(mu, m, a[2], s, out);
+}
+// out += s * sum_d <u u_d (a_d.psi) psi>
+__device__ __forceinline__ void acc_u_slope_u(const double *mu, const Mom &m, const double (*a)[5], double s, double *out) {
+  acc_apsi<2, 0, 0>(mu, m, a[0], s, out);
+  acc_apsi<1, 1, 0>(mu, m, a[1], s, out);
+  acc_apsi<1, 0, 1>(mu, m, a[2], s, out);
+}
+
+// Slope a with <a> = rho * dq in closed form (dq normalised by rho)
+__device__ __forceinline__ void slope(const Prim &p, double K, const double *dq, double *a) {
+  const double q2 = p.U * p.U + p.V * p.V + p.W * p.W, e = (K + 3.0) / (4.0 * p.lam);
+  const double R4 = 2.0 * dq[4] - (q2 + 2.0 * e) * dq[0];
+  const double R1 = dq[1] - p.U * dq[0], R2 = dq[2] - p.V * dq[0], R3 = dq[3] - p.W * dq[0];
+  a[4] = 4.0 * p.lam * p.lam / (K + 3.0) * (R4 - 2.0 * p.U * R1 - 2.0 * p.V * R2 - 2.0 * p.W * R3);
+  a[3] = 2.0 * p.lam * R3 - p.W * a[4];
+  a[2] = 2.0 * p.lam * R2 - p.V * a[4];
+  a[1] = 2.0 * p.lam * R1 - p.U * a[4];
+  a[0] = dq[0] - p.U * a[1] - p.V * a[2] - p.W * a[3] - 0.5 * a[4] * (q2 + 2.0 * e);
+}
+
+// boundary state outside a boundary face (face frame, x = outward normal):
+// walls mirror the inner state in (p, U, V, W, T = p/rho); far field = free stream
+__device__ void boundary_state(const hgks_params &P, int tag, const double *T, const double *Wl, const double *dWl,
+                               double *Wr, double *dWr) {
+  const double g = P.gamma;
+  if (tag == HGKS_BC_FARFIELD) {
+    double u[3];
+#pragma unroll
+    for (int r = 0; r < 3; r++) u[r] = T[3 * r] * P.u_inf[0] + T[3 * r + 1] * P.u_inf[1] + T[3 * r + 2] * P.u_inf[2];
+    Wr[0] = P.rho_inf;
+#pragma unroll
+    for (int r = 0; r < 3; r++) Wr[1 + r] = P.rho_inf * u[r];
+    Wr[4] = P.p_inf / (g - 1.0) + 0.5 * P.rho_inf * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+#pragma unroll
+    for (int k = 0; k < 15; k++) dWr[k] = 0.0;
+    return;
+  }
+  const double rho = Wl[0], ir = 1.0 / rho;
+  double u[3] = {Wl[1] * ir, Wl[2] * ir, Wl[3] * ir};
+  const double q2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const double pr = (g - 1.0) * (Wl[4] - 0.5 * rho * q2), Tl = pr * ir;
+  const bool T_odd = tag == HGKS_BC_WALL_ISO || tag == HGKS_BC_WALL_LID;
+  bool vodd[3] = {true, tag != HGKS_BC_SLIP, tag != HGKS_BC_SLIP};
+  double uw[3] = {0.0, 0.0, 0.0};
+  if (tag == HGKS_BC_WALL_LID)
+#pragma unroll
+    for (int r = 0; r < 3; r++) uw[r] = T[3 * r] * P.lid_speed;
+  double ug[3];
+#pragma unroll
+  for (int r = 0; r < 3; r++) ug[r] = vodd[r] ? 2.0 * uw[r] - u[r] : u[r];
+  const double Tg = T_odd ? 2.0 * P.wall_T - Tl : Tl, pg = pr;
+  const double rg = pg / Tg, qg2 = ug[0] * ug[0] + ug[1] * ug[1] + ug[2] * ug[2];
+  Wr[0] = rg;
+#pragma unroll
+  for (int r = 0; r < 3; r++) Wr[1 + r] = rg * ug[r];
+  Wr[4] = pg / (g - 1.0) + 0.5 * rg * qg2;
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    const double *dW = dWl + 5 * d;
+    double du[3], udu = 0.0;
+#pragma unroll
+    for (int r = 0; r < 3; r++) { du[r] = (dW[1 + r] - u[r] * dW[0]) * ir; udu += u[r] * du[r]; }
+    const double dp = (g - 1.0) * (dW[4] - 0.5 * dW[0] * q2 - rho * udu);
+    const double dT = (dp - Tl * dW[0]) * ir;
+    const double sn = d == 0 ? -1.0 : 1.0;   // even quantities flip their normal derivative
+    double dug[3], udug = 0.0;
+#pragma unroll
+    for (int r = 0; r < 3; r++) { dug[r] = vodd[r] ? -sn * du[r] : sn * du[r]; udug += ug[r] * dug[r]; }
+    const double dpg = sn * dp, dTg = T_odd ? -sn * dT : sn * dT;
+    const double drho = dpg / Tg - pg * dTg / (Tg * Tg);
+    dWr[5 * d] = drho;
+#pragma unroll
+    for (int r = 0; r < 3; r++) dWr[5 * d + 1 + r] = drho * ug[r] + rg * dug[r];
+    dWr[5 * d + 4] = dpg / (g - 1.0) + 0.5 * drho * qg2 + rg * udug;
+  }
+}
+
+// Flux (time average over [0, dt] of int u psi f dXi, Eq. (flux)) and, if Qp
+// is not NULL, the point value int psi f dXi at t* (Eq. (point)). Face frame.
+__device__ void gks_flux(const hgks_params &P, const double *Wl, const double *dWl, const double *Wr, const double *dWr,
+                         double dt, double *F, double *Qp) {
+  const double gam = P.gamma, K = (5.0 - 3.0 * gam) / (gam - 1.0);
+  const Prim pl = to_prim(Wl, gam), pr = to_prim(Wr, gam);
+  Mom ml, mr;
+  mom_vw(pl, K, ml);
+  mom_vw(pr, K, mr);
+  double uhl[7], uhr[7];
+  mom_u_half(pl, 1.0, uhl);
+  mom_u_half(pr, -1.0, uhr);
+  // compatibility condition: Q0 = int_{u>0} psi g_l + int_{u<0} psi g_r
+  double Q0[5] = {0, 0, 0, 0, 0};
+  acc_psi<0, 0, 0>(uhl, ml.v, ml.w, ml.xi2, pl.rho, Q0);
+  acc_psi<0, 0, 0>(uhr, mr.v, mr.w, mr.xi2, pr.rho, Q0);
+  const Prim p0 = to_prim(Q0, gam);
+  // collision time (Sec. 5)
+  const double prl = 0.5 * pl.rho / pl.lam, prr = 0.5 * pr.rho / pr.lam, pp0 = 0.5 * p0.rho / p0.lam;
+  const double jump = fabs((prl - prr) / (prl + prr));
+  const double tau = P.viscous ? P.mu / pp0 + P.tau_C * jump * dt : (P.tau_eps + P.tau_C * jump) * dt;
+  const double eta = exp(-dt / tau);
+  const double c1 = dt - tau * (1.0 - eta);
+  const double c2 = 2.0 * tau * tau * (1.0 - eta) - tau * dt * (1.0 + eta);
+  const double c3 = 0.5 * dt * dt - tau * dt + tau * tau * (1.0 - eta);
+  const double c4 = tau * (1.0 - eta);
+  const double c5 = 2.0 * tau * tau * (1.0 - eta) - tau * dt * eta;
+  const bool want_pt = Qp != nullptr, prandtl = P.Pr != 1.0;
+  const double ts = P.tstar_end ? dt : 0.0, es = exp(-ts / tau);
+  double Fl[5] = {0, 0, 0, 0, 0}, Wb[5] = {0, 0, 0, 0, 0}, Pt[5] = {0, 0, 0, 0, 0};
+  double dWs[15];
+#pragma unroll
+  for (int k = 0; k < 15; k++) dWs[k] = 0.5 * (dWl[k] + dWr[k]);
+  // the two initial distributions g_l (u > 0) and g_r (u < 0)
+#pragma unroll 1
+  for (int s = 0; s < 2; s++) {
+    const Prim &pk = s == 0 ? pl : pr;
+    const Mom &mk = s == 0 ? ml : mr;
+    const double *uh = s == 0 ? uhl : uhr;
+    const double *dW = s == 0 ? dWl : dWr;
+    const double irho = 1.0 / pk.rho;
+    double a[3][5], A[5], uf[7];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      double dq[5];
+#pragma unroll
+      for (int c = 0; c < 5; c++) dq[c] = dW[5 * d + c] * irho;
+      slope(pk, K, dq, a[d]);
+    }
+    mom_u_full(pk, uf);
+    double rhs[5] = {0, 0, 0, 0, 0};
+    acc_slope_u(uf, mk, a, -1.0, rhs);
+    slope(pk, K, rhs, A);
+    // flux terms of g_k
+    double fk[5] = {0, 0, 0, 0, 0};
+    acc_psi<1, 0, 0>(uh, mk.v, mk.w, mk.xi2, c4, fk);
+    acc_u_slope_u(uh, mk, a, -c5, fk);
+    acc_apsi<1, 0, 0>(uh, mk, A, -tau * c4, fk);
+#pragma unroll
+    for (int c = 0; c < 5; c++) Fl[c] = fma(pk.rho, fk[c], Fl[c]);
+    if (want_pt || prandtl) {
+      double m0[5] = {0, 0, 0, 0, 0}, ma[5] = {0, 0, 0, 0, 0}, mA[5] = {0, 0, 0, 0, 0};
+      acc_psi<0, 0, 0>(uh, mk.v, mk.w, mk.xi2, 1.0, m0);
+      acc_slope_u(uh, mk, a, 1.0, ma);
+      acc_apsi<0, 0, 0>(uh, mk, A, 1.0, mA);
+#pragma unroll
+      for (int c = 0; c < 5; c++) {
+        Pt[c] += pk.rho * es * (m0[c] - (tau + ts) * ma[c] - tau * mA[c]);
+        Wb[c] += pk.rho * (c4 * m0[c] - c5 * ma[c] - tau * c4 * mA[c]);
+      }
+    }
+  }
+  // the equilibrium part g0 with slopes from the average of both sides' gradients
+  {
+    Mom m0;
+    mom_vw(p0, K, m0);
+    double uf[7];
+    mom_u_full(p0, uf);
+    const double irho = 1.0 / p0.rho;
+    double a[3][5], A[5];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      double dq[5];
+#pragma unroll
+      for (int c = 0; c < 5; c++) dq[c] = dWs[5 * d + c] * irho;
+      slope(p0, K, dq, a[d]);
+    }
+    double S0[5] = {0, 0, 0, 0, 0}, rhs[5];
+    acc_slope_u(uf, m0, a, 1.0, S0);       // <(abar . u_vec) psi>
+#pragma unroll
+    for (int c = 0; c < 5; c++) rhs[c] = -S0[c];
+    slope(p0, K, rhs, A);                  // <Abar psi> = -S0
+    double f0[5] = {0, 0, 0, 0, 0};
+    acc_psi<1, 0, 0>(uf, m0.v, m0.w, m0.xi2, c1, f0);
+    acc_u_slope_u(uf, m0, a, c2, f0);
+    acc_apsi<1, 0, 0>(uf, m0, A, c3, f0);
+#pragma unroll
+    for (int c = 0; c < 5; c++) Fl[c] = fma(p0.rho, f0[c], Fl[c]);
+    if (want_pt || prandtl) {
+      double g0m[5] = {0, 0, 0, 0, 0};
+      acc_psi<0, 0, 0>(uf, m0.v, m0.w, m0.xi2, 1.0, g0m);
+#pragma unroll
+      for (int c = 0; c < 5; c++) {
+        Pt[c] += p0.rho * ((1.0 - es) * g0m[c] + ((ts + tau) * es - tau) * S0[c] - (ts - tau + tau * es) * S0[c]);
+        Wb[c] += p0.rho * (c1 * g0m[c] + c2 * S0[c] - c3 * S0[c]);
+      }
+    }
+  }
+  const double idt = 1.0 / dt;
+#pragma unroll
+  for (int c = 0; c < 5; c++) F[c] = Fl[c] * idt;
+  if (prandtl) {
+    double Wt[5];
+#pragma unroll
+    for (int c = 0; c < 5; c++) Wt[c] = Wb[c] * idt;
+    const double U = p0.U, V = p0.V, W = p0.W, q2 = U * U + V * V + W * W;
+    const double q = F[4] - (U * F[1] + V * F[2] + W * F[3]) + 0.5 * q2 * F[0] - U * Wt[4] +
+                     U * (U * Wt[1] + V * Wt[2] + W * Wt[3]) - 0.5 * U * q2 * Wt[0];
+    F[4] += (1.0 / P.Pr - 1.0) * q;
+  }
+  if (want_pt)
+#pragma unroll
+    for (int c = 0; c < 5; c++) Qp[c] = Pt[c];
+}
+
+__device__ __forceinline__ bool physical(const double *W, double gamma) {
+  const double p = (gamma - 1.0) * (W[4] - 0.5 * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]) / W[0]);
+  return W[0] > 0.0 && p > 0.0;
+}
+
+__global__ void __launch_bounds__(kBlock) k_flux(DevMesh m, hgks_params P, const double *__restrict__ Q,
+                                                  const double *__restrict__ dt, const double *__restrict__ wface,
+                                                  double *__restrict__ fflux, double *__restrict__ fpt, int *__restrict__ flags) {
+  const int N = m.N, F = m.F;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * F) return;
+  const int g = t / F, f = t - g * F;
+  double T[9];
+#pragma unroll
+  for (int k = 0; k < 9; k++) T[k] = m.fT[(size_t)k * F + f];
+  const int L = m.fl[f], R = m.fr[f];
+  double QL[5], QR[5], Qs[5], Qsl[5];
+#pragma unroll
+  for (int c = 0; c < 5; c++) {
+    QL[c] = Q[(size_t)c * N + L];
+    QR[c] = R >= 0 ? Q[(size_t)c * N + R] : QL[c];
+    Qs[c] = R >= 0 ? 0.5 * (QL[c] + QR[c]) : QL[c];
+  }
+  rot_in(T, Qs, Qsl);
+  const Eig e = eig_of(Qsl, P.gamma);
+  double W[2][5], dW[2][15];
+  int bad = 0;
+#pragma unroll 1
+  for (int s = 0; s < (R >= 0 ? 2 : 1); s++) {
+    const double *in = wface + ((size_t)(s * 3 + g) * kFaceState) * F + f;
+    double q[5];
+#pragma unroll
+    for (int c = 0; c < 5; c++) q[c] = in[(size_t)c * F];
+    if (P.characteristic) right_apply(e, q, W[s]);
+    else rot_in(T, q, W[s]);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+#pragma unroll
+      for (int c = 0; c < 5; c++) q[c] = in[(size_t)(5 + 5 * k + c) * F];
+      if (P.characteristic) right_apply(e, q, dW[s] + 5 * k);
+      else rot_in(T, q, dW[s] + 5 * k);
+    }
+    if (!physical(W[s], P.gamma)) {
+      rot_in(T, s == 0 ? QL : QR, W[s]);
+#pragma unroll
+      for (int k = 0; k < 15; k++) dW[s][k] = 0.0;
+      bad++;
+    }
+  }
+  if (R < 0) boundary_state(P, m.ftag[f], T, W[0], dW[0], W[1], dW[1]);
+  double dtf;
+  if (P.flux_dt > 0.0) dtf = P.flux_dt;
+  else dtf = (R >= 0 ? fmin(dt[L], dt[R]) : dt[L]) * (P.flux_cfl / P.cfl);
+  double Fl[5], Qp[5];
+  const bool compact = P.scheme == HGKS_HWENO;
+  gks_flux(P, W[0], dW[0], W[1], dW[1], dtf, Fl, compact ? Qp : nullptr);
+  if (bad) atomicAdd(flags, bad);
+  const double w = m.fS[f] * (1.0 / 3.0);
+  double Fg[5];
+  rot_out(T, Fl, Fg);
+#pragma unroll
+  for (int c = 0; c < 5; c++) fflux[(size_t)(g * 5 + c) * F + f] = w * Fg[c];
+  if (compact) {
+    rot_out(T, Qp, Fg);
+#pragma unroll
+    for (int c = 0; c < 5; c++) fpt[(size_t)(g * 5 + c) * F + f] = w * Fg[c];
+  }
+}
+
+// ------------------------------------------------------------------------
+// 4. face -> cell
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_gather(DevMesh m, int compact, const double *__restrict__ fflux,
+                                                    const double *__restrict__ fpt, double *__restrict__ R,
+                                                    double *__restrict__ Gnew) {
+  const int N = m.N, F = m.F;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double r[5] = {0, 0, 0, 0, 0}, gr[15];
+#pragma unroll
+  for (int k = 0; k < 15; k++) gr[k] = 0.0;
+#pragma unroll
+  for (int p = 0; p < 4; p++) {
+    const int cf = m.cface[(size_t)p * N + i];
+    const int f = cf >> 1;
+    const double sg = (cf & 1) ? 1.0 : -1.0;   // the flux leaves the left cell
+#pragma unroll
+    for (int c = 0; c < 5; c++) {
+      double s = fflux[(size_t)c * F + f] + fflux[(size_t)(5 + c) * F + f] + fflux[(size_t)(10 + c) * F + f];
+      r[c] = fma(sg, s, r[c]);
+    }
+    if (compact) {
+      double n[3];
+#pragma unroll
+      for (int d = 0; d < 3; d++) n[d] = -sg * m.fT[(size_t)d * F + f];   // outward normal of this cell
+#pragma unroll
+      for (int c = 0; c < 5; c++) {
+        double s = fpt[(size_t)c * F + f] + fpt[(size_t)(5 + c) * F + f] + fpt[(size_t)(10 + c) * F + f];
+#pragma unroll
+        for (int d = 0; d < 3; d++) gr[3 * c + d] = fma(s, n[d], gr[3 * c + d]);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 5; c++) R[(size_t)c * N + i] = r[c];
+  if (compact) {
+    const double iv = m.inv_vol[i];
+#pragma unroll
+    for (int k = 0; k < 15; k++) Gnew[(size_t)k * N + i] = gr[k] * iv;
+  }
+}
+
+__global__ void k_local_dt(DevMesh m, hgks_params P, const double *__restrict__ Q, double *__restrict__ dt) {
+  const int N = m.N, F = m.F;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double q[5];
+#pragma unroll
+  for (int c = 0; c < 5; c++) q[c] = Q[(size_t)c * N + i];
+  const double ir = 1.0 / q[0], u = q[1] * ir, v = q[2] * ir, w = q[3] * ir;
+  const double p = (P.gamma - 1.0) * (q[4] - 0.5 * q[0] * (u * u + v * v + w * w));
+  const double a = sqrt(P.gamma * p * ir);
+  const double nu = P.viscous ? 2.0 * P.gamma * P.mu / (P.Pr * q[0] * m.h[i]) : 0.0;
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const int f = m.cface[(size_t)k * N + i] >> 1;
+    const double un = u * m.fT[f] + v * m.fT[(size_t)F + f] + w * m.fT[(size_t)2 * F + f];
+    s += m.fS[f] * (fabs(un) + a + nu);
+  }
+  dt[i] = P.cfl * m.vol[i] / s;
+}
+
+}  // namespace
+
+void launch_local_dt(const DevMesh &m, const hgks_params &p, const double *Q, double *dt, cudaStream_t st) {
+  HGKS_PROF_BEGIN(K_DT, st);
+  k_local_dt<<<grid_for(m.N, kBlock), kBlock, 0, st>>>(m, p, Q, dt);
+  HGKS_PROF_END(K_DT, st);
+}
+
+void launch_residual(const DevMesh &m, Scratch &s, const hgks_params &p, const double *Q, const double *G, double *R,
+                     double *Gnew, cudaStream_t st) {
+  launch_local_dt(m, p, Q, s.dt, st);
+  HGKS_PROF_BEGIN(K_COEF, st);
+  if (p.scheme == HGKS_WENO) k_coef_weno<<<grid_for(5 * (int64_t)m.N, kBlock), kBlock, 0, st>>>(m, Q, s.coef);
+  else k_coef_hweno<<<grid_for(5 * (int64_t)m.N, kBlock), kBlock, 0, st>>>(m, Q, G, s.coef);
+  HGKS_PROF_END(K_COEF, st);
+  HGKS_PROF_BEGIN(K_RECON, st);
+  k_recon<<<grid_for(4 * (int64_t)m.N, kBlock), kBlock, 0, st>>>(m, p, Q, s.coef, s.wface);
+  HGKS_PROF_END(K_RECON, st);
+  HGKS_PROF_BEGIN(K_FLUX, st);
+  k_flux<<<grid_for(3 * (int64_t)m.F, kBlock), kBlock, 0, st>>>(m, p, Q, s.dt, s.wface, s.fflux, s.fpt, s.flags);
+  HGKS_PROF_END(K_FLUX, st);
+  HGKS_PROF_BEGIN(K_GATHER, st);
+  k_gather<<<grid_for(m.N, kBlock), kBlock, 0, st>>>(m, p.scheme == HGKS_HWENO, s.fflux, s.fpt, R, Gnew);
+  HGKS_PROF_END(K_GATHER, st);
+}
+
+}  // namespace hgks
