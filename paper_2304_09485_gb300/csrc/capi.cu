@@ -71,27 +71,29 @@ hgks_status check_params(const Mesh &m, const hgks_params *p) {
   return HGKS_OK;
 }
 
-// Scratch of the residual (always) and of the implicit solve (lazily, per Krylov size)
-hgks_status ensure_scratch(Mesh &m, int kdim, bool implicit) {
+// Scratch of the residual (always) and of the implicit solve (lazily, per Krylov
+// size and precision). Krylov vectors are padded to a multiple of 64 elements so
+// that every vector of the basis starts on a 512-byte boundary.
+hgks_status ensure_scratch(Mesh &m, int kdim, bool implicit, bool mixed = false) {
   Scratch &s = m.s;
   const size_t N = m.N, F = m.F;
+  hgks_status st;
   if (!s.coef) {
-    hgks_status st;
     if ((st = dalloc(m, &s.coef, (size_t)kCoef * N))) return st;
     if ((st = dalloc(m, &s.dt, N))) return st;
     if ((st = dalloc(m, &s.wface, (size_t)2 * 3 * kFaceState * F))) return st;
     if ((st = dalloc(m, &s.fflux, (size_t)15 * F))) return st;
     if ((st = dalloc(m, &s.fpt, (size_t)15 * F))) return st;
     if ((st = dalloc(m, &s.flags, 8))) return st;
-    if ((st = dalloc(m, &s.red, 1024))) return st;
+    if ((st = dalloc(m, &s.red, std::max<size_t>(4096, N / 64 + 64)))) return st;   // one partial per block
     if ((st = dalloc(m, &s.red_count, 4))) return st;
     HGKS_CUDA(cudaMemset(s.flags, 0, 8 * sizeof(int)));
     HGKS_CUDA(cudaMemset(s.red_count, 0, 4 * sizeof(unsigned)));
     HGKS_CUDA(cudaMemset(s.wface, 0, sizeof(double) * 2 * 3 * kFaceState * F));
   }
+  s.vstride = (int64_t)((5 * N + 63) / 64 * 64);
   if (implicit && !s.off) {
-    hgks_status st;
-    if ((st = dalloc(m, &s.off, (size_t)2 * 25 * F))) return st;
+    if ((st = dalloc(m, &s.off, (size_t)100 * N))) return st;
     if ((st = dalloc(m, &s.dval, N))) return st;
     if ((st = dalloc(m, &s.dinv, N))) return st;
     if ((st = dalloc(m, &s.R, 5 * N))) return st;
@@ -101,18 +103,30 @@ hgks_status ensure_scratch(Mesh &m, int kdim, bool implicit) {
     if ((st = dalloc(m, &s.t, 5 * N))) return st;
     if ((st = dalloc(m, &s.t2, 5 * N))) return st;
     if ((st = dalloc(m, &s.hs, 65 * 64 + 256))) return st;
-    HGKS_CUDA(cudaMemset(s.off, 0, sizeof(double) * 2 * 25 * F));
+    HGKS_CUDA(cudaMemset(s.off, 0, sizeof(double) * 100 * N));
   }
+  if (implicit && mixed && !s.off32) {
+    if ((st = dalloc(m, &s.off32, (size_t)100 * N))) return st;
+    if ((st = dalloc(m, &s.dval32, N))) return st;
+    if ((st = dalloc(m, &s.dinv32, N))) return st;
+    if ((st = dalloc(m, &s.w32, 5 * N))) return st;
+    if ((st = dalloc(m, &s.t32, 5 * N))) return st;
+    if ((st = dalloc(m, &s.t232, 5 * N))) return st;
+    if ((st = dalloc(m, &s.red32, std::max<size_t>(4096, N / 64 + 64)))) return st;
+  }
+  auto release = [&](void *p, size_t bytes) {
+    cudaFree(p);
+    for (auto &q : m.allocs) if (q == p) q = nullptr;
+    m.bytes -= bytes;
+  };
   if (implicit && kdim > s.kdim) {
-    if (s.V) {
-      cudaFree(s.V);
-      for (auto &p : m.allocs) if (p == s.V) p = nullptr;
-      m.bytes -= sizeof(double) * (size_t)(s.kdim + 1) * 5 * N;
-      s.V = nullptr;
-    }
-    hgks_status st;
-    if ((st = dalloc(m, &s.V, (size_t)(kdim + 1) * 5 * N))) return st;
+    if (s.V) { release(s.V, sizeof(double) * (size_t)(s.kdim + 1) * s.vstride); s.V = nullptr; }
+    if (s.V32) { release(s.V32, sizeof(float) * (size_t)(s.kdim + 1) * s.vstride); s.V32 = nullptr; }
+    if ((st = dalloc(m, &s.V, (size_t)(kdim + 1) * s.vstride))) return st;
     s.kdim = kdim;
+  }
+  if (implicit && mixed && !s.V32) {
+    if ((st = dalloc(m, &s.V32, (size_t)(s.kdim + 1) * s.vstride))) return st;
   }
   return HGKS_OK;
 }
@@ -310,7 +324,7 @@ hgks_status hgks_assemble(hgks_mesh mesh, const hgks_params *p, const double *Q,
   if (st) return st;
   if (!Q || !dt) return fail(HGKS_ERR_ARG, "Q or dt is NULL");
   if ((st = set_device(m))) return st;
-  if ((st = ensure_scratch(m, p->krylov_dim, true))) return st;
+  if ((st = ensure_scratch(m, p->krylov_dim, true, p->precision == HGKS_MIXED))) return st;
   launch_assemble(m.d, m.s, *p, Q, dt, diag_out, off_out, (cudaStream_t)cuda_stream);
   return last_launch();
 }
@@ -378,7 +392,7 @@ hgks_status hgks_gmres_step(hgks_mesh mesh, const hgks_params *p, double *Q, dou
   if (!Q) return fail(HGKS_ERR_ARG, "Q is NULL");
   if (p->scheme == HGKS_HWENO && !G) return fail(HGKS_ERR_ARG, "compact scheme needs G");
   if ((st = set_device(m))) return st;
-  if ((st = ensure_scratch(m, p->krylov_dim, true))) return st;
+  if ((st = ensure_scratch(m, p->krylov_dim, true, p->precision == HGKS_MIXED))) return st;
   if (info) std::memset(info, 0, sizeof(*info));
   return gmres_step_impl(m, p, Q, G, dQ_out, info, (cudaStream_t)cuda_stream);
 }
@@ -392,7 +406,7 @@ hgks_status hgks_solve_steady(hgks_mesh mesh, const hgks_params *p, double *Q, d
   if (!Q || (p->scheme == HGKS_HWENO && !G)) return fail(HGKS_ERR_ARG, "Q (or G) is NULL");
   if (!(drop_tol > 0.0) || max_steps < 0) return fail(HGKS_ERR_ARG, "drop_tol must be > 0 and max_steps >= 0");
   if ((st = set_device(m))) return st;
-  if ((st = ensure_scratch(m, p->krylov_dim, true))) return st;
+  if ((st = ensure_scratch(m, p->krylov_dim, true, p->precision == HGKS_MIXED))) return st;
   cudaStream_t s_ = (cudaStream_t)cuda_stream;
   double ref = 0.0, res = 0.0;
   int k = 0;
@@ -464,7 +478,7 @@ hgks_status hgks_gmres_step_host(hgks_mesh mesh, const hgks_params *p, double *Q
   const bool compact = p->scheme == HGKS_HWENO;
   if (!Q_host || (compact && !G_host)) return fail(HGKS_ERR_ARG, "NULL host array");
   if ((st = set_device(m))) return st;
-  if ((st = ensure_scratch(m, p->krylov_dim, true))) return st;
+  if ((st = ensure_scratch(m, p->krylov_dim, true, p->precision == HGKS_MIXED))) return st;
   double *buf;
   if ((st = host_state_buffer(m, &buf))) return st;
   const size_t N = m.N;

@@ -54,9 +54,11 @@ struct Scratch {
   double *fpt = nullptr;         // [3][5][F] global-frame point values * area / 3
   // implicit
   double *dinv = nullptr, *dval = nullptr;  // [N] the diagonal block is (|Omega|/dt + sum lambda S/2) I
-  double *off = nullptr;         // [2][25][F]: side s = row cell, block multiplies the other cell
-  float *off32 = nullptr;        // [2][25][F] FP32 copy (mixed precision)
-  float *dinv32 = nullptr;
+  double *off = nullptr;         // [4*25][N]: block of local face p of the row cell (0 on a boundary)
+  float *off32 = nullptr;        // [4*25][N] FP32 copy (mixed precision)
+  float *dinv32 = nullptr, *dval32 = nullptr;
+  float *red32 = nullptr;
+  int64_t vstride = 0;           // elements between Krylov vectors (5N padded to a multiple of 64)
   double *R = nullptr, *Gnew = nullptr, *dQ = nullptr;   // [5][N], [15][N], [5][N]
   double *V = nullptr;           // [(m+1)][5N] Krylov basis (FP64)
   float *V32 = nullptr;          // [(m+1)][5N] Krylov basis (FP32)

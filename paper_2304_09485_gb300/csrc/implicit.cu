@@ -6,15 +6,17 @@
 //    The Euler-Jacobian part of A_ii is J(Q_i) applied to sum_p n_p S_p, the
 //    sum of a closed cell's outward area vectors, which is zero: A_ii is a
 //    multiple of the identity and is stored as one number per cell. The
-//    off-diagonal blocks are stored per (face, side): side s holds the block
-//    of the row of the face's side-s cell ("structure array" of Sec. 4.3, laid
-//    out face-major so that a warp reads consecutive faces).
-//  * Jacobi preconditioner of Eq. (precond), k_max sweeps.
+//    off-diagonal blocks form the per-cell "structure array" of Sec. 4.3,
+//    stored component-major off[(p*25 + k)][N] (p = local face of the row cell)
+//    so that the thread of cell i reads consecutive addresses with its warp.
+//  * Jacobi preconditioner of Eq. (precond), k_max sweeps. The first sweep reads
+//    D^{-1} b of the neighbours on the fly (no separate x0 pass).
 //  * Restarted GMRES with modified Gram-Schmidt (Algorithm 1). Every inner
-//    product is one launch: blocks write partial sums, the last block to finish
-//    adds them in a fixed order (deterministic, no host round trip). The small
-//    least-squares problem (Givens rotations) runs in a single device thread,
-//    so a whole GMRES cycle is enqueued without synchronising the host.
+//    product finishes inside its launch: blocks write partial sums, the last
+//    block to finish adds them in a fixed order (deterministic, no host round
+//    trip); the first product (w, v_0) is fused into the last Jacobi sweep. The
+//    Hessenberg least-squares problem (Givens rotations) runs on the device, so a
+//    whole GMRES cycle is enqueued without synchronising the host.
 #include <cmath>
 #include "hgks_internal.h"
 
@@ -22,7 +24,8 @@ namespace hgks {
 namespace {
 
 constexpr int kBlock = 256;
-constexpr int kRedBlocks = 2 * 152;   // blocks of every reduction: a multiple of the SM count
+constexpr int kCellBlock = 128;
+constexpr int kRedBlocks = 152 * 4;   // blocks of the vector reductions: a multiple of the SM count
 
 __device__ __forceinline__ void euler_jacobian(const double *Q, const double *n, double gamma, double *J) {
   const double ir = 1.0 / Q[0];
@@ -44,9 +47,10 @@ __device__ __forceinline__ void euler_jacobian(const double *Q, const double *n,
   J[24] = gamma * un;
 }
 
-__global__ void k_assemble(DevMesh m, hgks_params P, const double *__restrict__ Q, const double *__restrict__ dt,
-                           double *__restrict__ dval, double *__restrict__ dinv, double *__restrict__ off,
-                           double *__restrict__ diag_out, double *__restrict__ off_out) {
+__global__ void __launch_bounds__(kCellBlock) k_assemble(DevMesh m, hgks_params P, const double *__restrict__ Q,
+                                                         const double *__restrict__ dt, double *__restrict__ dval,
+                                                         double *__restrict__ dinv, double *__restrict__ off,
+                                                         double *__restrict__ diag_out, double *__restrict__ off_out) {
   const int N = m.N, F = m.F;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -76,17 +80,12 @@ __global__ void k_assemble(DevMesh m, hgks_params P, const double *__restrict__ 
     if (P.viscous) lam += 2.0 * P.mu / (Qf[0] * m.fdist[f]);
     d += 0.5 * lam * S;
     double J[25];
-    if (j >= 0) {
-      euler_jacobian(Qj, n, P.gamma, J);
+    if (j >= 0) euler_jacobian(Qj, n, P.gamma, J);
 #pragma unroll
-      for (int k = 0; k < 25; k++) {
-        double o = 0.5 * (J[k] - (k % 6 == 0 ? lam : 0.0)) * S;
-        off[(size_t)(side * 25 + k) * F + f] = o;
-        if (off_out) off_out[(size_t)(p * 25 + k) * N + i] = o;
-      }
-    } else if (off_out) {
-#pragma unroll
-      for (int k = 0; k < 25; k++) off_out[(size_t)(p * 25 + k) * N + i] = 0.0;
+    for (int k = 0; k < 25; k++) {
+      const double o = j >= 0 ? 0.5 * (J[k] - (k % 6 == 0 ? lam : 0.0)) * S : 0.0;
+      off[(size_t)(p * 25 + k) * N + i] = o;
+      if (off_out) off_out[(size_t)(p * 25 + k) * N + i] = o;
     }
   }
   dval[i] = d;
@@ -96,107 +95,164 @@ __global__ void k_assemble(DevMesh m, hgks_params P, const double *__restrict__ 
     for (int k = 0; k < 25; k++) diag_out[(size_t)k * N + i] = k % 6 == 0 ? d : 0.0;
 }
 
-// y = b - (sum_p A_ip x_p) [+ diag x when with_diag]; (L+U) x when b = nullptr and with_diag = 0
-template <bool WithDiag, bool Jacobi>
-__global__ void k_offdiag(DevMesh m, const double *__restrict__ off, const double *__restrict__ dval,
-                          const double *__restrict__ dinv, const double *__restrict__ b, const double *__restrict__ x,
-                          double *__restrict__ y) {
-  const int N = m.N, F = m.F;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  double acc[5];
-#pragma unroll
-  for (int r = 0; r < 5; r++) acc[r] = WithDiag ? dval[i] * x[(size_t)r * N + i] : 0.0;
-#pragma unroll
-  for (int p = 0; p < 4; p++) {
-    const int j = m.cnb[(size_t)p * N + i];
-    if (j < 0) continue;
-    const int cf = m.cface[(size_t)p * N + i], f = cf >> 1, side = cf & 1;
-    double xj[5];
-#pragma unroll
-    for (int c = 0; c < 5; c++) xj[c] = x[(size_t)c * N + j];
-    const double *O = off + (size_t)side * 25 * F + f;
-#pragma unroll
-    for (int r = 0; r < 5; r++)
-#pragma unroll
-      for (int c = 0; c < 5; c++) acc[r] = fma(O[(size_t)(5 * r + c) * F], xj[c], acc[r]);
-  }
-  if (Jacobi) {
-    const double di = dinv[i];
-#pragma unroll
-    for (int r = 0; r < 5; r++) y[(size_t)r * N + i] = di * (b[(size_t)r * N + i] - acc[r]);
-  } else if (b) {
-#pragma unroll
-    for (int r = 0; r < 5; r++) y[(size_t)r * N + i] = b[(size_t)r * N + i] - acc[r];
-  } else {
-#pragma unroll
-    for (int r = 0; r < 5; r++) y[(size_t)r * N + i] = acc[r];
-  }
-}
-
-__global__ void k_diag_scale(int N, const double *__restrict__ dinv, const double *__restrict__ b, double *__restrict__ x) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 5 * N) return;
-  x[t] = dinv[t % N] * b[t];
-}
-
-// Deterministic reduction: per-block partial sums, the last block adds them in order.
-__device__ __forceinline__ double block_sum(double v) {
-  __shared__ double sh[kBlock / 32];
+// Deterministic reduction: per-block partial sums, the last block adds them in
+// a fixed order (strided per thread, then a fixed tree). T is the accumulation type.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v) {
+  __shared__ T sh[32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
   __syncthreads();
-  double s = 0.0;
+  T s = T(0);
   if (threadIdx.x < 32) {
-    s = threadIdx.x < kBlock / 32 ? sh[threadIdx.x] : 0.0;
+    s = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : T(0);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   }
   return s;   // valid in thread 0
 }
-// finish: out = f(sum of partials); mode 0: sum, 1: sqrt(sum)
-__device__ __forceinline__ void finish_reduction(double bsum, double *partials, unsigned int *count, double *out, int mode) {
+// *out = sum of all blocks' v (mode 0) or its square root (mode 1), stored as double
+template <typename T>
+__device__ __forceinline__ void grid_sum(T v, T *partials, unsigned int *count, double *out, int mode) {
   __shared__ bool last;
+  const T bs = block_sum(v);
   if (threadIdx.x == 0) {
-    partials[blockIdx.x] = bsum;
+    partials[blockIdx.x] = bs;
     __threadfence();
-    unsigned int prev = atomicAdd(count, 1u);
+    const unsigned int prev = atomicAdd(count, 1u);
     last = (prev == gridDim.x - 1);
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    double s = 0.0;
-    for (unsigned b = 0; b < gridDim.x; b++) s += ((volatile double *)partials)[b];
-    *out = mode == 1 ? sqrt(s) : s;
+  if (!last) return;
+  __threadfence();
+  T s = T(0);
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) s += ((volatile T *)partials)[b];
+  s = block_sum(s);
+  if (threadIdx.x == 0) {
+    *out = mode == 1 ? (double)sqrt(s) : (double)s;
     *count = 0u;
   }
 }
 
-// w -= h * v (if v != nullptr); out = (w . x) or ||w|| (x == w, mode 1)
-__global__ void __launch_bounds__(kBlock) k_axpy_dot(int64_t n, double *__restrict__ w, const double *__restrict__ v,
-                                                     const double *__restrict__ h, const double *__restrict__ x,
-                                                     int self, double *partials, unsigned int *count, double *out) {
-  const double hv = v ? -*h : 0.0;
-  double s = 0.0;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-    double wk = w[k];
-    if (v) { wk = fma(hv, v[k], wk); w[k] = wk; }
-    s = fma(wk, self ? wk : x[k], s);
+// One product with the off-diagonal part of A. Modes:
+//   kSpmv  : y = [b -] (d x + sum_p A_ip x_p)
+//   kJacobi: y = D^{-1} (b - sum_p A_ip x_p); FirstSweep: x_p = D^{-1} b at the neighbours
+// and optionally the inner product (y, dotv) reduced into *dot_out.
+// TM: type of the stored blocks, TV: type of b and x (and of the accumulation),
+// TO: type of y.
+enum { kSpmv = 0, kJacobi = 1 };
+template <typename TM, typename TV, typename TO, int Mode, bool FirstSweep>
+__global__ void __launch_bounds__(kCellBlock) k_apply(DevMesh m, const TM *__restrict__ off, const TM *__restrict__ dval,
+                                                      const TM *__restrict__ dinv, const TV *__restrict__ b,
+                                                      const TV *__restrict__ x, TO *__restrict__ y,
+                                                      const TO *__restrict__ dotv, TO *partials, unsigned int *count,
+                                                      double *dot_out) {
+  const int N = m.N;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  TO part = TO(0);
+  if (i < N) {
+    TV acc[5];
+    const TV di = Mode == kSpmv ? (TV)dval[i] : TV(0);
+#pragma unroll
+    for (int r = 0; r < 5; r++) acc[r] = Mode == kSpmv ? di * x[(size_t)r * N + i] : TV(0);
+#pragma unroll
+    for (int p = 0; p < 4; p++) {
+      const int j = m.cnb[(size_t)p * N + i];
+      if (j < 0) continue;
+      TV xj[5];
+      const TV sj = FirstSweep ? (TV)dinv[j] : TV(1);
+#pragma unroll
+      for (int c = 0; c < 5; c++) xj[c] = FirstSweep ? sj * b[(size_t)c * N + j] : x[(size_t)c * N + j];
+      const TM *O = off + (size_t)p * 25 * N + i;
+#pragma unroll
+      for (int r = 0; r < 5; r++)
+#pragma unroll
+        for (int c = 0; c < 5; c++) acc[r] = fma((TV)O[(size_t)(5 * r + c) * N], xj[c], acc[r]);
+    }
+    TV out[5];
+    if (Mode == kJacobi) {
+      const TV dd = (TV)dinv[i];
+#pragma unroll
+      for (int r = 0; r < 5; r++) out[r] = dd * (b[(size_t)r * N + i] - acc[r]);
+    } else if (b) {
+#pragma unroll
+      for (int r = 0; r < 5; r++) out[r] = b[(size_t)r * N + i] - acc[r];
+    } else {
+#pragma unroll
+      for (int r = 0; r < 5; r++) out[r] = acc[r];
+    }
+#pragma unroll
+    for (int r = 0; r < 5; r++) {
+      const TO o = (TO)out[r];
+      y[(size_t)r * N + i] = o;
+      if (dotv) part = fma(o, dotv[(size_t)r * N + i], part);
+    }
   }
-  finish_reduction(block_sum(s), partials, count, out, self);
+  if (dotv) grid_sum(part, partials, count, dot_out, 0);
+}
+
+template <typename T>
+__global__ void k_diag_scale(int N, const T *__restrict__ dinv, const T *__restrict__ b, T *__restrict__ x) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 5 * N) return;
+  x[t] = dinv[t % N] * b[t];
+}
+
+template <typename T> struct Vec2;
+template <> struct Vec2<double> { typedef double2 type; };
+template <> struct Vec2<float> { typedef float2 type; };
+
+// w -= h v (if v != nullptr); *out = (w, x) (mode 0) or ||w|| (x == w, mode 1).
+// Two elements per thread and step; every vector starts on a 16-byte boundary
+// (Krylov vectors are padded to a multiple of 64 elements), n may be odd.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_axpy_dot(int64_t n, T *__restrict__ w, const T *__restrict__ v,
+                                                     const double *__restrict__ h, const T *__restrict__ x,
+                                                     int self, T *partials, unsigned int *count, double *out) {
+  typedef typename Vec2<T>::type T2;
+  const T hv = v ? (T)(-*h) : T(0);
+  T s = T(0);
+  const int64_t n2 = n >> 1;
+  T2 *w2 = reinterpret_cast<T2 *>(w);
+  const T2 *v2 = reinterpret_cast<const T2 *>(v);
+  const T2 *x2 = reinterpret_cast<const T2 *>(x);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n2; k += (int64_t)gridDim.x * blockDim.x) {
+    T2 wk = w2[k];
+    if (v) {
+      const T2 vk = v2[k];
+      wk.x = fma(hv, vk.x, wk.x);
+      wk.y = fma(hv, vk.y, wk.y);
+      w2[k] = wk;
+    }
+    if (self) {
+      s = fma(wk.x, wk.x, s);
+      s = fma(wk.y, wk.y, s);
+    } else {
+      const T2 xk = x2[k];
+      s = fma(wk.x, xk.x, s);
+      s = fma(wk.y, xk.y, s);
+    }
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    T wk = w[n - 1];
+    if (v) { wk = fma(hv, v[n - 1], wk); w[n - 1] = wk; }
+    s = fma(wk, self ? wk : x[n - 1], s);
+  }
+  grid_sum(s, partials, count, out, self);
 }
 
 // v = w / h (v = 0 after a breakdown h == 0)
-__global__ void k_scale(int64_t n, const double *__restrict__ w, const double *__restrict__ h, double *__restrict__ v) {
+template <typename T>
+__global__ void k_scale(int64_t n, const T *__restrict__ w, const double *__restrict__ h, T *__restrict__ v) {
   const double hv = *h;
-  const double ih = hv != 0.0 ? 1.0 / hv : 0.0;
+  const T ih = hv != 0.0 ? (T)(1.0 / hv) : T(0);
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) v[k] = w[k] * ih;
 }
 
 // Givens QR of the (used+1) x used Hessenberg matrix and back substitution:
-// y minimises || beta e1 - H y ||. H[i*m + j] holds h_{i,j}. Single thread.
+// y minimises || beta e1 - H y ||. H[i*m + j] holds h_{i,j}. Single thread, FP64.
 __global__ void k_givens(int m, const double *__restrict__ H, const double *__restrict__ beta, double *__restrict__ y,
                          double *__restrict__ res_out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -230,20 +286,27 @@ __global__ void k_givens(int m, const double *__restrict__ H, const double *__re
   *res_out = fabs(gv[used]);
 }
 
-// dx += sum_j y_j V_j
-__global__ void k_combine(int64_t n, int m, const double *__restrict__ V, const double *__restrict__ y, double *__restrict__ dx) {
+// dx += sum_j y_j V_j (FP64 accumulation; V of either precision, stride vs)
+template <typename T>
+__global__ void k_combine(int64_t n, int64_t vs, int m, const T *__restrict__ V, const double *__restrict__ y,
+                          double *__restrict__ dx) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     double s = dx[k];
-    for (int j = 0; j < m; j++) s = fma(y[j], V[(size_t)j * n + k], s);
+    for (int j = 0; j < m; j++) s = fma(y[j], (double)V[(size_t)j * vs + k], s);
     dx[k] = s;
   }
+}
+
+// FP32 copies of the assembled blocks (mixed precision)
+__global__ void k_to_f32(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) b[k] = (float)a[k];
 }
 
 __global__ void __launch_bounds__(kBlock) k_density_l1(int N, const double *__restrict__ R, const double *__restrict__ inv_vol,
                                                        double *partials, unsigned int *count, double *out) {
   double s = 0.0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) s += fabs(R[k]) * inv_vol[k];
-  finish_reduction(block_sum(s), partials, count, out, 0);
+  grid_sum<double>(s, partials, count, out, 0);
 }
 
 __global__ void k_update(int64_t n5, int64_t ng, double *__restrict__ Q, const double *__restrict__ dQ, double *__restrict__ G,
@@ -260,35 +323,129 @@ unsigned vec_grid(int64_t n) {
   return (unsigned)std::max<int64_t>(1, std::min(g, cap));
 }
 
+// Buffers of one precision for the Krylov part of a step.
+template <typename T>
+struct KBuf {
+  const T *off, *dval, *dinv;
+  T *V, *w, *t, *t2, *red;
+};
+KBuf<double> kbuf64(Scratch &s) { return {s.off, s.dval, s.dinv, s.V, s.w, s.t, s.t2, s.red}; }
+KBuf<float> kbuf32(Scratch &s) { return {s.off32, s.dval32, s.dinv32, s.V32, s.w32, s.t32, s.t232, s.red32}; }
+
+// x = P^{-1} b (Eq. (precond)); if dotv is given, also (x, dotv) into *dot_out.
+template <typename T>
+void precondition_t(const DevMesh &m, Scratch &s, const KBuf<T> &k, int sweeps, const T *b, T *x, const T *dotv,
+                    double *dot_out, cudaStream_t st) {
+  const unsigned cg = grid_for(m.N, kCellBlock);
+  if (sweeps == 0) {
+    HGKS_PROF_BEGIN(K_DIAG, st);
+    k_diag_scale<T><<<grid_for(5 * (int64_t)m.N, kBlock), kBlock, 0, st>>>(m.N, k.dinv, b, x);
+    HGKS_PROF_END(K_DIAG, st);
+    if (dotv) {
+      HGKS_PROF_BEGIN(K_DOT, st);
+      k_axpy_dot<T><<<kRedBlocks, kBlock, 0, st>>>(5 * (int64_t)m.N, x, nullptr, nullptr, dotv, 0, k.red, s.red_count, dot_out);
+      HGKS_PROF_END(K_DOT, st);
+    }
+    return;
+  }
+  // sweep k writes to x when (sweeps - k) is even, else to t2: the last lands in x
+  const T *prev = nullptr;
+  for (int q = 1; q <= sweeps; q++) {
+    T *dst = ((sweeps - q) % 2 == 0) ? x : k.t2;
+    const T *dv = (q == sweeps) ? dotv : nullptr;
+    HGKS_PROF_BEGIN(K_JACOBI, st);
+    if (q == 1)
+      k_apply<T, T, T, kJacobi, true><<<cg, kCellBlock, 0, st>>>(m, k.off, k.dval, k.dinv, b, nullptr, dst, dv, k.red,
+                                                                  s.red_count, dot_out);
+    else
+      k_apply<T, T, T, kJacobi, false><<<cg, kCellBlock, 0, st>>>(m, k.off, k.dval, k.dinv, b, prev, dst, dv, k.red,
+                                                                   s.red_count, dot_out);
+    HGKS_PROF_END(K_JACOBI, st);
+    prev = dst;
+  }
+}
+
+// One restarted GMRES solve in precision T; rhs and dx stay FP64.
+template <typename T>
+void gmres_t(const DevMesh &m, Scratch &s, const KBuf<T> &k, const hgks_params &p, const double *rhs, double *dx,
+             cudaStream_t st) {
+  const int mk = p.krylov_dim;
+  const int64_t n = 5 * (int64_t)m.N, vs = s.vstride;
+  double *H = s.hs, *beta = s.hs + (mk + 1) * mk, *y = beta + 1, *lres = y + mk;
+  const unsigned vg = vec_grid(n), cg = grid_for(m.N, kCellBlock);
+  for (int it = 0; it < p.restarts; it++) {
+    cudaMemsetAsync(H, 0, sizeof(double) * (mk + 1) * mk, st);
+    // r0 = rhs - A dx (FP64 vectors, blocks of precision T), v1 = P^{-1} r0 / ||P^{-1} r0||
+    HGKS_PROF_BEGIN(K_SPMV, st);
+    k_apply<T, double, T, kSpmv, false><<<cg, kCellBlock, 0, st>>>(m, k.off, k.dval, k.dinv, rhs, dx, k.t, nullptr, nullptr,
+                                                                    nullptr, nullptr);
+    HGKS_PROF_END(K_SPMV, st);
+    precondition_t<T>(m, s, k, p.jacobi_sweeps, k.t, k.w, nullptr, nullptr, st);
+    HGKS_PROF_BEGIN(K_DOT, st);
+    k_axpy_dot<T><<<kRedBlocks, kBlock, 0, st>>>(n, k.w, nullptr, nullptr, k.w, 1, k.red, s.red_count, beta);
+    HGKS_PROF_END(K_DOT, st);
+    if (it == 0) cudaMemcpyAsync(lres, beta, sizeof(double), cudaMemcpyDeviceToDevice, st);
+    HGKS_PROF_BEGIN(K_SCALE, st);
+    k_scale<T><<<vg, kBlock, 0, st>>>(n, k.w, beta, k.V);
+    HGKS_PROF_END(K_SCALE, st);
+    for (int j = 0; j < mk; j++) {
+      // w = P^{-1} A v_j, with h_0j = (w, v_0) from the last sweep
+      HGKS_PROF_BEGIN(K_SPMV, st);
+      k_apply<T, T, T, kSpmv, false><<<cg, kCellBlock, 0, st>>>(m, k.off, k.dval, k.dinv, nullptr, k.V + (size_t)j * vs, k.t,
+                                                                 nullptr, nullptr, nullptr, nullptr);
+      HGKS_PROF_END(K_SPMV, st);
+      precondition_t<T>(m, s, k, p.jacobi_sweeps, k.t, k.w, k.V, H + j, st);
+      // modified Gram-Schmidt: w -= h_ij v_i, then h_{i+1,j} = (w, v_{i+1}) or ||w||
+      for (int i = 0; i <= j; i++) {
+        const bool last = (i == j);
+        HGKS_PROF_BEGIN(K_DOT, st);
+        k_axpy_dot<T><<<kRedBlocks, kBlock, 0, st>>>(n, k.w, k.V + (size_t)i * vs, H + i * mk + j,
+                                                       last ? k.w : k.V + (size_t)(i + 1) * vs, last ? 1 : 0, k.red,
+                                                       s.red_count, H + (i + 1) * mk + j);
+        HGKS_PROF_END(K_DOT, st);
+      }
+      HGKS_PROF_BEGIN(K_SCALE, st);
+      k_scale<T><<<vg, kBlock, 0, st>>>(n, k.w, H + (j + 1) * mk + j, k.V + (size_t)(j + 1) * vs);
+      HGKS_PROF_END(K_SCALE, st);
+    }
+    HGKS_PROF_BEGIN(K_GIVENS, st);
+    k_givens<<<1, 32, 0, st>>>(mk, H, beta, y, lres + 1);
+    HGKS_PROF_END(K_GIVENS, st);
+    HGKS_PROF_BEGIN(K_COMBINE, st);
+    k_combine<T><<<vg, kBlock, 0, st>>>(n, vs, mk, k.V, y, dx);
+    HGKS_PROF_END(K_COMBINE, st);
+  }
+}
+
 }  // namespace
 
 void launch_assemble(const DevMesh &m, Scratch &s, const hgks_params &p, const double *Q, const double *dt,
                      double *diag_out, double *off_out, cudaStream_t st) {
   HGKS_PROF_BEGIN(K_ASSEMBLE, st);
-  k_assemble<<<grid_for(m.N, 128), 128, 0, st>>>(m, p, Q, dt, s.dval, s.dinv, s.off, diag_out, off_out);
+  k_assemble<<<grid_for(m.N, kCellBlock), kCellBlock, 0, st>>>(m, p, Q, dt, s.dval, s.dinv, s.off, diag_out, off_out);
   HGKS_PROF_END(K_ASSEMBLE, st);
+  if (p.precision == HGKS_MIXED && s.off32) {
+    HGKS_PROF_BEGIN(K_ASSEMBLE, st);
+    k_to_f32<<<vec_grid(100 * (int64_t)m.N), kBlock, 0, st>>>(100 * (int64_t)m.N, s.off, s.off32);
+    HGKS_PROF_END(K_ASSEMBLE, st);
+    HGKS_PROF_BEGIN(K_ASSEMBLE, st);
+    k_to_f32<<<vec_grid(m.N), kBlock, 0, st>>>(m.N, s.dval, s.dval32);
+    HGKS_PROF_END(K_ASSEMBLE, st);
+    HGKS_PROF_BEGIN(K_ASSEMBLE, st);
+    k_to_f32<<<vec_grid(m.N), kBlock, 0, st>>>(m.N, s.dinv, s.dinv32);
+    HGKS_PROF_END(K_ASSEMBLE, st);
+  }
 }
 
 void launch_apply_A(const DevMesh &m, const Scratch &s, const double *x, double *y, cudaStream_t st) {
   HGKS_PROF_BEGIN(K_SPMV, st);
-  k_offdiag<true, false><<<grid_for(m.N, 128), 128, 0, st>>>(m, s.off, s.dval, s.dinv, nullptr, x, y);
+  k_apply<double, double, double, kSpmv, false><<<grid_for(m.N, kCellBlock), kCellBlock, 0, st>>>(
+      m, s.off, s.dval, s.dinv, nullptr, x, y, nullptr, nullptr, nullptr, nullptr);
   HGKS_PROF_END(K_SPMV, st);
 }
 
-// x = P^{-1} b: x0 = D^{-1} b, x_k = D^{-1} (b - (L+U) x_{k-1})
 void launch_precondition(const DevMesh &m, Scratch &s, int sweeps, const double *b, double *x, cudaStream_t st) {
-  double *bufs[2] = {s.t2, x};
-  double *cur = (sweeps % 2 == 0) ? x : s.t2;
-  HGKS_PROF_BEGIN(K_DIAG, st);
-  k_diag_scale<<<grid_for(5 * (int64_t)m.N, kBlock), kBlock, 0, st>>>(m.N, s.dinv, b, cur);
-  HGKS_PROF_END(K_DIAG, st);
-  for (int k = 1; k <= sweeps; k++) {
-    double *nxt = (cur == x) ? bufs[0] : bufs[1];
-    HGKS_PROF_BEGIN(K_JACOBI, st);
-    k_offdiag<false, true><<<grid_for(m.N, 128), 128, 0, st>>>(m, s.off, s.dval, s.dinv, b, cur, nxt);
-    HGKS_PROF_END(K_JACOBI, st);
-    cur = nxt;
-  }
+  precondition_t<double>(m, s, kbuf64(s), sweeps, b, x, nullptr, nullptr, st);
 }
 
 void launch_density_l1(const DevMesh &m, Scratch &s, const double *R, double *out_dev, cudaStream_t st) {
@@ -307,56 +464,10 @@ void launch_update(const DevMesh &m, double *Q, const double *dQ, double *G, con
 // hs layout: H[(m+1) m] | beta | y[m] | lin residual estimates
 hgks_status gmres_solve(const DevMesh &m, Scratch &s, const hgks_params &p, const double *rhs, double *dx,
                         hgks_step_info *info, cudaStream_t st) {
-  const int mk = p.krylov_dim;
-  const int64_t n = 5 * (int64_t)m.N;
-  double *H = s.hs, *beta = s.hs + (mk + 1) * mk, *y = beta + 1, *lres = y + mk;
-  const unsigned vg = vec_grid(n);
-  cudaMemsetAsync(dx, 0, sizeof(double) * n, st);
-  double *V = s.V;
-  for (int it = 0; it < p.restarts; it++) {
-    cudaMemsetAsync(H, 0, sizeof(double) * (mk + 1) * mk, st);
-    // r0 = rhs - A dx, v1 = P^{-1} r0 / ||P^{-1} r0||
-    HGKS_PROF_BEGIN(K_SPMV, st);
-    k_offdiag<true, false><<<grid_for(m.N, 128), 128, 0, st>>>(m, s.off, s.dval, s.dinv, rhs, dx, s.t);
-    HGKS_PROF_END(K_SPMV, st);
-    launch_precondition(m, s, p.jacobi_sweeps, s.t, s.w, st);
-    HGKS_PROF_BEGIN(K_DOT, st);
-    k_axpy_dot<<<kRedBlocks, kBlock, 0, st>>>(n, s.w, nullptr, nullptr, s.w, 1, s.red, s.red_count, beta);
-    HGKS_PROF_END(K_DOT, st);
-    if (it == 0) cudaMemcpyAsync(lres, beta, sizeof(double), cudaMemcpyDeviceToDevice, st);
-    HGKS_PROF_BEGIN(K_SCALE, st);
-    k_scale<<<vg, kBlock, 0, st>>>(n, s.w, beta, V);
-    HGKS_PROF_END(K_SCALE, st);
-    for (int j = 0; j < mk; j++) {
-      // w = P^{-1} A v_j
-      HGKS_PROF_BEGIN(K_SPMV, st);
-      k_offdiag<true, false><<<grid_for(m.N, 128), 128, 0, st>>>(m, s.off, s.dval, s.dinv, nullptr, V + (size_t)j * n, s.t);
-      HGKS_PROF_END(K_SPMV, st);
-      launch_precondition(m, s, p.jacobi_sweeps, s.t, s.w, st);
-      // modified Gram-Schmidt: h_ij = (w, v_i); w -= h_ij v_i; h_{j+1,j} = ||w||
-      HGKS_PROF_BEGIN(K_DOT, st);
-      k_axpy_dot<<<kRedBlocks, kBlock, 0, st>>>(n, s.w, nullptr, nullptr, V, 0, s.red, s.red_count, H + j);
-      HGKS_PROF_END(K_DOT, st);
-      for (int i = 0; i <= j; i++) {
-        const bool last = (i == j);
-        HGKS_PROF_BEGIN(K_DOT, st);
-        k_axpy_dot<<<kRedBlocks, kBlock, 0, st>>>(n, s.w, V + (size_t)i * n, H + i * mk + j,
-                                                    last ? s.w : V + (size_t)(i + 1) * n, last ? 1 : 0, s.red, s.red_count,
-                                                    H + (i + 1) * mk + j);
-        HGKS_PROF_END(K_DOT, st);
-      }
-      HGKS_PROF_BEGIN(K_SCALE, st);
-      k_scale<<<vg, kBlock, 0, st>>>(n, s.w, H + (j + 1) * mk + j, V + (size_t)(j + 1) * n);
-      HGKS_PROF_END(K_SCALE, st);
-    }
-    HGKS_PROF_BEGIN(K_GIVENS, st);
-    k_givens<<<1, 32, 0, st>>>(mk, H, beta, y, lres + 1);
-    HGKS_PROF_END(K_GIVENS, st);
-    HGKS_PROF_BEGIN(K_COMBINE, st);
-    k_combine<<<vg, kBlock, 0, st>>>(n, mk, V, y, dx);
-    HGKS_PROF_END(K_COMBINE, st);
-  }
-  if (info) info->krylov_iters = p.restarts * mk;
+  cudaMemsetAsync(dx, 0, sizeof(double) * 5 * (size_t)m.N, st);
+  if (p.precision == HGKS_MIXED) gmres_t<float>(m, s, kbuf32(s), p, rhs, dx, st);
+  else gmres_t<double>(m, s, kbuf64(s), p, rhs, dx, st);
+  if (info) info->krylov_iters = p.restarts * p.krylov_dim;
   return HGKS_OK;
 }
 

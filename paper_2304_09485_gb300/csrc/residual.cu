@@ -444,6 +444,24 @@ __device__ void boundary_state(const hgks_params &P, int tag, const double *T, c
   }
 }
 
+// out += s * J_d(W) x: the Euler flux along face-frame axis d, linearised at W
+// and applied to x. For the full-range moments of a Maxwellian,
+// <u_d (a_d . psi) psi> = J_d(W) dW/dx_d whenever <a_d> = dW/dx_d (a_d . psi g is the
+// derivative of g along dW), which replaces the moment sums of the time slopes.
+__device__ __forceinline__ void acc_jvp(const double *W, double gamma, int d, const double *x, double s, double *out) {
+  const double ir = 1.0 / W[0];
+  const double u[3] = {W[1] * ir, W[2] * ir, W[3] * ir};
+  const double q2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const double p = (gamma - 1.0) * (W[4] - 0.5 * W[0] * q2);
+  const double ud = u[d];
+  const double dud = (x[1 + d] - ud * x[0]) * ir;
+  const double dp = (gamma - 1.0) * (x[4] - (u[0] * x[1] + u[1] * x[2] + u[2] * x[3]) + 0.5 * q2 * x[0]);
+  out[0] = fma(s, x[1 + d], out[0]);
+#pragma unroll
+  for (int i = 0; i < 3; i++) out[1 + i] = fma(s, x[1 + i] * ud + u[i] * (x[1 + d] - ud * x[0]) + (i == d ? dp : 0.0), out[1 + i]);
+  out[4] = fma(s, (x[4] + dp) * ud + (W[4] + p) * dud, out[4]);
+}
+
 // Flux (time average over [0, dt] of int u psi f dXi, Eq. (flux)) and, if Qp
 // is not NULL, the point value int psi f dXi at t* (Eq. (point)). Face frame.
 __device__ void gks_flux(const hgks_params &P, const double *Wl, const double *dWl, const double *Wr, const double *dWr,
@@ -485,7 +503,7 @@ __device__ void gks_flux(const hgks_params &P, const double *Wl, const double *d
     const double *uh = s == 0 ? uhl : uhr;
     const double *dW = s == 0 ? dWl : dWr;
     const double irho = 1.0 / pk.rho;
-    double a[3][5], A[5], uf[7];
+    double a[3][5], A[5];
 #pragma unroll
     for (int d = 0; d < 3; d++) {
       double dq[5];
@@ -493,9 +511,11 @@ __device__ void gks_flux(const hgks_params &P, const double *Wl, const double *d
       for (int c = 0; c < 5; c++) dq[c] = dW[5 * d + c] * irho;
       slope(pk, K, dq, a[d]);
     }
-    mom_u_full(pk, uf);
+    // <a_n u + a_t1 v + a_t2 w + A> = 0 with <u_d (a_d.psi) psi> = J_d dW_d
     double rhs[5] = {0, 0, 0, 0, 0};
-    acc_slope_u(uf, mk, a, -1.0, rhs);
+    const double *Wk = s == 0 ? Wl : Wr;
+#pragma unroll
+    for (int d = 0; d < 3; d++) acc_jvp(Wk, gam, d, dW + 5 * d, -irho, rhs);
     slope(pk, K, rhs, A);
     // flux terms of g_k
     double fk[5] = {0, 0, 0, 0, 0};
@@ -523,7 +543,7 @@ __device__ void gks_flux(const hgks_params &P, const double *Wl, const double *d
     double uf[7];
     mom_u_full(p0, uf);
     const double irho = 1.0 / p0.rho;
-    double a[3][5], A[5];
+    double a[3][5];
 #pragma unroll
     for (int d = 0; d < 3; d++) {
       double dq[5];
@@ -531,15 +551,14 @@ __device__ void gks_flux(const hgks_params &P, const double *Wl, const double *d
       for (int c = 0; c < 5; c++) dq[c] = dWs[5 * d + c] * irho;
       slope(p0, K, dq, a[d]);
     }
-    double S0[5] = {0, 0, 0, 0, 0}, rhs[5];
-    acc_slope_u(uf, m0, a, 1.0, S0);       // <(abar . u_vec) psi>
+    // S0 = <(abar . u_vec) psi> = sum_d J_d(Q0) dQ0_d; <Abar psi> = -S0; <u Abar psi> = -J_x(Q0) S0
+    double S0[5] = {0, 0, 0, 0, 0};
 #pragma unroll
-    for (int c = 0; c < 5; c++) rhs[c] = -S0[c];
-    slope(p0, K, rhs, A);                  // <Abar psi> = -S0
+    for (int d = 0; d < 3; d++) acc_jvp(Q0, gam, d, dWs + 5 * d, irho, S0);
     double f0[5] = {0, 0, 0, 0, 0};
     acc_psi<1, 0, 0>(uf, m0.v, m0.w, m0.xi2, c1, f0);
     acc_u_slope_u(uf, m0, a, c2, f0);
-    acc_apsi<1, 0, 0>(uf, m0, A, c3, f0);
+    acc_jvp(Q0, gam, 0, S0, -c3, f0);
 #pragma unroll
     for (int c = 0; c < 5; c++) Fl[c] = fma(p0.rho, f0[c], Fl[c]);
     if (want_pt || prandtl) {

@@ -254,3 +254,80 @@ def test_full_size_sphere_sampled(cuda):
     scale = flux_scale(om, Q)
     err = np.abs(Rg[cells] - Ro[cells]) / scale[cells]
     assert err.max() <= TOL_R, err.max()
+
+
+def five_tet_cube():
+    """A unit cube split into 5 tetrahedra (odd cell count), far field on all sides."""
+    V = np.array([[a, b, c] for a in (0, 1) for b in (0, 1) for c in (0, 1)], dtype=np.float64)
+    idx = {tuple(v): k for k, v in enumerate(V.astype(int))}
+    even = [idx[(0, 0, 0)], idx[(1, 1, 0)], idx[(1, 0, 1)], idx[(0, 1, 1)]]
+    tets = [even]
+    bf = []
+    for odd in [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 1)]:
+        nb = [idx[tuple(np.array(odd) ^ np.eye(3, dtype=int)[d])] for d in range(3)]
+        tets.append([idx[odd]] + nb)
+        for d in range(3):
+            bf.append([idx[odd]] + [nb[k] for k in range(3) if k != d])
+    tet = np.array(tets, dtype=np.int64)
+    a = V[tet[:, 0]]
+    s = np.einsum("ij,ij->i", V[tet[:, 1]] - a, np.cross(V[tet[:, 2]] - a, V[tet[:, 3]] - a))
+    tet[s < 0, 2], tet[s < 0, 3] = tet[s < 0, 3].copy(), tet[s < 0, 2].copy()
+    return I.Mesh(V, tet, np.array(bf, dtype=np.int64), np.full(len(bf), I.BC_FARFIELD, np.int32))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_odd_cell_count(cuda, precision):
+    import torch
+    m = five_tet_cube()
+    cond = I.sphere_conditions(0.3)
+    om = O.OracleMesh(m)
+    hm = H.hgks_mesh_create(m, scheme_mask=2)
+    Q, G = I.smooth_state(m, amp=0.05, base=(1.0, 0.3, 0.05, -0.02, 1 / GAMMA))
+    kw = dict(scheme=1, krylov_dim=7, **cond)
+    Qo, Go, reso, dQo = om.gmres_step(O.make_params(**kw), Q, G)
+    Qd, Gd = hm.to_internal(Q), hm.to_internal(G)
+    dQd = torch.empty_like(Qd)
+    info = H.hgks_gmres_step(hm, H.hgks_default_params(precision=precision, **kw), Qd, Gd, dQd)
+    assert info.res_l1 == pytest.approx(reso, rel=1e-11)
+    rel = np.linalg.norm(hm.to_caller(dQd) - dQo) / np.linalg.norm(dQo)
+    assert rel <= (1e-9 if precision == 0 else 1e-4), rel
+
+
+MIXED_TOL = {"dQ_step": 1e-4, "Q_5steps": 1e-6}
+
+
+@pytest.mark.parametrize("name,kw", [("sphere6x6", dict(scheme=0, krylov_dim=20)),
+                                     ("sphere6x6_visc", dict(scheme=1, Pr=0.72, cfl=20.0)),
+                                     ("cavity8", dict(scheme=1, Pr=0.72))])
+def test_mixed_precision_step_error(cuda, name, kw):
+    """FP32 Krylov basis, Arnoldi and Jacobi (FP64 residual, update and least squares):
+    the update of one implicit step against the FP64 oracle."""
+    import torch
+    m, cond, om, hm = setup(name)
+    Q, G = state(m, cond, seed=9)
+    po = O.make_params(**{**cond, **kw})
+    Qo, Go, reso, dQo = om.gmres_step(po, Q, G)
+    ph = H.hgks_default_params(precision=1, **{**cond, **kw})
+    Qd, Gd = hm.to_internal(Q), hm.to_internal(G)
+    dQd = torch.empty_like(Qd)
+    info = H.hgks_gmres_step(hm, ph, Qd, Gd if kw["scheme"] == 1 else None, dQd)
+    assert info.res_l1 == pytest.approx(reso, rel=1e-11)     # the residual stays FP64
+    rel = np.linalg.norm(hm.to_caller(dQd) - dQo) / np.linalg.norm(dQo)
+    print(f"mixed precision {name}: relative L2 error of dQ against the FP64 oracle = {rel:.3e}")
+    assert rel <= MIXED_TOL["dQ_step"], rel
+
+
+def test_mixed_precision_trajectory_error(cuda):
+    """Five implicit steps on the viscous sphere (compact scheme): mixed precision against
+    the FP64 oracle, relative L2 of the state."""
+    m, cond, om, hm = setup("sphere6x6_visc")
+    kw = dict(scheme=1, Pr=0.72, cfl=20.0)
+    po = O.make_params(**{**cond, **kw}); ph = H.hgks_default_params(precision=1, **{**cond, **kw})
+    Q = I.state_from_conditions(m.n_tet, cond); G = np.zeros((m.n_tet, 15))
+    Qd, Gd = hm.to_internal(Q), hm.to_internal(G)
+    for k in range(5):
+        Q, G, res, _ = om.gmres_step(po, Q, G)
+        H.hgks_gmres_step(hm, ph, Qd, Gd)
+    rel = np.linalg.norm(hm.to_caller(Qd) - Q) / np.linalg.norm(Q)
+    print(f"mixed precision, 5 steps: relative L2 error of Q against the FP64 oracle = {rel:.3e}")
+    assert rel <= MIXED_TOL["Q_5steps"], rel
