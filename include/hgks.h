@@ -193,6 +193,24 @@ hgks_status hgks_residual_host(hgks_mesh mesh, const hgks_params *p, const doubl
 hgks_status hgks_gmres_step_host(hgks_mesh mesh, const hgks_params *p, double *Q_host,
                                  double *G_host, hgks_step_info *info, void *cuda_stream);
 
+/* hgks_residual with no memory allocation of its own. The paper has no
+ * counterpart: this serves callers that cannot call cudaMalloc once they are
+ * running (for example a process whose device memory is handed out by another
+ * runtime at start-up, or a service that must not enter the CUDA allocator while
+ * it answers requests). The mesh is still created up front with
+ * hgks_mesh_create; this call then allocates and frees nothing and leaves the
+ * handle's own scratch untouched: its scratch is one fixed array of 32 MiB
+ * compiled into the library, which every GPU that loads the library holds until
+ * the process exits. Meshes larger than that scratch allows (about 10,000
+ * tetrahedra: 106 N + 150 F doubles) are rejected with HGKS_ERR_ARG. Arguments,
+ * layouts and results are those of hgks_residual. The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture. All calls share the
+ * one array and it keeps the previous call's contents: calls that may overlap
+ * on the GPU (several streams or host threads) race with each other. */
+hgks_status hgks_residual_noalloc(hgks_mesh mesh, const hgks_params *p, const double *Q, const double *G,
+                                  double *R, double *G_new, void *cuda_stream);
+
 /* Wait for the stream and report any deferred device-side error. */
 hgks_status hgks_sync(void *cuda_stream);
 

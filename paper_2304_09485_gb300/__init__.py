@@ -82,6 +82,7 @@ def lib():
             "hgks_residual_host": [vp, P, dp, dp, dp, dp, vp],
             "hgks_gmres_step_host": [vp, P, dp, dp, C.POINTER(hgks_step_info), vp],
             "hgks_sync": [vp],
+            "hgks_residual_noalloc": [vp, P, dp, dp, dp, dp, vp],
             "hgks_profile_begin": [],
             "hgks_profile_end": [i32, dp, dp, dp, C.POINTER(C.c_int32)],
         }
@@ -188,6 +189,12 @@ def hgks_mesh_volumes(mesh: hgks_mesh) -> np.ndarray:
 
 def hgks_residual(mesh, params, Q, G, R, G_new=None, stream=None):
     _check(lib().hgks_residual(mesh.handle, C.byref(params), _ptr(Q), _ptr(G), _ptr(R), _ptr(G_new), _stream(stream)))
+
+
+def hgks_residual_noalloc(mesh, params, Q, G, R, G_new=None, stream=None):
+    """hgks_residual with its scratch in the library's fixed static array (no allocation)."""
+    _check(lib().hgks_residual_noalloc(mesh.handle, C.byref(params), _ptr(Q), _ptr(G), _ptr(R), _ptr(G_new),
+                                       _stream(stream)))
 
 
 def hgks_local_dt(mesh, params, Q, dt, stream=None):

@@ -145,6 +145,8 @@ hgks_status last_launch() {
 }  // namespace
 
 namespace hgks {
+Mesh *mesh_of(hgks_mesh h) { return &h->m; }
+void set_last_error(const char *msg) { g_err = msg; }
 bool g_prof_on = false;
 namespace {
 struct ProfRec { int kid; cudaEvent_t a, b; };

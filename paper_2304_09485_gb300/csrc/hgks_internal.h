@@ -113,6 +113,10 @@ void launch_density_l1(const DevMesh &m, Scratch &s, const double *R, double *ou
 void launch_update(const DevMesh &m, double *Q, const double *dQ, double *G, const double *Gnew, int ncomp_g,
                    cudaStream_t st);
 
+// accessors for entry points defined outside capi.cu
+Mesh *mesh_of(hgks_mesh h);
+void set_last_error(const char *msg);
+
 extern thread_local int64_t g_launches;
 inline void count_launch() { ++g_launches; }
 
