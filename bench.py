@@ -38,6 +38,10 @@ FP64_PEAK_GFLOPS = 1258.6
 # FP64 flops per unit of work of each kernel (2 per DFMA, 1 per DADD/DMUL), from the
 # ncu sass counters of the kernels on the 124,416-tet sphere (non-compact scheme,
 # inviscid, Pr = 1); see DESIGN.md "Roofline". unit -> (flops per unit, units)
+# DRAM bytes per unit of work from the same ncu captures (dram__bytes_read.sum +
+# dram__bytes_write.sum divided by the units of the 124,416-tet launch); the
+# traffic of a full launch is this times its units (traffic grows with the units).
+KERNEL_TRAFFIC = {"flux": 490.1, "recon": 4265.0, "jacobi": 931.0, "spmv": 889.0}
 KERNEL_FLOPS = {
     "flux": (3853.0, lambda N, F: 3 * F),        # per face Gauss point
     "recon": (4298.0, lambda N, F: 4 * N),       # per (cell, face)
@@ -106,6 +110,18 @@ class ClockSampler:
             out = {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
                    "samples": len(sm)}
         return out
+
+
+def aggregate(local_ms, n_cells, steps, world, device="cpu"):
+    """Max of the per-rank times (all ranks run their own replica) and the
+    whole-job throughput in Mcells/s: world * cells * steps / max time."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return ms, world * n_cells * steps / (ms / 1000.0) / 1e6
 
 
 def measured_peaks():
@@ -225,12 +241,7 @@ def main():
     prof = H.hgks_profile_end()
     launches = H.hgks_launch_count()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], device=f"cuda:{local}", dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
-    value = world * m.n_tet * args.steps / (ms / 1000.0) / 1e6
+    ms, value = aggregate(ev0.elapsed_time(ev1), m.n_tet, args.steps, world, device=f"cuda:{local}")
 
     if args.launch_list:
         if rank == 0:
@@ -249,6 +260,20 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     res_ms = e0.elapsed_time(e1) / nres
+
+    # the same step with the Krylov part in FP32 (precision = mixed), same state
+    pm = H.hgks_default_params(precision=1, **kw)
+    Qm = Q.clone()
+    for _ in range(2):
+        H.hgks_gmres_step(hm, pm, Qm)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        H.hgks_gmres_step(hm, pm, Qm)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    mixed_ms = e0.elapsed_time(e1) / args.steps
+    del Qm
 
     # end to end through the C ABI with host buffers: copies inside the timed region
     Qh = torch.empty((5, m.n_tet), dtype=torch.float64, pin_memory=True)
@@ -280,6 +305,9 @@ def main():
             per, units = KERNEL_FLOPS[name]
             fl = per * units(m.n_tet, F)
             r.update({"achieved": fl / avg_s / 1e9, "frac": fl / avg_s / 1e9 / FP64_PEAK_GFLOPS, "flops_per_launch": fl})
+            if name in KERNEL_TRAFFIC:
+                r["traffic"] = KERNEL_TRAFFIC[name] * units(m.n_tet, F)
+                r["traffic_note"] = "bytes per launch: ncu dram bytes per unit on the 124,416-tet sphere x units"
         else:
             r.update({"achieved": None, "frac": None})
         return r
@@ -294,6 +322,8 @@ def main():
                    "step": "dt + R(U) + A + 3 x GMRES(20) + update",
                    "l2": "inputs larger than L2 (mesh data + Jacobian + Krylov basis >> 129 MB)"},
         "residual_only": {"value": m.n_tet / (res_ms / 1000.0) / 1e6, "unit": "Mcells/s", "ms": res_ms},
+        "mixed": {"value": world * m.n_tet / (mixed_ms / 1000.0) / 1e6, "unit": "Mcells/s", "ms_per_step": mixed_ms,
+                  "note": "same step with FP32 Krylov basis, Arnoldi and Jacobi (FP64 residual and update)"},
         "e2e": {"value": e2e_val, "unit": "Mcells/s", "h2d_bytes_per_step": 5 * 8 * m.n_tet,
                 "d2h_bytes_per_step": 5 * 8 * m.n_tet},
         "gpu_launches": int(launches),
