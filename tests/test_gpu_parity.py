@@ -331,3 +331,21 @@ def test_mixed_precision_trajectory_error(cuda):
     rel = np.linalg.norm(hm.to_caller(Qd) - Q) / np.linalg.norm(Q)
     print(f"mixed precision, 5 steps: relative L2 error of Q against the FP64 oracle = {rel:.3e}")
     assert rel <= MIXED_TOL["Q_5steps"], rel
+
+
+def test_solve_steady_parity(cuda):
+    """Algorithm 1 through hgks_solve_steady on the small inviscid sphere (non-compact
+    scheme) against orc_solve_steady: same number of steps to a 5e-2 drop of the density
+    residual, and the same state (relative L2 1e-9)."""
+    m, cond, om, hm = setup("sphere6x6")
+    kw = dict(scheme=0, krylov_dim=10)
+    Q0 = I.state_from_conditions(m.n_tet, cond)
+    Qo, _, hist_o, conv_o = om.solve_steady(O.make_params(**{**cond, **kw}), Q0, drop=5e-2, max_steps=200)
+    Qd = hm.to_internal(Q0)
+    info, hist_g, conv_g = H.hgks_solve_steady(hm, H.hgks_default_params(**{**cond, **kw}), Qd, None,
+                                               drop_tol=5e-2, max_steps=200)
+    assert conv_o and conv_g
+    assert info.steps == len(hist_o) - 1
+    np.testing.assert_allclose(hist_g, hist_o, rtol=1e-8)
+    rel = np.linalg.norm(hm.to_caller(Qd) - Qo) / np.linalg.norm(Qo)
+    assert rel <= 1e-9, rel
