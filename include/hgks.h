@@ -211,6 +211,73 @@ hgks_status hgks_gmres_step_host(hgks_mesh mesh, const hgks_params *p, double *Q
 hgks_status hgks_residual_noalloc(hgks_mesh mesh, const hgks_params *p, const double *Q, const double *G,
                                   double *R, double *G_new, void *cuda_stream);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many independent steady problems advanced together, one kernel
+ * launch per phase (reconstruction, flux, assembly, each Arnoldi step) for all
+ * of them. Each mesh keeps its own parameters, state, Krylov space, Hessenberg
+ * least-squares problem and convergence test, so a mesh follows Algorithm 1
+ * exactly as it does alone (the only difference is the summation order inside
+ * inner products). The paper solves one problem at a time; batching is this
+ * library's way of filling one GPU with problems smaller than it.
+ * ------------------------------------------------------------------------- */
+typedef struct hgks_batch_s *hgks_batch;          /* opaque */
+
+typedef struct {
+  int64_t n_cells;           /* cells of the merged cell space, padding included      */
+  int64_t n_faces;
+  int64_t device_bytes;      /* device memory held by the batch                        */
+  int32_t n_meshes;
+  int32_t blk_recon, blk_flux;  /* launch shapes in use (hgks_batch_autotune)          */
+} hgks_batch_info_t;
+
+/* Merge n_meshes meshes (handles of one device) into a batch, with params[k]
+ * for mesh k (copied). The batch holds its own copy of every mesh's device
+ * data, so the handles may be destroyed afterwards. Mesh k's cells occupy a
+ * range of the merged cell space that starts on a multiple of 256; the cells
+ * between ranges are inert padding. scheme, precision, jv_mode, krylov_dim,
+ * restarts and jacobi_sweeps must agree across params; the rest (gamma, Pr,
+ * mu, viscous, cfl, free stream, walls, weights ...) may differ per mesh.
+ * State starts at zero: set it with hgks_batch_set_state. Errors: HGKS_ERR_ARG
+ * (n_meshes < 1 or > 32767, NULL, disagreeing parameters, a mesh built without
+ * the scheme's data, meshes on different devices), HGKS_ERR_OOM, HGKS_ERR_CUDA. */
+hgks_status hgks_batch_create(const hgks_mesh *meshes, const hgks_params *params, int32_t n_meshes,
+                              hgks_batch *out);
+hgks_status hgks_batch_destroy(hgks_batch batch);
+hgks_status hgks_batch_info(hgks_batch batch, hgks_batch_info_t *info);
+
+/* Copy mesh k's state in (set) or out (get). Q, R: device double[5][N_k], G,
+ * G_new: device double[15][N_k] (compact scheme; NULL otherwise), in mesh k's
+ * internal order, N_k its cell count. Any pointer of get_state may be NULL;
+ * R and G_new are those of the last hgks_batch_residual / step. */
+hgks_status hgks_batch_set_state(hgks_batch batch, int32_t k, const double *Q, const double *G,
+                                 void *cuda_stream);
+hgks_status hgks_batch_get_state(hgks_batch batch, int32_t k, double *Q, double *G, double *R,
+                                 double *G_new, void *cuda_stream);
+
+/* R(Q) (and G_new) of every mesh of the batch, as hgks_residual does for one. */
+hgks_status hgks_batch_residual(hgks_batch batch, void *cuda_stream);
+
+/* One outer step of Algorithm 1 for every mesh (as hgks_gmres_step).
+ * info (host, may be NULL) receives n_meshes records. Synchronises the stream. */
+hgks_status hgks_batch_gmres_step(hgks_batch batch, hgks_step_info *info, void *cuda_stream);
+
+/* Algorithm 1 for every mesh until each has converged (res/res_ref <= drop_tol,
+ * as hgks_solve_steady) or taken max_steps steps; a finished mesh is skipped
+ * by every later launch and keeps its state. The convergence test runs on the
+ * device, so the step's launch sequence is fixed: with use_graph != 0 it is
+ * captured once in a CUDA graph (on a stream owned by the batch, ordered after
+ * the caller's stream) and replayed. hist_host (may be NULL) receives
+ * n_meshes x (max_steps + 1) residuals, row k for mesh k (0 past its last
+ * step); info (host) n_meshes records. Returns HGKS_ERR_NOT_CONVERGED if any
+ * mesh hit max_steps, HGKS_ERR_NONPHYSICAL if any residual was not finite. */
+hgks_status hgks_batch_solve_steady(hgks_batch batch, double drop_tol, int32_t max_steps, int32_t use_graph,
+                                    double *hist_host, hgks_solve_info *info, void *cuda_stream);
+
+/* Time the reconstruction and flux kernels of this batch's current state at
+ * block sizes 64, 128 and 256 (CUDA events, 3 runs each) and keep the fastest
+ * for later calls; the chosen sizes are returned (may be NULL). */
+hgks_status hgks_batch_autotune(hgks_batch batch, int32_t *blk_recon, int32_t *blk_flux, void *cuda_stream);
+
 /* Wait for the stream and report any deferred device-side error. */
 hgks_status hgks_sync(void *cuda_stream);
 

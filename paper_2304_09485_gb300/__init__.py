@@ -51,6 +51,11 @@ class hgks_solve_info(C.Structure):
                 ("res_final", C.c_double)]
 
 
+class hgks_batch_info_t(C.Structure):
+    _fields_ = [("n_cells", C.c_int64), ("n_faces", C.c_int64), ("device_bytes", C.c_int64),
+                ("n_meshes", C.c_int32), ("blk_recon", C.c_int32), ("blk_flux", C.c_int32)]
+
+
 class HGKSError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"hgks status {status}: {msg}")
@@ -83,6 +88,15 @@ def lib():
             "hgks_gmres_step_host": [vp, P, dp, dp, C.POINTER(hgks_step_info), vp],
             "hgks_sync": [vp],
             "hgks_residual_noalloc": [vp, P, dp, dp, dp, dp, vp],
+            "hgks_batch_create": [dp, P, i32, C.POINTER(vp)],
+            "hgks_batch_destroy": [vp],
+            "hgks_batch_info": [vp, C.POINTER(hgks_batch_info_t)],
+            "hgks_batch_set_state": [vp, i32, dp, dp, vp],
+            "hgks_batch_get_state": [vp, i32, dp, dp, dp, dp, vp],
+            "hgks_batch_residual": [vp, vp],
+            "hgks_batch_gmres_step": [vp, dp, vp],
+            "hgks_batch_solve_steady": [vp, C.c_double, i32, i32, dp, dp, vp],
+            "hgks_batch_autotune": [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), vp],
             "hgks_profile_begin": [],
             "hgks_profile_end": [i32, dp, dp, dp, C.POINTER(C.c_int32)],
         }
@@ -239,6 +253,75 @@ def hgks_gmres_step_host(mesh, params, Q_host, G_host=None, stream=None) -> hgks
     _check(lib().hgks_gmres_step_host(mesh.handle, C.byref(params), _ptr(Q_host), _ptr(G_host), C.byref(info),
                                       _stream(stream)))
     return info
+
+
+class hgks_batch:
+    """A batch handle over several meshes (hgks_batch_create); keeps the meshes' order."""
+
+    def __init__(self, handle, meshes, params):
+        self.handle = C.c_void_p(handle)
+        self.meshes = list(meshes)
+        self.params = list(params)
+
+    def __len__(self):
+        return len(self.meshes)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            try:
+                lib().hgks_batch_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = C.c_void_p(0)
+
+
+def hgks_batch_create(meshes, params) -> hgks_batch:
+    n = len(meshes)
+    hs = (C.c_void_p * n)(*[m.handle.value for m in meshes])
+    ps = (hgks_params * n)(*params)
+    h = C.c_void_p()
+    _check(lib().hgks_batch_create(C.addressof(hs), ps, n, C.byref(h)))
+    return hgks_batch(h.value, meshes, params)
+
+
+def hgks_batch_info(batch) -> hgks_batch_info_t:
+    info = hgks_batch_info_t()
+    _check(lib().hgks_batch_info(batch.handle, C.byref(info)))
+    return info
+
+
+def hgks_batch_set_state(batch, k, Q, G=None, stream=None):
+    _check(lib().hgks_batch_set_state(batch.handle, k, _ptr(Q), _ptr(G), _stream(stream)))
+
+
+def hgks_batch_get_state(batch, k, Q=None, G=None, R=None, G_new=None, stream=None):
+    _check(lib().hgks_batch_get_state(batch.handle, k, _ptr(Q), _ptr(G), _ptr(R), _ptr(G_new), _stream(stream)))
+
+
+def hgks_batch_residual(batch, stream=None):
+    _check(lib().hgks_batch_residual(batch.handle, _stream(stream)))
+
+
+def hgks_batch_gmres_step(batch, stream=None):
+    info = (hgks_step_info * len(batch))()
+    _check(lib().hgks_batch_gmres_step(batch.handle, info, _stream(stream)))
+    return list(info)
+
+
+def hgks_batch_solve_steady(batch, drop_tol=1e-8, max_steps=1000, use_graph=True, stream=None):
+    """(infos, hist [n, max_steps+1], all_converged) of Algorithm 1 run on every mesh of the batch."""
+    n = len(batch)
+    hist = np.zeros((n, max_steps + 1))
+    info = (hgks_solve_info * n)()
+    st = _check(lib().hgks_batch_solve_steady(batch.handle, drop_tol, max_steps, 1 if use_graph else 0, _ptr(hist),
+                                              info, _stream(stream)), allow=(HGKS_ERR_NOT_CONVERGED,))
+    return list(info), hist, st == HGKS_OK
+
+
+def hgks_batch_autotune(batch, stream=None):
+    r, f = C.c_int32(0), C.c_int32(0)
+    _check(lib().hgks_batch_autotune(batch.handle, C.byref(r), C.byref(f), _stream(stream)))
+    return r.value, f.value
 
 
 def hgks_sync(stream=None):

@@ -17,8 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhgks.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["residual.cu", "implicit.cu", "capi.cu", "noalloc.cu", "mesh_setup.cpp"]
-HEADERS = ["hgks_internal.h"]
+SOURCES = ["residual.cu", "implicit.cu", "batch.cu", "batch_capi.cu", "capi.cu", "noalloc.cu", "mesh_setup.cpp"]
+HEADERS = ["hgks_internal.h", "givens.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

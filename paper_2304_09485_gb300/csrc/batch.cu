@@ -1,0 +1,354 @@
+// Batches of independent meshes: one launch per phase for all of them.
+//
+// A batch merges its meshes into one cell space. Each mesh's cells start on a
+// multiple of 256 (kBatchBlock), padded with inert cells, so a block of 256
+// cells always belongs to exactly one mesh. The residual kernels run once over
+// the merged space, reading each cell's (or face's) parameters from a per-mesh
+// table. The GMRES part keeps one Krylov space per mesh: every inner product is
+// a segmented reduction (the blocks of one mesh write partial sums, the last of
+// them to finish adds that mesh's partials in a fixed order), the Hessenberg
+// least-squares problems are solved one device thread per mesh, and the vector
+// updates read their mesh's coefficients. A mesh in a batch therefore follows
+// the same algorithm as alone (Algorithm 1), with its own Krylov space.
+#include <algorithm>
+#include <cmath>
+#include "hgks_internal.h"
+#include "givens.cuh"
+
+namespace hgks {
+namespace {
+
+constexpr int kB = kBatchBlock;
+
+template <typename T>
+__device__ __forceinline__ T bsum(T v) {
+  __shared__ T sh[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  T s = T(0);
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : T(0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  }
+  return s;
+}
+
+// per-mesh segmented sum: *out(mesh) = sum over the mesh's blocks (or its sqrt)
+template <typename T>
+__device__ __forceinline__ void mesh_sum(T v, const BatchDev &b, T *part, double *out, int stride, int mode) {
+  __shared__ bool last;
+  const int mesh = b.bmesh[blockIdx.x];
+  const T s0 = bsum(v);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s0;
+    __threadfence();
+    const unsigned prev = atomicAdd(b.counters + mesh, 1u);
+    last = (prev == (unsigned)(b.bstart[mesh + 1] - b.bstart[mesh] - 1));
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  T s = T(0);
+  for (int k = b.bstart[mesh] + threadIdx.x; k < b.bstart[mesh + 1]; k += blockDim.x) s += ((volatile T *)part)[k];
+  s = bsum(s);
+  if (threadIdx.x == 0) {
+    out[(size_t)mesh * stride] = mode == 1 ? (double)sqrt(s) : (double)s;
+    b.counters[mesh] = 0u;
+  }
+}
+
+enum { kSpmv = 0, kJacobi = 1 };
+// SpMV / Jacobi sweep over the merged cells with an optional per-mesh (y, dotv)
+template <typename TM, typename TV, typename TO, int Mode, bool First>
+__global__ void __launch_bounds__(kB) k_bapply(DevMesh m, BatchDev bd, const TM *__restrict__ off,
+                                               const TM *__restrict__ dval, const TM *__restrict__ dinv,
+                                               const TV *__restrict__ b, const TV *__restrict__ x, TO *__restrict__ y,
+                                               const TO *__restrict__ dotv, TO *part, double *dot_out, int stride) {
+  const int N = m.N;
+  const int i = blockIdx.x * kB + threadIdx.x;
+  if (!bd.active[bd.bmesh[blockIdx.x]]) return;
+  TV acc[5];
+  const TV di = Mode == kSpmv ? (TV)dval[i] : TV(0);
+#pragma unroll
+  for (int r = 0; r < 5; r++) acc[r] = Mode == kSpmv ? di * x[(size_t)r * N + i] : TV(0);
+#pragma unroll
+  for (int p = 0; p < 4; p++) {
+    const int j = m.cnb[(size_t)p * N + i];
+    if (j < 0) continue;
+    TV xj[5];
+    const TV sj = First ? (TV)dinv[j] : TV(1);
+#pragma unroll
+    for (int c = 0; c < 5; c++) xj[c] = First ? sj * b[(size_t)c * N + j] : x[(size_t)c * N + j];
+    const TM *O = off + (size_t)p * 25 * N + i;
+#pragma unroll
+    for (int r = 0; r < 5; r++)
+#pragma unroll
+      for (int c = 0; c < 5; c++) acc[r] = fma((TV)O[(size_t)(5 * r + c) * N], xj[c], acc[r]);
+  }
+  TO part_v = TO(0);
+#pragma unroll
+  for (int r = 0; r < 5; r++) {
+    TV o;
+    if (Mode == kJacobi) o = (TV)dinv[i] * (b[(size_t)r * N + i] - acc[r]);
+    else o = b ? b[(size_t)r * N + i] - acc[r] : acc[r];
+    const TO oo = (TO)o;
+    y[(size_t)r * N + i] = oo;
+    if (dotv) part_v = fma(oo, dotv[(size_t)r * N + i], part_v);
+  }
+  if (dotv) mesh_sum(part_v, bd, part, dot_out, stride, 0);
+}
+
+// w -= h(mesh) v (if v); out(mesh) = (w, x) or ||w|| (self)
+template <typename T>
+__global__ void __launch_bounds__(kB) k_baxpy_dot(int N, BatchDev bd, T *__restrict__ w, const T *__restrict__ v,
+                                                  const double *__restrict__ h, int hstride, const T *__restrict__ x,
+                                                  int self, T *part, double *out, int stride) {
+  const int i = blockIdx.x * kB + threadIdx.x;
+  const int mesh = bd.bmesh[blockIdx.x];
+  if (!bd.active[mesh]) return;
+  const T hv = v ? (T)(-h[(size_t)mesh * hstride]) : T(0);
+  T s = T(0);
+#pragma unroll
+  for (int c = 0; c < 5; c++) {
+    const size_t k = (size_t)c * N + i;
+    T wk = w[k];
+    if (v) { wk = fma(hv, v[k], wk); w[k] = wk; }
+    s = fma(wk, self ? wk : x[k], s);
+  }
+  mesh_sum(s, bd, part, out, stride, self);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kB) k_bscale(int N, BatchDev bd, const T *__restrict__ w, const double *__restrict__ h,
+                                               int hstride, T *__restrict__ v) {
+  const int i = blockIdx.x * kB + threadIdx.x;
+  if (!bd.active[bd.bmesh[blockIdx.x]]) return;
+  const double hv = h[(size_t)bd.bmesh[blockIdx.x] * hstride];
+  const T ih = hv != 0.0 ? (T)(1.0 / hv) : T(0);
+#pragma unroll
+  for (int c = 0; c < 5; c++) v[(size_t)c * N + i] = w[(size_t)c * N + i] * ih;
+}
+
+// one thread per mesh: y(mesh) = argmin || beta e1 - H y ||
+__global__ void k_bgivens(BatchDev bd, int m, double *__restrict__ hs, int stride) {
+  const int mesh = blockIdx.x * blockDim.x + threadIdx.x;
+  if (mesh >= bd.nmesh || !bd.active[mesh]) return;
+  double *H = hs + (size_t)mesh * stride, *beta = H + (m + 1) * m, *y = beta + 1, *lres = y + m;
+  lres[1] = givens_lsq(m, H, *beta, y);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kB) k_bcombine(int N, BatchDev bd, int64_t vs, int m, const T *__restrict__ V,
+                                                 const double *__restrict__ hs, int stride, double *__restrict__ dx) {
+  const int i = blockIdx.x * kB + threadIdx.x;
+  if (!bd.active[bd.bmesh[blockIdx.x]]) return;
+  const double *y = hs + (size_t)bd.bmesh[blockIdx.x] * stride + (m + 1) * m + 1;
+#pragma unroll
+  for (int c = 0; c < 5; c++) {
+    const size_t k = (size_t)c * N + i;
+    double s = dx[k];
+    for (int j = 0; j < m; j++) s = fma(y[j], (double)V[(size_t)j * vs + k], s);
+    dx[k] = s;
+  }
+}
+
+// per-mesh L1 norm of the density residual (padding cells hold R = 0)
+__global__ void __launch_bounds__(kB) k_bdensity(int N, BatchDev bd, const double *__restrict__ R,
+                                                 const double *__restrict__ inv_vol, double *part, double *out, int stride) {
+  const int i = blockIdx.x * kB + threadIdx.x;
+  if (!bd.active[bd.bmesh[blockIdx.x]]) return;
+  mesh_sum(fabs(R[i]) * inv_vol[i], bd, part, out, stride, 0);
+}
+
+// Q += dQ and G = G_new for the meshes still iterating
+__global__ void __launch_bounds__(kB) k_bupdate(int N, BatchDev bd, double *__restrict__ Q, const double *__restrict__ dQ,
+                                                double *__restrict__ G, const double *__restrict__ Gnew, int ng) {
+  const int i = blockIdx.x * kB + threadIdx.x;
+  if (!bd.active[bd.bmesh[blockIdx.x]]) return;
+#pragma unroll
+  for (int c = 0; c < 5; c++) Q[(size_t)c * N + i] += dQ[(size_t)c * N + i];
+  for (int c = 0; c < ng; c++) G[(size_t)c * N + i] = Gnew[(size_t)c * N + i];
+}
+
+
+// x = D^{-1} b (no Jacobi sweep), with an optional per-mesh (x, dotv)
+template <typename T>
+__global__ void __launch_bounds__(kB) k_bdiag(int N, BatchDev bd, const T *__restrict__ dinv, const T *__restrict__ b,
+                                              T *__restrict__ x, const T *__restrict__ dotv, T *part, double *dot_out,
+                                              int stride) {
+  const int i = blockIdx.x * kB + threadIdx.x;
+  if (!bd.active[bd.bmesh[blockIdx.x]]) return;
+  const T di = dinv[i];
+  T s = T(0);
+#pragma unroll
+  for (int c = 0; c < 5; c++) {
+    const T v = di * b[(size_t)c * N + i];
+    x[(size_t)c * N + i] = v;
+    if (dotv) s = fma(v, dotv[(size_t)c * N + i], s);
+  }
+  if (dotv) mesh_sum(s, bd, part, dot_out, stride, 0);
+}
+
+// Convergence test of every active mesh on the mean density residual of its
+// current state: history, running maximum (the reference), and the drop.
+__global__ void k_bcheck(BatchState bs, double drop_tol, int max_steps) {
+  const int mesh = blockIdx.x * blockDim.x + threadIdx.x;
+  const BatchDev &bd = bs.b;
+  if (mesh >= bd.nmesh || !bd.active[mesh]) return;
+  const double res = bs.hs[(size_t)mesh * bs.hsz + bs.l1_off] / (double)bs.ncell[mesh];
+  const int k = bs.steps[mesh];
+  bs.res[mesh] = res;
+  if (bs.hist && k < bs.hist_len) bs.hist[(size_t)mesh * bs.hist_len + k] = res;
+  if (!isfinite(res)) { bs.bad[mesh] = 1; bd.active[mesh] = 0; return; }
+  if (res > bs.ref[mesh]) bs.ref[mesh] = res;
+  if (res <= drop_tol * bs.ref[mesh]) { bs.conv[mesh] = 1; bd.active[mesh] = 0; return; }
+  if (k >= max_steps) { bd.active[mesh] = 0; return; }
+  bs.steps[mesh] = k + 1;
+}
+
+__global__ void k_fill(double *a, int64_t n, double v) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) a[k] = v;
+}
+
+// a[r][c] += add where a[r][c] >= 0, for the n columns of rows r < rows (row pitch `pitch`)
+__global__ void k_offset_index(int *a, int rows, int64_t n, int64_t pitch, int64_t add) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < (int64_t)rows * n; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = k / n, c = k - r * n;
+    int *q = a + r * pitch + c;
+    if (*q >= 0) *q = (int)(*q + add);
+  }
+}
+
+template <typename T>
+struct BBuf {
+  const T *off, *dval, *dinv;
+  T *V, *w, *t, *t2, *part;
+};
+BBuf<double> bbuf64(Scratch &s, BatchState &bs) { return {s.off, s.dval, s.dinv, s.V, s.w, s.t, s.t2, bs.part}; }
+BBuf<float> bbuf32(Scratch &s, BatchState &bs) { return {s.off32, s.dval32, s.dinv32, s.V32, s.w32, s.t32, s.t232, bs.part32}; }
+
+// x = P^{-1} b for every mesh (Eq. (precond)); with dotv, also (x, dotv) per mesh
+template <typename T>
+void bprecondition(const DevMesh &m, BatchState &bs, const BBuf<T> &k, int sweeps, const T *b, T *x, const T *dotv,
+                   double *dot_out, cudaStream_t st) {
+  const unsigned g = bs.b.nblocks;
+  const int hz = bs.hsz;
+  if (sweeps == 0) {
+    HGKS_PROF_BEGIN(K_DIAG, st);
+    k_bdiag<T><<<g, kB, 0, st>>>(m.N, bs.b, k.dinv, b, x, dotv, k.part, dot_out, hz);
+    HGKS_PROF_END(K_DIAG, st);
+    return;
+  }
+  const T *prev = nullptr;
+  for (int q = 1; q <= sweeps; q++) {
+    T *dst = ((sweeps - q) % 2 == 0) ? x : k.t2;
+    const T *dv = (q == sweeps) ? dotv : nullptr;
+    HGKS_PROF_BEGIN(K_JACOBI, st);
+    if (q == 1)
+      k_bapply<T, T, T, kJacobi, true><<<g, kB, 0, st>>>(m, bs.b, k.off, k.dval, k.dinv, b, nullptr, dst, dv, k.part,
+                                                          dot_out, hz);
+    else
+      k_bapply<T, T, T, kJacobi, false><<<g, kB, 0, st>>>(m, bs.b, k.off, k.dval, k.dinv, b, prev, dst, dv, k.part,
+                                                           dot_out, hz);
+    HGKS_PROF_END(K_JACOBI, st);
+    prev = dst;
+  }
+}
+
+// Restarted GMRES (Algorithm 1) for every mesh of the batch at once, each in
+// its own Krylov space; the launch sequence does not depend on the data, so it
+// can be captured in a CUDA graph.
+template <typename T>
+void bgmres_t(const DevMesh &m, Scratch &s, BatchState &bs, const BBuf<T> &k, const hgks_params &p, const double *rhs,
+              double *dx, cudaStream_t st) {
+  const int mk = p.krylov_dim, hz = bs.hsz, N = m.N, nm = bs.b.nmesh;
+  const int64_t vs = s.vstride;
+  double *H = bs.hs, *beta = H + (mk + 1) * mk, *lres = beta + 1 + mk;
+  const unsigned g = bs.b.nblocks;
+  for (int it = 0; it < p.restarts; it++) {
+    cudaMemset2DAsync(H, sizeof(double) * hz, 0, sizeof(double) * (mk + 1) * mk, nm, st);
+    HGKS_PROF_BEGIN(K_SPMV, st);
+    k_bapply<T, double, T, kSpmv, false><<<g, kB, 0, st>>>(m, bs.b, k.off, k.dval, k.dinv, rhs, dx, k.t, nullptr, nullptr,
+                                                            nullptr, hz);
+    HGKS_PROF_END(K_SPMV, st);
+    bprecondition<T>(m, bs, k, p.jacobi_sweeps, k.t, k.w, nullptr, nullptr, st);
+    HGKS_PROF_BEGIN(K_DOT, st);
+    k_baxpy_dot<T><<<g, kB, 0, st>>>(N, bs.b, k.w, nullptr, nullptr, hz, k.w, 1, k.part, beta, hz);
+    HGKS_PROF_END(K_DOT, st);
+    if (it == 0) cudaMemcpy2DAsync(lres, sizeof(double) * hz, beta, sizeof(double) * hz, sizeof(double), nm,
+                                   cudaMemcpyDeviceToDevice, st);
+    HGKS_PROF_BEGIN(K_SCALE, st);
+    k_bscale<T><<<g, kB, 0, st>>>(N, bs.b, k.w, beta, hz, k.V);
+    HGKS_PROF_END(K_SCALE, st);
+    for (int j = 0; j < mk; j++) {
+      HGKS_PROF_BEGIN(K_SPMV, st);
+      k_bapply<T, T, T, kSpmv, false><<<g, kB, 0, st>>>(m, bs.b, k.off, k.dval, k.dinv, nullptr, k.V + (size_t)j * vs,
+                                                         k.t, nullptr, nullptr, nullptr, hz);
+      HGKS_PROF_END(K_SPMV, st);
+      bprecondition<T>(m, bs, k, p.jacobi_sweeps, k.t, k.w, k.V, H + j, st);
+      for (int i = 0; i <= j; i++) {
+        const bool last = (i == j);
+        HGKS_PROF_BEGIN(K_DOT, st);
+        k_baxpy_dot<T><<<g, kB, 0, st>>>(N, bs.b, k.w, k.V + (size_t)i * vs, H + i * mk + j, hz,
+                                         last ? k.w : k.V + (size_t)(i + 1) * vs, last ? 1 : 0, k.part,
+                                         H + (i + 1) * mk + j, hz);
+        HGKS_PROF_END(K_DOT, st);
+      }
+      HGKS_PROF_BEGIN(K_SCALE, st);
+      k_bscale<T><<<g, kB, 0, st>>>(N, bs.b, k.w, H + (j + 1) * mk + j, hz, k.V + (size_t)(j + 1) * vs);
+      HGKS_PROF_END(K_SCALE, st);
+    }
+    HGKS_PROF_BEGIN(K_GIVENS, st);
+    k_bgivens<<<(nm + 63) / 64, 64, 0, st>>>(bs.b, mk, bs.hs, hz);
+    HGKS_PROF_END(K_GIVENS, st);
+    HGKS_PROF_BEGIN(K_COMBINE, st);
+    k_bcombine<T><<<g, kB, 0, st>>>(N, bs.b, vs, mk, k.V, bs.hs, hz, dx);
+    HGKS_PROF_END(K_COMBINE, st);
+  }
+}
+
+}  // namespace
+
+void launch_batch_gmres(const DevMesh &m, Scratch &s, BatchState &bs, const hgks_params &p, const double *rhs,
+                        double *dx, cudaStream_t st) {
+  cudaMemsetAsync(dx, 0, sizeof(double) * 5 * (size_t)m.N, st);
+  if (p.precision == HGKS_MIXED) bgmres_t<float>(m, s, bs, bbuf32(s, bs), p, rhs, dx, st);
+  else bgmres_t<double>(m, s, bs, bbuf64(s, bs), p, rhs, dx, st);
+}
+
+void launch_batch_density(const DevMesh &m, BatchState &bs, const double *R, cudaStream_t st) {
+  HGKS_PROF_BEGIN(K_NORM, st);
+  k_bdensity<<<bs.b.nblocks, kB, 0, st>>>(m.N, bs.b, R, m.inv_vol, bs.part, bs.hs + bs.l1_off, bs.hsz);
+  HGKS_PROF_END(K_NORM, st);
+}
+
+void launch_batch_check(BatchState &bs, double drop_tol, int max_steps, cudaStream_t st) {
+  HGKS_PROF_BEGIN(K_NORM, st);
+  k_bcheck<<<(bs.b.nmesh + 63) / 64, 64, 0, st>>>(bs, drop_tol, max_steps);
+  HGKS_PROF_END(K_NORM, st);
+}
+
+void launch_batch_update(const DevMesh &m, BatchState &bs, double *Q, const double *dQ, double *G, const double *Gnew,
+                         int ncomp_g, cudaStream_t st) {
+  HGKS_PROF_BEGIN(K_UPDATE, st);
+  k_bupdate<<<bs.b.nblocks, kB, 0, st>>>(m.N, bs.b, Q, dQ, G, Gnew, ncomp_g);
+  HGKS_PROF_END(K_UPDATE, st);
+}
+
+void launch_fill(double *a, int64_t n, double v, cudaStream_t st) {
+  if (n <= 0) return;
+  k_fill<<<grid_for(std::min<int64_t>(n, 152 * 2048), 256), 256, 0, st>>>(a, n, v);
+  count_launch();
+}
+
+void launch_offset_index(int *a, int rows, int64_t n, int64_t pitch, int64_t add, cudaStream_t st) {
+  if (n <= 0 || rows <= 0 || add == 0) return;
+  k_offset_index<<<grid_for(std::min<int64_t>((int64_t)rows * n, 152 * 2048), 256), 256, 0, st>>>(a, rows, n, pitch, add);
+  count_launch();
+}
+
+}  // namespace hgks

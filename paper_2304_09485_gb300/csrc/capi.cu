@@ -57,6 +57,30 @@ void free_all(Mesh &m) {
   m.allocs.clear();
 }
 
+hgks_status set_device(const Mesh &m) {
+  HGKS_CUDA(cudaSetDevice(m.device));
+  return HGKS_OK;
+}
+
+hgks_status last_launch() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return HGKS_OK;
+}
+
+}  // namespace
+
+namespace hgks {
+hgks_status fail_msg(hgks_status st, const std::string &msg) { return fail(st, msg); }
+hgks_status cuda_error(cudaError_t e, const char *where) { return cuda_fail(e, where); }
+hgks_status mesh_alloc(Mesh &m, void **p, size_t bytes) {
+  unsigned char *q = nullptr;
+  hgks_status st = dalloc(m, &q, bytes);
+  *p = q;
+  return st;
+}
+void mesh_free_all(Mesh &m) { free_all(m); }
+
 hgks_status check_params(const Mesh &m, const hgks_params *p) {
   if (!p) return fail(HGKS_ERR_ARG, "params is NULL");
   if (p->scheme != HGKS_WENO && p->scheme != HGKS_HWENO) return fail(HGKS_ERR_ARG, "unknown scheme");
@@ -74,7 +98,7 @@ hgks_status check_params(const Mesh &m, const hgks_params *p) {
 // Scratch of the residual (always) and of the implicit solve (lazily, per Krylov
 // size and precision). Krylov vectors are padded to a multiple of 64 elements so
 // that every vector of the basis starts on a 512-byte boundary.
-hgks_status ensure_scratch(Mesh &m, int kdim, bool implicit, bool mixed = false) {
+hgks_status ensure_scratch(Mesh &m, int kdim, bool implicit, bool mixed) {
   Scratch &s = m.s;
   const size_t N = m.N, F = m.F;
   hgks_status st;
@@ -122,8 +146,11 @@ hgks_status ensure_scratch(Mesh &m, int kdim, bool implicit, bool mixed = false)
   if (implicit && kdim > s.kdim) {
     if (s.V) { release(s.V, sizeof(double) * (size_t)(s.kdim + 1) * s.vstride); s.V = nullptr; }
     if (s.V32) { release(s.V32, sizeof(float) * (size_t)(s.kdim + 1) * s.vstride); s.V32 = nullptr; }
-    if ((st = dalloc(m, &s.V, (size_t)(kdim + 1) * s.vstride))) return st;
     s.kdim = kdim;
+  }
+  // the basis of the precision in use only: FP64 for HGKS_FP64, FP32 for HGKS_MIXED
+  if (implicit && !mixed && !s.V) {
+    if ((st = dalloc(m, &s.V, (size_t)(s.kdim + 1) * s.vstride))) return st;
   }
   if (implicit && mixed && !s.V32) {
     if ((st = dalloc(m, &s.V32, (size_t)(s.kdim + 1) * s.vstride))) return st;
@@ -131,20 +158,6 @@ hgks_status ensure_scratch(Mesh &m, int kdim, bool implicit, bool mixed = false)
   return HGKS_OK;
 }
 
-hgks_status set_device(const Mesh &m) {
-  HGKS_CUDA(cudaSetDevice(m.device));
-  return HGKS_OK;
-}
-
-hgks_status last_launch() {
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
-  return HGKS_OK;
-}
-
-}  // namespace
-
-namespace hgks {
 Mesh *mesh_of(hgks_mesh h) { return &h->m; }
 void set_last_error(const char *msg) { g_err = msg; }
 bool g_prof_on = false;

@@ -44,6 +44,36 @@ struct DevMesh {
   double *fT = nullptr;          // [9][F] rows n, t1, t2 (n from left to right)
   double *fS = nullptr;          // [F] area
   double *fdist = nullptr;       // [F] |x_L - x_R| (or twice the wall distance on a boundary)
+  // batches of meshes (hgks_batch_*): per-mesh parameters and the mesh of every
+  // cell (-1 for the padding cells that align each mesh to a 256-cell block) and face
+  const hgks_params *ptab = nullptr;
+  const short *cmesh = nullptr, *fmesh = nullptr;
+  const int *mact = nullptr;             // [meshes] 1 while the mesh iterates; its cells are skipped otherwise
+};
+
+// A batch's mesh offsets are multiples of kBatchBlock cells, so that a block of
+// the batched Krylov kernels (one thread per cell) lies in one mesh.
+constexpr int kBatchBlock = 256;
+struct BatchDev {
+  int nmesh = 0, nblocks = 0;
+  const short *bmesh = nullptr;    // [nblocks] mesh of each block of kBatchBlock cells
+  const int *bstart = nullptr;     // [nmesh + 1] first block of each mesh
+  unsigned *counters = nullptr;    // [nmesh] arrival counters of the per-mesh reductions (0 between launches)
+  int *active = nullptr;           // [nmesh] 1 while the mesh iterates
+};
+// Device scalars of a batch: per mesh hs[hsz] = H[(m+1) m] | beta | y[m] | lres[2] | density L1 | pad
+struct BatchState {
+  BatchDev b;
+  int hsz = 0, kdim = 0;
+  double *hs = nullptr;
+  double *part = nullptr;          // [nblocks] partial sums
+  float *part32 = nullptr;
+  const int *ncell = nullptr;      // [nmesh] real cells of each mesh
+  int *steps = nullptr, *conv = nullptr, *bad = nullptr;   // [nmesh]
+  double *ref = nullptr, *res = nullptr;                   // [nmesh]
+  double *hist = nullptr;          // [nmesh][hist_len] density residual history
+  int hist_len = 0;
+  int l1_off = 0;                  // offset of the density L1 in a mesh's hs record
 };
 
 struct Scratch {
@@ -71,6 +101,7 @@ struct Scratch {
   double *hostbuf = nullptr;     // [40][N] device state of the *_host entry points
   int kdim = 0;
   size_t bytes = 0;
+  int blk_recon = 128, blk_flux = 128;   // launch shapes of the two FP64-bound kernels (autotuned for batches)
 };
 
 struct Mesh {
@@ -102,9 +133,9 @@ hgks_status build_host_mesh(const double *xyz, int64_t nv, const int64_t *tet, i
 // ---- kernels (residual.cu, implicit.cu) ----
 void launch_local_dt(const DevMesh &m, const hgks_params &p, const double *Q, double *dt, cudaStream_t st);
 void launch_residual(const DevMesh &m, Scratch &s, const hgks_params &p, const double *Q, const double *G,
-                     double *R, double *Gnew, cudaStream_t st);
+                     double *R, double *Gnew, cudaStream_t st, bool batch = false);
 void launch_assemble(const DevMesh &m, Scratch &s, const hgks_params &p, const double *Q, const double *dt,
-                     double *diag_out, double *off_out, cudaStream_t st);
+                     double *diag_out, double *off_out, cudaStream_t st, bool batch = false);
 void launch_apply_A(const DevMesh &m, const Scratch &s, const double *x, double *y, cudaStream_t st);
 void launch_precondition(const DevMesh &m, Scratch &s, int sweeps, const double *b, double *x, cudaStream_t st);
 hgks_status gmres_solve(const DevMesh &m, Scratch &s, const hgks_params &p, const double *rhs, double *dx,
@@ -112,6 +143,23 @@ hgks_status gmres_solve(const DevMesh &m, Scratch &s, const hgks_params &p, cons
 void launch_density_l1(const DevMesh &m, Scratch &s, const double *R, double *out_dev, cudaStream_t st);
 void launch_update(const DevMesh &m, double *Q, const double *dQ, double *G, const double *Gnew, int ncomp_g,
                    cudaStream_t st);
+// batches (batch.cu): one launch per phase for all meshes of the batch
+void launch_batch_gmres(const DevMesh &m, Scratch &s, BatchState &bs, const hgks_params &p, const double *rhs,
+                        double *dx, cudaStream_t st);
+void launch_batch_density(const DevMesh &m, BatchState &bs, const double *R, cudaStream_t st);
+void launch_batch_check(BatchState &bs, double drop_tol, int max_steps, cudaStream_t st);
+void launch_batch_update(const DevMesh &m, BatchState &bs, double *Q, const double *dQ, double *G, const double *Gnew,
+                         int ncomp_g, cudaStream_t st);
+void launch_fill(double *a, int64_t n, double v, cudaStream_t st);
+void launch_offset_index(int *a, int rows, int64_t n, int64_t pitch, int64_t add, cudaStream_t st);
+
+// shared by the entry points (capi.cu)
+hgks_status ensure_scratch(Mesh &m, int kdim, bool implicit, bool mixed = false);
+hgks_status mesh_alloc(Mesh &m, void **p, size_t bytes);   // tracked in m.allocs, freed with the mesh
+void mesh_free_all(Mesh &m);
+hgks_status check_params(const Mesh &m, const hgks_params *p);
+hgks_status fail_msg(hgks_status st, const std::string &msg);
+hgks_status cuda_error(cudaError_t e, const char *where);
 
 // accessors for entry points defined outside capi.cu
 Mesh *mesh_of(hgks_mesh h);

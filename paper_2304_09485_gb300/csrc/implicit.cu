@@ -19,6 +19,7 @@
 //    whole GMRES cycle is enqueued without synchronising the host.
 #include <cmath>
 #include "hgks_internal.h"
+#include "givens.cuh"
 
 namespace hgks {
 namespace {
@@ -47,13 +48,23 @@ __device__ __forceinline__ void euler_jacobian(const double *Q, const double *n,
   J[24] = gamma * un;
 }
 
-__global__ void __launch_bounds__(kCellBlock) k_assemble(DevMesh m, hgks_params P, const double *__restrict__ Q,
+template <bool BATCH>
+__global__ void __launch_bounds__(kCellBlock) k_assemble(DevMesh m, hgks_params Pv, const double *__restrict__ Q,
                                                          const double *__restrict__ dt, double *__restrict__ dval,
                                                          double *__restrict__ dinv, double *__restrict__ off,
                                                          double *__restrict__ diag_out, double *__restrict__ off_out) {
   const int N = m.N, F = m.F;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
+  if (BATCH && m.cmesh[i] < 0) {                          // padding cell of a batch: identity row
+    dval[i] = 1.0;
+    dinv[i] = 1.0;
+#pragma unroll 4
+    for (int k = 0; k < 100; k++) off[(size_t)k * N + i] = 0.0;
+    return;
+  }
+  if (BATCH && !m.mact[m.cmesh[i]]) return;             // a mesh of a batch that has stopped
+  const hgks_params &P = BATCH ? m.ptab[m.cmesh[i]] : Pv;
   double Qi[5];
 #pragma unroll
   for (int c = 0; c < 5; c++) Qi[c] = Q[(size_t)c * N + i];
@@ -251,39 +262,11 @@ __global__ void k_scale(int64_t n, const T *__restrict__ w, const double *__rest
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) v[k] = w[k] * ih;
 }
 
-// Givens QR of the (used+1) x used Hessenberg matrix and back substitution:
-// y minimises || beta e1 - H y ||. H[i*m + j] holds h_{i,j}. Single thread, FP64.
-__global__ void k_givens(int m, const double *__restrict__ H, const double *__restrict__ beta, double *__restrict__ y,
+// y minimises || beta e1 - H y || (Givens rotations in place on H, one thread, FP64)
+__global__ void k_givens(int m, double *__restrict__ H, const double *__restrict__ beta, double *__restrict__ y,
                          double *__restrict__ res_out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double R[65 * 64], gv[65];
-  int used = m;
-  for (int j = 0; j < m; j++)
-    if (H[(j + 1) * m + j] == 0.0) { used = j + 1; break; }
-  for (int i = 0; i <= used; i++)
-    for (int j = 0; j < used; j++) R[i * 64 + j] = H[i * m + j];
-  for (int i = 0; i <= m; i++) gv[i] = 0.0;
-  gv[0] = *beta;
-  for (int j = 0; j < m; j++) y[j] = 0.0;
-  if (gv[0] == 0.0) { *res_out = 0.0; return; }
-  for (int j = 0; j < used; j++) {
-    const double a = R[j * 64 + j], b = R[(j + 1) * 64 + j], r = sqrt(a * a + b * b);
-    const double c = a / r, s = b / r;
-    for (int k = j; k < used; k++) {
-      const double h1 = R[j * 64 + k], h2 = R[(j + 1) * 64 + k];
-      R[j * 64 + k] = c * h1 + s * h2;
-      R[(j + 1) * 64 + k] = -s * h1 + c * h2;
-    }
-    const double g1 = gv[j], g2 = gv[j + 1];
-    gv[j] = c * g1 + s * g2;
-    gv[j + 1] = -s * g1 + c * g2;
-  }
-  for (int j = used - 1; j >= 0; j--) {
-    double s = gv[j];
-    for (int k = j + 1; k < used; k++) s -= R[j * 64 + k] * y[k];
-    y[j] = s / R[j * 64 + j];
-  }
-  *res_out = fabs(gv[used]);
+  *res_out = givens_lsq(m, H, *beta, y);
 }
 
 // dx += sum_j y_j V_j (FP64 accumulation; V of either precision, stride vs)
@@ -420,9 +403,12 @@ void gmres_t(const DevMesh &m, Scratch &s, const KBuf<T> &k, const hgks_params &
 }  // namespace
 
 void launch_assemble(const DevMesh &m, Scratch &s, const hgks_params &p, const double *Q, const double *dt,
-                     double *diag_out, double *off_out, cudaStream_t st) {
+                     double *diag_out, double *off_out, cudaStream_t st, bool batch) {
   HGKS_PROF_BEGIN(K_ASSEMBLE, st);
-  k_assemble<<<grid_for(m.N, kCellBlock), kCellBlock, 0, st>>>(m, p, Q, dt, s.dval, s.dinv, s.off, diag_out, off_out);
+  if (batch || m.ptab)
+    k_assemble<true><<<grid_for(m.N, kCellBlock), kCellBlock, 0, st>>>(m, p, Q, dt, s.dval, s.dinv, s.off, diag_out, off_out);
+  else
+    k_assemble<false><<<grid_for(m.N, kCellBlock), kCellBlock, 0, st>>>(m, p, Q, dt, s.dval, s.dinv, s.off, diag_out, off_out);
   HGKS_PROF_END(K_ASSEMBLE, st);
   if (p.precision == HGKS_MIXED && s.off32) {
     HGKS_PROF_BEGIN(K_ASSEMBLE, st);

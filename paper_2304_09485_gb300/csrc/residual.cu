@@ -93,11 +93,19 @@ __device__ __forceinline__ void right_apply(const Eig &e, const double *q, doubl
 // ------------------------------------------------------------------------
 // 1. polynomial coefficients
 // ------------------------------------------------------------------------
+// a real cell of a batch whose mesh still iterates (padding cells have mesh -1)
+__device__ __forceinline__ bool live(const DevMesh &m, int i) {
+  const int k = m.cmesh[i];
+  return k >= 0 && m.mact[k];
+}
+
+template <bool BATCH>
 __global__ void __launch_bounds__(kBlock) k_coef_weno(DevMesh m, const double *__restrict__ Q, double *__restrict__ coef) {
   const int N = m.N;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 5 * N) return;
   const int c = t / N, i = t - c * N;
+  if (BATCH && !live(m, i)) return;
   const double qi = Q[(size_t)c * N + i];
   double a[9], b[12];
 #pragma unroll
@@ -120,12 +128,14 @@ __global__ void __launch_bounds__(kBlock) k_coef_weno(DevMesh m, const double *_
   for (int d = 0; d < 12; d++) coef[(size_t)(kCoefA + d * 5 + c) * N + i] = b[d];
 }
 
+template <bool BATCH>
 __global__ void __launch_bounds__(kBlock) k_coef_hweno(DevMesh m, const double *__restrict__ Q, const double *__restrict__ G,
                                                         double *__restrict__ coef) {
   const int N = m.N;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 5 * N) return;
   const int c = t / N, i = t - c * N;
+  if (BATCH && !live(m, i)) return;
   const double qi = Q[(size_t)c * N + i];
   double data[19];
   int nb[4];
@@ -163,12 +173,15 @@ __global__ void __launch_bounds__(kBlock) k_coef_hweno(DevMesh m, const double *
 // ------------------------------------------------------------------------
 // 2. reconstruction at the Gauss points of one face, one side
 // ------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBlock) k_recon(DevMesh m, hgks_params P, const double *__restrict__ Q,
-                                                   const double *__restrict__ coef, double *__restrict__ wface) {
+template <bool BATCH>
+__global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const double *__restrict__ Q,
+                                               const double *__restrict__ coef, double *__restrict__ wface) {
   const int N = m.N, F = m.F;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 4 * N) return;
   const int slot = t / N, i = t - slot * N;
+  if (BATCH && !live(m, i)) return;                     // padding cell, or a mesh that has stopped
+  const hgks_params &P = BATCH ? m.ptab[m.cmesh[i]] : Pv;
   const int cf = m.cface[(size_t)slot * N + i];
   const int f = cf >> 1, side = cf & 1;
   double T[9];
@@ -593,13 +606,16 @@ __device__ __forceinline__ bool physical(const double *W, double gamma) {
   return W[0] > 0.0 && p > 0.0;
 }
 
-__global__ void __launch_bounds__(kBlock) k_flux(DevMesh m, hgks_params P, const double *__restrict__ Q,
+template <bool BATCH>
+__global__ void __launch_bounds__(256) k_flux(DevMesh m, hgks_params Pv, const double *__restrict__ Q,
                                                   const double *__restrict__ dt, const double *__restrict__ wface,
                                                   double *__restrict__ fflux, double *__restrict__ fpt, int *__restrict__ flags) {
   const int N = m.N, F = m.F;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 3 * F) return;
   const int g = t / F, f = t - g * F;
+  if (BATCH && !m.mact[m.fmesh[f]]) return;             // a mesh of a batch that has stopped
+  const hgks_params &P = BATCH ? m.ptab[m.fmesh[f]] : Pv;
   double T[9];
 #pragma unroll
   for (int k = 0; k < 9; k++) T[k] = m.fT[(size_t)k * F + f];
@@ -660,12 +676,22 @@ __global__ void __launch_bounds__(kBlock) k_flux(DevMesh m, hgks_params P, const
 // ------------------------------------------------------------------------
 // 4. face -> cell
 // ------------------------------------------------------------------------
+template <bool BATCH>
 __global__ void __launch_bounds__(kBlock) k_gather(DevMesh m, int compact, const double *__restrict__ fflux,
                                                     const double *__restrict__ fpt, double *__restrict__ R,
                                                     double *__restrict__ Gnew) {
   const int N = m.N, F = m.F;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
+  if (BATCH && m.cmesh[i] < 0) {                         // padding cell of a batch
+#pragma unroll
+    for (int c = 0; c < 5; c++) R[(size_t)c * N + i] = 0.0;
+    if (compact)
+#pragma unroll
+      for (int k = 0; k < 15; k++) Gnew[(size_t)k * N + i] = 0.0;
+    return;
+  }
+  if (BATCH && !m.mact[m.cmesh[i]]) return;             // a mesh of a batch that has stopped
   double r[5] = {0, 0, 0, 0, 0}, gr[15];
 #pragma unroll
   for (int k = 0; k < 15; k++) gr[k] = 0.0;
@@ -700,10 +726,14 @@ __global__ void __launch_bounds__(kBlock) k_gather(DevMesh m, int compact, const
   }
 }
 
-__global__ void k_local_dt(DevMesh m, hgks_params P, const double *__restrict__ Q, double *__restrict__ dt) {
+template <bool BATCH>
+__global__ void k_local_dt(DevMesh m, hgks_params Pv, const double *__restrict__ Q, double *__restrict__ dt) {
   const int N = m.N, F = m.F;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
+  if (BATCH && m.cmesh[i] < 0) { dt[i] = 1.0; return; }   // padding cell of a batch
+  if (BATCH && !m.mact[m.cmesh[i]]) return;
+  const hgks_params &P = BATCH ? m.ptab[m.cmesh[i]] : Pv;
   double q[5];
 #pragma unroll
   for (int c = 0; c < 5; c++) q[c] = Q[(size_t)c * N + i];
@@ -725,25 +755,38 @@ __global__ void k_local_dt(DevMesh m, hgks_params P, const double *__restrict__ 
 
 void launch_local_dt(const DevMesh &m, const hgks_params &p, const double *Q, double *dt, cudaStream_t st) {
   HGKS_PROF_BEGIN(K_DT, st);
-  k_local_dt<<<grid_for(m.N, kBlock), kBlock, 0, st>>>(m, p, Q, dt);
+  if (m.ptab) k_local_dt<true><<<grid_for(m.N, kBlock), kBlock, 0, st>>>(m, p, Q, dt);
+  else k_local_dt<false><<<grid_for(m.N, kBlock), kBlock, 0, st>>>(m, p, Q, dt);
   HGKS_PROF_END(K_DT, st);
 }
 
 void launch_residual(const DevMesh &m, Scratch &s, const hgks_params &p, const double *Q, const double *G, double *R,
-                     double *Gnew, cudaStream_t st) {
+                     double *Gnew, cudaStream_t st, bool batch) {
+  batch = batch || m.ptab != nullptr;
   launch_local_dt(m, p, Q, s.dt, st);
   HGKS_PROF_BEGIN(K_COEF, st);
-  if (p.scheme == HGKS_WENO) k_coef_weno<<<grid_for(5 * (int64_t)m.N, kBlock), kBlock, 0, st>>>(m, Q, s.coef);
-  else k_coef_hweno<<<grid_for(5 * (int64_t)m.N, kBlock), kBlock, 0, st>>>(m, Q, G, s.coef);
+  const unsigned gc = grid_for(5 * (int64_t)m.N, kBlock);
+  if (p.scheme == HGKS_WENO) {
+    if (batch) k_coef_weno<true><<<gc, kBlock, 0, st>>>(m, Q, s.coef);
+    else k_coef_weno<false><<<gc, kBlock, 0, st>>>(m, Q, s.coef);
+  } else {
+    if (batch) k_coef_hweno<true><<<gc, kBlock, 0, st>>>(m, Q, G, s.coef);
+    else k_coef_hweno<false><<<gc, kBlock, 0, st>>>(m, Q, G, s.coef);
+  }
   HGKS_PROF_END(K_COEF, st);
   HGKS_PROF_BEGIN(K_RECON, st);
-  k_recon<<<grid_for(4 * (int64_t)m.N, kBlock), kBlock, 0, st>>>(m, p, Q, s.coef, s.wface);
+  if (batch) k_recon<true><<<grid_for(4 * (int64_t)m.N, s.blk_recon), s.blk_recon, 0, st>>>(m, p, Q, s.coef, s.wface);
+  else k_recon<false><<<grid_for(4 * (int64_t)m.N, s.blk_recon), s.blk_recon, 0, st>>>(m, p, Q, s.coef, s.wface);
   HGKS_PROF_END(K_RECON, st);
   HGKS_PROF_BEGIN(K_FLUX, st);
-  k_flux<<<grid_for(3 * (int64_t)m.F, kBlock), kBlock, 0, st>>>(m, p, Q, s.dt, s.wface, s.fflux, s.fpt, s.flags);
+  if (batch)
+    k_flux<true><<<grid_for(3 * (int64_t)m.F, s.blk_flux), s.blk_flux, 0, st>>>(m, p, Q, s.dt, s.wface, s.fflux, s.fpt, s.flags);
+  else
+    k_flux<false><<<grid_for(3 * (int64_t)m.F, s.blk_flux), s.blk_flux, 0, st>>>(m, p, Q, s.dt, s.wface, s.fflux, s.fpt, s.flags);
   HGKS_PROF_END(K_FLUX, st);
   HGKS_PROF_BEGIN(K_GATHER, st);
-  k_gather<<<grid_for(m.N, kBlock), kBlock, 0, st>>>(m, p.scheme == HGKS_HWENO, s.fflux, s.fpt, R, Gnew);
+  if (batch) k_gather<true><<<grid_for(m.N, kBlock), kBlock, 0, st>>>(m, p.scheme == HGKS_HWENO, s.fflux, s.fpt, R, Gnew);
+  else k_gather<false><<<grid_for(m.N, kBlock), kBlock, 0, st>>>(m, p.scheme == HGKS_HWENO, s.fflux, s.fpt, R, Gnew);
   HGKS_PROF_END(K_GATHER, st);
 }
 

@@ -58,3 +58,21 @@ def test_params_struct_matches_header():
     ints = len(re.findall(r"int32_t ([a-z_]+);", body))
     assert ints == 10
     assert C.sizeof(H.hgks_params) == 10 * 4 + 17 * 8
+
+
+def test_batch_entry_points_reject_bad_arguments_without_gpu():
+    L = H.lib()
+    out = C.c_void_p()
+    assert L.hgks_batch_create(None, None, 0, C.byref(out)) == 1
+    assert out.value is None
+    p = H.hgks_default_params()
+    assert L.hgks_batch_create(None, C.byref(p), 1, C.byref(out)) == 1
+    for fn, args in (("hgks_batch_residual", (None, None)), ("hgks_batch_gmres_step", (None, None, None)),
+                     ("hgks_batch_solve_steady", (None, 1e-8, 10, 1, None, None, None)),
+                     ("hgks_batch_autotune", (None, None, None, None)), ("hgks_batch_info", (None, None)),
+                     ("hgks_batch_destroy", (None,)), ("hgks_batch_set_state", (None, 0, None, None, None)),
+                     ("hgks_batch_get_state", (None, 0, None, None, None, None, None))):
+        assert getattr(L, fn)(*args) == 1, fn
+        assert b"NULL" in L.hgks_last_error(), fn
+    # hgks_batch_info_t: three int64 and three int32, padded to 8 bytes
+    assert C.sizeof(H.hgks_batch_info_t) == 40
