@@ -180,6 +180,224 @@ def run_reference(args, rank, world):
     return 0
 
 
+def paper_timing_context(H, I, device):
+    """Seconds per 100 implicit steps on the paper's efficiency case: lid-driven
+    cavity, 6 x 20^3 tets with h_min = 2.5e-2 at the walls, Ma 0.15, Re 1000,
+    GMRES(10) x 3, Jacobi 2, CFL 10, FP64, from rest. The paper's figures are
+    30 s (non-compact) and 32 s (compact) on a Quadro RTX 8000."""
+    import torch
+    m = I.cavity_mesh(20, h_min=2.5e-2)
+    cond = I.cavity_conditions(0.15, 1000.0)
+    hm = H.hgks_mesh_create(m, scheme_mask=3, device=device)
+    out = {"workload": "cavity 6x20^3 = 48,000 tets, h_min 2.5e-2, Ma 0.15, Re 1000, GMRES(10)x3, Jacobi 2, CFL 10, FP64",
+           "paper_rtx8000_s_per_100_steps": {"weno": 30.0, "hweno": 32.0}}
+    for name, scheme in (("weno", 0), ("hweno", 1)):
+        p = H.hgks_default_params(scheme=scheme, Pr=0.72, krylov_dim=10, restarts=3, jacobi_sweeps=2, **cond)
+        Q = hm.to_internal(I.state_from_conditions(m.n_tet, cond), device=f"cuda:{device}")
+        G = torch.zeros((15, m.n_tet), dtype=torch.float64, device=f"cuda:{device}") if scheme else None
+        for _ in range(3):
+            H.hgks_gmres_step(hm, p, Q, G)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info, hist, _ = H.hgks_solve_steady(hm, p, Q, G, drop_tol=1e-300, max_steps=100)
+        torch.cuda.synchronize()
+        out[f"{name}_s_per_100_steps"] = (time.perf_counter() - t0) * 100.0 / max(1, info.steps)
+        out[f"{name}_residual_drop_after_100"] = float(hist[-1] / hist.max())
+    return out
+
+
+def run_batch(args, rank, world):
+    """Many independent steady problems of uneven size advanced together
+    (hgks_batch_*: one launch per phase for all meshes, the step replayed from a
+    CUDA graph) against the same meshes stepped one at a time through the
+    single-mesh path. Prints one JSON line of its own."""
+    import torch
+    import paper_2304_09485_gb300 as H
+    from paper_2304_09485_gb300 import inputs as I
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    t0 = time.perf_counter()
+    probs = I.batch_problems(args.batch_meshes, seed=I.BASE_SEED + 400 + 1000 * rank)
+    scheme = 1 if args.batch_scheme == "hweno" else 0
+    prec = 1 if args.batch_precision == "mixed" else 0
+    meshes, params, states = [], [], []
+    for pr in probs:
+        hm = H.hgks_mesh_create(pr["mesh"], scheme_mask=2 if scheme else 1, device=local)
+        kw = dict(pr["cond"], scheme=scheme, precision=prec, Pr=0.72, krylov_dim=10, restarts=3, jacobi_sweeps=2)
+        meshes.append(hm)
+        params.append(H.hgks_default_params(**kw))
+        Q = hm.to_internal(I.state_from_conditions(pr["n_cells"], pr["cond"]), device=f"cuda:{local}")
+        G = torch.zeros((15, pr["n_cells"]), dtype=torch.float64, device=f"cuda:{local}") if scheme else None
+        states.append((Q, G))
+        pr["mesh"] = None
+    setup_s = time.perf_counter() - t0
+    n_cells = sum(p["n_cells"] for p in probs)
+    b = H.hgks_batch_create(meshes, params)
+    for k, (Q, G) in enumerate(states):
+        H.hgks_batch_set_state(b, k, Q, G)
+    blk = H.hgks_batch_autotune(b)
+    for _ in range(max(3, args.warmup)):
+        H.hgks_batch_gmres_step(b)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    clocks.start()
+    # (a) batched steps replayed from the captured graph (tiny drop: every mesh keeps
+    # stepping; the solve takes `steps` steps and then one last residual and test)
+    H.hgks_launch_count(reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos, _, _ = H.hgks_batch_solve_steady(b, 1e-300, args.steps, use_graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = e0.elapsed_time(e1)
+    launches = H.hgks_launch_count()
+    steps_done = sum(i.steps for i in infos)
+    # (a') per-kernel times of one eager batched step
+    H.hgks_profile_begin()
+    H.hgks_batch_gmres_step(b)
+    prof = H.hgks_profile_end()
+    # (b) batched steps, eager launches
+    e0.record(stream)
+    for _ in range(args.steps):
+        H.hgks_batch_gmres_step(b)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    eager_ms = e0.elapsed_time(e1)
+    # (c) the same meshes one after another through the single-mesh path
+    for hm, p, (Q, G) in zip(meshes, params, states):
+        H.hgks_gmres_step(hm, p, Q, G)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for hm, p, (Q, G) in zip(meshes, params, states):
+        for _ in range(args.steps):
+            H.hgks_gmres_step(hm, p, Q, G)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    if rank != 0:
+        return 0
+    rate = lambda ms, steps: n_cells * steps / (ms / 1000.0) / 1e6
+    res = {"metric": "batched implicit steps Mcells/s", "value": n_cells * (steps_done / len(probs)) / (graph_ms / 1000.0) / 1e6,
+           "unit": "Mcells/s", "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
+           "ms_per_step": graph_ms / max(1, steps_done / len(probs)), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64+f32" if prec else "f64", "data": "synthetic",
+           "config": {"workload": f"{len(probs)} independent steady problems, cavity/sphere, "
+                                  f"{min(p['n_cells'] for p in probs)}-{max(p['n_cells'] for p in probs)} tets "
+                                  f"({n_cells} total), Mach U(0.1,0.5), Re logU(50,1000), "
+                                  f"{args.batch_scheme}, {args.batch_precision}, GMRES(10)x3, Jacobi 2, CFL 10",
+                      "n_cells": n_cells, "padded_cells": int(H.hgks_batch_info(b).n_cells),
+                      "l2": "inputs larger than L2", "blk_recon_flux": list(blk)},
+           "graph": {"value": rate(graph_ms, steps_done / len(probs)), "ms": graph_ms},
+           "eager": {"value": rate(eager_ms, args.steps), "ms": eager_ms},
+           "sequential_single_mesh": {"value": rate(seq_ms, args.steps), "ms": seq_ms},
+           "speedup_vs_sequential": seq_ms / graph_ms * (steps_done / len(probs)) / args.steps,
+           "graph_note": "the graph-replayed solve: steps full steps plus the final residual and test",
+           "kernels_ms_one_step": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
+           "gpu_launches": int(launches), "setup_s": setup_s, "clocks": clk,
+           "sizes": sorted(p["n_cells"] for p in probs)}
+    print(json.dumps(res))
+    return 0
+
+
+def run_serve(args, rank, world):
+    """Steady-solve requests with Poisson arrivals served by the continuous-
+    batching server (mixed precision) against the same requests solved one
+    after another with the single-mesh FP64 solver (first come, first served:
+    each waits for the one before). Time to convergence (TTC) runs from a
+    request's arrival to its finished state; mesh building is included."""
+    import torch
+    import paper_2304_09485_gb300 as H
+    from paper_2304_09485_gb300 import inputs as I
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    reqs = I.serving_requests(args.serve_requests, rate=args.serve_rate, seed=I.BASE_SEED + 500 + 1000 * rank)
+    kw = dict(scheme=0, krylov_dim=10, restarts=3, jacobi_sweeps=2)
+    drop, max_steps = args.serve_drop, args.serve_max_steps
+    for r in reqs:
+        r["Q0"] = I.state_from_conditions(r["n_cells"], r["cond"])
+        r["p"] = dict(r["cond"], Pr=0.72 if r["cond"]["viscous"] else 1.0, **kw)
+
+    def pct(v, q):
+        return float(np.percentile(np.asarray(v), q)) if v else None
+
+    # (a) the server, mixed precision, arrivals in real time
+    shared = H.hgks_default_params(precision=1, **kw)
+    srv = H.hgks_server(shared, hbm_budget_bytes=int(args.serve_budget_gb * 1e9), max_inflight=64, device=local)
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    ids, nxt, rounds, done = {}, 0, 0, 0
+    while done < len(reqs):
+        now = time.perf_counter() - t0
+        while nxt < len(reqs) and reqs[nxt]["arrival"] <= now:
+            r = reqs[nxt]
+            ids[nxt] = srv.submit(r["mesh"], H.hgks_default_params(precision=1, **r["p"]), r["Q0"], drop_tol=drop,
+                                  max_steps=max_steps)
+            nxt += 1
+        fin, run, wait = srv.step()
+        rounds += 1
+        done += fin
+        if run == 0:
+            if wait == 0 and nxt < len(reqs):
+                time.sleep(max(0.0, min(0.05, reqs[nxt]["arrival"] - (time.perf_counter() - t0))))
+            else:
+                time.sleep(0.002)
+    clk = clocks.stop()
+    served = []
+    for k, rid in ids.items():
+        st = srv.status(rid)
+        served.append(dict(ttc=st.t_done - st.t_submit, steps=st.solve.steps, converged=bool(st.solve.converged),
+                           admit_wait=st.t_admit - st.t_built, done=st.t_done, submit=st.t_submit))
+        srv.collect(rid)
+    info = srv.info()
+    del srv
+    span_a = max(s["done"] for s in served) - min(s["submit"] for s in served)
+    # (b) one after another, FP64, queueing simulated on the measured solve times
+    seq, end = [], 0.0
+    for r in reqs:
+        t1 = time.perf_counter()
+        hm = H.hgks_mesh_create(r["mesh"], scheme_mask=1, device=local)
+        Q = hm.to_internal(r["Q0"], device=f"cuda:{local}")
+        si, hist, conv = H.hgks_solve_steady(hm, H.hgks_default_params(**r["p"]), Q, None, drop_tol=drop,
+                                             max_steps=max_steps)
+        torch.cuda.synchronize()
+        dur = time.perf_counter() - t1
+        del hm, Q
+        start = max(r["arrival"], end)
+        end = start + dur
+        seq.append(dict(ttc=end - r["arrival"], steps=si.steps, converged=bool(conv), service=dur))
+    span_b = end - reqs[0]["arrival"]
+    if rank != 0:
+        return 0
+    conv_a = [s["ttc"] for s in served if s["converged"]]
+    conv_b = [s["ttc"] for s in seq if s["converged"]]
+    res = {"metric": "steady solves/hour (served, mixed)", "value": 3600.0 * len(served) / span_a, "unit": "solves/h",
+           "n_gpus": world, "steps": len(reqs), "warmup": 0, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+           "config": {"workload": f"{len(reqs)} steady-solve requests, Poisson arrivals at {args.serve_rate}/s, "
+                                  f"spheres of {min(r['n_cells'] for r in reqs)}-{max(r['n_cells'] for r in reqs)} tets, "
+                                  f"half inviscid (Mach U(0.2,0.5), AoA U(0,10)), half viscous (Re logU(50,1000)), "
+                                  f"WENO, GMRES(10)x3, Jacobi 2, CFL 10, drop {drop:g}, max {max_steps} steps",
+                      "hbm_budget_gb": args.serve_budget_gb, "arena_cells": int(info.n_cells),
+                      "arena_gb": info.device_bytes / 1e9},
+           "served_mixed": {"solves_per_hour": 3600.0 * len(served) / span_a, "p50_ttc_s": pct([s["ttc"] for s in served], 50),
+                            "p99_ttc_s": pct([s["ttc"] for s in served], 99), "converged": len(conv_a),
+                            "hit_max_steps": len(served) - len(conv_a), "p50_ttc_converged_s": pct(conv_a, 50),
+                            "p99_ttc_converged_s": pct(conv_a, 99), "rounds": rounds, "span_s": span_a,
+                            "mean_steps": float(np.mean([s["steps"] for s in served]))},
+           "sequential_fp64": {"solves_per_hour": 3600.0 * len(seq) / span_b, "p50_ttc_s": pct([s["ttc"] for s in seq], 50),
+                               "p99_ttc_s": pct([s["ttc"] for s in seq], 99), "converged": len(conv_b),
+                               "hit_max_steps": len(seq) - len(conv_b), "p50_ttc_converged_s": pct(conv_b, 50),
+                               "p99_ttc_converged_s": pct(conv_b, 99), "span_s": span_b,
+                               "mean_steps": float(np.mean([s["steps"] for s in seq])),
+                               "mean_service_s": float(np.mean([s["service"] for s in seq]))},
+           "clocks": clk}
+    print(json.dumps(res))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -188,6 +406,17 @@ def main():
     ap.add_argument("--impl", default="hgks", choices=["hgks", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="scaled-down mesh (profiling runs)")
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "batch", "serve"],
+                    help="sphere: the 2.36M-tet sphere (default); batch: many problems in one batch; "
+                         "serve: Poisson-arriving solves through the request server")
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-rate", type=float, default=0.5, help="requests per second")
+    ap.add_argument("--serve-drop", type=float, default=1e-3)
+    ap.add_argument("--serve-max-steps", type=int, default=400)
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0)
+    ap.add_argument("--batch-meshes", type=int, default=48)
+    ap.add_argument("--batch-scheme", default="hweno", choices=["weno", "hweno"])
+    ap.add_argument("--batch-precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--launch-list", action="store_true",
                     help="warm-up then the timed steps only (no e2e, no residual-only pass): for ncu launch lists")
     args = ap.parse_args()
@@ -195,6 +424,10 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", 1))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batch":
+        return run_batch(args, rank, world)
+    if args.workload == "serve":
+        return run_serve(args, rank, world)
 
     import torch
     import torch.distributed as dist
@@ -288,6 +521,10 @@ def main():
     e2e_s = time.perf_counter() - t0
     e2e_val = world * m.n_tet * args.steps / e2e_s / 1e6
 
+    # context: the paper's timing case (48,000-tet wall-clustered cavity, Re = 1000),
+    # seconds per 100 implicit steps of Algorithm 1 with both schemes, FP64
+    ctx = paper_timing_context(H, I, local) if rank == 0 and not args.small else None
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -332,6 +569,7 @@ def main():
         "roofline_frac_by_kernel": roof_all,
         "clocks": clk,
         "cpu_baseline": cb,
+        "paper_timing_context": ctx,
     }
     print(json.dumps(result))
     if world > 1:

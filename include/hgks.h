@@ -243,9 +243,24 @@ typedef struct {
 hgks_status hgks_batch_create(const hgks_mesh *meshes, const hgks_params *params, int32_t n_meshes,
                               hgks_batch *out);
 hgks_status hgks_batch_destroy(hgks_batch batch);
+/* n_meshes counts the slots in use; n_cells and n_faces are the arena's capacities. */
 hgks_status hgks_batch_info(hgks_batch batch, hgks_batch_info_t *info);
 
-/* Copy mesh k's state in (set) or out (get). Q, R: device double[5][N_k], G,
+/* An empty batch: an arena of cell_capacity cells and face_capacity faces with
+ * max_meshes slots, for meshes whose params agree with *shared in the fields
+ * listed above (shared->scheme decides which reconstruction data it holds).
+ * Device memory: about 8 KB per cell and 1.3 KB per face (FP64, Krylov 10). */
+hgks_status hgks_batch_create_empty(int32_t device, int64_t cell_capacity, int64_t face_capacity,
+                                    int32_t max_meshes, const hgks_params *shared, hgks_batch *out);
+/* Place a mesh (copied; the handle stays the caller's) in a free slot and in
+ * free cell and face ranges (first fit); *k_out receives the slot, the index
+ * every other hgks_batch_* call takes. HGKS_ERR_OOM if no slot or range is
+ * free (nothing changes then). */
+hgks_status hgks_batch_add(hgks_batch batch, hgks_mesh mesh, const hgks_params *p, int32_t *k_out);
+/* Free slot k and its ranges; later launches skip them. */
+hgks_status hgks_batch_remove(hgks_batch batch, int32_t k);
+
+/* Copy the state of the mesh in slot k in (set) or out (get). Q, R: device double[5][N_k], G,
  * G_new: device double[15][N_k] (compact scheme; NULL otherwise), in mesh k's
  * internal order, N_k its cell count. Any pointer of get_state may be NULL;
  * R and G_new are those of the last hgks_batch_residual / step. */
@@ -277,6 +292,56 @@ hgks_status hgks_batch_solve_steady(hgks_batch batch, double drop_tol, int32_t m
  * block sizes 64, 128 and 256 (CUDA events, 3 runs each) and keep the fastest
  * for later calls; the chosen sizes are returned (may be NULL). */
 hgks_status hgks_batch_autotune(hgks_batch batch, int32_t *blk_recon, int32_t *blk_flux, void *cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * Request server: continuous batching of steady solves on one GPU. Requests
+ * arrive at any time; a host thread builds each mesh (stencils, reconstruction
+ * matrices) in arrival order; every hgks_server_step() admits built requests,
+ * in arrival order, while the server's batch arena (sized from the HBM budget)
+ * has a free slot and free ranges for them, advances every running solve by
+ * one step of Algorithm 1 in one batched launch sequence (a replayed CUDA
+ * graph), and retires the solves that converged or reached their step limit.
+ * A solve gives the same result as alone (hgks_solve_steady with the same
+ * parameters) up to the summation order of its inner products.
+ * ------------------------------------------------------------------------- */
+typedef struct hgks_server_s *hgks_server;          /* opaque */
+
+typedef struct {
+  int32_t state;             /* 0 waiting for its build, 1 built, 2 running, 3 finished, 4 failed */
+  int32_t status;            /* HGKS_OK (converged), HGKS_ERR_NOT_CONVERGED, _NONPHYSICAL, or the build error */
+  int64_t n_cells;
+  hgks_solve_info solve;     /* steps, converged, res_ref, res_final (once finished)         */
+  double t_submit, t_built, t_admit, t_done;   /* seconds since the server was created       */
+} hgks_request_info;
+
+/* A server on `device` whose arena takes at most hbm_budget_bytes of device
+ * memory, with at most max_inflight solves running at once; every request's
+ * params must agree with *shared in scheme, precision, jv_mode, krylov_dim,
+ * restarts and jacobi_sweeps. use_graph != 0 replays the step from a CUDA graph. */
+hgks_status hgks_server_create(int32_t device, int64_t hbm_budget_bytes, int32_t max_inflight,
+                               const hgks_params *shared, int32_t use_graph, hgks_server *out);
+/* Stops the build thread and frees everything, finished or not. */
+hgks_status hgks_server_destroy(hgks_server server);
+/* Queue a steady solve. Mesh arrays as hgks_mesh_create (host, copied); Q0
+ * (host, caller cell order, double[n_tet][5]) the initial state, G0 (may be
+ * NULL: zero) double[n_tet][15] the initial gradients of the compact scheme;
+ * the solve stops at res/res_ref <= drop_tol or after max_steps steps.
+ * *id_out receives the request's id. HGKS_ERR_ARG if the mesh cannot fit in
+ * the arena at all. */
+hgks_status hgks_server_submit(hgks_server server, const double *xyz, int64_t n_vert, const int64_t *tet4,
+                               int64_t n_tet, const int64_t *bface3, const int32_t *btag, int64_t n_bface,
+                               const double *periodic_shift, int32_t n_periodic, const hgks_params *p,
+                               const double *Q0, const double *G0, double drop_tol, int32_t max_steps,
+                               int64_t *id_out);
+/* One scheduling round (admit, one batched step, retire). Outputs (may be
+ * NULL): solves finished in this round, solves running, requests waiting. */
+hgks_status hgks_server_step(hgks_server server, int32_t *n_finished, int32_t *n_running, int32_t *n_waiting);
+hgks_status hgks_server_status(hgks_server server, int64_t id, hgks_request_info *info);
+/* Copy a finished request's state (host, caller order: Q double[n][5], G
+ * double[n][15] or NULL) and forget the request. */
+hgks_status hgks_server_collect(hgks_server server, int64_t id, double *Q, double *G);
+/* The server's arena (n_meshes = solves running). */
+hgks_status hgks_server_info(hgks_server server, hgks_batch_info_t *info);
 
 /* Wait for the stream and report any deferred device-side error. */
 hgks_status hgks_sync(void *cuda_stream);

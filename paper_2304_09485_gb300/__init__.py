@@ -56,6 +56,11 @@ class hgks_batch_info_t(C.Structure):
                 ("n_meshes", C.c_int32), ("blk_recon", C.c_int32), ("blk_flux", C.c_int32)]
 
 
+class hgks_request_info(C.Structure):
+    _fields_ = [("state", C.c_int32), ("status", C.c_int32), ("n_cells", C.c_int64), ("solve", hgks_solve_info),
+                ("t_submit", C.c_double), ("t_built", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double)]
+
+
 class HGKSError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"hgks status {status}: {msg}")
@@ -90,6 +95,17 @@ def lib():
             "hgks_residual_noalloc": [vp, P, dp, dp, dp, dp, vp],
             "hgks_batch_create": [dp, P, i32, C.POINTER(vp)],
             "hgks_batch_destroy": [vp],
+            "hgks_batch_create_empty": [i32, i64, i64, i32, P, C.POINTER(vp)],
+            "hgks_batch_add": [vp, vp, P, C.POINTER(C.c_int32)],
+            "hgks_batch_remove": [vp, i32],
+            "hgks_server_create": [i32, i64, i32, P, i32, C.POINTER(vp)],
+            "hgks_server_destroy": [vp],
+            "hgks_server_submit": [vp, dp, i64, dp, i64, dp, dp, i64, dp, i32, P, dp, dp, C.c_double, i32,
+                                   C.POINTER(C.c_int64)],
+            "hgks_server_step": [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
+            "hgks_server_status": [vp, i64, C.POINTER(hgks_request_info)],
+            "hgks_server_collect": [vp, i64, dp, dp],
+            "hgks_server_info": [vp, C.POINTER(hgks_batch_info_t)],
             "hgks_batch_info": [vp, C.POINTER(hgks_batch_info_t)],
             "hgks_batch_set_state": [vp, i32, dp, dp, vp],
             "hgks_batch_get_state": [vp, i32, dp, dp, dp, dp, vp],
@@ -284,6 +300,27 @@ def hgks_batch_create(meshes, params) -> hgks_batch:
     return hgks_batch(h.value, meshes, params)
 
 
+def hgks_batch_create_empty(cell_capacity, face_capacity, max_meshes, shared, device=0) -> hgks_batch:
+    h = C.c_void_p()
+    _check(lib().hgks_batch_create_empty(device, cell_capacity, face_capacity, max_meshes, C.byref(shared), C.byref(h)))
+    b = hgks_batch(h.value, [None] * max_meshes, [None] * max_meshes)
+    return b
+
+
+def hgks_batch_add(batch, mesh, params) -> int:
+    k = C.c_int32(-1)
+    _check(lib().hgks_batch_add(batch.handle, mesh.handle, C.byref(params), C.byref(k)))
+    batch.meshes[k.value] = mesh
+    batch.params[k.value] = params
+    return k.value
+
+
+def hgks_batch_remove(batch, k):
+    _check(lib().hgks_batch_remove(batch.handle, k))
+    batch.meshes[k] = None
+    batch.params[k] = None
+
+
 def hgks_batch_info(batch) -> hgks_batch_info_t:
     info = hgks_batch_info_t()
     _check(lib().hgks_batch_info(batch.handle, C.byref(info)))
@@ -322,6 +359,66 @@ def hgks_batch_autotune(batch, stream=None):
     r, f = C.c_int32(0), C.c_int32(0)
     _check(lib().hgks_batch_autotune(batch.handle, C.byref(r), C.byref(f), _stream(stream)))
     return r.value, f.value
+
+
+class hgks_server:
+    """Continuous-batching request server (hgks_server_*)."""
+
+    def __init__(self, shared, hbm_budget_bytes, max_inflight=64, use_graph=True, device=0):
+        h = C.c_void_p()
+        _check(lib().hgks_server_create(device, int(hbm_budget_bytes), max_inflight, C.byref(shared),
+                                        1 if use_graph else 0, C.byref(h)))
+        self.handle = h
+        self.n_cells = {}
+
+    def __del__(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            try:
+                lib().hgks_server_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = C.c_void_p(0)
+
+    def submit(self, mesh, params, Q0, G0=None, drop_tol=1e-8, max_steps=1000) -> int:
+        """Queue a solve of an inputs.Mesh from Q0 (caller order [n, 5]); returns its id."""
+        xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
+        tet = np.ascontiguousarray(mesh.tet4, dtype=np.int64)
+        bf = np.ascontiguousarray(mesh.bface3, dtype=np.int64).reshape(-1, 3)
+        bt = np.ascontiguousarray(mesh.btag, dtype=np.int32)
+        ps = mesh.periodic_shift
+        psa = np.ascontiguousarray(ps if ps is not None else np.zeros((0, 3)), dtype=np.float64)
+        q = np.ascontiguousarray(Q0, dtype=np.float64)
+        g = None if G0 is None else np.ascontiguousarray(G0, dtype=np.float64)
+        rid = C.c_int64(0)
+        _check(lib().hgks_server_submit(self.handle, _ptr(xyz), xyz.shape[0], _ptr(tet), tet.shape[0],
+                                        _ptr(bf) if len(bf) else None, _ptr(bt) if len(bt) else None, bf.shape[0],
+                                        _ptr(psa) if len(psa) else None, psa.shape[0], C.byref(params), _ptr(q),
+                                        _ptr(g), drop_tol, max_steps, C.byref(rid)))
+        self.n_cells[rid.value] = tet.shape[0]
+        return rid.value
+
+    def step(self):
+        """One scheduling round: (finished in this round, running, waiting)."""
+        f, r, w = C.c_int32(0), C.c_int32(0), C.c_int32(0)
+        _check(lib().hgks_server_step(self.handle, C.byref(f), C.byref(r), C.byref(w)))
+        return f.value, r.value, w.value
+
+    def status(self, rid) -> hgks_request_info:
+        info = hgks_request_info()
+        _check(lib().hgks_server_status(self.handle, rid, C.byref(info)))
+        return info
+
+    def collect(self, rid, with_gradients=False):
+        n = self.n_cells.pop(rid)
+        Q = np.zeros((n, 5))
+        G = np.zeros((n, 15)) if with_gradients else None
+        _check(lib().hgks_server_collect(self.handle, rid, _ptr(Q), _ptr(G)))
+        return Q, G
+
+    def info(self) -> hgks_batch_info_t:
+        info = hgks_batch_info_t()
+        _check(lib().hgks_server_info(self.handle, C.byref(info)))
+        return info
 
 
 def hgks_sync(stream=None):

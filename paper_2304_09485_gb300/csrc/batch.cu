@@ -47,13 +47,14 @@ __device__ __forceinline__ void mesh_sum(T v, const BatchDev &b, T *part, double
     part[blockIdx.x] = s0;
     __threadfence();
     const unsigned prev = atomicAdd(b.counters + mesh, 1u);
-    last = (prev == (unsigned)(b.bstart[mesh + 1] - b.bstart[mesh] - 1));
+    last = (prev == (unsigned)(b.bcount[mesh] - 1));
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
   T s = T(0);
-  for (int k = b.bstart[mesh] + threadIdx.x; k < b.bstart[mesh + 1]; k += blockDim.x) s += ((volatile T *)part)[k];
+  const int k0 = b.bstart[mesh], k1 = k0 + b.bcount[mesh];
+  for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) s += ((volatile T *)part)[k];
   s = bsum(s);
   if (threadIdx.x == 0) {
     out[(size_t)mesh * stride] = mode == 1 ? (double)sqrt(s) : (double)s;
@@ -195,7 +196,7 @@ __global__ void __launch_bounds__(kB) k_bdiag(int N, BatchDev bd, const T *__res
 
 // Convergence test of every active mesh on the mean density residual of its
 // current state: history, running maximum (the reference), and the drop.
-__global__ void k_bcheck(BatchState bs, double drop_tol, int max_steps) {
+__global__ void k_bcheck(BatchState bs) {
   const int mesh = blockIdx.x * blockDim.x + threadIdx.x;
   const BatchDev &bd = bs.b;
   if (mesh >= bd.nmesh || !bd.active[mesh]) return;
@@ -205,12 +206,13 @@ __global__ void k_bcheck(BatchState bs, double drop_tol, int max_steps) {
   if (bs.hist && k < bs.hist_len) bs.hist[(size_t)mesh * bs.hist_len + k] = res;
   if (!isfinite(res)) { bs.bad[mesh] = 1; bd.active[mesh] = 0; return; }
   if (res > bs.ref[mesh]) bs.ref[mesh] = res;
-  if (res <= drop_tol * bs.ref[mesh]) { bs.conv[mesh] = 1; bd.active[mesh] = 0; return; }
-  if (k >= max_steps) { bd.active[mesh] = 0; return; }
+  if (res <= bs.drop[mesh] * bs.ref[mesh]) { bs.conv[mesh] = 1; bd.active[mesh] = 0; return; }
+  if (k >= bs.max_steps[mesh]) { bd.active[mesh] = 0; return; }
   bs.steps[mesh] = k + 1;
 }
 
-__global__ void k_fill(double *a, int64_t n, double v) {
+template <typename T>
+__global__ void k_fill(T *a, int64_t n, T v) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) a[k] = v;
 }
 
@@ -235,7 +237,7 @@ BBuf<float> bbuf32(Scratch &s, BatchState &bs) { return {s.off32, s.dval32, s.di
 template <typename T>
 void bprecondition(const DevMesh &m, BatchState &bs, const BBuf<T> &k, int sweeps, const T *b, T *x, const T *dotv,
                    double *dot_out, cudaStream_t st) {
-  const unsigned g = bs.b.nblocks;
+  const unsigned g = std::max(1, bs.b.nblocks);
   const int hz = bs.hsz;
   if (sweeps == 0) {
     HGKS_PROF_BEGIN(K_DIAG, st);
@@ -268,7 +270,7 @@ void bgmres_t(const DevMesh &m, Scratch &s, BatchState &bs, const BBuf<T> &k, co
   const int mk = p.krylov_dim, hz = bs.hsz, N = m.N, nm = bs.b.nmesh;
   const int64_t vs = s.vstride;
   double *H = bs.hs, *beta = H + (mk + 1) * mk, *lres = beta + 1 + mk;
-  const unsigned g = bs.b.nblocks;
+  const unsigned g = std::max(1, bs.b.nblocks);
   for (int it = 0; it < p.restarts; it++) {
     cudaMemset2DAsync(H, sizeof(double) * hz, 0, sizeof(double) * (mk + 1) * mk, nm, st);
     HGKS_PROF_BEGIN(K_SPMV, st);
@@ -315,33 +317,39 @@ void bgmres_t(const DevMesh &m, Scratch &s, BatchState &bs, const BBuf<T> &k, co
 
 void launch_batch_gmres(const DevMesh &m, Scratch &s, BatchState &bs, const hgks_params &p, const double *rhs,
                         double *dx, cudaStream_t st) {
-  cudaMemsetAsync(dx, 0, sizeof(double) * 5 * (size_t)m.N, st);
+  cudaMemset2DAsync(dx, sizeof(double) * m.N, 0, sizeof(double) * m.NL, 5, st);
   if (p.precision == HGKS_MIXED) bgmres_t<float>(m, s, bs, bbuf32(s, bs), p, rhs, dx, st);
   else bgmres_t<double>(m, s, bs, bbuf64(s, bs), p, rhs, dx, st);
 }
 
 void launch_batch_density(const DevMesh &m, BatchState &bs, const double *R, cudaStream_t st) {
   HGKS_PROF_BEGIN(K_NORM, st);
-  k_bdensity<<<bs.b.nblocks, kB, 0, st>>>(m.N, bs.b, R, m.inv_vol, bs.part, bs.hs + bs.l1_off, bs.hsz);
+  k_bdensity<<<std::max(1, bs.b.nblocks), kB, 0, st>>>(m.N, bs.b, R, m.inv_vol, bs.part, bs.hs + bs.l1_off, bs.hsz);
   HGKS_PROF_END(K_NORM, st);
 }
 
-void launch_batch_check(BatchState &bs, double drop_tol, int max_steps, cudaStream_t st) {
+void launch_batch_check(BatchState &bs, cudaStream_t st) {
   HGKS_PROF_BEGIN(K_NORM, st);
-  k_bcheck<<<(bs.b.nmesh + 63) / 64, 64, 0, st>>>(bs, drop_tol, max_steps);
+  k_bcheck<<<(bs.b.nmesh + 63) / 64, 64, 0, st>>>(bs);
   HGKS_PROF_END(K_NORM, st);
 }
 
 void launch_batch_update(const DevMesh &m, BatchState &bs, double *Q, const double *dQ, double *G, const double *Gnew,
                          int ncomp_g, cudaStream_t st) {
   HGKS_PROF_BEGIN(K_UPDATE, st);
-  k_bupdate<<<bs.b.nblocks, kB, 0, st>>>(m.N, bs.b, Q, dQ, G, Gnew, ncomp_g);
+  k_bupdate<<<std::max(1, bs.b.nblocks), kB, 0, st>>>(m.N, bs.b, Q, dQ, G, Gnew, ncomp_g);
   HGKS_PROF_END(K_UPDATE, st);
 }
 
 void launch_fill(double *a, int64_t n, double v, cudaStream_t st) {
   if (n <= 0) return;
-  k_fill<<<grid_for(std::min<int64_t>(n, 152 * 2048), 256), 256, 0, st>>>(a, n, v);
+  k_fill<double><<<grid_for(std::min<int64_t>(n, 152 * 2048), 256), 256, 0, st>>>(a, n, v);
+  count_launch();
+}
+
+void launch_fill_short(short *a, int64_t n, short v, cudaStream_t st) {
+  if (n <= 0) return;
+  k_fill<short><<<grid_for(std::min<int64_t>(n, 152 * 2048), 256), 256, 0, st>>>(a, n, v);
   count_launch();
 }
 

@@ -366,13 +366,16 @@ hgks_status hgks_precondition(hgks_mesh mesh, int32_t sweeps, const double *b, d
   return last_launch();
 }
 
+// have_residual: s.R, s.Gnew, s.dt and the density L1 already hold those of Q
 static hgks_status gmres_step_impl(Mesh &m, const hgks_params *p, double *Q, double *G, double *dQ_out,
-                                   hgks_step_info *info, cudaStream_t st_) {
+                                   hgks_step_info *info, cudaStream_t st_, bool have_residual = false) {
   const DevMesh &d = m.d;
   Scratch &s = m.s;
-  launch_residual(d, s, *p, Q, G, s.R, p->scheme == HGKS_HWENO ? s.Gnew : nullptr, st_);
   double *res_dev = s.hs + 65 * 64 + 200;
-  launch_density_l1(d, s, s.R, res_dev, st_);
+  if (!have_residual) {
+    launch_residual(d, s, *p, Q, G, s.R, p->scheme == HGKS_HWENO ? s.Gnew : nullptr, st_);
+    launch_density_l1(d, s, s.R, res_dev, st_);
+  }
   launch_assemble(d, s, *p, Q, s.dt, nullptr, nullptr, st_);
   hgks_status st = gmres_solve(d, s, *p, s.R, s.dQ, info, st_);
   if (st) return st;
@@ -441,7 +444,7 @@ hgks_status hgks_solve_steady(hgks_mesh mesh, const hgks_params *p, double *Q, d
     if (res <= drop_tol * ref) { conv = true; break; }
     if (k >= max_steps) break;
     hgks_step_info si;
-    if ((st = gmres_step_impl(m, p, Q, G, nullptr, &si, s_))) break;
+    if ((st = gmres_step_impl(m, p, Q, G, nullptr, &si, s_, true))) break;
   }
   if (info) { info->steps = k; info->converged = conv; info->res_ref = ref; info->res_final = res; }
   if (st) return st;

@@ -49,17 +49,23 @@ struct DevMesh {
   const hgks_params *ptab = nullptr;
   const short *cmesh = nullptr, *fmesh = nullptr;
   const int *mact = nullptr;             // [meshes] 1 while the mesh iterates; its cells are skipped otherwise
+  int NL = 0, FL = 0;                    // batches: cells [0, NL) and faces [0, FL) hold every mesh in use
 };
 
-// A batch's mesh offsets are multiples of kBatchBlock cells, so that a block of
-// the batched Krylov kernels (one thread per cell) lies in one mesh.
+// A batch is an arena of cells and faces shared by up to `nmesh` meshes (slots).
+// Each mesh occupies a range of cells starting on a multiple of kBatchBlock, so
+// that a block of the batched Krylov kernels (one thread per cell) lies in one
+// mesh, and a range of faces. Cells and faces outside every range, and padding
+// cells, have mesh -1; per-mesh arrays are indexed from -1 (entry -1 is a
+// permanently inactive slot), so "mesh of x" can always be looked up.
 constexpr int kBatchBlock = 256;
 struct BatchDev {
   int nmesh = 0, nblocks = 0;
-  const short *bmesh = nullptr;    // [nblocks] mesh of each block of kBatchBlock cells
-  const int *bstart = nullptr;     // [nmesh + 1] first block of each mesh
+  const short *bmesh = nullptr;    // [nblocks] mesh of each block of kBatchBlock cells (-1: free)
+  const int *bstart = nullptr;     // [nmesh] first block of each mesh
+  const int *bcount = nullptr;     // [nmesh] blocks of each mesh
   unsigned *counters = nullptr;    // [nmesh] arrival counters of the per-mesh reductions (0 between launches)
-  int *active = nullptr;           // [nmesh] 1 while the mesh iterates
+  int *active = nullptr;           // [-1 .. nmesh-1] 1 while the mesh iterates; active[-1] = 0
 };
 // Device scalars of a batch: per mesh hs[hsz] = H[(m+1) m] | beta | y[m] | lres[2] | density L1 | pad
 struct BatchState {
@@ -71,7 +77,9 @@ struct BatchState {
   const int *ncell = nullptr;      // [nmesh] real cells of each mesh
   int *steps = nullptr, *conv = nullptr, *bad = nullptr;   // [nmesh]
   double *ref = nullptr, *res = nullptr;                   // [nmesh]
-  double *hist = nullptr;          // [nmesh][hist_len] density residual history
+  double *drop = nullptr;          // [nmesh] drop tolerance of the convergence test
+  int *max_steps = nullptr;        // [nmesh] step limit
+  double *hist = nullptr;          // [nmesh][hist_len] density residual history (may be null)
   int hist_len = 0;
   int l1_off = 0;                  // offset of the density L1 in a mesh's hs record
 };
@@ -147,10 +155,11 @@ void launch_update(const DevMesh &m, double *Q, const double *dQ, double *G, con
 void launch_batch_gmres(const DevMesh &m, Scratch &s, BatchState &bs, const hgks_params &p, const double *rhs,
                         double *dx, cudaStream_t st);
 void launch_batch_density(const DevMesh &m, BatchState &bs, const double *R, cudaStream_t st);
-void launch_batch_check(BatchState &bs, double drop_tol, int max_steps, cudaStream_t st);
+void launch_batch_check(BatchState &bs, cudaStream_t st);
 void launch_batch_update(const DevMesh &m, BatchState &bs, double *Q, const double *dQ, double *G, const double *Gnew,
                          int ncomp_g, cudaStream_t st);
 void launch_fill(double *a, int64_t n, double v, cudaStream_t st);
+void launch_fill_short(short *a, int64_t n, short v, cudaStream_t st);
 void launch_offset_index(int *a, int rows, int64_t n, int64_t pitch, int64_t add, cudaStream_t st);
 
 // shared by the entry points (capi.cu)

@@ -285,6 +285,18 @@ __global__ void k_to_f32(int64_t n, const double *__restrict__ a, float *__restr
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) b[k] = (float)a[k];
 }
 
+// FP32 copies of the first nl columns of the [100][pitch] blocks and of dval, dinv
+__global__ void k_to_f32_rows(int64_t nl, int64_t pitch, const double *__restrict__ off, float *__restrict__ off32,
+                              const double *__restrict__ dval, float *__restrict__ dval32, const double *__restrict__ dinv,
+                              float *__restrict__ dinv32) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 102 * nl; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = k / nl, i = k - r * nl;
+    if (r < 100) off32[r * pitch + i] = (float)off[r * pitch + i];
+    else if (r == 100) dval32[i] = (float)dval[i];
+    else dinv32[i] = (float)dinv[i];
+  }
+}
+
 __global__ void __launch_bounds__(kBlock) k_density_l1(int N, const double *__restrict__ R, const double *__restrict__ inv_vol,
                                                        double *partials, unsigned int *count, double *out) {
   double s = 0.0;
@@ -405,12 +417,19 @@ void gmres_t(const DevMesh &m, Scratch &s, const KBuf<T> &k, const hgks_params &
 void launch_assemble(const DevMesh &m, Scratch &s, const hgks_params &p, const double *Q, const double *dt,
                      double *diag_out, double *off_out, cudaStream_t st, bool batch) {
   HGKS_PROF_BEGIN(K_ASSEMBLE, st);
-  if (batch || m.ptab)
-    k_assemble<true><<<grid_for(m.N, kCellBlock), kCellBlock, 0, st>>>(m, p, Q, dt, s.dval, s.dinv, s.off, diag_out, off_out);
+  batch = batch || m.ptab;
+  if (batch)
+    k_assemble<true><<<grid_for(m.NL, kCellBlock), kCellBlock, 0, st>>>(m, p, Q, dt, s.dval, s.dinv, s.off, diag_out, off_out);
   else
     k_assemble<false><<<grid_for(m.N, kCellBlock), kCellBlock, 0, st>>>(m, p, Q, dt, s.dval, s.dinv, s.off, diag_out, off_out);
   HGKS_PROF_END(K_ASSEMBLE, st);
-  if (p.precision == HGKS_MIXED && s.off32) {
+  if (batch && p.precision == HGKS_MIXED && s.off32) {
+    // the cells in use only: rows of pitch N, the first NL columns
+    HGKS_PROF_BEGIN(K_ASSEMBLE, st);
+    k_to_f32_rows<<<vec_grid(102 * (int64_t)m.NL), kBlock, 0, st>>>(m.NL, m.N, s.off, s.off32, s.dval, s.dval32, s.dinv,
+                                                                       s.dinv32);
+    HGKS_PROF_END(K_ASSEMBLE, st);
+  } else if (p.precision == HGKS_MIXED && s.off32) {
     HGKS_PROF_BEGIN(K_ASSEMBLE, st);
     k_to_f32<<<vec_grid(100 * (int64_t)m.N), kBlock, 0, st>>>(100 * (int64_t)m.N, s.off, s.off32);
     HGKS_PROF_END(K_ASSEMBLE, st);

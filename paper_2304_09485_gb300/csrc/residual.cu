@@ -103,8 +103,9 @@ template <bool BATCH>
 __global__ void __launch_bounds__(kBlock) k_coef_weno(DevMesh m, const double *__restrict__ Q, double *__restrict__ coef) {
   const int N = m.N;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 5 * N) return;
-  const int c = t / N, i = t - c * N;
+  const int NL = BATCH ? m.NL : N;
+  if (t >= 5 * NL) return;
+  const int c = t / NL, i = t - c * NL;
   if (BATCH && !live(m, i)) return;
   const double qi = Q[(size_t)c * N + i];
   double a[9], b[12];
@@ -133,8 +134,9 @@ __global__ void __launch_bounds__(kBlock) k_coef_hweno(DevMesh m, const double *
                                                         double *__restrict__ coef) {
   const int N = m.N;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 5 * N) return;
-  const int c = t / N, i = t - c * N;
+  const int NL = BATCH ? m.NL : N;
+  if (t >= 5 * NL) return;
+  const int c = t / NL, i = t - c * NL;
   if (BATCH && !live(m, i)) return;
   const double qi = Q[(size_t)c * N + i];
   double data[19];
@@ -178,8 +180,9 @@ __global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const 
                                                const double *__restrict__ coef, double *__restrict__ wface) {
   const int N = m.N, F = m.F;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 4 * N) return;
-  const int slot = t / N, i = t - slot * N;
+  const int NL = BATCH ? m.NL : N;
+  if (t >= 4 * NL) return;
+  const int slot = t / NL, i = t - slot * NL;
   if (BATCH && !live(m, i)) return;                     // padding cell, or a mesh that has stopped
   const hgks_params &P = BATCH ? m.ptab[m.cmesh[i]] : Pv;
   const int cf = m.cface[(size_t)slot * N + i];
@@ -612,8 +615,9 @@ __global__ void __launch_bounds__(256) k_flux(DevMesh m, hgks_params Pv, const d
                                                   double *__restrict__ fflux, double *__restrict__ fpt, int *__restrict__ flags) {
   const int N = m.N, F = m.F;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 3 * F) return;
-  const int g = t / F, f = t - g * F;
+  const int FL = BATCH ? m.FL : F;
+  if (t >= 3 * FL) return;
+  const int g = t / FL, f = t - g * FL;
   if (BATCH && !m.mact[m.fmesh[f]]) return;             // a mesh of a batch that has stopped
   const hgks_params &P = BATCH ? m.ptab[m.fmesh[f]] : Pv;
   double T[9];
@@ -755,7 +759,7 @@ __global__ void k_local_dt(DevMesh m, hgks_params Pv, const double *__restrict__
 
 void launch_local_dt(const DevMesh &m, const hgks_params &p, const double *Q, double *dt, cudaStream_t st) {
   HGKS_PROF_BEGIN(K_DT, st);
-  if (m.ptab) k_local_dt<true><<<grid_for(m.N, kBlock), kBlock, 0, st>>>(m, p, Q, dt);
+  if (m.ptab) k_local_dt<true><<<grid_for(m.NL, kBlock), kBlock, 0, st>>>(m, p, Q, dt);
   else k_local_dt<false><<<grid_for(m.N, kBlock), kBlock, 0, st>>>(m, p, Q, dt);
   HGKS_PROF_END(K_DT, st);
 }
@@ -765,7 +769,8 @@ void launch_residual(const DevMesh &m, Scratch &s, const hgks_params &p, const d
   batch = batch || m.ptab != nullptr;
   launch_local_dt(m, p, Q, s.dt, st);
   HGKS_PROF_BEGIN(K_COEF, st);
-  const unsigned gc = grid_for(5 * (int64_t)m.N, kBlock);
+  const int64_t NL = batch ? m.NL : m.N, FL = batch ? m.FL : m.F;
+  const unsigned gc = grid_for(5 * NL, kBlock);
   if (p.scheme == HGKS_WENO) {
     if (batch) k_coef_weno<true><<<gc, kBlock, 0, st>>>(m, Q, s.coef);
     else k_coef_weno<false><<<gc, kBlock, 0, st>>>(m, Q, s.coef);
@@ -775,17 +780,17 @@ void launch_residual(const DevMesh &m, Scratch &s, const hgks_params &p, const d
   }
   HGKS_PROF_END(K_COEF, st);
   HGKS_PROF_BEGIN(K_RECON, st);
-  if (batch) k_recon<true><<<grid_for(4 * (int64_t)m.N, s.blk_recon), s.blk_recon, 0, st>>>(m, p, Q, s.coef, s.wface);
+  if (batch) k_recon<true><<<grid_for(4 * NL, s.blk_recon), s.blk_recon, 0, st>>>(m, p, Q, s.coef, s.wface);
   else k_recon<false><<<grid_for(4 * (int64_t)m.N, s.blk_recon), s.blk_recon, 0, st>>>(m, p, Q, s.coef, s.wface);
   HGKS_PROF_END(K_RECON, st);
   HGKS_PROF_BEGIN(K_FLUX, st);
   if (batch)
-    k_flux<true><<<grid_for(3 * (int64_t)m.F, s.blk_flux), s.blk_flux, 0, st>>>(m, p, Q, s.dt, s.wface, s.fflux, s.fpt, s.flags);
+    k_flux<true><<<grid_for(3 * FL, s.blk_flux), s.blk_flux, 0, st>>>(m, p, Q, s.dt, s.wface, s.fflux, s.fpt, s.flags);
   else
     k_flux<false><<<grid_for(3 * (int64_t)m.F, s.blk_flux), s.blk_flux, 0, st>>>(m, p, Q, s.dt, s.wface, s.fflux, s.fpt, s.flags);
   HGKS_PROF_END(K_FLUX, st);
   HGKS_PROF_BEGIN(K_GATHER, st);
-  if (batch) k_gather<true><<<grid_for(m.N, kBlock), kBlock, 0, st>>>(m, p.scheme == HGKS_HWENO, s.fflux, s.fpt, R, Gnew);
+  if (batch) k_gather<true><<<grid_for(NL, kBlock), kBlock, 0, st>>>(m, p.scheme == HGKS_HWENO, s.fflux, s.fpt, R, Gnew);
   else k_gather<false><<<grid_for(m.N, kBlock), kBlock, 0, st>>>(m, p.scheme == HGKS_HWENO, s.fflux, s.fpt, R, Gnew);
   HGKS_PROF_END(K_GATHER, st);
 }

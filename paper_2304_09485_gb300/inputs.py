@@ -83,22 +83,41 @@ def _orient_positive(xyz, tet):
     return tet
 
 
+def wall_clustered_nodes(n: int, h_min: float) -> np.ndarray:
+    """n + 1 nodes on [0, 1], cell sizes h_min r^min(i, n-1-i) (geometric growth
+    from both walls to the middle), r found by bisection so that they sum to 1."""
+    if h_min * n >= 1.0:
+        return np.linspace(0.0, 1.0, n + 1)
+    k = np.minimum(np.arange(n), n - 1 - np.arange(n)).astype(np.float64)
+    lo, hi = 1.0, 2.0
+    for _ in range(200):
+        r = 0.5 * (lo + hi)
+        lo, hi = (r, hi) if (h_min * r ** k).sum() < 1.0 else (lo, r)
+    sz = h_min * (0.5 * (lo + hi)) ** k
+    x = np.concatenate([[0.0], np.cumsum(sz)])
+    return x / x[-1]
+
+
 def cavity_mesh(n: int = 8, jitter: float = 0.1, seed: int = BASE_SEED + 0,
                 permute: bool = True, lid_tag: int = BC_WALL_LID,
-                wall_tag: int = BC_WALL_ISO) -> Mesh:
+                wall_tag: int = BC_WALL_ISO, h_min: float | None = None) -> Mesh:
     """Unit cube, n^3 hexahedra, each split into 6 tetrahedra (6 n^3 cells).
 
-    Interior vertices are moved by U(-jitter*h, +jitter*h) per axis; the order of
-    the cells is randomly permuted. The lid is the face y = 1 (Sec. 5.1).
+    Interior vertices are moved by U(-jitter*h, +jitter*h) per axis (h the smaller
+    neighbouring spacing along that axis); the order of the cells is randomly
+    permuted. The lid is the face y = 1 (Sec. 5.1). With h_min, the spacing grows
+    geometrically from h_min at every wall (Sec. 5.1's refined cavity mesh).
     """
     rng = np.random.default_rng(seed)
-    h = 1.0 / n
+    x1 = np.linspace(0.0, 1.0, n + 1) if h_min is None else wall_clustered_nodes(n, h_min)
+    sp = np.diff(x1)
+    hloc = np.minimum(np.concatenate([[sp[0]], sp]), np.concatenate([sp, [sp[-1]]]))   # per node
     g = np.arange(n + 1)
     I, J, K = np.meshgrid(g, g, g, indexing="ij")
     lat = np.stack([I, J, K], axis=-1).reshape(-1, 3)
-    xyz = lat.astype(np.float64) * h
+    xyz = x1[lat]
     interior = np.all((lat > 0) & (lat < n), axis=1)
-    d = rng.uniform(-jitter * h, jitter * h, size=xyz.shape)
+    d = rng.uniform(-jitter, jitter, size=xyz.shape) * hloc[lat]
     xyz[interior] += d[interior]
 
     def vid(i, j, k):
@@ -125,7 +144,7 @@ def cavity_mesh(n: int = 8, jitter: float = 0.1, seed: int = BASE_SEED + 0,
     bface = np.concatenate(bf).astype(np.int64)
     btag = np.concatenate(bt)
     return Mesh(xyz, tet.astype(np.int64), bface, btag, None,
-                name=f"cavity{n}", meta=dict(n=n, jitter=jitter, seed=seed))
+                name=f"cavity{n}", meta=dict(n=n, jitter=jitter, seed=seed, h_min=h_min))
 
 
 def periodic_cube_mesh(n: int = 6, jitter: float = 0.1, seed: int = BASE_SEED + 100,
@@ -327,3 +346,72 @@ def state_from_conditions(n: int, cond: dict) -> np.ndarray:
     u = cond["u_inf"]
     return uniform_state(n, rho=cond["rho_inf"], u=u[0], v=u[1], w=u[2], p=cond["p_inf"],
                          gamma=cond.get("gamma", 1.4))
+
+
+def sphere_stretch(n_layers: int, r_in: float = 0.5, r_out: float = 10.0, dr1: float | None = None) -> float:
+    """Geometric stretching ratio s with dr1 (s^L - 1) / (s - 1) = r_out - r_in; the
+    first layer defaults to the tangential size of a patch cell at the wall (pi r_in / (2 n))
+    scaled like the C2 grid (dr1 ~ 0.36 of it)."""
+    if dr1 is None:
+        dr1 = 0.36 * math.pi * r_in / (2 * max(2, n_layers // 2))
+    lo, hi = 1.0 + 1e-9, 2.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        tot = dr1 * (mid ** n_layers - 1) / (mid - 1)
+        lo, hi = (mid, hi) if tot < r_out - r_in else (lo, mid)
+    return 0.5 * (lo + hi)
+
+
+def batch_problems(n_problems: int = 48, n_min: float = 20e3, n_max: float = 500e3, seed: int = BASE_SEED + 400,
+                   viscous_sphere: bool = True):
+    """Many independent steady problems of uneven size: kind ~ Bernoulli(1/2)
+    cavity / sphere, N ~ log-uniform in [n_min, n_max] tets (cavity n = (N/6)^(1/3),
+    sphere patches n = (N/72)^(1/3) with 2n layers), Mach ~ U(0.1, 0.5),
+    Re ~ log-uniform in [50, 1000] (the sphere viscous as well when viscous_sphere).
+    Returns a list of dicts: kind, n, mesh, cond, n_cells."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_problems):
+        kind = "cavity" if rng.random() < 0.5 else "sphere"
+        N = math.exp(rng.uniform(math.log(n_min), math.log(n_max)))
+        mach = rng.uniform(0.1, 0.5)
+        Re = math.exp(rng.uniform(math.log(50.0), math.log(1000.0)))
+        if kind == "cavity":
+            n = max(2, int(round((N / 6.0) ** (1.0 / 3.0))))
+            mesh = cavity_mesh(n, seed=seed + 1 + k)
+            cond = cavity_conditions(mach, Re)
+        else:
+            n = max(2, int(round((N / 72.0) ** (1.0 / 3.0))))
+            mesh = sphere_mesh(n, 2 * n, stretch=sphere_stretch(2 * n),
+                               wall_tag=BC_NOSLIP_ADIA if viscous_sphere else BC_SLIP, seed=seed + 1 + k)
+            cond = sphere_conditions(mach, Re if viscous_sphere else None)
+        out.append(dict(kind=kind, n=n, mesh=mesh, cond=cond, n_cells=mesh.n_tet, mach=mach, Re=Re))
+    return out
+
+
+def serving_requests(n_requests: int = 24, n_min: float = 30e3, n_max: float = 250e3, rate: float = 1.0,
+                     seed: int = BASE_SEED + 500):
+    """Steady-solve requests with Poisson arrivals (exponential gaps of mean 1/rate s):
+    half inviscid spheres (Mach ~ U(0.2, 0.5), angle of attack ~ U(0, 10) deg), half
+    viscous spheres (Mach ~ U(0.2, 0.5), Re ~ log-uniform in [50, 1000]); N ~
+    log-uniform in [n_min, n_max] tets (patches n = (N/72)^(1/3), 2n layers).
+    Returns dicts: arrival (s), kind, mesh, cond, n_cells."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for k in range(n_requests):
+        t += rng.exponential(1.0 / rate)
+        N = math.exp(rng.uniform(math.log(n_min), math.log(n_max)))
+        n = max(2, int(round((N / 72.0) ** (1.0 / 3.0))))
+        mach = rng.uniform(0.2, 0.5)
+        if rng.random() < 0.5:
+            kind = "inviscid sphere"
+            cond = sphere_conditions(mach, None, aoa_deg=rng.uniform(0.0, 10.0))
+            wall = BC_SLIP
+        else:
+            kind = "viscous sphere"
+            cond = sphere_conditions(mach, math.exp(rng.uniform(math.log(50.0), math.log(1000.0))))
+            wall = BC_NOSLIP_ADIA
+        mesh = sphere_mesh(n, 2 * n, stretch=sphere_stretch(2 * n), wall_tag=wall, seed=seed + 1 + k)
+        out.append(dict(arrival=t, kind=kind, mesh=mesh, cond=cond, n_cells=mesh.n_tet))
+    return out

@@ -76,3 +76,18 @@ def test_batch_entry_points_reject_bad_arguments_without_gpu():
         assert b"NULL" in L.hgks_last_error(), fn
     # hgks_batch_info_t: three int64 and three int32, padded to 8 bytes
     assert C.sizeof(H.hgks_batch_info_t) == 40
+
+
+def test_server_and_dynamic_batch_entry_points_reject_bad_arguments_without_gpu():
+    L = H.lib()
+    out = C.c_void_p()
+    assert L.hgks_server_create(0, 1 << 30, 4, None, 1, C.byref(out)) == 1
+    assert L.hgks_batch_create_empty(0, 1024, 4096, 4, None, C.byref(out)) == 1
+    for fn, args in (("hgks_server_destroy", (None,)), ("hgks_server_step", (None, None, None, None)),
+                     ("hgks_server_status", (None, 1, None)), ("hgks_server_collect", (None, 1, None, None)),
+                     ("hgks_server_info", (None, None)), ("hgks_batch_add", (None, None, None, None)),
+                     ("hgks_batch_remove", (None, 0))):
+        assert getattr(L, fn)(*args) == 1, fn
+        assert b"NULL" in L.hgks_last_error(), fn
+    # hgks_request_info: 2 int32, 1 int64, hgks_solve_info (24 bytes), 4 doubles
+    assert C.sizeof(H.hgks_request_info) == 72

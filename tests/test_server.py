@@ -1,0 +1,142 @@
+"""Continuous batching (hgks_server_*, hgks_batch_add/remove): solves that join
+and leave a running batch give what they give alone.
+
+A solve in the server follows Algorithm 1 exactly as alone (same parameters,
+same kernels); only the summation order of its inner products differs, so the
+steady state must agree with hgks_solve_steady's to the steady-state tolerance
+(relative L2 1e-9) with the same number of steps, whatever else ran beside it
+and whenever it was admitted.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import paper_2304_09485_gb300 as H
+from paper_2304_09485_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+REQUESTS = [
+    ("sphere4", lambda: (I.sphere_mesh(4, 4, stretch=1.3), I.sphere_conditions(0.3, aoa_deg=4.0))),
+    ("cavity3", lambda: (I.cavity_mesh(3, seed=I.BASE_SEED + 21), I.cavity_conditions(0.2, 80.0))),
+    ("periodic4", lambda: (I.periodic_cube_mesh(4), I.sphere_conditions(0.35))),
+    ("sphere3", lambda: (I.sphere_mesh(3, 6, stretch=1.25), I.sphere_conditions(0.45, aoa_deg=8.0))),
+    ("cavity4", lambda: (I.cavity_mesh(4, seed=I.BASE_SEED + 22), I.cavity_conditions(0.3, 300.0))),
+]
+KW = dict(scheme=0, krylov_dim=8, restarts=2, jacobi_sweeps=2)
+DROP, MAX_STEPS = 0.2, 25
+
+
+def problems():
+    out = []
+    for k, (name, make) in enumerate(REQUESTS):
+        m, cond = make()
+        u = cond["u_inf"]
+        base = (cond["rho_inf"], u[0] + 0.04, u[1] + 0.02, u[2] - 0.01, cond["p_inf"])
+        Q0, _ = I.smooth_state(m, seed=I.BASE_SEED + 60 + k, amp=0.03, base=base)
+        p = H.hgks_default_params(**{**cond, "Pr": 0.72 if cond["viscous"] else 1.0, **KW})
+        out.append((name, m, cond, p, Q0))
+    return out
+
+
+def alone(m, p, Q0):
+    import torch
+    hm = H.hgks_mesh_create(m, scheme_mask=1)
+    Qd = hm.to_internal(Q0)
+    info, hist, conv = H.hgks_solve_steady(hm, p, Qd, None, drop_tol=DROP, max_steps=MAX_STEPS)
+    torch.cuda.synchronize()
+    return hm.to_caller(Qd), info
+
+
+def test_server_results_equal_alone_with_memory_admission(cuda):
+    probs = problems()
+    largest = max(m.n_tet for _, m, _, _, _ in probs)
+    shared = H.hgks_default_params(**KW)
+    # an arena for about one and a half of the largest meshes: later requests wait for memory
+    srv = H.hgks_server(shared, hbm_budget_bytes=int(1.6 * largest * 9000), max_inflight=8)
+    cap = srv.info().n_cells
+    assert largest <= cap < 3 * largest
+    ids = {}
+    for name, m, cond, p, Q0 in probs[:3]:
+        ids[name] = srv.submit(m, p, Q0, drop_tol=DROP, max_steps=MAX_STEPS)
+    waited_for_memory = False
+    late = probs[3:]
+    rounds = 0
+    while True:
+        fin, run, wait = srv.step()
+        rounds += 1
+        states = {n: srv.status(i).state for n, i in ids.items()}
+        running = [n for n, s in states.items() if s == 2]
+        # the running solves fit in the arena; a built request (state 1) waits only for room
+        assert sum((m.n_tet + 255) // 256 * 256 for n, m, *_ in probs if n in running) <= cap
+        if running and any(s == 1 for s in states.values()):
+            waited_for_memory = True
+        if rounds == 3:                          # more requests arrive while others run
+            for name, m, cond, p, Q0 in late:
+                ids[name] = srv.submit(m, p, Q0, drop_tol=DROP, max_steps=MAX_STEPS)
+        if rounds > 3 and run == 0 and wait == 0:
+            break
+        if run == 0:
+            time.sleep(0.005)                    # builds still running on the host
+        assert rounds < 5000
+    assert waited_for_memory
+    for name, m, cond, p, Q0 in probs:
+        st = srv.status(ids[name])
+        assert st.state == 3, name
+        Qs, _ = srv.collect(ids[name])
+        Qa, ia = alone(m, p, Q0)
+        assert st.solve.steps == ia.steps, f"{name}: {st.solve.steps} steps served, {ia.steps} alone"
+        assert bool(st.solve.converged) == bool(ia.converged)
+        rel = np.linalg.norm(Qs - Qa) / np.linalg.norm(Qa)
+        assert rel <= 1e-9, f"{name}: served vs alone {rel:.3e}"
+        assert st.t_submit <= st.t_built <= st.t_admit <= st.t_done
+
+
+def test_batch_add_remove_reuses_ranges(cuda):
+    import torch
+    probs = problems()
+    # A (384 tets) and B (384) fill the arena exactly; C (162) fits only into A's range once A leaves
+    (_, mA, _, pA, QA), (_, mB, _, pB, QB), (_, mC, _, pC, QC) = probs[4], probs[2], probs[1]
+    hA, hB, hC = (H.hgks_mesh_create(m, scheme_mask=1) for m in (mA, mB, mC))
+    pad = lambda n: (n + 255) // 256 * 256
+    assert pad(mC.n_tet) <= pad(mA.n_tet)
+    cells = pad(mA.n_tet) + pad(mB.n_tet)
+    b = H.hgks_batch_create_empty(cells, 3 * cells, 2, H.hgks_default_params(**KW))
+    kA = H.hgks_batch_add(b, hA, pA)
+    kB = H.hgks_batch_add(b, hB, pB)
+    with pytest.raises(H.HGKSError):            # no free slot
+        H.hgks_batch_add(b, hC, pC)
+    H.hgks_batch_remove(b, kA)
+    kC = H.hgks_batch_add(b, hC, pC)            # into the freed slot and range
+    for k, hm, Q in ((kB, hB, QB), (kC, hC, QC)):
+        H.hgks_batch_set_state(b, k, hm.to_internal(Q))
+    H.hgks_batch_gmres_step(b)
+    for k, hm, p, Q in ((kB, hB, pB, QB), (kC, hC, pC, QC)):
+        Qd = hm.to_internal(Q)
+        Q0 = Qd.clone()
+        H.hgks_gmres_step(hm, p, Qd, None)
+        Qb = torch.empty_like(Qd)
+        H.hgks_batch_get_state(b, k, Q=Qb)
+        torch.cuda.synchronize()
+        rel = (torch.linalg.norm((Qb - Q0) - (Qd - Q0)) / torch.linalg.norm(Qd - Q0)).item()
+        assert rel <= 1e-10, rel
+    assert H.hgks_batch_info(b).n_meshes == 2
+
+
+def test_server_reports_a_failed_build(cuda):
+    shared = H.hgks_default_params(**KW)
+    srv = H.hgks_server(shared, hbm_budget_bytes=1 << 30, max_inflight=2)
+    m, cond = I.cavity_mesh(2), I.cavity_conditions()
+    bad = I.Mesh(m.xyz.copy(), m.tet4.copy(), m.bface3.copy(), m.btag.copy(), None)
+    bad.xyz[:] = 0.0                              # every tetrahedron degenerate
+    p = H.hgks_default_params(**{**cond, **KW})
+    rid = srv.submit(bad, p, I.state_from_conditions(bad.n_tet, cond), drop_tol=0.1, max_steps=3)
+    for _ in range(200):
+        srv.step()
+        if srv.status(rid).state == 4:
+            break
+        time.sleep(0.01)
+    assert srv.status(rid).state == 4
+    with pytest.raises(H.HGKSError):
+        srv.collect(rid)
