@@ -42,7 +42,7 @@ def build(force: bool = False) -> str:
 class Params(C.Structure):
     _fields_ = [("scheme", C.c_int32), ("weights", C.c_int32), ("viscous", C.c_int32),
                 ("characteristic", C.c_int32), ("krylov_dim", C.c_int32), ("restarts", C.c_int32),
-                ("jacobi_sweeps", C.c_int32), ("tstar_end", C.c_int32),
+                ("jacobi_sweeps", C.c_int32), ("tstar_end", C.c_int32), ("jv_mode", C.c_int32),
                 ("gamma", C.c_double), ("Pr", C.c_double), ("mu", C.c_double), ("cfl", C.c_double), ("flux_cfl", C.c_double),
                 ("tau_eps", C.c_double), ("tau_C", C.c_double), ("lin_weight", C.c_double),
                 ("weno_eps", C.c_double), ("flux_dt", C.c_double),
@@ -53,7 +53,7 @@ class Params(C.Structure):
 def make_params(**kw) -> Params:
     """Parameters with the paper's defaults (Sec. 3.4, Sec. 4, Sec. 5)."""
     d = dict(scheme=0, weights=0, viscous=0, characteristic=1, krylov_dim=10, restarts=3,
-             jacobi_sweeps=2, tstar_end=1, gamma=1.4, Pr=1.0, mu=0.0, cfl=10.0, flux_cfl=1.0, tau_eps=0.1,
+             jacobi_sweeps=2, tstar_end=1, jv_mode=0, gamma=1.4, Pr=1.0, mu=0.0, cfl=10.0, flux_cfl=1.0, tau_eps=0.1,
              tau_C=1.0, lin_weight=0.025, weno_eps=1e-8, flux_dt=0.0, rho_inf=1.0,
              u_inf=(0.3, 0.0, 0.0), p_inf=1.0 / 1.4, wall_T=1.0 / 1.4, lid_speed=0.0)
     d.update(kw)
@@ -79,7 +79,8 @@ def lib():
         L.orc_mesh_create.argtypes = [dp, i64, C.POINTER(C.c_int64), i64, C.POINTER(C.c_int64),
                                       C.POINTER(C.c_int32), i64, dp, i32, C.c_char_p, C.c_int]
         L.orc_mesh_destroy.argtypes = [vp]
-        for name in ["orc_residual", "orc_local_dt", "orc_jacobian", "orc_precondition", "orc_gmres",
+        for name in ["orc_residual", "orc_residual_dt", "orc_apply_fd", "orc_local_dt", "orc_jacobian",
+                     "orc_precondition", "orc_gmres",
                      "orc_gmres_step", "orc_solve_steady", "orc_recon_side", "orc_fit_cell", "orc_slope",
                      "orc_lu_solve", "orc_inverse"]:
             getattr(L, name).restype = C.c_int
@@ -200,6 +201,32 @@ class OracleMesh:
         if rc:
             raise RuntimeError("orc_gmres failed")
         return dx, hist
+
+    def residual_dt(self, params, Q, G, dt):
+        """R = L(Q) with the given local time step (caller order [n, 5])."""
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        Ga = np.ascontiguousarray(G, dtype=np.float64) if G is not None else None
+        R = np.zeros_like(Q)
+        rc = lib().orc_residual_dt(C.c_void_p(self.h), C.byref(params), _p(Q), _p(Ga) if Ga is not None else None,
+                                   _p(np.ascontiguousarray(dt, dtype=np.float64)), _p(R), None, None, C.c_int64(0))
+        if rc:
+            raise RuntimeError(f"orc_residual_dt failed ({rc})")
+        return R
+
+    def apply_fd(self, params, Q, G, dt, x):
+        """(y, sigma): y = |Omega|/dt x - (L(Q + sigma x) - L(Q)) / sigma, Eq. (frechet)."""
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        Ga = np.ascontiguousarray(G, dtype=np.float64) if G is not None else None
+        dt = np.ascontiguousarray(dt, dtype=np.float64)
+        LQ = self.residual_dt(params, Q, G, dt)
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.zeros_like(x)
+        sig = C.c_double(0)
+        rc = lib().orc_apply_fd(C.c_void_p(self.h), C.byref(params), _p(Q), _p(Ga) if Ga is not None else None,
+                                _p(dt), _p(LQ), _p(x), _p(y), C.byref(sig))
+        if rc:
+            raise RuntimeError("orc_apply_fd failed")
+        return y, sig.value
 
     def gmres_step(self, params, Q, G=None):
         Q = np.array(Q, dtype=np.float64, copy=True)

@@ -30,6 +30,8 @@ typedef struct {
   int32_t characteristic;/* 1: reconstruct characteristic variables (Sec. 5) */
   int32_t krylov_dim, restarts, jacobi_sweeps;
   int32_t tstar_end;     /* compact point value at t = dt (1) or t = 0 (0)  */
+  int32_t jv_mode;       /* 0: assembled approximate A (Eq. (A-system-2)), 1: matrix-free A x
+                            from the Frechet difference of Eq. (frechet)      */
   double gamma, Pr, mu, cfl, flux_cfl; /* flux_cfl: CFL of the time step used inside the flux */
   double tau_eps, tau_C, lin_weight, weno_eps;
   double flux_dt;        /* > 0: fixed time step inside the flux (tests)     */
@@ -108,13 +110,23 @@ void orc_euler_jacobian(const double *Q, const double *n, double gamma, double *
 int orc_local_dt(orc_mesh *m, const orc_params *p, const double *Q, double *dt);
 int orc_residual(orc_mesh *m, const orc_params *p, const double *Q, const double *G,
                  double *R, double *Gnew, const int64_t *cells, int64_t ncells);
+/* the same with the local time step given (dt_in) instead of computed from Q */
+int orc_residual_dt(orc_mesh *m, const orc_params *p, const double *Q, const double *G, const double *dt_in,
+                    double *R, double *Gnew, const int64_t *cells, int64_t ncells);
+/* y = A x without A: |Omega|/dt x - (L(Q + sigma x) - L(Q)) / sigma (Eq. (frechet)) */
+int orc_apply_fd(orc_mesh *m, const orc_params *p, const double *Q, const double *G, const double *dt,
+                 const double *LQ, const double *x, double *y, double *sigma_out);
 int orc_jacobian(orc_mesh *m, const orc_params *p, const double *Q, const double *dt,
                  double *diag /*[nc][25]*/, double *off /*[nc][4][25]*/);
 void orc_apply_A(const orc_mesh *m, const double *diag, const double *off, const double *x, double *y);
 int orc_precondition(const orc_mesh *m, const double *diag, const double *off, int sweeps,
                      const double *b, double *x);
+/* the state a matrix-free product needs (jv_mode 1): Q, G, dt and L(Q) of the step */
+typedef struct { orc_mesh *m; const double *Q, *G, *dt, *LQ; } orc_fd_ctx;
 int orc_gmres(const orc_mesh *m, const double *diag, const double *off, const orc_params *p,
               const double *rhs, double *dx, double *hist);
+int orc_gmres_fd(const orc_mesh *m, const double *diag, const double *off, const orc_params *p,
+                 const orc_fd_ctx *fd, const double *rhs, double *dx, double *hist);
 int orc_gmres_step(orc_mesh *m, const orc_params *p, double *Q, double *G, double *res,
                    double *dQ_out);
 int orc_solve_steady(orc_mesh *m, const orc_params *p, double *Q, double *G, double drop,

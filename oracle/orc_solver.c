@@ -6,6 +6,7 @@
  * of Eq. (point) by Gauss's theorem, Eq. (derivative).
  * Implicit system: Eq. (A-system-2) with the Rusanov-type split Jacobians of
  * Eq. (deri-matrix); Jacobi preconditioner of Eq. (precond); Algorithm 1. */
+#include <float.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -41,6 +42,11 @@ int orc_local_dt(orc_mesh *m, const orc_params *p, const double *Q, double *dt) 
 
 int orc_residual(orc_mesh *m, const orc_params *p, const double *Q, const double *G,
                  double *R, double *Gnew, const int64_t *cells, int64_t ncells) {
+  return orc_residual_dt(m, p, Q, G, NULL, R, Gnew, cells, ncells);
+}
+
+int orc_residual_dt(orc_mesh *m, const orc_params *p, const double *Q, const double *G, const double *dt_in,
+                    double *R, double *Gnew, const int64_t *cells, int64_t ncells) {
   const int64_t nc = m->nc, nf = m->nf;
   char *fsel = (char *)calloc(nf + 1, 1), *csel = (char *)calloc(nc + 1, 1);
   if (cells) {
@@ -55,7 +61,8 @@ int orc_residual(orc_mesh *m, const orc_params *p, const double *Q, const double
   for (int64_t i = 0; i < nc; i++) if (csel[i]) err |= orc_fit_cell(m, i, p->scheme) != 0;
   if (err) { free(fsel); free(csel); return -1; }
   double *dt = (double *)malloc(sizeof(double) * (nc + 1));
-  orc_local_dt(m, p, Q, dt);
+  if (dt_in) memcpy(dt, dt_in, sizeof(double) * nc);
+  else orc_local_dt(m, p, Q, dt);
   double *Ff = (double *)calloc(5 * (nf + 1), sizeof(double)), *Pf = (double *)calloc(5 * (nf + 1), sizeof(double));
 #pragma omp parallel for schedule(dynamic, 16) reduction(| : err)
   for (int64_t f = 0; f < nf; f++) {
@@ -203,10 +210,53 @@ int orc_precondition(const orc_mesh *m, const double *diag, const double *off, i
 
 static double dot(int64_t n, const double *a, const double *b) { double s = 0.0; for (int64_t i = 0; i < n; i++) s += a[i] * b[i]; return s; }
 
+/* Matrix-free product with the implicit operator of Eq. (impEuler):
+ * A = |Omega|/dt I - dL/dQ, where dL/dQ x is replaced by the Frechet difference
+ * of Eq. (frechet), (L(Q + sigma x) - L(Q)) / sigma, with the step's dt and G
+ * held fixed. The paper leaves sigma to the user; the reading taken is
+ * sigma = sqrt(eps_mach) (1 + ||Q||_2) / ||x||_2. x = 0 gives y = 0. */
+int orc_apply_fd(orc_mesh *m, const orc_params *p, const double *Q, const double *G, const double *dt,
+                 const double *LQ, const double *x, double *y, double *sigma_out) {
+  const int64_t nc = m->nc, n = 5 * nc;
+  const double nx = sqrt(dot(n, x, x)), nq = sqrt(dot(n, Q, Q));
+  if (nx == 0.0) {
+    for (int64_t k = 0; k < n; k++) y[k] = 0.0;
+    if (sigma_out) *sigma_out = 0.0;
+    return 0;
+  }
+  const double sigma = sqrt(DBL_EPSILON) * (1.0 + nq) / nx;
+  double *Qs = (double *)malloc(sizeof(double) * (n + 1)), *Ls = (double *)malloc(sizeof(double) * (n + 1));
+  for (int64_t k = 0; k < n; k++) Qs[k] = Q[k] + sigma * x[k];
+  int rc = orc_residual_dt(m, p, Qs, G, dt, Ls, NULL, NULL, 0);
+  if (!rc)
+    for (int64_t i = 0; i < nc; i++)
+      for (int c = 0; c < 5; c++) {
+        const int64_t k = 5 * i + c;
+        y[k] = m->vol[i] / dt[i] * x[k] - (Ls[k] - LQ[k]) / sigma;
+      }
+  if (sigma_out) *sigma_out = sigma;
+  free(Qs); free(Ls);
+  return rc;
+}
+
+static int apply_op(const orc_mesh *m, const double *diag, const double *off, const orc_params *p,
+                    const orc_fd_ctx *fd, const double *x, double *y) {
+  if (fd && p->jv_mode == 1) return orc_apply_fd(fd->m, p, fd->Q, fd->G, fd->dt, fd->LQ, x, y, NULL);
+  orc_apply_A(m, diag, off, x, y);
+  return 0;
+}
+
 /* Restarted GMRES on P^{-1} A x = P^{-1} rhs from x = 0 with modified
  * Gram-Schmidt Arnoldi, Algorithm 1; hist[restart] = ||P^{-1} r0||. */
 int orc_gmres(const orc_mesh *m, const double *diag, const double *off, const orc_params *p,
               const double *rhs, double *dx, double *hist) {
+  return orc_gmres_fd(m, diag, off, p, NULL, rhs, dx, hist);
+}
+
+/* the same; with jv_mode 1 every product with A is the matrix-free one, while
+ * the preconditioner keeps the assembled approximate A (Eq. (precond)) */
+int orc_gmres_fd(const orc_mesh *m, const double *diag, const double *off, const orc_params *p,
+                 const orc_fd_ctx *fd, const double *rhs, double *dx, double *hist) {
   const int64_t n = 5 * m->nc;
   const int mk = p->krylov_dim;
   double *V = (double *)malloc(sizeof(double) * n * (mk + 1)), *w = (double *)malloc(sizeof(double) * (n + 1)),
@@ -215,7 +265,7 @@ int orc_gmres(const orc_mesh *m, const double *diag, const double *off, const or
   memset(dx, 0, sizeof(double) * n);
   int rc = 0;
   for (int it = 0; it < p->restarts; it++) {
-    orc_apply_A(m, diag, off, dx, t);
+    if (apply_op(m, diag, off, p, fd, dx, t)) { rc = -1; break; }
     for (int64_t k = 0; k < n; k++) t[k] = rhs[k] - t[k];
     if (orc_precondition(m, diag, off, p->jacobi_sweeps, t, r)) { rc = -1; break; }
     double beta = sqrt(dot(n, r, r));
@@ -225,7 +275,7 @@ int orc_gmres(const orc_mesh *m, const double *diag, const double *off, const or
     memset(H, 0, sizeof(double) * (mk + 1) * mk);
     int used = 0;
     for (int j = 0; j < mk; j++) {
-      orc_apply_A(m, diag, off, V + n * j, t);
+      if (apply_op(m, diag, off, p, fd, V + n * j, t)) { rc = -1; break; }
       orc_precondition(m, diag, off, p->jacobi_sweeps, t, w);
       for (int i = 0; i <= j; i++) {
         double h = dot(n, w, V + n * i);
@@ -238,6 +288,7 @@ int orc_gmres(const orc_mesh *m, const double *diag, const double *off, const or
       if (hn == 0.0) break;
       for (int64_t k = 0; k < n; k++) V[n * (j + 1) + k] = w[k] / hn;
     }
+    if (rc) break;
     /* minimise || beta e1 - H y || by Givens rotations, then back substitution */
     double *gvec = (double *)calloc(mk + 1, sizeof(double)), *y = (double *)calloc(mk + 1, sizeof(double));
     gvec[0] = beta;
@@ -283,7 +334,8 @@ int orc_gmres_step(orc_mesh *m, const orc_params *p, double *Q, double *G, doubl
   if (!rc) {
     if (res) *res = density_res(m, R);
     orc_jacobian(m, p, Q, dt, diag, off);
-    rc = orc_gmres(m, diag, off, p, R, dQ, NULL);
+    orc_fd_ctx fd = {m, Q, G, dt, R};
+    rc = orc_gmres_fd(m, diag, off, p, &fd, R, dQ, NULL);
   }
   if (!rc) {
     for (int64_t k = 0; k < 5 * nc; k++) Q[k] += dQ[k];
