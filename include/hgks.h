@@ -77,7 +77,10 @@ typedef struct {
   int32_t viscous;         /* 0: tau = eps dt + C|dp|dt, 1: tau = mu/p + C|dp|dt (Sec. 5) */
   int32_t characteristic;  /* 1: reconstruct characteristic variables (Sec. 5), 0: conservative */
   int32_t precision;       /* HGKS_FP64 | HGKS_MIXED (FP32 Krylov basis, Arnoldi, Jacobi) */
-  int32_t jv_mode;         /* 0: assembled approximate Jacobian (Eq. (deri-matrix))    */
+  int32_t jv_mode;         /* 0: products with the assembled approximate A (Eq. (deri-matrix));
+                              1: matrix-free products (Eq. (frechet), hgks_apply_jacobian_fd),
+                              the Jacobi preconditioner still from the assembled A; single
+                              meshes only (batches and servers take 0)                  */
   int32_t krylov_dim;      /* Arnoldi steps per restart, 1..64                        */
   int32_t restarts;        /* GMRES cycles per implicit step                          */
   int32_t jacobi_sweeps;   /* k_max of Eq. (precond)                                  */
@@ -165,6 +168,12 @@ hgks_status hgks_assemble(hgks_mesh mesh, const hgks_params *p, const double *Q,
                           double *diag_out, double *off_out, void *cuda_stream);
 /* y = A x with the assembled A (device double[5][N]). */
 hgks_status hgks_apply_jacobian(hgks_mesh mesh, const double *x, double *y, void *cuda_stream);
+/* y = A x without A (Eq. (frechet)): y = |Omega|/dt x - (L(Q + sigma x) - L(Q)) / sigma
+ * with sigma = sqrt(eps_mach) (1 + ||Q||_2) / ||x||_2 (y = 0 for x = 0), L evaluated
+ * with the given time step dt and gradients G held fixed (G NULL for WENO). All
+ * arrays device, internal order, [5][N] (dt [N]). Uses the handle's scratch. */
+hgks_status hgks_apply_jacobian_fd(hgks_mesh mesh, const hgks_params *p, const double *Q, const double *G,
+                                   const double *dt, const double *x, double *y, void *cuda_stream);
 /* x = P^{-1} b, Jacobi iteration of Eq. (precond) with `sweeps` sweeps. */
 hgks_status hgks_precondition(hgks_mesh mesh, int32_t sweeps, const double *b, double *x,
                               void *cuda_stream);

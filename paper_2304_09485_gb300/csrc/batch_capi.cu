@@ -194,6 +194,7 @@ hgks_status batch_new(int device, int64_t cell_cap, int64_t face_cap, int nslot,
   *out = nullptr;
   const int64_t N = (cell_cap + kBatchBlock - 1) / kBatchBlock * kBatchBlock, F = std::max<int64_t>(face_cap, 1);
   if (N <= 0 || nslot < 1 || nslot > 32767) return fail_msg(HGKS_ERR_ARG, "batch capacity or slot count out of range");
+  if (shared.jv_mode != 0) return fail_msg(HGKS_ERR_ARG, "batches use the assembled A (jv_mode 0)");
   if (6 * std::max(N, F) >= (int64_t)INT32_MAX) return fail_msg(HGKS_ERR_ARG, "batch too large for 32-bit indexing");
   if (!(schemes & (shared.scheme == HGKS_WENO ? 1 : 2))) return fail_msg(HGKS_ERR_ARG, "batch has no data for its scheme");
   Batch *B = new (std::nothrow) Batch;

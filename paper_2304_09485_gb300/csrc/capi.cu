@@ -91,7 +91,7 @@ hgks_status check_params(const Mesh &m, const hgks_params *p) {
   if (p->viscous && !(p->mu > 0.0)) return fail(HGKS_ERR_ARG, "viscous flow needs mu > 0");
   if (!p->viscous && !(p->tau_eps > 0.0)) return fail(HGKS_ERR_ARG, "inviscid flow needs tau_eps > 0");
   if (p->precision != HGKS_FP64 && p->precision != HGKS_MIXED) return fail(HGKS_ERR_ARG, "unknown precision");
-  if (p->jv_mode != 0) return fail(HGKS_ERR_ARG, "only the assembled Jacobian is available");
+  if (p->jv_mode != 0 && p->jv_mode != 1) return fail(HGKS_ERR_ARG, "jv_mode must be 0 (assembled) or 1 (matrix-free)");
   return HGKS_OK;
 }
 
@@ -155,6 +155,13 @@ hgks_status ensure_scratch(Mesh &m, int kdim, bool implicit, bool mixed) {
   if (implicit && mixed && !s.V32) {
     if ((st = dalloc(m, &s.V32, (size_t)(s.kdim + 1) * s.vstride))) return st;
   }
+  return HGKS_OK;
+}
+
+// the perturbed state and its residual of the matrix-free products (jv_mode 1)
+static hgks_status ensure_fd(Mesh &m) {
+  hgks_status st;
+  if (!m.s.Qp && ((st = dalloc(m, &m.s.Qp, 5 * (size_t)m.N)) || (st = dalloc(m, &m.s.Rp, 5 * (size_t)m.N)))) return st;
   return HGKS_OK;
 }
 
@@ -340,6 +347,7 @@ hgks_status hgks_assemble(hgks_mesh mesh, const hgks_params *p, const double *Q,
   if (!Q || !dt) return fail(HGKS_ERR_ARG, "Q or dt is NULL");
   if ((st = set_device(m))) return st;
   if ((st = ensure_scratch(m, p->krylov_dim, true, p->precision == HGKS_MIXED))) return st;
+  if (p->jv_mode == 1 && (st = ensure_fd(m))) return st;
   launch_assemble(m.d, m.s, *p, Q, dt, diag_out, off_out, (cudaStream_t)cuda_stream);
   return last_launch();
 }
@@ -351,6 +359,22 @@ hgks_status hgks_apply_jacobian(hgks_mesh mesh, const double *x, double *y, void
   hgks_status st;
   if ((st = set_device(m))) return st;
   launch_apply_A(m.d, m.s, x, y, (cudaStream_t)cuda_stream);
+  return last_launch();
+}
+
+hgks_status hgks_apply_jacobian_fd(hgks_mesh mesh, const hgks_params *p, const double *Q, const double *G,
+                                   const double *dt, const double *x, double *y, void *cuda_stream) {
+  if (!mesh) return fail(HGKS_ERR_ARG, "mesh is NULL");
+  Mesh &m = mesh->m;
+  hgks_status st = check_params(m, p);
+  if (st) return st;
+  if (!Q || !dt || !x || !y || (p->scheme == HGKS_HWENO && !G)) return fail(HGKS_ERR_ARG, "NULL argument");
+  if ((st = set_device(m)) || (st = ensure_scratch(m, p->krylov_dim, true, false)) || (st = ensure_fd(m))) return st;
+  cudaStream_t s_ = (cudaStream_t)cuda_stream;
+  HGKS_CUDA(cudaMemcpyAsync(m.s.dt, dt, sizeof(double) * m.N, cudaMemcpyDeviceToDevice, s_));
+  launch_residual(m.d, m.s, *p, Q, G, m.s.R, nullptr, s_, false, false);
+  launch_norm(m.d, m.s, Q, m.s.hs + kHsNormQ, s_);
+  launch_apply_fd(m.d, m.s, *p, Q, G, x, nullptr, y, s_);
   return last_launch();
 }
 
@@ -377,7 +401,7 @@ static hgks_status gmres_step_impl(Mesh &m, const hgks_params *p, double *Q, dou
     launch_density_l1(d, s, s.R, res_dev, st_);
   }
   launch_assemble(d, s, *p, Q, s.dt, nullptr, nullptr, st_);
-  hgks_status st = gmres_solve(d, s, *p, s.R, s.dQ, info, st_);
+  hgks_status st = gmres_solve(d, s, *p, s.R, s.dQ, info, st_, Q, G);
   if (st) return st;
   if (dQ_out) HGKS_CUDA(cudaMemcpyAsync(dQ_out, s.dQ, sizeof(double) * 5 * m.N, cudaMemcpyDeviceToDevice, st_));
   launch_update(d, Q, s.dQ, G, s.Gnew, p->scheme == HGKS_HWENO ? 15 : 0, st_);
@@ -411,6 +435,7 @@ hgks_status hgks_gmres_step(hgks_mesh mesh, const hgks_params *p, double *Q, dou
   if (p->scheme == HGKS_HWENO && !G) return fail(HGKS_ERR_ARG, "compact scheme needs G");
   if ((st = set_device(m))) return st;
   if ((st = ensure_scratch(m, p->krylov_dim, true, p->precision == HGKS_MIXED))) return st;
+  if (p->jv_mode == 1 && (st = ensure_fd(m))) return st;
   if (info) std::memset(info, 0, sizeof(*info));
   return gmres_step_impl(m, p, Q, G, dQ_out, info, (cudaStream_t)cuda_stream);
 }
@@ -425,6 +450,7 @@ hgks_status hgks_solve_steady(hgks_mesh mesh, const hgks_params *p, double *Q, d
   if (!(drop_tol > 0.0) || max_steps < 0) return fail(HGKS_ERR_ARG, "drop_tol must be > 0 and max_steps >= 0");
   if ((st = set_device(m))) return st;
   if ((st = ensure_scratch(m, p->krylov_dim, true, p->precision == HGKS_MIXED))) return st;
+  if (p->jv_mode == 1 && (st = ensure_fd(m))) return st;
   cudaStream_t s_ = (cudaStream_t)cuda_stream;
   double ref = 0.0, res = 0.0;
   int k = 0;
@@ -497,6 +523,7 @@ hgks_status hgks_gmres_step_host(hgks_mesh mesh, const hgks_params *p, double *Q
   if (!Q_host || (compact && !G_host)) return fail(HGKS_ERR_ARG, "NULL host array");
   if ((st = set_device(m))) return st;
   if ((st = ensure_scratch(m, p->krylov_dim, true, p->precision == HGKS_MIXED))) return st;
+  if (p->jv_mode == 1 && (st = ensure_fd(m))) return st;
   double *buf;
   if ((st = host_state_buffer(m, &buf))) return st;
   const size_t N = m.N;

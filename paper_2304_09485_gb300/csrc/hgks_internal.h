@@ -107,6 +107,7 @@ struct Scratch {
   double *hs = nullptr;          // small device scalars: H, beta, y, norms
   int *flags = nullptr;          // [8] device flags (nonphysical count, breakdown)
   double *hostbuf = nullptr;     // [40][N] device state of the *_host entry points
+  double *Qp = nullptr, *Rp = nullptr;   // [5][N] perturbed state and its residual (matrix-free products)
   int kdim = 0;
   size_t bytes = 0;
   int blk_recon = 128, blk_flux = 128;   // launch shapes of the two FP64-bound kernels (autotuned for batches)
@@ -140,14 +141,22 @@ hgks_status build_host_mesh(const double *xyz, int64_t nv, const int64_t *tet, i
 
 // ---- kernels (residual.cu, implicit.cu) ----
 void launch_local_dt(const DevMesh &m, const hgks_params &p, const double *Q, double *dt, cudaStream_t st);
+// fresh_dt = false keeps s.dt (the residual then uses the step's time step)
 void launch_residual(const DevMesh &m, Scratch &s, const hgks_params &p, const double *Q, const double *G,
-                     double *R, double *Gnew, cudaStream_t st, bool batch = false);
+                     double *R, double *Gnew, cudaStream_t st, bool batch = false, bool fresh_dt = true);
 void launch_assemble(const DevMesh &m, Scratch &s, const hgks_params &p, const double *Q, const double *dt,
                      double *diag_out, double *off_out, cudaStream_t st, bool batch = false);
 void launch_apply_A(const DevMesh &m, const Scratch &s, const double *x, double *y, cudaStream_t st);
 void launch_precondition(const DevMesh &m, Scratch &s, int sweeps, const double *b, double *x, cudaStream_t st);
+// Q, G: the step's state, for the matrix-free products of jv_mode 1 (s.R = L(Q), s.dt its time step)
 hgks_status gmres_solve(const DevMesh &m, Scratch &s, const hgks_params &p, const double *rhs, double *dx,
-                        hgks_step_info *info, cudaStream_t st);
+                        hgks_step_info *info, cudaStream_t st, const double *Q = nullptr, const double *G = nullptr);
+// y = A x (b null) or b - A x with A x = |Omega|/dt x - (L(Q + sigma x) - L(Q)) / sigma, Eq. (frechet);
+// needs s.R = L(Q) and s.dt, and ||Q|| in s.hs[kHsNormQ]
+void launch_apply_fd(const DevMesh &m, Scratch &s, const hgks_params &p, const double *Q, const double *G,
+                     const double *x, const double *b, double *y, cudaStream_t st);
+void launch_norm(const DevMesh &m, Scratch &s, const double *x, double *out_dev, cudaStream_t st);
+constexpr int kHsNormQ = 65 * 64 + 210;   // hs slots of the matrix-free products: ||Q||, ||x||, sigma, 0
 void launch_density_l1(const DevMesh &m, Scratch &s, const double *R, double *out_dev, cudaStream_t st);
 void launch_update(const DevMesh &m, double *Q, const double *dQ, double *G, const double *Gnew, int ncomp_g,
                    cudaStream_t st);

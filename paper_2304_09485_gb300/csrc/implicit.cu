@@ -312,6 +312,31 @@ __global__ void k_update(int64_t n5, int64_t ng, double *__restrict__ Q, const d
   }
 }
 
+// ---- matrix-free products (jv_mode 1), Eq. (frechet) ----
+// Qp = Q + sigma x, sigma = sqrt(eps_mach) (1 + ||Q||) / ||x|| (0 for x = 0); nrm = {||Q||, ||x||, sigma}
+template <typename TV>
+__global__ void k_fd_perturb(int64_t n, const double *__restrict__ Q, const TV *__restrict__ x, double *__restrict__ nrm,
+                             double *__restrict__ Qp) {
+  const double nx = nrm[1];
+  const double sigma = nx > 0.0 ? 0x1p-26 * (1.0 + nrm[0]) / nx : 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) nrm[2] = sigma;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    Qp[k] = Q[k] + sigma * (double)x[k];
+}
+
+// y = A x or b - A x, A x = |Omega_i|/dt_i x - (L(Qp) - L(Q)) / sigma (A x = 0 when sigma = 0)
+template <typename TV, typename TO>
+__global__ void k_fd_combine(int N, const double *__restrict__ vol, const double *__restrict__ dt, const TV *__restrict__ x,
+                             const double *__restrict__ Rp, const double *__restrict__ R0, const double *__restrict__ sig,
+                             const double *__restrict__ b, TO *__restrict__ y) {
+  const double sigma = *sig;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 5 * (int64_t)N; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = k % N;
+    const double ax = sigma > 0.0 ? vol[i] / dt[i] * (double)x[k] - (Rp[k] - R0[k]) / sigma : 0.0;
+    y[k] = (TO)(b ? b[k] - ax : ax);
+  }
+}
+
 unsigned vec_grid(int64_t n) {
   int64_t g = (n + kBlock - 1) / kBlock;
   const int64_t cap = 152 * 8;
@@ -326,6 +351,29 @@ struct KBuf {
 };
 KBuf<double> kbuf64(Scratch &s) { return {s.off, s.dval, s.dinv, s.V, s.w, s.t, s.t2, s.red}; }
 KBuf<float> kbuf32(Scratch &s) { return {s.off32, s.dval32, s.dinv32, s.V32, s.w32, s.t32, s.t232, s.red32}; }
+
+template <typename T> T *partials(Scratch &s);
+template <> double *partials<double>(Scratch &s) { return s.red; }
+template <> float *partials<float>(Scratch &s) { return s.red32; }
+
+// y = A x (b null) or b - A x with the matrix-free A of Eq. (frechet); s.R = L(Q), s.dt, ||Q|| in hs
+template <typename TV, typename TO>
+void fd_apply(const DevMesh &m, Scratch &s, const hgks_params &p, const double *Q, const double *G, const TV *x,
+              const double *b, TO *y, cudaStream_t st) {
+  const int64_t n = 5 * (int64_t)m.N;
+  double *nrm = s.hs + kHsNormQ;
+  HGKS_PROF_BEGIN(K_DOT, st);
+  k_axpy_dot<TV><<<kRedBlocks, kBlock, 0, st>>>(n, const_cast<TV *>(x), nullptr, nullptr, x, 1, partials<TV>(s),
+                                                 s.red_count, nrm + 1);
+  HGKS_PROF_END(K_DOT, st);
+  HGKS_PROF_BEGIN(K_SPMV, st);
+  k_fd_perturb<TV><<<vec_grid(n), kBlock, 0, st>>>(n, Q, x, nrm, s.Qp);
+  HGKS_PROF_END(K_SPMV, st);
+  launch_residual(m, s, p, s.Qp, G, s.Rp, nullptr, st, false, false);
+  HGKS_PROF_BEGIN(K_SPMV, st);
+  k_fd_combine<TV, TO><<<vec_grid(n), kBlock, 0, st>>>(m.N, m.vol, s.dt, x, s.Rp, s.R, nrm + 2, b, y);
+  HGKS_PROF_END(K_SPMV, st);
+}
 
 // x = P^{-1} b (Eq. (precond)); if dotv is given, also (x, dotv) into *dot_out.
 template <typename T>
@@ -363,7 +411,8 @@ void precondition_t(const DevMesh &m, Scratch &s, const KBuf<T> &k, int sweeps, 
 // One restarted GMRES solve in precision T; rhs and dx stay FP64.
 template <typename T>
 void gmres_t(const DevMesh &m, Scratch &s, const KBuf<T> &k, const hgks_params &p, const double *rhs, double *dx,
-             cudaStream_t st) {
+             cudaStream_t st, const double *Q, const double *G) {
+  const bool fd = p.jv_mode == 1;
   const int mk = p.krylov_dim;
   const int64_t n = 5 * (int64_t)m.N, vs = s.vstride;
   double *H = s.hs, *beta = s.hs + (mk + 1) * mk, *y = beta + 1, *lres = y + mk;
@@ -371,10 +420,18 @@ void gmres_t(const DevMesh &m, Scratch &s, const KBuf<T> &k, const hgks_params &
   for (int it = 0; it < p.restarts; it++) {
     cudaMemsetAsync(H, 0, sizeof(double) * (mk + 1) * mk, st);
     // r0 = rhs - A dx (FP64 vectors, blocks of precision T), v1 = P^{-1} r0 / ||P^{-1} r0||
-    HGKS_PROF_BEGIN(K_SPMV, st);
-    k_apply<T, double, T, kSpmv, false><<<cg, kCellBlock, 0, st>>>(m, k.off, k.dval, k.dinv, rhs, dx, k.t, nullptr, nullptr,
-                                                                    nullptr, nullptr);
-    HGKS_PROF_END(K_SPMV, st);
+    if (fd && it > 0) {
+      fd_apply<double, T>(m, s, p, Q, G, dx, rhs, k.t, st);
+    } else if (fd) {                       // dx = 0: r0 = rhs (the product of a zero vector is zero)
+      HGKS_PROF_BEGIN(K_SPMV, st);
+      k_fd_combine<double, T><<<vec_grid(n), kBlock, 0, st>>>(m.N, m.vol, s.dt, dx, s.Rp, s.R, s.hs + kHsNormQ + 3, rhs, k.t);
+      HGKS_PROF_END(K_SPMV, st);
+    } else {
+      HGKS_PROF_BEGIN(K_SPMV, st);
+      k_apply<T, double, T, kSpmv, false><<<cg, kCellBlock, 0, st>>>(m, k.off, k.dval, k.dinv, rhs, dx, k.t, nullptr,
+                                                                      nullptr, nullptr, nullptr);
+      HGKS_PROF_END(K_SPMV, st);
+    }
     precondition_t<T>(m, s, k, p.jacobi_sweeps, k.t, k.w, nullptr, nullptr, st);
     HGKS_PROF_BEGIN(K_DOT, st);
     k_axpy_dot<T><<<kRedBlocks, kBlock, 0, st>>>(n, k.w, nullptr, nullptr, k.w, 1, k.red, s.red_count, beta);
@@ -385,10 +442,14 @@ void gmres_t(const DevMesh &m, Scratch &s, const KBuf<T> &k, const hgks_params &
     HGKS_PROF_END(K_SCALE, st);
     for (int j = 0; j < mk; j++) {
       // w = P^{-1} A v_j, with h_0j = (w, v_0) from the last sweep
-      HGKS_PROF_BEGIN(K_SPMV, st);
-      k_apply<T, T, T, kSpmv, false><<<cg, kCellBlock, 0, st>>>(m, k.off, k.dval, k.dinv, nullptr, k.V + (size_t)j * vs, k.t,
-                                                                 nullptr, nullptr, nullptr, nullptr);
-      HGKS_PROF_END(K_SPMV, st);
+      if (fd) {
+        fd_apply<T, T>(m, s, p, Q, G, k.V + (size_t)j * vs, nullptr, k.t, st);
+      } else {
+        HGKS_PROF_BEGIN(K_SPMV, st);
+        k_apply<T, T, T, kSpmv, false><<<cg, kCellBlock, 0, st>>>(m, k.off, k.dval, k.dinv, nullptr, k.V + (size_t)j * vs,
+                                                                   k.t, nullptr, nullptr, nullptr, nullptr);
+        HGKS_PROF_END(K_SPMV, st);
+      }
       precondition_t<T>(m, s, k, p.jacobi_sweeps, k.t, k.w, k.V, H + j, st);
       // modified Gram-Schmidt: w -= h_ij v_i, then h_{i+1,j} = (w, v_{i+1}) or ||w||
       for (int i = 0; i <= j; i++) {
@@ -453,6 +514,18 @@ void launch_precondition(const DevMesh &m, Scratch &s, int sweeps, const double 
   precondition_t<double>(m, s, kbuf64(s), sweeps, b, x, nullptr, nullptr, st);
 }
 
+void launch_norm(const DevMesh &m, Scratch &s, const double *x, double *out_dev, cudaStream_t st) {
+  HGKS_PROF_BEGIN(K_DOT, st);
+  k_axpy_dot<double><<<kRedBlocks, kBlock, 0, st>>>(5 * (int64_t)m.N, const_cast<double *>(x), nullptr, nullptr, x, 1,
+                                                     s.red, s.red_count, out_dev);
+  HGKS_PROF_END(K_DOT, st);
+}
+
+void launch_apply_fd(const DevMesh &m, Scratch &s, const hgks_params &p, const double *Q, const double *G,
+                     const double *x, const double *b, double *y, cudaStream_t st) {
+  fd_apply<double, double>(m, s, p, Q, G, x, b, y, st);
+}
+
 void launch_density_l1(const DevMesh &m, Scratch &s, const double *R, double *out_dev, cudaStream_t st) {
   HGKS_PROF_BEGIN(K_NORM, st);
   k_density_l1<<<kRedBlocks, kBlock, 0, st>>>(m.N, R, m.inv_vol, s.red, s.red_count, out_dev);
@@ -468,10 +541,15 @@ void launch_update(const DevMesh &m, double *Q, const double *dQ, double *G, con
 
 // hs layout: H[(m+1) m] | beta | y[m] | lin residual estimates
 hgks_status gmres_solve(const DevMesh &m, Scratch &s, const hgks_params &p, const double *rhs, double *dx,
-                        hgks_step_info *info, cudaStream_t st) {
+                        hgks_step_info *info, cudaStream_t st, const double *Q, const double *G) {
   cudaMemsetAsync(dx, 0, sizeof(double) * 5 * (size_t)m.N, st);
-  if (p.precision == HGKS_MIXED) gmres_t<float>(m, s, kbuf32(s), p, rhs, dx, st);
-  else gmres_t<double>(m, s, kbuf64(s), p, rhs, dx, st);
+  if (p.jv_mode == 1) {
+    if (!Q || !s.Qp) return HGKS_ERR_ARG;
+    cudaMemsetAsync(s.hs + kHsNormQ + 3, 0, sizeof(double), st);
+    launch_norm(m, s, Q, s.hs + kHsNormQ, st);
+  }
+  if (p.precision == HGKS_MIXED) gmres_t<float>(m, s, kbuf32(s), p, rhs, dx, st, Q, G);
+  else gmres_t<double>(m, s, kbuf64(s), p, rhs, dx, st, Q, G);
   if (info) info->krylov_iters = p.restarts * p.krylov_dim;
   return HGKS_OK;
 }

@@ -765,9 +765,9 @@ void launch_local_dt(const DevMesh &m, const hgks_params &p, const double *Q, do
 }
 
 void launch_residual(const DevMesh &m, Scratch &s, const hgks_params &p, const double *Q, const double *G, double *R,
-                     double *Gnew, cudaStream_t st, bool batch) {
+                     double *Gnew, cudaStream_t st, bool batch, bool fresh_dt) {
   batch = batch || m.ptab != nullptr;
-  launch_local_dt(m, p, Q, s.dt, st);
+  if (fresh_dt) launch_local_dt(m, p, Q, s.dt, st);
   HGKS_PROF_BEGIN(K_COEF, st);
   const int64_t NL = batch ? m.NL : m.N, FL = batch ? m.FL : m.F;
   const unsigned gc = grid_for(5 * NL, kBlock);
@@ -790,8 +790,9 @@ void launch_residual(const DevMesh &m, Scratch &s, const hgks_params &p, const d
     k_flux<false><<<grid_for(3 * (int64_t)m.F, s.blk_flux), s.blk_flux, 0, st>>>(m, p, Q, s.dt, s.wface, s.fflux, s.fpt, s.flags);
   HGKS_PROF_END(K_FLUX, st);
   HGKS_PROF_BEGIN(K_GATHER, st);
-  if (batch) k_gather<true><<<grid_for(NL, kBlock), kBlock, 0, st>>>(m, p.scheme == HGKS_HWENO, s.fflux, s.fpt, R, Gnew);
-  else k_gather<false><<<grid_for(m.N, kBlock), kBlock, 0, st>>>(m, p.scheme == HGKS_HWENO, s.fflux, s.fpt, R, Gnew);
+  const int grad = p.scheme == HGKS_HWENO && Gnew != nullptr;   // gradients wanted
+  if (batch) k_gather<true><<<grid_for(NL, kBlock), kBlock, 0, st>>>(m, grad, s.fflux, s.fpt, R, Gnew);
+  else k_gather<false><<<grid_for(m.N, kBlock), kBlock, 0, st>>>(m, grad, s.fflux, s.fpt, R, Gnew);
   HGKS_PROF_END(K_GATHER, st);
 }
 
