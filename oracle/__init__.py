@@ -79,7 +79,7 @@ def lib():
         L.orc_mesh_create.argtypes = [dp, i64, C.POINTER(C.c_int64), i64, C.POINTER(C.c_int64),
                                       C.POINTER(C.c_int32), i64, dp, i32, C.c_char_p, C.c_int]
         L.orc_mesh_destroy.argtypes = [vp]
-        for name in ["orc_residual", "orc_residual_dt", "orc_apply_fd", "orc_local_dt", "orc_jacobian",
+        for name in ["orc_residual", "orc_residual_dt", "orc_apply_fd", "orc_wall_force", "orc_local_dt", "orc_jacobian",
                      "orc_precondition", "orc_gmres",
                      "orc_gmres_step", "orc_solve_steady", "orc_recon_side", "orc_fit_cell", "orc_slope",
                      "orc_lu_solve", "orc_inverse"]:
@@ -212,6 +212,17 @@ class OracleMesh:
         if rc:
             raise RuntimeError(f"orc_residual_dt failed ({rc})")
         return R
+
+    def wall_force(self, params, Q, G, tag):
+        """Force [3] of the flow on the boundary faces with the given tag."""
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        Ga = np.ascontiguousarray(G, dtype=np.float64) if G is not None else None
+        f = np.zeros(3)
+        rc = lib().orc_wall_force(C.c_void_p(self.h), C.byref(params), _p(Q), _p(Ga) if Ga is not None else None,
+                                  int(tag), _p(f))
+        if rc:
+            raise RuntimeError("orc_wall_force failed")
+        return f
 
     def apply_fd(self, params, Q, G, dt, x):
         """(y, sigma): y = |Omega|/dt x - (L(Q + sigma x) - L(Q)) / sigma, Eq. (frechet)."""

@@ -113,6 +113,8 @@ int orc_residual(orc_mesh *m, const orc_params *p, const double *Q, const double
 /* the same with the local time step given (dt_in) instead of computed from Q */
 int orc_residual_dt(orc_mesh *m, const orc_params *p, const double *Q, const double *G, const double *dt_in,
                     double *R, double *Gnew, const int64_t *cells, int64_t ncells);
+/* force[3] of the flow on the boundary faces with tag `tag` (face fluxes x area) */
+int orc_wall_force(orc_mesh *m, const orc_params *p, const double *Q, const double *G, int tag, double *force);
 /* y = A x without A: |Omega|/dt x - (L(Q + sigma x) - L(Q)) / sigma (Eq. (frechet)) */
 int orc_apply_fd(orc_mesh *m, const orc_params *p, const double *Q, const double *G, const double *dt,
                  const double *LQ, const double *x, double *y, double *sigma_out);

@@ -45,8 +45,32 @@ int orc_residual(orc_mesh *m, const orc_params *p, const double *Q, const double
   return orc_residual_dt(m, p, Q, G, NULL, R, Gnew, cells, ncells);
 }
 
+static int residual_core(orc_mesh *m, const orc_params *p, const double *Q, const double *G, const double *dt_in,
+                         double *R, double *Gnew, const int64_t *cells, int64_t ncells, double *Fface);
+
 int orc_residual_dt(orc_mesh *m, const orc_params *p, const double *Q, const double *G, const double *dt_in,
                     double *R, double *Gnew, const int64_t *cells, int64_t ncells) {
+  return residual_core(m, p, Q, G, dt_in, R, Gnew, cells, ncells, NULL);
+}
+
+/* Force of the flow on the boundary faces tagged `tag`: the sum over those faces
+ * of the momentum part of the face flux of Eq. (flux) times the face area (the
+ * flux leaving the fluid through the wall: pressure and viscous stress on it). */
+int orc_wall_force(orc_mesh *m, const orc_params *p, const double *Q, const double *G, int tag, double *force) {
+  const int64_t nc = m->nc, nf = m->nf;
+  double *R = (double *)malloc(sizeof(double) * 5 * (nc + 1)), *Ff = (double *)calloc(5 * (nf + 1), sizeof(double));
+  int rc = residual_core(m, p, Q, G, NULL, R, NULL, NULL, 0, Ff);
+  force[0] = force[1] = force[2] = 0.0;
+  if (!rc)
+    for (int64_t f = 0; f < nf; f++)
+      if (m->fr[f] < 0 && m->ftag[f] == tag)
+        for (int d = 0; d < 3; d++) force[d] += Ff[5 * f + 1 + d];
+  free(R); free(Ff);
+  return rc;
+}
+
+static int residual_core(orc_mesh *m, const orc_params *p, const double *Q, const double *G, const double *dt_in,
+                         double *R, double *Gnew, const int64_t *cells, int64_t ncells, double *Fface) {
   const int64_t nc = m->nc, nf = m->nf;
   char *fsel = (char *)calloc(nf + 1, 1), *csel = (char *)calloc(nc + 1, 1);
   if (cells) {
@@ -102,6 +126,7 @@ int orc_residual_dt(orc_mesh *m, const orc_params *p, const double *Q, const dou
     }
   }
   if (Gnew) for (int64_t i = 0; i < nc; i++) for (int c = 0; c < 15; c++) Gnew[15 * i + c] /= m->vol[i];
+  if (Fface) memcpy(Fface, Ff, sizeof(double) * 5 * nf);
   free(fsel); free(csel); free(dt); free(Ff); free(Pf);
   return 0;
 }
