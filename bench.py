@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -301,6 +302,91 @@ def run_batch(args, rank, world):
     return 0
 
 
+def run_precision(args, rank, world):
+    """The precision workload: viscous flow past a sphere (Re 118, Ma 0.2535,
+    6 x 24 x 24 patches, 48 layers stretched so that the first is 3e-2 thick,
+    ~995k tets, adiabatic no-slip wall), compact HWENO, CFL 20. The same steps
+    in FP64 and with the FP32 Krylov part, from the free stream: drag
+    coefficient and state difference after every few steps, time per step.
+    On a scaled-down sphere of the same construction (6 x 8 x 8, 16 layers)
+    the oracle gives the reference for both."""
+    import torch
+    import oracle as O
+    import paper_2304_09485_gb300 as H
+    from paper_2304_09485_gb300 import inputs as I
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    cond = I.sphere_conditions(0.2535, Re=118.0)
+    kw = dict(scheme=1, Pr=0.72, cfl=20.0, krylov_dim=10, restarts=3, jacobi_sweeps=2)
+    qinf = 0.5 * cond["rho_inf"] * cond["u_inf"][0] ** 2 * math.pi * 0.25
+
+    def cd(hm, p, Q, G):
+        return float(H.hgks_wall_force(hm, p, Q, G, I.BC_NOSLIP_ADIA)[0] / qinf)
+
+    out = {}
+    # the full-size case on the GPU: FP64 against mixed
+    m = I.sphere_mesh(24, 48, stretch=I.sphere_stretch(48, dr1=3e-2), wall_tag=I.BC_NOSLIP_ADIA)
+    hm = H.hgks_mesh_create(m, scheme_mask=2, device=local)
+    traj = {}
+    for prec in (0, 1):
+        p = H.hgks_default_params(precision=prec, **cond, **kw)
+        Q = hm.to_internal(I.state_from_conditions(m.n_tet, cond), device=f"cuda:{local}")
+        G = torch.zeros((15, m.n_tet), dtype=torch.float64, device=f"cuda:{local}")
+        cds, ms = [], 0.0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for k in range(args.steps):
+            e0.record()
+            H.hgks_gmres_step(hm, p, Q, G)
+            e1.record()
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            if (k + 1) % max(1, args.steps // 5) == 0:
+                cds.append(cd(hm, p, Q, G))
+        traj[prec] = (Q, G, cds, ms / args.steps)
+    (Q64, G64, cd64, ms64), (Q32, G32, cd32, ms32) = traj[0], traj[1]
+    out["full"] = {"n_cells": m.n_tet, "steps": args.steps, "cd_fp64": cd64, "cd_mixed": cd32,
+                   "cd_rel_diff": abs(cd32[-1] - cd64[-1]) / abs(cd64[-1]),
+                   "state_rel_l2": float(torch.linalg.norm(Q32 - Q64) / torch.linalg.norm(Q64)),
+                   "ms_per_step_fp64": ms64, "ms_per_step_mixed": ms32,
+                   "mcells_per_s_fp64": m.n_tet / ms64 / 1e3, "mcells_per_s_mixed": m.n_tet / ms32 / 1e3}
+    del traj, Q64, G64, Q32, G32, hm
+    # the scaled-down case against the oracle
+    ms_ = I.sphere_mesh(8, 16, stretch=I.sphere_stretch(16, dr1=3e-2 * 3), wall_tag=I.BC_NOSLIP_ADIA)
+    om = O.OracleMesh(ms_)
+    hs = H.hgks_mesh_create(ms_, scheme_mask=2, device=local)
+    po = O.make_params(**cond, **{k: v for k, v in kw.items()})
+    Qo = I.state_from_conditions(ms_.n_tet, cond)
+    Go = np.zeros((ms_.n_tet, 15))
+    small = {"n_cells": ms_.n_tet, "steps": args.oracle_steps}
+    res = {}
+    for prec in (0, 1):
+        p = H.hgks_default_params(precision=prec, **cond, **kw)
+        Q = hs.to_internal(Qo, device=f"cuda:{local}")
+        G = hs.to_internal(Go, device=f"cuda:{local}")
+        for _ in range(args.oracle_steps):
+            H.hgks_gmres_step(hs, p, Q, G)
+        res[prec] = (hs.to_caller(Q), cd(hs, p, Q, G))
+    Qr, Gr = Qo.copy(), Go.copy()
+    for _ in range(args.oracle_steps):
+        Qr, Gr, _, _ = om.gmres_step(po, Qr, Gr)
+    cdo = float(om.wall_force(po, Qr, Gr, I.BC_NOSLIP_ADIA)[0] / qinf)
+    for prec, name in ((0, "fp64"), (1, "mixed")):
+        Qg, cdg = res[prec]
+        small[name] = {"cd": cdg, "cd_rel_err_vs_oracle": abs(cdg - cdo) / abs(cdo),
+                       "state_rel_l2_vs_oracle": float(np.linalg.norm(Qg - Qr) / np.linalg.norm(Qr))}
+    small["cd_oracle"] = cdo
+    out["small_vs_oracle"] = small
+    if rank != 0:
+        return 0
+    res_line = {"metric": "precision: drag coefficient and state error, FP32 Krylov vs FP64", "value": out["full"]["cd_rel_diff"],
+                "unit": "relative C_D difference", "n_gpus": world, "steps": args.steps, "warmup": 0,
+                "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+                "config": {"workload": "viscous sphere Re 118, Ma 0.2535, 6x24x24x48 (first layer 3e-2), HWENO, CFL 20, "
+                                       "GMRES(10)x3, Jacobi 2, from the free stream"}, **out}
+    print(json.dumps(res_line))
+    return 0
+
+
 def run_serve(args, rank, world):
     """Steady-solve requests with Poisson arrivals served by the continuous-
     batching server (mixed precision) against the same requests solved one
@@ -406,9 +492,10 @@ def main():
     ap.add_argument("--impl", default="hgks", choices=["hgks", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="scaled-down mesh (profiling runs)")
-    ap.add_argument("--workload", default="sphere", choices=["sphere", "batch", "serve"],
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "batch", "serve", "precision"],
                     help="sphere: the 2.36M-tet sphere (default); batch: many problems in one batch; "
                          "serve: Poisson-arriving solves through the request server")
+    ap.add_argument("--oracle-steps", type=int, default=3, help="precision workload: oracle steps on the small sphere")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=0.5, help="requests per second")
     ap.add_argument("--serve-drop", type=float, default=1e-3)
@@ -428,6 +515,8 @@ def main():
         return run_batch(args, rank, world)
     if args.workload == "serve":
         return run_serve(args, rank, world)
+    if args.workload == "precision":
+        return run_precision(args, rank, world)
 
     import torch
     import torch.distributed as dist

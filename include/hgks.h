@@ -174,6 +174,13 @@ hgks_status hgks_apply_jacobian(hgks_mesh mesh, const double *x, double *y, void
  * arrays device, internal order, [5][N] (dt [N]). Uses the handle's scratch. */
 hgks_status hgks_apply_jacobian_fd(hgks_mesh mesh, const hgks_params *p, const double *Q, const double *G,
                                    const double *dt, const double *x, double *y, void *cuda_stream);
+/* Force of the flow on the boundary faces tagged `tag` (HGKS_BC_*): the sum over
+ * those faces of the momentum part of the face flux of Eq. (flux) times the face
+ * area, i.e. pressure and viscous stress on the wall, in the global frame, into
+ * force_host[3] (host). Evaluates R(Q) on the way (the handle's scratch);
+ * synchronises the stream. Drag coefficient of a body: force . e_U / (rho U^2 A / 2). */
+hgks_status hgks_wall_force(hgks_mesh mesh, const hgks_params *p, const double *Q, const double *G, int32_t tag,
+                            double *force_host, void *cuda_stream);
 /* x = P^{-1} b, Jacobi iteration of Eq. (precond) with `sweeps` sweeps. */
 hgks_status hgks_precondition(hgks_mesh mesh, int32_t sweeps, const double *b, double *x,
                               void *cuda_stream);

@@ -87,6 +87,7 @@ def lib():
             "hgks_assemble": [vp, P, dp, dp, dp, dp, vp],
             "hgks_apply_jacobian": [vp, dp, dp, vp],
             "hgks_apply_jacobian_fd": [vp, P, dp, dp, dp, dp, dp, vp],
+            "hgks_wall_force": [vp, P, dp, dp, i32, dp, vp],
             "hgks_precondition": [vp, i32, dp, dp, vp],
             "hgks_gmres_step": [vp, P, dp, dp, dp, C.POINTER(hgks_step_info), vp],
             "hgks_solve_steady": [vp, P, dp, dp, C.c_double, i32, dp, C.POINTER(hgks_solve_info), vp],
@@ -244,6 +245,12 @@ def hgks_apply_jacobian(mesh, x, y, stream=None):
 def hgks_apply_jacobian_fd(mesh, params, Q, G, dt, x, y, stream=None):
     _check(lib().hgks_apply_jacobian_fd(mesh.handle, C.byref(params), _ptr(Q), _ptr(G), _ptr(dt), _ptr(x), _ptr(y),
                                         _stream(stream)))
+
+
+def hgks_wall_force(mesh, params, Q, G, tag, stream=None) -> np.ndarray:
+    f = np.zeros(3)
+    _check(lib().hgks_wall_force(mesh.handle, C.byref(params), _ptr(Q), _ptr(G), tag, _ptr(f), _stream(stream)))
+    return f
 
 
 def hgks_precondition(mesh, sweeps, b, x, stream=None):

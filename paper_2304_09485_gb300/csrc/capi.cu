@@ -378,6 +378,23 @@ hgks_status hgks_apply_jacobian_fd(hgks_mesh mesh, const hgks_params *p, const d
   return last_launch();
 }
 
+hgks_status hgks_wall_force(hgks_mesh mesh, const hgks_params *p, const double *Q, const double *G, int32_t tag,
+                            double *force_host, void *cuda_stream) {
+  if (!mesh) return fail(HGKS_ERR_ARG, "mesh is NULL");
+  Mesh &m = mesh->m;
+  hgks_status st = check_params(m, p);
+  if (st) return st;
+  if (!Q || !force_host || (p->scheme == HGKS_HWENO && !G)) return fail(HGKS_ERR_ARG, "NULL argument");
+  if ((st = set_device(m)) || (st = ensure_scratch(m, p->krylov_dim, true, p->precision == HGKS_MIXED))) return st;
+  cudaStream_t s_ = (cudaStream_t)cuda_stream;
+  launch_residual(m.d, m.s, *p, Q, G, m.s.R, nullptr, s_);
+  double *fdev = m.s.hs + kHsNormQ + 4;
+  launch_wall_force(m.d, m.s, tag, fdev, s_);
+  HGKS_CUDA(cudaMemcpyAsync(force_host, fdev, 3 * sizeof(double), cudaMemcpyDeviceToHost, s_));
+  HGKS_CUDA(cudaStreamSynchronize(s_));
+  return last_launch();
+}
+
 hgks_status hgks_precondition(hgks_mesh mesh, int32_t sweeps, const double *b, double *x, void *cuda_stream) {
   if (!mesh || !b || !x) return fail(HGKS_ERR_ARG, "NULL argument");
   if (b == x) return fail(HGKS_ERR_ARG, "b and x must not alias");

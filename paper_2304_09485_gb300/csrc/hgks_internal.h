@@ -156,6 +156,8 @@ hgks_status gmres_solve(const DevMesh &m, Scratch &s, const hgks_params &p, cons
 void launch_apply_fd(const DevMesh &m, Scratch &s, const hgks_params &p, const double *Q, const double *G,
                      const double *x, const double *b, double *y, cudaStream_t st);
 void launch_norm(const DevMesh &m, Scratch &s, const double *x, double *out_dev, cudaStream_t st);
+// force[3] on the boundary faces tagged `tag`, from the face fluxes of the last residual
+void launch_wall_force(const DevMesh &m, const Scratch &s, int tag, double *force_dev, cudaStream_t st);
 constexpr int kHsNormQ = 65 * 64 + 210;   // hs slots of the matrix-free products: ||Q||, ||x||, sigma, 0
 void launch_density_l1(const DevMesh &m, Scratch &s, const double *R, double *out_dev, cudaStream_t st);
 void launch_update(const DevMesh &m, double *Q, const double *dQ, double *G, const double *Gnew, int ncomp_g,

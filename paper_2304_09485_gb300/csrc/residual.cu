@@ -757,6 +757,40 @@ __global__ void k_local_dt(DevMesh m, hgks_params Pv, const double *__restrict__
 
 }  // namespace
 
+// force[3] = sum over the faces tagged `tag` of the momentum part of fflux ([3][5][F],
+// global frame, area included); one block, fixed summation order
+__global__ void __launch_bounds__(1024) k_wall_force(DevMesh m, int tag, const double *__restrict__ fflux,
+                                                     double *__restrict__ force) {
+  __shared__ double sh[3][1024];
+  const int F = m.F;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int f = threadIdx.x; f < F; f += blockDim.x) {
+    if (m.fr[f] >= 0 || m.ftag[f] != tag) continue;
+#pragma unroll
+    for (int g = 0; g < 3; g++)
+#pragma unroll
+      for (int d = 0; d < 3; d++) acc[d] += fflux[(size_t)(5 * g + 1 + d) * F + f];
+  }
+#pragma unroll
+  for (int d = 0; d < 3; d++) sh[d][threadIdx.x] = acc[d];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+#pragma unroll
+      for (int d = 0; d < 3; d++) sh[d][threadIdx.x] += sh[d][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int d = 0; d < 3; d++) force[d] = sh[d][0];
+}
+
+void launch_wall_force(const DevMesh &m, const Scratch &s, int tag, double *force_dev, cudaStream_t st) {
+  HGKS_PROF_BEGIN(K_NORM, st);
+  k_wall_force<<<1, 1024, 0, st>>>(m, tag, s.fflux, force_dev);
+  HGKS_PROF_END(K_NORM, st);
+}
+
 void launch_local_dt(const DevMesh &m, const hgks_params &p, const double *Q, double *dt, cudaStream_t st) {
   HGKS_PROF_BEGIN(K_DT, st);
   if (m.ptab) k_local_dt<true><<<grid_for(m.NL, kBlock), kBlock, 0, st>>>(m, p, Q, dt);
