@@ -38,7 +38,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_PEAK_GFLOPS = 1258.6
 # FP64 flops per unit of work of each kernel (2 per DFMA, 1 per DADD/DMUL), from the
 # ncu sass counters of the kernels on the 124,416-tet sphere (non-compact scheme,
-# inviscid, Pr = 1); see DESIGN.md "Roofline". unit -> (flops per unit, units)
+# inviscid, Pr = 1), from ncu SASS instruction counters. unit -> (flops per unit, units)
 # DRAM bytes per unit of work from the same ncu captures (dram__bytes_read.sum +
 # dram__bytes_write.sum divided by the units of the 124,416-tet launch); the
 # traffic of a full launch is this times its units (traffic grows with the units).
@@ -241,6 +241,15 @@ def run_batch(args, rank, world):
         H.hgks_batch_gmres_step(b)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
+    if args.launch_list:                  # one batched step after the warm-up (ncu launch lists)
+        H.hgks_launch_count(reset=True)
+        H.hgks_profile_begin()
+        H.hgks_batch_gmres_step(b)
+        prof = H.hgks_profile_end()
+        if rank == 0:
+            print(json.dumps({"launch_list": True, "gpu_launches": H.hgks_launch_count(), "n_cells": n_cells,
+                              "kernels_ms": {k: round(v[0], 3) for k, v in prof.items()}}))
+        return 0
     clocks = ClockSampler(local)
     clocks.start()
     # (a) batched steps replayed from the captured graph (tiny drop: every mesh keeps

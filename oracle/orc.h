@@ -11,7 +11,7 @@
  * (impEuler), (impsystem), (A-system-1/2), (deri-matrix), (precond), the
  * algorithm "preconditioned GMRES" (Algorithm 1), and Sec. 5's collision time
  * and characteristic-variable reconstruction. Where the paper is silent the
- * oracle takes the readings listed in DESIGN.md ("Readings of the paper").
+ * oracle takes the same readings as the library, each stated where it is used.
  *
  * Data layout is the natural one for a reader: cell arrays are [cell][5] in the
  * caller's cell order, gradients [cell][5][3] (component, then direction).
