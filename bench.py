@@ -444,7 +444,8 @@ def run_serve(args, rank, world):
     for k, rid in ids.items():
         st = srv.status(rid)
         served.append(dict(ttc=st.t_done - st.t_submit, steps=st.solve.steps, converged=bool(st.solve.converged),
-                           admit_wait=st.t_admit - st.t_built, done=st.t_done, submit=st.t_submit))
+                           failed=st.status == H.HGKS_ERR_NONPHYSICAL, admit_wait=st.t_admit - st.t_built,
+                           done=st.t_done, submit=st.t_submit))
         srv.collect(rid)
     info = srv.info()
     del srv
@@ -455,14 +456,21 @@ def run_serve(args, rank, world):
         t1 = time.perf_counter()
         hm = H.hgks_mesh_create(r["mesh"], scheme_mask=1, device=local)
         Q = hm.to_internal(r["Q0"], device=f"cuda:{local}")
-        si, hist, conv = H.hgks_solve_steady(hm, H.hgks_default_params(**r["p"]), Q, None, drop_tol=drop,
-                                             max_steps=max_steps)
+        failed = False
+        try:
+            si, hist, conv = H.hgks_solve_steady(hm, H.hgks_default_params(**r["p"]), Q, None, drop_tol=drop,
+                                                 max_steps=max_steps)
+            steps = si.steps
+        except H.HGKSError as e:
+            if e.status != H.HGKS_ERR_NONPHYSICAL:
+                raise
+            failed, conv, steps = True, False, -1
         torch.cuda.synchronize()
         dur = time.perf_counter() - t1
         del hm, Q
         start = max(r["arrival"], end)
         end = start + dur
-        seq.append(dict(ttc=end - r["arrival"], steps=si.steps, converged=bool(conv), service=dur))
+        seq.append(dict(ttc=end - r["arrival"], steps=steps, converged=bool(conv), failed=failed, service=dur))
     span_b = end - reqs[0]["arrival"]
     if rank != 0:
         return 0
@@ -479,14 +487,18 @@ def run_serve(args, rank, world):
                       "arena_gb": info.device_bytes / 1e9},
            "served_mixed": {"solves_per_hour": 3600.0 * len(served) / span_a, "p50_ttc_s": pct([s["ttc"] for s in served], 50),
                             "p99_ttc_s": pct([s["ttc"] for s in served], 99), "converged": len(conv_a),
-                            "hit_max_steps": len(served) - len(conv_a), "p50_ttc_converged_s": pct(conv_a, 50),
+                            "failed_nonfinite": sum(s["failed"] for s in served),
+                            "hit_max_steps": len(served) - len(conv_a) - sum(s["failed"] for s in served),
+                            "p50_ttc_converged_s": pct(conv_a, 50),
                             "p99_ttc_converged_s": pct(conv_a, 99), "rounds": rounds, "span_s": span_a,
                             "mean_steps": float(np.mean([s["steps"] for s in served]))},
            "sequential_fp64": {"solves_per_hour": 3600.0 * len(seq) / span_b, "p50_ttc_s": pct([s["ttc"] for s in seq], 50),
                                "p99_ttc_s": pct([s["ttc"] for s in seq], 99), "converged": len(conv_b),
-                               "hit_max_steps": len(seq) - len(conv_b), "p50_ttc_converged_s": pct(conv_b, 50),
+                               "failed_nonfinite": sum(s["failed"] for s in seq),
+                               "hit_max_steps": len(seq) - len(conv_b) - sum(s["failed"] for s in seq),
+                               "p50_ttc_converged_s": pct(conv_b, 50),
                                "p99_ttc_converged_s": pct(conv_b, 99), "span_s": span_b,
-                               "mean_steps": float(np.mean([s["steps"] for s in seq])),
+                               "mean_steps": float(np.mean([s["steps"] for s in seq if s["steps"] >= 0])),
                                "mean_service_s": float(np.mean([s["service"] for s in seq]))},
            "clocks": clk}
     print(json.dumps(res))
@@ -507,8 +519,8 @@ def main():
     ap.add_argument("--oracle-steps", type=int, default=3, help="precision workload: oracle steps on the small sphere")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=0.5, help="requests per second")
-    ap.add_argument("--serve-drop", type=float, default=1e-3)
-    ap.add_argument("--serve-max-steps", type=int, default=400)
+    ap.add_argument("--serve-drop", type=float, default=1e-2)
+    ap.add_argument("--serve-max-steps", type=int, default=500)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--batch-meshes", type=int, default=48)
     ap.add_argument("--batch-scheme", default="hweno", choices=["weno", "hweno"])

@@ -18,6 +18,7 @@ import numpy as np
 from . import _native
 
 HGKS_OK = 0
+HGKS_ERR_NONPHYSICAL = 5
 HGKS_ERR_NOT_CONVERGED = 7
 HGKS_WENO, HGKS_HWENO = 0, 1
 HGKS_NONLINEAR, HGKS_LINEAR = 0, 1

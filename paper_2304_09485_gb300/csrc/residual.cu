@@ -30,15 +30,17 @@ namespace {
 
 constexpr int kBlock = 128;
 
-struct Prim { double rho, U, V, W, lam; };
+// primitive state of a Maxwellian: lam = rho / (2 p), il = 1 / (2 lam) = p / rho, ir = 1 / rho
+struct Prim { double rho, U, V, W, lam, il, ir; };
 
 __device__ __forceinline__ Prim to_prim(const double *Q, double gamma) {
   Prim p;
   p.rho = Q[0];
-  double ir = 1.0 / Q[0];
-  p.U = Q[1] * ir; p.V = Q[2] * ir; p.W = Q[3] * ir;
-  double pr = (gamma - 1.0) * (Q[4] - 0.5 * Q[0] * (p.U * p.U + p.V * p.V + p.W * p.W));
-  p.lam = 0.5 * Q[0] / pr;
+  p.ir = 1.0 / Q[0];
+  p.U = Q[1] * p.ir; p.V = Q[2] * p.ir; p.W = Q[3] * p.ir;
+  const double pr = (gamma - 1.0) * (Q[4] - 0.5 * Q[0] * (p.U * p.U + p.V * p.V + p.W * p.W));
+  p.il = pr * p.ir;
+  p.lam = 0.5 / p.il;
   return p;
 }
 
@@ -316,7 +318,7 @@ __global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const 
 struct Mom { double u[7], v[6], w[6], xi2, xi4; };
 
 __device__ __forceinline__ void mom_vw(const Prim &p, double K, Mom &m) {
-  const double il = 0.5 / p.lam;   // 1/(2 lambda)
+  const double il = p.il;   // 1/(2 lambda)
   m.v[0] = 1.0; m.v[1] = p.V; m.w[0] = 1.0; m.w[1] = p.W;
 #pragma unroll
   for (int n = 0; n < 4; n++) {
@@ -327,16 +329,16 @@ __device__ __forceinline__ void mom_vw(const Prim &p, double K, Mom &m) {
   m.xi4 = (K * K + 2.0 * K) * il * il;
 }
 __device__ __forceinline__ void mom_u_full(const Prim &p, double *u) {
-  const double il = 0.5 / p.lam;
+  const double il = p.il;
   u[0] = 1.0; u[1] = p.U;
 #pragma unroll
   for (int n = 0; n < 5; n++) u[n + 2] = p.U * u[n + 1] + (n + 1) * il * u[n];
 }
 // sgn = +1: u > 0, sgn = -1: u < 0
 __device__ __forceinline__ void mom_u_half(const Prim &p, double sgn, double *u) {
-  const double il = 0.5 / p.lam, sl = sqrt(p.lam);
+  const double il = p.il, rs = rsqrt(p.lam), sl = p.lam * rs;
   u[0] = 0.5 * erfc(-sgn * sl * p.U);
-  u[1] = p.U * u[0] + sgn * 0.5 * exp(-p.lam * p.U * p.U) / (sl * 1.7724538509055160273);   // sqrt(pi)
+  u[1] = p.U * u[0] + sgn * 0.5 * exp(-p.lam * p.U * p.U) * rs * 0.56418958354775628695;   // 1/sqrt(pi)
 #pragma unroll
   for (int n = 0; n < 5; n++) u[n + 2] = p.U * u[n + 1] + (n + 1) * il * u[n];
 }
@@ -391,12 +393,13 @@ __device__ __forceinline__ void acc_u_slope_u(const double *mu, const Mom &m, co
   acc_apsi<1, 0, 1>(mu, m, a[2], s, out);
 }
 
-// Slope a with <a> = rho * dq in closed form (dq normalised by rho)
-__device__ __forceinline__ void slope(const Prim &p, double K, const double *dq, double *a) {
-  const double q2 = p.U * p.U + p.V * p.V + p.W * p.W, e = (K + 3.0) / (4.0 * p.lam);
+// Slope a with <a> = rho * dq in closed form (dq normalised by rho); K + 3 = 2 / (gamma - 1),
+// so (K + 3) / (4 lam) = il / (gamma - 1) and 4 lam^2 / (K + 3) = 2 (gamma - 1) lam^2
+__device__ __forceinline__ void slope(const Prim &p, double g1, double ig1, const double *dq, double *a) {
+  const double q2 = p.U * p.U + p.V * p.V + p.W * p.W, e = p.il * ig1;
   const double R4 = 2.0 * dq[4] - (q2 + 2.0 * e) * dq[0];
   const double R1 = dq[1] - p.U * dq[0], R2 = dq[2] - p.V * dq[0], R3 = dq[3] - p.W * dq[0];
-  a[4] = 4.0 * p.lam * p.lam / (K + 3.0) * (R4 - 2.0 * p.U * R1 - 2.0 * p.V * R2 - 2.0 * p.W * R3);
+  a[4] = 2.0 * g1 * p.lam * p.lam * (R4 - 2.0 * p.U * R1 - 2.0 * p.V * R2 - 2.0 * p.W * R3);
   a[3] = 2.0 * p.lam * R3 - p.W * a[4];
   a[2] = 2.0 * p.lam * R2 - p.V * a[4];
   a[1] = 2.0 * p.lam * R1 - p.U * a[4];
@@ -464,8 +467,8 @@ __device__ void boundary_state(const hgks_params &P, int tag, const double *T, c
 // and applied to x. For the full-range moments of a Maxwellian,
 // <u_d (a_d . psi) psi> = J_d(W) dW/dx_d whenever <a_d> = dW/dx_d (a_d . psi g is the
 // derivative of g along dW), which replaces the moment sums of the time slopes.
-__device__ __forceinline__ void acc_jvp(const double *W, double gamma, int d, const double *x, double s, double *out) {
-  const double ir = 1.0 / W[0];
+__device__ __forceinline__ void acc_jvp(const double *W, double ir, double gamma, int d, const double *x, double s,
+                                        double *out) {
   const double u[3] = {W[1] * ir, W[2] * ir, W[3] * ir};
   const double q2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
   const double p = (gamma - 1.0) * (W[4] - 0.5 * W[0] * q2);
@@ -482,7 +485,7 @@ __device__ __forceinline__ void acc_jvp(const double *W, double gamma, int d, co
 // is not NULL, the point value int psi f dXi at t* (Eq. (point)). Face frame.
 __device__ void gks_flux(const hgks_params &P, const double *Wl, const double *dWl, const double *Wr, const double *dWr,
                          double dt, double *F, double *Qp) {
-  const double gam = P.gamma, K = (5.0 - 3.0 * gam) / (gam - 1.0);
+  const double gam = P.gamma, g1 = gam - 1.0, ig1 = 1.0 / g1, K = (5.0 - 3.0 * gam) * ig1;
   const Prim pl = to_prim(Wl, gam), pr = to_prim(Wr, gam);
   Mom ml, mr;
   mom_vw(pl, K, ml);
@@ -496,17 +499,18 @@ __device__ void gks_flux(const hgks_params &P, const double *Wl, const double *d
   acc_psi<0, 0, 0>(uhr, mr.v, mr.w, mr.xi2, pr.rho, Q0);
   const Prim p0 = to_prim(Q0, gam);
   // collision time (Sec. 5)
-  const double prl = 0.5 * pl.rho / pl.lam, prr = 0.5 * pr.rho / pr.lam, pp0 = 0.5 * p0.rho / p0.lam;
+  const double prl = pl.rho * pl.il, prr = pr.rho * pr.il, pp0 = p0.rho * p0.il;
   const double jump = fabs((prl - prr) / (prl + prr));
   const double tau = P.viscous ? P.mu / pp0 + P.tau_C * jump * dt : (P.tau_eps + P.tau_C * jump) * dt;
-  const double eta = exp(-dt / tau);
+  const double itau = 1.0 / tau;
+  const double eta = exp(-dt * itau);
   const double c1 = dt - tau * (1.0 - eta);
   const double c2 = 2.0 * tau * tau * (1.0 - eta) - tau * dt * (1.0 + eta);
   const double c3 = 0.5 * dt * dt - tau * dt + tau * tau * (1.0 - eta);
   const double c4 = tau * (1.0 - eta);
   const double c5 = 2.0 * tau * tau * (1.0 - eta) - tau * dt * eta;
   const bool want_pt = Qp != nullptr, prandtl = P.Pr != 1.0;
-  const double ts = P.tstar_end ? dt : 0.0, es = exp(-ts / tau);
+  const double ts = P.tstar_end ? dt : 0.0, es = exp(-ts * itau);
   double Fl[5] = {0, 0, 0, 0, 0}, Wb[5] = {0, 0, 0, 0, 0}, Pt[5] = {0, 0, 0, 0, 0};
   double dWs[15];
 #pragma unroll
@@ -518,21 +522,21 @@ __device__ void gks_flux(const hgks_params &P, const double *Wl, const double *d
     const Mom &mk = s == 0 ? ml : mr;
     const double *uh = s == 0 ? uhl : uhr;
     const double *dW = s == 0 ? dWl : dWr;
-    const double irho = 1.0 / pk.rho;
+    const double irho = pk.ir;
     double a[3][5], A[5];
 #pragma unroll
     for (int d = 0; d < 3; d++) {
       double dq[5];
 #pragma unroll
       for (int c = 0; c < 5; c++) dq[c] = dW[5 * d + c] * irho;
-      slope(pk, K, dq, a[d]);
+      slope(pk, g1, ig1, dq, a[d]);
     }
     // <a_n u + a_t1 v + a_t2 w + A> = 0 with <u_d (a_d.psi) psi> = J_d dW_d
     double rhs[5] = {0, 0, 0, 0, 0};
     const double *Wk = s == 0 ? Wl : Wr;
 #pragma unroll
-    for (int d = 0; d < 3; d++) acc_jvp(Wk, gam, d, dW + 5 * d, -irho, rhs);
-    slope(pk, K, rhs, A);
+    for (int d = 0; d < 3; d++) acc_jvp(Wk, irho, gam, d, dW + 5 * d, -irho, rhs);
+    slope(pk, g1, ig1, rhs, A);
     // flux terms of g_k
     double fk[5] = {0, 0, 0, 0, 0};
     acc_psi<1, 0, 0>(uh, mk.v, mk.w, mk.xi2, c4, fk);
@@ -558,23 +562,23 @@ __device__ void gks_flux(const hgks_params &P, const double *Wl, const double *d
     mom_vw(p0, K, m0);
     double uf[7];
     mom_u_full(p0, uf);
-    const double irho = 1.0 / p0.rho;
+    const double irho = p0.ir;
     double a[3][5];
 #pragma unroll
     for (int d = 0; d < 3; d++) {
       double dq[5];
 #pragma unroll
       for (int c = 0; c < 5; c++) dq[c] = dWs[5 * d + c] * irho;
-      slope(p0, K, dq, a[d]);
+      slope(p0, g1, ig1, dq, a[d]);
     }
     // S0 = <(abar . u_vec) psi> = sum_d J_d(Q0) dQ0_d; <Abar psi> = -S0; <u Abar psi> = -J_x(Q0) S0
     double S0[5] = {0, 0, 0, 0, 0};
 #pragma unroll
-    for (int d = 0; d < 3; d++) acc_jvp(Q0, gam, d, dWs + 5 * d, irho, S0);
+    for (int d = 0; d < 3; d++) acc_jvp(Q0, irho, gam, d, dWs + 5 * d, irho, S0);
     double f0[5] = {0, 0, 0, 0, 0};
     acc_psi<1, 0, 0>(uf, m0.v, m0.w, m0.xi2, c1, f0);
     acc_u_slope_u(uf, m0, a, c2, f0);
-    acc_jvp(Q0, gam, 0, S0, -c3, f0);
+    acc_jvp(Q0, irho, gam, 0, S0, -c3, f0);
 #pragma unroll
     for (int c = 0; c < 5; c++) Fl[c] = fma(p0.rho, f0[c], Fl[c]);
     if (want_pt || prandtl) {
