@@ -616,6 +616,9 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     mixed_ms = e0.elapsed_time(e1) / args.steps
+    H.hgks_profile_begin()
+    H.hgks_gmres_step(hm, pm, Qm)
+    mixed_prof = H.hgks_profile_end()
     del Qm
 
     # the same step with matrix-free products (Eq. (frechet)): one residual per Krylov vector
@@ -682,7 +685,8 @@ def main():
                    "l2": "inputs larger than L2 (mesh data + Jacobian + Krylov basis >> 129 MB)"},
         "residual_only": {"value": m.n_tet / (res_ms / 1000.0) / 1e6, "unit": "Mcells/s", "ms": res_ms},
         "mixed": {"value": world * m.n_tet / (mixed_ms / 1000.0) / 1e6, "unit": "Mcells/s", "ms_per_step": mixed_ms,
-                  "note": "same step with FP32 Krylov basis, Arnoldi and Jacobi (FP64 residual and update)"},
+                  "note": "same step with FP32 Krylov basis, Arnoldi and Jacobi (FP64 residual and update)",
+                  "kernels_ms_one_step": {k: round(v[0], 3) for k, v in sorted(mixed_prof.items(), key=lambda kv: -kv[1][0])}},
         "matrix_free": {"value": world * m.n_tet / (fd_ms / 1000.0) / 1e6, "unit": "Mcells/s", "ms_per_step": fd_ms,
                         "vs_assembled": ms / args.steps / fd_ms,
                         "note": "same step with the Frechet-difference products of Eq. (frechet) (jv_mode 1); "

@@ -12,8 +12,10 @@
 // the same algorithm as alone (Algorithm 1), with its own Krylov space.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include "hgks_internal.h"
 #include "givens.cuh"
+#include "offdiag.cuh"
 
 namespace hgks {
 namespace {
@@ -84,11 +86,15 @@ __global__ void __launch_bounds__(kB) k_bapply(DevMesh m, BatchDev bd, const TM 
     const TV sj = First ? (TV)dinv[j] : TV(1);
 #pragma unroll
     for (int c = 0; c < 5; c++) xj[c] = First ? sj * b[(size_t)c * N + j] : x[(size_t)c * N + j];
-    const TM *O = off + (size_t)p * 25 * N + i;
+    if constexpr (std::is_same<TM, float>::value) {
+      offdiag_product<TV>(reinterpret_cast<const float *>(off), N, i, p, j, xj, acc);
+    } else {
+      const TM *O = off + (size_t)p * 25 * N + i;
 #pragma unroll
-    for (int r = 0; r < 5; r++)
+      for (int r = 0; r < 5; r++)
 #pragma unroll
-      for (int c = 0; c < 5; c++) acc[r] = fma((TV)O[(size_t)(5 * r + c) * N], xj[c], acc[r]);
+        for (int c = 0; c < 5; c++) acc[r] = fma((TV)O[(size_t)(5 * r + c) * N], xj[c], acc[r]);
+    }
   }
   TO part_v = TO(0);
 #pragma unroll
@@ -231,7 +237,7 @@ struct BBuf {
   T *V, *w, *t, *t2, *part;
 };
 BBuf<double> bbuf64(Scratch &s, BatchState &bs) { return {s.off, s.dval, s.dinv, s.V, s.w, s.t, s.t2, bs.part}; }
-BBuf<float> bbuf32(Scratch &s, BatchState &bs) { return {s.off32, s.dval32, s.dinv32, s.V32, s.w32, s.t32, s.t232, bs.part32}; }
+BBuf<float> bbuf32(Scratch &s, BatchState &bs) { return {s.jv32, s.dval32, s.dinv32, s.V32, s.w32, s.t32, s.t232, bs.part32}; }
 
 // x = P^{-1} b for every mesh (Eq. (precond)); with dotv, also (x, dotv) per mesh
 template <typename T>

@@ -154,7 +154,7 @@ int64_t arena_bytes(int64_t cells, int64_t faces, const hgks_params &p, int sche
   if (schemes & 2) c += 8 * (9 * 19 + 12 * 7);                  // compact matrices
   c += 8 * (5 + (hw ? 15 : 0));                                 // Q, G
   c += 8 * (kCoef + 1 + 100 + 2 + 5 + 15 + 5 + 15);             // coef, dt, off, dval/dinv, R, Gnew, dQ, w/t/t2
-  c += mixed ? (4 * 100 + 4 * 2 + 4 * 15 + 4 * 5 * (p.krylov_dim + 1)) : 8 * 5 * (p.krylov_dim + 1);
+  c += mixed ? (4 * 22 + 4 * 2 + 4 * 15 + 4 * 5 * (p.krylov_dim + 1)) : 8 * 5 * (p.krylov_dim + 1);
   const int64_t f = 4 * 2 + 1 + 8 * (9 + 2) + 2 + 8 * (2 * 3 * kFaceState + 15 + 15);
   return N * c + F * f + nb * (2 + 8 + 4) + 8 * std::max<int64_t>(4096, N / 64 + 64) + (64 << 10);
 }

@@ -129,8 +129,8 @@ hgks_status ensure_scratch(Mesh &m, int kdim, bool implicit, bool mixed) {
     if ((st = dalloc(m, &s.hs, 65 * 64 + 256))) return st;
     HGKS_CUDA(cudaMemset(s.off, 0, sizeof(double) * 100 * N));
   }
-  if (implicit && mixed && !s.off32) {
-    if ((st = dalloc(m, &s.off32, (size_t)100 * N))) return st;
+  if (implicit && mixed && !s.jv32) {
+    if ((st = dalloc(m, &s.jv32, (size_t)22 * N))) return st;
     if ((st = dalloc(m, &s.dval32, N))) return st;
     if ((st = dalloc(m, &s.dinv32, N))) return st;
     if ((st = dalloc(m, &s.w32, 5 * N))) return st;

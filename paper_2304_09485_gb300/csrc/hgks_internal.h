@@ -93,7 +93,9 @@ struct Scratch {
   // implicit
   double *dinv = nullptr, *dval = nullptr;  // [N] the diagonal block is (|Omega|/dt + sum lambda S/2) I
   double *off = nullptr;         // [4*25][N]: block of local face p of the row cell (0 on a boundary)
-  float *off32 = nullptr;        // [4*25][N] FP32 copy (mixed precision)
+  float *jv32 = nullptr;         // [22][N] mixed precision: the off-diagonal blocks as products,
+                                 // rows 0-5 per cell (u, v, w, H, (gamma-1)|u|^2/2, gamma-1),
+                                 // rows 6 + 4p + k per (cell, local face p): n S/2 (k < 3), lambda S/2
   float *dinv32 = nullptr, *dval32 = nullptr;
   float *red32 = nullptr;
   int64_t vstride = 0;           // elements between Krylov vectors (5N padded to a multiple of 64)

@@ -18,8 +18,10 @@
 //    Hessenberg least-squares problem (Givens rotations) runs on the device, so a
 //    whole GMRES cycle is enqueued without synchronising the host.
 #include <cmath>
+#include <type_traits>
 #include "hgks_internal.h"
 #include "givens.cuh"
+#include "offdiag.cuh"
 
 namespace hgks {
 namespace {
@@ -48,11 +50,15 @@ __device__ __forceinline__ void euler_jacobian(const double *Q, const double *n,
   J[24] = gamma * un;
 }
 
+// jv32 (may be null): FP32 operands of the product form of the off-diagonal
+// blocks (mixed precision), with dval32, dinv32
 template <bool BATCH>
 __global__ void __launch_bounds__(kCellBlock) k_assemble(DevMesh m, hgks_params Pv, const double *__restrict__ Q,
                                                          const double *__restrict__ dt, double *__restrict__ dval,
                                                          double *__restrict__ dinv, double *__restrict__ off,
-                                                         double *__restrict__ diag_out, double *__restrict__ off_out) {
+                                                         double *__restrict__ diag_out, double *__restrict__ off_out,
+                                                         float *__restrict__ dval32, float *__restrict__ dinv32,
+                                                         float *__restrict__ jv32) {
   const int N = m.N, F = m.F;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -61,6 +67,12 @@ __global__ void __launch_bounds__(kCellBlock) k_assemble(DevMesh m, hgks_params 
     dinv[i] = 1.0;
 #pragma unroll 4
     for (int k = 0; k < 100; k++) off[(size_t)k * N + i] = 0.0;
+    if (jv32) {
+      dval32[i] = 1.0f;
+      dinv32[i] = 1.0f;
+#pragma unroll 2
+      for (int k = 0; k < 22; k++) jv32[(size_t)k * N + i] = 0.0f;
+    }
     return;
   }
   if (BATCH && !m.mact[m.cmesh[i]]) return;             // a mesh of a batch that has stopped
@@ -68,6 +80,13 @@ __global__ void __launch_bounds__(kCellBlock) k_assemble(DevMesh m, hgks_params 
   double Qi[5];
 #pragma unroll
   for (int c = 0; c < 5; c++) Qi[c] = Q[(size_t)c * N + i];
+  if (jv32) {                                           // this cell's primitives, for the rows of its neighbours
+    const double ir = 1.0 / Qi[0], g1 = P.gamma - 1.0;
+    const double u = Qi[1] * ir, v = Qi[2] * ir, w = Qi[3] * ir, phi = 0.5 * g1 * (u * u + v * v + w * w);
+    const double pk[6] = {u, v, w, P.gamma * Qi[4] * ir - phi, phi, g1};
+#pragma unroll
+    for (int k = 0; k < 6; k++) jv32[(size_t)k * N + i] = (float)pk[k];
+  }
   double d = m.vol[i] / dt[i];
 #pragma unroll 1
   for (int p = 0; p < 4; p++) {
@@ -90,6 +109,10 @@ __global__ void __launch_bounds__(kCellBlock) k_assemble(DevMesh m, hgks_params 
     double lam = fabs(u * n[0] + v * n[1] + w * n[2]) + sqrt(P.gamma * pr * ir);
     if (P.viscous) lam += 2.0 * P.mu / (Qf[0] * m.fdist[f]);
     d += 0.5 * lam * S;
+    if (jv32)
+#pragma unroll
+      for (int k = 0; k < 4; k++)
+        jv32[(size_t)(6 + 4 * p + k) * N + i] = j >= 0 ? (float)(0.5 * S * (k < 3 ? n[k] : lam)) : 0.0f;
     double J[25];
     if (j >= 0) euler_jacobian(Qj, n, P.gamma, J);
 #pragma unroll
@@ -101,6 +124,10 @@ __global__ void __launch_bounds__(kCellBlock) k_assemble(DevMesh m, hgks_params 
   }
   dval[i] = d;
   dinv[i] = 1.0 / d;
+  if (jv32) {
+    dval32[i] = (float)d;
+    dinv32[i] = (float)(1.0 / d);
+  }
   if (diag_out)
 #pragma unroll
     for (int k = 0; k < 25; k++) diag_out[(size_t)k * N + i] = k % 6 == 0 ? d : 0.0;
@@ -154,6 +181,9 @@ __device__ __forceinline__ void grid_sum(T v, T *partials, unsigned int *count, 
 // TM: type of the stored blocks, TV: type of b and x (and of the accumulation),
 // TO: type of y.
 enum { kSpmv = 0, kJacobi = 1 };
+
+// TM = float: the off-diagonal blocks come as products from jv (mixed precision);
+// TM = double: stored 5x5 blocks in off.
 template <typename TM, typename TV, typename TO, int Mode, bool FirstSweep>
 __global__ void __launch_bounds__(kCellBlock) k_apply(DevMesh m, const TM *__restrict__ off, const TM *__restrict__ dval,
                                                       const TM *__restrict__ dinv, const TV *__restrict__ b,
@@ -176,11 +206,15 @@ __global__ void __launch_bounds__(kCellBlock) k_apply(DevMesh m, const TM *__res
       const TV sj = FirstSweep ? (TV)dinv[j] : TV(1);
 #pragma unroll
       for (int c = 0; c < 5; c++) xj[c] = FirstSweep ? sj * b[(size_t)c * N + j] : x[(size_t)c * N + j];
-      const TM *O = off + (size_t)p * 25 * N + i;
+      if constexpr (std::is_same<TM, float>::value) {
+        offdiag_product<TV>(reinterpret_cast<const float *>(off), N, i, p, j, xj, acc);
+      } else {
+        const TM *O = off + (size_t)p * 25 * N + i;
 #pragma unroll
-      for (int r = 0; r < 5; r++)
+        for (int r = 0; r < 5; r++)
 #pragma unroll
-        for (int c = 0; c < 5; c++) acc[r] = fma((TV)O[(size_t)(5 * r + c) * N], xj[c], acc[r]);
+          for (int c = 0; c < 5; c++) acc[r] = fma((TV)O[(size_t)(5 * r + c) * N], xj[c], acc[r]);
+      }
     }
     TV out[5];
     if (Mode == kJacobi) {
@@ -280,23 +314,6 @@ __global__ void k_combine(int64_t n, int64_t vs, int m, const T *__restrict__ V,
   }
 }
 
-// FP32 copies of the assembled blocks (mixed precision)
-__global__ void k_to_f32(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) b[k] = (float)a[k];
-}
-
-// FP32 copies of the first nl columns of the [100][pitch] blocks and of dval, dinv
-__global__ void k_to_f32_rows(int64_t nl, int64_t pitch, const double *__restrict__ off, float *__restrict__ off32,
-                              const double *__restrict__ dval, float *__restrict__ dval32, const double *__restrict__ dinv,
-                              float *__restrict__ dinv32) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 102 * nl; k += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = k / nl, i = k - r * nl;
-    if (r < 100) off32[r * pitch + i] = (float)off[r * pitch + i];
-    else if (r == 100) dval32[i] = (float)dval[i];
-    else dinv32[i] = (float)dinv[i];
-  }
-}
-
 __global__ void __launch_bounds__(kBlock) k_density_l1(int N, const double *__restrict__ R, const double *__restrict__ inv_vol,
                                                        double *partials, unsigned int *count, double *out) {
   double s = 0.0;
@@ -350,7 +367,7 @@ struct KBuf {
   T *V, *w, *t, *t2, *red;
 };
 KBuf<double> kbuf64(Scratch &s) { return {s.off, s.dval, s.dinv, s.V, s.w, s.t, s.t2, s.red}; }
-KBuf<float> kbuf32(Scratch &s) { return {s.off32, s.dval32, s.dinv32, s.V32, s.w32, s.t32, s.t232, s.red32}; }
+KBuf<float> kbuf32(Scratch &s) { return {s.jv32, s.dval32, s.dinv32, s.V32, s.w32, s.t32, s.t232, s.red32}; }
 
 template <typename T> T *partials(Scratch &s);
 template <> double *partials<double>(Scratch &s) { return s.red; }
@@ -477,30 +494,18 @@ void gmres_t(const DevMesh &m, Scratch &s, const KBuf<T> &k, const hgks_params &
 
 void launch_assemble(const DevMesh &m, Scratch &s, const hgks_params &p, const double *Q, const double *dt,
                      double *diag_out, double *off_out, cudaStream_t st, bool batch) {
+  // mixed precision: the FP32 operands of the product form come out of the same pass
+  const bool mixed = p.precision == HGKS_MIXED && s.jv32;
+  float *dv32 = mixed ? s.dval32 : nullptr, *di32 = mixed ? s.dinv32 : nullptr, *jv = mixed ? s.jv32 : nullptr;
   HGKS_PROF_BEGIN(K_ASSEMBLE, st);
   batch = batch || m.ptab;
   if (batch)
-    k_assemble<true><<<grid_for(m.NL, kCellBlock), kCellBlock, 0, st>>>(m, p, Q, dt, s.dval, s.dinv, s.off, diag_out, off_out);
+    k_assemble<true><<<grid_for(m.NL, kCellBlock), kCellBlock, 0, st>>>(m, p, Q, dt, s.dval, s.dinv, s.off, diag_out,
+                                                                         off_out, dv32, di32, jv);
   else
-    k_assemble<false><<<grid_for(m.N, kCellBlock), kCellBlock, 0, st>>>(m, p, Q, dt, s.dval, s.dinv, s.off, diag_out, off_out);
+    k_assemble<false><<<grid_for(m.N, kCellBlock), kCellBlock, 0, st>>>(m, p, Q, dt, s.dval, s.dinv, s.off, diag_out,
+                                                                          off_out, dv32, di32, jv);
   HGKS_PROF_END(K_ASSEMBLE, st);
-  if (batch && p.precision == HGKS_MIXED && s.off32) {
-    // the cells in use only: rows of pitch N, the first NL columns
-    HGKS_PROF_BEGIN(K_ASSEMBLE, st);
-    k_to_f32_rows<<<vec_grid(102 * (int64_t)m.NL), kBlock, 0, st>>>(m.NL, m.N, s.off, s.off32, s.dval, s.dval32, s.dinv,
-                                                                       s.dinv32);
-    HGKS_PROF_END(K_ASSEMBLE, st);
-  } else if (p.precision == HGKS_MIXED && s.off32) {
-    HGKS_PROF_BEGIN(K_ASSEMBLE, st);
-    k_to_f32<<<vec_grid(100 * (int64_t)m.N), kBlock, 0, st>>>(100 * (int64_t)m.N, s.off, s.off32);
-    HGKS_PROF_END(K_ASSEMBLE, st);
-    HGKS_PROF_BEGIN(K_ASSEMBLE, st);
-    k_to_f32<<<vec_grid(m.N), kBlock, 0, st>>>(m.N, s.dval, s.dval32);
-    HGKS_PROF_END(K_ASSEMBLE, st);
-    HGKS_PROF_BEGIN(K_ASSEMBLE, st);
-    k_to_f32<<<vec_grid(m.N), kBlock, 0, st>>>(m.N, s.dinv, s.dinv32);
-    HGKS_PROF_END(K_ASSEMBLE, st);
-  }
 }
 
 void launch_apply_A(const DevMesh &m, const Scratch &s, const double *x, double *y, cudaStream_t st) {
