@@ -210,3 +210,22 @@ def test_batch_rejects_disagreeing_shared_parameters(cuda):
     p1 = params_for(probs[1][2], scheme=0, krylov_dim=10)
     with pytest.raises(H.HGKSError):
         H.hgks_batch_create([probs[0][3], probs[1][3]], [p0, p1])
+
+
+def test_batch_of_one_mesh_equals_alone(cuda):
+    import torch
+    name, m, cond, hm = problems()[1]
+    p = params_for(cond, scheme=0, krylov_dim=8, restarts=2)
+    b = H.hgks_batch_create([hm], [p])
+    Q, _ = perturbed(m, cond, 61)
+    Qd = hm.to_internal(Q)
+    H.hgks_batch_set_state(b, 0, Qd)
+    (info,) = H.hgks_batch_gmres_step(b)
+    Q0 = Qd.clone()
+    si = H.hgks_gmres_step(hm, p, Qd, None)
+    Qb = torch.empty_like(Qd)
+    H.hgks_batch_get_state(b, 0, Q=Qb)
+    torch.cuda.synchronize()
+    assert abs(info.res_l1 - si.res_l1) <= 1e-13 * si.res_l1
+    rel = (torch.linalg.norm((Qb - Q0) - (Qd - Q0)) / torch.linalg.norm(Qd - Q0)).item()
+    assert rel <= 1e-10, rel

@@ -140,3 +140,55 @@ def test_server_reports_a_failed_build(cuda):
     assert srv.status(rid).state == 4
     with pytest.raises(H.HGKSError):
         srv.collect(rid)
+
+
+def test_server_compact_scheme_with_gradients_equals_alone(cuda):
+    """The compact scheme carries G: served results (Q and G, caller order) equal the solve alone."""
+    import torch
+    kw = dict(scheme=1, krylov_dim=6, restarts=2, jacobi_sweeps=2)
+    shared = H.hgks_default_params(**kw)
+    srv = H.hgks_server(shared, hbm_budget_bytes=1 << 30, max_inflight=4)
+    probs = []
+    for k, (m, cond) in enumerate([(I.sphere_mesh(3, 4, stretch=1.3, wall_tag=I.BC_NOSLIP_ADIA),
+                                    I.sphere_conditions(0.25, Re=118.0)),
+                                   (I.cavity_mesh(3, seed=I.BASE_SEED + 23), I.cavity_conditions(0.2, 100.0))]):
+        Q0, G0 = I.smooth_state(m, seed=I.BASE_SEED + 95 + k, amp=0.02,
+                                base=(1.0, cond["u_inf"][0] + 0.03, 0.02, -0.01, cond["p_inf"]))
+        p = H.hgks_default_params(**{**cond, "Pr": 0.72, **kw})
+        rid = srv.submit(m, p, Q0, G0, drop_tol=0.3, max_steps=8)
+        probs.append((m, p, Q0, G0, rid))
+    while True:
+        fin, run, wait = srv.step()
+        if run == 0 and wait == 0:
+            break
+        if run == 0:
+            time.sleep(0.005)
+    for m, p, Q0, G0, rid in probs:
+        st = srv.status(rid)
+        Qs, Gs = srv.collect(rid, with_gradients=True)
+        hm = H.hgks_mesh_create(m, scheme_mask=2)
+        Qd, Gd = hm.to_internal(Q0), hm.to_internal(G0)
+        info, _, _ = H.hgks_solve_steady(hm, p, Qd, Gd, drop_tol=0.3, max_steps=8)
+        torch.cuda.synchronize()
+        assert st.solve.steps == info.steps
+        Qa, Ga = hm.to_caller(Qd), hm.to_caller(Gd)
+        assert np.linalg.norm(Qs - Qa) <= 1e-9 * np.linalg.norm(Qa)
+        assert np.linalg.norm(Gs - Ga) <= 1e-9 * np.linalg.norm(Ga)
+
+
+def test_server_with_one_slot_runs_requests_in_order(cuda):
+    """max_inflight = 1: one request at a time, admitted in arrival order."""
+    probs = problems()[:3]
+    srv = H.hgks_server(H.hgks_default_params(**KW), hbm_budget_bytes=1 << 30, max_inflight=1)
+    ids = [srv.submit(m, p, Q0, drop_tol=DROP, max_steps=6) for _, m, _, p, Q0 in probs]
+    while True:
+        fin, run, wait = srv.step()
+        assert run <= 1
+        if run == 0 and wait == 0:
+            break
+        if run == 0:
+            time.sleep(0.005)
+    st = [srv.status(i) for i in ids]
+    assert all(s.state == 3 for s in st)
+    assert st[0].t_admit <= st[1].t_admit <= st[2].t_admit
+    assert st[0].t_done <= st[1].t_admit and st[1].t_done <= st[2].t_admit
