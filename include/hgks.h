@@ -49,7 +49,8 @@ typedef enum {
   HGKS_ERR_NONPHYSICAL = 5,  /* non-finite residual or non-positive cell state     */
   HGKS_ERR_BREAKDOWN = 6,    /* reserved                                           */
   HGKS_ERR_NOT_CONVERGED = 7,/* hgks_solve_steady reached max_steps                */
-  HGKS_ERR_TIMEOUT = 8       /* reserved                                           */
+  HGKS_ERR_TIMEOUT = 8,      /* reserved                                           */
+  HGKS_ERR_CANCELLED = 9     /* a server request cancelled with hgks_server_cancel */
 } hgks_status;
 
 /* boundary tags of hgks_mesh_create (paper Sec. 5.1, 5.2) */
@@ -353,6 +354,11 @@ hgks_status hgks_server_submit(hgks_server server, const double *xyz, int64_t n_
  * NULL): solves finished in this round, solves running, requests waiting. */
 hgks_status hgks_server_step(hgks_server server, int32_t *n_finished, int32_t *n_running, int32_t *n_waiting);
 hgks_status hgks_server_status(hgks_server server, int64_t id, hgks_request_info *info);
+/* Cancel a request: one waiting for its build or for admission is dropped at
+ * once, one running leaves at the start of the next round with its current
+ * state (collectable); either way it finishes with status HGKS_ERR_CANCELLED.
+ * Cancelling a finished request does nothing. */
+hgks_status hgks_server_cancel(hgks_server server, int64_t id);
 /* Copy a finished request's state (host, caller order: Q double[n][5], G
  * double[n][15] or NULL) and forget the request. */
 hgks_status hgks_server_collect(hgks_server server, int64_t id, double *Q, double *G);

@@ -20,6 +20,7 @@ from . import _native
 HGKS_OK = 0
 HGKS_ERR_NONPHYSICAL = 5
 HGKS_ERR_NOT_CONVERGED = 7
+HGKS_ERR_CANCELLED = 9
 HGKS_WENO, HGKS_HWENO = 0, 1
 HGKS_NONLINEAR, HGKS_LINEAR = 0, 1
 HGKS_FP64, HGKS_MIXED = 0, 1
@@ -108,6 +109,7 @@ def lib():
             "hgks_server_step": [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
             "hgks_server_status": [vp, i64, C.POINTER(hgks_request_info)],
             "hgks_server_collect": [vp, i64, dp, dp],
+            "hgks_server_cancel": [vp, i64],
             "hgks_server_info": [vp, C.POINTER(hgks_batch_info_t)],
             "hgks_batch_info": [vp, C.POINTER(hgks_batch_info_t)],
             "hgks_batch_set_state": [vp, i32, dp, dp, vp],
@@ -421,6 +423,9 @@ class hgks_server:
         info = hgks_request_info()
         _check(lib().hgks_server_status(self.handle, rid, C.byref(info)))
         return info
+
+    def cancel(self, rid):
+        _check(lib().hgks_server_cancel(self.handle, rid))
 
     def collect(self, rid, with_gradients=False):
         n = self.n_cells.pop(rid)

@@ -47,6 +47,7 @@ struct Request {
   hgks_status status = HGKS_OK;
   int state = Q_WAIT;
   int slot = -1;
+  bool cancel = false;                 // set by hgks_server_cancel while building or running
   std::vector<double> Q, G;            // result, caller order
   hgks_solve_info info{};
   double t_submit = 0, t_built = 0, t_admit = 0, t_done = 0;
@@ -93,7 +94,12 @@ void builder_loop(hgks_server_s *S) {
                                      r->hm, err);
     std::lock_guard<std::mutex> lk(S->mu);
     r->t_built = now_s(S->t0);
-    if (st) {
+    if (r->cancel) {
+      r->status = HGKS_ERR_CANCELLED;
+      r->state = Q_DONE;
+      r->t_done = r->t_built;
+      r->hm = HostMesh{};
+    } else if (st) {
       r->status = st;
       r->err = err;
       r->state = Q_FAIL;
@@ -160,11 +166,14 @@ hgks_status admit(hgks_server_s &S, bool &changed) {
   }
 }
 
-hgks_status retire(hgks_server_s &S, const std::vector<int> &act, int *n_finished) {
+// retire the running requests whose slot is no longer active (act[1 + k] == 0),
+// or, with cancelled_only, those cancelled by the user
+hgks_status retire(hgks_server_s &S, const std::vector<int> &act, int *n_finished, bool cancelled_only = false) {
   Batch &B = *S.B;
   for (int k = 0; k < B.nslot; k++) {
     Request *r = S.running[k];
-    if (!r || act[1 + k]) continue;
+    if (!r) continue;
+    if (cancelled_only ? !r->cancel : act[1 + k] != 0) continue;
     int steps = 0, conv = 0, bad = 0;
     double ref = 0.0, res = 0.0;
     const size_t n = r->perm.size();
@@ -186,7 +195,7 @@ hgks_status retire(hgks_server_s &S, const std::vector<int> &act, int *n_finishe
     r->info.converged = conv;
     r->info.res_ref = ref;
     r->info.res_final = res;
-    r->status = bad ? HGKS_ERR_NONPHYSICAL : (conv ? HGKS_OK : HGKS_ERR_NOT_CONVERGED);
+    r->status = cancelled_only ? HGKS_ERR_CANCELLED : bad ? HGKS_ERR_NONPHYSICAL : (conv ? HGKS_OK : HGKS_ERR_NOT_CONVERGED);
     r->state = Q_DONE;
     r->t_done = now_s(S.t0);
     S.running[k] = nullptr;
@@ -292,6 +301,18 @@ hgks_status hgks_server_step(hgks_server S, int32_t *n_finished, int32_t *n_runn
   bool changed = false;
   hgks_status st;
   if (cudaSetDevice(B.m.device) != cudaSuccess) return fail_msg(HGKS_ERR_CUDA, "cudaSetDevice");
+  {
+    bool any_cancel = false;
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      for (auto *r : S->running) any_cancel = any_cancel || (r && r->cancel);
+    }
+    if (any_cancel) {
+      std::vector<int> none(B.nslot + 1, 0);
+      if ((st = retire(*S, none, &fin, true))) return st;
+      changed = true;
+    }
+  }
   if ((st = admit(*S, changed))) return st;
   int run = 0;
   for (auto *r : S->running) run += r ? 1 : 0;
@@ -334,6 +355,32 @@ hgks_status hgks_server_status(hgks_server S, int64_t id, hgks_request_info *inf
   return HGKS_OK;
 }
 
+hgks_status hgks_server_cancel(hgks_server S, int64_t id) {
+  if (!S) return fail_msg(HGKS_ERR_ARG, "server is NULL");
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->all.find(id);
+  if (it == S->all.end()) return fail_msg(HGKS_ERR_ARG, "unknown request id");
+  Request *r = it->second.get();
+  auto drop = [&](std::deque<Request *> &q) {
+    auto qi = std::find(q.begin(), q.end(), r);
+    if (qi == q.end()) return false;
+    q.erase(qi);
+    r->status = HGKS_ERR_CANCELLED;
+    r->state = Q_DONE;
+    r->t_done = now_s(S->t0);
+    r->hm = HostMesh{};
+    return true;
+  };
+  if (r->state == Q_WAIT) {
+    if (!drop(S->to_build)) r->cancel = true;          // being built now: the builder drops it
+  } else if (r->state == Q_BUILT) {
+    drop(S->built);
+  } else if (r->state == Q_RUN) {
+    r->cancel = true;                                  // leaves at the start of the next round
+  }
+  return HGKS_OK;
+}
+
 hgks_status hgks_server_collect(hgks_server S, int64_t id, double *Q, double *G) {
   if (!S) return fail_msg(HGKS_ERR_ARG, "server is NULL");
   std::unique_ptr<Request> r;
@@ -346,6 +393,7 @@ hgks_status hgks_server_collect(hgks_server S, int64_t id, double *Q, double *G)
     S->all.erase(it);
   }
   if (r->state == Q_FAIL) return fail_msg(r->status, r->err);
+  if (r->status == HGKS_ERR_CANCELLED && r->Q.empty()) return fail_msg(HGKS_ERR_CANCELLED, "cancelled before it ran");
   if (Q) std::memcpy(Q, r->Q.data(), sizeof(double) * r->Q.size());
   if (G && !r->G.empty()) std::memcpy(G, r->G.data(), sizeof(double) * r->G.size());
   return HGKS_OK;

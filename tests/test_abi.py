@@ -85,7 +85,8 @@ def test_server_and_dynamic_batch_entry_points_reject_bad_arguments_without_gpu(
     assert L.hgks_batch_create_empty(0, 1024, 4096, 4, None, C.byref(out)) == 1
     for fn, args in (("hgks_server_destroy", (None,)), ("hgks_server_step", (None, None, None, None)),
                      ("hgks_server_status", (None, 1, None)), ("hgks_server_collect", (None, 1, None, None)),
-                     ("hgks_server_info", (None, None)), ("hgks_batch_add", (None, None, None, None)),
+                     ("hgks_server_info", (None, None)), ("hgks_server_cancel", (None, 1)),
+                     ("hgks_batch_add", (None, None, None, None)),
                      ("hgks_batch_remove", (None, 0))):
         assert getattr(L, fn)(*args) == 1, fn
         assert b"NULL" in L.hgks_last_error(), fn

@@ -192,3 +192,63 @@ def test_server_with_one_slot_runs_requests_in_order(cuda):
     assert all(s.state == 3 for s in st)
     assert st[0].t_admit <= st[1].t_admit <= st[2].t_admit
     assert st[0].t_done <= st[1].t_admit and st[1].t_done <= st[2].t_admit
+
+
+def _drain(srv):
+    while True:
+        fin, run, wait = srv.step()
+        if run == 0 and wait == 0:
+            return
+        if run == 0:
+            time.sleep(0.005)
+
+
+def test_a_failing_request_leaves_the_others_bit_for_bit(cuda):
+    """A request whose state holds a NaN fails (non-finite residual) while the
+    requests beside it end exactly as they end without it: a mesh's arithmetic
+    in the arena does not depend on its neighbours."""
+    probs = problems()[:3]
+    shared = H.hgks_default_params(**KW)
+
+    def serve(with_bad):
+        srv = H.hgks_server(shared, hbm_budget_bytes=1 << 30, max_inflight=8)
+        ids = [srv.submit(m, p, Q0, drop_tol=DROP, max_steps=10) for _, m, _, p, Q0 in probs]
+        bad = None
+        if with_bad:
+            _, m, _, p, Q0 = problems()[4]
+            Qn = Q0.copy()
+            Qn[7, 0] = np.nan
+            bad = srv.submit(m, p, Qn, drop_tol=DROP, max_steps=10)
+        _drain(srv)
+        out = [srv.collect(i)[0] for i in ids]
+        st = srv.status(bad) if with_bad else None
+        return out, st
+
+    ref, _ = serve(False)
+    mixed, st_bad = serve(True)
+    assert st_bad.state == 3 and st_bad.status == H.HGKS_ERR_NONPHYSICAL
+    for a, b in zip(ref, mixed):
+        assert np.array_equal(a, b)
+
+
+def test_cancel_queued_and_running_requests(cuda):
+    probs = problems()[:3]
+    srv = H.hgks_server(H.hgks_default_params(**KW), hbm_budget_bytes=1 << 30, max_inflight=1)
+    ids = [srv.submit(m, p, Q0, drop_tol=1e-12, max_steps=40) for _, m, _, p, Q0 in probs]
+    for _ in range(2000):                   # until the first request runs
+        srv.step()
+        if srv.status(ids[0]).state == 2:
+            break
+        time.sleep(0.002)
+    srv.step()
+    srv.cancel(ids[0])                     # running: leaves with its state at the next round
+    srv.cancel(ids[2])                     # waiting: dropped
+    _drain(srv)
+    s0, s1, s2 = (srv.status(i) for i in ids)
+    assert s0.status == H.HGKS_ERR_CANCELLED and 0 < s0.solve.steps < 40
+    assert s1.state == 3 and s1.status == H.HGKS_ERR_NOT_CONVERGED and s1.solve.steps == 40
+    assert s2.status == H.HGKS_ERR_CANCELLED
+    Q0c, _ = srv.collect(ids[0])           # the cancelled running request's state at cancellation
+    assert np.isfinite(Q0c).all()
+    with pytest.raises(H.HGKSError):
+        srv.collect(ids[2])
