@@ -201,6 +201,16 @@ hgks_status hgks_solve_steady(hgks_mesh mesh, const hgks_params *p, double *Q, d
                               double drop_tol, int32_t max_steps, double *hist_host,
                               hgks_solve_info *info, void *cuda_stream);
 
+/* Resume Algorithm 1 from a snapshot: Q, G the state a solve stopped with (for
+ * example copied to the host and back) and *from its hgks_solve_info (steps
+ * taken, res_ref). The solve continues counting steps from from->steps up to
+ * max_steps with the same drop reference, so it reproduces the uninterrupted
+ * solve's iterates bit for bit. hist_host (may be NULL) is indexed by the
+ * absolute step (max_steps + 1 entries). */
+hgks_status hgks_solve_resume(hgks_mesh mesh, const hgks_params *p, double *Q, double *G, double drop_tol,
+                              int32_t max_steps, const hgks_solve_info *from, double *hist_host,
+                              hgks_solve_info *info, void *cuda_stream);
+
 /* Host-buffer variants: Q, G (and R, G_new) are host arrays in internal order
  * and layout above; the copies to and from the device happen inside the call
  * on the given stream, which is synchronised before return. */

@@ -93,6 +93,8 @@ def lib():
             "hgks_precondition": [vp, i32, dp, dp, vp],
             "hgks_gmres_step": [vp, P, dp, dp, dp, C.POINTER(hgks_step_info), vp],
             "hgks_solve_steady": [vp, P, dp, dp, C.c_double, i32, dp, C.POINTER(hgks_solve_info), vp],
+            "hgks_solve_resume": [vp, P, dp, dp, C.c_double, i32, C.POINTER(hgks_solve_info), dp,
+                                  C.POINTER(hgks_solve_info), vp],
             "hgks_residual_host": [vp, P, dp, dp, dp, dp, vp],
             "hgks_gmres_step_host": [vp, P, dp, dp, C.POINTER(hgks_step_info), vp],
             "hgks_sync": [vp],
@@ -272,6 +274,16 @@ def hgks_solve_steady(mesh, params, Q, G=None, drop_tol=1e-8, max_steps=1000, st
     info = hgks_solve_info()
     st = _check(lib().hgks_solve_steady(mesh.handle, C.byref(params), _ptr(Q), _ptr(G), drop_tol, max_steps,
                                         _ptr(hist), C.byref(info), _stream(stream)), allow=(HGKS_ERR_NOT_CONVERGED,))
+    return info, hist[: info.steps + 1], st == HGKS_OK
+
+
+def hgks_solve_resume(mesh, params, Q, G, frm, drop_tol=1e-8, max_steps=1000, stream=None):
+    """Continue a solve from its state and hgks_solve_info: (info, hist [absolute steps], converged)."""
+    hist = np.zeros(max_steps + 1)
+    info = hgks_solve_info()
+    st = _check(lib().hgks_solve_resume(mesh.handle, C.byref(params), _ptr(Q), _ptr(G), drop_tol, max_steps,
+                                        C.byref(frm), _ptr(hist), C.byref(info), _stream(stream)),
+                allow=(HGKS_ERR_NOT_CONVERGED,))
     return info, hist[: info.steps + 1], st == HGKS_OK
 
 

@@ -457,20 +457,23 @@ hgks_status hgks_gmres_step(hgks_mesh mesh, const hgks_params *p, double *Q, dou
   return gmres_step_impl(m, p, Q, G, dQ_out, info, (cudaStream_t)cuda_stream);
 }
 
-hgks_status hgks_solve_steady(hgks_mesh mesh, const hgks_params *p, double *Q, double *G, double drop_tol,
-                              int32_t max_steps, double *hist_host, hgks_solve_info *info, void *cuda_stream) {
+// Algorithm 1 from step k0 with the drop reference ref0 (0, 0: a fresh solve)
+static hgks_status solve_impl(hgks_mesh mesh, const hgks_params *p, double *Q, double *G, double drop_tol,
+                              int32_t max_steps, int32_t k0, double ref0, double *hist_host, hgks_solve_info *info,
+                              void *cuda_stream) {
   if (!mesh) return fail(HGKS_ERR_ARG, "mesh is NULL");
   Mesh &m = mesh->m;
   hgks_status st = check_params(m, p);
   if (st) return st;
   if (!Q || (p->scheme == HGKS_HWENO && !G)) return fail(HGKS_ERR_ARG, "Q (or G) is NULL");
   if (!(drop_tol > 0.0) || max_steps < 0) return fail(HGKS_ERR_ARG, "drop_tol must be > 0 and max_steps >= 0");
+  if (k0 < 0 || k0 > max_steps || !(ref0 >= 0.0)) return fail(HGKS_ERR_ARG, "resume point out of range");
   if ((st = set_device(m))) return st;
   if ((st = ensure_scratch(m, p->krylov_dim, true, p->precision == HGKS_MIXED))) return st;
   if (p->jv_mode == 1 && (st = ensure_fd(m))) return st;
   cudaStream_t s_ = (cudaStream_t)cuda_stream;
-  double ref = 0.0, res = 0.0;
-  int k = 0;
+  double ref = ref0, res = 0.0;
+  int k = k0;
   bool conv = false;
   for (;; k++) {
     // the residual of the current state decides; the step then updates it
@@ -493,6 +496,18 @@ hgks_status hgks_solve_steady(hgks_mesh mesh, const hgks_params *p, double *Q, d
   if (st) return st;
   if (!conv) return fail(HGKS_ERR_NOT_CONVERGED, "max_steps reached");
   return HGKS_OK;
+}
+
+hgks_status hgks_solve_steady(hgks_mesh mesh, const hgks_params *p, double *Q, double *G, double drop_tol,
+                              int32_t max_steps, double *hist_host, hgks_solve_info *info, void *cuda_stream) {
+  return solve_impl(mesh, p, Q, G, drop_tol, max_steps, 0, 0.0, hist_host, info, cuda_stream);
+}
+
+hgks_status hgks_solve_resume(hgks_mesh mesh, const hgks_params *p, double *Q, double *G, double drop_tol,
+                              int32_t max_steps, const hgks_solve_info *from, double *hist_host,
+                              hgks_solve_info *info, void *cuda_stream) {
+  if (!from) return fail(HGKS_ERR_ARG, "from is NULL");
+  return solve_impl(mesh, p, Q, G, drop_tol, max_steps, from->steps, from->res_ref, hist_host, info, cuda_stream);
 }
 
 // device copies of host-side state for the *_host entry points: Q, G, R, G_new

@@ -349,3 +349,24 @@ def test_solve_steady_parity(cuda):
     np.testing.assert_allclose(hist_g, hist_o, rtol=1e-8)
     rel = np.linalg.norm(hm.to_caller(Qd) - Qo) / np.linalg.norm(Qo)
     assert rel <= 1e-9, rel
+
+
+def test_solve_resumes_from_a_host_snapshot_bit_for_bit(cuda):
+    """Checkpoint/resume: stop a solve at 6 steps, copy (Q, G) to the host and
+    back, resume to 12 steps: the iterates equal the uninterrupted 12-step solve."""
+    import torch
+    m, cond, om, hm = setup("cavity5")
+    Q, G = state(m, cond, seed=9)
+    p = H.hgks_default_params(scheme=1, Pr=0.72, krylov_dim=6, restarts=2, **cond)
+    Qa, Ga = hm.to_internal(Q), hm.to_internal(G)
+    ia, ha, _ = H.hgks_solve_steady(hm, p, Qa, Ga, drop_tol=1e-12, max_steps=12)
+    Qb, Gb = hm.to_internal(Q), hm.to_internal(G)
+    i6, h6, _ = H.hgks_solve_steady(hm, p, Qb, Gb, drop_tol=1e-12, max_steps=6)
+    snap_Q, snap_G = Qb.cpu().numpy().copy(), Gb.cpu().numpy().copy()
+    Qc, Gc = torch.from_numpy(snap_Q).cuda(), torch.from_numpy(snap_G).cuda()
+    ib, hb, _ = H.hgks_solve_resume(hm, p, Qc, Gc, i6, drop_tol=1e-12, max_steps=12)
+    torch.cuda.synchronize()
+    assert ib.steps == ia.steps == 12 and ib.res_ref == ia.res_ref
+    assert torch.equal(Qc, Qa) and torch.equal(Gc, Ga)
+    np.testing.assert_array_equal(hb[6:], ha[6:])
+    np.testing.assert_array_equal(h6, ha[:7])
