@@ -53,6 +53,15 @@ hgks_status upload(Mesh &m, T **p, const std::vector<T> &v) {
 }
 
 void free_all(Mesh &m) {
+  if (m.graph) {
+    if (m.graph->stream) cudaStreamSynchronize(m.graph->stream);
+    if (m.graph->exec) cudaGraphExecDestroy(m.graph->exec);
+    if (m.graph->ev_in) cudaEventDestroy(m.graph->ev_in);
+    if (m.graph->ev_out) cudaEventDestroy(m.graph->ev_out);
+    if (m.graph->stream) cudaStreamDestroy(m.graph->stream);
+    delete m.graph;
+    m.graph = nullptr;
+  }
   for (void *p : m.allocs) cudaFree(p);
   m.allocs.clear();
 }
@@ -408,8 +417,10 @@ hgks_status hgks_precondition(hgks_mesh mesh, int32_t sweeps, const double *b, d
 }
 
 // have_residual: s.R, s.Gnew, s.dt and the density L1 already hold those of Q
-static hgks_status gmres_step_impl(Mesh &m, const hgks_params *p, double *Q, double *G, double *dQ_out,
-                                   hgks_step_info *info, cudaStream_t st_, bool have_residual = false) {
+// The device work of one outer step of Algorithm 1 (launch sequence fixed by
+// the parameters: capturable).
+static hgks_status enqueue_step(Mesh &m, const hgks_params *p, double *Q, double *G, double *dQ_out,
+                                bool have_residual, cudaStream_t st_) {
   const DevMesh &d = m.d;
   Scratch &s = m.s;
   double *res_dev = s.hs + 65 * 64 + 200;
@@ -418,11 +429,60 @@ static hgks_status gmres_step_impl(Mesh &m, const hgks_params *p, double *Q, dou
     launch_density_l1(d, s, s.R, res_dev, st_);
   }
   launch_assemble(d, s, *p, Q, s.dt, nullptr, nullptr, st_);
-  hgks_status st = gmres_solve(d, s, *p, s.R, s.dQ, info, st_, Q, G);
+  hgks_status st = gmres_solve(d, s, *p, s.R, s.dQ, nullptr, st_, Q, G);
   if (st) return st;
   if (dQ_out) HGKS_CUDA(cudaMemcpyAsync(dQ_out, s.dQ, sizeof(double) * 5 * m.N, cudaMemcpyDeviceToDevice, st_));
   launch_update(d, Q, s.dQ, G, s.Gnew, p->scheme == HGKS_HWENO ? 15 : 0, st_);
-  if ((st = last_launch())) return st;
+  return last_launch();
+}
+
+// Runs the step's device work as a CUDA graph (captured on the mesh's own stream,
+// again whenever the parameters or the state pointers change); eagerly while the
+// per-kernel profiler is on.
+static hgks_status run_step(Mesh &m, const hgks_params *p, double *Q, double *G, double *dQ_out, bool have_residual,
+                            cudaStream_t user) {
+  if (g_prof_on) return enqueue_step(m, p, Q, G, dQ_out, have_residual, user);
+  if (!m.graph) {
+    m.graph = new (std::nothrow) StepGraph;
+    if (!m.graph) return fail(HGKS_ERR_OOM, "host allocation");
+    HGKS_CUDA(cudaStreamCreateWithFlags(&m.graph->stream, cudaStreamNonBlocking));
+    HGKS_CUDA(cudaEventCreateWithFlags(&m.graph->ev_in, cudaEventDisableTiming));
+    HGKS_CUDA(cudaEventCreateWithFlags(&m.graph->ev_out, cudaEventDisableTiming));
+  }
+  StepGraph &g = *m.graph;
+  const bool same = g.exec && std::memcmp(&g.p, p, sizeof(hgks_params)) == 0 && g.Q == Q && g.G == G &&
+                    g.dQ_out == dQ_out && g.have_res == have_residual;
+  if (!same) {
+    if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
+    cudaGraph_t graph = nullptr;
+    HGKS_CUDA(cudaStreamBeginCapture(g.stream, cudaStreamCaptureModeThreadLocal));
+    const int64_t l0 = g_launches;
+    hgks_status st = enqueue_step(m, p, Q, G, dQ_out, have_residual, g.stream);
+    g.launches = g_launches - l0;
+    g_launches = l0;
+    cudaError_t e = cudaStreamEndCapture(g.stream, &graph);
+    if (!st && e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (st) return st;
+    if (e != cudaSuccess) { cudaGetLastError(); g.exec = nullptr; return cuda_fail(e, "CUDA graph capture of the step"); }
+    g.p = *p; g.Q = Q; g.G = G; g.dQ_out = dQ_out; g.have_res = have_residual;
+  }
+  HGKS_CUDA(cudaEventRecord(g.ev_in, user));
+  HGKS_CUDA(cudaStreamWaitEvent(g.stream, g.ev_in, 0));
+  HGKS_CUDA(cudaGraphLaunch(g.exec, g.stream));
+  g_launches += g.launches;
+  HGKS_CUDA(cudaEventRecord(g.ev_out, g.stream));
+  HGKS_CUDA(cudaStreamWaitEvent(user, g.ev_out, 0));
+  return HGKS_OK;
+}
+
+static hgks_status gmres_step_impl(Mesh &m, const hgks_params *p, double *Q, double *G, double *dQ_out,
+                                   hgks_step_info *info, cudaStream_t st_, bool have_residual = false) {
+  Scratch &s = m.s;
+  double *res_dev = s.hs + 65 * 64 + 200;
+  hgks_status st = run_step(m, p, Q, G, dQ_out, have_residual, st_);
+  if (st) return st;
+  if (info) info->krylov_iters = p->restarts * p->krylov_dim;
   double host[3];
   const int mk = p->krylov_dim;
   HGKS_CUDA(cudaMemcpyAsync(host, res_dev, sizeof(double), cudaMemcpyDeviceToHost, st_));

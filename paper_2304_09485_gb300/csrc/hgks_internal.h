@@ -115,6 +115,18 @@ struct Scratch {
   int blk_recon = 128, blk_flux = 128;   // launch shapes of the two FP64-bound kernels (autotuned for batches)
 };
 
+// A captured implicit step of one mesh (CUDA graph), replayed while the
+// parameters and state pointers stay the same.
+struct StepGraph {
+  cudaStream_t stream = nullptr;   // capture and replay stream, ordered after the caller's by events
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  hgks_params p{};
+  const double *Q = nullptr, *G = nullptr, *dQ_out = nullptr;
+  bool have_res = false;
+  int64_t launches = 0;
+};
+
 struct Mesh {
   int device = 0;
   int64_t N = 0, F = 0, Fb = 0;
@@ -124,6 +136,7 @@ struct Mesh {
   std::vector<double> vol_host;
   size_t bytes = 0;
   std::vector<void *> allocs;
+  StepGraph *graph = nullptr;
 };
 
 // ---- host mesh construction (mesh_setup.cpp) ----
