@@ -256,6 +256,37 @@ def test_full_size_sphere_sampled(cuda):
     assert err.max() <= TOL_R, err.max()
 
 
+def test_full_size_viscous_sphere_compact_sampled(cuda):
+    """The 995,328-cell viscous sphere of the precision workload (6x24x24, 48 layers,
+    first layer 3e-2, adiabatic no-slip wall), compact HWENO with Pr 0.72: residual
+    and gradient update on sampled cells against the oracle."""
+    import torch
+    m = I.sphere_mesh(24, 48, stretch=I.sphere_stretch(48, dr1=3e-2), wall_tag=I.BC_NOSLIP_ADIA)
+    cond = I.sphere_conditions(0.2535, Re=118.0)
+    hm = H.hgks_mesh_create(m, scheme_mask=2)
+    Q, G = I.smooth_state(m, amp=0.02, base=(1.0, 0.2535, 0.0, 0.0, 1 / GAMMA), wavenumber=1.0)
+    kw = dict(scheme=1, Pr=0.72, cfl=20.0, **cond)
+    Qd, Gd = hm.to_internal(Q), hm.to_internal(G)
+    Rd, Gn = torch.empty_like(Qd), torch.empty_like(Gd)
+    H.hgks_residual(hm, H.hgks_default_params(**kw), Qd, Gd, Rd, Gn)
+    torch.cuda.synchronize()
+    om = O.OracleMesh(m)
+    rng = np.random.default_rng(3)
+    # sampled cells: random ones and the wall layer (where the viscous terms are largest)
+    wall = np.where(np.isin(m.tet4, m.bface3[m.btag == I.BC_NOSLIP_ADIA]).sum(1) >= 3)[0]
+    cells = np.unique(np.concatenate([rng.choice(m.n_tet, 300, replace=False), rng.choice(wall, 100, replace=False)]))
+    Ro, Go = om.residual(O.make_params(**kw), Q, G, cells=cells)
+    Rg, Gg = hm.to_caller(Rd), hm.to_caller(Gn)
+    scale = flux_scale(om, Q)
+    err = np.abs(Rg[cells] - Ro[cells]) / scale[cells]
+    assert err.max() <= TOL_R, err.max()
+    # gradients against the cell's largest state component times its area/volume
+    # (momentum components of this flow can be zero in a cell)
+    gs = (np.abs(Q).max(axis=1) * area_over_volume(om))[cells][:, None]
+    gerr = np.abs(Gg[cells] - Go[cells]) / gs
+    assert gerr.max() <= TOL_R, gerr.max()
+
+
 def five_tet_cube():
     """A unit cube split into 5 tetrahedra (odd cell count), far field on all sides."""
     V = np.array([[a, b, c] for a in (0, 1) for b in (0, 1) for c in (0, 1)], dtype=np.float64)
