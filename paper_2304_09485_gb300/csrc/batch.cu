@@ -323,6 +323,7 @@ void bgmres_t(const DevMesh &m, Scratch &s, BatchState &bs, const BBuf<T> &k, co
 
 void launch_batch_gmres(const DevMesh &m, Scratch &s, BatchState &bs, const hgks_params &p, const double *rhs,
                         double *dx, cudaStream_t st) {
+  HGKS_RANGE("hgks batch gmres");
   cudaMemset2DAsync(dx, sizeof(double) * m.N, 0, sizeof(double) * m.NL, 5, st);
   if (p.precision == HGKS_MIXED) bgmres_t<float>(m, s, bs, bbuf32(s, bs), p, rhs, dx, st);
   else bgmres_t<double>(m, s, bs, bbuf64(s, bs), p, rhs, dx, st);

@@ -264,6 +264,7 @@ hgks_status hgks_mesh_create(const double *xyz, int64_t n_vert, const int64_t *t
                              const int64_t *bface3, const int32_t *btag, int64_t n_bface,
                              const double *periodic_shift, int32_t n_periodic, int32_t scheme_mask,
                              int32_t device, hgks_mesh *out, int64_t *perm_out) {
+  HGKS_RANGE("hgks mesh create");
   if (!out) return fail(HGKS_ERR_ARG, "out is NULL");
   *out = nullptr;
   if ((scheme_mask & 3) == 0) return fail(HGKS_ERR_ARG, "scheme_mask selects no scheme");

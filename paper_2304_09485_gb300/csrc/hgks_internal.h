@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include "../../include/hgks.h"
 
 namespace hgks {
@@ -199,6 +200,17 @@ hgks_status cuda_error(cudaError_t e, const char *where);
 // accessors for entry points defined outside capi.cu
 Mesh *mesh_of(hgks_mesh h);
 void set_last_error(const char *msg);
+
+// NVTX range over one phase of Algorithm 1 (inert unless a profiler is attached)
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define HGKS_CAT2(a, b) a##b
+#define HGKS_CAT(a, b) HGKS_CAT2(a, b)
+#define HGKS_RANGE(name) hgks::NvtxRange HGKS_CAT(hgks_nvtx_, __LINE__)(name)
 
 extern thread_local int64_t g_launches;
 inline void count_launch() { ++g_launches; }

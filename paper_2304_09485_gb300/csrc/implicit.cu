@@ -494,6 +494,7 @@ void gmres_t(const DevMesh &m, Scratch &s, const KBuf<T> &k, const hgks_params &
 
 void launch_assemble(const DevMesh &m, Scratch &s, const hgks_params &p, const double *Q, const double *dt,
                      double *diag_out, double *off_out, cudaStream_t st, bool batch) {
+  HGKS_RANGE("hgks assemble");
   // mixed precision: the FP32 operands of the product form come out of the same pass
   const bool mixed = p.precision == HGKS_MIXED && s.jv32;
   float *dv32 = mixed ? s.dval32 : nullptr, *di32 = mixed ? s.dinv32 : nullptr, *jv = mixed ? s.jv32 : nullptr;
@@ -547,6 +548,7 @@ void launch_update(const DevMesh &m, double *Q, const double *dQ, double *G, con
 // hs layout: H[(m+1) m] | beta | y[m] | lin residual estimates
 hgks_status gmres_solve(const DevMesh &m, Scratch &s, const hgks_params &p, const double *rhs, double *dx,
                         hgks_step_info *info, cudaStream_t st, const double *Q, const double *G) {
+  HGKS_RANGE("hgks gmres");
   cudaMemsetAsync(dx, 0, sizeof(double) * 5 * (size_t)m.N, st);
   if (p.jv_mode == 1) {
     if (!Q || !s.Qp) return HGKS_ERR_ARG;

@@ -804,6 +804,7 @@ void launch_local_dt(const DevMesh &m, const hgks_params &p, const double *Q, do
 
 void launch_residual(const DevMesh &m, Scratch &s, const hgks_params &p, const double *Q, const double *G, double *R,
                      double *Gnew, cudaStream_t st, bool batch, bool fresh_dt) {
+  HGKS_RANGE("hgks residual");
   batch = batch || m.ptab != nullptr;
   if (fresh_dt) launch_local_dt(m, p, Q, s.dt, st);
   HGKS_PROF_BEGIN(K_COEF, st);

@@ -295,6 +295,7 @@ hgks_status hgks_server_submit(hgks_server S, const double *xyz, int64_t n_vert,
 }
 
 hgks_status hgks_server_step(hgks_server S, int32_t *n_finished, int32_t *n_running, int32_t *n_waiting) {
+  HGKS_RANGE("hgks server step");
   if (!S) return fail_msg(HGKS_ERR_ARG, "server is NULL");
   Batch &B = *S->B;
   int fin = 0;
