@@ -701,6 +701,10 @@ def main():
                                 "one residual per Krylov vector, the cost the paper avoids with the assembled A"},
         "e2e": {"value": e2e_val, "unit": "Mcells/s", "h2d_bytes_per_step": 5 * 8 * m.n_tet,
                 "d2h_bytes_per_step": 5 * 8 * m.n_tet},
+        "gmres_iterations_per_s": {
+            "fp64": world * kw["krylov_dim"] * p.restarts / (ms / args.steps / 1000.0),
+            "mixed": world * kw["krylov_dim"] * p.restarts / (mixed_ms / 1000.0),
+            "note": "Arnoldi steps (Krylov vectors) per second, whole job, inside full implicit steps"},
         "gpu_launches": int(launches),
         "kernels_ms": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
         "roofline": roof,
