@@ -51,9 +51,12 @@ KERNEL_FLOPS = {
 }
 
 
-def workload(small=False):
+def workload(small=False, sphere_n=0):
     from paper_2304_09485_gb300 import inputs as I
-    if small:
+    if sphere_n:
+        m = I.sphere_mesh(sphere_n, 2 * sphere_n, stretch=I.sphere_stretch(2 * sphere_n))
+        name = f"sphere O-grid 6x{sphere_n}x{sphere_n}x{2 * sphere_n} -> {m.n_tet:,} tets (profiling size)"
+    elif small:
         m = I.sphere_mesh(12, 24, stretch=1.2)
         name = "sphere O-grid 6x12x12x24 -> 124,416 tets (scaled-down sample of the 6x32x32x64 case)"
     else:
@@ -517,6 +520,7 @@ def main():
     ap.add_argument("--impl", default="hgks", choices=["hgks", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="scaled-down mesh (profiling runs)")
+    ap.add_argument("--sphere-n", type=int, default=0, help="sphere of n x n patches and 2n layers (profiling runs)")
     ap.add_argument("--workload", default="sphere", choices=["sphere", "batch", "serve", "precision"],
                     help="sphere: the 2.36M-tet sphere (default); batch: many problems in one batch; "
                          "serve: Poisson-arriving solves through the request server")
@@ -560,7 +564,7 @@ def main():
         cb = cpu_baseline(steps=1)
         cb.pop("seconds", None)
 
-    m, cond, kw, name = workload(small=args.small)
+    m, cond, kw, name = workload(small=args.small, sphere_n=args.sphere_n)
     hm = H.hgks_mesh_create(m, scheme_mask=1, device=local)
     p = H.hgks_default_params(**kw)
     if args.launch_list and args.launch_precision == "mixed":
