@@ -245,45 +245,53 @@ __global__ void k_diag_scale(int N, const T *__restrict__ dinv, const T *__restr
   x[t] = dinv[t % N] * b[t];
 }
 
-template <typename T> struct Vec2;
-template <> struct Vec2<double> { typedef double2 type; };
-template <> struct Vec2<float> { typedef float2 type; };
+// 16-byte vectors of T: every Krylov vector starts on a 256-byte boundary
+// (vectors are padded to a multiple of 64 elements) and so do the device arrays
+// the reductions read.
+template <typename T> struct Vec16;
+template <> struct Vec16<double> { typedef double2 type; static constexpr int n = 2; };
+template <> struct Vec16<float> { typedef float4 type; static constexpr int n = 4; };
 
 // w -= h v (if v != nullptr); *out = (w, x) (mode 0) or ||w|| (x == w, mode 1).
-// Two elements per thread and step; every vector starts on a 16-byte boundary
-// (Krylov vectors are padded to a multiple of 64 elements), n may be odd.
+// 16 bytes per vector per thread and step, four steps in flight; n need not be
+// a multiple of the vector width.
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_axpy_dot(int64_t n, T *__restrict__ w, const T *__restrict__ v,
                                                      const double *__restrict__ h, const T *__restrict__ x,
                                                      int self, T *partials, unsigned int *count, double *out) {
-  typedef typename Vec2<T>::type T2;
+  typedef typename Vec16<T>::type TV;
+  constexpr int L = Vec16<T>::n;
   const T hv = v ? (T)(-*h) : T(0);
   T s = T(0);
-  const int64_t n2 = n >> 1;
-  T2 *w2 = reinterpret_cast<T2 *>(w);
-  const T2 *v2 = reinterpret_cast<const T2 *>(v);
-  const T2 *x2 = reinterpret_cast<const T2 *>(x);
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n2; k += (int64_t)gridDim.x * blockDim.x) {
-    T2 wk = w2[k];
+  const int64_t nv = n / L, stride = (int64_t)gridDim.x * blockDim.x;
+  TV *wv = reinterpret_cast<TV *>(w);
+  const TV *vv = reinterpret_cast<const TV *>(v);
+  const TV *xv = reinterpret_cast<const TV *>(x);
+#pragma unroll 4
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nv; k += stride) {
+    TV wk = wv[k];
+    T *wa = reinterpret_cast<T *>(&wk);
     if (v) {
-      const T2 vk = v2[k];
-      wk.x = fma(hv, vk.x, wk.x);
-      wk.y = fma(hv, vk.y, wk.y);
-      w2[k] = wk;
+      const TV vk = vv[k];
+      const T *va = reinterpret_cast<const T *>(&vk);
+#pragma unroll
+      for (int l = 0; l < L; l++) wa[l] = fma(hv, va[l], wa[l]);
+      wv[k] = wk;
     }
     if (self) {
-      s = fma(wk.x, wk.x, s);
-      s = fma(wk.y, wk.y, s);
+#pragma unroll
+      for (int l = 0; l < L; l++) s = fma(wa[l], wa[l], s);
     } else {
-      const T2 xk = x2[k];
-      s = fma(wk.x, xk.x, s);
-      s = fma(wk.y, xk.y, s);
+      const TV xk = xv[k];
+      const T *xa = reinterpret_cast<const T *>(&xk);
+#pragma unroll
+      for (int l = 0; l < L; l++) s = fma(wa[l], xa[l], s);
     }
   }
-  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
-    T wk = w[n - 1];
-    if (v) { wk = fma(hv, v[n - 1], wk); w[n - 1] = wk; }
-    s = fma(wk, self ? wk : x[n - 1], s);
+  for (int64_t k = nv * L + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += stride) {
+    T wk = w[k];
+    if (v) { wk = fma(hv, v[k], wk); w[k] = wk; }
+    s = fma(wk, self ? wk : x[k], s);
   }
   grid_sum(s, partials, count, out, self);
 }
