@@ -16,6 +16,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <exception>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -88,10 +89,17 @@ void builder_loop(hgks_server_s *S) {
       S->to_build.pop_front();
     }
     std::string err;
-    hgks_status st = build_host_mesh(r->xyz.data(), (int64_t)r->xyz.size() / 3, r->tet.data(), (int64_t)r->tet.size() / 4,
-                                     r->bface.empty() ? nullptr : r->bface.data(), r->btag.empty() ? nullptr : r->btag.data(),
-                                     (int64_t)r->btag.size(), r->pshift.empty() ? nullptr : r->pshift.data(), r->nps, mask,
-                                     r->hm, err);
+    hgks_status st;
+    try {
+      st = build_host_mesh(r->xyz.data(), (int64_t)r->xyz.size() / 3, r->tet.data(), (int64_t)r->tet.size() / 4,
+                           r->bface.empty() ? nullptr : r->bface.data(), r->btag.empty() ? nullptr : r->btag.data(),
+                           (int64_t)r->btag.size(), r->pshift.empty() ? nullptr : r->pshift.data(), r->nps, mask, r->hm,
+                           err);
+    } catch (const std::exception &e) {     // host memory exhausted while building: the request fails
+      st = HGKS_ERR_OOM;
+      err = std::string("mesh build: ") + e.what();
+      r->hm = HostMesh{};
+    }
     std::lock_guard<std::mutex> lk(S->mu);
     r->t_built = now_s(S->t0);
     if (r->cancel) {
@@ -143,7 +151,20 @@ hgks_status admit(hgks_server_s &S, bool &changed) {
     int slot = -1;
     hgks_status st = batch_place(B, source_of(r->hm, inv), r->p, &slot);
     if (st) return st;
-    if (slot < 0) return HGKS_OK;          // the head of the queue waits for room
+    if (slot < 0) {
+      bool empty = true;
+      for (auto *q : S.running) empty = empty && q == nullptr;
+      if (!empty) return HGKS_OK;          // the head of the queue waits for room
+      // nothing runs and it still does not fit (its faces exceed the arena's): it never will
+      std::lock_guard<std::mutex> lk(S.mu);
+      S.built.pop_front();
+      r->hm = HostMesh{};
+      r->status = HGKS_ERR_OOM;
+      r->err = "mesh does not fit the server's arena";
+      r->state = Q_FAIL;
+      r->t_done = now_s(S.t0);
+      continue;
+    }
     const bool cmp = compact(B);
     std::vector<double> Qi = to_internal(r->Q0, r->perm, 5), Gi;
     if (cmp) Gi = r->G0.empty() ? std::vector<double>((size_t)15 * r->perm.size(), 0.0) : to_internal(r->G0, r->perm, 15);
