@@ -525,8 +525,9 @@ def main():
                     help="sphere: the 2.36M-tet sphere (default); batch: many problems in one batch; "
                          "serve: Poisson-arriving solves through the request server")
     ap.add_argument("--oracle-steps", type=int, default=3, help="precision workload: oracle steps on the small sphere")
-    ap.add_argument("--serve-requests", type=int, default=24)
-    ap.add_argument("--serve-rate", type=float, default=0.5, help="requests per second")
+    ap.add_argument("--serve-requests", type=int, default=96)
+    ap.add_argument("--serve-rate", type=float, default=0.4,
+                    help="requests per second (0.4: about 0.8 x the measured served capacity of ~0.5/s)")
     ap.add_argument("--serve-drop", type=float, default=1e-2)
     ap.add_argument("--serve-max-steps", type=int, default=500)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
