@@ -382,6 +382,28 @@ def test_solve_steady_parity(cuda):
     assert rel <= 1e-9, rel
 
 
+def test_converged_steady_state_parity(cuda):
+    """A converged steady state: the 3,456-tet inviscid sphere (4x4 patches, 6
+    layers) run by Algorithm 1 to a 1e-5 drop of the density residual (about 340
+    steps) on the GPU and in the oracle: the same number of steps, the same
+    residual history (relative 1e-8) and the same converged state (relative L2 1e-9)."""
+    m = I.sphere_mesh(4, 6, stretch=1.3)
+    cond = I.sphere_conditions(0.3)
+    om = O.OracleMesh(m)
+    hm = H.hgks_mesh_create(m, scheme_mask=1)
+    kw = dict(scheme=0, krylov_dim=10)
+    Q0 = I.state_from_conditions(m.n_tet, cond)
+    Qd = hm.to_internal(Q0)
+    info, hist_g, conv_g = H.hgks_solve_steady(hm, H.hgks_default_params(**{**cond, **kw}), Qd, None,
+                                               drop_tol=1e-5, max_steps=600)
+    Qo, _, hist_o, conv_o = om.solve_steady(O.make_params(**{**cond, **kw}), Q0, drop=1e-5, max_steps=600)
+    assert conv_g and conv_o and info.steps > 200
+    assert info.steps == len(hist_o) - 1
+    np.testing.assert_allclose(hist_g, hist_o, rtol=1e-8)
+    rel = np.linalg.norm(hm.to_caller(Qd) - Qo) / np.linalg.norm(Qo)
+    assert rel <= 1e-9, rel
+
+
 def test_solve_resumes_from_a_host_snapshot_bit_for_bit(cuda):
     """Checkpoint/resume: stop a solve at 6 steps, copy (Q, G) to the host and
     back, resume to 12 steps: the iterates equal the uninterrupted 12-step solve."""
