@@ -414,7 +414,9 @@ def run_serve(args, rank, world):
     from paper_2304_09485_gb300 import inputs as I
     local = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(local)
-    reqs = I.serving_requests(args.serve_requests, rate=args.serve_rate, seed=I.BASE_SEED + 500 + 1000 * rank)
+    reqs = I.serving_requests(args.serve_requests, n_min=args.serve_min_tets, n_max=args.serve_max_tets,
+                              rate=args.serve_rate, seed=I.BASE_SEED + 500 + 1000 * rank,
+                              viscous_fraction=args.serve_viscous_fraction)
     kw = dict(scheme=0, krylov_dim=10, restarts=3, jacobi_sweeps=2)
     drop, max_steps = args.serve_drop, args.serve_max_steps
     for r in reqs:
@@ -488,7 +490,8 @@ def run_serve(args, rank, world):
            "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
            "config": {"workload": f"{len(reqs)} steady-solve requests, Poisson arrivals at {args.serve_rate}/s, "
                                   f"spheres of {min(r['n_cells'] for r in reqs)}-{max(r['n_cells'] for r in reqs)} tets, "
-                                  f"half inviscid (Mach U(0.2,0.5), AoA U(0,10)), half viscous (Re logU(50,1000)), "
+                                  f"inviscid (Mach U(0.2,0.5), AoA U(0,10)) and a fraction {args.serve_viscous_fraction} "
+                                  f"viscous (Re logU(50,1000)), "
                                   f"WENO, GMRES(10)x3, Jacobi 2, CFL 10, drop {drop:g}, max {max_steps} steps",
                       "hbm_budget_gb": args.serve_budget_gb, "arena_cells": int(info.n_cells),
                       "arena_gb": info.device_bytes / 1e9},
@@ -528,6 +531,9 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=96)
     ap.add_argument("--serve-rate", type=float, default=0.4,
                     help="requests per second (0.4: about 0.8 x the measured served capacity of ~0.5/s)")
+    ap.add_argument("--serve-min-tets", type=float, default=30e3)
+    ap.add_argument("--serve-max-tets", type=float, default=250e3)
+    ap.add_argument("--serve-viscous-fraction", type=float, default=0.5)
     ap.add_argument("--serve-drop", type=float, default=1e-2)
     ap.add_argument("--serve-max-steps", type=int, default=500)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)

@@ -390,7 +390,7 @@ def batch_problems(n_problems: int = 48, n_min: float = 20e3, n_max: float = 500
 
 
 def serving_requests(n_requests: int = 24, n_min: float = 30e3, n_max: float = 250e3, rate: float = 1.0,
-                     seed: int = BASE_SEED + 500):
+                     seed: int = BASE_SEED + 500, viscous_fraction: float = 0.5):
     """Steady-solve requests with Poisson arrivals (exponential gaps of mean 1/rate s):
     half inviscid spheres (Mach ~ U(0.2, 0.5), angle of attack ~ U(0, 10) deg), half
     viscous spheres (Mach ~ U(0.2, 0.5), Re ~ log-uniform in [50, 1000]); N ~
@@ -404,7 +404,7 @@ def serving_requests(n_requests: int = 24, n_min: float = 30e3, n_max: float = 2
         N = math.exp(rng.uniform(math.log(n_min), math.log(n_max)))
         n = max(2, int(round((N / 72.0) ** (1.0 / 3.0))))
         mach = rng.uniform(0.2, 0.5)
-        if rng.random() < 0.5:
+        if rng.random() < 1.0 - viscous_fraction:
             kind = "inviscid sphere"
             cond = sphere_conditions(mach, None, aoa_deg=rng.uniform(0.0, 10.0))
             wall = BC_SLIP
