@@ -211,7 +211,10 @@ __global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const 
   unsigned valid = P.scheme == HGKS_WENO ? m.subvalid[i] : 0xFu;
   const int M = __popc(valid);
   const double gm = P.lin_weight, g0 = M ? 1.0 - gm * M : 1.0;
-  const double ig0 = 1.0 / g0;
+  const double ig0 = 1.0 / g0, iM = M ? 1.0 / M : 0.0;
+  double Th[9];                                         // face frame rows / h: scaled derivatives
+#pragma unroll
+  for (int k = 0; k < 9; k++) Th[k] = ih * T[k];
   double *out = wface + (size_t)side * 3 * kFaceState * F + f;
   for (int c = 0; c < 5; c++) {
     double mr[5];
@@ -245,18 +248,16 @@ __global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const 
     }
     // smoothness indicators in the scaled frame: beta_0 = avg |grad P0|^2 + sum of squared second derivatives
     const double H00 = 2.0 * ac[3], H11 = 2.0 * ac[4], H22 = 2.0 * ac[5], H01 = ac[6], H02 = ac[7], H12 = ac[8];
-    double beta0 = ac[0] * ac[0] + ac[1] * ac[1] + ac[2] * ac[2];
-    {
-      const double Hr[3][3] = {{H00, H01, H02}, {H01, H11, H12}, {H02, H12, H22}};
-#pragma unroll
-      for (int j = 0; j < 3; j++) {
-        double y0 = m2[0] * Hr[j][0] + m2[3] * Hr[j][1] + m2[4] * Hr[j][2];
-        double y1 = m2[3] * Hr[j][0] + m2[1] * Hr[j][1] + m2[5] * Hr[j][2];
-        double y2 = m2[4] * Hr[j][0] + m2[5] * Hr[j][1] + m2[2] * Hr[j][2];
-        beta0 += Hr[j][0] * y0 + Hr[j][1] * y1 + Hr[j][2] * y2;
-      }
-    }
-    beta0 += H00 * H00 + H11 * H11 + H22 * H22 + H01 * H01 + H02 * H02 + H12 * H12;
+    // avg |grad P0|^2 = |a|^2 + tr(M2 H^2) (M2: second moments, H symmetric)
+    const double s00 = H00 * H00, s11 = H11 * H11, s22 = H22 * H22, s01 = H01 * H01, s02 = H02 * H02, s12 = H12 * H12;
+    const double S00 = s00 + s01 + s02, S11 = s01 + s11 + s12, S22 = s02 + s12 + s22;
+    const double S01 = fma(H00, H01, fma(H01, H11, H02 * H12));
+    const double S02 = fma(H00, H02, fma(H01, H12, H02 * H22));
+    const double S12 = fma(H01, H02, fma(H11, H12, H12 * H22));
+    const double trMH2 = fma(m2[0], S00, fma(m2[1], S11, m2[2] * S22)) +
+                         2.0 * fma(m2[3], S01, fma(m2[4], S02, m2[5] * S12));
+    const double beta0 = fma(ac[0], ac[0], fma(ac[1], ac[1], ac[2] * ac[2])) + trMH2 +
+                         ((s00 + s11 + s22) + (s01 + s02 + s12));
     double kap0, kap[4];
     if (P.weights == HGKS_LINEAR || M == 0) {
       kap0 = 1.0;
@@ -269,11 +270,23 @@ __global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const 
         beta[mm] = bc[3 * mm] * bc[3 * mm] + bc[3 * mm + 1] * bc[3 * mm + 1] + bc[3 * mm + 2] * bc[3 * mm + 2];
         if (valid >> mm & 1) tz += fabs(beta0 - beta[mm]);
       }
-      tz /= M;
-      double w0 = g0 * (1.0 + tz / (beta0 + P.weno_eps)), w[4], sum = w0;
+      tz *= iM;
+      // 1 / (beta + eps) of the five stencils from one division (prefix products)
+      const double d0 = beta0 + P.weno_eps;
+      double dm[4];
+#pragma unroll
+      for (int mm = 0; mm < 4; mm++) dm[mm] = (valid >> mm & 1) ? beta[mm] + P.weno_eps : 1.0;
+      const double p1 = d0 * dm[0], p2 = p1 * dm[1], p3 = p2 * dm[2];
+      double inv = 1.0 / (p3 * dm[3]), r[4];
+      r[3] = inv * p3; inv *= dm[3];
+      r[2] = inv * p2; inv *= dm[2];
+      r[1] = inv * p1; inv *= dm[1];
+      r[0] = inv * d0;
+      const double r0 = inv * dm[0];
+      double w0 = g0 * fma(tz, r0, 1.0), w[4], sum = w0;
 #pragma unroll
       for (int mm = 0; mm < 4; mm++) {
-        w[mm] = (valid >> mm & 1) ? gm * (1.0 + tz / (beta[mm] + P.weno_eps)) : 0.0;
+        w[mm] = (valid >> mm & 1) ? gm * fma(tz, r[mm], 1.0) : 0.0;
         sum += w[mm];
       }
       double is = 1.0 / sum;
@@ -294,18 +307,23 @@ __global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const 
     double qd[6];
 #pragma unroll
     for (int k = 0; k < 6; k++) qd[k] = kap0 * ac[3 + k];
+    // P(x) = q0 + lin . x + sum_k qd_k (mono_k(x) - m2_k), nested so that the value
+    // and the gradient share their partial sums
+    const double q0m = q0 - (qd[0] * m2[0] + qd[1] * m2[1] + qd[2] * m2[2] + qd[3] * m2[3] + qd[4] * m2[4] + qd[5] * m2[5]);
 #pragma unroll
     for (int g = 0; g < 3; g++) {
       const double x = xg[3 * g], y = xg[3 * g + 1], z = xg[3 * g + 2];
-      double val = q0 + lin[0] * x + lin[1] * y + lin[2] * z + qd[0] * (x * x - m2[0]) + qd[1] * (y * y - m2[1]) +
-                   qd[2] * (z * z - m2[2]) + qd[3] * (x * y - m2[3]) + qd[4] * (x * z - m2[4]) + qd[5] * (y * z - m2[5]);
-      double gx = lin[0] + 2.0 * qd[0] * x + qd[3] * y + qd[4] * z;
-      double gy = lin[1] + 2.0 * qd[1] * y + qd[3] * x + qd[5] * z;
-      double gz = lin[2] + 2.0 * qd[2] * z + qd[4] * x + qd[5] * y;
+      const double ax = fma(qd[0], x, fma(qd[3], y, fma(qd[4], z, lin[0])));   // lin0 + qd0 x + qd3 y + qd4 z
+      const double by = fma(qd[1], y, fma(qd[5], z, lin[1]));                  // lin1 + qd1 y + qd5 z
+      const double cz = fma(qd[2], z, lin[2]);                                 // lin2 + qd2 z
+      const double val = fma(x, ax, fma(y, by, fma(z, cz, q0m)));
+      const double gx = fma(qd[0], x, ax);
+      const double gy = fma(qd[3], x, fma(qd[1], y, by));
+      const double gz = fma(qd[4], x, fma(qd[5], y, fma(qd[2], z, cz)));
       double *o = out + (size_t)g * kFaceState * F;
       o[(size_t)c * F] = val;
 #pragma unroll
-      for (int k = 0; k < 3; k++) o[(size_t)(5 + 5 * k + c) * F] = ih * (T[3 * k] * gx + T[3 * k + 1] * gy + T[3 * k + 2] * gz);
+      for (int k = 0; k < 3; k++) o[(size_t)(5 + 5 * k + c) * F] = Th[3 * k] * gx + Th[3 * k + 1] * gy + Th[3 * k + 2] * gz;
     }
   }
 }
@@ -313,21 +331,7 @@ __global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const 
 // ------------------------------------------------------------------------
 // 3. gas-kinetic flux
 // ------------------------------------------------------------------------
-// moments of the normalised Maxwellian: u (full or half range) up to u^6,
-// v and w up to the 5th power, xi^2 and xi^4
-struct Mom { double u[7], v[6], w[6], xi2, xi4; };
-
-__device__ __forceinline__ void mom_vw(const Prim &p, double K, Mom &m) {
-  const double il = p.il;   // 1/(2 lambda)
-  m.v[0] = 1.0; m.v[1] = p.V; m.w[0] = 1.0; m.w[1] = p.W;
-#pragma unroll
-  for (int n = 0; n < 4; n++) {
-    m.v[n + 2] = p.V * m.v[n + 1] + (n + 1) * il * m.v[n];
-    m.w[n + 2] = p.W * m.w[n + 1] + (n + 1) * il * m.w[n];
-  }
-  m.xi2 = K * il;
-  m.xi4 = (K * K + 2.0 * K) * il * il;
-}
+// moments of the normalised Maxwellian in u (full or half range) up to u^6
 __device__ __forceinline__ void mom_u_full(const Prim &p, double *u) {
   const double il = p.il;
   u[0] = 1.0; u[1] = p.U;
@@ -343,67 +347,91 @@ __device__ __forceinline__ void mom_u_half(const Prim &p, double sgn, double *u)
   for (int n = 0; n < 5; n++) u[n + 2] = p.U * u[n + 1] + (n + 1) * il * u[n];
 }
 
-// out += s <u^A v^B w^C psi>
-template <int A, int B, int C>
-__device__ __forceinline__ void acc_psi(const double *mu, const double *mv, const double *mw, double xi2, double s, double *out) {
-  const double vw = mv[B] * mw[C];
-  const double g = mu[A] * vw;
-  out[0] = fma(s, g, out[0]);
-  out[1] = fma(s, mu[A + 1] * vw, out[1]);
-  out[2] = fma(s, mu[A] * mv[B + 1] * mw[C], out[2]);
-  out[3] = fma(s, mu[A] * mv[B] * mw[C + 1], out[3]);
-  out[4] = fma(0.5 * s, mu[A + 2] * vw + mu[A] * (mv[B + 2] * mw[C] + mv[B] * mw[C + 2]) + xi2 * g, out[4]);
-}
-// out += s <u^A v^B w^C xi^2 psi>
-template <int A, int B, int C>
-__device__ __forceinline__ void acc_psi_xi(const double *mu, const double *mv, const double *mw, double xi2, double xi4, double s,
-                                           double *out) {
-  const double vw = mv[B] * mw[C];
-  const double g = mu[A] * vw;
-  const double sx = s * xi2;
-  out[0] = fma(sx, g, out[0]);
-  out[1] = fma(sx, mu[A + 1] * vw, out[1]);
-  out[2] = fma(sx, mu[A] * mv[B + 1] * mw[C], out[2]);
-  out[3] = fma(sx, mu[A] * mv[B] * mw[C + 1], out[3]);
-  out[4] = fma(0.5 * s, xi2 * (mu[A + 2] * vw + mu[A] * (mv[B + 2] * mw[C] + mv[B] * mw[C + 2])) + xi4 * g, out[4]);
-}
-// out += s <u^A v^B w^C (a.psi) psi>
-template <int A, int B, int C>
-__device__ __forceinline__ void acc_apsi(const double *mu, const Mom &m, const double *a, double s, double *out) {
-  acc_psi<A, B, C>(mu, m.v, m.w, m.xi2, s * a[0], out);
-  acc_psi<A + 1, B, C>(mu, m.v, m.w, m.xi2, s * a[1], out);
-  acc_psi<A, B + 1, C>(mu, m.v, m.w, m.xi2, s * a[2], out);
-  acc_psi<A, B, C + 1>(mu, m.v, m.w, m.xi2, s * a[3], out);
-  const double h = 0.5 * s * a[4];
-  acc_psi<A + 2, B, C>(mu, m.v, m.w, m.xi2, h, out);
-  acc_psi<A, B + 2, C>(mu, m.v, m.w, m.xi2, h, out);
-  acc_psi<A, B, C + 2>(mu, m.v, m.w, m.xi2, h, out);
-  acc_psi_xi<A, B, C>(mu, m.v, m.w, m.xi2, m.xi4, h, out);
-}
-// out += s * sum_d <u_d (a_d.psi) psi> (u_d = u, v, w): the moment of (a . u_vec) psi
-__device__ __forceinline__ void acc_slope_u(const double *mu, const Mom &m, const double (*a)[5], double s, double *out) {
-  acc_apsi<1, 0, 0>(mu, m, a[0], s, out);
-  acc_apsi<0, 1, 0>(mu, m, a[1], s, out);
-  acc_apsi<0, 0, 1>(mu, m, a[2], s, out);
-}
-// out += s * sum_d <u u_d (a_d.psi) psi>
-__device__ __forceinline__ void acc_u_slope_u(const double *mu, const Mom &m, const double (*a)[5], double s, double *out) {
-  acc_apsi<2, 0, 0>(mu, m, a[0], s, out);
-  acc_apsi<1, 1, 0>(mu, m, a[1], s, out);
-  acc_apsi<1, 0, 1>(mu, m, a[2], s, out);
+// The v, w and xi moments are taken in the frame that moves with the tangential
+// velocity (V, W) of the Maxwellian: v' = v - V, w' = w - W. There they are the
+// central moments of a Gaussian of variance il = 1 / (2 lambda),
+//   <v'^b> = (b - 1)!! il^(b/2) for even b, 0 for odd b,   <xi^2> = K il,
+//   <xi^4> = (K^2 + 2K) il^2,
+// so every product with an odd tangential power vanishes and is dropped at
+// compile time. The moment vectors follow from the Galilean transform psi = L psi',
+//   psi_2 = psi'_2 + V psi'_0,   psi_3 = psi'_3 + W psi'_0,
+//   psi_4 = psi'_4 + V psi'_2 + W psi'_3 + (V^2 + W^2)/2 psi'_0,
+// as <phi psi> = L <phi psi'>; a slope enters as a . psi = (L^T a) . psi'.
+struct Frame { double il, il2, K; };
+
+// (b - 1)!!: <v'^b> / il^(b/2) for even b
+__host__ __device__ constexpr double cmom(int b) { return b <= 0 ? 1.0 : (b - 1) * cmom(b - 2); }
+template <int n>
+__device__ __forceinline__ double il_pow(const Frame &f) {
+  static_assert(n >= 0 && n <= 3, "tangential degree");
+  if constexpr (n == 0) return 1.0;
+  else if constexpr (n == 1) return f.il;
+  else if constexpr (n == 2) return f.il2;
+  else return f.il2 * f.il;
 }
 
-// Slope a with <a> = rho * dq in closed form (dq normalised by rho); K + 3 = 2 / (gamma - 1),
-// so (K + 3) / (4 lam) = il / (gamma - 1) and 4 lam^2 / (K + 3) = 2 (gamma - 1) lam^2
-__device__ __forceinline__ void slope(const Prim &p, double g1, double ig1, const double *dq, double *a) {
-  const double q2 = p.U * p.U + p.V * p.V + p.W * p.W, e = p.il * ig1;
-  const double R4 = 2.0 * dq[4] - (q2 + 2.0 * e) * dq[0];
-  const double R1 = dq[1] - p.U * dq[0], R2 = dq[2] - p.V * dq[0], R3 = dq[3] - p.W * dq[0];
-  a[4] = 2.0 * g1 * p.lam * p.lam * (R4 - 2.0 * p.U * R1 - 2.0 * p.V * R2 - 2.0 * p.W * R3);
-  a[3] = 2.0 * p.lam * R3 - p.W * a[4];
-  a[2] = 2.0 * p.lam * R2 - p.V * a[4];
-  a[1] = 2.0 * p.lam * R1 - p.U * a[4];
-  a[0] = dq[0] - p.U * a[1] - p.V * a[2] - p.W * a[3] - 0.5 * a[4] * (q2 + 2.0 * e);
+// out += s <u^A v'^B w'^C xi^(2E) psi'>   (E = 0 or 1; mu: moments of u)
+template <int A, int B, int C, int E>
+__device__ __forceinline__ void acc_c(const double *mu, const Frame &f, double s, double *out) {
+  constexpr bool eb = B % 2 == 0, ec = C % 2 == 0;
+  // the moment products do not depend on s: written this way they are shared by
+  // every call with the same (A, B, C, E)
+  if constexpr (eb && ec) {
+    double t = (cmom(B) * cmom(C)) * il_pow<(B + C) / 2>(f);   // <v'^B w'^C>
+    if constexpr (E == 1) t *= f.K * f.il;                       // <xi^2>
+    // <... psi'_4> = 1/2 <v'^B w'^C xi^2E> (mu[A+2] + (B + C + 2 + 2E + K) il mu[A])
+    constexpr double k4 = B + C + 2 + 2 * E;
+    out[0] = fma(s, t * mu[A], out[0]);
+    out[1] = fma(s, t * mu[A + 1], out[1]);
+    out[4] = fma(s, (0.5 * t) * fma((k4 + f.K) * f.il, mu[A], mu[A + 2]), out[4]);
+  } else if constexpr (!eb && ec) {
+    double t = (cmom(B + 1) * cmom(C)) * il_pow<(B + C + 1) / 2>(f);
+    if constexpr (E == 1) t *= f.K * f.il;
+    out[2] = fma(s, t * mu[A], out[2]);
+  } else if constexpr (eb && !ec) {
+    double t = (cmom(B) * cmom(C + 1)) * il_pow<(B + C + 1) / 2>(f);
+    if constexpr (E == 1) t *= f.K * f.il;
+    out[3] = fma(s, t * mu[A], out[3]);
+  }
+}
+// out += s <u^A v'^B w'^C (a . psi') psi'>
+template <int A, int B, int C>
+__device__ __forceinline__ void acc_capsi(const double *mu, const Frame &f, const double *a, double s, double *out) {
+  acc_c<A, B, C, 0>(mu, f, s * a[0], out);
+  acc_c<A + 1, B, C, 0>(mu, f, s * a[1], out);
+  acc_c<A, B + 1, C, 0>(mu, f, s * a[2], out);
+  acc_c<A, B, C + 1, 0>(mu, f, s * a[3], out);
+  const double h = 0.5 * s * a[4];
+  acc_c<A + 2, B, C, 0>(mu, f, h, out);
+  acc_c<A, B + 2, C, 0>(mu, f, h, out);
+  acc_c<A, B, C + 2, 0>(mu, f, h, out);
+  acc_c<A, B, C, 1>(mu, f, h, out);
+}
+// out += s L x (x in the tangential frame of p)
+__device__ __forceinline__ void acc_from_frame(const Prim &p, const double *x, double s, double *out) {
+  const double h = 0.5 * (p.V * p.V + p.W * p.W);
+  out[0] = fma(s, x[0], out[0]);
+  out[1] = fma(s, x[1], out[1]);
+  out[2] = fma(s, fma(p.V, x[0], x[2]), out[2]);
+  out[3] = fma(s, fma(p.W, x[0], x[3]), out[3]);
+  out[4] = fma(s, x[4] + p.V * x[2] + p.W * x[3] + h * x[0], out[4]);
+}
+
+// Slope a' (tangential frame) with <a . psi> = dq (moments of the Maxwellian
+// normalised by rho; a is linear in dq, so dq = dW gives rho a): L^{-1} dq, then
+// the closed form of the 5x5 moment system at V = W = 0. K + 3 = 2 / (gamma - 1),
+// so (K + 3) / (4 lam) = il / (gamma - 1) and 4 lam^2 / (K + 3) = 2 (gamma - 1) lam^2.
+__device__ __forceinline__ void slope_c(const Prim &p, double g1, double ig1, const double *dq, double *a) {
+  const double d2 = dq[2] - p.V * dq[0], d3 = dq[3] - p.W * dq[0];
+  const double d4 = dq[4] - p.V * d2 - p.W * d3 - 0.5 * (p.V * p.V + p.W * p.W) * dq[0];
+  const double e2 = p.U * p.U + 2.0 * p.il * ig1;
+  const double R1 = dq[1] - p.U * dq[0];
+  const double tl = 2.0 * p.lam;
+  a[4] = 2.0 * g1 * p.lam * p.lam * (2.0 * d4 - e2 * dq[0] - 2.0 * p.U * R1);
+  a[3] = tl * d3;
+  a[2] = tl * d2;
+  a[1] = tl * R1 - p.U * a[4];
+  a[0] = dq[0] - p.U * a[1] - 0.5 * a[4] * e2;
 }
 
 // boundary state outside a boundary face (face frame, x = outward normal):
@@ -483,20 +511,26 @@ __device__ __forceinline__ void acc_jvp(const double *W, double ir, double gamma
 
 // Flux (time average over [0, dt] of int u psi f dXi, Eq. (flux)) and, if Qp
 // is not NULL, the point value int psi f dXi at t* (Eq. (point)). Face frame.
+// The moment sums of each Maxwellian are taken in its own tangential frame.
 __device__ void gks_flux(const hgks_params &P, const double *Wl, const double *dWl, const double *Wr, const double *dWr,
                          double dt, double *F, double *Qp) {
   const double gam = P.gamma, g1 = gam - 1.0, ig1 = 1.0 / g1, K = (5.0 - 3.0 * gam) * ig1;
   const Prim pl = to_prim(Wl, gam), pr = to_prim(Wr, gam);
-  Mom ml, mr;
-  mom_vw(pl, K, ml);
-  mom_vw(pr, K, mr);
   double uhl[7], uhr[7];
   mom_u_half(pl, 1.0, uhl);
   mom_u_half(pr, -1.0, uhr);
+  const Frame fl{pl.il, pl.il * pl.il, K}, fr{pr.il, pr.il * pr.il, K};
   // compatibility condition: Q0 = int_{u>0} psi g_l + int_{u<0} psi g_r
   double Q0[5] = {0, 0, 0, 0, 0};
-  acc_psi<0, 0, 0>(uhl, ml.v, ml.w, ml.xi2, pl.rho, Q0);
-  acc_psi<0, 0, 0>(uhr, mr.v, mr.w, mr.xi2, pr.rho, Q0);
+  {
+    double m[5] = {0, 0, 0, 0, 0};
+    acc_c<0, 0, 0, 0>(uhl, fl, 1.0, m);
+    acc_from_frame(pl, m, pl.rho, Q0);
+#pragma unroll
+    for (int c = 0; c < 5; c++) m[c] = 0.0;
+    acc_c<0, 0, 0, 0>(uhr, fr, 1.0, m);
+    acc_from_frame(pr, m, pr.rho, Q0);
+  }
   const Prim p0 = to_prim(Q0, gam);
   // collision time (Sec. 5)
   const double prl = pl.rho * pl.il, prr = pr.rho * pr.il, pp0 = p0.rho * p0.il;
@@ -510,84 +544,98 @@ __device__ void gks_flux(const hgks_params &P, const double *Wl, const double *d
   const double c4 = tau * (1.0 - eta);
   const double c5 = 2.0 * tau * tau * (1.0 - eta) - tau * dt * eta;
   const bool want_pt = Qp != nullptr, prandtl = P.Pr != 1.0;
-  const double ts = P.tstar_end ? dt : 0.0, es = exp(-ts * itau);
+  const double ts = P.tstar_end ? dt : 0.0, es = want_pt || prandtl ? exp(-ts * itau) : 1.0;
   double Fl[5] = {0, 0, 0, 0, 0}, Wb[5] = {0, 0, 0, 0, 0}, Pt[5] = {0, 0, 0, 0, 0};
   double dWs[15];
 #pragma unroll
   for (int k = 0; k < 15; k++) dWs[k] = 0.5 * (dWl[k] + dWr[k]);
   // the two initial distributions g_l (u > 0) and g_r (u < 0)
-#pragma unroll 1
+#pragma unroll
   for (int s = 0; s < 2; s++) {
     const Prim &pk = s == 0 ? pl : pr;
-    const Mom &mk = s == 0 ? ml : mr;
+    const Frame &fk = s == 0 ? fl : fr;
     const double *uh = s == 0 ? uhl : uhr;
     const double *dW = s == 0 ? dWl : dWr;
     const double irho = pk.ir;
+    // rho a_d and rho A in the tangential frame of g_k (the slope is linear in dW, so
+    // every moment sum below comes out multiplied by rho)
     double a[3][5], A[5];
 #pragma unroll
-    for (int d = 0; d < 3; d++) {
-      double dq[5];
-#pragma unroll
-      for (int c = 0; c < 5; c++) dq[c] = dW[5 * d + c] * irho;
-      slope(pk, g1, ig1, dq, a[d]);
-    }
+    for (int d = 0; d < 3; d++) slope_c(pk, g1, ig1, dW + 5 * d, a[d]);
     // <a_n u + a_t1 v + a_t2 w + A> = 0 with <u_d (a_d.psi) psi> = J_d dW_d
     double rhs[5] = {0, 0, 0, 0, 0};
     const double *Wk = s == 0 ? Wl : Wr;
 #pragma unroll
-    for (int d = 0; d < 3; d++) acc_jvp(Wk, irho, gam, d, dW + 5 * d, -irho, rhs);
-    slope(pk, g1, ig1, rhs, A);
-    // flux terms of g_k
-    double fk[5] = {0, 0, 0, 0, 0};
-    acc_psi<1, 0, 0>(uh, mk.v, mk.w, mk.xi2, c4, fk);
-    acc_u_slope_u(uh, mk, a, -c5, fk);
-    acc_apsi<1, 0, 0>(uh, mk, A, -tau * c4, fk);
+    for (int d = 0; d < 3; d++) acc_jvp(Wk, irho, gam, d, dW + 5 * d, -1.0, rhs);
+    slope_c(pk, g1, ig1, rhs, A);
+    // flux terms of g_k: c4 <u psi> - c5 sum_d <u u_d (a_d.psi) psi> - tau c4 <u (A.psi) psi>,
+    // with v = v' + V, w = w' + W folded into the coefficients of <u (b.psi') psi'>
+    double b[5], fkp[5] = {0, 0, 0, 0, 0};
 #pragma unroll
-    for (int c = 0; c < 5; c++) Fl[c] = fma(pk.rho, fk[c], Fl[c]);
+    for (int c = 0; c < 5; c++) b[c] = -tau * c4 * A[c] - c5 * (pk.V * a[1][c] + pk.W * a[2][c]);
+    b[0] += c4 * pk.rho;
+    acc_capsi<1, 0, 0>(uh, fk, b, 1.0, fkp);
+    acc_capsi<2, 0, 0>(uh, fk, a[0], -c5, fkp);
+    acc_capsi<1, 1, 0>(uh, fk, a[1], -c5, fkp);
+    acc_capsi<1, 0, 1>(uh, fk, a[2], -c5, fkp);
+    acc_from_frame(pk, fkp, 1.0, Fl);
     if (want_pt || prandtl) {
-      double m0[5] = {0, 0, 0, 0, 0}, ma[5] = {0, 0, 0, 0, 0}, mA[5] = {0, 0, 0, 0, 0};
-      acc_psi<0, 0, 0>(uh, mk.v, mk.w, mk.xi2, 1.0, m0);
-      acc_slope_u(uh, mk, a, 1.0, ma);
-      acc_apsi<0, 0, 0>(uh, mk, A, 1.0, mA);
+      // m0 = <psi>, ma = sum_d <u_d (a_d.psi) psi>, mA = <(A.psi) psi> (all times rho)
+      double m0[5] = {0, 0, 0, 0, 0}, ma[5] = {0, 0, 0, 0, 0}, mA[5] = {0, 0, 0, 0, 0}, vw[5];
+      acc_c<0, 0, 0, 0>(uh, fk, pk.rho, m0);
+#pragma unroll
+      for (int c = 0; c < 5; c++) vw[c] = pk.V * a[1][c] + pk.W * a[2][c];
+      acc_capsi<0, 0, 0>(uh, fk, vw, 1.0, ma);
+      acc_capsi<1, 0, 0>(uh, fk, a[0], 1.0, ma);
+      acc_capsi<0, 1, 0>(uh, fk, a[1], 1.0, ma);
+      acc_capsi<0, 0, 1>(uh, fk, a[2], 1.0, ma);
+      acc_capsi<0, 0, 0>(uh, fk, A, 1.0, mA);
+      double pt[5], wb[5];
 #pragma unroll
       for (int c = 0; c < 5; c++) {
-        Pt[c] += pk.rho * es * (m0[c] - (tau + ts) * ma[c] - tau * mA[c]);
-        Wb[c] += pk.rho * (c4 * m0[c] - c5 * ma[c] - tau * c4 * mA[c]);
+        pt[c] = es * (m0[c] - (tau + ts) * ma[c] - tau * mA[c]);
+        wb[c] = c4 * m0[c] - c5 * ma[c] - tau * c4 * mA[c];
       }
+      acc_from_frame(pk, pt, 1.0, Pt);
+      acc_from_frame(pk, wb, 1.0, Wb);
     }
   }
   // the equilibrium part g0 with slopes from the average of both sides' gradients
   {
-    Mom m0;
-    mom_vw(p0, K, m0);
+    const Frame f0{p0.il, p0.il * p0.il, K};
     double uf[7];
     mom_u_full(p0, uf);
     const double irho = p0.ir;
-    double a[3][5];
+    double a[3][5];                       // rho_0 abar_d, tangential frame of g0
 #pragma unroll
-    for (int d = 0; d < 3; d++) {
-      double dq[5];
-#pragma unroll
-      for (int c = 0; c < 5; c++) dq[c] = dWs[5 * d + c] * irho;
-      slope(p0, g1, ig1, dq, a[d]);
-    }
-    // S0 = <(abar . u_vec) psi> = sum_d J_d(Q0) dQ0_d; <Abar psi> = -S0; <u Abar psi> = -J_x(Q0) S0
+    for (int d = 0; d < 3; d++) slope_c(p0, g1, ig1, dWs + 5 * d, a[d]);
+    // rho_0 S0 = rho_0 <(abar . u_vec) psi> = sum_d J_d(Q0) dQ0_d; <Abar psi> = -S0;
+    // <u Abar psi> = -J_x(Q0) S0
     double S0[5] = {0, 0, 0, 0, 0};
 #pragma unroll
-    for (int d = 0; d < 3; d++) acc_jvp(Q0, irho, gam, d, dWs + 5 * d, irho, S0);
-    double f0[5] = {0, 0, 0, 0, 0};
-    acc_psi<1, 0, 0>(uf, m0.v, m0.w, m0.xi2, c1, f0);
-    acc_u_slope_u(uf, m0, a, c2, f0);
-    acc_jvp(Q0, irho, gam, 0, S0, -c3, f0);
+    for (int d = 0; d < 3; d++) acc_jvp(Q0, irho, gam, d, dWs + 5 * d, 1.0, S0);
+    // rho_0 (c1 <u psi> + c2 sum_d <u u_d (abar_d.psi) psi> - c3 J_x(Q0) S0)
+    double b[5], f0p[5] = {0, 0, 0, 0, 0};
 #pragma unroll
-    for (int c = 0; c < 5; c++) Fl[c] = fma(p0.rho, f0[c], Fl[c]);
+    for (int c = 0; c < 5; c++) b[c] = c2 * (p0.V * a[1][c] + p0.W * a[2][c]);
+    b[0] += c1 * p0.rho;
+    acc_capsi<1, 0, 0>(uf, f0, b, 1.0, f0p);
+    acc_capsi<2, 0, 0>(uf, f0, a[0], c2, f0p);
+    acc_capsi<1, 1, 0>(uf, f0, a[1], c2, f0p);
+    acc_capsi<1, 0, 1>(uf, f0, a[2], c2, f0p);
+    double f0v[5] = {0, 0, 0, 0, 0};
+    acc_from_frame(p0, f0p, 1.0, f0v);
+    acc_jvp(Q0, irho, gam, 0, S0, -c3, f0v);
+#pragma unroll
+    for (int c = 0; c < 5; c++) Fl[c] += f0v[c];
     if (want_pt || prandtl) {
-      double g0m[5] = {0, 0, 0, 0, 0};
-      acc_psi<0, 0, 0>(uf, m0.v, m0.w, m0.xi2, 1.0, g0m);
+      double g0p[5] = {0, 0, 0, 0, 0}, g0m[5] = {0, 0, 0, 0, 0};     // rho_0 <psi>
+      acc_c<0, 0, 0, 0>(uf, f0, p0.rho, g0p);
+      acc_from_frame(p0, g0p, 1.0, g0m);
 #pragma unroll
       for (int c = 0; c < 5; c++) {
-        Pt[c] += p0.rho * ((1.0 - es) * g0m[c] + ((ts + tau) * es - tau) * S0[c] - (ts - tau + tau * es) * S0[c]);
-        Wb[c] += p0.rho * (c1 * g0m[c] + c2 * S0[c] - c3 * S0[c]);
+        Pt[c] += (1.0 - es) * g0m[c] + ((ts + tau) * es - tau) * S0[c] - (ts - tau + tau * es) * S0[c];
+        Wb[c] += c1 * g0m[c] + c2 * S0[c] - c3 * S0[c];
       }
     }
   }
