@@ -68,7 +68,7 @@ MeshSource source_of(const Mesh &a) {
   s.N = a.N; s.F = a.F; s.Fb = a.Fb; s.schemes = a.schemes;
   s.vol = d.vol; s.inv_vol = d.inv_vol; s.h = d.h; s.m2 = d.m2; s.xg = d.xg;
   s.cnb = d.cnb; s.cface = d.cface; s.sten = d.sten; s.fl = d.fl; s.fr = d.fr; s.subvalid = d.subvalid;
-  s.X0 = d.X0; s.Xm = d.Xm; s.H0 = d.H0; s.Hm = d.Hm; s.ftag = d.ftag; s.fT = d.fT; s.fS = d.fS; s.fdist = d.fdist;
+  s.X0 = d.X0; s.Xs = d.Xs; s.ssl = d.ssl; s.H0 = d.H0; s.Hm = d.Hm; s.ftag = d.ftag; s.fT = d.fT; s.fS = d.fS; s.fdist = d.fdist;
   return s;
 }
 MeshSource source_of(const HostMesh &hm, std::vector<double> &inv) {
@@ -80,7 +80,7 @@ MeshSource source_of(const HostMesh &hm, std::vector<double> &inv) {
   auto P = [](const auto &v) { return v.empty() ? nullptr : v.data(); };
   s.vol = P(hm.vol); s.inv_vol = inv.data(); s.h = P(hm.h); s.m2 = P(hm.m2); s.xg = P(hm.xg);
   s.cnb = P(hm.cnb); s.cface = P(hm.cface); s.sten = P(hm.sten); s.fl = P(hm.fl); s.fr = P(hm.fr);
-  s.subvalid = P(hm.subvalid); s.X0 = P(hm.X0); s.Xm = P(hm.Xm); s.H0 = P(hm.H0); s.Hm = P(hm.Hm);
+  s.subvalid = P(hm.subvalid); s.X0 = P(hm.X0); s.Xs = P(hm.Xs); s.ssl = P(hm.ssl); s.H0 = P(hm.H0); s.Hm = P(hm.Hm);
   s.ftag = P(hm.ftag); s.fT = P(hm.fT); s.fS = P(hm.fS); s.fdist = P(hm.fdist);
   return s;
 }
@@ -150,7 +150,7 @@ int64_t arena_bytes(int64_t cells, int64_t faces, const hgks_params &p, int sche
   const bool mixed = p.precision == HGKS_MIXED, hw = p.scheme == HGKS_HWENO;
   int64_t c = 0;
   c += 8 * (3 + 6 + 36) + 4 * 8 + 1 + 2;                       // geometry, neighbours, faces, mesh id
-  if (schemes & 1) c += 4 * kBig + 8 * (9 + 12) * kBig;         // big stencil and its matrices
+  if (schemes & 1) c += 4 * kBig + 8 * 9 * kBig + 8 * 12 * kSubK + 4 * 4;   // big stencil, its matrices, sub-stencil slots
   if (schemes & 2) c += 8 * (9 * 19 + 12 * 7);                  // compact matrices
   c += 8 * (5 + (hw ? 15 : 0));                                 // Q, G
   c += 8 * (kCoef + 1 + 100 + 2 + 5 + 15 + 5 + 15);             // coef, dt, off, dval/dinv, R, Gnew, dQ, w/t/t2
@@ -225,7 +225,7 @@ hgks_status batch_new(int device, int64_t cell_cap, int64_t face_cap, int nslot,
       (s = balloc(M, &d.fr, F)) || (s = balloc(M, &d.ftag, F)) || (s = balloc(M, &d.fT, 9 * F)) ||
       (s = balloc(M, &d.fS, F)) || (s = balloc(M, &d.fdist, F)) ||
       (weno && ((s = balloc(M, &d.sten, (size_t)kBig * N)) || (s = balloc(M, &d.X0, (size_t)9 * kBig * N)) ||
-                (s = balloc(M, &d.Xm, (size_t)12 * kBig * N)))) ||
+                (s = balloc(M, &d.Xs, (size_t)12 * kSubK * N)) || (s = balloc(M, &d.ssl, (size_t)4 * N)))) ||
       (hweno && ((s = balloc(M, &d.H0, (size_t)9 * 19 * N)) || (s = balloc(M, &d.Hm, (size_t)12 * 7 * N)))))
     return bail(s);
   BatchState &bs = B->bs;
@@ -261,7 +261,8 @@ hgks_status batch_new(int device, int64_t cell_cap, int64_t face_cap, int nslot,
   if (weno) {
     cudaMemsetAsync(d.sten, 0xff, sizeof(int) * kBig * N, st);
     cudaMemsetAsync(d.X0, 0, sizeof(double) * 9 * kBig * N, st);
-    cudaMemsetAsync(d.Xm, 0, sizeof(double) * 12 * kBig * N, st);
+    cudaMemsetAsync(d.Xs, 0, sizeof(double) * 12 * kSubK * N, st);
+    cudaMemsetAsync(d.ssl, 0, sizeof(unsigned) * 4 * N, st);
   }
   if (hweno) {
     cudaMemsetAsync(d.H0, 0, sizeof(double) * 9 * 19 * N, st);
@@ -325,7 +326,7 @@ hgks_status batch_place(Batch &B, const MeshSource &src, const hgks_params &p, i
       (s = copy_in(d.ftag, F, f0, src.ftag, fk, 1, st)) || (s = copy_in(d.fT, F, f0, src.fT, fk, 9, st)) ||
       (s = copy_in(d.fS, F, f0, src.fS, fk, 1, st)) || (s = copy_in(d.fdist, F, f0, src.fdist, fk, 1, st)) ||
       (weno && ((s = copy_in(d.sten, N, c0, src.sten, nk, kBig, st)) || (s = copy_in(d.X0, N, c0, src.X0, nk, 9 * kBig, st)) ||
-                (s = copy_in(d.Xm, N, c0, src.Xm, nk, 12 * kBig, st)))) ||
+                (s = copy_in(d.Xs, N, c0, src.Xs, nk, 12 * kSubK, st)) || (s = copy_in(d.ssl, N, c0, src.ssl, nk, 4, st)))) ||
       (hweno && ((s = copy_in(d.H0, N, c0, src.H0, nk, 9 * 19, st)) || (s = copy_in(d.Hm, N, c0, src.Hm, nk, 12 * 7, st)))))
     return s;
   // padding cells of the range: no neighbours

@@ -25,7 +25,8 @@ struct MeshSource {
   const double *vol = nullptr, *inv_vol = nullptr, *h = nullptr, *m2 = nullptr, *xg = nullptr;
   const int *cnb = nullptr, *cface = nullptr, *sten = nullptr, *fl = nullptr, *fr = nullptr;
   const unsigned char *subvalid = nullptr;
-  const double *X0 = nullptr, *Xm = nullptr, *H0 = nullptr, *Hm = nullptr;
+  const double *X0 = nullptr, *Xs = nullptr, *H0 = nullptr, *Hm = nullptr;
+  const unsigned *ssl = nullptr;
   const signed char *ftag = nullptr;
   const double *fT = nullptr, *fS = nullptr, *fdist = nullptr;
   int schemes = 0;

@@ -290,7 +290,7 @@ hgks_status hgks_mesh_create(const double *xyz, int64_t n_vert, const int64_t *t
   if ((st = upload(m, &d.vol, hm.vol)) || (st = upload(m, &d.inv_vol, inv_vol)) || (st = upload(m, &d.h, hm.h)) ||
       (st = upload(m, &d.m2, hm.m2)) || (st = upload(m, &d.cnb, hm.cnb)) || (st = upload(m, &d.cface, hm.cface)) ||
       (st = upload(m, &d.xg, hm.xg)) || (st = upload(m, &d.sten, hm.sten)) || (st = upload(m, &d.X0, hm.X0)) ||
-      (st = upload(m, &d.Xm, hm.Xm)) || (st = upload(m, &d.subvalid, hm.subvalid)) || (st = upload(m, &d.H0, hm.H0)) ||
+      (st = upload(m, &d.Xs, hm.Xs)) || (st = upload(m, &d.ssl, hm.ssl)) || (st = upload(m, &d.subvalid, hm.subvalid)) || (st = upload(m, &d.H0, hm.H0)) ||
       (st = upload(m, &d.Hm, hm.Hm)) || (st = upload(m, &d.fl, hm.fl)) || (st = upload(m, &d.fr, hm.fr)) ||
       (st = upload(m, &d.ftag, hm.ftag)) || (st = upload(m, &d.fT, hm.fT)) || (st = upload(m, &d.fS, hm.fS)) ||
       (st = upload(m, &d.fdist, hm.fdist)))

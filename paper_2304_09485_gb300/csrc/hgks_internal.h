@@ -18,6 +18,7 @@
 namespace hgks {
 
 constexpr int kBig = 16;        // non-compact big stencil size (excluding the target)
+constexpr int kSubK = 6;        // cells of a non-compact sub-stencil (three face neighbours + three)
 constexpr int kSub = 4;         // sub-stencils per tetrahedron
 constexpr int kCoefA = 45;      // quadratic coefficients: 9 x 5
 constexpr int kCoef = 105;      // + 4 linear sub-polynomials: 4 x 3 x 5
@@ -34,7 +35,8 @@ struct DevMesh {
   // non-compact (WENO)
   int *sten = nullptr;           // [16][N] big stencil, -1 padded
   double *X0 = nullptr;          // [9*16][N] a_d = sum_k X0[d*16+k] (Q_k - Q_i)
-  double *Xm = nullptr;          // [4*3*16][N] b_j^m = sum_k Xm[(m*3+j)*16+k] (Q_k - Q_i)
+  double *Xs = nullptr;          // [4*3*6][N] b_j^m = sum_s Xs[(m*3+j)*6+s] (Q_k(s) - Q_i)
+  unsigned *ssl = nullptr;       // [4][N] k(s) of sub-stencil m: 4-bit big-stencil slots, s = 0..5, ascending
   unsigned char *subvalid = nullptr;  // [N] bit m: sub-stencil m used
   // compact (HWENO)
   double *H0 = nullptr;          // [9*19][N] a_d from (dQ of slots 0..3, G_i, G of slots 0..3)
@@ -148,7 +150,8 @@ struct HostMesh {
   std::vector<int> cnb, cface, sten, fl, fr;
   std::vector<signed char> ftag;
   std::vector<unsigned char> subvalid;
-  std::vector<double> X0, Xm, H0, Hm, fT, fS, fdist;
+  std::vector<double> X0, Xs, H0, Hm, fT, fS, fdist;
+  std::vector<unsigned> ssl;
 };
 hgks_status build_host_mesh(const double *xyz, int64_t nv, const int64_t *tet, int64_t nt,
                             const int64_t *bface, const int32_t *btag, int64_t nb,

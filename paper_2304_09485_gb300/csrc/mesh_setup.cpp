@@ -334,7 +334,8 @@ hgks_status build_host_mesh(const double *xyz, int64_t nv, const int64_t *tet, i
   if (weno) {
     hm.sten.assign((size_t)kBig * N, -1);
     hm.X0.assign((size_t)9 * kBig * N, 0.0);
-    hm.Xm.assign((size_t)4 * 3 * kBig * N, 0.0);
+    hm.Xs.assign((size_t)4 * 3 * kSubK * N, 0.0);
+    hm.ssl.assign((size_t)4 * N, 0u);
     hm.subvalid.assign(N, 0);
   }
   if (hweno) {
@@ -423,9 +424,19 @@ hgks_status build_host_mesh(const double *xyz, int64_t nv, const int64_t *tet, i
             }
             if (sv_ratio3(Ks, As.data()) < 1e-3) continue;
             if (!lsq_map(Ks, 3, As.data(), Xs.data())) continue;
+            if (Ks > kSubK) { fail = 5; return; }
             valid |= (unsigned char)(1u << m);
-            for (int j = 0; j < 3; j++)
-              for (int k = 0; k < Ks; k++) hm.Xm[(size_t)((m * 3 + j) * kBig + slot[k]) * N + i] += Xs[j * Ks + k];
+            // the sub-stencil's cells in the order of their big-stencil slots; unused
+            // entries keep slot 0 and a zero weight
+            std::vector<int> ord(Ks);
+            for (int k = 0; k < Ks; k++) ord[k] = k;
+            std::sort(ord.begin(), ord.end(), [&](int x, int y) { return slot[x] < slot[y]; });
+            unsigned packed = 0;
+            for (int s = 0; s < Ks; s++) {
+              packed |= (unsigned)slot[ord[s]] << (4 * s);
+              for (int j = 0; j < 3; j++) hm.Xs[(size_t)((m * 3 + j) * kSubK + s) * N + i] = Xs[j * Ks + ord[s]];
+            }
+            hm.ssl[(size_t)m * N + i] = packed;
           }
           hm.subvalid[i] = valid;
         }
@@ -517,7 +528,8 @@ hgks_status build_host_mesh(const double *xyz, int64_t nv, const int64_t *tet, i
   for (auto &t : pool) t.join();
   if (fail.load()) {
     const char *why[] = {"", "non-compact stencil has fewer than 9 cells", "singular least-squares stencil",
-                         "sub-stencil cell outside the big stencil", "singular constrained least-squares system"};
+                         "sub-stencil cell outside the big stencil", "singular constrained least-squares system",
+                         "sub-stencil with more than six cells"};
     err = why[fail.load()];
     return HGKS_ERR_MESH;
   }

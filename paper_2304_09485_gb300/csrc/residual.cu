@@ -101,8 +101,12 @@ __device__ __forceinline__ bool live(const DevMesh &m, int i) {
   return k >= 0 && m.mact[k];
 }
 
+// One thread per (component, cell): P0's 9 coefficients over the big stencil, then
+// the four sub-stencils' 3 each over their six cells, whose differences the thread
+// keeps in shared memory (its own column) from the first pass.
 template <bool BATCH>
 __global__ void __launch_bounds__(kBlock) k_coef_weno(DevMesh m, const double *__restrict__ Q, double *__restrict__ coef) {
+  __shared__ double sdq[kBig][kBlock];
   const int N = m.N;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int NL = BATCH ? m.NL : N;
@@ -110,25 +114,33 @@ __global__ void __launch_bounds__(kBlock) k_coef_weno(DevMesh m, const double *_
   const int c = t / NL, i = t - c * NL;
   if (BATCH && !live(m, i)) return;
   const double qi = Q[(size_t)c * N + i];
-  double a[9], b[12];
+  double a[9];
 #pragma unroll
   for (int d = 0; d < 9; d++) a[d] = 0.0;
-#pragma unroll
-  for (int d = 0; d < 12; d++) b[d] = 0.0;
 #pragma unroll
   for (int k = 0; k < kBig; k++) {
     int j = m.sten[(size_t)k * N + i];
     if (j < 0) break;
-    double dq = Q[(size_t)c * N + j] - qi;
+    const double dq = Q[(size_t)c * N + j] - qi;
+    sdq[k][threadIdx.x] = dq;
 #pragma unroll
     for (int d = 0; d < 9; d++) a[d] = fma(m.X0[(size_t)(d * kBig + k) * N + i], dq, a[d]);
-#pragma unroll
-    for (int d = 0; d < 12; d++) b[d] = fma(m.Xm[(size_t)(d * kBig + k) * N + i], dq, b[d]);
   }
 #pragma unroll
   for (int d = 0; d < 9; d++) coef[(size_t)(d * 5 + c) * N + i] = a[d];
 #pragma unroll
-  for (int d = 0; d < 12; d++) coef[(size_t)(kCoefA + d * 5 + c) * N + i] = b[d];
+  for (int mm = 0; mm < 4; mm++) {
+    const unsigned sl = m.ssl[(size_t)mm * N + i];
+    double b[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int s = 0; s < kSubK; s++) {
+      const double dq = sdq[(sl >> (4 * s)) & 15u][threadIdx.x];
+#pragma unroll
+      for (int j = 0; j < 3; j++) b[j] = fma(m.Xs[(size_t)((mm * 3 + j) * kSubK + s) * N + i], dq, b[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 3; j++) coef[(size_t)(kCoefA + (mm * 3 + j) * 5 + c) * N + i] = b[j];
+  }
 }
 
 template <bool BATCH>
