@@ -42,12 +42,12 @@ FP64_PEAK_GFLOPS = 1258.6
 # DRAM bytes per unit of work from the same ncu captures (dram__bytes_read.sum +
 # dram__bytes_write.sum divided by the units of the 124,416-tet launch); the
 # traffic of a full launch is this times its units (traffic grows with the units).
-KERNEL_TRAFFIC = {"flux": 465.4, "recon": 4351.3, "jacobi": 931.0, "spmv": 889.0}
+KERNEL_TRAFFIC = {"flux": 465.4, "recon": 4351.3, "jacobi": 897.4, "spmv": 855.8}
 KERNEL_FLOPS = {
     "flux": (2364.3, lambda N, F: 3 * F),        # per face Gauss point
     "recon": (3015.9, lambda N, F: 4 * N),       # per (cell, face)
-    "jacobi": (229.0, lambda N, F: N),           # per cell and sweep
-    "spmv": (205.0, lambda N, F: N),             # per cell
+    "jacobi": (218.7, lambda N, F: N),           # per cell and sweep (mean of the first and later sweeps)
+    "spmv": (195.7, lambda N, F: N),             # per cell
 }
 
 

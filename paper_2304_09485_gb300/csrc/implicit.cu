@@ -213,7 +213,10 @@ __global__ void __launch_bounds__(kCellBlock) k_apply(DevMesh m, const TM *__res
 #pragma unroll
         for (int r = 0; r < 5; r++)
 #pragma unroll
-          for (int c = 0; c < 5; c++) acc[r] = fma((TV)O[(size_t)(5 * r + c) * N], xj[c], acc[r]);
+          for (int c = 0; c < 5; c++) {
+            if (r == 0 && c == 4) continue;     // row 0 of J(Q)n is (0, n, 0): this entry is zero
+            acc[r] = fma((TV)O[(size_t)(5 * r + c) * N], xj[c], acc[r]);
+          }
       }
     }
     TV out[5];
