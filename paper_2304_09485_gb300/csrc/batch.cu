@@ -64,7 +64,7 @@ __device__ __forceinline__ void mesh_sum(T v, const BatchDev &b, T *part, double
   }
 }
 
-enum { kSpmv = 0, kJacobi = 1 };
+enum { kSpmv = 0, kJacobi = 1, kNeumann = 2 };   // as k_apply of the single-mesh path
 // SpMV / Jacobi sweep over the merged cells with an optional per-mesh (y, dotv)
 template <typename TM, typename TV, typename TO, int Mode, bool First>
 __global__ void __launch_bounds__(kB) k_bapply(DevMesh m, BatchDev bd, const TM *__restrict__ off,
@@ -103,7 +103,8 @@ __global__ void __launch_bounds__(kB) k_bapply(DevMesh m, BatchDev bd, const TM 
 #pragma unroll
   for (int r = 0; r < 5; r++) {
     TV o;
-    if (Mode == kJacobi) o = (TV)dinv[i] * (b[(size_t)r * N + i] - acc[r]);
+    if (Mode == kJacobi) o = (TV)dinv[i] * ((b ? b[(size_t)r * N + i] : TV(0)) - acc[r]);
+    else if (Mode == kNeumann) o = fma((TV)dinv[i], acc[r], b[(size_t)r * N + i]);
     else o = b ? b[(size_t)r * N + i] - acc[r] : acc[r];
     const TO oo = (TO)o;
     y[(size_t)r * N + i] = oo;
@@ -270,6 +271,29 @@ void bprecondition(const DevMesh &m, BatchState &bs, const BBuf<T> &k, int sweep
   }
 }
 
+// w = P^{-1} A v for a Krylov vector v of every mesh: w = v + E (-E)^k v with
+// E = D^{-1} O, as neumann_t of the single-mesh path; (w, dotv) per mesh from
+// the last launch
+template <typename T>
+void bneumann(const DevMesh &m, BatchState &bs, const BBuf<T> &k, int sweeps, const T *v, T *w, const T *dotv,
+              double *dot_out, cudaStream_t st) {
+  const unsigned g = std::max(1, bs.b.nblocks);
+  const int hz = bs.hsz;
+  const T *z = v;
+  for (int q = 0; q < sweeps; q++) {
+    T *dst = (q % 2 == 0) ? k.t : k.t2;
+    HGKS_PROF_BEGIN(K_JACOBI, st);
+    k_bapply<T, T, T, kJacobi, false><<<g, kB, 0, st>>>(m, bs.b, k.off, k.dval, k.dinv, nullptr, z, dst, nullptr, k.part,
+                                                         nullptr, hz);
+    HGKS_PROF_END(K_JACOBI, st);
+    z = dst;
+  }
+  HGKS_PROF_BEGIN(K_SPMV, st);
+  k_bapply<T, T, T, kNeumann, false><<<g, kB, 0, st>>>(m, bs.b, k.off, k.dval, k.dinv, v, z, w, dotv, k.part, dot_out,
+                                                        hz);
+  HGKS_PROF_END(K_SPMV, st);
+}
+
 // Restarted GMRES (Algorithm 1) for every mesh of the batch at once, each in
 // its own Krylov space; the launch sequence does not depend on the data, so it
 // can be captured in a CUDA graph.
@@ -296,11 +320,7 @@ void bgmres_t(const DevMesh &m, Scratch &s, BatchState &bs, const BBuf<T> &k, co
     k_bscale<T><<<g, kB, 0, st>>>(N, bs.b, k.w, beta, hz, k.V);
     HGKS_PROF_END(K_SCALE, st);
     for (int j = 0; j < mk; j++) {
-      HGKS_PROF_BEGIN(K_SPMV, st);
-      k_bapply<T, T, T, kSpmv, false><<<g, kB, 0, st>>>(m, bs.b, k.off, k.dval, k.dinv, nullptr, k.V + (size_t)j * vs,
-                                                         k.t, nullptr, nullptr, nullptr, hz);
-      HGKS_PROF_END(K_SPMV, st);
-      bprecondition<T>(m, bs, k, p.jacobi_sweeps, k.t, k.w, k.V, H + j, st);
+      bneumann<T>(m, bs, k, p.jacobi_sweeps, k.V + (size_t)j * vs, k.w, k.V, H + j, st);
       for (int i = 0; i <= j; i++) {
         const bool last = (i == j);
         HGKS_PROF_BEGIN(K_DOT, st);

@@ -175,12 +175,14 @@ __device__ __forceinline__ void grid_sum(T v, T *partials, unsigned int *count, 
 }
 
 // One product with the off-diagonal part of A. Modes:
-//   kSpmv  : y = [b -] (d x + sum_p A_ip x_p)
-//   kJacobi: y = D^{-1} (b - sum_p A_ip x_p); FirstSweep: x_p = D^{-1} b at the neighbours
+//   kSpmv   : y = [b -] (d x + sum_p A_ip x_p)
+//   kJacobi : y = D^{-1} ([b] - sum_p A_ip x_p) (b = 0 if null); FirstSweep: x_p = D^{-1} b
+//             at the neighbours
+//   kNeumann: y = b + D^{-1} sum_p A_ip x_p
 // and optionally the inner product (y, dotv) reduced into *dot_out.
 // TM: type of the stored blocks, TV: type of b and x (and of the accumulation),
 // TO: type of y.
-enum { kSpmv = 0, kJacobi = 1 };
+enum { kSpmv = 0, kJacobi = 1, kNeumann = 2 };
 
 // TM = float: the off-diagonal blocks come as products from jv (mixed precision);
 // TM = double: stored 5x5 blocks in off.
@@ -223,7 +225,11 @@ __global__ void __launch_bounds__(kCellBlock) k_apply(DevMesh m, const TM *__res
     if (Mode == kJacobi) {
       const TV dd = (TV)dinv[i];
 #pragma unroll
-      for (int r = 0; r < 5; r++) out[r] = dd * (b[(size_t)r * N + i] - acc[r]);
+      for (int r = 0; r < 5; r++) out[r] = dd * ((b ? b[(size_t)r * N + i] : TV(0)) - acc[r]);
+    } else if (Mode == kNeumann) {
+      const TV dd = (TV)dinv[i];
+#pragma unroll
+      for (int r = 0; r < 5; r++) out[r] = fma(dd, acc[r], b[(size_t)r * N + i]);
     } else if (b) {
 #pragma unroll
       for (int r = 0; r < 5; r++) out[r] = b[(size_t)r * N + i] - acc[r];
@@ -436,6 +442,32 @@ void precondition_t(const DevMesh &m, Scratch &s, const KBuf<T> &k, int sweeps, 
   }
 }
 
+// w = P^{-1} A v for a Krylov vector v, with the operator of precondition_t after
+// the product with A. Write A = D (I + E), E = D^{-1} O (O: the off-diagonal
+// blocks); the Jacobi iteration started from D^{-1} (A v) gives after k sweeps
+// P^{-1} A v = v - (-E)^(k+1) v, i.e. w = v + E z with z = (-E)^k v: k + 1
+// products with O instead of the product with A followed by k sweeps: the same
+// vector up to rounding, without the diagonal terms of A and the scaling of the
+// neighbours' values by D^{-1}. The last launch also reduces (w, dotv) into *dot_out.
+template <typename T>
+void neumann_t(const DevMesh &m, Scratch &s, const KBuf<T> &k, int sweeps, const T *v, T *w, const T *dotv,
+               double *dot_out, cudaStream_t st) {
+  const unsigned cg = grid_for(m.N, kCellBlock);
+  const T *z = v;
+  for (int q = 0; q < sweeps; q++) {
+    T *dst = (q % 2 == 0) ? k.t : k.t2;
+    HGKS_PROF_BEGIN(K_JACOBI, st);
+    k_apply<T, T, T, kJacobi, false><<<cg, kCellBlock, 0, st>>>(m, k.off, k.dval, k.dinv, nullptr, z, dst, nullptr,
+                                                                 k.red, s.red_count, nullptr);
+    HGKS_PROF_END(K_JACOBI, st);
+    z = dst;
+  }
+  HGKS_PROF_BEGIN(K_SPMV, st);
+  k_apply<T, T, T, kNeumann, false><<<cg, kCellBlock, 0, st>>>(m, k.off, k.dval, k.dinv, v, z, w, dotv, k.red,
+                                                                s.red_count, dot_out);
+  HGKS_PROF_END(K_SPMV, st);
+}
+
 // One restarted GMRES solve in precision T; rhs and dx stay FP64.
 template <typename T>
 void gmres_t(const DevMesh &m, Scratch &s, const KBuf<T> &k, const hgks_params &p, const double *rhs, double *dx,
@@ -469,16 +501,13 @@ void gmres_t(const DevMesh &m, Scratch &s, const KBuf<T> &k, const hgks_params &
     k_scale<T><<<vg, kBlock, 0, st>>>(n, k.w, beta, k.V);
     HGKS_PROF_END(K_SCALE, st);
     for (int j = 0; j < mk; j++) {
-      // w = P^{-1} A v_j, with h_0j = (w, v_0) from the last sweep
+      // w = P^{-1} A v_j, with h_0j = (w, v_0) from the last launch
       if (fd) {
         fd_apply<T, T>(m, s, p, Q, G, k.V + (size_t)j * vs, nullptr, k.t, st);
+        precondition_t<T>(m, s, k, p.jacobi_sweeps, k.t, k.w, k.V, H + j, st);
       } else {
-        HGKS_PROF_BEGIN(K_SPMV, st);
-        k_apply<T, T, T, kSpmv, false><<<cg, kCellBlock, 0, st>>>(m, k.off, k.dval, k.dinv, nullptr, k.V + (size_t)j * vs,
-                                                                   k.t, nullptr, nullptr, nullptr, nullptr);
-        HGKS_PROF_END(K_SPMV, st);
+        neumann_t<T>(m, s, k, p.jacobi_sweeps, k.V + (size_t)j * vs, k.w, k.V, H + j, st);
       }
-      precondition_t<T>(m, s, k, p.jacobi_sweeps, k.t, k.w, k.V, H + j, st);
       // modified Gram-Schmidt: w -= h_ij v_i, then h_{i+1,j} = (w, v_{i+1}) or ||w||
       for (int i = 0; i <= j; i++) {
         const bool last = (i == j);
