@@ -64,7 +64,7 @@ __device__ __forceinline__ void mesh_sum(T v, const BatchDev &b, T *part, double
   }
 }
 
-enum { kSpmv = 0, kJacobi = 1, kNeumann = 2 };   // as k_apply of the single-mesh path
+enum { kSpmv = 0, kJacobi = 1, kNeumann = 2, kE = 3, kNegE = 4 };   // as k_apply of the single-mesh path
 // SpMV / Jacobi sweep over the merged cells with an optional per-mesh (y, dotv)
 template <typename TM, typename TV, typename TO, int Mode, bool First>
 __global__ void __launch_bounds__(kB) k_bapply(DevMesh m, BatchDev bd, const TM *__restrict__ off,
@@ -103,7 +103,9 @@ __global__ void __launch_bounds__(kB) k_bapply(DevMesh m, BatchDev bd, const TM 
 #pragma unroll
   for (int r = 0; r < 5; r++) {
     TV o;
-    if (Mode == kJacobi) o = (TV)dinv[i] * ((b ? b[(size_t)r * N + i] : TV(0)) - acc[r]);
+    if (Mode == kJacobi) o = (TV)dinv[i] * (b[(size_t)r * N + i] - acc[r]);
+    else if (Mode == kE) o = (TV)dinv[i] * acc[r];
+    else if (Mode == kNegE) o = -(TV)dinv[i] * acc[r];
     else if (Mode == kNeumann) o = fma((TV)dinv[i], acc[r], b[(size_t)r * N + i]);
     else o = b ? b[(size_t)r * N + i] - acc[r] : acc[r];
     const TO oo = (TO)o;
@@ -272,8 +274,8 @@ void bprecondition(const DevMesh &m, BatchState &bs, const BBuf<T> &k, int sweep
 }
 
 // w = P^{-1} A v for a Krylov vector v of every mesh: w = v + E (-E)^k v with
-// E = D^{-1} O, as neumann_t of the single-mesh path; (w, dotv) per mesh from
-// the last launch
+// E = D^{-1} O (the sign in the first product), as neumann_t of the single-mesh
+// path; (w, dotv) per mesh from the last launch
 template <typename T>
 void bneumann(const DevMesh &m, BatchState &bs, const BBuf<T> &k, int sweeps, const T *v, T *w, const T *dotv,
               double *dot_out, cudaStream_t st) {
@@ -283,8 +285,12 @@ void bneumann(const DevMesh &m, BatchState &bs, const BBuf<T> &k, int sweeps, co
   for (int q = 0; q < sweeps; q++) {
     T *dst = (q % 2 == 0) ? k.t : k.t2;
     HGKS_PROF_BEGIN(K_JACOBI, st);
-    k_bapply<T, T, T, kJacobi, false><<<g, kB, 0, st>>>(m, bs.b, k.off, k.dval, k.dinv, nullptr, z, dst, nullptr, k.part,
+    if (q == 0 && sweeps % 2 == 1)
+      k_bapply<T, T, T, kNegE, false><<<g, kB, 0, st>>>(m, bs.b, k.off, k.dval, k.dinv, nullptr, z, dst, nullptr, k.part,
                                                          nullptr, hz);
+    else
+      k_bapply<T, T, T, kE, false><<<g, kB, 0, st>>>(m, bs.b, k.off, k.dval, k.dinv, nullptr, z, dst, nullptr, k.part,
+                                                      nullptr, hz);
     HGKS_PROF_END(K_JACOBI, st);
     z = dst;
   }

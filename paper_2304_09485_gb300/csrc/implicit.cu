@@ -176,13 +176,13 @@ __device__ __forceinline__ void grid_sum(T v, T *partials, unsigned int *count, 
 
 // One product with the off-diagonal part of A. Modes:
 //   kSpmv   : y = [b -] (d x + sum_p A_ip x_p)
-//   kJacobi : y = D^{-1} ([b] - sum_p A_ip x_p) (b = 0 if null); FirstSweep: x_p = D^{-1} b
-//             at the neighbours
+//   kJacobi : y = D^{-1} (b - sum_p A_ip x_p); FirstSweep: x_p = D^{-1} b at the neighbours
 //   kNeumann: y = b + D^{-1} sum_p A_ip x_p
+//   kE, kNegE: y = +- D^{-1} sum_p A_ip x_p
 // and optionally the inner product (y, dotv) reduced into *dot_out.
 // TM: type of the stored blocks, TV: type of b and x (and of the accumulation),
 // TO: type of y.
-enum { kSpmv = 0, kJacobi = 1, kNeumann = 2 };
+enum { kSpmv = 0, kJacobi = 1, kNeumann = 2, kE = 3, kNegE = 4 };
 
 // TM = float: the off-diagonal blocks come as products from jv (mixed precision);
 // TM = double: stored 5x5 blocks in off.
@@ -225,7 +225,11 @@ __global__ void __launch_bounds__(kCellBlock) k_apply(DevMesh m, const TM *__res
     if (Mode == kJacobi) {
       const TV dd = (TV)dinv[i];
 #pragma unroll
-      for (int r = 0; r < 5; r++) out[r] = dd * ((b ? b[(size_t)r * N + i] : TV(0)) - acc[r]);
+      for (int r = 0; r < 5; r++) out[r] = dd * (b[(size_t)r * N + i] - acc[r]);
+    } else if (Mode == kE || Mode == kNegE) {
+      const TV dd = Mode == kE ? (TV)dinv[i] : -(TV)dinv[i];
+#pragma unroll
+      for (int r = 0; r < 5; r++) out[r] = dd * acc[r];
     } else if (Mode == kNeumann) {
       const TV dd = (TV)dinv[i];
 #pragma unroll
@@ -445,7 +449,8 @@ void precondition_t(const DevMesh &m, Scratch &s, const KBuf<T> &k, int sweeps, 
 // w = P^{-1} A v for a Krylov vector v, with the operator of precondition_t after
 // the product with A. Write A = D (I + E), E = D^{-1} O (O: the off-diagonal
 // blocks); the Jacobi iteration started from D^{-1} (A v) gives after k sweeps
-// P^{-1} A v = v - (-E)^(k+1) v, i.e. w = v + E z with z = (-E)^k v: k + 1
+// P^{-1} A v = v - (-E)^(k+1) v, i.e. w = v + E z with z = (-E)^k v (formed as
+// E^k v with the sign in its first product): k + 1
 // products with O instead of the product with A followed by k sweeps: the same
 // vector up to rounding, without the diagonal terms of A and the scaling of the
 // neighbours' values by D^{-1}. The last launch also reduces (w, dotv) into *dot_out.
@@ -457,8 +462,12 @@ void neumann_t(const DevMesh &m, Scratch &s, const KBuf<T> &k, int sweeps, const
   for (int q = 0; q < sweeps; q++) {
     T *dst = (q % 2 == 0) ? k.t : k.t2;
     HGKS_PROF_BEGIN(K_JACOBI, st);
-    k_apply<T, T, T, kJacobi, false><<<cg, kCellBlock, 0, st>>>(m, k.off, k.dval, k.dinv, nullptr, z, dst, nullptr,
+    if (q == 0 && sweeps % 2 == 1)
+      k_apply<T, T, T, kNegE, false><<<cg, kCellBlock, 0, st>>>(m, k.off, k.dval, k.dinv, nullptr, z, dst, nullptr,
                                                                  k.red, s.red_count, nullptr);
+    else
+      k_apply<T, T, T, kE, false><<<cg, kCellBlock, 0, st>>>(m, k.off, k.dval, k.dinv, nullptr, z, dst, nullptr,
+                                                              k.red, s.red_count, nullptr);
     HGKS_PROF_END(K_JACOBI, st);
     z = dst;
   }
