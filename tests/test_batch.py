@@ -115,10 +115,11 @@ def test_batch_residual_equals_single_and_oracle(cuda, scheme):
             assert oerr.max() <= 1e-11, f"{name}: batch vs oracle {oerr.max():.3e}"
 
 
-@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
-def test_batch_gmres_step_equals_single(cuda, precision):
+@pytest.mark.parametrize("precision,sweeps", [(0, 2), (1, 2), (0, 1), (1, 3)],
+                         ids=["fp64", "mixed", "fp64-1sweep", "mixed-3sweeps"])
+def test_batch_gmres_step_equals_single(cuda, precision, sweeps):
     import torch
-    kw = dict(scheme=0, krylov_dim=8, restarts=2, precision=precision)
+    kw = dict(scheme=0, krylov_dim=8, restarts=2, precision=precision, jacobi_sweeps=sweeps)
     b, singles = make_batch(kw, seed=21)
     infos = H.hgks_batch_gmres_step(b)
     tol = 1e-10 if precision == 0 else 2e-4

@@ -187,6 +187,29 @@ def test_gmres_step_parity(cuda, name, kw):
         assert np.linalg.norm(Gg - Go) / np.linalg.norm(Go) <= 1e-11
 
 
+@pytest.mark.parametrize("sweeps", [0, 1, 3])
+def test_gmres_step_parity_jacobi_sweeps(cuda, sweeps):
+    """Other sweep counts of the Jacobi preconditioner (k = 0, odd, 3): the GPU forms
+    P^{-1} A v_j in its Neumann form v + E (-E)^k v, whose sign depends on k."""
+    import torch
+    m, cond, om, hm = setup("sphere6x6")
+    Q, G = state(m, cond, seed=12)
+    kw = dict(scheme=0, krylov_dim=10, restarts=2, jacobi_sweeps=sweeps)
+    po = O.make_params(**{**cond, **kw}); ph = H.hgks_default_params(**{**cond, **kw})
+    _, _, reso, dQo = om.gmres_step(po, Q, G)
+    Qd = hm.to_internal(Q)
+    dQd = torch.empty_like(Qd)
+    info = H.hgks_gmres_step(hm, ph, Qd, None, dQd)
+    assert info.res_l1 == pytest.approx(reso, rel=1e-11)
+    rel = np.linalg.norm(hm.to_caller(dQd) - dQo) / np.linalg.norm(dQo)
+    assert rel <= 1e-9, rel
+    # the FP32 Krylov part: the same step to the mixed-precision tolerance
+    Qd = hm.to_internal(Q)
+    H.hgks_gmres_step(hm, H.hgks_default_params(**{**cond, **kw, "precision": 1}), Qd, None, dQd)
+    rel32 = np.linalg.norm(hm.to_caller(dQd) - dQo) / np.linalg.norm(dQo)
+    assert rel32 <= MIXED_TOL["dQ_step"], rel32
+
+
 def test_gmres_steps_track_oracle(cuda):
     """Five consecutive implicit steps on the viscous sphere stay within 1e-9 (relative L2)."""
     import torch
