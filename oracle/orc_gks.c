@@ -241,12 +241,16 @@ void orc_boundary_state(const orc_params *p, int tag, const double *T3, const do
   else { vel_odd[0] = vel_odd[1] = vel_odd[2] = 1; }
   for (int i = 0; i < 3; i++) ug[i] = vel_odd[i] ? 2.0 * uw[i] - u[i] : u[i];
   Tg = T_odd ? 2.0 * p->wall_T - T : T;
+  /* a cell hotter than 1.5 T_w would give an image colder than T_w / 2 (or
+     negative): the image temperature is held at T_w / 2, uniform */
+  int T_held = T_odd && Tg < 0.5 * p->wall_T;
+  if (T_held) Tg = 0.5 * p->wall_T;
   double dug[3][3], dpg[3], dTg[3];
   for (int d = 0; d < 3; d++) {
     double sn = d == 0 ? -1.0 : 1.0;   /* even: flip the normal derivative */
     for (int i = 0; i < 3; i++) dug[d][i] = vel_odd[i] ? -sn * du[d][i] : sn * du[d][i];
     dpg[d] = sn * dp[d];
-    dTg[d] = T_odd ? -sn * dT[d] : sn * dT[d];
+    dTg[d] = T_held ? 0.0 : (T_odd ? -sn * dT[d] : sn * dT[d]);
   }
   double rg = pg / Tg, qg2 = ug[0] * ug[0] + ug[1] * ug[1] + ug[2] * ug[2];
   Wr[0] = rg; Wr[1] = rg * ug[0]; Wr[2] = rg * ug[1]; Wr[3] = rg * ug[2];

@@ -476,7 +476,9 @@ __device__ void boundary_state(const hgks_params &P, int tag, const double *T, c
   double ug[3];
 #pragma unroll
   for (int r = 0; r < 3; r++) ug[r] = vodd[r] ? 2.0 * uw[r] - u[r] : u[r];
-  const double Tg = T_odd ? 2.0 * P.wall_T - Tl : Tl, pg = pr;
+  // an image colder than T_w / 2 (a cell hotter than 1.5 T_w) is held at T_w / 2, uniform
+  const bool T_held = T_odd && 2.0 * P.wall_T - Tl < 0.5 * P.wall_T;
+  const double Tg = T_held ? 0.5 * P.wall_T : (T_odd ? 2.0 * P.wall_T - Tl : Tl), pg = pr;
   const double rg = pg / Tg, qg2 = ug[0] * ug[0] + ug[1] * ug[1] + ug[2] * ug[2];
   Wr[0] = rg;
 #pragma unroll
@@ -494,7 +496,7 @@ __device__ void boundary_state(const hgks_params &P, int tag, const double *T, c
     double dug[3], udug = 0.0;
 #pragma unroll
     for (int r = 0; r < 3; r++) { dug[r] = vodd[r] ? -sn * du[r] : sn * du[r]; udug += ug[r] * dug[r]; }
-    const double dpg = sn * dp, dTg = T_odd ? -sn * dT : sn * dT;
+    const double dpg = sn * dp, dTg = T_held ? 0.0 : (T_odd ? -sn * dT : sn * dT);
     const double drho = dpg / Tg - pg * dTg / (Tg * Tg);
     dWr[5 * d] = drho;
 #pragma unroll

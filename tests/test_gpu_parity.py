@@ -81,6 +81,8 @@ CASES = [
     ("sphere6x6", dict(scheme=0)), ("sphere6x6", dict(scheme=1, weights=1)),
     ("sphere6x6_visc", dict(scheme=1, Pr=0.72)), ("sphere6x6_visc", dict(scheme=0, Pr=0.72, tstar_end=0)),
     ("cavity8", dict(scheme=1, Pr=0.72, flux_dt=1e-3)),
+    # walls colder than the cells' T/1.5 at some cells: their images are held at T_w/2
+    ("cavity5", dict(scheme=0, wall_T=21.0)),
 ]
 
 

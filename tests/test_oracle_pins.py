@@ -288,6 +288,50 @@ def test_boundary_states():
     assert np.all(dWr == 0)
 
 
+def test_wall_fluxes_by_symmetry():
+    """The mirror image of a slip wall is the reflection x -> -x, u -> -u of phase space, a
+    symmetry of the BGK equation: no mass, tangential momentum or energy crosses the wall,
+    whatever the gradients. At an adiabatic no-slip wall at rest the image reverses all
+    velocities, which is a symmetry only without tangential variation: with normal
+    gradients alone no mass or energy crosses (the shear stress remains)."""
+    rng = np.random.default_rng(23)
+    T3 = O.face_frame(np.array([0.3, -0.5, 0.81]) / np.linalg.norm([0.3, -0.5, 0.81]))
+    p = O.make_params(viscous=1, mu=2e-3, wall_T=0.9)
+    for _ in range(20):
+        W = rand_state(rng)
+        dW = rng.normal(size=(3, 5)) * 0.2
+        Wr, dWr = O.boundary_state(p, 3, T3, W, dW)
+        F, _ = O.gks_flux(p, W, dW, Wr, dWr, 0.02)
+        assert np.all(np.abs(F[[0, 2, 3, 4]]) <= 1e-14 * np.abs(F).max()), F
+        dW[1:] = 0.0
+        Wr, dWr = O.boundary_state(p, 4, T3, W, dW)
+        F, _ = O.gks_flux(p, W, dW, Wr, dWr, 0.02)
+        assert np.all(np.abs(F[[0, 4]]) <= 1e-14 * np.abs(F).max()), F
+        assert np.abs(F[2:4]).max() > 1e-6 * np.abs(F).max()
+
+
+def test_isothermal_image_held_at_half_wall_temperature():
+    """A cell hotter than 1.5 T_w would give an image colder than T_w / 2: the image
+    temperature is held at T_w / 2 with zero gradient, same pressure."""
+    T3 = O.face_frame(np.array([0.0, 0.0, 1.0]))
+    p = O.make_params(wall_T=0.4, lid_speed=0.0)
+    rho, T = 1.2, 1.0                     # T > 1.5 T_w: the reflected 2 T_w - T would be -0.2
+    W = np.array([rho, 0.1 * rho, 0.0, 0.0, rho * T / (GAMMA - 1) + 0.5 * rho * 0.01])
+    dW = np.random.default_rng(29).normal(size=(3, 5)) * 0.1
+    Wr, dWr = O.boundary_state(p, 1, T3, W, dW)
+    pr = (GAMMA - 1) * (W[4] - 0.5 * (W[1:4] @ W[1:4]) / W[0])
+    pg = (GAMMA - 1) * (Wr[4] - 0.5 * (Wr[1:4] @ Wr[1:4]) / Wr[0])
+    assert pg == pytest.approx(pr, rel=1e-14)
+    assert pg / Wr[0] == pytest.approx(0.2, rel=1e-14)
+    # the image's temperature is uniform: dT = (dp - T drho) / rho = 0 along every axis
+    for d in range(3):
+        u = Wr[1:4] / Wr[0]
+        dpg = (GAMMA - 1) * (dWr[d, 4] - u @ dWr[d, 1:4] + 0.5 * (u @ u) * dWr[d, 0])
+        assert abs(dpg - 0.2 * dWr[d, 0]) <= 1e-13 * (abs(dpg) + 1e-300)
+    F, _ = O.gks_flux(O.make_params(viscous=1, mu=1e-3, wall_T=0.4), W, dW, Wr, dWr, 0.01)
+    assert np.all(np.isfinite(F))
+
+
 # ---------------------------------------------------------------------------
 # reconstruction (Sec. 3)
 # ---------------------------------------------------------------------------
