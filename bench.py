@@ -42,10 +42,10 @@ FP64_PEAK_GFLOPS = 1258.6
 # DRAM bytes per unit of work from the same ncu captures (dram__bytes_read.sum +
 # dram__bytes_write.sum divided by the units of the 124,416-tet launch); the
 # traffic of a full launch is this times its units (traffic grows with the units).
-KERNEL_TRAFFIC = {"flux": 465.4, "recon": 4351.3, "jacobi": 858.0, "spmv": 935.0}
+KERNEL_TRAFFIC = {"flux": 467.8, "recon": 4358.7, "jacobi": 858.0, "spmv": 935.0}
 KERNEL_FLOPS = {
-    "flux": (2364.3, lambda N, F: 3 * F),        # per face Gauss point
-    "recon": (3015.9, lambda N, F: 4 * N),       # per (cell, face)
+    "flux": (2242.5, lambda N, F: 3 * F),        # per face Gauss point
+    "recon": (3000.9, lambda N, F: 4 * N),       # per (cell, face)
     # the Krylov products: "jacobi" = products D^-1 O x (120 of a C2 step's 126
     # launches are the E products of the Neumann form, 195.7 flop; 6 are the sweeps
     # of the restart vector, ~219), "spmv" = products with O plus a vector (60 of 63

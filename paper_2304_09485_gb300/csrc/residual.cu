@@ -34,13 +34,16 @@ constexpr int kBlock = 128;
 struct Prim { double rho, U, V, W, lam, il, ir; };
 
 __device__ __forceinline__ Prim to_prim(const double *Q, double gamma) {
+  // rho p from the conservative variables without a division; one reciprocal
+  // r = 1 / (rho^2 p) then gives both 1/rho = rho p r and lam = rho / (2p) = rho^3 r / 2
   Prim p;
   p.rho = Q[0];
-  p.ir = 1.0 / Q[0];
+  const double rp = (gamma - 1.0) * (Q[4] * Q[0] - 0.5 * (Q[1] * Q[1] + Q[2] * Q[2] + Q[3] * Q[3]));   // rho p
+  const double r = 1.0 / (Q[0] * rp);
+  p.ir = rp * r;
   p.U = Q[1] * p.ir; p.V = Q[2] * p.ir; p.W = Q[3] * p.ir;
-  const double pr = (gamma - 1.0) * (Q[4] - 0.5 * Q[0] * (p.U * p.U + p.V * p.V + p.W * p.W));
-  p.il = pr * p.ir;
-  p.lam = 0.5 / p.il;
+  p.il = rp * p.ir * p.ir;
+  p.lam = 0.5 * Q[0] * Q[0] * Q[0] * r;
   return p;
 }
 
@@ -65,8 +68,9 @@ __device__ __forceinline__ Eig eig_of(const double *Q, double gamma) {
   e.u = Q[1] * ir; e.v = Q[2] * ir; e.w = Q[3] * ir;
   e.q2 = e.u * e.u + e.v * e.v + e.w * e.w;
   double p = (gamma - 1.0) * (Q[4] - 0.5 * Q[0] * e.q2);
-  e.a = sqrt(gamma * p * ir);
-  e.ia = 1.0 / e.a;
+  const double a2 = gamma * p * ir;
+  e.ia = rsqrt(a2);
+  e.a = a2 * e.ia;
   e.H = (Q[4] + p) * ir;
   e.b1 = (gamma - 1.0) * e.ia * e.ia;
   e.b2 = 0.5 * e.b1 * e.q2;
@@ -352,9 +356,13 @@ __device__ __forceinline__ void mom_u_full(const Prim &p, double *u) {
 }
 // sgn = +1: u > 0, sgn = -1: u < 0
 __device__ __forceinline__ void mom_u_half(const Prim &p, double sgn, double *u) {
+  // erfc(x) = erfcx(|x|) exp(-x^2) for x >= 0 and 2 - erfcx(|x|) exp(-x^2) below,
+  // with the exponential that u[1] needs as well
   const double il = p.il, rs = rsqrt(p.lam), sl = p.lam * rs;
-  u[0] = 0.5 * erfc(-sgn * sl * p.U);
-  u[1] = p.U * u[0] + sgn * 0.5 * exp(-p.lam * p.U * p.U) * rs * 0.56418958354775628695;   // 1/sqrt(pi)
+  const double x = -sgn * sl * p.U, e = exp(-p.lam * p.U * p.U);
+  const double t = erfcx(fabs(x)) * e;
+  u[0] = 0.5 * (x >= 0.0 ? t : 2.0 - t);
+  u[1] = p.U * u[0] + sgn * 0.5 * e * rs * 0.56418958354775628695;   // 1/sqrt(pi)
 #pragma unroll
   for (int n = 0; n < 5; n++) u[n + 2] = p.U * u[n + 1] + (n + 1) * il * u[n];
 }
@@ -670,9 +678,10 @@ __device__ void gks_flux(const hgks_params &P, const double *Wl, const double *d
     for (int c = 0; c < 5; c++) Qp[c] = Pt[c];
 }
 
+// rho > 0 and p > 0, the latter as rho p > 0 (no division)
 __device__ __forceinline__ bool physical(const double *W, double gamma) {
-  const double p = (gamma - 1.0) * (W[4] - 0.5 * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]) / W[0]);
-  return W[0] > 0.0 && p > 0.0;
+  const double rp = (gamma - 1.0) * (W[4] * W[0] - 0.5 * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]));
+  return W[0] > 0.0 && rp > 0.0;
 }
 
 template <bool BATCH>
