@@ -118,7 +118,8 @@ hgks_status ensure_scratch(Mesh &m, int kdim, bool implicit, bool mixed) {
     if ((st = dalloc(m, &s.fflux, (size_t)15 * F))) return st;
     if ((st = dalloc(m, &s.fpt, (size_t)15 * F))) return st;
     if ((st = dalloc(m, &s.flags, 8))) return st;
-    if ((st = dalloc(m, &s.red, std::max<size_t>(4096, N / 64 + 64)))) return st;   // one partial per block
+    // one partial per block and sum (the MGS pass reduces 16 sums over 608 blocks)
+    if ((st = dalloc(m, &s.red, std::max<size_t>(16 * 608 + 64, N / 64 + 64)))) return st;
     if ((st = dalloc(m, &s.red_count, 4))) return st;
     HGKS_CUDA(cudaMemset(s.flags, 0, 8 * sizeof(int)));
     HGKS_CUDA(cudaMemset(s.red_count, 0, 4 * sizeof(unsigned)));
@@ -136,6 +137,7 @@ hgks_status ensure_scratch(Mesh &m, int kdim, bool implicit, bool mixed) {
     if ((st = dalloc(m, &s.t, 5 * N))) return st;
     if ((st = dalloc(m, &s.t2, 5 * N))) return st;
     if ((st = dalloc(m, &s.hs, 65 * 64 + 256))) return st;
+    if ((st = dalloc(m, &s.gram, 65 * 65 + 2 * 65 + 64))) return st;
     HGKS_CUDA(cudaMemset(s.off, 0, sizeof(double) * 100 * N));
   }
   if (implicit && mixed && !s.jv32) {
@@ -145,7 +147,7 @@ hgks_status ensure_scratch(Mesh &m, int kdim, bool implicit, bool mixed) {
     if ((st = dalloc(m, &s.w32, 5 * N))) return st;
     if ((st = dalloc(m, &s.t32, 5 * N))) return st;
     if ((st = dalloc(m, &s.t232, 5 * N))) return st;
-    if ((st = dalloc(m, &s.red32, std::max<size_t>(4096, N / 64 + 64)))) return st;
+    if ((st = dalloc(m, &s.red32, std::max<size_t>(16 * 608 + 64, N / 64 + 64)))) return st;
   }
   auto release = [&](void *p, size_t bytes) {
     cudaFree(p);

@@ -110,6 +110,7 @@ struct Scratch {
   double *red = nullptr;         // reduction partials
   unsigned int *red_count = nullptr;
   double *hs = nullptr;          // small device scalars: H, beta, y, norms
+  double *gram = nullptr;        // [65*65 + 2*65] Gram matrix of the Krylov basis and the MGS pass sums
   int *flags = nullptr;          // [8] device flags (nonphysical count, breakdown)
   double *hostbuf = nullptr;     // [40][N] device state of the *_host entry points
   double *Qp = nullptr, *Rp = nullptr;   // [5][N] perturbed state and its residual (matrix-free products)

@@ -309,6 +309,133 @@ __global__ void __launch_bounds__(kBlock) k_axpy_dot(int64_t n, T *__restrict__ 
   grid_sum(s, partials, count, out, self);
 }
 
+// ---- modified Gram-Schmidt from one pass over the basis ----
+// Algorithm 1 orthogonalises w against v_0..v_j one vector after the other:
+// h_i = (w_i, v_i), w_{i+1} = w_i - h_i v_i. Since w_i = w - sum_{k<i} h_k v_k,
+//   h_i = a_i - sum_{k<i} h_k G_ki,  a_i = (w, v_i),  G_ki = (v_k, v_i),
+// so one pass over the basis (k_mdot: all a_i, and the new row of G, v_j against
+// the older vectors) and a forward substitution (k_mgs_coef) give the same
+// coefficients, and one more pass (k_mupdate) subtracts them in MGS order and
+// takes ||w||: about 2 (j + 1) vector passes instead of 4 (j + 1) for step j
+// (used with FP32 vectors, see gmres_t).
+constexpr int kMdot = 8;              // basis vectors per k_mdot launch (register accumulators)
+
+// a[k] = (w, v_k) for k in [k0, k0 + nk), and g[k] = (v_j, v_k) for those k < j
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_mdot(int64_t n, const T *__restrict__ w, const T *__restrict__ V, int64_t vs,
+                                                 int k0, int nk, int j, T *partials, unsigned int *count,
+                                                 double *__restrict__ a, double *__restrict__ g) {
+  typedef typename Vec16<T>::type TV;
+  constexpr int L = Vec16<T>::n;
+  T sa[kMdot], sg[kMdot];
+#pragma unroll
+  for (int q = 0; q < kMdot; q++) { sa[q] = T(0); sg[q] = T(0); }
+  const int64_t nv = n / L, stride = (int64_t)gridDim.x * blockDim.x;
+  const TV *wv = reinterpret_cast<const TV *>(w);
+  const TV *jv = reinterpret_cast<const TV *>(V + (size_t)j * vs);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nv; k += stride) {
+    const TV wk = wv[k], vj = jv[k];
+    const T *wa = reinterpret_cast<const T *>(&wk);
+    const T *ja = reinterpret_cast<const T *>(&vj);
+#pragma unroll
+    for (int q = 0; q < kMdot; q++) {
+      if (q < nk) {
+        const TV vk = reinterpret_cast<const TV *>(V + (size_t)(k0 + q) * vs)[k];
+        const T *va = reinterpret_cast<const T *>(&vk);
+#pragma unroll
+        for (int l = 0; l < L; l++) sa[q] = fma(wa[l], va[l], sa[q]);
+        if (k0 + q < j)
+#pragma unroll
+          for (int l = 0; l < L; l++) sg[q] = fma(ja[l], va[l], sg[q]);
+      }
+    }
+  }
+  for (int64_t k = nv * L + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += stride) {
+    const T wk = w[k], vj = V[(size_t)j * vs + k];
+#pragma unroll
+    for (int q = 0; q < kMdot; q++)
+      if (q < nk) {
+        const T vk = V[(size_t)(k0 + q) * vs + k];
+        sa[q] = fma(wk, vk, sa[q]);
+        if (k0 + q < j) sg[q] = fma(vj, vk, sg[q]);
+      }
+  }
+  // per block: 2 kMdot partials; the last block adds every slot's partials in block order
+  __shared__ bool last;
+#pragma unroll
+  for (int q = 0; q < 2 * kMdot; q++) {
+    const T bs = block_sum(q < kMdot ? sa[q] : sg[q - kMdot]);
+    if (threadIdx.x == 0) partials[(size_t)q * gridDim.x + blockIdx.x] = bs;
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = (atomicAdd(count, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int q = 0; q < 2 * kMdot; q++) {
+    const int kk = k0 + (q % kMdot);
+    const bool want = (q % kMdot) < nk && (q < kMdot || kk < j);   // uniform over the block
+    if (!want) continue;
+    T sum = T(0);
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) sum += ((volatile T *)partials)[(size_t)q * gridDim.x + b];
+    sum = block_sum(sum);
+    if (threadIdx.x == 0) (q < kMdot ? a : g)[kk] = (double)sum;
+  }
+  if (threadIdx.x == 0) *count = 0u;
+}
+
+// the MGS coefficients of step j by forward substitution; column j of H and row
+// j of the basis Gram matrix G (leading dimension kGramLd, G[k][i] = (v_k, v_i), k < i)
+constexpr int kGramLd = 65;
+__global__ void k_mgs_coef(int j, int mk, const double *__restrict__ a, const double *__restrict__ g,
+                           double *__restrict__ G, double *__restrict__ H) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int k = 0; k < j; k++) G[k * kGramLd + j] = g[k];
+  for (int i = 0; i <= j; i++) {
+    double h = a[i];
+    for (int k = 0; k < i; k++) h -= H[k * mk + j] * G[k * kGramLd + i];
+    H[i * mk + j] = h;
+  }
+}
+
+// w -= sum_{k <= j} h_kj v_k in the order of k (MGS order), then h_{j+1,j} = ||w||
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_mupdate(int64_t n, T *__restrict__ w, const T *__restrict__ V, int64_t vs,
+                                                    int j, int mk, const double *__restrict__ H, T *partials,
+                                                    unsigned int *count, double *norm_out) {
+  typedef typename Vec16<T>::type TV;
+  constexpr int L = Vec16<T>::n;
+  __shared__ T nh[kGramLd];
+  for (int k = threadIdx.x; k <= j; k += blockDim.x) nh[k] = (T)(-H[k * mk + j]);
+  __syncthreads();
+  T s = T(0);
+  const int64_t nv = n / L, stride = (int64_t)gridDim.x * blockDim.x;
+  TV *wv = reinterpret_cast<TV *>(w);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nv; k += stride) {
+    TV wk = wv[k];
+    T *wa = reinterpret_cast<T *>(&wk);
+#pragma unroll 4
+    for (int q = 0; q <= j; q++) {
+      const TV vk = reinterpret_cast<const TV *>(V + (size_t)q * vs)[k];
+      const T *va = reinterpret_cast<const T *>(&vk);
+#pragma unroll
+      for (int l = 0; l < L; l++) wa[l] = fma(nh[q], va[l], wa[l]);
+    }
+    wv[k] = wk;
+#pragma unroll
+    for (int l = 0; l < L; l++) s = fma(wa[l], wa[l], s);
+  }
+  for (int64_t k = nv * L + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += stride) {
+    T wk = w[k];
+    for (int q = 0; q <= j; q++) wk = fma(nh[q], V[(size_t)q * vs + k], wk);
+    w[k] = wk;
+    s = fma(wk, wk, s);
+  }
+  grid_sum(s, partials, count, norm_out, 1);
+}
+
 // v = w / h (v = 0 after a breakdown h == 0)
 template <typename T>
 __global__ void k_scale(int64_t n, const T *__restrict__ w, const double *__restrict__ h, T *__restrict__ v) {
@@ -485,6 +612,12 @@ void gmres_t(const DevMesh &m, Scratch &s, const KBuf<T> &k, const hgks_params &
   const int mk = p.krylov_dim;
   const int64_t n = 5 * (int64_t)m.N, vs = s.vstride;
   double *H = s.hs, *beta = s.hs + (mk + 1) * mk, *y = beta + 1, *lres = y + mk;
+  double *gram = s.gram, *ga = s.gram + kGramLd * kGramLd, *gg = ga + kGramLd;   // G, a, g of the MGS passes
+  // The one-pass MGS does 3 FMAs per element and basis vector against 2 for the
+  // step-by-step form, and reads about half the bytes: with FP32 vectors it is
+  // bound by HBM and wins; with FP64 vectors both forms sit at GB300's FP64 rate
+  // (one FP64 FMA per 8 bytes read already exceeds it), so FP64 keeps the steps.
+  constexpr bool one_pass = std::is_same<T, float>::value;
   const unsigned vg = vec_grid(n), cg = grid_for(m.N, kCellBlock);
   for (int it = 0; it < p.restarts; it++) {
     cudaMemsetAsync(H, 0, sizeof(double) * (mk + 1) * mk, st);
@@ -510,21 +643,40 @@ void gmres_t(const DevMesh &m, Scratch &s, const KBuf<T> &k, const hgks_params &
     k_scale<T><<<vg, kBlock, 0, st>>>(n, k.w, beta, k.V);
     HGKS_PROF_END(K_SCALE, st);
     for (int j = 0; j < mk; j++) {
-      // w = P^{-1} A v_j, with h_0j = (w, v_0) from the last launch
+      // w = P^{-1} A v_j (FP64: with h_0j = (w, v_0) from the last launch)
+      const T *dv = one_pass ? nullptr : k.V;
+      double *dout = one_pass ? nullptr : H + j;
       if (fd) {
         fd_apply<T, T>(m, s, p, Q, G, k.V + (size_t)j * vs, nullptr, k.t, st);
-        precondition_t<T>(m, s, k, p.jacobi_sweeps, k.t, k.w, k.V, H + j, st);
+        precondition_t<T>(m, s, k, p.jacobi_sweeps, k.t, k.w, dv, dout, st);
       } else {
-        neumann_t<T>(m, s, k, p.jacobi_sweeps, k.V + (size_t)j * vs, k.w, k.V, H + j, st);
+        neumann_t<T>(m, s, k, p.jacobi_sweeps, k.V + (size_t)j * vs, k.w, dv, dout, st);
       }
-      // modified Gram-Schmidt: w -= h_ij v_i, then h_{i+1,j} = (w, v_{i+1}) or ||w||
-      for (int i = 0; i <= j; i++) {
-        const bool last = (i == j);
+      if (one_pass) {
+        // modified Gram-Schmidt: the coefficients h_ij from one pass over the basis,
+        // then w -= sum h_ij v_i in MGS order and h_{j+1,j} = ||w||
+        for (int k0 = 0; k0 <= j; k0 += kMdot) {
+          HGKS_PROF_BEGIN(K_DOT, st);
+          k_mdot<T><<<kRedBlocks, kBlock, 0, st>>>(n, k.w, k.V, vs, k0, std::min(kMdot, j + 1 - k0), j, k.red,
+                                                    s.red_count, ga, gg);
+          HGKS_PROF_END(K_DOT, st);
+        }
         HGKS_PROF_BEGIN(K_DOT, st);
-        k_axpy_dot<T><<<kRedBlocks, kBlock, 0, st>>>(n, k.w, k.V + (size_t)i * vs, H + i * mk + j,
-                                                       last ? k.w : k.V + (size_t)(i + 1) * vs, last ? 1 : 0, k.red,
-                                                       s.red_count, H + (i + 1) * mk + j);
+        k_mgs_coef<<<1, 32, 0, st>>>(j, mk, ga, gg, gram, H);
         HGKS_PROF_END(K_DOT, st);
+        HGKS_PROF_BEGIN(K_DOT, st);
+        k_mupdate<T><<<kRedBlocks, kBlock, 0, st>>>(n, k.w, k.V, vs, j, mk, H, k.red, s.red_count, H + (j + 1) * mk + j);
+        HGKS_PROF_END(K_DOT, st);
+      } else {
+        // modified Gram-Schmidt step by step: w -= h_ij v_i, then h_{i+1,j} = (w, v_{i+1}) or ||w||
+        for (int i = 0; i <= j; i++) {
+          const bool last = (i == j);
+          HGKS_PROF_BEGIN(K_DOT, st);
+          k_axpy_dot<T><<<kRedBlocks, kBlock, 0, st>>>(n, k.w, k.V + (size_t)i * vs, H + i * mk + j,
+                                                         last ? k.w : k.V + (size_t)(i + 1) * vs, last ? 1 : 0, k.red,
+                                                         s.red_count, H + (i + 1) * mk + j);
+          HGKS_PROF_END(K_DOT, st);
+        }
       }
       HGKS_PROF_BEGIN(K_SCALE, st);
       k_scale<T><<<vg, kBlock, 0, st>>>(n, k.w, H + (j + 1) * mk + j, k.V + (size_t)(j + 1) * vs);

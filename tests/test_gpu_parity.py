@@ -83,6 +83,8 @@ CASES = [
     ("cavity8", dict(scheme=1, Pr=0.72, flux_dt=1e-3)),
     # walls colder than the cells' T/1.5 at some cells: their images are held at T_w/2
     ("cavity5", dict(scheme=0, wall_T=21.0)),
+    # a monatomic gas: K = (5 - 3 gamma) / (gamma - 1) = 0 internal degrees of freedom
+    ("sphere6x6", dict(scheme=0, gamma=5.0 / 3.0)), ("cavity5", dict(scheme=1, gamma=5.0 / 3.0)),
 ]
 
 
