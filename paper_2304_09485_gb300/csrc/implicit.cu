@@ -436,12 +436,22 @@ __global__ void __launch_bounds__(kBlock) k_mupdate(int64_t n, T *__restrict__ w
   grid_sum(s, partials, count, norm_out, 1);
 }
 
-// v = w / h (v = 0 after a breakdown h == 0)
+// v = w / h (v = 0 after a breakdown h == 0), 16 bytes per thread and step
 template <typename T>
 __global__ void k_scale(int64_t n, const T *__restrict__ w, const double *__restrict__ h, T *__restrict__ v) {
+  typedef typename Vec16<T>::type TV;
+  constexpr int L = Vec16<T>::n;
   const double hv = *h;
   const T ih = hv != 0.0 ? (T)(1.0 / hv) : T(0);
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) v[k] = w[k] * ih;
+  const int64_t nv = n / L, stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nv; k += stride) {
+    TV x = reinterpret_cast<const TV *>(w)[k];
+    T *xa = reinterpret_cast<T *>(&x);
+#pragma unroll
+    for (int l = 0; l < L; l++) xa[l] *= ih;
+    reinterpret_cast<TV *>(v)[k] = x;
+  }
+  for (int64_t k = nv * L + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += stride) v[k] = w[k] * ih;
 }
 
 // y minimises || beta e1 - H y || (Givens rotations in place on H, one thread, FP64)
@@ -451,14 +461,35 @@ __global__ void k_givens(int m, double *__restrict__ H, const double *__restrict
   *res_out = givens_lsq(m, H, *beta, y);
 }
 
-// dx += sum_j y_j V_j (FP64 accumulation; V of either precision, stride vs)
+// dx += sum_j y_j V_j (FP64 accumulation in the order of j; V of either
+// precision, stride vs, read 16 bytes per vector and step)
 template <typename T>
-__global__ void k_combine(int64_t n, int64_t vs, int m, const T *__restrict__ V, const double *__restrict__ y,
-                          double *__restrict__ dx) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-    double s = dx[k];
-    for (int j = 0; j < m; j++) s = fma(y[j], (double)V[(size_t)j * vs + k], s);
-    dx[k] = s;
+__global__ void __launch_bounds__(kBlock) k_combine(int64_t n, int64_t vs, int m, const T *__restrict__ V,
+                                                    const double *__restrict__ y, double *__restrict__ dx) {
+  typedef typename Vec16<T>::type TV;
+  constexpr int L = Vec16<T>::n;
+  __shared__ double ys[kGramLd];
+  for (int j = threadIdx.x; j < m; j += blockDim.x) ys[j] = y[j];
+  __syncthreads();
+  const int64_t nv = n / L, stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nv; k += stride) {
+    double acc[L];
+#pragma unroll
+    for (int l = 0; l < L; l++) acc[l] = dx[k * L + l];
+#pragma unroll 4
+    for (int j = 0; j < m; j++) {
+      const TV v = reinterpret_cast<const TV *>(V + (size_t)j * vs)[k];
+      const T *va = reinterpret_cast<const T *>(&v);
+#pragma unroll
+      for (int l = 0; l < L; l++) acc[l] = fma(ys[j], (double)va[l], acc[l]);
+    }
+#pragma unroll
+    for (int l = 0; l < L; l++) dx[k * L + l] = acc[l];
+  }
+  for (int64_t k = nv * L + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += stride) {
+    double acc = dx[k];
+    for (int j = 0; j < m; j++) acc = fma(ys[j], (double)V[(size_t)j * vs + k], acc);
+    dx[k] = acc;
   }
 }
 
