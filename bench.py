@@ -168,6 +168,19 @@ def cpu_baseline(steps=1, max_seconds=30.0):
             "seconds": dt}
 
 
+# the default workload's size: 6 patches x 32 x 32 x 64 layers, 6 tets per hex;
+# faces (4 N + boundary faces) / 2 with 2 x 6 x 32^2 x 2 boundary triangles
+C2_CELLS = 6 * 32 * 32 * 64 * 6
+C2_FACES = (4 * C2_CELLS + 24 * 32 * 32) // 2
+
+
+def step_config(name, n_cells, n_faces, world):
+    """The `config` object of the whole-step line (both arms)."""
+    return {"workload": name, "n_cells": int(n_cells), "n_faces": int(n_faces), "parallelism": f"replicas{world}",
+            "step": "dt + R(U) + A + 3 x GMRES(20) + update",
+            "l2": "inputs larger than L2 (mesh data + Jacobian + Krylov basis >> 129 MB)"}
+
+
 def run_reference(args, rank, world):
     """The reference arm: the CPU oracle (the paper publishes no code) on the same
     metric and workload, each step a bounded sample of it (one implicit step on
@@ -189,8 +202,7 @@ def run_reference(args, rank, world):
     res = {"metric": METRIC, "value": value, "unit": "Mcells/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1000.0 * t_all / max(1, args.steps), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": name, "parallelism": f"replicas{world}",
-                      "step": "dt + R(U) + A + 3 x GMRES(20) + update"},
+           "config": step_config(name, C2_CELLS, C2_FACES, world),
            "impl": "reference", "cpu_baseline": cb,
            "e2e": {"value": value, "unit": "Mcells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(res))
@@ -728,9 +740,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "Mcells/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": name, "n_cells": m.n_tet, "n_faces": F, "parallelism": f"replicas{world}",
-                   "step": "dt + R(U) + A + 3 x GMRES(20) + update",
-                   "l2": "inputs larger than L2 (mesh data + Jacobian + Krylov basis >> 129 MB)"},
+        "config": step_config(name, m.n_tet, F, world),
         "residual_only": {"value": m.n_tet / (res_ms / 1000.0) / 1e6, "unit": "Mcells/s", "ms": res_ms},
         "mixed": {"value": world * m.n_tet / (mixed_ms / 1000.0) / 1e6, "unit": "Mcells/s", "ms_per_step": mixed_ms,
                   "note": "same step with FP32 Krylov basis, Arnoldi and Jacobi (FP64 residual and update)",
