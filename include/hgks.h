@@ -361,7 +361,9 @@ hgks_status hgks_server_submit(hgks_server server, const double *xyz, int64_t n_
                                const double *Q0, const double *G0, double drop_tol, int32_t max_steps,
                                int64_t *id_out);
 /* One scheduling round (admit, one batched step, retire). Outputs (may be
- * NULL): solves finished in this round, solves running, requests waiting.
+ * NULL): solves finished in this round, solves running, requests waiting
+ * (for their build, in it, or for admission: zero running and zero waiting
+ * means every request submitted so far has finished).
  * Drive the rounds from one thread; submit, status, cancel and collect may be
  * called from any thread meanwhile. */
 hgks_status hgks_server_step(hgks_server server, int32_t *n_finished, int32_t *n_running, int32_t *n_waiting);

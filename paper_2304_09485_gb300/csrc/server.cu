@@ -66,6 +66,7 @@ struct hgks_server_s {
   std::mutex mu;
   std::condition_variable cv;
   std::deque<Request *> to_build;
+  int building = 0;                     // taken off to_build by the builder, not yet back (still waiting)
   std::deque<Request *> built;          // built, waiting for admission (submission order)
   std::map<int64_t, std::unique_ptr<Request>> all;
   std::vector<Request *> running;       // by slot
@@ -87,6 +88,7 @@ void builder_loop(hgks_server_s *S) {
       if (S->stop) return;
       r = S->to_build.front();
       S->to_build.pop_front();
+      S->building++;
     }
     std::string err;
     hgks_status st;
@@ -101,6 +103,7 @@ void builder_loop(hgks_server_s *S) {
       r->hm = HostMesh{};
     }
     std::lock_guard<std::mutex> lk(S->mu);
+    S->building--;
     r->t_built = now_s(S->t0);
     if (r->cancel) {
       r->status = HGKS_ERR_CANCELLED;
@@ -355,7 +358,9 @@ hgks_status hgks_server_step(hgks_server S, int32_t *n_finished, int32_t *n_runn
   for (auto *r : S->running) run += r ? 1 : 0;
   if (n_finished) *n_finished = fin;
   if (n_running) *n_running = run;
-  if (n_waiting) *n_waiting = (int32_t)(S->to_build.size() + S->built.size());
+  // a request under construction still waits: a caller that drains the server
+  // until nothing runs or waits must not stop while the builder holds one
+  if (n_waiting) *n_waiting = (int32_t)(S->to_build.size() + S->building + S->built.size());
   return HGKS_OK;
 }
 
