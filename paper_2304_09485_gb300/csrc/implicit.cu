@@ -436,6 +436,129 @@ __global__ void __launch_bounds__(kBlock) k_mupdate(int64_t n, T *__restrict__ w
   grid_sum(s, partials, count, norm_out, 1);
 }
 
+// ---- modified Gram-Schmidt two basis vectors per pass (FP64 vectors) ----
+// For a pair (v_c, v_{c+1}) Algorithm 1 takes h_c = (w_c, v_c) and
+//   h_{c+1} = (w_c - h_c v_c, v_{c+1}) = (w_c, v_{c+1}) - h_c g_c,  g_c = (v_c, v_{c+1}),
+// so one pass over w, v_c and v_{c+1} gives both coefficients. The same pass first
+// subtracts the previous pair (v_a, v_b) with its known coefficients, in MGS
+// order. The last pass of step j (vc == nullptr) subtracts the last vectors and
+// takes ||w|| and (w, v_j): then g_j = (v_j, w / ||w||) = (v_j, v_{j+1}) for the
+// steps that follow. Per pair 48 bytes and 4 FMAs per element (24 bytes per basis
+// vector against 32 for one vector per pass) keep the pass bound by HBM.
+//   update: w -= ha va; if vb: w -= hb vb
+//   vc:     *hc_out = (w, vc); if vd: *hd_out = (w, vd) - (w, vc) * *g_io
+//   !vc:    *hc_out = ||w||; *g_io = (w, vlast) / ||w|| (0 if ||w|| == 0), vlast = vb ? vb : va
+template <typename T, int NB, int ND>
+__global__ void __launch_bounds__(kBlock) k_mgs2(int64_t n, T *__restrict__ w, const T *__restrict__ va,
+                                                 const T *__restrict__ vb, const double *__restrict__ ha,
+                                                 const double *__restrict__ hb, const T *__restrict__ vc,
+                                                 const T *__restrict__ vd, T *partials, unsigned int *count,
+                                                 double *hc_out, double *hd_out, double *g_io) {
+  // NB: vectors subtracted (1: va, 2: va and vb); ND: vectors dotted (0: the last
+  // pass, 1: vc, 2: vc and vd)
+  typedef typename Vec16<T>::type TV;
+  constexpr int L = Vec16<T>::n;
+  constexpr bool fin = ND == 0;
+  const T na = (T)(-*ha), nb = NB == 2 ? (T)(-*hb) : T(0);
+  // the vectors of the two sums: (w, x0) and (w, x1); the last pass: x0 = w, x1 = vlast
+  const T *x1 = fin ? (NB == 2 ? vb : va) : vd;
+  T s0 = T(0), s1 = T(0);
+  const int64_t nv = n / L, stride = (int64_t)gridDim.x * blockDim.x;
+  const TV *VA = reinterpret_cast<const TV *>(va), *VB = reinterpret_cast<const TV *>(vb);
+  const TV *VC = reinterpret_cast<const TV *>(vc), *X1 = reinterpret_cast<const TV *>(x1);
+  TV *WV = reinterpret_cast<TV *>(w);
+#pragma unroll 2
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nv; k += stride) {
+    // every load of the step first (w is written only after them)
+    TV wk = WV[k];
+    const TV ak = VA[k];
+    TV bk, ck, xk;
+    if constexpr (NB == 2) bk = VB[k];
+    if constexpr (!fin) ck = VC[k];
+    if constexpr (fin || ND == 2) xk = X1[k];
+    T *wa = reinterpret_cast<T *>(&wk);
+    const T *aa = reinterpret_cast<const T *>(&ak);
+#pragma unroll
+    for (int l = 0; l < L; l++) wa[l] = fma(na, aa[l], wa[l]);
+    if constexpr (NB == 2) {
+      const T *ba = reinterpret_cast<const T *>(&bk);
+#pragma unroll
+      for (int l = 0; l < L; l++) wa[l] = fma(nb, ba[l], wa[l]);
+    }
+    if constexpr (fin) {
+#pragma unroll
+      for (int l = 0; l < L; l++) s0 = fma(wa[l], wa[l], s0);
+    } else {
+      const T *ca = reinterpret_cast<const T *>(&ck);
+#pragma unroll
+      for (int l = 0; l < L; l++) s0 = fma(wa[l], ca[l], s0);
+    }
+    if constexpr (fin || ND == 2) {
+      const T *xa = reinterpret_cast<const T *>(&xk);
+#pragma unroll
+      for (int l = 0; l < L; l++) s1 = fma(wa[l], xa[l], s1);
+    }
+    WV[k] = wk;
+  }
+  for (int64_t k = nv * L + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += stride) {
+    T wk = fma(na, va[k], w[k]);
+    if constexpr (NB == 2) wk = fma(nb, vb[k], wk);
+    w[k] = wk;
+    s0 = fma(wk, fin ? wk : vc[k], s0);
+    if constexpr (fin || ND == 2) s1 = fma(wk, x1[k], s1);
+  }
+  // deterministic reduction of both sums (as grid_sum)
+  __shared__ bool last;
+  const T b0 = block_sum(s0);
+  const T b1 = block_sum(s1);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = b0;
+    partials[gridDim.x + blockIdx.x] = b1;
+    __threadfence();
+    const unsigned int prev = atomicAdd(count, 1u);
+    last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  T t0 = T(0), t1 = T(0);
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+    t0 += ((volatile T *)partials)[b];
+    t1 += ((volatile T *)partials)[gridDim.x + b];
+  }
+  t0 = block_sum(t0);
+  t1 = block_sum(t1);
+  if (threadIdx.x == 0) {
+    if (fin) {
+      const double nrm = sqrt((double)t0);
+      *hc_out = nrm;
+      *g_io = nrm > 0.0 ? (double)t1 / nrm : 0.0;
+    } else {
+      *hc_out = (double)t0;
+      if (ND == 2) *hd_out = (double)t1 - (double)t0 * *g_io;
+    }
+    *count = 0u;
+  }
+}
+
+// one pass of the pair MGS with the instance for the number of vectors
+template <typename T>
+void launch_mgs2(cudaStream_t st, int64_t n, T *w, const T *va, const T *vb, const double *ha, const double *hb,
+                 const T *vc, const T *vd, T *partials, unsigned int *count, double *hc_out, double *hd_out,
+                 double *g_io) {
+  const int nb = vb ? 2 : 1, nd = vc ? (vd ? 2 : 1) : 0;
+#define HGKS_MGS2(NB, ND)                                                                                        \
+  k_mgs2<T, NB, ND><<<kRedBlocks, kBlock, 0, st>>>(n, w, va, vb, ha, hb, vc, vd, partials, count, hc_out, hd_out, \
+                                                   g_io)
+  if (nb == 1 && nd == 0) HGKS_MGS2(1, 0);
+  else if (nb == 1 && nd == 1) HGKS_MGS2(1, 1);
+  else if (nb == 1) HGKS_MGS2(1, 2);
+  else if (nd == 0) HGKS_MGS2(2, 0);
+  else if (nd == 1) HGKS_MGS2(2, 1);
+  else HGKS_MGS2(2, 2);
+#undef HGKS_MGS2
+}
+
 // v = w / h (v = 0 after a breakdown h == 0), 16 bytes per thread and step
 template <typename T>
 __global__ void k_scale(int64_t n, const T *__restrict__ w, const double *__restrict__ h, T *__restrict__ v) {
@@ -699,14 +822,25 @@ void gmres_t(const DevMesh &m, Scratch &s, const KBuf<T> &k, const hgks_params &
         k_mupdate<T><<<kRedBlocks, kBlock, 0, st>>>(n, k.w, k.V, vs, j, mk, H, k.red, s.red_count, H + (j + 1) * mk + j);
         HGKS_PROF_END(K_DOT, st);
       } else {
-        // modified Gram-Schmidt step by step: w -= h_ij v_i, then h_{i+1,j} = (w, v_{i+1}) or ||w||
-        for (int i = 0; i <= j; i++) {
-          const bool last = (i == j);
+        // modified Gram-Schmidt two vectors per pass (h_0j came with the product):
+        // subtract the pending vectors (ua, ub), take the inner products with the
+        // next two (c, c + 1); the last pass takes ||w|| and g_j = (v_j, v_{j+1})
+        // into gram[j]
+        auto vec = [&](int q) { return k.V + (size_t)q * vs; };
+        int ua = 0, ub = -1, c = 1;
+        for (;;) {
+          const bool fin = c > j;
+          const int d = (!fin && c + 1 <= j) ? c + 1 : -1;
           HGKS_PROF_BEGIN(K_DOT, st);
-          k_axpy_dot<T><<<kRedBlocks, kBlock, 0, st>>>(n, k.w, k.V + (size_t)i * vs, H + i * mk + j,
-                                                         last ? k.w : k.V + (size_t)(i + 1) * vs, last ? 1 : 0, k.red,
-                                                         s.red_count, H + (i + 1) * mk + j);
+          launch_mgs2<T>(st, n, k.w, vec(ua), ub >= 0 ? vec(ub) : nullptr, H + ua * mk + j,
+                         ub >= 0 ? H + ub * mk + j : nullptr, fin ? nullptr : vec(c), d >= 0 ? vec(d) : nullptr, k.red,
+                         s.red_count, fin ? H + (j + 1) * mk + j : H + c * mk + j, d >= 0 ? H + d * mk + j : nullptr,
+                         fin ? gram + j : (d >= 0 ? gram + c : nullptr));
           HGKS_PROF_END(K_DOT, st);
+          if (fin) break;
+          ua = c;
+          ub = d;
+          c += d >= 0 ? 2 : 1;
         }
       }
       HGKS_PROF_BEGIN(K_SCALE, st);
