@@ -23,20 +23,31 @@ SOURCES = ["orc_linalg.c", "orc_mesh.c", "orc_gks.c", "orc_recon.c", "orc_solver
 LIBNAME = os.path.join(HERE, "_build", "liboracle.so")
 
 
+# A test that plants a mistake in the oracle builds a modified copy of the
+# sources elsewhere (compile_library) and points this variable at it; lib()
+# then loads that copy instead of building the oracle.
+PLANTED_ENV = "HGKS_ORACLE_LIB"
+
+
+def compile_library(src_dir: str, out_path: str) -> str:
+    """gcc (-O2, OpenMP, no FP contraction) of the oracle sources in src_dir."""
+    tmp = out_path + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-o", tmp] + [os.path.join(src_dir, s) for s in SOURCES] + ["-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, out_path)
+    return out_path
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (-O2, OpenMP, no FP contraction)."""
+    """Compile the oracle in place (oracle/_build/liboracle.so)."""
     os.makedirs(os.path.dirname(LIBNAME), exist_ok=True)
     srcs = [os.path.join(HERE, s) for s in SOURCES] + [os.path.join(HERE, "orc.h")]
     if not force and os.path.exists(LIBNAME):
         t = os.path.getmtime(LIBNAME)
         if all(os.path.getmtime(s) <= t for s in srcs):
             return LIBNAME
-    tmp = LIBNAME + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-fopenmp",
-           "-ffp-contract=off", "-o", tmp] + [os.path.join(HERE, s) for s in SOURCES] + ["-lm"]
-    subprocess.check_call(cmd)
-    os.replace(tmp, LIBNAME)
-    return LIBNAME
+    return compile_library(HERE, LIBNAME)
 
 
 class Params(C.Structure):
@@ -72,7 +83,7 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        path = build()
+        path = os.environ.get(PLANTED_ENV) or build()
         L = C.CDLL(path)
         vp, i64, i32, dp = C.c_void_p, C.c_int64, C.c_int32, C.POINTER(C.c_double)
         L.orc_mesh_create.restype = vp

@@ -610,3 +610,212 @@ def test_local_time_step_invariants():
     d2 = o2.local_dt(O.make_params(cfl=1.0), Q)
     np.testing.assert_allclose(d3, 3 * d1, rtol=1e-14)
     np.testing.assert_allclose(d2, 2 * d1, rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# pins added where a planted mistake went unnoticed (tests/test_oracle_planted.py)
+# ---------------------------------------------------------------------------
+
+def test_cell_volumes_fill_the_box():
+    """The tetrahedra of the periodic unit cube fill it: their volumes sum to 1."""
+    om = O.OracleMesh(I.periodic_cube_mesh(4))
+    assert om.vol.sum() == pytest.approx(1.0, rel=1e-13)
+
+
+def test_local_time_step_acoustic_scaling():
+    """At rest the step is limited by sound waves alone: it is finite and scales like
+    1/a (four times the pressure at the same density halves it). With the flow speed
+    and the sound speed both doubled it halves as well; a flow or a viscosity only
+    shortens it."""
+    m = I.periodic_cube_mesh(4)
+    om = O.OracleMesh(m)
+    n = m.n_tet
+    p = O.make_params(cfl=1.0)
+    d1 = om.local_dt(p, I.uniform_state(n, u=0.0, p=1.0))
+    d4 = om.local_dt(p, I.uniform_state(n, u=0.0, p=4.0))
+    assert np.all(np.isfinite(d1)) and np.all(d1 > 0)
+    np.testing.assert_allclose(d4, 0.5 * d1, rtol=1e-13)
+    m1 = om.local_dt(p, I.uniform_state(n, u=0.3, v=-0.2, w=0.1, p=1.0))
+    m4 = om.local_dt(p, I.uniform_state(n, u=0.6, v=-0.4, w=0.2, p=4.0))
+    np.testing.assert_allclose(m4, 0.5 * m1, rtol=1e-13)
+    assert np.all(m1 < d1)
+    pv = O.make_params(cfl=1.0, viscous=1, mu=1e-2)
+    assert np.all(om.local_dt(pv, I.uniform_state(n, u=0.3, v=-0.2, w=0.1, p=1.0)) < m1)
+
+
+def _euler_flux_rows(Q, n, g=GAMMA):
+    rho = Q[:, 0]
+    u = Q[:, 1:4] / rho[:, None]
+    p = (g - 1) * (Q[:, 4] - 0.5 * rho * np.einsum("ij,ij->i", u, u))
+    un = np.einsum("ij,ij->i", u, n)
+    return np.column_stack([rho * un, Q[:, 1:4] * un[:, None] + p[:, None] * n, (Q[:, 4] + p) * un])
+
+
+def test_assembled_matrix_is_the_first_order_rusanov_jacobian():
+    """Eq. (A-system-2) with the split Jacobians of Eq. (deri-matrix): A = |Omega|/dt I +
+    dR1/dQ, R1 the first-order residual sum_p S_p [(F(Q_i) + F(Q_p)).n_p / 2 -
+    lambda_p (Q_p - Q_i) / 2] with lambda_p = |U.n| + a at the face average held fixed
+    and the outer state of a boundary face held fixed. Products A x against central
+    differences of R1; the geometry and the neighbours are computed here from the
+    vertex lists, the time steps are arbitrary."""
+    m = I.cavity_mesh(3)
+    om = O.OracleMesh(m)
+    n = m.n_tet
+    Q, _ = I.smooth_state(m, amp=0.1)
+    rng = np.random.default_rng(59)
+    dt = rng.uniform(0.5, 2.0, n) * 1e-2
+    diag, off = om.jacobian(O.make_params(scheme=0), Q, dt=dt)
+    A = dense_A(om, diag, off)
+    V = m.xyz[m.tet4]
+    vol = np.abs(np.einsum("ij,ij->i", V[:, 1] - V[:, 0], np.cross(V[:, 2] - V[:, 0], V[:, 3] - V[:, 0]))) / 6
+    faces = {}
+    for i in range(n):
+        for k in range(4):
+            faces.setdefault(tuple(sorted(np.delete(m.tet4[i], k))), []).append((i, k))
+    cell, nbr, nrm, area = [], [], [], []
+    for i in range(n):
+        for k in range(4):
+            F3 = V[i, [a for a in range(4) if a != k]]
+            c = np.cross(F3[1] - F3[0], F3[2] - F3[0])
+            if c @ (F3[0] - V[i, k]) < 0:
+                c = -c
+            other = [j for j, _ in faces[tuple(sorted(np.delete(m.tet4[i], k)))] if j != i]
+            cell.append(i); nbr.append(other[0] if other else -1)
+            area.append(0.5 * np.linalg.norm(c)); nrm.append(c / np.linalg.norm(c))
+    cell, nbr, nrm, area = np.array(cell), np.array(nbr), np.array(nrm), np.array(area)
+    inner = nbr >= 0
+    Qf = np.where(inner[:, None], 0.5 * (Q[cell] + Q[np.maximum(nbr, 0)]), Q[cell])
+    rf = Qf[:, 0]
+    uf = Qf[:, 1:4] / rf[:, None]
+    pf = (GAMMA - 1) * (Qf[:, 4] - 0.5 * rf * np.einsum("ij,ij->i", uf, uf))
+    lam = np.abs(np.einsum("ij,ij->i", uf, nrm)) + np.sqrt(GAMMA * pf / rf)
+    Qg = Q[cell]                                  # outer state of the boundary faces, held fixed
+
+    def R1(X):
+        Xo = np.where(inner[:, None], X[np.maximum(nbr, 0)], Qg)
+        Xi = X[cell]
+        fl = area[:, None] * (0.5 * (_euler_flux_rows(Xi, nrm) + _euler_flux_rows(Xo, nrm)) - 0.5 * lam[:, None] * (Xo - Xi))
+        out = np.zeros_like(X)
+        np.add.at(out, cell, fl)
+        return out
+    for trial in range(2):
+        x = rng.normal(size=(n, 5)) * np.abs(Q).mean(0)
+        e = 1e-6
+        ref = (vol / dt)[:, None] * x + (R1(Q + e * x) - R1(Q - e * x)) / (2 * e)
+        np.testing.assert_allclose(A @ x.ravel(), ref.ravel(), rtol=1e-6, atol=1e-7 * np.abs(ref).max())
+
+
+def test_density_residual_norm_is_the_mean_rate_of_change():
+    """Algorithm 1's test residual, the L1 norm of the density residual (Sec. 5), read as
+    (1/N) sum_i |R_rho,i| / |Omega_i|: the mean of |d rho / dt| over the cells. On the
+    density wave rho = 1 + 0.2 sin 2 pi (x+y+z) carried by U = (1,1,1)/2 it approaches the
+    mean of |cell average of -U . grad rho|, whose amplitude is 0.6 pi."""
+    u0 = 0.5
+
+    def Qx(X):
+        rho = 1 + 0.2 * np.sin(2 * np.pi * X.sum(-1))
+        return np.stack([rho, rho * u0, rho * u0, rho * u0, 1 / (GAMMA - 1) + 0.5 * rho * 3 * u0 * u0], -1)
+    m = I.periodic_cube_mesh(16, jitter=0.1)
+    om = O.OracleMesh(m)
+    V = m.xyz[m.tet4]
+    Q = cell_average(V, Qx)
+    p = O.make_params(scheme=0, weights=0, flux_dt=1e-8, characteristic=1)
+    _, _, hist, _ = om.solve_steady(p, Q, max_steps=0)
+    drho = cell_average(V, lambda X: -u0 * 0.2 * 2 * np.pi * 3 * np.cos(2 * np.pi * X.sum(-1)))
+    assert hist[0] == pytest.approx(np.abs(drho).mean(), rel=0.01)
+
+
+def test_prandtl_fix_scales_the_heat_flux():
+    """Pr != 1 (the Prandtl-number fix, reading of the paper's Pr): the energy flux gains
+    (1/Pr - 1) q, q the heat flux of the time-averaged distribution relative to the
+    velocity of Q0. For continuous data that distribution is g0 - tau (a.u + A) g0 +
+    (dt/2) A g0: its heat flux is the Navier-Stokes -kappa dT/dx (kappa = (K+5)/2 mu,
+    the BGK value) plus (dt/2) (K+5)/2 p dU_x/dt, the heat flux relative to a fixed
+    velocity of a Maxwellian whose velocity drifts by dU/dt over the half step."""
+    rng = np.random.default_rng(61)
+    mu, dt, Pr = 2e-3, 0.02, 0.72
+    for _ in range(3):
+        W = rand_state(rng)
+        dW = rng.normal(size=(3, 5)) * 0.3
+        F1, _ = O.gks_flux(O.make_params(viscous=1, mu=mu, Pr=1.0), W, dW, W, dW, dt)
+        FP, _ = O.gks_flux(O.make_params(viscous=1, mu=mu, Pr=Pr), W, dW, W, dW, dt)
+        rho, u, pr = prim_of(W)
+        T = pr / rho
+        drho = dW[0, 0]
+        du = (dW[0, 1:4] - u * drho) / rho
+        dp = (GAMMA - 1) * (dW[0, 4] - 0.5 * drho * (u @ u) - rho * (u @ du))
+        dT = (dp - T * drho) / rho
+        # Euler time derivative of W by central differences of the Euler fluxes
+        dQdt = np.zeros(5)
+        for d in range(3):
+            nd = np.eye(3)[d]
+            for k in range(5):
+                h = 1e-7 * max(1.0, abs(W[k]))
+                e = np.zeros(5); e[k] = h
+                dQdt -= (euler_flux(W + e, nd) - euler_flux(W - e, nd)) / (2 * h) * dW[d, k]
+        dux_dt = (dQdt[1] - u[0] * dQdt[0]) / rho
+        q = -mu * (K + 5) / 2 * dT + 0.5 * dt * (K + 5) / 2 * pr * dux_dt
+        expect = F1.copy()
+        expect[4] += (1 / Pr - 1) * q
+        np.testing.assert_allclose(FP, expect, rtol=1e-7, atol=1e-9)
+        assert abs(FP[4] - F1[4]) > 1e-5          # the fix is not negligible here
+
+
+def test_nonlinear_weights_brute_force():
+    """Eq. (weno) with nonlinear weights, recomputed from the definitions for single
+    cells on a quadratic density field (the other components uniform, the projection
+    to characteristic variables off): P0 is the quadratic itself (the big stencil fits
+    it exactly), P_m the least-squares linear fit of the cell averages over the
+    paper's sub-stencil m (the three face neighbours of its triple and the three other
+    neighbours of face neighbour m, Sec. 3.1), beta_m from its defining integrals
+    (every distinct derivative multi-index up to r_0 = 2, r_m = 1, scaled by
+    |Omega|^(2|l|/3 - 1), Sec. 3.4), tau_Z the mean of |beta_0 - beta_m|, and the
+    weights gamma_m (1 + tau_Z / (beta_m + eps)) normalised."""
+    m = I.periodic_cube_mesh(5)
+    om = O.OracleMesh(m)
+    rng = np.random.default_rng(67)
+    Hq = rng.normal(size=(3, 3)) * 3.0
+    Hq = 0.05 * (Hq + Hq.T)
+    gq = 0.05 * rng.normal(size=3)
+
+    def rho(X):
+        Y = X - 0.5
+        return 1.0 + Y @ gq + 0.5 * np.einsum("...i,ij,...j->...", Y, Hq, Y)
+
+    def f(X):
+        z = np.zeros(X.shape[:-1])
+        return np.stack([rho(X), z, z, z, z + 2.5], -1)
+    Q = tet_average_quadratic(m.xyz, m.tet4, f)
+    V = m.xyz[m.tet4]
+    cen = V.mean(1)
+    vol = np.abs(np.einsum("ij,ij->i", V[:, 1] - V[:, 0], np.cross(V[:, 2] - V[:, 0], V[:, 3] - V[:, 0]))) / 6
+    nb = om.neighbours
+    p = O.make_params(scheme=0, weights=0, characteristic=0)
+    M, gm = 4, p.lin_weight
+    g0 = 1 - M * gm
+    TRIPLES = [(0, 1, 2), (0, 1, 3), (1, 2, 3), (2, 0, 3)]   # S_1..S_4 of Sec. 3.1, faces from 0
+    inner = np.where(np.all((cen > 0.35) & (cen < 0.65), axis=1))[0]
+    moved = 0.0
+    for i in inner[:12]:
+        b = []
+        for mm in range(4):
+            cells = [nb[i, t] for t in TRIPLES[mm]] + [k for k in nb[nb[i, mm]] if k != i]
+            cells = list(dict.fromkeys(int(c) for c in cells))
+            b.append(np.linalg.lstsq(cen[cells] - cen[i], Q[cells, 0] - Q[i, 0], rcond=None)[0])
+        # beta_0 of the quadratic: |Omega|^(-1/3) int |grad|^2 + |Omega|^(1/3) int (second derivatives)^2
+        grad2 = tet_average_quadratic(m.xyz, m.tet4[i:i + 1],
+                                      lambda X: (((X - 0.5) @ Hq + gq) ** 2).sum(-1)[..., None])[0, 0]
+        second = Hq[0, 0] ** 2 + Hq[1, 1] ** 2 + Hq[2, 2] ** 2 + Hq[0, 1] ** 2 + Hq[0, 2] ** 2 + Hq[1, 2] ** 2
+        b0 = vol[i] ** (2 / 3) * grad2 + vol[i] ** (4 / 3) * second
+        bm = np.array([vol[i] ** (2 / 3) * (bb @ bb) for bb in b])
+        tz = np.abs(b0 - bm).sum() / M
+        w = np.array([g0 * (1 + tz / (b0 + p.weno_eps))] + list(gm * (1 + tz / (bm + p.weno_eps))))
+        w /= w.sum()
+        moved = max(moved, np.abs(w - np.array([g0] + [gm] * 4)).max())
+        for slot in range(4):
+            gp = om.face_gauss_points(int(i), slot)
+            Pm = np.array([Q[i, 0] + (gp - cen[i]) @ bb for bb in b])          # [4, 3 points]
+            expect = w[0] * (rho(gp) / g0 - (gm / g0) * Pm.sum(0)) + (w[1:, None] * Pm).sum(0)
+            _, _, Wg, _ = om.recon_side(p, Q, None, int(i), slot)
+            np.testing.assert_allclose(Wg[:, 0], expect, rtol=1e-11, atol=1e-12)
+    assert moved > 1e-3                              # the weights are far from the linear ones
