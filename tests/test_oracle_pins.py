@@ -819,3 +819,24 @@ def test_nonlinear_weights_brute_force():
             _, _, Wg, _ = om.recon_side(p, Q, None, int(i), slot)
             np.testing.assert_allclose(Wg[:, 0], expect, rtol=1e-11, atol=1e-12)
     assert moved > 1e-3                              # the weights are far from the linear ones
+
+
+def test_compact_gradient_update_is_exact_for_linear_fields():
+    """Eq. (derivative): the cell-averaged gradients from the Gauss-point values of
+    Eq. (point) by Gauss's theorem. For a linear field (the HWENO reconstruction is
+    exact, the face rule integrates linear functions exactly) and a negligible time
+    step inside the flux, the update returns the field's gradient in every cell."""
+    m = I.periodic_cube_mesh(4)
+    om = O.OracleMesh(m)
+    rng = np.random.default_rng(71)
+    A = rng.normal(size=(5, 3)) * 0.05
+    b = np.array([1.0, 0.2, -0.1, 0.05, 2.5])
+    cen = m.xyz[m.tet4].mean(1)
+    # a linear field is not periodic: use the cells whose faces and stencils stay off the seam
+    inner = np.where(np.all((cen > 0.3) & (cen < 0.7), axis=1))[0]
+    f = lambda X: X @ A.T + b
+    Q = tet_average_quadratic(m.xyz, m.tet4, f)
+    G = np.repeat(A.reshape(1, 15), m.n_tet, axis=0)
+    p = O.make_params(scheme=1, weights=0, flux_dt=1e-10)
+    _, Gn = om.residual(p, Q, G)
+    np.testing.assert_allclose(Gn[inner], G[inner], rtol=1e-7, atol=1e-8)

@@ -72,6 +72,24 @@ PLANTED = [
      "tz += fabs(beta[0] - beta[1 + mm]) / M;", "tz += fabs(beta[0] - beta[1 + mm]);"),
     ("nonlinear weight of P0 with beta_1", "orc_recon.c",
      "om[0] = gam0 * (1.0 + tz / (beta[0] + p->weno_eps));", "om[0] = gam0 * (1.0 + tz / (beta[1] + p->weno_eps));"),
+    # compact HWENO (Sec. 3.3, Eq. (compact-big-1/2), Eq. (derivative))
+    ("HWENO: neighbour gradients taken from the target", "orc_recon.c",
+     "for (int j = 0; j < 3; j++) data[4 + 3 * k + j] = G[15 * ck + 3 * c + j];",
+     "for (int j = 0; j < 3; j++) data[4 + 3 * k + j] = G[15 * i + 3 * c + j];"),
+    ("HWENO sub-stencil: the neighbour's gradient dropped", "orc_recon.c",
+     "if (jm >= 0) for (int j = 0; j < 3; j++) dm[4 + j] = G[15 * jm + 3 * c + j];", ""),
+    ("HWENO fit: equality rows without the target's own average", "orc_mesh.c",
+     "for (int d = 0; d < 9; d++) C[r][d] = av[d] - avg_i[d];", "for (int d = 0; d < 9; d++) C[r][d] = av[d];"),
+    ("HWENO fit: gradient data not scaled by h", "orc_mesh.c",
+     "double dval = m->h[rk->cell];", "double dval = 1.0;"),
+    ("HWENO sub-stencil fit: gradient data not scaled by h", "orc_mesh.c",
+     "rhs[j] = (hk[k] / m->h[i]) * hk[k];", "rhs[j] = hk[k] / m->h[i];"),
+    ("compact gradient not divided by the volume", "orc_solver.c",
+     "if (Gnew) for (int64_t i = 0; i < nc; i++) for (int c = 0; c < 15; c++) Gnew[15 * i + c] /= m->vol[i];", ""),
+    ("compact gradient from the face flux instead of the point value", "orc_solver.c",
+     "Gnew[15 * L + 3 * c + d] += Pf[5 * f + c] * n[d];", "Gnew[15 * L + 3 * c + d] += Ff[5 * f + c] * n[d];"),
+    ("point value at t = 0 regardless of the reading", "orc_gks.c",
+     "double ts = p->tstar_end ? dt : 0.0", "double ts = 0.0"),
     # geometry and fits (Sec. 2, Sec. 3.1 - 3.3)
     ("face Gauss points at (1/2, 1/4, 1/4)", "orc_mesh.c",
      "(2.0 / 3.0) * vv[g][d] + (1.0 / 6.0) *", "(1.0 / 2.0) * vv[g][d] + (1.0 / 4.0) *"),
