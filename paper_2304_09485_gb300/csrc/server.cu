@@ -48,7 +48,8 @@ struct Request {
   hgks_status status = HGKS_OK;
   int state = Q_WAIT;
   int slot = -1;
-  bool cancel = false;                 // set by hgks_server_cancel while building or running
+  bool cancel = false;                 // set by hgks_server_cancel while building, admitting or running
+  bool admitting = false;              // at the head of `built`, being placed by the round's thread
   std::vector<double> Q, G;            // result, caller order
   hgks_solve_info info{};
   double t_submit = 0, t_built = 0, t_admit = 0, t_done = 0;
@@ -140,27 +141,56 @@ void to_caller(const std::vector<double> &in, const std::vector<int64_t> &perm, 
     for (int c = 0; c < k; c++) out[(size_t)perm[i] * k + c] = in[(size_t)c * n + i];
 }
 
-// admit built requests in submission order while the arena has room
+// admit built requests in submission order while the arena has room. The head
+// request is marked `admitting` while it is placed outside the lock: a concurrent
+// hgks_server_cancel then only flags it (it stays at the head of `built`, and its
+// mesh and state stay valid) and this function finishes the cancellation.
 hgks_status admit(hgks_server_s &S, bool &changed) {
   Batch &B = *S.B;
+  // under S.mu: take the head request off `built` as cancelled
+  auto cancel_head = [&](Request *r) {
+    S.built.pop_front();
+    r->admitting = false;
+    r->hm = HostMesh{};
+    r->status = HGKS_ERR_CANCELLED;
+    r->state = Q_DONE;
+    r->t_done = now_s(S.t0);
+  };
+  auto stop_admitting = [&](Request *r) {
+    std::lock_guard<std::mutex> lk(S.mu);
+    r->admitting = false;
+  };
   for (;;) {
     Request *r = nullptr;
     {
       std::lock_guard<std::mutex> lk(S.mu);
       if (S.built.empty()) return HGKS_OK;
       r = S.built.front();
+      if (r->cancel) {                     // flagged during an earlier attempt
+        cancel_head(r);
+        continue;
+      }
+      r->admitting = true;
     }
     std::vector<double> inv;
     int slot = -1;
     hgks_status st = batch_place(B, source_of(r->hm, inv), r->p, &slot);
-    if (st) return st;
+    if (st) { stop_admitting(r); return st; }
     if (slot < 0) {
       bool empty = true;
       for (auto *q : S.running) empty = empty && q == nullptr;
-      if (!empty) return HGKS_OK;          // the head of the queue waits for room
-      // nothing runs and it still does not fit (its faces exceed the arena's): it never will
       std::lock_guard<std::mutex> lk(S.mu);
+      if (r->cancel) {
+        cancel_head(r);
+        continue;
+      }
+      if (!empty) {                        // the head of the queue waits for room
+        r->admitting = false;
+        return HGKS_OK;
+      }
+      // nothing runs and it still does not fit (its faces exceed the arena's): it never will
       S.built.pop_front();
+      r->admitting = false;
       r->hm = HostMesh{};
       r->status = HGKS_ERR_OOM;
       r->err = "mesh does not fit the server's arena";
@@ -172,12 +202,19 @@ hgks_status admit(hgks_server_s &S, bool &changed) {
     std::vector<double> Qi = to_internal(r->Q0, r->perm, 5), Gi;
     if (cmp) Gi = r->G0.empty() ? std::vector<double>((size_t)15 * r->perm.size(), 0.0) : to_internal(r->G0, r->perm, 15);
     if ((st = batch_set_state(B, slot, Qi.data(), cmp ? Gi.data() : nullptr)) ||
-        (st = batch_arm(B, slot, r->drop, r->max_steps)))
+        (st = batch_arm(B, slot, r->drop, r->max_steps))) {
+      stop_admitting(r);
       return st;
-    if (cudaStreamSynchronize(B.stream) != cudaSuccess) return cuda_error(cudaGetLastError(), "admission");
+    }
+    if (cudaStreamSynchronize(B.stream) != cudaSuccess) {
+      stop_admitting(r);
+      return cuda_error(cudaGetLastError(), "admission");
+    }
     {
+      // admitted; a cancel that came meanwhile retires it at the start of the next round
       std::lock_guard<std::mutex> lk(S.mu);
       S.built.pop_front();
+      r->admitting = false;
       r->hm = HostMesh{};
       r->Q0.clear(); r->Q0.shrink_to_fit();
       r->G0.clear(); r->G0.shrink_to_fit();
@@ -401,7 +438,8 @@ hgks_status hgks_server_cancel(hgks_server S, int64_t id) {
   if (r->state == Q_WAIT) {
     if (!drop(S->to_build)) r->cancel = true;          // being built now: the builder drops it
   } else if (r->state == Q_BUILT) {
-    drop(S->built);
+    if (r->admitting) r->cancel = true;                // being placed now: admission finishes it
+    else drop(S->built);
   } else if (r->state == Q_RUN) {
     r->cancel = true;                                  // leaves at the start of the next round
   }

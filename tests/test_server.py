@@ -252,3 +252,36 @@ def test_cancel_queued_and_running_requests(cuda):
     assert np.isfinite(Q0c).all()
     with pytest.raises(H.HGKSError):
         srv.collect(ids[2])
+
+
+def test_cancel_from_another_thread_while_rounds_run(cuda):
+    """hgks_server_cancel may come from any thread while another drives the rounds:
+    requests cancelled at arbitrary moments (waiting for their build, built, being
+    admitted, running) all end, cancelled or finished, and the others end normally."""
+    import threading
+    probs = problems()
+    srv = H.hgks_server(H.hgks_default_params(**KW), hbm_budget_bytes=1 << 30, max_inflight=1)
+    ids = [srv.submit(m, p, Q0, drop_tol=DROP, max_steps=4) for _ in range(3) for _, m, _, p, Q0 in probs]
+    victims = set(ids[1::2])
+
+    def canceller():
+        rng = np.random.default_rng(5)
+        for rid in sorted(victims):
+            time.sleep(float(rng.uniform(0.0, 0.01)))
+            srv.cancel(rid)
+    t = threading.Thread(target=canceller)
+    t.start()
+    while t.is_alive():
+        fin, run, wait = srv.step()
+        if run == 0:
+            time.sleep(0.001)
+    t.join()
+    _drain(srv)
+    for rid in ids:
+        st = srv.status(rid)
+        assert st.state == 3, (rid, st.state)
+        if rid in victims:
+            assert st.status in (H.HGKS_OK, H.HGKS_ERR_NOT_CONVERGED, H.HGKS_ERR_CANCELLED)
+        else:
+            assert st.status in (H.HGKS_OK, H.HGKS_ERR_NOT_CONVERGED), (rid, st.status)
+    assert any(srv.status(r).status == H.HGKS_ERR_CANCELLED for r in victims)
