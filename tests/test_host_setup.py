@@ -1,0 +1,204 @@
+"""The library's host-side mesh construction (csrc/mesh_setup.cpp), run on the
+CPU through a test-only shim (tests/host_setup/hs_shim.cpp): cell order, face
+table, stencils and the reconstruction fits of Sec. 3.1 - 3.3, checked against
+closed forms and exact polynomial reproduction (not against the oracle)."""
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2304_09485_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2304_09485_gb300", "csrc")
+CUDA_INC = "/usr/local/cuda/include"
+
+
+@pytest.fixture(scope="module")
+def shim(tmp_path_factory):
+    if not os.path.isdir(CUDA_INC):
+        pytest.skip("CUDA headers not found")
+    out = str(tmp_path_factory.mktemp("hs") / "libhs.so")
+    subprocess.check_call(["g++", "-std=c++17", "-O2", "-fPIC", "-shared", "-pthread", "-ffp-contract=off",
+                           "-I" + CUDA_INC, os.path.join(ROOT, "tests", "host_setup", "hs_shim.cpp"),
+                           os.path.join(CSRC, "mesh_setup.cpp"), "-o", out, "-ldl"])
+    L = C.CDLL(out)
+    L.hs_error.restype = C.c_char_p
+    L.hs_get.argtypes = [C.c_char_p, C.c_void_p, C.c_int64]
+    return L
+
+
+class Built:
+    def __init__(self, L, m, mask=3):
+        xyz = np.ascontiguousarray(m.xyz, dtype=np.float64)
+        tet = np.ascontiguousarray(m.tet4, dtype=np.int64)
+        bf = np.ascontiguousarray(m.bface3, dtype=np.int64).reshape(-1, 3)
+        bt = np.ascontiguousarray(m.btag, dtype=np.int32)
+        ps = m.periodic_shift
+        psa = np.ascontiguousarray(ps if ps is not None else np.zeros((0, 3)), dtype=np.float64)
+        sizes = np.zeros(3, dtype=np.int64)
+        p = lambda a: a.ctypes.data_as(C.c_void_p)
+        rc = L.hs_build(p(xyz), C.c_int64(len(xyz)), p(tet), C.c_int64(len(tet)), p(bf), p(bt), C.c_int64(len(bt)),
+                        p(psa), C.c_int32(len(psa)), C.c_int(mask), p(sizes))
+        assert rc == 0, L.hs_error()
+        self.L, self.N, self.F, self.Fb = L, int(sizes[0]), int(sizes[1]), int(sizes[2])
+
+    def get(self, name, dtype, rows=1, per="N"):
+        n = rows * (self.N if per == "N" else self.F)
+        a = np.empty(n, dtype=dtype)
+        assert self.L.hs_get(name.encode(), a.ctypes.data_as(C.c_void_p), a.nbytes) == 0, name
+        return a.reshape(rows, -1) if rows > 1 else a
+
+
+def geometry(m):
+    V = m.xyz[m.tet4]
+    vol = np.abs(np.einsum("ij,ij->i", V[:, 1] - V[:, 0], np.cross(V[:, 2] - V[:, 0], V[:, 3] - V[:, 0]))) / 6
+    return vol, V.mean(1)
+
+
+def tet_average_quadratic(xyz, tet, f):
+    """Exact cell average of a quadratic: -1/20 sum over vertices + 1/5 sum over edge midpoints."""
+    V = xyz[tet]
+    vs = sum(f(V[:, a]) for a in range(4))
+    es = sum(f(0.5 * (V[:, a] + V[:, b])) for a in range(4) for b in range(a + 1, 4))
+    return -vs / 20 + es / 5
+
+
+@pytest.mark.parametrize("kind", ["cavity", "periodic"])
+def test_cell_order_and_face_table(shim, kind):
+    m = I.cavity_mesh(3) if kind == "cavity" else I.periodic_cube_mesh(3)
+    b = Built(shim, m)
+    N, F = b.N, b.F
+    perm = b.get("perm", np.int64)
+    assert N == m.n_tet and np.array_equal(np.sort(perm), np.arange(N))
+    vol, cen = geometry(m)
+    np.testing.assert_allclose(b.get("vol", np.float64), vol[perm], rtol=1e-13)
+    np.testing.assert_allclose(b.get("h", np.float64), np.cbrt(vol[perm]), rtol=1e-13)
+    assert b.Fb == len(m.btag) and 2 * F == 4 * N + b.Fb
+    fl, fr = b.get("fl", np.int32, per="F"), b.get("fr", np.int32, per="F")
+    cnb, cface = b.get("cnb", np.int32, 4), b.get("cface", np.int32, 4)
+    fT, fS = b.get("fT", np.float64, 9, per="F"), b.get("fS", np.float64, per="F")
+    assert np.all(fl >= 0) and int((fr < 0).sum()) == b.Fb
+    assert np.all(fl[fr >= 0] < fr[fr >= 0])                 # left is the lower cell
+    # every (cell, slot) names its face and side; neighbours are mutual
+    area_vec = np.zeros((N, 3))
+    for p_ in range(4):
+        f, side = cface[p_] >> 1, cface[p_] & 1
+        owner = np.where(side == 0, fl[f], fr[f])
+        other = np.where(side == 0, fr[f], fl[f])
+        assert np.array_equal(owner, np.arange(N))
+        assert np.array_equal(cnb[p_], other)
+        sgn = np.where(side == 0, 1.0, -1.0)
+        area_vec += (sgn * fS[f])[:, None] * fT[0:3, f].T
+    for i in range(N):
+        for j in cnb[:, i]:
+            if j >= 0:
+                assert i in cnb[:, j]
+    # closed cells: the outward area vectors of each tetrahedron sum to zero
+    assert np.abs(area_vec).max() <= 1e-14 * fS.max() * 10
+    # face frames are orthonormal
+    Tm = fT.T.reshape(F, 3, 3)
+    np.testing.assert_allclose(np.einsum("fij,fkj->fik", Tm, Tm), np.broadcast_to(np.eye(3), (F, 3, 3)), atol=1e-13)
+    if kind == "cavity":
+        assert fS[fr < 0].sum() == pytest.approx(6.0, rel=1e-12)       # surface of the unit cube
+    # the space-filling-curve order keeps neighbours close in memory
+    dist = np.abs(cnb - np.arange(N)[None, :])[cnb >= 0]
+    assert dist.mean() < 0.2 * N
+
+
+def _quadratic(rng):
+    g = rng.normal(size=3)
+    Hq = rng.normal(size=(3, 3))
+    Hq = Hq + Hq.T
+    c0 = 1.3
+    f = lambda X: c0 + X @ g + 0.5 * np.einsum("...i,ij,...j->...", X, Hq, X)
+    grad = lambda X: g + X @ Hq
+    return f, grad, Hq
+
+
+def _scaled_coefficients(grad_c, Hq, h):
+    """Coefficients of (x, y, z, x^2, y^2, z^2, xy, xz, yz) in the frame (x - centroid) / h."""
+    a = np.zeros((len(h), 9))
+    a[:, 0:3] = h[:, None] * grad_c
+    for j in range(3):
+        a[:, 3 + j] = 0.5 * h ** 2 * Hq[j, j]
+    a[:, 6], a[:, 7], a[:, 8] = h ** 2 * Hq[0, 1], h ** 2 * Hq[0, 2], h ** 2 * Hq[1, 2]
+    return a
+
+
+def test_non_compact_fits_reproduce_quadratics_and_linear_fields(shim):
+    """Eq. (polys): the big-stencil least squares returns a quadratic's coefficients
+    exactly; every sub-stencil fit in use returns a linear field's gradient."""
+    m = I.cavity_mesh(4)
+    b = Built(shim, m, mask=1)
+    N = b.N
+    perm = b.get("perm", np.int64)
+    _, cen = geometry(m)
+    cen = cen[perm]
+    h = b.get("h", np.float64)
+    sten, X0 = b.get("sten", np.int32, 16), b.get("X0", np.float64, 9 * 16)
+    rng = np.random.default_rng(3)
+    f, grad, Hq = _quadratic(rng)
+    Q = tet_average_quadratic(m.xyz, m.tet4, lambda X: f(X)[..., None])[:, 0][perm]
+    dQ = np.where(sten >= 0, Q[np.maximum(sten, 0)] - Q[None, :], 0.0)        # [16, N]
+    a = np.einsum("dkn,kn->nd", X0.reshape(9, 16, N), dQ)
+    ref = _scaled_coefficients(grad(cen), Hq, h)
+    # rounding, amplified by the conditioning of the wall cells' stencils; a wrong fit is off by O(h^2)
+    np.testing.assert_allclose(a, ref, rtol=1e-8, atol=1e-10 * np.abs(ref).max())
+    # sub-stencils on a linear field
+    gl = rng.normal(size=3)
+    Ql = tet_average_quadratic(m.xyz, m.tet4, lambda X: (0.7 + X @ gl)[..., None])[:, 0][perm]
+    Xs, ssl, valid = b.get("Xs", np.float64, 4 * 3 * 6), b.get("ssl", np.uint32, 4), b.get("subvalid", np.uint8)
+    Xs = Xs.reshape(4, 3, 6, N)
+    used = 0
+    for mm in range(4):
+        slots = np.stack([(ssl[mm] >> (4 * s)) & 15 for s in range(6)]).astype(np.int64)    # [6, N]
+        cells = sten[slots, np.arange(N)[None, :]]
+        d = np.where(cells >= 0, Ql[np.maximum(cells, 0)] - Ql[None, :], 0.0)
+        bm = np.einsum("jsn,sn->nj", Xs[mm], d)
+        ok = (valid >> mm) & 1 == 1
+        used += int(ok.sum())
+        np.testing.assert_allclose(bm[ok], (h[:, None] * gl[None, :])[ok], rtol=1e-10, atol=1e-12)
+    assert used >= 3 * N                     # most sub-stencils are in use
+
+
+def test_compact_fits_reproduce_quadratics_and_linear_fields(shim):
+    """Eq. (compact-big-1): with exact cell averages and exact cell-averaged gradients
+    the constrained least squares returns a quadratic's coefficients (cells with at
+    least three face neighbours); Eq. (compact-big-2): every sub-stencil returns a
+    linear field's gradient."""
+    m = I.cavity_mesh(4)
+    b = Built(shim, m, mask=2)
+    N = b.N
+    perm = b.get("perm", np.int64)
+    _, cen = geometry(m)
+    cen = cen[perm]
+    h = b.get("h", np.float64)
+    cnb = b.get("cnb", np.int32, 4)
+    H0, Hm = b.get("H0", np.float64, 9 * 19).reshape(9, 19, N), b.get("Hm", np.float64, 4 * 3 * 7).reshape(4, 3, 7, N)
+    rng = np.random.default_rng(5)
+    f, grad, Hq = _quadratic(rng)
+    Q = tet_average_quadratic(m.xyz, m.tet4, lambda X: f(X)[..., None])[:, 0][perm]
+    G = grad(cen)                                              # cell-averaged gradient = gradient at the centroid
+    has = cnb >= 0
+    data = np.zeros((19, N))
+    data[0:4] = np.where(has, Q[np.maximum(cnb, 0)] - Q[None, :], 0.0)
+    data[4:7] = G.T
+    for p_ in range(4):
+        data[7 + 3 * p_:10 + 3 * p_] = np.where(has[p_][None, :], G[np.maximum(cnb[p_], 0)].T, 0.0)
+    a = np.einsum("dcn,cn->nd", H0, data)
+    full = has.sum(0) >= 3
+    assert full.mean() > 0.9
+    ref = _scaled_coefficients(grad(cen), Hq, h)[full]
+    np.testing.assert_allclose(a[full], ref, rtol=1e-8, atol=1e-10 * np.abs(ref).max())
+    gl = rng.normal(size=3)
+    Ql = tet_average_quadratic(m.xyz, m.tet4, lambda X: (0.7 + X @ gl)[..., None])[:, 0][perm]
+    for mm in range(4):
+        d = np.zeros((7, N))
+        d[0] = np.where(has[mm], Ql[np.maximum(cnb[mm], 0)] - Ql, 0.0)
+        d[1:4] = gl[:, None]
+        d[4:7] = np.where(has[mm][None, :], gl[:, None], 0.0)
+        bm = np.einsum("jcn,cn->nj", Hm[mm], d)
+        np.testing.assert_allclose(bm, h[:, None] * gl[None, :], rtol=1e-10, atol=1e-12)
