@@ -46,6 +46,7 @@ extern "C" int hs_get(const char *name, void *out, int64_t bytes) {
   if (n == "Hm") return copy_out(g_hm.Hm, out, bytes);
   if (n == "fT") return copy_out(g_hm.fT, out, bytes);
   if (n == "fS") return copy_out(g_hm.fS, out, bytes);
+  if (n == "fdist") return copy_out(g_hm.fdist, out, bytes);
   if (n == "cnb") return copy_out(g_hm.cnb, out, bytes);
   if (n == "cface") return copy_out(g_hm.cface, out, bytes);
   if (n == "sten") return copy_out(g_hm.sten, out, bytes);

@@ -202,3 +202,67 @@ def test_compact_fits_reproduce_quadratics_and_linear_fields(shim):
         d[4:7] = np.where(has[mm][None, :], gl[:, None], 0.0)
         bm = np.einsum("jcn,cn->nj", Hm[mm], d)
         np.testing.assert_allclose(bm, h[:, None] * gl[None, :], rtol=1e-10, atol=1e-12)
+
+
+def test_stencils_gauss_points_and_face_geometry(shim):
+    """Sec. 3.1 stencils as the paper builds them (big stencil: face neighbours and
+    their neighbours; sub-stencil m: the three face neighbours of its triple and the
+    three other neighbours of face neighbour m), the face Gauss points (barycentric
+    2/3, 1/6, 1/6 on the face shared with the slot's neighbour), normals from the
+    left to the right cell, and the distances used by the viscous spectral radius."""
+    m = I.cavity_mesh(4)
+    b = Built(shim, m, mask=1)
+    N, F = b.N, b.F
+    perm = b.get("perm", np.int64)
+    _, cen_c = geometry(m)
+    cen = cen_c[perm]
+    h = b.get("h", np.float64)
+    cnb, cface = b.get("cnb", np.int32, 4), b.get("cface", np.int32, 4)
+    sten, ssl, valid = b.get("sten", np.int32, 16), b.get("ssl", np.uint32, 4), b.get("subvalid", np.uint8)
+    xg = b.get("xg", np.float64, 36).reshape(4, 3, 3, N)
+    fT, fl, fr, fdist = (b.get("fT", np.float64, 9, per="F"), b.get("fl", np.int32, per="F"),
+                         b.get("fr", np.int32, per="F"), b.get("fdist", np.float64, per="F"))
+    TRIPLES = [(0, 1, 2), (0, 1, 3), (1, 2, 3), (2, 0, 3)]
+    tets = m.tet4[perm]
+    checked_big = checked_sub = 0
+    for i in range(N):
+        l1 = [int(j) for j in cnb[:, i] if j >= 0]
+        ring = list(dict.fromkeys(l1 + [int(k) for j in l1 for k in cnb[:, j] if k >= 0 and k != i]))
+        got = [int(k) for k in sten[:, i] if k >= 0]
+        if len(ring) >= 12:
+            assert got == ring, i                          # the same cells, in the same order
+            checked_big += 1
+        for mm in range(4):
+            if not (valid[i] >> mm) & 1:
+                continue
+            want = [int(cnb[t, i]) for t in TRIPLES[mm] if cnb[t, i] >= 0]
+            if cnb[mm, i] >= 0:
+                want += [int(k) for k in cnb[:, cnb[mm, i]] if k >= 0 and k != i]
+            want = set(want)
+            slots = sorted(got.index(c) for c in want)
+            dec = [int((ssl[mm, i] >> (4 * s)) & 15) for s in range(len(slots))]
+            assert dec == slots, (i, mm)
+            checked_sub += 1
+        # Gauss points: on the face shared with the slot's neighbour, barycentric (2/3, 1/6, 1/6)
+        Vt = m.xyz[tets[i]]
+        Bm = np.vstack([Vt.T, np.ones(4)])
+        for p_ in range(4):
+            X = cen[i][None, :] + h[i] * xg[p_, :, :, i]                         # [3 points, 3]
+            lam = np.linalg.solve(Bm, np.vstack([X.T, np.ones(3)]))            # [4 vertices, 3 points]
+            zero = np.abs(lam).max(1) < 1e-12
+            assert zero.sum() == 1
+            np.testing.assert_allclose(np.sort(lam[~zero], axis=0), np.array([[1 / 6] * 3, [1 / 6] * 3, [2 / 3] * 3]),
+                                       atol=1e-12)
+            if cnb[p_, i] >= 0:                           # the vertex off the face is not in the neighbour
+                assert tets[i][np.argmax(zero)] not in tets[cnb[p_, i]]
+    assert checked_big > N // 2 and checked_sub > 2 * N
+    # normals from left to right; distances between centroids (inside) or twice the wall distance
+    inner = fr >= 0
+    d = cen[fr[inner]] - cen[fl[inner]]
+    assert np.all(np.einsum("ij,ji->i", d, fT[0:3, inner]) > 0)
+    np.testing.assert_allclose(fdist[inner], np.linalg.norm(d, axis=1), rtol=1e-13)
+    for f in np.where(~inner)[0][:50]:
+        L = fl[f]
+        p_ = int(np.where(cface[:, L] >> 1 == f)[0][0])
+        fc = cen[L] + h[L] * xg[p_, :, :, L].mean(0)
+        assert fdist[f] == pytest.approx(2 * abs((fc - cen[L]) @ fT[0:3, f]), rel=1e-12)
