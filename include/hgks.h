@@ -188,7 +188,9 @@ hgks_status hgks_precondition(hgks_mesh mesh, int32_t sweeps, const double *b, d
 
 /* One pass of Algorithm 1's outer loop: time step, R(Q) (and G_new), A,
  * `restarts` cycles of left-preconditioned GMRES(krylov_dim) with modified
- * Gram-Schmidt, Q += dQ, and G = G_new for the compact scheme. Q, G are device
+ * Gram-Schmidt (Algorithm 1's coefficients up to rounding: an FP64 basis is
+ * taken two vectors per pass, an FP32 basis from one pass with its Gram
+ * matrix), Q += dQ, and G = G_new for the compact scheme. Q, G are device
  * arrays updated in place; dQ_out (device, may be NULL) receives the update.
  * Synchronises the stream (to return info->res_l1). */
 hgks_status hgks_gmres_step(hgks_mesh mesh, const hgks_params *p, double *Q, double *G,
