@@ -325,6 +325,25 @@ def slope(prim, K, dQ):
     return a
 
 
+def lu_solve(A, b):
+    """x with A x = b by the oracle's elimination (the primitive its steps call)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(len(b))
+    if lib().orc_lu_solve(int(len(b)), _p(A), _p(b), _p(x)):
+        raise RuntimeError("singular matrix")
+    return x
+
+
+def lsq_pinv(A):
+    """X (cols x rows) with X b the least-squares solution of A x = b (Householder QR)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    X = np.zeros((A.shape[1], A.shape[0]))
+    if lib().orc_lsq_pinv(int(A.shape[0]), int(A.shape[1]), _p(A), _p(X)):
+        raise RuntimeError("rank-deficient or short matrix")
+    return X
+
+
 def euler_jacobian(Q, n, gamma=1.4):
     J = np.zeros((5, 5))
     lib().orc_euler_jacobian(_p(np.ascontiguousarray(Q, dtype=np.float64)),

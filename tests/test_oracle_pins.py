@@ -840,3 +840,22 @@ def test_compact_gradient_update_is_exact_for_linear_fields():
     p = O.make_params(scheme=1, weights=0, flux_dt=1e-10)
     _, Gn = om.residual(p, Q, G)
     np.testing.assert_allclose(Gn[inner], G[inner], rtol=1e-7, atol=1e-8)
+
+
+def test_dense_primitives_match_library_routines():
+    """The oracle's dense primitives (Gaussian elimination with partial pivoting,
+    Householder least squares) against numpy on systems that need row exchanges
+    (zero and tiny leading pivots) and on tall least-squares problems."""
+    rng = np.random.default_rng(73)
+    for n in (2, 5, 13):
+        A = rng.normal(size=(n, n))
+        A[0, 0] = 0.0                                    # no solve without a row exchange
+        A[1, 1] = 1e-14 * A[1, 1]
+        b = rng.normal(size=n)
+        np.testing.assert_allclose(O.lu_solve(A, b), np.linalg.solve(A, b), rtol=1e-10, atol=1e-12)
+    P = np.eye(6)[[3, 0, 5, 1, 4, 2]]                    # a permutation: every pivot is a row exchange
+    b = rng.normal(size=6)
+    np.testing.assert_allclose(O.lu_solve(P, b), P.T @ b, rtol=0, atol=1e-15)
+    for rows, cols in ((16, 9), (7, 3), (3, 3)):
+        A = rng.normal(size=(rows, cols))
+        np.testing.assert_allclose(O.lsq_pinv(A), np.linalg.pinv(A), rtol=1e-10, atol=1e-12)

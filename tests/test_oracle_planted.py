@@ -99,6 +99,18 @@ PLANTED = [
      "for (int d = 0; d < 9; d++) A[r * 9 + d] = av[d] - avg_i[d];", "for (int d = 0; d < 9; d++) A[r * 9 + d] = av[d];"),
     ("tetrahedron volume / 3", "orc_mesh.c",
      "e1[2] * c[2]) / 6.0;", "e1[2] * c[2]) / 3.0;"),
+    ("sub-stencil 4 paired with the wrong triple", "orc_mesh.c",
+     "{{0, 1, 2}, {0, 1, 3}, {1, 2, 3}, {2, 0, 3}}", "{{0, 1, 2}, {0, 1, 3}, {1, 2, 3}, {2, 0, 1}}"),
+    ("sub-stencil without the neighbours of neighbour m", "orc_mesh.c",
+     "for (int q = 0; q < 4; q++) { double s[3]; int64_t k = nb_of(m, &rm, q, s); add_ref(F->sub[mm], &F->n_sub[mm], ORC_MAXSUB, i, k, s); }",
+     "for (int q = 0; q < 1; q++) { double s[3]; int64_t k = nb_of(m, &rm, q, s); add_ref(F->sub[mm], &F->n_sub[mm], ORC_MAXSUB, i, k, s); }"),
+    # dense linear algebra (the library primitives the oracle's steps call)
+    ("elimination without pivoting", "orc_linalg.c",
+     "if (fabs(M[r * (n + 1) + c]) > best) { best = fabs(M[r * (n + 1) + c]); piv = r; }",
+     "if (0) { best = fabs(M[r * (n + 1) + c]); piv = r; }"),
+    ("back substitution skips the last column", "orc_linalg.c",
+     "for (int j = i + 1; j < n; j++) s -= M[i * (n + 1) + j] * x[j];",
+     "for (int j = i + 1; j < n - 1; j++) s -= M[i * (n + 1) + j] * x[j];"),
     # residual, implicit system, solver (Eq. (finite), (derivative), (deri-matrix), (precond), Algorithm 1)
     ("local time step without the sound speed", "orc_solver.c",
      "pr[3] * n[2]) + a + nu);", "pr[3] * n[2]) + nu);"),
