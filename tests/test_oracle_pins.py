@@ -859,3 +859,28 @@ def test_dense_primitives_match_library_routines():
     for rows, cols in ((16, 9), (7, 3), (3, 3)):
         A = rng.normal(size=(rows, cols))
         np.testing.assert_allclose(O.lsq_pinv(A), np.linalg.pinv(A), rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_residual_is_invariant_under_cell_renumbering(scheme):
+    """The scheme is defined on the mesh, not on the numbering of its cells: numbering
+    the same tetrahedra in another order (which swaps the left and right cells of many
+    faces) permutes R and G_new the same way, with nonlinear weights in characteristic
+    variables on a non-uniform state (the characteristic frame is taken at a state
+    that must not depend on which side is called left)."""
+    m = I.cavity_mesh(3)
+    rng = np.random.default_rng(79)
+    perm = rng.permutation(m.n_tet)
+    m2 = I.Mesh(m.xyz, m.tet4[perm], m.bface3, m.btag, m.periodic_shift)
+    Q, G = I.smooth_state(m, amp=0.15)
+    p = O.make_params(scheme=scheme, weights=0, characteristic=1, viscous=1, mu=1e-2, Pr=0.72,
+                      **{k: v for k, v in I.cavity_conditions().items() if k not in ("viscous", "mu")})
+    o1, o2 = O.OracleMesh(m), O.OracleMesh(m2)
+    if scheme == 1:
+        R1, G1 = o1.residual(p, Q, G)
+        R2, G2 = o2.residual(p, Q[perm], G[perm])
+        np.testing.assert_allclose(G2, G1[perm], rtol=1e-11, atol=1e-11 * np.abs(G1).max())
+    else:
+        R1 = o1.residual(p, Q)
+        R2 = o2.residual(p, Q[perm])
+    np.testing.assert_allclose(R2, R1[perm], rtol=1e-11, atol=1e-12 * np.abs(R1).max())

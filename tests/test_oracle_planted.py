@@ -59,9 +59,17 @@ PLANTED = [
      "T_odd = (tag == 1 || tag == 2)", "T_odd = (tag == 2)"),
     ("wall image keeps the normal derivatives", "orc_gks.c",
      "double sn = d == 0 ? -1.0 : 1.0;", "double sn = 1.0;"),
+    ("far field from the interior density", "orc_gks.c",
+     "Wr[0] = r; Wr[1] = r * u[0]; Wr[2] = r * u[1]; Wr[3] = r * u[2];",
+     "r = Wl[0]; Wr[0] = r; Wr[1] = r * u[0]; Wr[2] = r * u[1]; Wr[3] = r * u[2];"),
+    ("time slope of g0 from the left state", "orc_gks.c",
+     "time_slope(p0, K, ab, Ab);", "time_slope(pl, K, ab, Ab);"),
     # reconstruction (Sec. 3, Eq. (weno), characteristic variables of Sec. 5)
     ("eigenvector u + a with H - u a", "orc_recon.c",
      "{1, u + a, v, w, H + u * a}", "{1, u + a, v, w, H - u * a}"),
+    ("characteristic projection at the left state, not the face average", "orc_recon.c",
+     "Qs[c] = R_ >= 0 ? 0.5 * (Q[5 * L_ + c] + Q[5 * R_ + c]) : Q[5 * i + c];",
+     "Qs[c] = Q[5 * L_ + c];"),
     ("Gauss-point gradient not rescaled by h", "orc_recon.c",
      "qg[j][c] = grad[j] / m->h[i];", "qg[j][c] = grad[j];"),
     ("Eq. (weno): gamma_m / gamma_0 taken as gamma_m", "orc_recon.c",
