@@ -126,11 +126,15 @@ def test_uniform_flux_is_euler_flux():
         np.testing.assert_allclose(Qp, W, rtol=1e-13, atol=1e-14)
 
 
-def test_two_state_flux_time_integral():
+@pytest.mark.parametrize("viscous", [0, 1])
+def test_two_state_flux_time_integral(viscous):
     """Zero slopes, W_l != W_r: f(t) = (1 - e^{-t/tau}) g0 + e^{-t/tau} (g_l H(u) + g_r (1 - H(u)))
-    (Eq. (flux)); its flux averaged over [0, dt] by numerical integration in u and t."""
+    (Eq. (flux)); its flux averaged over [0, dt] by numerical integration in u and t.
+    tau as in Sec. 5: eps dt + C |p_l - p_r|/(p_l + p_r) dt (inviscid) or mu / p(Q0) +
+    C |p_l - p_r|/(p_l + p_r) dt (viscous, p of the state Q0 at the interface)."""
     rng = np.random.default_rng(7)
-    p = O.make_params(viscous=0, tau_eps=0.1, tau_C=1.0)
+    mu = 3e-3
+    p = O.make_params(viscous=viscous, mu=mu, tau_eps=0.1, tau_C=1.0)
     Wl, Wr = rand_state(rng), rand_state(rng)
     dt = 0.05
     F, _ = O.gks_flux(p, Wl, np.zeros((3, 5)), Wr, np.zeros((3, 5)), dt)
@@ -160,7 +164,8 @@ def test_two_state_flux_time_integral():
     Feq = euler_flux(Q0, np.array([1.0, 0, 0]))
     Fkin = flux_half(Wl, +1) + flux_half(Wr, -1)
     pl, pr = prim_of(Wl)[2], prim_of(Wr)[2]
-    tau = 0.1 * dt + abs((pl - pr) / (pl + pr)) * dt     # Sec. 5, inviscid
+    jump = abs((pl - pr) / (pl + pr)) * dt
+    tau = mu / prim_of(Q0)[2] + jump if viscous else 0.1 * dt + jump     # Sec. 5
     avg = lambda fn: integrate.quad(fn, 0, dt, epsabs=1e-16, epsrel=1e-13)[0] / dt
     expect = avg(lambda t: 1 - math.exp(-t / tau)) * Feq + avg(lambda t: math.exp(-t / tau)) * Fkin
     np.testing.assert_allclose(F, expect, rtol=1e-10, atol=1e-12)
@@ -884,3 +889,71 @@ def test_residual_is_invariant_under_cell_renumbering(scheme):
         R1 = o1.residual(p, Q)
         R2 = o2.residual(p, Q[perm])
     np.testing.assert_allclose(R2, R1[perm], rtol=1e-11, atol=1e-12 * np.abs(R1).max())
+
+
+def _monomials(Xh):
+    x, y, z = Xh[..., 0], Xh[..., 1], Xh[..., 2]
+    return np.stack([x, y, z, x * x, y * y, z * z, x * y, x * z, y * z], -1)
+
+
+def _grad_monomials(xh):
+    """[3, 9]: derivatives of the monomials along x_hat, y_hat, z_hat at one point."""
+    x, y, z = xh
+    D = np.zeros((3, 9))
+    D[0, 0] = D[1, 1] = D[2, 2] = 1.0
+    D[0, 3], D[1, 4], D[2, 5] = 2 * x, 2 * y, 2 * z
+    D[0, 6], D[1, 6] = y, x
+    D[0, 7], D[2, 7] = z, x
+    D[1, 8], D[2, 8] = z, y
+    return D
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_central_polynomial_brute_force(scheme):
+    """P0 of Eq. (polys) recomputed from its definition for single cells on random
+    (non-polynomial) data, where the weighting of the fit matters. WENO: the plain
+    least-squares fit of the big stencil's cell averages (face neighbours and their
+    neighbours, Sec. 3.1/3.2), the target's average kept by the zero-mean basis.
+    HWENO: the constrained least squares of Eq. (compact-big-1): the face
+    neighbours' averages as equalities, the h-scaled cell-averaged gradients of the
+    target and its face neighbours in the least-squares sense (Sec. 3.3). With
+    linear weights and the projection off, Eq. (weno) returns P0 at the Gauss points."""
+    m = I.cavity_mesh(4)
+    om = O.OracleMesh(m)
+    rng = np.random.default_rng(83)
+    n = m.n_tet
+    Q = np.array([1.0, 0.1, -0.05, 0.02, 2.5]) + 0.05 * rng.normal(size=(n, 5))
+    G = 0.3 * rng.normal(size=(n, 15))
+    V = m.xyz[m.tet4]
+    cen = V.mean(1)
+    h = np.cbrt(np.abs(np.einsum("ij,ij->i", V[:, 1] - V[:, 0], np.cross(V[:, 2] - V[:, 0], V[:, 3] - V[:, 0]))) / 6)
+    nb = om.neighbours
+    p = O.make_params(scheme=scheme, weights=1, characteristic=0)
+    done = 0
+    for i in range(n):
+        if np.any(nb[i] < 0):
+            continue
+        l1 = [int(j) for j in nb[i]]
+        ring = list(dict.fromkeys(l1 + [int(k) for j in l1 for k in nb[j] if k >= 0 and k != i]))
+        if len(ring) < 12:
+            continue
+        avg = lambda k: tet_average_quadratic(m.xyz, m.tet4[[k]], lambda X: _monomials((X - cen[i]) / h[i]))[0]
+        own = avg(i)
+        if scheme == 0:
+            A = np.array([avg(k) - own for k in ring])
+            a = np.linalg.lstsq(A, Q[ring] - Q[i], rcond=None)[0]                      # [9, 5]
+        else:
+            Cm = np.array([avg(k) - own for k in l1])                                   # equalities
+            B = np.vstack([(h[k] / h[i]) * _grad_monomials((cen[k] - cen[i]) / h[i]) for k in [i] + l1])
+            r = np.vstack([h[k] * G[k].reshape(5, 3).T for k in [i] + l1])              # [15, 5]
+            K = np.block([[B.T @ B, Cm.T], [Cm, np.zeros((4, 4))]])
+            a = np.linalg.solve(K, np.vstack([B.T @ r, Q[l1] - Q[i]]))[:9]
+        for slot in range(4):
+            gp = om.face_gauss_points(i, slot)
+            P0 = Q[i][None, :] + (_monomials((gp - cen[i]) / h[i]) - own) @ a
+            _, _, Wg, _ = om.recon_side(p, Q, G, i, slot)
+            np.testing.assert_allclose(Wg, P0, rtol=1e-10, atol=1e-11)
+        done += 1
+        if done == 10:
+            break
+    assert done == 10

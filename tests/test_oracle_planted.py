@@ -32,6 +32,8 @@ PLANTED = [
     # time evolution and flux (Eq. (flux), Sec. 4.1, Sec. 5)
     ("collision time without the pressure jump", "orc_gks.c",
      "p->tau_eps * dt + p->tau_C * jump * dt", "p->tau_eps * dt"),
+    ("viscous collision time with the left pressure instead of Q0's", "orc_gks.c",
+     "p->viscous ? p->mu / pp0", "p->viscous ? p->mu / prl"),
     ("time coefficient c2: sign of tau dt (1 + e)", "orc_gks.c",
      "- tau * dt * (1.0 + e);", "+ tau * dt * (1.0 + e);"),
     ("time coefficient c3: sign of tau dt", "orc_gks.c",
@@ -92,6 +94,14 @@ PLANTED = [
      "double dval = m->h[rk->cell];", "double dval = 1.0;"),
     ("HWENO sub-stencil fit: gradient data not scaled by h", "orc_mesh.c",
      "rhs[j] = (hk[k] / m->h[i]) * hk[k];", "rhs[j] = hk[k] / m->h[i];"),
+    ("HWENO fit: gradient rows and data without the h_k weights", "orc_mesh.c",
+     ("B[3 * k + j][d] = (hk / m->h[i]) * av[d];", "double dval = m->h[rk->cell];"),
+     ("B[3 * k + j][d] = av[d];", "double dval = m->h[i];")),
+    ("WENO big-stencil fit weighted (rows and data) instead of plain least squares", "orc_mesh.c",
+     ("for (int d = 0; d < 9; d++) A[r * 9 + d] = av[d] - avg_i[d];",
+      "for (int d = 0; d < 9; d++) for (int r = 0; r < F->n_big; r++) F->X0[d][r] = X[d * F->n_big + r];"),
+     ("for (int d = 0; d < 9; d++) A[r * 9 + d] = (1.0 + 0.5 * r) * (av[d] - avg_i[d]);",
+      "for (int d = 0; d < 9; d++) for (int r = 0; r < F->n_big; r++) F->X0[d][r] = (1.0 + 0.5 * r) * X[d * F->n_big + r];")),
     ("compact gradient not divided by the volume", "orc_solver.c",
      "if (Gnew) for (int64_t i = 0; i < nc; i++) for (int c = 0; c < 15; c++) Gnew[15 * i + c] /= m->vol[i];", ""),
     ("compact gradient from the face flux instead of the point value", "orc_solver.c",
@@ -152,8 +162,10 @@ def _run_case(case, workdir):
         shutil.copy(os.path.join(O.HERE, f), d)
     path = os.path.join(d, fname)
     src = open(path).read()
-    assert src.count(orig) == 1, f"{name}: the text to change occurs {src.count(orig)} times in {fname}"
-    open(path, "w").write(src.replace(orig, planted))
+    for o, pl in zip(*((orig, planted) if isinstance(orig, tuple) else ((orig,), (planted,)))):
+        assert src.count(o) == 1, f"{name}: the text to change occurs {src.count(o)} times in {fname}"
+        src = src.replace(o, pl)
+    open(path, "w").write(src)
     lib = O.compile_library(d, os.path.join(d, "liboracle_planted.so"))
     env = dict(os.environ, HGKS_ORACLE_LIB=lib, OMP_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider", "-m", "not gpu", *PINS],
