@@ -32,16 +32,21 @@ sys.path.insert(0, ROOT)
 
 METRIC = "residual Mcells/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 (non-tensor) arithmetic peak of one GB300: 152 SMs x 2 DFMA per SM and clock
-# (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on peak_sustained = 2/cycle) x 2
-# flops x 2070 MHz = 1259 GFLOP/s, the recipe's nominal 1.25 TFLOP/s.
-FP64_PEAK_GFLOPS = 1258.6
-# FP64 flops per unit of work of each kernel (2 per DFMA, 1 per DADD/DMUL), from the
-# ncu sass counters of the kernels on the 124,416-tet sphere (non-compact scheme,
-# inviscid, Pr = 1), from ncu SASS instruction counters. unit -> (flops per unit, units)
-# DRAM bytes per unit of work from the same ncu captures (dram__bytes_read.sum +
-# dram__bytes_write.sum divided by the units of the 124,416-tet launch); the
-# traffic of a full launch is this times its units (traffic grows with the units).
+# FP64 (non-tensor) arithmetic peak of one GB300 from the unit counts: 152 SMs x 2
+# DFMA per SM and clock (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
+# peak_sustained = 2/cycle) x 2 flops x 2070 MHz = 1259 GFLOP/s. The roofline uses
+# the rate measured in the same run (hgks_fp64_peak: DFMA chains); this nominal
+# figure is reported beside it.
+FP64_NOMINAL_GFLOPS = 1258.6
+# The work per unit of each FP64-bound kernel, held fixed (the roofline
+# numerator): FP64 flops (2 per DFMA, 1 per DADD/DMUL) per unit, counted once by
+# ncu's SASS instruction counters on the 124,416-tet sphere (non-compact scheme,
+# inviscid, Pr = 1) for the kernels of the step at 190.8 ms per 2.36M-tet step,
+# and frozen there as the method's work per unit: a later rewrite that needs
+# fewer operations for the same result shows as a higher fraction, not a lower
+# count. DRAM bytes per unit of work from the same ncu captures
+# (dram__bytes_read.sum + dram__bytes_write.sum divided by the units of the
+# 124,416-tet launch); the traffic of a full launch is this times its units.
 KERNEL_TRAFFIC = {"flux": 467.8, "recon": 4358.7, "jacobi": 858.0, "spmv": 935.0}
 KERNEL_FLOPS = {
     "flux": (2242.5, lambda N, F: 3 * F),        # per face Gauss point
@@ -168,12 +173,6 @@ def cpu_baseline(steps=1, max_seconds=30.0):
             "seconds": dt}
 
 
-# the default workload's size: 6 patches x 32 x 32 x 64 layers, 6 tets per hex;
-# faces (4 N + boundary faces) / 2 with 2 x 6 x 32^2 x 2 boundary triangles
-C2_CELLS = 6 * 32 * 32 * 64 * 6
-C2_FACES = (4 * C2_CELLS + 24 * 32 * 32) // 2
-
-
 def step_config(name, n_cells, n_faces, world):
     """The `config` object of the whole-step line (both arms)."""
     return {"workload": name, "n_cells": int(n_cells), "n_faces": int(n_faces), "parallelism": f"replicas{world}",
@@ -201,7 +200,7 @@ def run_reference(args, rank, world):
         Q, _, _, _ = om.gmres_step(p, Q)
     t_all = time.perf_counter() - t0
     value = m.n_tet * args.steps / t_all / 1e6 if args.steps else 0.0
-    _, _, _, name = workload(small=False)
+    _, _, _, name = workload(small=True)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     cb = {"value": value, "unit": "Mcells/s", "cores": cores, "kind": "oracle",
           "sample": f"{args.steps} implicit step(s) on {m.n_tet} tets (6x12x12x24 sphere, same scheme and "
@@ -209,7 +208,7 @@ def run_reference(args, rank, world):
     res = {"metric": METRIC, "value": value, "unit": "Mcells/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1000.0 * t_all / max(1, args.steps), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": step_config(name, C2_CELLS, C2_FACES, world),
+           "config": step_config(name, m.n_tet, om.nf, world),
            "impl": "reference", "cpu_baseline": cb,
            "e2e": {"value": value, "unit": "Mcells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(res))
@@ -513,7 +512,7 @@ def run_serve(args, rank, world):
         return 0
     conv_a = [s["ttc"] for s in served if s["converged"]]
     conv_b = [s["ttc"] for s in seq if s["converged"]]
-    res = {"metric": "steady solves/hour (served, mixed)", "value": 3600.0 * len(served) / span_a, "unit": "solves/h",
+    res = {"metric": "steady solves/hour (served, mixed)", "value": 3600.0 * len(conv_a) / span_a, "unit": "solves/h",
            "n_gpus": world, "steps": len(reqs), "warmup": 0, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
            "config": {"workload": f"{len(reqs)} steady-solve requests, Poisson arrivals at {args.serve_rate}/s, "
@@ -523,14 +522,16 @@ def run_serve(args, rank, world):
                                   f"WENO, GMRES(10)x3, Jacobi 2, CFL 10, drop {drop:g}, max {max_steps} steps",
                       "hbm_budget_gb": args.serve_budget_gb, "arena_cells": int(info.n_cells),
                       "arena_gb": info.device_bytes / 1e9},
-           "served_mixed": {"solves_per_hour": 3600.0 * len(served) / span_a, "p50_ttc_s": pct([s["ttc"] for s in served], 50),
+           "served_mixed": {"solves_per_hour": 3600.0 * len(conv_a) / span_a,
+                            "finished_per_hour": 3600.0 * len(served) / span_a, "p50_ttc_s": pct([s["ttc"] for s in served], 50),
                             "p99_ttc_s": pct([s["ttc"] for s in served], 99), "converged": len(conv_a),
                             "failed_nonfinite": sum(s["failed"] for s in served),
                             "hit_max_steps": len(served) - len(conv_a) - sum(s["failed"] for s in served),
                             "p50_ttc_converged_s": pct(conv_a, 50),
                             "p99_ttc_converged_s": pct(conv_a, 99), "rounds": rounds, "span_s": span_a,
                             "mean_steps": float(np.mean([s["steps"] for s in served]))},
-           "sequential_fp64": {"solves_per_hour": 3600.0 * len(seq) / span_b, "p50_ttc_s": pct([s["ttc"] for s in seq], 50),
+           "sequential_fp64": {"solves_per_hour": 3600.0 * len(conv_b) / span_b,
+                               "finished_per_hour": 3600.0 * len(seq) / span_b, "p50_ttc_s": pct([s["ttc"] for s in seq], 50),
                                "p99_ttc_s": pct([s["ttc"] for s in seq], 99), "converged": len(conv_b),
                                "failed_nonfinite": sum(s["failed"] for s in seq),
                                "hit_max_steps": len(seq) - len(conv_b) - sum(s["failed"] for s in seq),
@@ -598,6 +599,12 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(steps=1)
         cb.pop("seconds", None)
+
+    # the FP64 roofline of this GPU, measured (DFMA chains, about 2 s)
+    peak_clk = ClockSampler(local)
+    peak_clk.start()
+    fp64_peak = H.hgks_fp64_peak(local, 2.0)
+    peak_clk = peak_clk.stop()
 
     m, cond, kw, name = workload(small=args.small, sphere_n=args.sphere_n)
     hm = H.hgks_mesh_create(m, scheme_mask=1, device=local)
@@ -727,13 +734,15 @@ def main():
     def kroof(name):
         kms, kcnt = prof[name]
         avg_s = kms / kcnt / 1000.0
-        r = {"kernel": name, "bound": "alu", "unit": "GFLOP/s", "peak": FP64_PEAK_GFLOPS,
-             "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (recipe nominal FP64 1.25 TFLOP/s)",
+        r = {"kernel": name, "bound": "alu", "unit": "GFLOP/s", "peak": fp64_peak,
+             "peak_source": "measured: FP64 FMA chains on this GPU in this run (hgks_fp64_peak), "
+                            f"sm clock median {peak_clk.get('sm_mhz')} MHz during the measurement; "
+                            f"nominal {FP64_NOMINAL_GFLOPS} (152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz)",
              "avg_launch_ms": avg_s * 1000.0, "launches": kcnt, "traffic": None}
         if name in KERNEL_FLOPS:
             per, units = KERNEL_FLOPS[name]
             fl = per * units(m.n_tet, F)
-            r.update({"achieved": fl / avg_s / 1e9, "frac": fl / avg_s / 1e9 / FP64_PEAK_GFLOPS, "flops_per_launch": fl})
+            r.update({"achieved": fl / avg_s / 1e9, "frac": fl / avg_s / 1e9 / fp64_peak, "flops_per_launch": fl})
             if name in KERNEL_TRAFFIC:
                 r["traffic"] = KERNEL_TRAFFIC[name] * units(m.n_tet, F)
                 r["traffic_note"] = "bytes per launch: ncu dram bytes per unit on the 124,416-tet sphere x units"
@@ -769,6 +778,7 @@ def main():
         "profiled_ms_per_step": profiled_ms,
         "roofline": roof,
         "roofline_frac_by_kernel": roof_all,
+        "fp64_peak_gflops": {"measured": fp64_peak, "nominal": FP64_NOMINAL_GFLOPS, "clocks": peak_clk},
         "clocks": clk,
         "cpu_baseline": cb,
         "paper_timing_context": ctx,

@@ -30,6 +30,10 @@
  *  - Work is enqueued on the caller's CUDA stream (cudaStream_t passed as
  *    void*; NULL is the legacy default stream). Calls on one mesh handle must
  *    not overlap: the handle's scratch is shared.
+ *  - Devices: a call makes the device of its mesh (batch, server) current
+ *    while it runs and makes the caller's current device current again before
+ *    it returns, so the calling thread's current device is unchanged. The
+ *    stream passed must belong to that device.
  */
 #ifndef HGKS_H
 #define HGKS_H
@@ -71,7 +75,24 @@ typedef struct hgks_mesh_s *hgks_mesh;            /* opaque */
 /* Plain-old-data parameters, copied by every call. Defaults (paper Sec. 3.4,
  * Sec. 4, Sec. 5): scheme WENO, nonlinear weights, characteristic variables,
  * Krylov 10, 3 restarts, 2 Jacobi sweeps, gamma 1.4, Pr 1, CFL 10,
- * tau_eps 0.1, tau_C 1, lin_weight 0.025; see hgks_default_params(). */
+ * tau_eps 0.1, tau_C 1, lin_weight 0.025; see hgks_default_params().
+ *
+ * Flow conditions. The paper states its problems by Mach number, Reynolds
+ * number and angle of attack (Sec. 5.1, 5.2). With Mach > 0 the library derives
+ * the free stream, the wall temperature and the viscosity from Mach, Re and
+ * aoa_deg, and the explicit fields rho_inf, u_inf, p_inf, wall_T, mu and
+ * viscous are ignored (reference length 1: the cavity's side, the sphere's
+ * diameter):
+ *   external flow (lid_speed == 0, Sec. 5.2): (rho, U, V, W, p) =
+ *     (1, Mach cos a, Mach sin a, 0, 1/gamma) with a = aoa_deg in the x-y
+ *     plane; wall_T = 1/gamma; mu = Mach / Re;
+ *   lid-driven cavity (lid_speed > 0, Sec. 5.1): fluid at rest, rho = 1,
+ *     p = lid_speed^2 / (gamma Mach^2) (Mach of the lid), wall_T = p;
+ *     mu = lid_speed / Re;
+ *   Re > 0 makes the flow viscous (tau = mu/p + ...), Re == 0 inviscid.
+ * With Mach == 0 (the default) the explicit fields are used as given, which
+ * serves states that no Mach number describes (tests, far-field states of
+ * other problems). Mach, Re < 0 or a non-finite aoa_deg are HGKS_ERR_ARG. */
 typedef struct {
   int32_t scheme;          /* HGKS_WENO | HGKS_HWENO                                  */
   int32_t weights;         /* HGKS_NONLINEAR | HGKS_LINEAR                            */
@@ -98,6 +119,9 @@ typedef struct {
   double rho_inf, u_inf[3], p_inf;  /* free stream (far field)                        */
   double wall_T;           /* isothermal wall temperature p/rho                       */
   double lid_speed;        /* speed of HGKS_BC_WALL_LID walls along +x                */
+  double Mach;             /* > 0: derive the flow conditions (above); 0: explicit    */
+  double Re;               /* Reynolds number (0: inviscid) when Mach > 0             */
+  double aoa_deg;          /* angle of attack in degrees (x-y plane) when Mach > 0    */
 } hgks_params;
 
 typedef struct {
@@ -227,16 +251,20 @@ hgks_status hgks_gmres_step_host(hgks_mesh mesh, const hgks_params *p, double *Q
  * running (for example a process whose device memory is handed out by another
  * runtime at start-up, or a service that must not enter the CUDA allocator while
  * it answers requests). The mesh is still created up front with
- * hgks_mesh_create; this call then allocates and frees nothing and leaves the
- * handle's own scratch untouched: its scratch is one fixed array of 32 MiB
- * compiled into the library, which every GPU that loads the library holds until
- * the process exits. Meshes larger than that scratch allows (about 10,000
- * tetrahedra: 106 N + 150 F doubles) are rejected with HGKS_ERR_ARG. Arguments,
- * layouts and results are those of hgks_residual. The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture. All calls share the
- * one array and it keeps the previous call's contents: calls that may overlap
- * on the GPU (several streams or host threads) race with each other. */
+ * hgks_mesh_create; this call leaves the handle's own scratch untouched and uses
+ * one fixed array of 32 MiB compiled into the library instead. Meshes larger
+ * than that array allows (about 10,000 tetrahedra: 106 N + 150 F doubles) are
+ * rejected with HGKS_ERR_ARG. Arguments, checks, layouts and results are those of
+ * hgks_residual (the same kernels: the results are identical).
+ * Set-up: under CUDA's lazy module loading (the default) the driver allocates
+ * the array on a device when the first call of this entry point on that device
+ * loads it, and that call also looks up the array's device address
+ * (cudaGetSymbolAddress) with the device current. Make the first call on each
+ * device at start-up, before any stream capture and before device memory is
+ * handed to another runtime; from then on the device holds the array until the
+ * process exits and no call allocates or frees anything. All calls share the one
+ * array and it keeps the previous call's contents: calls that may overlap on the
+ * GPU (several streams or host threads) race with each other. */
 hgks_status hgks_residual_noalloc(hgks_mesh mesh, const hgks_params *p, const double *Q, const double *G,
                                   double *R, double *G_new, void *cuda_stream);
 
@@ -393,6 +421,15 @@ hgks_status hgks_sync(void *cuda_stream);
 hgks_status hgks_profile_begin(void);
 hgks_status hgks_profile_end(int32_t max_kernels, char *names, double *total_ms, int64_t *launches,
                              int32_t *n_out);
+
+/* Measured FP64 arithmetic rate of `device` in GFLOP/s (the roofline the
+ * FP64-bound kernels are held against): independent double-precision FMA
+ * chains (x <- x a + b, 2 flops each) in every thread of one full wave of
+ * resident blocks, no memory traffic, timed with CUDA events on a stream of the
+ * library's own; *gflops_out = the best of 10 launches of about seconds/10
+ * each. Not part of the paper's method. Errors: HGKS_ERR_ARG (NULL, seconds
+ * outside (0, 60], no such device), HGKS_ERR_CUDA/OOM. */
+hgks_status hgks_fp64_peak(int32_t device, double seconds, double *gflops_out);
 
 /* Kernel launches made by this thread since the last reset (profiling aid). */
 int64_t hgks_launch_count(int32_t reset);

@@ -35,7 +35,8 @@ class hgks_params(C.Structure):
                 ("flux_cfl", C.c_double), ("tau_eps", C.c_double), ("tau_C", C.c_double),
                 ("lin_weight", C.c_double), ("weno_eps", C.c_double), ("flux_dt", C.c_double),
                 ("rho_inf", C.c_double), ("u_inf", C.c_double * 3), ("p_inf", C.c_double),
-                ("wall_T", C.c_double), ("lid_speed", C.c_double)]
+                ("wall_T", C.c_double), ("lid_speed", C.c_double),
+                ("Mach", C.c_double), ("Re", C.c_double), ("aoa_deg", C.c_double)]
 
 
 class hgks_mesh_info_t(C.Structure):
@@ -121,6 +122,7 @@ def lib():
             "hgks_batch_solve_steady": [vp, C.c_double, i32, i32, dp, dp, vp],
             "hgks_batch_autotune": [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), vp],
             "hgks_profile_begin": [],
+            "hgks_fp64_peak": [i32, C.c_double, C.POINTER(C.c_double)],
             "hgks_profile_end": [i32, dp, dp, dp, C.POINTER(C.c_int32)],
         }
         for name, args in sig.items():
@@ -476,3 +478,10 @@ def hgks_profile_end(max_kernels=32):
 
 def hgks_launch_count(reset=False) -> int:
     return int(lib().hgks_launch_count(1 if reset else 0))
+
+
+def hgks_fp64_peak(device=0, seconds=2.0) -> float:
+    """Measured FP64 FMA rate of the device in GFLOP/s (the FP64 roofline)."""
+    g = C.c_double(0)
+    _check(lib().hgks_fp64_peak(int(device), float(seconds), C.byref(g)))
+    return g.value

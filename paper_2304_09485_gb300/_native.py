@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhgks.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["residual.cu", "implicit.cu", "batch.cu", "batch_capi.cu", "server.cu", "capi.cu", "noalloc.cu", "mesh_setup.cpp"]
+SOURCES = ["residual.cu", "implicit.cu", "batch.cu", "batch_capi.cu", "server.cu", "capi.cu", "noalloc.cu", "peak.cu", "mesh_setup.cpp"]
 HEADERS = ["hgks_internal.h", "givens.cuh", "offdiag.cuh", "batch_impl.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

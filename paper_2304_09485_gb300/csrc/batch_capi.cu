@@ -161,7 +161,7 @@ int64_t arena_bytes(int64_t cells, int64_t faces, const hgks_params &p, int sche
 
 void batch_delete(Batch *B) {
   if (!B) return;
-  cudaSetDevice(B->m.device);
+  DeviceScope dev_scope(B->m.device);
   if (B->stream) cudaStreamSynchronize(B->stream);
   if (B->graph) cudaGraphExecDestroy(B->graph);
   mesh_free_all(B->m);
@@ -172,8 +172,8 @@ void batch_delete(Batch *B) {
   delete B;
 }
 
+// the caller has made the batch's device current (HGKS_ON_DEVICE)
 hgks_status enter(Batch &B, cudaStream_t user) {
-  BCUDA(cudaSetDevice(B.m.device));
   BCUDA(cudaEventRecord(B.ev_in, user));
   BCUDA(cudaStreamWaitEvent(B.stream, B.ev_in, 0));
   return HGKS_OK;
@@ -210,7 +210,8 @@ hgks_status batch_new(int device, int64_t cell_cap, int64_t face_cap, int nslot,
   M.device = device; M.N = N; M.F = F; M.schemes = schemes;
   DevMesh &d = M.d;
   d.N = (int)N; d.F = (int)F;
-  if (cudaSetDevice(device) != cudaSuccess) return bail(fail_msg(HGKS_ERR_CUDA, "cudaSetDevice"));
+  DeviceScope dev_scope(device);
+  if (dev_scope.error() != cudaSuccess) return bail(fail_msg(HGKS_ERR_CUDA, "cudaSetDevice"));
   if (cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&B->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&B->ev_out, cudaEventDisableTiming) != cudaSuccess)
@@ -494,24 +495,26 @@ hgks_status hgks_batch_create(const hgks_mesh *meshes, const hgks_params *params
   int schemes = 3;
   int64_t N = 0, F = 0;
   hgks_status st;
+  std::vector<hgks_params> P(n_meshes);
   for (int k = 0; k < n_meshes; k++) {
     if (!meshes[k]) return fail_msg(HGKS_ERR_ARG, "a mesh handle is NULL");
     const Mesh &a = *mesh_of(meshes[k]);
     if (a.device != mesh_of(meshes[0])->device) return fail_msg(HGKS_ERR_ARG, "meshes of a batch must be on one device");
-    if ((st = check_params(a, &params[k]))) return st;
-    if (!same_shared(params[0], params[k]))
+    if ((st = take_params(a, &params[k], &P[k]))) return st;
+    if (!same_shared(P[0], P[k]))
       return fail_msg(HGKS_ERR_ARG, "scheme, precision, jv_mode, krylov_dim, restarts, jacobi_sweeps must agree");
     schemes &= a.schemes;
     N += (a.N + kBatchBlock - 1) / kBatchBlock * kBatchBlock;
     F += a.F;
   }
   // the batch carries the data of its scheme only
-  schemes &= params[0].scheme == HGKS_WENO ? 1 : 2;
+  schemes &= P[0].scheme == HGKS_WENO ? 1 : 2;
+  HGKS_ON_DEVICE(mesh_of(meshes[0])->device);
   Batch *B = nullptr;
-  if ((st = batch_new(mesh_of(meshes[0])->device, N, F, n_meshes, params[0], schemes, &B))) return st;
+  if ((st = batch_new(mesh_of(meshes[0])->device, N, F, n_meshes, P[0], schemes, &B))) return st;
   for (int k = 0; k < n_meshes; k++) {
     int slot = -1;
-    if ((st = batch_place(*B, source_of(*mesh_of(meshes[k])), params[k], &slot)) || slot != k) {
+    if ((st = batch_place(*B, source_of(*mesh_of(meshes[k])), P[k], &slot)) || slot != k) {
       batch_delete(B);
       return st ? st : fail_msg(HGKS_ERR_CUDA, "batch placement");
     }
@@ -529,6 +532,7 @@ hgks_status hgks_batch_create_empty(int32_t device, int64_t cell_capacity, int64
   *out = nullptr;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return fail_msg(HGKS_ERR_ARG, "no such device");
+  HGKS_ON_DEVICE(device);
   Batch *B = nullptr;
   hgks_status st = batch_new(device, cell_capacity, face_capacity, max_meshes, *shared,
                              shared->scheme == HGKS_WENO ? 1 : 2, &B);
@@ -546,10 +550,12 @@ hgks_status hgks_batch_add(hgks_batch batch, hgks_mesh mesh, const hgks_params *
   *k_out = -1;
   const Mesh &a = *mesh_of(mesh);
   if (a.device != B.m.device) return fail_msg(HGKS_ERR_ARG, "mesh is on another device");
-  hgks_status st = check_params(a, p);
+  hgks_params P;
+  hgks_status st = take_params(a, p, &P);
   if (st) return st;
+  HGKS_ON_DEVICE(B.m.device);
   int slot = -1;
-  if ((st = batch_place(B, source_of(a), *p, &slot))) return st;
+  if ((st = batch_place(B, source_of(a), P, &slot))) return st;
   if (slot < 0) return fail_msg(HGKS_ERR_OOM, "no free slot, cell range or face range in the batch");
   *k_out = slot;
   return HGKS_OK;
@@ -558,6 +564,7 @@ hgks_status hgks_batch_add(hgks_batch batch, hgks_mesh mesh, const hgks_params *
 hgks_status hgks_batch_remove(hgks_batch batch, int32_t k) {
   hgks_status st = check_slot(batch, k);
   if (st) return st;
+  HGKS_ON_DEVICE(batch->B->m.device);
   batch_release(*batch->B, k);
   return HGKS_OK;
 }
@@ -588,6 +595,7 @@ hgks_status hgks_batch_set_state(hgks_batch batch, int32_t k, const double *Q, c
   Batch &B = *batch->B;
   if (!Q || (compact(B) && !G)) return fail_msg(HGKS_ERR_ARG, "Q (or G) is NULL");
   cudaStream_t user = (cudaStream_t)cuda_stream;
+  HGKS_ON_DEVICE(B.m.device);
   if ((st = enter(B, user)) || (st = batch_set_state(B, k, Q, G))) return st;
   return leave(B, user);
 }
@@ -598,6 +606,7 @@ hgks_status hgks_batch_get_state(hgks_batch batch, int32_t k, double *Q, double 
   if (st) return st;
   Batch &B = *batch->B;
   cudaStream_t user = (cudaStream_t)cuda_stream;
+  HGKS_ON_DEVICE(B.m.device);
   if ((st = enter(B, user)) || (st = batch_get_state(B, k, Q, G, R, G_new))) return st;
   return leave(B, user);
 }
@@ -607,6 +616,7 @@ hgks_status hgks_batch_residual(hgks_batch batch, void *cuda_stream) {
   Batch &B = *batch->B;
   cudaStream_t user = (cudaStream_t)cuda_stream;
   hgks_status st;
+  HGKS_ON_DEVICE(B.m.device);
   if ((st = enter(B, user)) || (st = batch_set_active(B, used_mask(B)))) return st;
   launch_residual(B.m.d, B.m.s, B.p0, B.Q, B.G, B.m.s.R, compact(B) ? B.m.s.Gnew : nullptr, B.stream, true);
   if ((st = launch_status())) return st;
@@ -618,6 +628,7 @@ hgks_status hgks_batch_gmres_step(hgks_batch batch, hgks_step_info *info, void *
   Batch &B = *batch->B;
   cudaStream_t user = (cudaStream_t)cuda_stream;
   hgks_status st;
+  HGKS_ON_DEVICE(B.m.device);
   if ((st = enter(B, user)) || (st = batch_set_active(B, used_mask(B)))) return st;
   if ((st = batch_enqueue_step(B, false, false))) return st;
   const int n = B.nslot, hz = B.bs.hsz;
@@ -656,6 +667,7 @@ hgks_status hgks_batch_solve_steady(hgks_batch batch, double drop_tol, int32_t m
   const int n = B.nslot;
   cudaStream_t user = (cudaStream_t)cuda_stream;
   hgks_status st;
+  HGKS_ON_DEVICE(B.m.device);
   if ((st = enter(B, user))) return st;
   const int64_t hlen = (int64_t)max_steps + 1;
   if (hist_host && B.hist_cap < hlen * n) {
@@ -718,6 +730,7 @@ hgks_status hgks_batch_autotune(hgks_batch batch, int32_t *blk_recon, int32_t *b
   Scratch &s = B.m.s;
   cudaStream_t user = (cudaStream_t)cuda_stream;
   hgks_status st;
+  HGKS_ON_DEVICE(B.m.device);
   if ((st = enter(B, user)) || (st = batch_set_active(B, used_mask(B)))) return st;
   cudaEvent_t a = nullptr, b = nullptr;
   BCUDA(cudaEventCreate(&a));

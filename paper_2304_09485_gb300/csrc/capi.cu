@@ -66,11 +66,6 @@ void free_all(Mesh &m) {
   m.allocs.clear();
 }
 
-hgks_status set_device(const Mesh &m) {
-  HGKS_CUDA(cudaSetDevice(m.device));
-  return HGKS_OK;
-}
-
 hgks_status last_launch() {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
@@ -101,6 +96,41 @@ hgks_status check_params(const Mesh &m, const hgks_params *p) {
   if (!p->viscous && !(p->tau_eps > 0.0)) return fail(HGKS_ERR_ARG, "inviscid flow needs tau_eps > 0");
   if (p->precision != HGKS_FP64 && p->precision != HGKS_MIXED) return fail(HGKS_ERR_ARG, "unknown precision");
   if (p->jv_mode != 0 && p->jv_mode != 1) return fail(HGKS_ERR_ARG, "jv_mode must be 0 (assembled) or 1 (matrix-free)");
+  return HGKS_OK;
+}
+
+// Flow conditions of the paper's problem statements (Sec. 5.1, 5.2) from Mach,
+// Re and the angle of attack; reference length 1 (cavity side, sphere diameter).
+hgks_status take_params(const Mesh &m, const hgks_params *p, hgks_params *out) {
+  if (!p) return fail(HGKS_ERR_ARG, "params is NULL");
+  if (!(p->Mach >= 0.0) || !(p->Re >= 0.0) || !std::isfinite(p->Mach) || !std::isfinite(p->Re) ||
+      !std::isfinite(p->aoa_deg))
+    return fail(HGKS_ERR_ARG, "Mach and Re must be finite and >= 0, aoa_deg finite");
+  hgks_params q = *p;
+  if (p->Mach > 0.0) {
+    const double g = p->gamma;
+    if (!(g > 1.0)) return fail(HGKS_ERR_ARG, "gamma, cfl, flux_cfl, Pr out of range");
+    q.rho_inf = 1.0;
+    if (p->lid_speed > 0.0) {
+      // lid-driven cavity: fluid at rest, the Mach number is the lid's
+      const double U = p->lid_speed;
+      q.u_inf[0] = q.u_inf[1] = q.u_inf[2] = 0.0;
+      q.p_inf = U * U / (g * p->Mach * p->Mach);
+      q.wall_T = q.p_inf / q.rho_inf;
+      q.mu = p->Re > 0.0 ? q.rho_inf * U / p->Re : 0.0;
+    } else {
+      // free stream (1, Ma cos a, Ma sin a, 0, 1/gamma), unit speed of sound
+      const double a = p->aoa_deg * (M_PI / 180.0);
+      q.u_inf[0] = p->Mach * std::cos(a); q.u_inf[1] = p->Mach * std::sin(a); q.u_inf[2] = 0.0;
+      q.p_inf = 1.0 / g;
+      q.wall_T = q.p_inf / q.rho_inf;
+      q.mu = p->Re > 0.0 ? q.rho_inf * p->Mach / p->Re : 0.0;
+    }
+    q.viscous = p->Re > 0.0 ? 1 : 0;
+  }
+  hgks_status st = check_params(m, &q);
+  if (st) return st;
+  *out = q;
   return HGKS_OK;
 }
 
@@ -284,7 +314,8 @@ hgks_status hgks_mesh_create(const double *xyz, int64_t n_vert, const int64_t *t
   m.device = device;
   m.N = hm.N; m.F = hm.F; m.Fb = hm.Fb; m.schemes = scheme_mask & 3;
   auto bail = [&](hgks_status s2) { free_all(m); delete h; return s2; };
-  if ((st = set_device(m))) return bail(st);
+  DeviceScope dev_scope(device);
+  if (dev_scope.error() != cudaSuccess) return bail(cuda_fail(dev_scope.error(), "cudaSetDevice"));
   DevMesh &d = m.d;
   d.N = (int)hm.N; d.F = (int)hm.F;
   std::vector<double> inv_vol(hm.N);
@@ -306,7 +337,7 @@ hgks_status hgks_mesh_create(const double *xyz, int64_t n_vert, const int64_t *t
 
 hgks_status hgks_mesh_destroy(hgks_mesh mesh) {
   if (!mesh) return fail(HGKS_ERR_ARG, "mesh is NULL");
-  cudaSetDevice(mesh->m.device);
+  DeviceScope dev_scope(mesh->m.device);
   free_all(mesh->m);
   delete mesh;
   return HGKS_OK;
@@ -329,11 +360,13 @@ hgks_status hgks_residual(hgks_mesh mesh, const hgks_params *p, const double *Q,
                           double *G_new, void *cuda_stream) {
   if (!mesh) return fail(HGKS_ERR_ARG, "mesh is NULL");
   Mesh &m = mesh->m;
-  hgks_status st = check_params(m, p);
+  hgks_params P;
+  hgks_status st = take_params(m, p, &P);
   if (st) return st;
+  p = &P;
   if (!Q || !R) return fail(HGKS_ERR_ARG, "Q or R is NULL");
   if (p->scheme == HGKS_HWENO && (!G || !G_new)) return fail(HGKS_ERR_ARG, "compact scheme needs G and G_new");
-  if ((st = set_device(m))) return st;
+  HGKS_ON_DEVICE(m.device);
   if ((st = ensure_scratch(m, 0, false))) return st;
   launch_residual(m.d, m.s, *p, Q, G, R, G_new, (cudaStream_t)cuda_stream);
   return last_launch();
@@ -342,10 +375,12 @@ hgks_status hgks_residual(hgks_mesh mesh, const hgks_params *p, const double *Q,
 hgks_status hgks_local_dt(hgks_mesh mesh, const hgks_params *p, const double *Q, double *dt, void *cuda_stream) {
   if (!mesh) return fail(HGKS_ERR_ARG, "mesh is NULL");
   Mesh &m = mesh->m;
-  hgks_status st = check_params(m, p);
+  hgks_params P;
+  hgks_status st = take_params(m, p, &P);
   if (st) return st;
+  p = &P;
   if (!Q || !dt) return fail(HGKS_ERR_ARG, "Q or dt is NULL");
-  if ((st = set_device(m))) return st;
+  HGKS_ON_DEVICE(m.device);
   launch_local_dt(m.d, *p, Q, dt, (cudaStream_t)cuda_stream);
   return last_launch();
 }
@@ -354,10 +389,12 @@ hgks_status hgks_assemble(hgks_mesh mesh, const hgks_params *p, const double *Q,
                           double *off_out, void *cuda_stream) {
   if (!mesh) return fail(HGKS_ERR_ARG, "mesh is NULL");
   Mesh &m = mesh->m;
-  hgks_status st = check_params(m, p);
+  hgks_params P;
+  hgks_status st = take_params(m, p, &P);
   if (st) return st;
+  p = &P;
   if (!Q || !dt) return fail(HGKS_ERR_ARG, "Q or dt is NULL");
-  if ((st = set_device(m))) return st;
+  HGKS_ON_DEVICE(m.device);
   if ((st = ensure_scratch(m, p->krylov_dim, true, p->precision == HGKS_MIXED))) return st;
   if (p->jv_mode == 1 && (st = ensure_fd(m))) return st;
   launch_assemble(m.d, m.s, *p, Q, dt, diag_out, off_out, (cudaStream_t)cuda_stream);
@@ -369,7 +406,7 @@ hgks_status hgks_apply_jacobian(hgks_mesh mesh, const double *x, double *y, void
   Mesh &m = mesh->m;
   if (!m.s.off) return fail(HGKS_ERR_ARG, "hgks_assemble has not been called");
   hgks_status st;
-  if ((st = set_device(m))) return st;
+  HGKS_ON_DEVICE(m.device);
   launch_apply_A(m.d, m.s, x, y, (cudaStream_t)cuda_stream);
   return last_launch();
 }
@@ -378,10 +415,13 @@ hgks_status hgks_apply_jacobian_fd(hgks_mesh mesh, const hgks_params *p, const d
                                    const double *dt, const double *x, double *y, void *cuda_stream) {
   if (!mesh) return fail(HGKS_ERR_ARG, "mesh is NULL");
   Mesh &m = mesh->m;
-  hgks_status st = check_params(m, p);
+  hgks_params P;
+  hgks_status st = take_params(m, p, &P);
   if (st) return st;
+  p = &P;
   if (!Q || !dt || !x || !y || (p->scheme == HGKS_HWENO && !G)) return fail(HGKS_ERR_ARG, "NULL argument");
-  if ((st = set_device(m)) || (st = ensure_scratch(m, p->krylov_dim, true, false)) || (st = ensure_fd(m))) return st;
+  HGKS_ON_DEVICE(m.device);
+  if ((st = ensure_scratch(m, p->krylov_dim, true, false)) || (st = ensure_fd(m))) return st;
   cudaStream_t s_ = (cudaStream_t)cuda_stream;
   HGKS_CUDA(cudaMemcpyAsync(m.s.dt, dt, sizeof(double) * m.N, cudaMemcpyDeviceToDevice, s_));
   launch_residual(m.d, m.s, *p, Q, G, m.s.R, nullptr, s_, false, false);
@@ -394,10 +434,13 @@ hgks_status hgks_wall_force(hgks_mesh mesh, const hgks_params *p, const double *
                             double *force_host, void *cuda_stream) {
   if (!mesh) return fail(HGKS_ERR_ARG, "mesh is NULL");
   Mesh &m = mesh->m;
-  hgks_status st = check_params(m, p);
+  hgks_params P;
+  hgks_status st = take_params(m, p, &P);
   if (st) return st;
+  p = &P;
   if (!Q || !force_host || (p->scheme == HGKS_HWENO && !G)) return fail(HGKS_ERR_ARG, "NULL argument");
-  if ((st = set_device(m)) || (st = ensure_scratch(m, p->krylov_dim, true, p->precision == HGKS_MIXED))) return st;
+  HGKS_ON_DEVICE(m.device);
+  if ((st = ensure_scratch(m, p->krylov_dim, true, p->precision == HGKS_MIXED))) return st;
   cudaStream_t s_ = (cudaStream_t)cuda_stream;
   launch_residual(m.d, m.s, *p, Q, G, m.s.R, nullptr, s_);
   double *fdev = m.s.hs + kHsNormQ + 4;
@@ -414,7 +457,7 @@ hgks_status hgks_precondition(hgks_mesh mesh, int32_t sweeps, const double *b, d
   Mesh &m = mesh->m;
   if (!m.s.off) return fail(HGKS_ERR_ARG, "hgks_assemble has not been called");
   hgks_status st;
-  if ((st = set_device(m))) return st;
+  HGKS_ON_DEVICE(m.device);
   launch_precondition(m.d, m.s, sweeps, b, x, (cudaStream_t)cuda_stream);
   return last_launch();
 }
@@ -509,11 +552,13 @@ hgks_status hgks_gmres_step(hgks_mesh mesh, const hgks_params *p, double *Q, dou
                             hgks_step_info *info, void *cuda_stream) {
   if (!mesh) return fail(HGKS_ERR_ARG, "mesh is NULL");
   Mesh &m = mesh->m;
-  hgks_status st = check_params(m, p);
+  hgks_params P;
+  hgks_status st = take_params(m, p, &P);
   if (st) return st;
+  p = &P;
   if (!Q) return fail(HGKS_ERR_ARG, "Q is NULL");
   if (p->scheme == HGKS_HWENO && !G) return fail(HGKS_ERR_ARG, "compact scheme needs G");
-  if ((st = set_device(m))) return st;
+  HGKS_ON_DEVICE(m.device);
   if ((st = ensure_scratch(m, p->krylov_dim, true, p->precision == HGKS_MIXED))) return st;
   if (p->jv_mode == 1 && (st = ensure_fd(m))) return st;
   if (info) std::memset(info, 0, sizeof(*info));
@@ -526,12 +571,14 @@ static hgks_status solve_impl(hgks_mesh mesh, const hgks_params *p, double *Q, d
                               void *cuda_stream) {
   if (!mesh) return fail(HGKS_ERR_ARG, "mesh is NULL");
   Mesh &m = mesh->m;
-  hgks_status st = check_params(m, p);
+  hgks_params P;
+  hgks_status st = take_params(m, p, &P);
   if (st) return st;
+  p = &P;
   if (!Q || (p->scheme == HGKS_HWENO && !G)) return fail(HGKS_ERR_ARG, "Q (or G) is NULL");
   if (!(drop_tol > 0.0) || max_steps < 0) return fail(HGKS_ERR_ARG, "drop_tol must be > 0 and max_steps >= 0");
   if (k0 < 0 || k0 > max_steps || !(ref0 >= 0.0)) return fail(HGKS_ERR_ARG, "resume point out of range");
-  if ((st = set_device(m))) return st;
+  HGKS_ON_DEVICE(m.device);
   if ((st = ensure_scratch(m, p->krylov_dim, true, p->precision == HGKS_MIXED))) return st;
   if (p->jv_mode == 1 && (st = ensure_fd(m))) return st;
   cudaStream_t s_ = (cudaStream_t)cuda_stream;
@@ -587,11 +634,13 @@ hgks_status hgks_residual_host(hgks_mesh mesh, const hgks_params *p, const doubl
                                double *R_host, double *G_new_host, void *cuda_stream) {
   if (!mesh) return fail(HGKS_ERR_ARG, "mesh is NULL");
   Mesh &m = mesh->m;
-  hgks_status st = check_params(m, p);
+  hgks_params P;
+  hgks_status st = take_params(m, p, &P);
   if (st) return st;
+  p = &P;
   const bool compact = p->scheme == HGKS_HWENO;
   if (!Q_host || !R_host || (compact && (!G_host || !G_new_host))) return fail(HGKS_ERR_ARG, "NULL host array");
-  if ((st = set_device(m))) return st;
+  HGKS_ON_DEVICE(m.device);
   if ((st = ensure_scratch(m, 0, false))) return st;
   double *buf;
   if ((st = host_state_buffer(m, &buf))) return st;
@@ -612,11 +661,13 @@ hgks_status hgks_gmres_step_host(hgks_mesh mesh, const hgks_params *p, double *Q
                                  hgks_step_info *info, void *cuda_stream) {
   if (!mesh) return fail(HGKS_ERR_ARG, "mesh is NULL");
   Mesh &m = mesh->m;
-  hgks_status st = check_params(m, p);
+  hgks_params P;
+  hgks_status st = take_params(m, p, &P);
   if (st) return st;
+  p = &P;
   const bool compact = p->scheme == HGKS_HWENO;
   if (!Q_host || (compact && !G_host)) return fail(HGKS_ERR_ARG, "NULL host array");
-  if ((st = set_device(m))) return st;
+  HGKS_ON_DEVICE(m.device);
   if ((st = ensure_scratch(m, p->krylov_dim, true, p->precision == HGKS_MIXED))) return st;
   if (p->jv_mode == 1 && (st = ensure_fd(m))) return st;
   double *buf;

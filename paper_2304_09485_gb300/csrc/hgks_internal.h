@@ -198,12 +198,37 @@ hgks_status ensure_scratch(Mesh &m, int kdim, bool implicit, bool mixed = false)
 hgks_status mesh_alloc(Mesh &m, void **p, size_t bytes);   // tracked in m.allocs, freed with the mesh
 void mesh_free_all(Mesh &m);
 hgks_status check_params(const Mesh &m, const hgks_params *p);
+// check_params of the parameters in effect: with p->Mach > 0 the flow conditions
+// derived from Mach, Re and aoa_deg (Sec. 5.1, 5.2) replace the explicit ones
+hgks_status take_params(const Mesh &m, const hgks_params *p, hgks_params *out);
 hgks_status fail_msg(hgks_status st, const std::string &msg);
 hgks_status cuda_error(cudaError_t e, const char *where);
 
 // accessors for entry points defined outside capi.cu
 Mesh *mesh_of(hgks_mesh h);
 void set_last_error(const char *msg);
+
+// The device of a mesh (batch, server) made current for the duration of one
+// entry point; the caller's current device is made current again on return.
+class DeviceScope {
+ public:
+  explicit DeviceScope(int dev) {
+    if (cudaGetDevice(&prev_) != cudaSuccess) prev_ = -1;
+    if (prev_ != dev) { err_ = cudaSetDevice(dev); changed_ = err_ == cudaSuccess && prev_ >= 0; }
+  }
+  ~DeviceScope() { if (changed_) cudaSetDevice(prev_); }
+  cudaError_t error() const { return err_; }
+  DeviceScope(const DeviceScope &) = delete;
+  DeviceScope &operator=(const DeviceScope &) = delete;
+
+ private:
+  int prev_ = -1;
+  bool changed_ = false;
+  cudaError_t err_ = cudaSuccess;
+};
+#define HGKS_ON_DEVICE(dev)                                                                  \
+  hgks::DeviceScope hgks_device_scope_(dev);                                                 \
+  if (hgks_device_scope_.error() != cudaSuccess) return hgks::cuda_error(hgks_device_scope_.error(), "cudaSetDevice")
 
 // NVTX range over one phase of Algorithm 1 (inert unless a profiler is attached)
 struct NvtxRange {

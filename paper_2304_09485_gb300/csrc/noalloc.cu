@@ -9,12 +9,17 @@
 // neither allocates nor frees anything, and it does not touch the scratch
 // buffers owned by the mesh handle.
 //
-// The scratch is the file-scope array below. Every GPU that loads the library
-// holds it (32 MiB) until the process exits. Its device address is looked up
-// once per device with cudaGetSymbolAddress: the host-side symbol is only a
-// stand-in and must never be passed to a kernel. Every call shares the array
-// and it keeps the last call's contents, so calls that may overlap on the GPU
-// (other streams, other host threads) race with each other.
+// The scratch is the file-scope array below (32 MiB). Under CUDA's lazy module
+// loading (the default) the driver allocates it on a device when this file's
+// module is first used there, which is the first call of this entry point on
+// that device: that call also looks up the array's device address with
+// cudaGetSymbolAddress (the host-side symbol is only a stand-in and must never
+// be passed to a kernel). So the first call on each device belongs to the
+// caller's start-up, before any stream capture and before its device memory is
+// handed to another runtime; from then on the device holds the array until the
+// process exits and no call allocates. Every call shares the array and it keeps
+// the last call's contents, so calls that may overlap on the GPU (other
+// streams, other host threads) race with each other.
 #include <mutex>
 #include "hgks_internal.h"
 
@@ -38,30 +43,22 @@ size_t noalloc_need(size_t N, size_t F) {
 
 using namespace hgks;
 
-namespace {
-hgks_status report(hgks_status st, const char *msg) {
-  set_last_error(msg);
-  return st;
-}
-}  // namespace
-
 extern "C" hgks_status hgks_residual_noalloc(hgks_mesh mesh, const hgks_params *p, const double *Q, const double *G,
                                              double *R, double *G_new, void *cuda_stream) {
-  if (!mesh || !p || !Q || !R) return report(HGKS_ERR_ARG, "NULL mesh, params, Q or R");
+  if (!mesh) return fail_msg(HGKS_ERR_ARG, "mesh is NULL");
   Mesh &m = *mesh_of(mesh);
-  if (p->scheme != HGKS_WENO && p->scheme != HGKS_HWENO) return report(HGKS_ERR_ARG, "unknown scheme");
-  if (!(m.schemes & (p->scheme == HGKS_WENO ? 1 : 2)))
-    return report(HGKS_ERR_ARG, "mesh was built without data for this scheme");
-  if (p->scheme == HGKS_HWENO && (!G || !G_new)) return report(HGKS_ERR_ARG, "compact scheme needs G and G_new");
-  if (!(p->gamma > 1.0) || !(p->cfl > 0.0) || !(p->flux_cfl > 0.0) || !(p->Pr > 0.0) ||
-      (p->viscous && !(p->mu > 0.0)) || (!p->viscous && !(p->tau_eps > 0.0)))
-    return report(HGKS_ERR_ARG, "parameter out of range");
+  hgks_params P;   // the same argument checks (and flow conditions) as hgks_residual
+  hgks_status st0 = take_params(m, p, &P);
+  if (st0) return st0;
+  p = &P;
+  if (!Q || !R) return fail_msg(HGKS_ERR_ARG, "Q or R is NULL");
+  if (p->scheme == HGKS_HWENO && (!G || !G_new)) return fail_msg(HGKS_ERR_ARG, "compact scheme needs G and G_new");
   const size_t need = noalloc_need((size_t)m.N, (size_t)m.F);
   if (need > kNoallocDoubles)
-    return report(HGKS_ERR_ARG,
-                  "mesh too large for the static scratch of hgks_residual_noalloc (32 MiB: about 10,000 tetrahedra)");
-  if (m.device < 0 || m.device >= 64) return report(HGKS_ERR_ARG, "device index out of range");
-  if (cudaSetDevice(m.device) != cudaSuccess) return report(HGKS_ERR_CUDA, "cudaSetDevice failed");
+    return fail_msg(HGKS_ERR_ARG,
+                    "mesh too large for the static scratch of hgks_residual_noalloc (32 MiB: about 10,000 tetrahedra)");
+  if (m.device < 0 || m.device >= 64) return fail_msg(HGKS_ERR_ARG, "device index out of range");
+  HGKS_ON_DEVICE(m.device);
   double *base;
   {
     // set-up, once per device, with that device current
@@ -69,7 +66,7 @@ extern "C" hgks_status hgks_residual_noalloc(hgks_mesh mesh, const hgks_params *
     if (!g_noalloc_ptr[m.device]) {
       void *ptr = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-      if (e != cudaSuccess || !ptr) return report(HGKS_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed");
+      if (e != cudaSuccess || !ptr) return fail_msg(HGKS_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed");
       g_noalloc_ptr[m.device] = (double *)ptr;
     }
     base = g_noalloc_ptr[m.device];
@@ -87,9 +84,9 @@ extern "C" hgks_status hgks_residual_noalloc(hgks_mesh mesh, const hgks_params *
   // the positivity counter must start at zero; every other region is fully
   // written before it is read
   if (cudaMemsetAsync(s.flags, 0, 8 * sizeof(int), st) != cudaSuccess)
-    return report(HGKS_ERR_CUDA, "cudaMemsetAsync failed");
+    return fail_msg(HGKS_ERR_CUDA, "cudaMemsetAsync failed");
   launch_residual(m.d, s, *p, Q, G, R, G_new, st);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return report(HGKS_ERR_CUDA, cudaGetErrorString(e));
+  if (e != cudaSuccess) return cuda_error(e, "kernel launch");
   return HGKS_OK;
 }

@@ -286,6 +286,7 @@ hgks_status hgks_server_create(int32_t device, int64_t hbm_budget_bytes, int32_t
   }
   const int64_t ncap = lo / kBatchBlock * kBatchBlock;
   if (ncap < kBatchBlock) return fail_msg(HGKS_ERR_ARG, "HBM budget too small for any mesh");
+  HGKS_ON_DEVICE(device);
   hgks_server_s *S = new (std::nothrow) hgks_server_s;
   if (!S) return fail_msg(HGKS_ERR_OOM, "host allocation");
   hgks_status st = batch_new(device, ncap, faces_for(ncap), max_inflight, *shared, schemes, &S->B);
@@ -321,8 +322,10 @@ hgks_status hgks_server_submit(hgks_server S, const double *xyz, int64_t n_vert,
   Batch &B = *S->B;
   Mesh probe;
   probe.schemes = B.m.schemes;
-  hgks_status st = check_params(probe, p);
+  hgks_params P;
+  hgks_status st = take_params(probe, p, &P);
   if (st) return st;
+  p = &P;
   if (!same_shared(B.p0, *p))
     return fail_msg(HGKS_ERR_ARG, "scheme, precision, jv_mode, krylov_dim, restarts, jacobi_sweeps must match the server's");
   if ((n_tet + kBatchBlock - 1) / kBatchBlock * kBatchBlock > B.m.N)
@@ -362,7 +365,7 @@ hgks_status hgks_server_step(hgks_server S, int32_t *n_finished, int32_t *n_runn
   int fin = 0;
   bool changed = false;
   hgks_status st;
-  if (cudaSetDevice(B.m.device) != cudaSuccess) return fail_msg(HGKS_ERR_CUDA, "cudaSetDevice");
+  HGKS_ON_DEVICE(B.m.device);
   {
     bool any_cancel = false;
     {
