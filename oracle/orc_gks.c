@@ -208,8 +208,10 @@ void orc_gks_flux(const orc_params *p, const double *Wl, const double *dWl, cons
  * (x along the outward normal). Walls mirror the interior state through the
  * wall in primitive variables (p, U, V, W, T = p/rho): quantities even under
  * the reflection keep their value and flip their normal derivative; odd ones
- * (about the wall value) are reflected and keep their normal derivative. The
- * far field is the free stream with zero slopes. */
+ * (about the wall value) are reflected and keep their normal derivative. At an
+ * isothermal wall the image's density is the one that sends back as much mass
+ * as reaches the wall (its pressure follows from it); walls carry no mass
+ * (orc_solver.c). The far field is the free stream with zero slopes. */
 void orc_boundary_state(const orc_params *p, int tag, const double *T3, const double *Wl,
                         const double *dWl, double *Wr, double *dWr) {
   const double g = p->gamma;
@@ -253,6 +255,20 @@ void orc_boundary_state(const orc_params *p, int tag, const double *T3, const do
     dTg[d] = T_held ? 0.0 : (T_odd ? -sn * dT[d] : sn * dT[d]);
   }
   double rg = pg / Tg, qg2 = ug[0] * ug[0] + ug[1] * ug[1] + ug[2] * ug[2];
+  if (T_odd) {
+    /* an isothermal wall lets no mass through: the image emits toward the fluid as
+       many particles as the cell sends into the wall (half-range Maxwellians, no
+       slopes): rho_g <u>_{u>0}(U_n, T_g) = rho <u>_{u>0}(U_n, T) with the image's
+       normal velocity -U_n; its pressure follows, p_g = rho_g T_g */
+    double Un = u[0], Ml, Mg;
+    double lam_l = 1.0 / (2.0 * T), lam_g = 1.0 / (2.0 * Tg);
+    Ml = 0.5 * Un * erfc(-sqrt(lam_l) * Un) + 0.5 * exp(-lam_l * Un * Un) / sqrt(M_PI * lam_l);
+    Mg = 0.5 * Un * erfc(-sqrt(lam_g) * Un) + 0.5 * exp(-lam_g * Un * Un) / sqrt(M_PI * lam_g);
+    rg = rho * Ml / Mg;
+    double ratio = rg * Tg / pr;   /* the image keeps the cell's relative pressure gradient */
+    pg = rg * Tg;
+    for (int d = 0; d < 3; d++) dpg[d] *= ratio;
+  }
   Wr[0] = rg; Wr[1] = rg * ug[0]; Wr[2] = rg * ug[1]; Wr[3] = rg * ug[2];
   Wr[4] = pg / (g - 1.0) + 0.5 * rg * qg2;
   for (int d = 0; d < 3; d++) {

@@ -103,6 +103,8 @@ static int residual_core(orc_mesh *m, const orc_params *p, const double *Q, cons
       double F[5], Qp[5], Fg[5], Qg[5];
       orc_gks_flux(p, WL + 5 * g, dWL + 15 * g, WR + 5 * g, dWR + 15 * g, dtf, F, Qp);
       rot5t3(T3, F, Fg); rot5t3(T3, Qp, Qg);
+      /* walls (tags 1-4) are impermeable: their faces carry momentum and energy, no mass */
+      if (Rr < 0 && m->ftag[f] >= 1 && m->ftag[f] <= 4) Fg[0] = 0.0;
       for (int c = 0; c < 5; c++) { Ff[5 * f + c] += m->farea[f] * Fg[c] / 3.0; Pf[5 * f + c] += m->farea[f] * Qg[c] / 3.0; }
     }
   }

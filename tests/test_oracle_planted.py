@@ -64,6 +64,12 @@ PLANTED = [
     ("far field from the interior density", "orc_gks.c",
      "Wr[0] = r; Wr[1] = r * u[0]; Wr[2] = r * u[1]; Wr[3] = r * u[2];",
      "r = Wl[0]; Wr[0] = r; Wr[1] = r * u[0]; Wr[2] = r * u[1]; Wr[3] = r * u[2];"),
+    ("isothermal image keeps the cell's density ratio p/T_g (mass leaks through the wall)", "orc_gks.c",
+     "rg = rho * Ml / Mg;", "rg = pr / Tg;"),
+    ("isothermal image density from the wall temperature's mean speed only", "orc_gks.c",
+     "Mg = 0.5 * Un * erfc(-sqrt(lam_g) * Un)", "Mg = 0.5 * Un * erfc(-sqrt(lam_l) * Un)"),
+    ("wall faces carry mass", "orc_solver.c",
+     "if (Rr < 0 && m->ftag[f] >= 1 && m->ftag[f] <= 4) Fg[0] = 0.0;", "if (Rr < 0 && m->ftag[f] >= 1 && m->ftag[f] <= 3) Fg[0] = 0.0;"),
     ("time slope of g0 from the left state", "orc_gks.c",
      "time_slope(p0, K, ab, Ab);", "time_slope(pl, K, ab, Ab);"),
     # reconstruction (Sec. 3, Eq. (weno), characteristic variables of Sec. 5)
