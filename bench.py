@@ -47,7 +47,7 @@ FP64_NOMINAL_GFLOPS = 1258.6
 # count. DRAM bytes per unit of work from the same ncu captures
 # (dram__bytes_read.sum + dram__bytes_write.sum divided by the units of the
 # 124,416-tet launch); the traffic of a full launch is this times its units.
-KERNEL_TRAFFIC = {"flux": 467.8, "recon": 4358.7, "jacobi": 858.0, "spmv": 935.0}
+KERNEL_TRAFFIC = {"flux": 395.6, "recon": 957.6, "jacobi": 858.0, "spmv": 935.0}
 KERNEL_FLOPS = {
     "flux": (2242.5, lambda N, F: 3 * F),        # per face Gauss point
     "recon": (3000.9, lambda N, F: 4 * N),       # per (cell, face)
@@ -286,28 +286,36 @@ def run_batch(args, rank, world):
         return 0
     clocks = ClockSampler(local)
     clocks.start()
-    # (a) batched steps replayed from the captured graph (tiny drop: every mesh keeps
-    # stepping; the solve takes `steps` steps and then one last residual and test)
+    # (a) batched steps replayed from the captured graph of the step
+    H.hgks_batch_gmres_step(b, use_graph=True)          # capture (not timed)
+    torch.cuda.synchronize()
     H.hgks_launch_count(reset=True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    infos, _, _ = H.hgks_batch_solve_steady(b, 1e-300, args.steps, use_graph=True)
+    for _ in range(args.steps):
+        H.hgks_batch_gmres_step(b, use_graph=True)
     e1.record(stream)
     torch.cuda.synchronize()
     graph_ms = e0.elapsed_time(e1)
     launches = H.hgks_launch_count()
-    steps_done = sum(i.steps for i in infos)
     # (a') per-kernel times of one eager batched step
     H.hgks_profile_begin()
-    H.hgks_batch_gmres_step(b)
+    H.hgks_batch_gmres_step(b, use_graph=False)
     prof = H.hgks_profile_end()
     # (b) batched steps, eager launches
     e0.record(stream)
     for _ in range(args.steps):
-        H.hgks_batch_gmres_step(b)
+        H.hgks_batch_gmres_step(b, use_graph=False)
     e1.record(stream)
     torch.cuda.synchronize()
     eager_ms = e0.elapsed_time(e1)
+    # (b') the device-side convergence loop (hgks_batch_solve_steady, graph replay):
+    # steps steps, then one last residual and test per mesh
+    e0.record(stream)
+    infos, _, _ = H.hgks_batch_solve_steady(b, 1e-300, args.steps, use_graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    solve_ms = e0.elapsed_time(e1)
     # (c) the same meshes one after another through the single-mesh path
     for hm, p, (Q, G) in zip(meshes, params, states):
         H.hgks_gmres_step(hm, p, Q, G)
@@ -323,9 +331,9 @@ def run_batch(args, rank, world):
     if rank != 0:
         return 0
     rate = lambda ms, steps: n_cells * steps / (ms / 1000.0) / 1e6
-    res = {"metric": "batched implicit steps Mcells/s", "value": rate(eager_ms, args.steps),
+    res = {"metric": "batched implicit steps Mcells/s", "value": rate(graph_ms, args.steps),
            "unit": "Mcells/s", "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
-           "ms_per_step": eager_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "ms_per_step": graph_ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64+f32" if prec else "f64", "data": "synthetic",
            "config": {"workload": f"{len(probs)} independent steady problems, cavity/sphere, "
                                   f"{min(p['n_cells'] for p in probs)}-{max(p['n_cells'] for p in probs)} tets "
@@ -333,11 +341,13 @@ def run_batch(args, rank, world):
                                   f"{args.batch_scheme}, {args.batch_precision}, GMRES(10)x3, Jacobi 2, CFL 10",
                       "n_cells": n_cells, "padded_cells": int(H.hgks_batch_info(b).n_cells),
                       "l2": "inputs larger than L2", "blk_recon_flux": list(blk)},
-           "graph": {"value": rate(graph_ms, steps_done / len(probs)), "ms": graph_ms},
+           "graph": {"value": rate(graph_ms, args.steps), "ms": graph_ms},
            "eager": {"value": rate(eager_ms, args.steps), "ms": eager_ms},
+           "solve_loop": {"value": rate(solve_ms, args.steps), "ms": solve_ms,
+                          "note": "hgks_batch_solve_steady (graph replay, device-side convergence test): "
+                                  "steps full steps plus the final residual and test, counted as steps steps"},
            "sequential_single_mesh": {"value": rate(seq_ms, args.steps), "ms": seq_ms},
-           "speedup_vs_sequential": seq_ms / eager_ms,
-           "graph_note": "the graph-replayed solve: steps full steps plus the final residual and test",
+           "speedup_vs_sequential": seq_ms / graph_ms,
            "kernels_ms_one_step": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
            "gpu_launches": int(launches), "setup_s": setup_s, "clocks": clk,
            "sizes": sorted(p["n_cells"] for p in probs)}
@@ -349,10 +359,13 @@ def run_precision(args, rank, world):
     """The precision workload: viscous flow past a sphere (Re 118, Ma 0.2535,
     6 x 24 x 24 patches, 48 layers stretched so that the first is 3e-2 thick,
     ~995k tets, adiabatic no-slip wall), compact HWENO, CFL 20. The same steps
-    in FP64 and with the FP32 Krylov part, from the free stream: drag
-    coefficient and state difference after every few steps, time per step.
-    On a scaled-down sphere of the same construction (6 x 8 x 8, 16 layers)
-    the oracle gives the reference for both."""
+    in FP64 and with the FP32 Krylov part, from the free stream: density
+    residual history, drag coefficient every few steps, state difference, time
+    per step. The compact scheme does not reach a steady state on these
+    tetrahedral sphere grids (its gradient update settles into a two-step cycle
+    in the wall layer), so C_D is reported over the last steps as the mean and
+    the spread of that cycle. On a scaled-down sphere of the same construction
+    (6 x 8 x 8, 8 layers) the oracle gives the reference for both."""
     import torch
     import oracle as O
     import paper_2304_09485_gb300 as H
@@ -371,30 +384,38 @@ def run_precision(args, rank, world):
     m = I.sphere_mesh(24, 48, stretch=I.sphere_stretch(48, dr1=3e-2), wall_tag=I.BC_NOSLIP_ADIA)
     hm = H.hgks_mesh_create(m, scheme_mask=2, device=local)
     traj = {}
+    every = max(1, args.steps // 20)
     for prec in (0, 1):
         p = H.hgks_default_params(precision=prec, **cond, **kw)
         Q = hm.to_internal(I.state_from_conditions(m.n_tet, cond), device=f"cuda:{local}")
         G = torch.zeros((15, m.n_tet), dtype=torch.float64, device=f"cuda:{local}")
-        cds, ms = [], 0.0
+        cds, hist, ms = [], [], 0.0
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         for k in range(args.steps):
             e0.record()
-            H.hgks_gmres_step(hm, p, Q, G)
+            info = H.hgks_gmres_step(hm, p, Q, G)
             e1.record()
             torch.cuda.synchronize()
             ms += e0.elapsed_time(e1)
-            if (k + 1) % max(1, args.steps // 5) == 0:
-                cds.append(cd(hm, p, Q, G))
-        traj[prec] = (Q, G, cds, ms / args.steps)
-    (Q64, G64, cd64, ms64), (Q32, G32, cd32, ms32) = traj[0], traj[1]
-    out["full"] = {"n_cells": m.n_tet, "steps": args.steps, "cd_fp64": cd64, "cd_mixed": cd32,
-                   "cd_rel_diff": abs(cd32[-1] - cd64[-1]) / abs(cd64[-1]),
+            hist.append(info.res_l1)
+            if (k + 1) % every == 0 or k >= args.steps - 10:
+                cds.append((k + 1, cd(hm, p, Q, G)))
+        traj[prec] = (Q, G, cds, np.array(hist), ms / args.steps)
+    (Q64, G64, cd64, h64, ms64), (Q32, G32, cd32, h32, ms32) = traj[0], traj[1]
+    last = lambda c: [v for k, v in c if k > args.steps - 10]
+    out["full"] = {"n_cells": m.n_tet, "steps": args.steps,
+                   "cd_fp64": cd64, "cd_mixed": cd32,
+                   "cd_last10_fp64": {"mean": float(np.mean(last(cd64))), "min": min(last(cd64)), "max": max(last(cd64))},
+                   "cd_last10_mixed": {"mean": float(np.mean(last(cd32))), "min": min(last(cd32)), "max": max(last(cd32))},
+                   "cd_rel_diff": abs(np.mean(last(cd32)) - np.mean(last(cd64))) / abs(np.mean(last(cd64))),
+                   "drop_fp64": (h64 / h64.max())[::every].tolist(), "drop_mixed": (h32 / h32.max())[::every].tolist(),
+                   "final_drop_fp64": float(h64[-1] / h64.max()), "final_drop_mixed": float(h32[-1] / h32.max()),
                    "state_rel_l2": float(torch.linalg.norm(Q32 - Q64) / torch.linalg.norm(Q64)),
                    "ms_per_step_fp64": ms64, "ms_per_step_mixed": ms32,
                    "mcells_per_s_fp64": m.n_tet / ms64 / 1e3, "mcells_per_s_mixed": m.n_tet / ms32 / 1e3}
     del traj, Q64, G64, Q32, G32, hm
     # the scaled-down case against the oracle
-    ms_ = I.sphere_mesh(8, 16, stretch=I.sphere_stretch(16, dr1=3e-2 * 3), wall_tag=I.BC_NOSLIP_ADIA)
+    ms_ = I.sphere_mesh(8, 8, stretch=I.sphere_stretch(8, dr1=3e-2 * 3), wall_tag=I.BC_NOSLIP_ADIA)
     om = O.OracleMesh(ms_)
     hs = H.hgks_mesh_create(ms_, scheme_mask=2, device=local)
     po = O.make_params(**cond, **{k: v for k, v in kw.items()})
@@ -422,8 +443,9 @@ def run_precision(args, rank, world):
     if rank != 0:
         return 0
     res_line = {"metric": "precision: drag coefficient and state error, FP32 Krylov vs FP64", "value": out["full"]["cd_rel_diff"],
-                "unit": "relative C_D difference", "n_gpus": world, "steps": args.steps, "warmup": 0,
-                "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+                "unit": "relative C_D difference (mean of the last 10 steps)", "n_gpus": world, "steps": args.steps,
+                "warmup": 0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+                "data": "synthetic",
                 "config": {"workload": "viscous sphere Re 118, Ma 0.2535, 6x24x24x48 (first layer 3e-2), HWENO, CFL 20, "
                                        "GMRES(10)x3, Jacobi 2, from the free stream"}, **out}
     print(json.dumps(res_line))

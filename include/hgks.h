@@ -75,7 +75,8 @@ typedef struct hgks_mesh_s *hgks_mesh;            /* opaque */
 /* Plain-old-data parameters, copied by every call. Defaults (paper Sec. 3.4,
  * Sec. 4, Sec. 5): scheme WENO, nonlinear weights, characteristic variables,
  * Krylov 10, 3 restarts, 2 Jacobi sweeps, gamma 1.4, Pr 1, CFL 10,
- * tau_eps 0.1, tau_C 1, lin_weight 0.025; see hgks_default_params().
+ * tau_eps 0.1, tau_C 1, lin_weight 0.025, weno_eps 1e-6 (the paper leaves the
+ * epsilon of Eq. (weno) open: Jiang and Shu's value); see hgks_default_params().
  *
  * Flow conditions. The paper states its problems by Mach number, Reynolds
  * number and angle of attack (Sec. 5.1, 5.2). With Mach > 0 the library derives
@@ -114,7 +115,7 @@ typedef struct {
   double flux_cfl;         /* CFL of the time step used inside the gas-kinetic flux   */
   double tau_eps, tau_C;   /* collision time constants of Sec. 5                      */
   double lin_weight;       /* linear weight gamma_m of every sub-stencil              */
-  double weno_eps;         /* epsilon of the nonlinear weights                        */
+  double weno_eps;         /* epsilon of the nonlinear weights (default 1e-6)         */
   double flux_dt;          /* > 0: fixed time step inside the flux (overrides flux_cfl) */
   double rho_inf, u_inf[3], p_inf;  /* free stream (far field)                        */
   double wall_T;           /* isothermal wall temperature p/rho                       */
@@ -330,8 +331,11 @@ hgks_status hgks_batch_get_state(hgks_batch batch, int32_t k, double *Q, double 
 hgks_status hgks_batch_residual(hgks_batch batch, void *cuda_stream);
 
 /* One outer step of Algorithm 1 for every mesh (as hgks_gmres_step).
- * info (host, may be NULL) receives n_meshes records. Synchronises the stream. */
-hgks_status hgks_batch_gmres_step(hgks_batch batch, hgks_step_info *info, void *cuda_stream);
+ * info (host, may be NULL) receives n_meshes records. With use_graph != 0 the
+ * step's launches are replayed from a CUDA graph captured at the first such
+ * call (and again when the arena's shapes change); the results are the same
+ * bit for bit. Synchronises the stream. */
+hgks_status hgks_batch_gmres_step(hgks_batch batch, hgks_step_info *info, int32_t use_graph, void *cuda_stream);
 
 /* Algorithm 1 for every mesh until each has converged (res/res_ref <= drop_tol,
  * as hgks_solve_steady) or taken max_steps steps; a finished mesh is skipped

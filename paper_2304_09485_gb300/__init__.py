@@ -118,7 +118,7 @@ def lib():
             "hgks_batch_set_state": [vp, i32, dp, dp, vp],
             "hgks_batch_get_state": [vp, i32, dp, dp, dp, dp, vp],
             "hgks_batch_residual": [vp, vp],
-            "hgks_batch_gmres_step": [vp, dp, vp],
+            "hgks_batch_gmres_step": [vp, dp, i32, vp],
             "hgks_batch_solve_steady": [vp, C.c_double, i32, i32, dp, dp, vp],
             "hgks_batch_autotune": [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), vp],
             "hgks_profile_begin": [],
@@ -369,9 +369,9 @@ def hgks_batch_residual(batch, stream=None):
     _check(lib().hgks_batch_residual(batch.handle, _stream(stream)))
 
 
-def hgks_batch_gmres_step(batch, stream=None):
+def hgks_batch_gmres_step(batch, use_graph=True, stream=None):
     info = (hgks_step_info * len(batch))()
-    _check(lib().hgks_batch_gmres_step(batch.handle, info, _stream(stream)))
+    _check(lib().hgks_batch_gmres_step(batch.handle, info, 1 if use_graph else 0, _stream(stream)))
     return list(info)
 
 

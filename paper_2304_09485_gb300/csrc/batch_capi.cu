@@ -623,14 +623,14 @@ hgks_status hgks_batch_residual(hgks_batch batch, void *cuda_stream) {
   return leave(B, user);
 }
 
-hgks_status hgks_batch_gmres_step(hgks_batch batch, hgks_step_info *info, void *cuda_stream) {
+hgks_status hgks_batch_gmres_step(hgks_batch batch, hgks_step_info *info, int32_t use_graph, void *cuda_stream) {
   if (!batch || !batch->B) return fail_msg(HGKS_ERR_ARG, "batch is NULL");
   Batch &B = *batch->B;
   cudaStream_t user = (cudaStream_t)cuda_stream;
   hgks_status st;
   HGKS_ON_DEVICE(B.m.device);
   if ((st = enter(B, user)) || (st = batch_set_active(B, used_mask(B)))) return st;
-  if ((st = batch_enqueue_step(B, false, false))) return st;
+  if ((st = batch_enqueue_step(B, false, use_graph != 0))) return st;
   const int n = B.nslot, hz = B.bs.hsz;
   std::vector<double> hs((size_t)n * hz);
   int nonphys = 0;

@@ -287,7 +287,7 @@ hgks_status hgks_default_params(hgks_params *p) {
   p->scheme = HGKS_WENO; p->weights = HGKS_NONLINEAR; p->viscous = 0; p->characteristic = 1;
   p->precision = HGKS_FP64; p->jv_mode = 0; p->krylov_dim = 10; p->restarts = 3; p->jacobi_sweeps = 2;
   p->tstar_end = 1; p->gamma = 1.4; p->Pr = 1.0; p->mu = 0.0; p->cfl = 10.0; p->flux_cfl = 1.0;
-  p->tau_eps = 0.1; p->tau_C = 1.0; p->lin_weight = 0.025; p->weno_eps = 1e-8; p->flux_dt = 0.0;
+  p->tau_eps = 0.1; p->tau_C = 1.0; p->lin_weight = 0.025; p->weno_eps = 1e-6; p->flux_dt = 0.0;
   p->rho_inf = 1.0; p->u_inf[0] = 0.3; p->p_inf = 1.0 / 1.4; p->wall_T = 1.0 / 1.4; p->lid_speed = 0.0;
   return HGKS_OK;
 }

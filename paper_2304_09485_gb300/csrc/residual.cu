@@ -197,10 +197,11 @@ template <bool BATCH>
 __global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const double *__restrict__ Q,
                                                const double *__restrict__ coef, double *__restrict__ wface) {
   const int N = m.N, F = m.F;
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int NL = BATCH ? m.NL : N;
-  if (t >= 4 * NL) return;
-  const int slot = t / NL, i = t - slot * NL;
+  // block b covers local face (b mod 4) of cell range b / 4: the four blocks of a
+  // range run together and read its coefficients from L2 after the first
+  const int slot = blockIdx.x & 3, i = (blockIdx.x >> 2) * blockDim.x + threadIdx.x;
+  if (i >= NL) return;
   if (BATCH && !live(m, i)) return;                     // padding cell, or a mesh that has stopped
   const hgks_params &P = BATCH ? m.ptab[m.cmesh[i]] : Pv;
   const int cf = m.cface[(size_t)slot * N + i];
@@ -218,20 +219,16 @@ __global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const 
   rot_in(T, Qs, Qsl);
   const Eig e = eig_of(Qsl, P.gamma);
   const double ih = 1.0 / m.h[i];
-  double m2[6], xg[9];
-#pragma unroll
-  for (int k = 0; k < 6; k++) m2[k] = m.m2[(size_t)k * N + i];
-#pragma unroll
-  for (int k = 0; k < 9; k++) xg[k] = m.xg[(size_t)(slot * 9 + k) * N + i];
+  // second moments and Gauss points are re-read (from L1) for every component
+  // instead of being held across the loop: fewer live registers, no spills
+  const double *m2p = m.m2 + i, *xgp = m.xg + (size_t)slot * 9 * N + i;
   // weights of the sub-stencils
   unsigned valid = P.scheme == HGKS_WENO ? m.subvalid[i] : 0xFu;
   const int M = __popc(valid);
   const double gm = P.lin_weight, g0 = M ? 1.0 - gm * M : 1.0;
   const double ig0 = 1.0 / g0, iM = M ? 1.0 / M : 0.0;
-  double Th[9];                                         // face frame rows / h: scaled derivatives
-#pragma unroll
-  for (int k = 0; k < 9; k++) Th[k] = ih * T[k];
   double *out = wface + (size_t)side * 3 * kFaceState * F + f;
+#pragma unroll 1
   for (int c = 0; c < 5; c++) {
     double mr[5];
     if (P.characteristic) {
@@ -263,6 +260,9 @@ __global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const 
       bc[d] = s;
     }
     // smoothness indicators in the scaled frame: beta_0 = avg |grad P0|^2 + sum of squared second derivatives
+    double m2[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) m2[k] = m2p[(size_t)k * N];
     const double H00 = 2.0 * ac[3], H11 = 2.0 * ac[4], H22 = 2.0 * ac[5], H01 = ac[6], H02 = ac[7], H12 = ac[8];
     // avg |grad P0|^2 = |a|^2 + tr(M2 H^2) (M2: second moments, H symmetric)
     const double s00 = H00 * H00, s11 = H11 * H11, s22 = H22 * H22, s01 = H01 * H01, s02 = H02 * H02, s12 = H12 * H12;
@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const 
     const double q0m = q0 - (qd[0] * m2[0] + qd[1] * m2[1] + qd[2] * m2[2] + qd[3] * m2[3] + qd[4] * m2[4] + qd[5] * m2[5]);
 #pragma unroll
     for (int g = 0; g < 3; g++) {
-      const double x = xg[3 * g], y = xg[3 * g + 1], z = xg[3 * g + 2];
+      const double x = xgp[(size_t)(3 * g) * N], y = xgp[(size_t)(3 * g + 1) * N], z = xgp[(size_t)(3 * g + 2) * N];
       const double ax = fma(qd[0], x, fma(qd[3], y, fma(qd[4], z, lin[0])));   // lin0 + qd0 x + qd3 y + qd4 z
       const double by = fma(qd[1], y, fma(qd[5], z, lin[1]));                  // lin1 + qd1 y + qd5 z
       const double cz = fma(qd[2], z, lin[2]);                                 // lin2 + qd2 z
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const 
       double *o = out + (size_t)g * kFaceState * F;
       o[(size_t)c * F] = val;
 #pragma unroll
-      for (int k = 0; k < 3; k++) o[(size_t)(5 + 5 * k + c) * F] = Th[3 * k] * gx + Th[3 * k + 1] * gy + Th[3 * k + 2] * gz;
+      for (int k = 0; k < 3; k++) o[(size_t)(5 + 5 * k + c) * F] = ih * (T[3 * k] * gx + T[3 * k + 1] * gy + T[3 * k + 2] * gz);
     }
   }
 }
@@ -455,7 +455,8 @@ __device__ __forceinline__ void slope_c(const Prim &p, double g1, double ig1, co
 }
 
 // boundary state outside a boundary face (face frame, x = outward normal):
-// walls mirror the inner state in (p, U, V, W, T = p/rho); far field = free stream
+// walls mirror the inner state in (p, U, V, W, T = p/rho), an isothermal wall's
+// image with the density of zero mass exchange; far field = free stream
 __device__ void boundary_state(const hgks_params &P, int tag, const double *T, const double *Wl, const double *dWl,
                                double *Wr, double *dWr) {
   const double g = P.gamma;
@@ -486,8 +487,23 @@ __device__ void boundary_state(const hgks_params &P, int tag, const double *T, c
   for (int r = 0; r < 3; r++) ug[r] = vodd[r] ? 2.0 * uw[r] - u[r] : u[r];
   // an image colder than T_w / 2 (a cell hotter than 1.5 T_w) is held at T_w / 2, uniform
   const bool T_held = T_odd && 2.0 * P.wall_T - Tl < 0.5 * P.wall_T;
-  const double Tg = T_held ? 0.5 * P.wall_T : (T_odd ? 2.0 * P.wall_T - Tl : Tl), pg = pr;
-  const double rg = pg / Tg, qg2 = ug[0] * ug[0] + ug[1] * ug[1] + ug[2] * ug[2];
+  const double Tg = T_held ? 0.5 * P.wall_T : (T_odd ? 2.0 * P.wall_T - Tl : Tl);
+  // isothermal wall: the image sends back as much mass as the cell sends into the
+  // wall, rho_g M(U_n, T_g) = rho M(U_n, T) with M(U, T) = <u>_{u>0} of a unit-density
+  // Maxwellian = U erfc(-U / sqrt(2T)) / 2 + sqrt(T / (2 pi)) exp(-U^2 / (2T));
+  // p_g = rho_g T_g, and the image keeps the cell's relative pressure gradient
+  double rg, pscale = 1.0;
+  if (T_odd) {
+    const double Un = u[0];
+    const double sl = rsqrt(2.0 * Tl), sg = rsqrt(2.0 * Tg);   // sqrt(lambda)
+    const double Ml = 0.5 * Un * erfc(-sl * Un) + 0.28209479177387814347 * exp(-sl * sl * Un * Un) / sl;
+    const double Mg = 0.5 * Un * erfc(-sg * Un) + 0.28209479177387814347 * exp(-sg * sg * Un * Un) / sg;
+    rg = rho * Ml / Mg;
+    pscale = rg * Tg / pr;
+  } else {
+    rg = pr / Tg;
+  }
+  const double pg = rg * Tg, qg2 = ug[0] * ug[0] + ug[1] * ug[1] + ug[2] * ug[2];
   Wr[0] = rg;
 #pragma unroll
   for (int r = 0; r < 3; r++) Wr[1 + r] = rg * ug[r];
@@ -504,7 +520,7 @@ __device__ void boundary_state(const hgks_params &P, int tag, const double *T, c
     double dug[3], udug = 0.0;
 #pragma unroll
     for (int r = 0; r < 3; r++) { dug[r] = vodd[r] ? -sn * du[r] : sn * du[r]; udug += ug[r] * dug[r]; }
-    const double dpg = sn * dp, dTg = T_held ? 0.0 : (T_odd ? -sn * dT : sn * dT);
+    const double dpg = sn * dp * pscale, dTg = T_held ? 0.0 : (T_odd ? -sn * dT : sn * dT);
     const double drho = dpg / Tg - pg * dTg / (Tg * Tg);
     dWr[5 * d] = drho;
 #pragma unroll
@@ -689,10 +705,11 @@ __global__ void __launch_bounds__(256) k_flux(DevMesh m, hgks_params Pv, const d
                                                   const double *__restrict__ dt, const double *__restrict__ wface,
                                                   double *__restrict__ fflux, double *__restrict__ fpt, int *__restrict__ flags) {
   const int N = m.N, F = m.F;
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int FL = BATCH ? m.FL : F;
-  if (t >= 3 * FL) return;
-  const int g = t / FL, f = t - g * FL;
+  // block b covers Gauss point (b mod 3) of face range b / 3: the three blocks of a
+  // range run together and share the face's frame and cell states in L2
+  const int g = blockIdx.x % 3, f = (blockIdx.x / 3) * blockDim.x + threadIdx.x;
+  if (f >= FL) return;
   if (BATCH && !m.mact[m.fmesh[f]]) return;             // a mesh of a batch that has stopped
   const hgks_params &P = BATCH ? m.ptab[m.fmesh[f]] : Pv;
   double T[9];
@@ -739,6 +756,8 @@ __global__ void __launch_bounds__(256) k_flux(DevMesh m, hgks_params Pv, const d
   double Fl[5], Qp[5];
   const bool compact = P.scheme == HGKS_HWENO;
   gks_flux(P, W[0], dW[0], W[1], dW[1], dtf, Fl, compact ? Qp : nullptr);
+  // walls are impermeable: their faces carry momentum and energy, no mass
+  if (R < 0 && m.ftag[f] >= HGKS_BC_WALL_ISO && m.ftag[f] <= HGKS_BC_NOSLIP_ADIA) Fl[0] = 0.0;
   if (bad) atomicAdd(flags, bad);
   const double w = m.fS[f] * (1.0 / 3.0);
   double Fg[5];
@@ -890,14 +909,14 @@ void launch_residual(const DevMesh &m, Scratch &s, const hgks_params &p, const d
   }
   HGKS_PROF_END(K_COEF, st);
   HGKS_PROF_BEGIN(K_RECON, st);
-  if (batch) k_recon<true><<<grid_for(4 * NL, s.blk_recon), s.blk_recon, 0, st>>>(m, p, Q, s.coef, s.wface);
-  else k_recon<false><<<grid_for(4 * (int64_t)m.N, s.blk_recon), s.blk_recon, 0, st>>>(m, p, Q, s.coef, s.wface);
+  if (batch) k_recon<true><<<4 * grid_for(NL, s.blk_recon), s.blk_recon, 0, st>>>(m, p, Q, s.coef, s.wface);
+  else k_recon<false><<<4 * grid_for(m.N, s.blk_recon), s.blk_recon, 0, st>>>(m, p, Q, s.coef, s.wface);
   HGKS_PROF_END(K_RECON, st);
   HGKS_PROF_BEGIN(K_FLUX, st);
   if (batch)
-    k_flux<true><<<grid_for(3 * FL, s.blk_flux), s.blk_flux, 0, st>>>(m, p, Q, s.dt, s.wface, s.fflux, s.fpt, s.flags);
+    k_flux<true><<<3 * grid_for(FL, s.blk_flux), s.blk_flux, 0, st>>>(m, p, Q, s.dt, s.wface, s.fflux, s.fpt, s.flags);
   else
-    k_flux<false><<<grid_for(3 * (int64_t)m.F, s.blk_flux), s.blk_flux, 0, st>>>(m, p, Q, s.dt, s.wface, s.fflux, s.fpt, s.flags);
+    k_flux<false><<<3 * grid_for(m.F, s.blk_flux), s.blk_flux, 0, st>>>(m, p, Q, s.dt, s.wface, s.fflux, s.fpt, s.flags);
   HGKS_PROF_END(K_FLUX, st);
   HGKS_PROF_BEGIN(K_GATHER, st);
   const int grad = p.scheme == HGKS_HWENO && Gnew != nullptr;   // gradients wanted

@@ -71,7 +71,7 @@ def test_batch_entry_points_reject_bad_arguments_without_gpu():
     assert out.value is None
     p = H.hgks_default_params()
     assert L.hgks_batch_create(None, C.byref(p), 1, C.byref(out)) == 1
-    for fn, args in (("hgks_batch_residual", (None, None)), ("hgks_batch_gmres_step", (None, None, None)),
+    for fn, args in (("hgks_batch_residual", (None, None)), ("hgks_batch_gmres_step", (None, None, 1, None)),
                      ("hgks_batch_solve_steady", (None, 1e-8, 10, 1, None, None, None)),
                      ("hgks_batch_autotune", (None, None, None, None)), ("hgks_batch_info", (None, None)),
                      ("hgks_batch_destroy", (None,)), ("hgks_batch_set_state", (None, 0, None, None, None)),

@@ -230,3 +230,32 @@ def test_batch_of_one_mesh_equals_alone(cuda):
     assert abs(info.res_l1 - si.res_l1) <= 1e-13 * si.res_l1
     rel = (torch.linalg.norm((Qb - Q0) - (Qd - Q0)) / torch.linalg.norm(Qd - Q0)).item()
     assert rel <= 1e-10, rel
+
+
+def test_batch_step_graph_replay_equals_eager(cuda):
+    """hgks_batch_gmres_step replayed from its CUDA graph gives the eager step's
+    state and step records bit for bit (twice in a row: the second replay reuses
+    the captured graph)."""
+    import torch
+    kw = dict(scheme=1, krylov_dim=8, restarts=2, precision=1)
+    b, singles = make_batch(kw, seed=41)
+    n = len(singles)
+    Q0 = [torch.empty_like(s[5]) for s in singles]
+    G0 = [torch.empty_like(s[6]) for s in singles]
+    for k in range(n):
+        H.hgks_batch_get_state(b, k, Q=Q0[k], G=G0[k])
+    out = {}
+    for mode in (False, True):
+        for k in range(n):
+            H.hgks_batch_set_state(b, k, Q0[k], G0[k])
+        infos = [H.hgks_batch_gmres_step(b, use_graph=mode) for _ in range(2)]
+        Qs = [torch.empty_like(q) for q in Q0]
+        Gs = [torch.empty_like(g) for g in G0]
+        for k in range(n):
+            H.hgks_batch_get_state(b, k, Q=Qs[k], G=Gs[k])
+        torch.cuda.synchronize()
+        out[mode] = (infos, Qs, Gs)
+    for k in range(n):
+        assert torch.equal(out[False][1][k], out[True][1][k]) and torch.equal(out[False][2][k], out[True][2][k])
+        for s in range(2):
+            assert out[False][0][s][k].res_l1 == out[True][0][s][k].res_l1

@@ -3,9 +3,14 @@
 Tolerance for the residual: the paper's method forms R_i as a sum of face
 fluxes that cancel (R = 0 for a uniform flow), so each component is compared
 against the size of the terms it is summed from,
-    |R_gpu - R_oracle|_{i,c} <= 1e-11 * sum_p S_p |F_Euler(Q_i) . n_p|_c,
-a relative error of 1e-11 per residual component with respect to its flux
-scale. Gradients from Eq. (derivative) are compared the same way against
+    |R_gpu - R_oracle|_{i,c} <= 2e-12 * sum_p S_p |F_Euler(Q_i) . n_p|_c,
+a relative error of 2e-12 per residual component with respect to its flux
+scale (the measured maximum is 4e-13; the contract's 1e-11 bounds the full-size
+sampled cells and the gradients). Relative to the residual itself the two
+agree to 2e-11 wherever the face fluxes cancel to no less than 1e-2 of their
+size; where they cancel further, rounding of the flux terms (1e-16 of the
+flux scale in each of two independent FP64 evaluations) bounds what any two
+implementations can share. Gradients from Eq. (derivative) are compared against
 |Q_i,c| * sum_p S_p / |Omega_i|.
 """
 import numpy as np
@@ -18,7 +23,9 @@ from paper_2304_09485_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 GAMMA = 1.4
-TOL_R = 1e-11
+TOL_R = 1e-11          # the contract: gradients, full-size sampled cells
+TOL_R_FLUX = 2e-12     # residuals of the parity cases (measured maximum 4e-13)
+TOL_R_REL = 2e-11      # relative to |R| where |R| >= 1e-2 of the flux scale
 
 
 def euler_flux_rows(Q, n):
@@ -105,7 +112,11 @@ def test_residual_parity(cuda, name, kw):
     Rg = hm.to_caller(Rd)
     scale = flux_scale(om, Q)
     err = np.abs(Rg - Ro) / scale
-    assert err.max() <= TOL_R, f"max rel err {err.max():.3e} at {np.unravel_index(err.argmax(), err.shape)}"
+    assert err.max() <= TOL_R_FLUX, f"max rel err {err.max():.3e} at {np.unravel_index(err.argmax(), err.shape)}"
+    big = np.abs(Ro) >= 1e-2 * scale
+    assert big.mean() > 0.05
+    rel = np.abs(Rg - Ro)[big] / np.abs(Ro)[big]
+    assert rel.max() <= TOL_R_REL, f"max error relative to |R| {rel.max():.3e} ({big.mean():.2f} of the components)"
     if kw.get("scheme") == 1:
         Gg = hm.to_caller(Gn)
         gs = np.repeat(np.abs(Q), 3, axis=1) * area_over_volume(om)[:, None]
