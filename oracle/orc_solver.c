@@ -375,7 +375,8 @@ int orc_gmres_step(orc_mesh *m, const orc_params *p, double *Q, double *G, doubl
 
 /* Algorithm 1: iterate while res/res_ref > drop (the printed loop test is
  * inverted); res_ref is the largest residual seen so far (a flow started from
- * rest has a zero density residual at its first step). hist[k] = res of the
+ * rest has a zero density residual at its first step, and while every residual
+ * seen is zero there is no drop to measure). hist[k] = res of the
  * k-th state. Returns 0 if converged, 1 if the step limit was reached, < 0 on
  * error. */
 int orc_solve_steady(orc_mesh *m, const orc_params *p, double *Q, double *G, double drop,
@@ -389,7 +390,7 @@ int orc_solve_steady(orc_mesh *m, const orc_params *p, double *Q, double *G, dou
     double res = density_res(m, R);
     if (hist) hist[k] = res;
     if (res > res0) res0 = res;
-    if (res <= drop * res0) { rc = 0; break; }
+    if (res0 > 0.0 && res <= drop * res0) { rc = 0; break; }   /* a zero reference certifies no drop */
     if (k >= max_steps) { rc = 1; break; }
     double r2;
     if (orc_gmres_step(m, p, Q, G, &r2, NULL)) { rc = -1; break; }

@@ -218,7 +218,7 @@ __global__ void k_bcheck(BatchState bs) {
   if (bs.hist && k < bs.hist_len) bs.hist[(size_t)mesh * bs.hist_len + k] = res;
   if (!isfinite(res)) { bs.bad[mesh] = 1; bd.active[mesh] = 0; return; }
   if (res > bs.ref[mesh]) bs.ref[mesh] = res;
-  if (res <= bs.drop[mesh] * bs.ref[mesh]) { bs.conv[mesh] = 1; bd.active[mesh] = 0; return; }
+  if (bs.ref[mesh] > 0.0 && res <= bs.drop[mesh] * bs.ref[mesh]) { bs.conv[mesh] = 1; bd.active[mesh] = 0; return; }
   if (k >= bs.max_steps[mesh]) { bd.active[mesh] = 0; return; }
   bs.steps[mesh] = k + 1;
 }

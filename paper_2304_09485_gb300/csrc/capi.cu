@@ -597,7 +597,7 @@ static hgks_status solve_impl(hgks_mesh mesh, const hgks_params *p, double *Q, d
     if (!std::isfinite(res)) { st = fail(HGKS_ERR_NONPHYSICAL, "non-finite residual"); break; }
     if (hist_host) hist_host[k] = res;
     if (res > ref) ref = res;
-    if (res <= drop_tol * ref) { conv = true; break; }
+    if (ref > 0.0 && res <= drop_tol * ref) { conv = true; break; }   // a zero reference certifies no drop
     if (k >= max_steps) break;
     hgks_step_info si;
     if ((st = gmres_step_impl(m, p, Q, G, nullptr, &si, s_, true))) break;

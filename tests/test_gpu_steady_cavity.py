@@ -45,3 +45,24 @@ def test_cavity_compact_solve_to_1e8_matches_oracle(cuda):
     assert np.linalg.norm(Gc[cells] - Go) <= 1e-9 * np.linalg.norm(Go)
     assert abs(np.linalg.norm(Qc) - ref["Q_norm"]) <= 1e-9 * ref["Q_norm"]
     assert abs(np.linalg.norm(Gc) - ref["G_norm"]) <= 1e-9 * ref["G_norm"]
+
+
+def test_zero_reference_is_no_drop(cuda):
+    """The compact scheme reproduces a fluid at rest exactly, so a cavity started
+    from rest has a density residual of exactly zero at its first state; a zero
+    reference certifies no drop (as in the oracle's loop): with a drop of 1 the
+    solve, and every mesh of a batch, stops after one step, not before it."""
+    import torch
+    m = I.cavity_mesh(3)
+    cond = I.cavity_conditions(0.2, 50.0)
+    hm = H.hgks_mesh_create(m, scheme_mask=2)
+    p = H.hgks_default_params(scheme=1, Pr=0.72, **cond)
+    Q = hm.to_internal(I.state_from_conditions(m.n_tet, cond))
+    G = torch.zeros((15, m.n_tet), dtype=torch.float64, device="cuda")
+    b = H.hgks_batch_create([hm, hm], [p, p])
+    for k in range(2):
+        H.hgks_batch_set_state(b, k, Q, G)
+    info, hist, conv = H.hgks_solve_steady(hm, p, Q.clone(), G.clone(), drop_tol=1.0, max_steps=5)
+    assert hist[0] == 0.0 and conv and info.steps == 1
+    infos, bh, ok = H.hgks_batch_solve_steady(b, 1.0, 5)
+    assert ok and all(i.steps == 1 for i in infos)

@@ -670,8 +670,17 @@ def test_steady_loop_stops_at_the_first_drop_below_the_largest_residual():
     assert hist[k] <= drop * max(hist[:k + 1])
     assert all(hist[j] > drop * max(hist[:j + 1]) for j in range(k))
     np.testing.assert_array_equal(Q, Qs)
-    # a drop of 1 is met by the first state; no step is taken beyond max_steps
-    _, _, h1, c1 = om.solve_steady(p, Q0, drop=1.0, max_steps=10)
+    # the compact scheme reconstructs the fluid at rest exactly (G = 0), so the
+    # first state's density residual is exactly zero: a zero reference certifies
+    # no drop, and even a drop of 1 is met only after the first step
+    cond2 = I.cavity_conditions(0.2, 50.0)
+    p2 = O.make_params(scheme=1, Pr=0.72, **cond2)
+    Q2 = I.state_from_conditions(m.n_tet, cond2)
+    _, _, h2, c2 = om.solve_steady(p2, Q2, np.zeros((m.n_tet, 15)), drop=1.0, max_steps=5)
+    assert h2[0] == 0.0 and c2 and len(h2) == 2
+    # from a moving state a drop of 1 is met by the first state; no step is
+    # taken beyond max_steps
+    _, _, h1, c1 = om.solve_steady(p, Qs, drop=1.0, max_steps=10)
     assert c1 and len(h1) == 1
     Qm, _, h0, c0 = om.solve_steady(p, Qs, drop=1e-12, max_steps=0)
     assert not c0 and len(h0) == 1

@@ -154,6 +154,8 @@ PLANTED = [
     ("Givens rotation: sign of s", "orc_solver.c",
      "H[(j + 1) * mk + k] = -s * h1 + c * h2;", "H[(j + 1) * mk + k] = s * h1 + c * h2;"),
     ("back substitution adds", "orc_solver.c", "s -= H[j * mk + k] * y[k];", "s += H[j * mk + k] * y[k];"),
+    ("the steady loop takes a zero reference as a drop", "orc_solver.c",
+     "if (res0 > 0.0 && res <= drop * res0)", "if (res <= drop * res0)"),
     ("density residual norm without the volume", "orc_solver.c",
      "s += fabs(R[5 * i]) / m->vol[i];", "s += fabs(R[5 * i]);"),
     ("matrix-free product: sign of the Frechet difference", "orc_solver.c",
