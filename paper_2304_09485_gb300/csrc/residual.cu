@@ -219,16 +219,20 @@ __global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const 
   rot_in(T, Qs, Qsl);
   const Eig e = eig_of(Qsl, P.gamma);
   const double ih = 1.0 / m.h[i];
-  // second moments and Gauss points are re-read (from L1) for every component
-  // instead of being held across the loop: fewer live registers, no spills
-  const double *m2p = m.m2 + i, *xgp = m.xg + (size_t)slot * 9 * N + i;
+  double m2[6], xg[9];
+#pragma unroll
+  for (int k = 0; k < 6; k++) m2[k] = m.m2[(size_t)k * N + i];
+#pragma unroll
+  for (int k = 0; k < 9; k++) xg[k] = m.xg[(size_t)(slot * 9 + k) * N + i];
   // weights of the sub-stencils
   unsigned valid = P.scheme == HGKS_WENO ? m.subvalid[i] : 0xFu;
   const int M = __popc(valid);
   const double gm = P.lin_weight, g0 = M ? 1.0 - gm * M : 1.0;
   const double ig0 = 1.0 / g0, iM = M ? 1.0 / M : 0.0;
+  double Th[9];                                         // face frame rows / h: scaled derivatives
+#pragma unroll
+  for (int k = 0; k < 9; k++) Th[k] = ih * T[k];
   double *out = wface + (size_t)side * 3 * kFaceState * F + f;
-#pragma unroll 1
   for (int c = 0; c < 5; c++) {
     double mr[5];
     if (P.characteristic) {
@@ -260,9 +264,6 @@ __global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const 
       bc[d] = s;
     }
     // smoothness indicators in the scaled frame: beta_0 = avg |grad P0|^2 + sum of squared second derivatives
-    double m2[6];
-#pragma unroll
-    for (int k = 0; k < 6; k++) m2[k] = m2p[(size_t)k * N];
     const double H00 = 2.0 * ac[3], H11 = 2.0 * ac[4], H22 = 2.0 * ac[5], H01 = ac[6], H02 = ac[7], H12 = ac[8];
     // avg |grad P0|^2 = |a|^2 + tr(M2 H^2) (M2: second moments, H symmetric)
     const double s00 = H00 * H00, s11 = H11 * H11, s22 = H22 * H22, s01 = H01 * H01, s02 = H02 * H02, s12 = H12 * H12;
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const 
     const double q0m = q0 - (qd[0] * m2[0] + qd[1] * m2[1] + qd[2] * m2[2] + qd[3] * m2[3] + qd[4] * m2[4] + qd[5] * m2[5]);
 #pragma unroll
     for (int g = 0; g < 3; g++) {
-      const double x = xgp[(size_t)(3 * g) * N], y = xgp[(size_t)(3 * g + 1) * N], z = xgp[(size_t)(3 * g + 2) * N];
+      const double x = xg[3 * g], y = xg[3 * g + 1], z = xg[3 * g + 2];
       const double ax = fma(qd[0], x, fma(qd[3], y, fma(qd[4], z, lin[0])));   // lin0 + qd0 x + qd3 y + qd4 z
       const double by = fma(qd[1], y, fma(qd[5], z, lin[1]));                  // lin1 + qd1 y + qd5 z
       const double cz = fma(qd[2], z, lin[2]);                                 // lin2 + qd2 z
@@ -339,7 +340,7 @@ __global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const 
       double *o = out + (size_t)g * kFaceState * F;
       o[(size_t)c * F] = val;
 #pragma unroll
-      for (int k = 0; k < 3; k++) o[(size_t)(5 + 5 * k + c) * F] = ih * (T[3 * k] * gx + T[3 * k + 1] * gy + T[3 * k + 2] * gz);
+      for (int k = 0; k < 3; k++) o[(size_t)(5 + 5 * k + c) * F] = Th[3 * k] * gx + Th[3 * k + 1] * gy + Th[3 * k + 2] * gz;
     }
   }
 }
