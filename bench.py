@@ -364,10 +364,10 @@ def run_precision(args, rank, world):
     per step. The compact scheme does not reach a steady state on these
     tetrahedral sphere grids (its gradient update settles into a two-step cycle
     in the wall layer), so C_D is reported over the last steps as the mean and
-    the spread of that cycle. On a scaled-down sphere of the same construction
-    (6 x 8 x 8, 8 layers) the oracle gives the reference for both."""
+    the spread of that cycle. The comparison with the oracle on a scaled-down
+    sphere of the same construction is a GPU test
+    (tests/test_gpu_precision.py)."""
     import torch
-    import oracle as O
     import paper_2304_09485_gb300 as H
     from paper_2304_09485_gb300 import inputs as I
     local = int(os.environ.get("LOCAL_RANK", 0))
@@ -414,32 +414,6 @@ def run_precision(args, rank, world):
                    "ms_per_step_fp64": ms64, "ms_per_step_mixed": ms32,
                    "mcells_per_s_fp64": m.n_tet / ms64 / 1e3, "mcells_per_s_mixed": m.n_tet / ms32 / 1e3}
     del traj, Q64, G64, Q32, G32, hm
-    # the scaled-down case against the oracle
-    ms_ = I.sphere_mesh(8, 8, stretch=I.sphere_stretch(8, dr1=3e-2 * 3), wall_tag=I.BC_NOSLIP_ADIA)
-    om = O.OracleMesh(ms_)
-    hs = H.hgks_mesh_create(ms_, scheme_mask=2, device=local)
-    po = O.make_params(**cond, **{k: v for k, v in kw.items()})
-    Qo = I.state_from_conditions(ms_.n_tet, cond)
-    Go = np.zeros((ms_.n_tet, 15))
-    small = {"n_cells": ms_.n_tet, "steps": args.oracle_steps}
-    res = {}
-    for prec in (0, 1):
-        p = H.hgks_default_params(precision=prec, **cond, **kw)
-        Q = hs.to_internal(Qo, device=f"cuda:{local}")
-        G = hs.to_internal(Go, device=f"cuda:{local}")
-        for _ in range(args.oracle_steps):
-            H.hgks_gmres_step(hs, p, Q, G)
-        res[prec] = (hs.to_caller(Q), cd(hs, p, Q, G))
-    Qr, Gr = Qo.copy(), Go.copy()
-    for _ in range(args.oracle_steps):
-        Qr, Gr, _, _ = om.gmres_step(po, Qr, Gr)
-    cdo = float(om.wall_force(po, Qr, Gr, I.BC_NOSLIP_ADIA)[0] / qinf)
-    for prec, name in ((0, "fp64"), (1, "mixed")):
-        Qg, cdg = res[prec]
-        small[name] = {"cd": cdg, "cd_rel_err_vs_oracle": abs(cdg - cdo) / abs(cdo),
-                       "state_rel_l2_vs_oracle": float(np.linalg.norm(Qg - Qr) / np.linalg.norm(Qr))}
-    small["cd_oracle"] = cdo
-    out["small_vs_oracle"] = small
     if rank != 0:
         return 0
     res_line = {"metric": "precision: drag coefficient and state error, FP32 Krylov vs FP64", "value": out["full"]["cd_rel_diff"],
@@ -578,7 +552,6 @@ def main():
     ap.add_argument("--workload", default="sphere", choices=["sphere", "batch", "serve", "precision"],
                     help="sphere: the 2.36M-tet sphere (default); batch: many problems in one batch; "
                          "serve: Poisson-arriving solves through the request server")
-    ap.add_argument("--oracle-steps", type=int, default=3, help="precision workload: oracle steps on the small sphere")
     ap.add_argument("--serve-requests", type=int, default=96)
     ap.add_argument("--serve-rate", type=float, default=0.4,
                     help="requests per second (0.4: about 0.8 x the measured served capacity of ~0.5/s)")
