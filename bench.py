@@ -429,9 +429,12 @@ def run_precision(args, rank, world):
 def run_serve(args, rank, world):
     """Steady-solve requests with Poisson arrivals served by the continuous-
     batching server (mixed precision) against the same requests solved one
-    after another with the single-mesh FP64 solver (first come, first served:
-    each waits for the one before). Time to convergence (TTC) runs from a
-    request's arrival to its finished state; mesh building is included."""
+    after another with the single-mesh FP64 solver (a live stream too: first
+    come, first served, each waits for its arrival and for the one before).
+    Time to convergence (TTC) runs from a request's arrival to its finished
+    state; mesh building is included. Solves per hour count converged requests
+    only; requests that hit the step limit or went non-finite are reported
+    apart."""
     import torch
     import paper_2304_09485_gb300 as H
     from paper_2304_09485_gb300 import inputs as I
@@ -482,9 +485,14 @@ def run_serve(args, rank, world):
     info = srv.info()
     del srv
     span_a = max(s["done"] for s in served) - min(s["submit"] for s in served)
-    # (b) one after another, FP64, queueing simulated on the measured solve times
+    # (b) one after another, FP64, as a live stream: each request is taken when it
+    # has arrived and the one before it is done (first come, first served)
     seq, end = [], 0.0
+    t0b = time.perf_counter()
     for r in reqs:
+        wait = r["arrival"] - (time.perf_counter() - t0b)
+        if wait > 0:
+            time.sleep(wait)
         t1 = time.perf_counter()
         hm = H.hgks_mesh_create(r["mesh"], scheme_mask=1, device=local)
         Q = hm.to_internal(r["Q0"], device=f"cuda:{local}")
@@ -498,10 +506,9 @@ def run_serve(args, rank, world):
                 raise
             failed, conv, steps = True, False, -1
         torch.cuda.synchronize()
+        end = time.perf_counter() - t0b
         dur = time.perf_counter() - t1
         del hm, Q
-        start = max(r["arrival"], end)
-        end = start + dur
         seq.append(dict(ttc=end - r["arrival"], steps=steps, converged=bool(conv), failed=failed, service=dur))
     span_b = end - reqs[0]["arrival"]
     if rank != 0:

@@ -285,3 +285,34 @@ def test_cancel_from_another_thread_while_rounds_run(cuda):
         else:
             assert st.status in (H.HGKS_OK, H.HGKS_ERR_NOT_CONVERGED), (rid, st.status)
     assert any(srv.status(r).status == H.HGKS_ERR_CANCELLED for r in victims)
+
+
+def test_served_request_matches_the_oracle_solve(cuda):
+    """A request served beside others (FP64 server) ends in the state the oracle's
+    own steady solve (Algorithm 1, orc_solve_steady) reaches from the same start:
+    the 3,456-tet inviscid sphere to a 1e-3 drop of the density residual, the
+    same step count and the state within a relative L2 of 1e-9."""
+    import oracle as O
+    m = I.sphere_mesh(4, 6, stretch=1.3)
+    cond = I.sphere_conditions(0.3)
+    kw = dict(scheme=0, krylov_dim=10, restarts=3, jacobi_sweeps=2)
+    Q0 = I.state_from_conditions(m.n_tet, cond)
+    drop, max_steps = 1e-3, 400
+    om = O.OracleMesh(m)
+    Qo, _, hist_o, conv_o = om.solve_steady(O.make_params(**cond, **kw), Q0, drop=drop, max_steps=max_steps)
+    assert conv_o
+    srv = H.hgks_server(H.hgks_default_params(**kw), hbm_budget_bytes=int(2e9), max_inflight=4)
+    # two other requests run beside it
+    others = [(I.cavity_mesh(3, seed=I.BASE_SEED + 31), I.cavity_conditions(0.2, 80.0)),
+              (I.sphere_mesh(3, 6, stretch=1.25), I.sphere_conditions(0.45, aoa_deg=8.0))]
+    for mo, co in others:
+        srv.submit(mo, H.hgks_default_params(**{**co, "Pr": 0.72 if co["viscous"] else 1.0, **kw}),
+                   I.state_from_conditions(mo.n_tet, co), drop_tol=drop, max_steps=50)
+    rid = srv.submit(m, H.hgks_default_params(**cond, **kw), Q0, drop_tol=drop, max_steps=max_steps)
+    t0 = time.time()
+    while srv.status(rid).state < 3 and time.time() - t0 < 300:
+        srv.step()
+    st = srv.status(rid)
+    assert st.status == 0 and st.solve.converged and st.solve.steps == len(hist_o) - 1, (st.solve.steps, len(hist_o) - 1)
+    Q, _ = srv.collect(rid)
+    assert np.linalg.norm(Q - Qo) <= 1e-9 * np.linalg.norm(Qo)
