@@ -192,12 +192,14 @@ def sphere_mesh(n: int = 32, layers: int = 64, r_in: float = 0.5, r_out: float =
     """Cubed-sphere O-grid around a sphere, split into tetrahedra.
 
     Six n x n patches (equiangular) on the sphere, `layers` radial layers. Each
-    surface quadrilateral is cut along the diagonal through its lowest-index
-    vertex; each triangle is extruded into prisms, and each prism is cut into 3
-    tetrahedra by the lowest-vertex-index rule. That rule makes every shared
-    quadrilateral get the same diagonal from both sides, so the mesh is
-    conforming across the patch seams. Cell count = 6 n^2 layers * 6, the same as
-    6 tetrahedra per hexahedron.
+    surface quadrilateral is cut along its shorter diagonal (at the eight cube
+    corners, where three patches meet at 120 degrees, this gives the corner vertex
+    six triangles instead of obtuse ones); each triangle is extruded into prisms,
+    and each prism is cut into 3 tetrahedra by the lowest-vertex-index rule. That
+    rule makes every lateral quadrilateral shared by two prisms get the same
+    diagonal from both sides (a surface quadrilateral's diagonal is its own), so
+    the mesh is conforming across the patch seams. Cell count = 6 n^2 layers * 6,
+    the same as 6 tetrahedra per hexahedron.
     """
     rng = np.random.default_rng(seed)
     # surface lattice points of the cube [0,n]^3
@@ -233,8 +235,10 @@ def sphere_mesh(n: int = 32, layers: int = 64, r_in: float = 0.5, r_out: float =
                 return S(c[0], c[1], c[2])
             quads.append(np.stack([P(a, b), P(a + 1, b), P(a + 1, b + 1), P(a, b + 1)], axis=1))
     quads = np.concatenate(quads, axis=0)
-    # split each quad along the diagonal through its minimum-index vertex
-    m = np.argmin(quads, axis=1)
+    # split each quad along its shorter diagonal (ties: the diagonal through vertex 0)
+    d02 = np.linalg.norm(unit[quads[:, 0]] - unit[quads[:, 2]], axis=1)
+    d13 = np.linalg.norm(unit[quads[:, 1]] - unit[quads[:, 3]], axis=1)
+    m = np.where(d02 <= d13 * (1.0 + 1e-12), 0, 1)
     r = np.arange(quads.shape[0])
     q0 = quads[r, m]
     q1 = quads[r, (m + 1) % 4]
