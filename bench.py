@@ -167,9 +167,26 @@ def cpu_baseline(steps=1, max_seconds=30.0):
     om.residual(p, Q)                  # the residual alone (fits already built)
     res_s = time.perf_counter() - t1
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    # the residual of the compact cavity (3,072 tets, HWENO, viscous) on one core and on all
+    mc = I.cavity_mesh(8)
+    cc = I.cavity_conditions(0.15, 100.0)
+    oc = O.OracleMesh(mc)
+    pc = O.make_params(scheme=1, Pr=0.72, **cc)
+    Qc, Gc = I.smooth_state(mc, amp=0.02, base=(1.0, 0.1, 0.0, 0.0, cc["p_inf"]))
+    oc.residual(pc, Qc, Gc)                                  # fits (setup, not timed)
+    cav = {}
+    prev = O.set_threads(1)
+    for label, nt in (("1_core", 1), (f"{prev}_cores", prev)):
+        O.set_threads(nt)
+        t2 = time.perf_counter()
+        for _ in range(5):
+            oc.residual(pc, Qc, Gc)
+        cav[label] = mc.n_tet * 5 / (time.perf_counter() - t2) / 1e6
+    O.set_threads(prev)
     return {"value": m.n_tet * done / dt / 1e6, "unit": "Mcells/s", "cores": cores, "kind": "oracle",
             "sample": f"{done} implicit step(s) on {m.n_tet} tets (6x12x12x24 sphere, same scheme and parameters)",
             "residual_only": {"value": m.n_tet / res_s / 1e6, "unit": "Mcells/s"},
+            "residual_cavity_3072_hweno_mcells_per_s": cav,
             "seconds": dt}
 
 

@@ -95,6 +95,8 @@ def lib():
                      "orc_gmres_step", "orc_solve_steady", "orc_recon_side", "orc_fit_cell", "orc_slope",
                      "orc_lu_solve", "orc_inverse"]:
             getattr(L, name).restype = C.c_int
+        L.orc_set_threads.restype = C.c_int
+        L.orc_set_threads.argtypes = [C.c_int]
         L.orc_monomial_moment.restype = C.c_double
         L.orc_monomial_moment.argtypes = [dp, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]
         _lib = L
@@ -367,3 +369,8 @@ def primitive(Q, gamma=1.4):
     pr = np.zeros(5)
     lib().orc_primitive(_p(np.ascontiguousarray(Q, dtype=np.float64)), C.c_double(gamma), _p(pr))
     return pr
+
+
+def set_threads(n: int) -> int:
+    """OpenMP threads of the oracle's loops (n > 0); returns the previous maximum."""
+    return int(lib().orc_set_threads(int(n)))

@@ -133,4 +133,5 @@ int orc_gmres_step(orc_mesh *m, const orc_params *p, double *Q, double *G, doubl
                    double *dQ_out);
 int orc_solve_steady(orc_mesh *m, const orc_params *p, double *Q, double *G, double drop,
                      int max_steps, double *hist, int *steps_out);
+int orc_set_threads(int n);   /* OpenMP threads of the loops above; returns the previous maximum */
 #endif

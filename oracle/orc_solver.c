@@ -8,6 +8,7 @@
  * Eq. (deri-matrix); Jacobi preconditioner of Eq. (precond); Algorithm 1. */
 #include <float.h>
 #include <math.h>
+#include <omp.h>
 #include <stdlib.h>
 #include <string.h>
 #include "orc.h"
@@ -398,4 +399,12 @@ int orc_solve_steady(orc_mesh *m, const orc_params *p, double *Q, double *G, dou
   if (steps_out) *steps_out = k;
   free(R);
   return rc;
+}
+
+/* Threads of the OpenMP loops (timing the oracle single-threaded and on all
+ * cores); returns the previous maximum. */
+int orc_set_threads(int n) {
+  int prev = omp_get_max_threads();
+  if (n > 0) omp_set_num_threads(n);
+  return prev;
 }
