@@ -285,6 +285,7 @@ def run_batch(args, rank, world):
     setup_s = time.perf_counter() - t0
     n_cells = sum(p["n_cells"] for p in probs)
     b = H.hgks_batch_create(meshes, params)
+    init_states = [(Q.clone(), None if G is None else G.clone()) for Q, G in states]
     for k, (Q, G) in enumerate(states):
         H.hgks_batch_set_state(b, k, Q, G)
     blk = H.hgks_batch_autotune(b)
@@ -345,6 +346,22 @@ def run_batch(args, rank, world):
     torch.cuda.synchronize()
     seq_ms = e0.elapsed_time(e1)
     clk = clocks.stop()
+    # (d) optionally: every mesh solved from its initial state to a drop, as one batch
+    # (device-side convergence test, graph replay): how many converge, in how many steps
+    solve = None
+    if args.batch_drop > 0:
+        for k, (Q0k, G0k) in enumerate(init_states):
+            H.hgks_batch_set_state(b, k, Q0k, G0k)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        infos_d, hist_d, _ = H.hgks_batch_solve_steady(b, args.batch_drop, args.batch_max_steps, use_graph=True)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t1
+        solve = {"drop": args.batch_drop, "max_steps": args.batch_max_steps, "seconds": wall,
+                 "converged": sum(1 for i in infos_d if i.converged), "meshes": len(infos_d),
+                 "steps_converged": sorted(int(i.steps) for i in infos_d if i.converged),
+                 "final_drop_not_converged": sorted(float(i.res_final / i.res_ref) for i in infos_d
+                                                   if not i.converged and i.res_ref > 0)}
     if rank != 0:
         return 0
     rate = lambda ms, steps: n_cells * steps / (ms / 1000.0) / 1e6
@@ -367,6 +384,7 @@ def run_batch(args, rank, world):
            "speedup_vs_sequential": seq_ms / graph_ms,
            "kernels_ms_one_step": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
            "gpu_launches": int(launches), "setup_s": setup_s, "clocks": clk,
+           "solve_to_drop": solve,
            "sizes": sorted(p["n_cells"] for p in probs)}
     print(json.dumps(res))
     return 0
@@ -588,6 +606,9 @@ def main():
     ap.add_argument("--batch-meshes", type=int, default=48)
     ap.add_argument("--batch-scheme", default="hweno", choices=["weno", "hweno"])
     ap.add_argument("--batch-precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--batch-drop", type=float, default=0.0,
+                    help="batch workload: also solve every mesh from its start to this drop (0: skip)")
+    ap.add_argument("--batch-max-steps", type=int, default=500)
     ap.add_argument("--launch-precision", default="fp64", choices=["fp64", "mixed"],
                     help="precision of the step timed by --launch-list")
     ap.add_argument("--launch-list", action="store_true",
