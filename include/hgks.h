@@ -123,6 +123,10 @@ typedef struct {
   double Mach;             /* > 0: derive the flow conditions (above); 0: explicit    */
   double Re;               /* Reynolds number (0: inviscid) when Mach > 0             */
   double aoa_deg;          /* angle of attack in degrees (x-y plane) when Mach > 0    */
+  double grad_relax;       /* compact scheme: G^{n+1} = G^n + grad_relax (G_new - G^n);
+                              1 (the default) or 0: Algorithm 1's G^{n+1} = G_new;
+                              values in (0, 1) under-relax the update (an option the
+                              paper does not have); outside [0, 1]: HGKS_ERR_ARG      */
 } hgks_params;
 
 typedef struct {

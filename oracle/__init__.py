@@ -58,7 +58,7 @@ class Params(C.Structure):
                 ("tau_eps", C.c_double), ("tau_C", C.c_double), ("lin_weight", C.c_double),
                 ("weno_eps", C.c_double), ("flux_dt", C.c_double),
                 ("rho_inf", C.c_double), ("u_inf", C.c_double * 3), ("p_inf", C.c_double),
-                ("wall_T", C.c_double), ("lid_speed", C.c_double)]
+                ("wall_T", C.c_double), ("lid_speed", C.c_double), ("grad_relax", C.c_double)]
 
 
 def make_params(**kw) -> Params:
@@ -66,7 +66,8 @@ def make_params(**kw) -> Params:
     d = dict(scheme=0, weights=0, viscous=0, characteristic=1, krylov_dim=10, restarts=3,
              jacobi_sweeps=2, tstar_end=1, jv_mode=0, gamma=1.4, Pr=1.0, mu=0.0, cfl=10.0, flux_cfl=1.0, tau_eps=0.1,
              tau_C=1.0, lin_weight=0.025, weno_eps=1e-6, flux_dt=0.0, rho_inf=1.0,
-             u_inf=(0.3, 0.0, 0.0), p_inf=1.0 / 1.4, wall_T=1.0 / 1.4, lid_speed=0.0)
+             u_inf=(0.3, 0.0, 0.0), p_inf=1.0 / 1.4, wall_T=1.0 / 1.4, lid_speed=0.0,
+             grad_relax=1.0)
     d.update(kw)
     p = Params()
     for k, v in d.items():

@@ -37,6 +37,7 @@ typedef struct {
   double flux_dt;        /* > 0: fixed time step inside the flux (tests)     */
   double rho_inf, u_inf[3], p_inf; /* far-field state                        */
   double wall_T, lid_speed;        /* isothermal wall temperature p/rho; lid speed along +x */
+  double grad_relax;     /* compact: G += grad_relax (G_new - G); 0 or 1: G = G_new (Algorithm 1) */
 } orc_params;
 
 typedef struct { int64_t cell; double shift[3]; } orc_sref;

@@ -367,7 +367,12 @@ int orc_gmres_step(orc_mesh *m, const orc_params *p, double *Q, double *G, doubl
   }
   if (!rc) {
     for (int64_t k = 0; k < 5 * nc; k++) Q[k] += dQ[k];
-    if (Gn) memcpy(G, Gn, sizeof(double) * 15 * nc);
+    if (Gn) {
+      /* Algorithm 1: G^{n+1} = G_new; optionally under-relaxed, G += a (G_new - G) */
+      const double a = p->grad_relax > 0.0 ? p->grad_relax : 1.0;
+      if (a == 1.0) memcpy(G, Gn, sizeof(double) * 15 * nc);
+      else for (int64_t k = 0; k < 15 * nc; k++) G[k] += a * (Gn[k] - G[k]);
+    }
     if (dQ_out) memcpy(dQ_out, dQ, sizeof(double) * 5 * nc);
   }
   free(dt); free(R); free(Gn); free(diag); free(off); free(dQ);

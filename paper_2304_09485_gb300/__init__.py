@@ -36,7 +36,7 @@ class hgks_params(C.Structure):
                 ("lin_weight", C.c_double), ("weno_eps", C.c_double), ("flux_dt", C.c_double),
                 ("rho_inf", C.c_double), ("u_inf", C.c_double * 3), ("p_inf", C.c_double),
                 ("wall_T", C.c_double), ("lid_speed", C.c_double),
-                ("Mach", C.c_double), ("Re", C.c_double), ("aoa_deg", C.c_double)]
+                ("Mach", C.c_double), ("Re", C.c_double), ("aoa_deg", C.c_double), ("grad_relax", C.c_double)]
 
 
 class hgks_mesh_info_t(C.Structure):

@@ -178,13 +178,19 @@ __global__ void __launch_bounds__(kB) k_bdensity(int N, BatchDev bd, const doubl
 }
 
 // Q += dQ and G = G_new for the meshes still iterating
-__global__ void __launch_bounds__(kB) k_bupdate(int N, BatchDev bd, double *__restrict__ Q, const double *__restrict__ dQ,
+__global__ void __launch_bounds__(kB) k_bupdate(int N, BatchDev bd, const hgks_params *__restrict__ ptab,
+                                                double *__restrict__ Q, const double *__restrict__ dQ,
                                                 double *__restrict__ G, const double *__restrict__ Gnew, int ng) {
   const int i = blockIdx.x * kB + threadIdx.x;
-  if (!bd.active[bd.bmesh[blockIdx.x]]) return;
+  const int mesh = bd.bmesh[blockIdx.x];
+  if (!bd.active[mesh]) return;
 #pragma unroll
   for (int c = 0; c < 5; c++) Q[(size_t)c * N + i] += dQ[(size_t)c * N + i];
-  for (int c = 0; c < ng; c++) G[(size_t)c * N + i] = Gnew[(size_t)c * N + i];
+  const double a = ptab[mesh].grad_relax > 0.0 ? ptab[mesh].grad_relax : 1.0;   // per-mesh relaxation of G
+  for (int c = 0; c < ng; c++) {
+    const size_t k = (size_t)c * N + i;
+    G[k] = a == 1.0 ? Gnew[k] : fma(a, Gnew[k] - G[k], G[k]);
+  }
 }
 
 
@@ -373,7 +379,7 @@ void launch_batch_check(BatchState &bs, cudaStream_t st) {
 void launch_batch_update(const DevMesh &m, BatchState &bs, double *Q, const double *dQ, double *G, const double *Gnew,
                          int ncomp_g, cudaStream_t st) {
   HGKS_PROF_BEGIN(K_UPDATE, st);
-  k_bupdate<<<std::max(1, bs.b.nblocks), kB, 0, st>>>(m.N, bs.b, Q, dQ, G, Gnew, ncomp_g);
+  k_bupdate<<<std::max(1, bs.b.nblocks), kB, 0, st>>>(m.N, bs.b, m.ptab, Q, dQ, G, Gnew, ncomp_g);
   HGKS_PROF_END(K_UPDATE, st);
 }
 

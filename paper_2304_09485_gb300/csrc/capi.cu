@@ -96,6 +96,7 @@ hgks_status check_params(const Mesh &m, const hgks_params *p) {
   if (!p->viscous && !(p->tau_eps > 0.0)) return fail(HGKS_ERR_ARG, "inviscid flow needs tau_eps > 0");
   if (p->precision != HGKS_FP64 && p->precision != HGKS_MIXED) return fail(HGKS_ERR_ARG, "unknown precision");
   if (p->jv_mode != 0 && p->jv_mode != 1) return fail(HGKS_ERR_ARG, "jv_mode must be 0 (assembled) or 1 (matrix-free)");
+  if (!(p->grad_relax >= 0.0 && p->grad_relax <= 1.0)) return fail(HGKS_ERR_ARG, "grad_relax must be in [0, 1]");
   return HGKS_OK;
 }
 
@@ -289,6 +290,7 @@ hgks_status hgks_default_params(hgks_params *p) {
   p->tstar_end = 1; p->gamma = 1.4; p->Pr = 1.0; p->mu = 0.0; p->cfl = 10.0; p->flux_cfl = 1.0;
   p->tau_eps = 0.1; p->tau_C = 1.0; p->lin_weight = 0.025; p->weno_eps = 1e-6; p->flux_dt = 0.0;
   p->rho_inf = 1.0; p->u_inf[0] = 0.3; p->p_inf = 1.0 / 1.4; p->wall_T = 1.0 / 1.4; p->lid_speed = 0.0;
+  p->grad_relax = 1.0;
   return HGKS_OK;
 }
 
@@ -478,7 +480,7 @@ static hgks_status enqueue_step(Mesh &m, const hgks_params *p, double *Q, double
   hgks_status st = gmres_solve(d, s, *p, s.R, s.dQ, nullptr, st_, Q, G);
   if (st) return st;
   if (dQ_out) HGKS_CUDA(cudaMemcpyAsync(dQ_out, s.dQ, sizeof(double) * 5 * m.N, cudaMemcpyDeviceToDevice, st_));
-  launch_update(d, Q, s.dQ, G, s.Gnew, p->scheme == HGKS_HWENO ? 15 : 0, st_);
+  launch_update(d, Q, s.dQ, G, s.Gnew, p->scheme == HGKS_HWENO ? 15 : 0, p->grad_relax, st_);
   return last_launch();
 }
 

@@ -180,8 +180,9 @@ void launch_norm(const DevMesh &m, Scratch &s, const double *x, double *out_dev,
 void launch_wall_force(const DevMesh &m, const Scratch &s, int tag, double *force_dev, cudaStream_t st);
 constexpr int kHsNormQ = 65 * 64 + 210;   // hs slots of the matrix-free products: ||Q||, ||x||, sigma, 0
 void launch_density_l1(const DevMesh &m, Scratch &s, const double *R, double *out_dev, cudaStream_t st);
+// G = G + relax (Gnew - G) (relax 0 or 1: G = Gnew)
 void launch_update(const DevMesh &m, double *Q, const double *dQ, double *G, const double *Gnew, int ncomp_g,
-                   cudaStream_t st);
+                   double relax, cudaStream_t st);
 // batches (batch.cu): one launch per phase for all meshes of the batch
 void launch_batch_gmres(const DevMesh &m, Scratch &s, BatchState &bs, const hgks_params &p, const double *rhs,
                         double *dx, cudaStream_t st);

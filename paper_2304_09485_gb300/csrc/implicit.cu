@@ -624,10 +624,11 @@ __global__ void __launch_bounds__(kBlock) k_density_l1(int N, const double *__re
 }
 
 __global__ void k_update(int64_t n5, int64_t ng, double *__restrict__ Q, const double *__restrict__ dQ, double *__restrict__ G,
-                         const double *__restrict__ Gnew) {
+                         const double *__restrict__ Gnew, double relax) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n5 + ng; k += (int64_t)gridDim.x * blockDim.x) {
     if (k < n5) Q[k] += dQ[k];
-    else G[k - n5] = Gnew[k - n5];
+    else if (relax == 1.0) G[k - n5] = Gnew[k - n5];
+    else G[k - n5] = fma(relax, Gnew[k - n5] - G[k - n5], G[k - n5]);
   }
 }
 
@@ -904,10 +905,11 @@ void launch_density_l1(const DevMesh &m, Scratch &s, const double *R, double *ou
   HGKS_PROF_END(K_NORM, st);
 }
 
-void launch_update(const DevMesh &m, double *Q, const double *dQ, double *G, const double *Gnew, int ncomp_g, cudaStream_t st) {
+void launch_update(const DevMesh &m, double *Q, const double *dQ, double *G, const double *Gnew, int ncomp_g,
+                   double relax, cudaStream_t st) {
   const int64_t n5 = 5 * (int64_t)m.N, ng = (int64_t)ncomp_g * m.N;
   HGKS_PROF_BEGIN(K_UPDATE, st);
-  k_update<<<vec_grid(n5 + ng), kBlock, 0, st>>>(n5, ng, Q, dQ, G, Gnew);
+  k_update<<<vec_grid(n5 + ng), kBlock, 0, st>>>(n5, ng, Q, dQ, G, Gnew, relax > 0.0 ? relax : 1.0);
   HGKS_PROF_END(K_UPDATE, st);
 }
 

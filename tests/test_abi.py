@@ -57,11 +57,11 @@ def test_params_struct_matches_header():
     body = src[src.index("typedef struct {\n  int32_t scheme;"):src.index("} hgks_params;")]
     ints = len(re.findall(r"int32_t ([a-z_]+);", body))
     assert ints == 10
-    assert C.sizeof(H.hgks_params) == 10 * 4 + 20 * 8
+    assert C.sizeof(H.hgks_params) == 10 * 4 + 21 * 8
     names = [f[0] for f in H.hgks_params._fields_]
-    assert names[-3:] == ["Mach", "Re", "aoa_deg"]
+    assert names[-4:] == ["Mach", "Re", "aoa_deg", "grad_relax"]
     p = H.hgks_default_params()
-    assert p.Mach == 0.0 and p.Re == 0.0 and p.aoa_deg == 0.0
+    assert p.Mach == 0.0 and p.Re == 0.0 and p.aoa_deg == 0.0 and p.grad_relax == 1.0
 
 
 def test_batch_entry_points_reject_bad_arguments_without_gpu():

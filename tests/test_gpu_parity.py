@@ -183,7 +183,8 @@ def test_local_dt_and_jacobian_parity(cuda):
 
 
 @pytest.mark.parametrize("name,kw", [("cavity8", dict(scheme=1, Pr=0.72)), ("sphere6x6", dict(scheme=0, krylov_dim=20)),
-                                     ("sphere6x6_visc", dict(scheme=1, Pr=0.72, cfl=20.0))])
+                                     ("sphere6x6_visc", dict(scheme=1, Pr=0.72, cfl=20.0)),
+                                     ("sphere6x6_visc", dict(scheme=1, Pr=0.72, cfl=20.0, grad_relax=0.5))])
 def test_gmres_step_parity(cuda, name, kw):
     import torch
     m, cond, om, hm = setup(name)
@@ -225,11 +226,13 @@ def test_gmres_step_parity_jacobi_sweeps(cuda, sweeps):
     assert rel32 <= MIXED_TOL["dQ_step"], rel32
 
 
-def test_gmres_steps_track_oracle(cuda):
-    """Five consecutive implicit steps on the viscous sphere stay within 1e-9 (relative L2)."""
+@pytest.mark.parametrize("relax", [1.0, 0.5])
+def test_gmres_steps_track_oracle(cuda, relax):
+    """Five consecutive implicit steps on the viscous sphere stay within 1e-9
+    (relative L2), with Algorithm 1's gradient update and with it under-relaxed."""
     import torch
     m, cond, om, hm = setup("sphere6x6_visc")
-    kw = dict(scheme=1, Pr=0.72, cfl=20.0)
+    kw = dict(scheme=1, Pr=0.72, cfl=20.0, grad_relax=relax)
     po = O.make_params(**{**cond, **kw}); ph = H.hgks_default_params(**{**cond, **kw})
     Q = I.state_from_conditions(m.n_tet, cond); G = np.zeros((m.n_tet, 15))
     Qd, Gd = hm.to_internal(Q), hm.to_internal(G)
