@@ -408,7 +408,7 @@ def run_precision(args, rank, world):
     local = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(local)
     cond = I.sphere_conditions(0.2535, Re=118.0)
-    kw = dict(scheme=1, Pr=0.72, cfl=20.0, krylov_dim=10, restarts=3, jacobi_sweeps=2)
+    kw = dict(scheme=1, Pr=0.72, cfl=20.0, krylov_dim=10, restarts=3, jacobi_sweeps=2, grad_relax=args.grad_relax)
     qinf = 0.5 * cond["rho_inf"] * cond["u_inf"][0] ** 2 * math.pi * 0.25
 
     def cd(hm, p, Q, G):
@@ -456,7 +456,8 @@ def run_precision(args, rank, world):
                 "warmup": 0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
                 "data": "synthetic",
                 "config": {"workload": "viscous sphere Re 118, Ma 0.2535, 6x24x24x48 (first layer 3e-2), HWENO, CFL 20, "
-                                       "GMRES(10)x3, Jacobi 2, from the free stream"}, **out}
+                                       "GMRES(10)x3, Jacobi 2, from the free stream",
+                           "grad_relax": args.grad_relax}, **out}
     print(json.dumps(res_line))
     return 0
 
@@ -606,6 +607,8 @@ def main():
     ap.add_argument("--batch-meshes", type=int, default=48)
     ap.add_argument("--batch-scheme", default="hweno", choices=["weno", "hweno"])
     ap.add_argument("--batch-precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--grad-relax", type=float, default=1.0,
+                    help="precision workload: relaxation of the compact gradient update (1: Algorithm 1's)")
     ap.add_argument("--batch-drop", type=float, default=0.0,
                     help="batch workload: also solve every mesh from its start to this drop (0: skip)")
     ap.add_argument("--batch-max-steps", type=int, default=500)
