@@ -354,14 +354,18 @@ def run_batch(args, rank, world):
             H.hgks_batch_set_state(b, k, Q0k, G0k)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        infos_d, hist_d, _ = H.hgks_batch_solve_steady(b, args.batch_drop, args.batch_max_steps, use_graph=True)
+        infos_d, hist_d, _ = H.hgks_batch_solve_steady(b, args.batch_drop, args.batch_max_steps, use_graph=True,
+                                                       raise_nonfinite=False)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t1
+        bad = [i for i in infos_d if not math.isfinite(i.res_final)]
         solve = {"drop": args.batch_drop, "max_steps": args.batch_max_steps, "seconds": wall,
                  "converged": sum(1 for i in infos_d if i.converged), "meshes": len(infos_d),
+                 "non_finite": len(bad),
                  "steps_converged": sorted(int(i.steps) for i in infos_d if i.converged),
                  "final_drop_not_converged": sorted(float(i.res_final / i.res_ref) for i in infos_d
-                                                   if not i.converged and i.res_ref > 0)}
+                                                   if not i.converged and i.res_ref > 0
+                                                   and math.isfinite(i.res_final))}
     if rank != 0:
         return 0
     rate = lambda ms, steps: n_cells * steps / (ms / 1000.0) / 1e6

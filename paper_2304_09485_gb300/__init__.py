@@ -375,13 +375,16 @@ def hgks_batch_gmres_step(batch, use_graph=True, stream=None):
     return list(info)
 
 
-def hgks_batch_solve_steady(batch, drop_tol=1e-8, max_steps=1000, use_graph=True, stream=None):
-    """(infos, hist [n, max_steps+1], all_converged) of Algorithm 1 run on every mesh of the batch."""
+def hgks_batch_solve_steady(batch, drop_tol=1e-8, max_steps=1000, use_graph=True, stream=None, raise_nonfinite=True):
+    """(infos, hist [n, max_steps+1], all_converged) of Algorithm 1 run on every mesh of the batch.
+    With raise_nonfinite=False a mesh whose residual went non-finite does not raise: its
+    record shows it (res_final not finite) and all_converged is False."""
     n = len(batch)
     hist = np.zeros((n, max_steps + 1))
     info = (hgks_solve_info * n)()
+    allow = (HGKS_ERR_NOT_CONVERGED,) if raise_nonfinite else (HGKS_ERR_NOT_CONVERGED, HGKS_ERR_NONPHYSICAL)
     st = _check(lib().hgks_batch_solve_steady(batch.handle, drop_tol, max_steps, 1 if use_graph else 0, _ptr(hist),
-                                              info, _stream(stream)), allow=(HGKS_ERR_NOT_CONVERGED,))
+                                              info, _stream(stream)), allow=allow)
     return list(info), hist, st == HGKS_OK
 
 
