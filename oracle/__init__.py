@@ -87,14 +87,14 @@ def lib():
         path = os.environ.get(PLANTED_ENV) or build()
         L = C.CDLL(path)
         vp, i64, i32, dp = C.c_void_p, C.c_int64, C.c_int32, C.POINTER(C.c_double)
-        L.orc_mesh_create.restype = vp
-        L.orc_mesh_create.argtypes = [dp, i64, C.POINTER(C.c_int64), i64, C.POINTER(C.c_int64),
+        L.orc_mesh_create_cells.restype = vp
+        L.orc_mesh_create_cells.argtypes = [dp, i64, C.POINTER(C.c_int64), C.c_int32, i64, C.POINTER(C.c_int64),
                                       C.POINTER(C.c_int32), i64, dp, i32, C.c_char_p, C.c_int]
         L.orc_mesh_destroy.argtypes = [vp]
         for name in ["orc_residual", "orc_residual_dt", "orc_apply_fd", "orc_wall_force", "orc_local_dt", "orc_jacobian",
                      "orc_precondition", "orc_gmres",
                      "orc_gmres_step", "orc_solve_steady", "orc_recon_side", "orc_fit_cell", "orc_slope",
-                     "orc_lu_solve", "orc_inverse"]:
+                     "orc_lu_solve", "orc_inverse", "orc_stencil"]:
             getattr(L, name).restype = C.c_int
         L.orc_set_threads.restype = C.c_int
         L.orc_set_threads.argtypes = [C.c_int]
@@ -115,35 +115,39 @@ def _pi(a):
 # mesh struct field offsets are read through a mirror of the C struct
 class _MeshC(C.Structure):
     _fields_ = [("nv", C.c_int64), ("nc", C.c_int64), ("nf", C.c_int64),
-                ("xyz", C.POINTER(C.c_double)), ("tet", C.POINTER(C.c_int64)),
+                ("xyz", C.POINTER(C.c_double)), ("cv", C.POINTER(C.c_int64)),
                 ("vol", C.POINTER(C.c_double)), ("cen", C.POINTER(C.c_double)), ("h", C.POINTER(C.c_double)),
                 ("cface", C.POINTER(C.c_int64)), ("cnb", C.POINTER(C.c_int64)), ("cshift", C.POINTER(C.c_double)),
                 ("cside", C.POINTER(C.c_int32)), ("fl", C.POINTER(C.c_int64)), ("fr", C.POINTER(C.c_int64)),
                 ("flp", C.POINTER(C.c_int32)), ("frp", C.POINTER(C.c_int32)), ("ftag", C.POINTER(C.c_int32)),
                 ("farea", C.POINTER(C.c_double)), ("fnrm", C.POINTER(C.c_double)), ("fgp", C.POINTER(C.c_double)),
-                ("fshift", C.POINTER(C.c_double)), ("fcen", C.POINTER(C.c_double)), ("fit", C.c_void_p)]
+                ("fshift", C.POINTER(C.c_double)), ("fcen", C.POINTER(C.c_double)), ("fit", C.c_void_p),
+                ("nvc", C.c_int32), ("nfc", C.c_int32), ("ngp", C.c_int32), ("pad", C.c_int32),
+                ("fgw", C.POINTER(C.c_double))]
 
 
 class OracleMesh:
-    """An oracle mesh built from an inputs.Mesh (caller order)."""
+    """An oracle mesh built from an inputs.Mesh or inputs.HexMesh (caller order)."""
 
     def __init__(self, mesh):
         L = lib()
         self.mesh = mesh
         xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
-        tet = np.ascontiguousarray(mesh.tet4, dtype=np.int64)
-        bf = np.ascontiguousarray(mesh.bface3, dtype=np.int64).reshape(-1, 3)
+        cells = np.ascontiguousarray(mesh.cells, dtype=np.int64)
+        nvc = cells.shape[1]
+        bf = np.ascontiguousarray(mesh.bface4 if nvc == 8 else mesh.bface3, dtype=np.int64).reshape(-1, 4 if nvc == 8 else 3)
         bt = np.ascontiguousarray(mesh.btag, dtype=np.int32)
         ps = mesh.periodic_shift
         psa = np.ascontiguousarray(ps if ps is not None else np.zeros((0, 3)), dtype=np.float64)
         err = C.create_string_buffer(256)
-        self.h = L.orc_mesh_create(_p(xyz), xyz.shape[0], _pi(tet), tet.shape[0], _pi(bf),
-                                   bt.ctypes.data_as(C.POINTER(C.c_int32)), bf.shape[0], _p(psa),
-                                   psa.shape[0], err, 256)
+        self.h = L.orc_mesh_create_cells(_p(xyz), xyz.shape[0], _pi(cells), nvc, cells.shape[0], _pi(bf),
+                                         bt.ctypes.data_as(C.POINTER(C.c_int32)), bf.shape[0], _p(psa),
+                                         psa.shape[0], err, 256)
         if not self.h:
             raise ValueError("oracle mesh: " + err.value.decode())
         self.s = C.cast(self.h, C.POINTER(_MeshC)).contents
         self.nc, self.nf = int(self.s.nc), int(self.s.nf)
+        self.nfc, self.ngp = int(self.s.nfc), int(self.s.ngp)
 
     def __del__(self):
         if getattr(self, "h", None):
@@ -165,7 +169,7 @@ class OracleMesh:
 
     @property
     def neighbours(self):
-        return self.arr("cnb", (self.nc, 4), np.int64)
+        return self.arr("cnb", (self.nc, self.nfc), np.int64)
 
     # -- residual ---------------------------------------------------------
     def residual(self, params, Q, G=None, cells=None):
@@ -193,7 +197,7 @@ class OracleMesh:
             dt = self.local_dt(params, Q)
         dt = np.ascontiguousarray(dt, dtype=np.float64)
         diag = np.zeros((self.nc, 5, 5))
-        off = np.zeros((self.nc, 4, 5, 5))
+        off = np.zeros((self.nc, self.nfc, 5, 5))
         lib().orc_jacobian(C.c_void_p(self.h), C.byref(params), _p(Q), _p(dt), _p(diag), _p(off))
         return diag, off
 
@@ -276,22 +280,41 @@ class OracleMesh:
         return Q, G, hist[: steps.value + 1], rc == 0
 
     def recon_side(self, params, Q, G, cell, slot):
-        """Values/gradients at the 3 Gauss points of face `slot` of `cell`.
+        """Values/gradients at the ngp Gauss points of face `slot` of `cell`.
 
-        Returns (Wloc [3,5], dWloc [3,3,5] along (n,t1,t2), Wglob [3,5], gradglob [3,5,3])."""
+        Returns (Wloc [ngp,5], dWloc [ngp,3,5] along (n,t1,t2), Wglob [ngp,5], gradglob [ngp,5,3])."""
         Q = np.ascontiguousarray(Q, dtype=np.float64)
         Ga = np.ascontiguousarray(G, dtype=np.float64) if G is not None else None
-        Wl = np.zeros((3, 5)); dWl = np.zeros((3, 3, 5)); Wg = np.zeros((3, 5)); gg = np.zeros((3, 5, 3))
+        g = self.ngp
+        Wl = np.zeros((g, 5)); dWl = np.zeros((g, 3, 5)); Wg = np.zeros((g, 5)); gg = np.zeros((g, 5, 3))
         rc = lib().orc_recon_side(C.c_void_p(self.h), C.byref(params), _p(Q), _p(Ga) if Ga is not None else None,
                                   C.c_int64(cell), C.c_int(slot), _p(Wl), _p(dWl), _p(Wg), _p(gg))
         if rc:
             raise RuntimeError("orc_recon_side failed")
         return Wl, dWl, Wg, gg
 
+    def stencil(self, cell, which=-1):
+        """(cells, valid) of the non-compact big stencil (which = -1) or of
+        sub-stencil `which` of `cell`."""
+        out = np.zeros(64, dtype=np.int64)
+        v = C.c_int(0)
+        n = lib().orc_stencil(C.c_void_p(self.h), C.c_int64(cell), int(which), _pi(out), C.byref(v))
+        if n < 0:
+            raise RuntimeError("orc_stencil failed")
+        return out[:n].copy(), bool(v.value)
+
+    def face_geometry(self):
+        """Per face: area, unit normal (left to right), Gauss points [ngp, 3]
+        (left cell's frame) and Gauss weights [ngp]; left/right cells."""
+        return dict(area=self.arr("farea", (self.nf,)), normal=self.arr("fnrm", (self.nf, 3)),
+                    gp=self.arr("fgp", (self.nf, self.ngp, 3)), gw=self.arr("fgw", (self.nf, self.ngp)),
+                    left=self.arr("fl", (self.nf,), np.int64), right=self.arr("fr", (self.nf,), np.int64),
+                    shift=self.arr("fshift", (self.nf, 3)))
+
     def face_gauss_points(self, cell, slot):
-        f = int(self.arr("cface", (self.nc, 4), np.int64)[cell, slot])
-        side = int(self.arr("cside", (self.nc, 4), np.int32)[cell, slot])
-        gp = self.arr("fgp", (self.nf, 3, 3))[f]
+        f = int(self.arr("cface", (self.nc, self.nfc), np.int64)[cell, slot])
+        side = int(self.arr("cside", (self.nc, self.nfc), np.int32)[cell, slot])
+        gp = self.arr("fgp", (self.nf, self.ngp, 3))[f]
         if side == 1:
             gp = gp - self.arr("fshift", (self.nf, 3))[f][None, :]
         return gp

@@ -15,13 +15,18 @@
  *
  * Data layout is the natural one for a reader: cell arrays are [cell][5] in the
  * caller's cell order, gradients [cell][5][3] (component, then direction).
+ * Cells are tetrahedra or hexahedra (Sec. 3.1: four or six faces).
  */
 #ifndef HGKS_ORACLE_H
 #define HGKS_ORACLE_H
 #include <stdint.h>
 
-#define ORC_MAXSTEN 16   /* non-compact big stencil, excluding the target cell */
+#define ORC_MAXF 6       /* faces of a cell: 4 (tetrahedron) or 6 (hexahedron) */
+#define ORC_MAXG 4       /* Gauss points of a face: 3 (triangle) or 2 x 2 (quadrilateral) */
+#define ORC_MAXSTEN 24   /* non-compact big stencil, excluding the target cell */
 #define ORC_MAXSUB 8     /* cells of one sub-stencil, excluding the target cell */
+#define ORC_NSUB 8       /* sub-stencils: 4 (tetrahedron) or 8 (hexahedron), Sec. 3.1 */
+#define ORC_HCOLS (ORC_MAXF + 3 * (1 + ORC_MAXF))   /* data columns of the compact fit */
 
 typedef struct {
   int32_t scheme;        /* 0: non-compact WENO, 1: compact HWENO           */
@@ -46,41 +51,57 @@ typedef struct {
   /* non-compact (WENO) */
   int n_big;                    orc_sref big[ORC_MAXSTEN];
   double X0[9][ORC_MAXSTEN];    /* a_d = sum_k X0[d][k] (Q_k - Q_0)           */
-  int n_sub[4];                 orc_sref sub[4][ORC_MAXSUB];
-  double Xm[4][3][ORC_MAXSUB];  /* b_j^m = sum_k Xm[m][j][k] (Q_k - Q_0)      */
-  int sub_valid[4];
-  /* compact (HWENO): data = (Q_k - Q_0 for face neighbours k, then gradients) */
-  int n_nb;                     orc_sref nb[4]; int nb_slot[4];
-  double H0[9][4 + 15];         /* a_d = sum H0[d][col] data[col]              */
-  double Hm[4][3][1 + 6];       /* b^m from (Q_m - Q_0, G_0 (3), G_m (3))      */
-  int hsub_has_nb[4];
+  int n_sub[ORC_NSUB];          orc_sref sub[ORC_NSUB][ORC_MAXSUB];
+  double Xm[ORC_NSUB][3][ORC_MAXSUB];  /* b_j^m = sum_k Xm[m][j][k] (Q_k - Q_0) */
+  int sub_valid[ORC_NSUB];
+  /* compact (HWENO): data = (Q_k - Q_0 for the face neighbours k, in face order,
+     then the gradients of the target and of those neighbours); columns
+     [0, nfc) hold the differences, nfc + 3 k + j gradient j of entry k (0 = target) */
+  int n_nb;                     orc_sref nb[ORC_MAXF]; int nb_slot[ORC_MAXF];
+  double H0[9][ORC_HCOLS];      /* a_d = sum H0[d][col] data[col]              */
+  double Hm[ORC_MAXF][3][1 + 6];/* b^m from (Q_m - Q_0, G_0 (3), G_m (3))      */
+  int hsub_has_nb[ORC_MAXF];
   int ready_weno, ready_hweno;
 } orc_fit;
 
+/* Cells are tetrahedra (nvc 4, nfc 4 faces, ngp 3 Gauss points a face) or
+ * hexahedra (nvc 8, nfc 6, ngp 4); every cell array is [nc][nfc]. */
 typedef struct {
   int64_t nv, nc, nf;
   double *xyz;                 /* [nv][3] */
-  int64_t *tet;                /* [nc][4] */
-  double *vol, *cen, *h;       /* [nc], [nc][3], [nc] */
-  int64_t *cface;              /* [nc][4] face across local face p (opposite vertex p) */
-  int64_t *cnb;                /* [nc][4] neighbour cell, -1 on a boundary */
-  double *cshift;              /* [nc][4][3] add to the neighbour's coordinates to bring it next to this cell */
-  int32_t *cside;              /* [nc][4] 0: this cell is the face's left cell, 1: right */
+  int64_t *cv;                 /* [nc][nvc] cell vertices */
+  double *vol, *cen, *h;       /* [nc], [nc][3] volume centroid, [nc] */
+  int64_t *cface;              /* [nc][nfc] face across local face p */
+  int64_t *cnb;                /* [nc][nfc] neighbour cell, -1 on a boundary */
+  double *cshift;              /* [nc][nfc][3] add to the neighbour's coordinates to bring it next to this cell */
+  int32_t *cside;              /* [nc][nfc] 0: this cell is the face's left cell, 1: right */
   int64_t *fl, *fr;            /* [nf] left/right cell (fr = -1 on a boundary) */
   int32_t *flp, *frp, *ftag;   /* local face index in left/right; boundary tag (0 interior) */
   double *farea, *fnrm;        /* [nf], [nf][3] unit normal from left to right */
-  double *fgp;                 /* [nf][3][3] Gauss points, left cell's frame */
+  double *fgp;                 /* [nf][ngp][3] Gauss points, left cell's frame */
   double *fshift;              /* [nf][3] x(left frame) = x(right frame) + shift */
-  double *fcen;                /* [nf][3] face centroid, left frame */
+  double *fcen;                /* [nf][3] mean of the face's vertices, left frame */
   orc_fit *fit;                /* [nc], filled on demand */
+  int32_t nvc, nfc, ngp, pad;
+  double *fgw;                 /* [nf][ngp] Gauss weights of the face (sum 1) */
 } orc_mesh;
 
 /* ---- mesh (orc_mesh.c) ---- */
 orc_mesh *orc_mesh_create(const double *xyz, int64_t nv, const int64_t *tet, int64_t nc,
                           const int64_t *bface, const int32_t *btag, int64_t nb,
                           const double *pshift, int32_t npshift, char *err, int errlen);
+/* cells of nvc = 4 (tetrahedra) or 8 (hexahedra) vertices; boundary faces of
+ * nvc == 4 ? 3 : 4 vertices (quadrilaterals in cyclic order) */
+orc_mesh *orc_mesh_create_cells(const double *xyz, int64_t nv, const int64_t *cells, int32_t nvc, int64_t nc,
+                                const int64_t *bface, const int32_t *btag, int64_t nb,
+                                const double *pshift, int32_t npshift, char *err, int errlen);
+/* quadrature of cell k exact for its degree-2 integrands: points (global frame)
+ * and weights summing to 1; returns the number of points (<= 64) */
+int orc_cell_quad(const orc_mesh *m, int64_t k, double (*xq)[3], double *wq);
 void orc_mesh_destroy(orc_mesh *m);
 int orc_fit_cell(orc_mesh *m, int64_t i, int scheme);   /* 0 ok, <0 error */
+/* the non-compact stencils of cell i (which = -1: big stencil, 0..7: sub-stencil) */
+int orc_stencil(orc_mesh *m, int64_t i, int which, int64_t *out, int *valid);
 
 /* ---- small dense linear algebra (orc_linalg.c) ---- */
 int orc_lu_solve(int n, const double *A, const double *b, double *x);  /* A row-major n x n */
@@ -103,8 +124,8 @@ void orc_primitive(const double *Q, double gamma, double *prim /*rho,U,V,W,lambd
 void orc_face_frame(const double *n, double *T /*3x3 rows*/);
 void orc_char_eigen(const double *Qloc, double gamma, double *R, double *L);
 int orc_recon_side(orc_mesh *m, const orc_params *p, const double *Q, const double *G,
-                   int64_t cell, int slot, double *Wloc /*[3][5]*/, double *dWloc /*[3][3][5]*/,
-                   double *Wglob /*[3][5] or NULL*/, double *gradglob /*[3][5][3] or NULL*/);
+                   int64_t cell, int slot, double *Wloc /*[ngp][5]*/, double *dWloc /*[ngp][3][5]*/,
+                   double *Wglob /*[ngp][5] or NULL*/, double *gradglob /*[ngp][5][3] or NULL*/);
 
 /* ---- residual and implicit solver (orc_solver.c) ---- */
 void orc_euler_jacobian(const double *Q, const double *n, double gamma, double *J);
@@ -120,7 +141,7 @@ int orc_wall_force(orc_mesh *m, const orc_params *p, const double *Q, const doub
 int orc_apply_fd(orc_mesh *m, const orc_params *p, const double *Q, const double *G, const double *dt,
                  const double *LQ, const double *x, double *y, double *sigma_out);
 int orc_jacobian(orc_mesh *m, const orc_params *p, const double *Q, const double *dt,
-                 double *diag /*[nc][25]*/, double *off /*[nc][4][25]*/);
+                 double *diag /*[nc][25]*/, double *off /*[nc][nfc][25]*/);
 void orc_apply_A(const orc_mesh *m, const double *diag, const double *off, const double *x, double *y);
 int orc_precondition(const orc_mesh *m, const double *diag, const double *off, int sweeps,
                      const double *b, double *x);

@@ -11,12 +11,12 @@
  * 4. Smoothness indicators and the nonlinear weights of Eq. (weno), per
  *    characteristic component.
  * 5. Values and gradients at the Gauss points, projected back with R*.
- * Cell averages over the target cell use the degree-2 tetrahedron rule. */
+ * Cell averages over the target cell use the cell's quadrature (orc_cell_quad).
+ * Sub-stencils: 4 (tetrahedron) or 8 (hexahedron) non-compact ones, one per
+ * face for the compact scheme. */
 #include <math.h>
 #include <string.h>
 #include "orc.h"
-
-static const double QA = 0.5854101966249685, QB = 0.1381966011250105;
 
 void orc_face_frame(const double *n, double *T) {
   const double wgt[3] = {1.0, 1.001, 1.002};
@@ -60,10 +60,12 @@ int orc_recon_side(orc_mesh *m, const orc_params *p, const double *Q, const doub
   const int64_t i = cell;
   if (orc_fit_cell(m, i, p->scheme)) return -1;
   const orc_fit *F = m->fit + i;
-  const int64_t f = m->cface[4 * i + slot];
+  const int nfc = m->nfc, ngp = m->ngp;
+  const int64_t f = m->cface[nfc * i + slot];
+  const int nsub = p->scheme == 0 ? (m->nvc == 8 ? 8 : 4) : nfc;
   /* 1. coefficients in conservative variables, per component: a[d][c], b[mm][j][c] */
-  double a[9][5], b[4][3][5];
-  int valid[4];
+  double a[9][5], b[ORC_NSUB][3][5];
+  int valid[ORC_NSUB];
   memset(a, 0, sizeof(a)); memset(b, 0, sizeof(b));
   if (p->scheme == 0) {
     for (int c = 0; c < 5; c++) {
@@ -72,7 +74,7 @@ int orc_recon_side(orc_mesh *m, const orc_params *p, const double *Q, const doub
         for (int r = 0; r < F->n_big; r++) s += F->X0[d][r] * (Q[5 * F->big[r].cell + c] - Q[5 * i + c]);
         a[d][c] = s;
       }
-      for (int mm = 0; mm < 4; mm++) {
+      for (int mm = 0; mm < nsub; mm++) {
         if (!F->sub_valid[mm]) continue;
         for (int j = 0; j < 3; j++) {
           double s = 0.0;
@@ -81,27 +83,27 @@ int orc_recon_side(orc_mesh *m, const orc_params *p, const double *Q, const doub
         }
       }
     }
-    for (int mm = 0; mm < 4; mm++) valid[mm] = F->sub_valid[mm];
+    for (int mm = 0; mm < nsub; mm++) valid[mm] = F->sub_valid[mm];
   } else {
     for (int c = 0; c < 5; c++) {
-      double data[19];
+      double data[ORC_HCOLS];
       memset(data, 0, sizeof(data));
       for (int r = 0; r < F->n_nb; r++) data[r] = Q[5 * F->nb[r].cell + c] - Q[5 * i + c];
       for (int k = 0; k <= F->n_nb; k++) {
         int64_t ck = k == 0 ? i : F->nb[k - 1].cell;
-        for (int j = 0; j < 3; j++) data[4 + 3 * k + j] = G[15 * ck + 3 * c + j];
+        for (int j = 0; j < 3; j++) data[nfc + 3 * k + j] = G[15 * ck + 3 * c + j];
       }
-      for (int d = 0; d < 9; d++) { double s = 0.0; for (int col = 0; col < 19; col++) s += F->H0[d][col] * data[col]; a[d][c] = s; }
-      for (int mm = 0; mm < 4; mm++) {
+      for (int d = 0; d < 9; d++) { double s = 0.0; for (int col = 0; col < ORC_HCOLS; col++) s += F->H0[d][col] * data[col]; a[d][c] = s; }
+      for (int mm = 0; mm < nfc; mm++) {
         double dm[7] = {0};
-        int64_t jm = m->cnb[4 * i + mm];
+        int64_t jm = m->cnb[nfc * i + mm];
         if (jm >= 0) dm[0] = Q[5 * jm + c] - Q[5 * i + c];
         for (int j = 0; j < 3; j++) dm[1 + j] = G[15 * i + 3 * c + j];
         if (jm >= 0) for (int j = 0; j < 3; j++) dm[4 + j] = G[15 * jm + 3 * c + j];
         for (int j = 0; j < 3; j++) { double s = 0.0; for (int col = 0; col < 7; col++) s += F->Hm[mm][j][col] * dm[col]; b[mm][j][c] = s; }
       }
     }
-    for (int mm = 0; mm < 4; mm++) valid[mm] = 1;
+    for (int mm = 0; mm < nfc; mm++) valid[mm] = 1;
   }
   /* 2. face frame, 3. projection */
   double T3[9];
@@ -130,66 +132,63 @@ int orc_recon_side(orc_mesh *m, const orc_params *p, const double *Q, const doub
   } else {
     for (int k = 0; k < 25; k++) Pm[k] = Rb[k] = (k % 6 == 0) ? 1.0 : 0.0;
   }
-  double q0[5], ac[9][5], bc[4][3][5];
+  double q0[5], ac[9][5], bc[ORC_NSUB][3][5];
   for (int c = 0; c < 5; c++) {
     double s = 0.0; for (int k = 0; k < 5; k++) s += Pm[c * 5 + k] * Q[5 * i + k]; q0[c] = s;
     for (int d = 0; d < 9; d++) { s = 0.0; for (int k = 0; k < 5; k++) s += Pm[c * 5 + k] * a[d][k]; ac[d][c] = s; }
-    for (int mm = 0; mm < 4; mm++)
+    for (int mm = 0; mm < nsub; mm++)
       for (int j = 0; j < 3; j++) { s = 0.0; for (int k = 0; k < 5; k++) s += Pm[c * 5 + k] * b[mm][j][k]; bc[mm][j][c] = s; }
   }
   /* cell averages of the monomials over the target cell (basis offsets of Eq. (polys)) */
-  double xq[4][3], avg[9];
-  for (int q = 0; q < 4; q++)
-    for (int d = 0; d < 3; d++) {
-      double x = 0.0;
-      for (int v = 0; v < 4; v++) x += (v == q ? QA : QB) * m->xyz[3 * m->tet[4 * i + v] + d];
-      xq[q][d] = (x - m->cen[3 * i + d]) / m->h[i];
-    }
+  double xq[64][3], wq[64], avg[9];
+  const int nq = orc_cell_quad(m, i, xq, wq);
+  for (int q = 0; q < nq; q++)
+    for (int d = 0; d < 3; d++) xq[q][d] = (xq[q][d] - m->cen[3 * i + d]) / m->h[i];
   for (int d = 0; d < 9; d++) avg[d] = 0.0;
-  for (int q = 0; q < 4; q++) {
+  for (int q = 0; q < nq; q++) {
     double x = xq[q][0], y = xq[q][1], z = xq[q][2];
     double mo[9] = {x, y, z, x * x, y * y, z * z, x * y, x * z, y * z};
-    for (int d = 0; d < 9; d++) avg[d] += 0.25 * mo[d];
+    for (int d = 0; d < 9; d++) avg[d] += wq[q] * mo[d];
   }
   /* 4. smoothness indicators (scaled frame: the |Omega|^(2|l|/3 - 1) factors cancel the scaling) */
-  int M = 0; for (int mm = 0; mm < 4; mm++) M += valid[mm];
+  int M = 0; for (int mm = 0; mm < nsub; mm++) M += valid[mm];
   double gam_m = p->lin_weight, gam0 = 1.0 - gam_m * M;
-  double wbar[5][5];   /* [component][0..4], 0 = P0 */
+  double wbar[5][1 + ORC_NSUB];   /* [component][0..nsub], 0 = P0 */
   for (int c = 0; c < 5; c++) {
-    double beta[5];
+    double beta[1 + ORC_NSUB];
     /* beta_0: first derivatives (linear functions) averaged over the cell, second derivatives constant */
     double s = 0.0;
-    for (int q = 0; q < 4; q++) {
+    for (int q = 0; q < nq; q++) {
       double x = xq[q][0], y = xq[q][1], z = xq[q][2];
       double dx = ac[0][c] + 2 * ac[3][c] * x + ac[6][c] * y + ac[7][c] * z;
       double dy = ac[1][c] + 2 * ac[4][c] * y + ac[6][c] * x + ac[8][c] * z;
       double dz = ac[2][c] + 2 * ac[5][c] * z + ac[7][c] * x + ac[8][c] * y;
-      s += 0.25 * (dx * dx + dy * dy + dz * dz);
+      s += wq[q] * (dx * dx + dy * dy + dz * dz);
     }
     double hxx = 2 * ac[3][c], hyy = 2 * ac[4][c], hzz = 2 * ac[5][c];
     s += hxx * hxx + hyy * hyy + hzz * hzz + ac[6][c] * ac[6][c] + ac[7][c] * ac[7][c] + ac[8][c] * ac[8][c];
     beta[0] = s;
-    for (int mm = 0; mm < 4; mm++)
+    for (int mm = 0; mm < nsub; mm++)
       beta[1 + mm] = bc[mm][0][c] * bc[mm][0][c] + bc[mm][1][c] * bc[mm][1][c] + bc[mm][2][c] * bc[mm][2][c];
-    double om[5];
+    double om[1 + ORC_NSUB];
     if (p->weights == 1 || M == 0) {
       wbar[c][0] = M == 0 ? 1.0 : gam0;
-      for (int mm = 0; mm < 4; mm++) wbar[c][1 + mm] = valid[mm] ? gam_m : 0.0;
+      for (int mm = 0; mm < nsub; mm++) wbar[c][1 + mm] = valid[mm] ? gam_m : 0.0;
     } else {
       double tz = 0.0;
-      for (int mm = 0; mm < 4; mm++) if (valid[mm]) tz += fabs(beta[0] - beta[1 + mm]) / M;
+      for (int mm = 0; mm < nsub; mm++) if (valid[mm]) tz += fabs(beta[0] - beta[1 + mm]) / M;
       om[0] = gam0 * (1.0 + tz / (beta[0] + p->weno_eps));
       double sum = om[0];
-      for (int mm = 0; mm < 4; mm++) { om[1 + mm] = valid[mm] ? gam_m * (1.0 + tz / (beta[1 + mm] + p->weno_eps)) : 0.0; sum += om[1 + mm]; }
-      for (int k = 0; k < 5; k++) wbar[c][k] = om[k] / sum;
+      for (int mm = 0; mm < nsub; mm++) { om[1 + mm] = valid[mm] ? gam_m * (1.0 + tz / (beta[1 + mm] + p->weno_eps)) : 0.0; sum += om[1 + mm]; }
+      for (int k = 0; k <= nsub; k++) wbar[c][k] = om[k] / sum;
     }
   }
   double g0eff = M == 0 ? 1.0 : gam0;
   /* 5. Gauss points */
-  const double *sh = m->cside[4 * i + slot] == 1 ? m->fshift + 3 * f : NULL;
-  for (int gp = 0; gp < 3; gp++) {
+  const double *sh = m->cside[nfc * i + slot] == 1 ? m->fshift + 3 * f : NULL;
+  for (int gp = 0; gp < ngp; gp++) {
     double x[3];
-    for (int d = 0; d < 3; d++) x[d] = (m->fgp[9 * f + 3 * gp + d] - (sh ? sh[d] : 0.0) - m->cen[3 * i + d]) / m->h[i];
+    for (int d = 0; d < 3; d++) x[d] = (m->fgp[3 * ngp * f + 3 * gp + d] - (sh ? sh[d] : 0.0) - m->cen[3 * i + d]) / m->h[i];
     double pd[9] = {x[0], x[1], x[2], x[0] * x[0], x[1] * x[1], x[2] * x[2], x[0] * x[1], x[0] * x[2], x[1] * x[2]};
     for (int d = 0; d < 9; d++) pd[d] -= avg[d];
     double dpd[3][9];
@@ -200,22 +199,22 @@ int orc_recon_side(orc_mesh *m, const orc_params *p, const double *Q, const doub
     dpd[0][6] = x[1]; dpd[0][7] = x[2]; dpd[1][6] = x[0]; dpd[1][8] = x[2]; dpd[2][7] = x[0]; dpd[2][8] = x[1];
     double qv[5], qg[3][5];
     for (int c = 0; c < 5; c++) {
-      double P0 = q0[c], dP0[3] = {0, 0, 0}, Pm_[4], dPm[4][3];
+      double P0 = q0[c], dP0[3] = {0, 0, 0}, Pm_[ORC_NSUB], dPm[ORC_NSUB][3];
       for (int d = 0; d < 9; d++) { P0 += ac[d][c] * pd[d]; for (int j = 0; j < 3; j++) dP0[j] += ac[d][c] * dpd[j][d]; }
-      for (int mm = 0; mm < 4; mm++) {
+      for (int mm = 0; mm < nsub; mm++) {
         Pm_[mm] = q0[c];
         for (int j = 0; j < 3; j++) { Pm_[mm] += bc[mm][j][c] * pd[j]; dPm[mm][j] = bc[mm][j][c]; }
       }
       /* Eq. (weno) */
       double val = P0 / g0eff, grad[3] = {dP0[0] / g0eff, dP0[1] / g0eff, dP0[2] / g0eff};
-      for (int mm = 0; mm < 4; mm++) {
+      for (int mm = 0; mm < nsub; mm++) {
         if (!valid[mm]) continue;
         val -= gam_m / g0eff * Pm_[mm];
         for (int j = 0; j < 3; j++) grad[j] -= gam_m / g0eff * dPm[mm][j];
       }
       val *= wbar[c][0];
       for (int j = 0; j < 3; j++) grad[j] *= wbar[c][0];
-      for (int mm = 0; mm < 4; mm++) {
+      for (int mm = 0; mm < nsub; mm++) {
         if (!valid[mm]) continue;
         val += wbar[c][1 + mm] * Pm_[mm];
         for (int j = 0; j < 3; j++) grad[j] += wbar[c][1 + mm] * dPm[mm][j];

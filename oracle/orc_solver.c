@@ -1,8 +1,8 @@
 /* ORACLE (test infrastructure only): residual, local time step, approximate
  * Jacobian, Jacobi preconditioner, restarted GMRES and the steady loop.
  *
- * Residual: Eq. (finite) with the time-averaged flux of Sec. 4.1, 3-point Gauss
- * rule per face; compact scheme: cell-averaged gradients from the point values
+ * Residual: Eq. (finite) with the time-averaged flux of Sec. 4.1, the face's
+ * Gauss rule (3 points on a triangle, 2 x 2 on a quadrilateral); compact scheme: cell-averaged gradients from the point values
  * of Eq. (point) by Gauss's theorem, Eq. (derivative).
  * Implicit system: Eq. (A-system-2) with the Rusanov-type split Jacobians of
  * Eq. (deri-matrix); Jacobi preconditioner of Eq. (precond); Algorithm 1. */
@@ -19,8 +19,8 @@ static void rot5t3(const double *T, const double *in, double *out) {
 }
 
 static void outward(const orc_mesh *m, int64_t i, int p, double *n) {
-  int64_t f = m->cface[4 * i + p];
-  double s = m->cside[4 * i + p] == 0 ? 1.0 : -1.0;
+  int64_t f = m->cface[m->nfc * i + p];
+  double s = m->cside[m->nfc * i + p] == 0 ? 1.0 : -1.0;
   for (int d = 0; d < 3; d++) n[d] = s * m->fnrm[3 * f + d];
 }
 
@@ -31,9 +31,9 @@ int orc_local_dt(orc_mesh *m, const orc_params *p, const double *Q, double *dt) 
     double pres = pr[0] / (2.0 * pr[4]), a = sqrt(p->gamma * pres / pr[0]);
     double nu = p->viscous ? 2.0 * p->gamma * p->mu / (p->Pr * pr[0] * m->h[i]) : 0.0;
     double s = 0.0;
-    for (int q = 0; q < 4; q++) {
+    for (int q = 0; q < m->nfc; q++) {
       double n[3]; outward(m, i, q, n);
-      int64_t f = m->cface[4 * i + q];
+      int64_t f = m->cface[m->nfc * i + q];
       s += m->farea[f] * (fabs(pr[1] * n[0] + pr[2] * n[1] + pr[3] * n[2]) + a + nu);
     }
     dt[i] = p->cfl * m->vol[i] / s;
@@ -77,7 +77,7 @@ static int residual_core(orc_mesh *m, const orc_params *p, const double *Q, cons
   if (cells) {
     for (int64_t a = 0; a < ncells; a++) {
       int64_t i = cells[a];
-      for (int q = 0; q < 4; q++) fsel[m->cface[4 * i + q]] = 1;
+      for (int q = 0; q < m->nfc; q++) fsel[m->cface[m->nfc * i + q]] = 1;
     }
   } else memset(fsel, 1, nf);
   for (int64_t f = 0; f < nf; f++) if (fsel[f]) { csel[m->fl[f]] = 1; if (m->fr[f] >= 0) csel[m->fr[f]] = 1; }
@@ -93,20 +93,26 @@ static int residual_core(orc_mesh *m, const orc_params *p, const double *Q, cons
   for (int64_t f = 0; f < nf; f++) {
     if (!fsel[f]) continue;
     int64_t L = m->fl[f], Rr = m->fr[f];
-    double WL[15], dWL[45], WR[15], dWR[45], T3[9];
+    const int ngp = m->ngp;
+    double WL[5 * ORC_MAXG], dWL[15 * ORC_MAXG], WR[5 * ORC_MAXG], dWR[15 * ORC_MAXG], T3[9];
     orc_face_frame(m->fnrm + 3 * f, T3);
     err |= orc_recon_side(m, p, Q, G, L, m->flp[f], WL, dWL, NULL, NULL) != 0;
     if (Rr >= 0) err |= orc_recon_side(m, p, Q, G, Rr, m->frp[f], WR, dWR, NULL, NULL) != 0;
-    else for (int g = 0; g < 3; g++) orc_boundary_state(p, m->ftag[f], T3, WL + 5 * g, dWL + 15 * g, WR + 5 * g, dWR + 15 * g);
+    else for (int g = 0; g < ngp; g++) orc_boundary_state(p, m->ftag[f], T3, WL + 5 * g, dWL + 15 * g, WR + 5 * g, dWR + 15 * g);
     /* time step inside the flux: the local step at CFL = flux_cfl, single-valued per face */
     double dtf = p->flux_dt > 0 ? p->flux_dt : (Rr >= 0 ? fmin(dt[L], dt[Rr]) : dt[L]) * (p->flux_cfl / p->cfl);
-    for (int g = 0; g < 3; g++) {
+    for (int g = 0; g < ngp; g++) {
       double F[5], Qp[5], Fg[5], Qg[5];
       orc_gks_flux(p, WL + 5 * g, dWL + 15 * g, WR + 5 * g, dWR + 15 * g, dtf, F, Qp);
       rot5t3(T3, F, Fg); rot5t3(T3, Qp, Qg);
       /* walls (tags 1-4) are impermeable: their faces carry momentum and energy, no mass */
       if (Rr < 0 && m->ftag[f] >= 1 && m->ftag[f] <= 4) Fg[0] = 0.0;
-      for (int c = 0; c < 5; c++) { Ff[5 * f + c] += m->farea[f] * Fg[c] / 3.0; Pf[5 * f + c] += m->farea[f] * Qg[c] / 3.0; }
+      /* Gauss weights: 1/3 on a triangle, the area-element weights fgw on a quadrilateral */
+      if (ngp == 3) for (int c = 0; c < 5; c++) { Ff[5 * f + c] += m->farea[f] * Fg[c] / 3.0; Pf[5 * f + c] += m->farea[f] * Qg[c] / 3.0; }
+      else {
+        const double wS = m->farea[f] * m->fgw[ngp * f + g];
+        for (int c = 0; c < 5; c++) { Ff[5 * f + c] += wS * Fg[c]; Pf[5 * f + c] += wS * Qg[c]; }
+      }
     }
   }
   if (err) { free(fsel); free(csel); free(dt); free(Ff); free(Pf); return -1; }
@@ -158,10 +164,10 @@ int orc_jacobian(orc_mesh *m, const orc_params *p, const double *Q, const double
   for (int64_t i = 0; i < m->nc; i++) {
     double *D = diag + 25 * i;
     for (int k = 0; k < 25; k++) D[k] = (k % 6 == 0) ? m->vol[i] / dt[i] : 0.0;
-    for (int q = 0; q < 4; q++) {
+    for (int q = 0; q < m->nfc; q++) {
       double n[3], J[25], Qf[5], pf[5];
       outward(m, i, q, n);
-      int64_t f = m->cface[4 * i + q], j = m->cnb[4 * i + q];
+      int64_t f = m->cface[m->nfc * i + q], j = m->cnb[m->nfc * i + q];
       double S = m->farea[f];
       for (int c = 0; c < 5; c++) Qf[c] = j >= 0 ? 0.5 * (Q[5 * i + c] + Q[5 * j + c]) : Q[5 * i + c];
       orc_primitive(Qf, p->gamma, pf);
@@ -171,12 +177,12 @@ int orc_jacobian(orc_mesh *m, const orc_params *p, const double *Q, const double
         double df;
         if (j >= 0) {
           double s2 = 0.0;
-          for (int d = 0; d < 3; d++) { double t = m->cen[3 * i + d] - (m->cen[3 * j + d] + m->cshift[12 * i + 3 * q + d]); s2 += t * t; }
+          for (int d = 0; d < 3; d++) { double t = m->cen[3 * i + d] - (m->cen[3 * j + d] + m->cshift[3 * m->nfc * i + 3 * q + d]); s2 += t * t; }
           df = sqrt(s2);
         } else {
           double s = 0.0;
           double fc[3];
-          for (int d = 0; d < 3; d++) fc[d] = m->fcen[3 * f + d] - (m->cside[4 * i + q] == 1 ? m->fshift[3 * f + d] : 0.0);
+          for (int d = 0; d < 3; d++) fc[d] = m->fcen[3 * f + d] - (m->cside[m->nfc * i + q] == 1 ? m->fshift[3 * f + d] : 0.0);
           for (int d = 0; d < 3; d++) s += (fc[d] - m->cen[3 * i + d]) * n[d];
           df = 2.0 * fabs(s);
         }
@@ -184,7 +190,7 @@ int orc_jacobian(orc_mesh *m, const orc_params *p, const double *Q, const double
       }
       orc_euler_jacobian(Q + 5 * i, n, p->gamma, J);
       for (int k = 0; k < 25; k++) D[k] += 0.5 * (J[k] + (k % 6 == 0 ? lam : 0.0)) * S;
-      double *O = off + 100 * i + 25 * q;
+      double *O = off + 25 * m->nfc * i + 25 * q;
       if (j >= 0) {
         orc_euler_jacobian(Q + 5 * j, n, p->gamma, J);
         for (int k = 0; k < 25; k++) O[k] = 0.5 * (J[k] - (k % 6 == 0 ? lam : 0.0)) * S;
@@ -199,10 +205,10 @@ void orc_apply_A(const orc_mesh *m, const double *diag, const double *off, const
     for (int r = 0; r < 5; r++) {
       double s = 0.0;
       for (int c = 0; c < 5; c++) s += diag[25 * i + 5 * r + c] * x[5 * i + c];
-      for (int q = 0; q < 4; q++) {
-        int64_t j = m->cnb[4 * i + q];
+      for (int q = 0; q < m->nfc; q++) {
+        int64_t j = m->cnb[m->nfc * i + q];
         if (j < 0) continue;
-        for (int c = 0; c < 5; c++) s += off[100 * i + 25 * q + 5 * r + c] * x[5 * j + c];
+        for (int c = 0; c < 5; c++) s += off[25 * m->nfc * i + 25 * q + 5 * r + c] * x[5 * j + c];
       }
       y[5 * i + r] = s;
     }
@@ -222,10 +228,10 @@ int orc_precondition(const orc_mesh *m, const double *diag, const double *off, i
       double t[5];
       for (int r = 0; r < 5; r++) {
         double s = b[5 * i + r];
-        for (int q = 0; q < 4; q++) {
-          int64_t j = m->cnb[4 * i + q];
+        for (int q = 0; q < m->nfc; q++) {
+          int64_t j = m->cnb[m->nfc * i + q];
           if (j < 0) continue;
-          for (int c = 0; c < 5; c++) s -= off[100 * i + 25 * q + 5 * r + c] * prev[5 * j + c];
+          for (int c = 0; c < 5; c++) s -= off[25 * m->nfc * i + 25 * q + 5 * r + c] * prev[5 * j + c];
         }
         t[r] = s;
       }
@@ -355,7 +361,7 @@ int orc_gmres_step(orc_mesh *m, const orc_params *p, double *Q, double *G, doubl
   const int64_t nc = m->nc;
   double *dt = (double *)malloc(sizeof(double) * (nc + 1)), *R = (double *)malloc(sizeof(double) * 5 * (nc + 1));
   double *Gn = p->scheme == 1 ? (double *)malloc(sizeof(double) * 15 * (nc + 1)) : NULL;
-  double *diag = (double *)malloc(sizeof(double) * 25 * (nc + 1)), *off = (double *)malloc(sizeof(double) * 100 * (nc + 1));
+  double *diag = (double *)malloc(sizeof(double) * 25 * (nc + 1)), *off = (double *)malloc(sizeof(double) * 25 * m->nfc * (nc + 1));
   double *dQ = (double *)malloc(sizeof(double) * 5 * (nc + 1));
   int rc = orc_local_dt(m, p, Q, dt);
   if (!rc) rc = orc_residual(m, p, Q, G, R, Gn, NULL, 0);

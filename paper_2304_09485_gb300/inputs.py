@@ -1,9 +1,9 @@
-"""Seeded synthetic inputs: tetrahedral meshes and flow states.
+"""Seeded synthetic inputs: tetrahedral and hexahedral meshes and flow states.
 
 This module is shared by the CUDA path's tests/benchmark and by the oracle's
 tests. It holds no arithmetic of the method (no geometry of cells or faces, no
 reconstruction, no flux): it only lays vertices out, connects them into
-tetrahedra, tags boundary triangles and draws seeded states.
+tetrahedra or hexahedra, tags boundary faces and draws seeded states.
 
 Meshes stand in for the paper's workloads (Sec. 5.1 lid-driven cavity on
 tetrahedra split from hexahedra; Sec. 5.2 flow past a sphere). The paper's own
@@ -44,6 +44,39 @@ class Mesh:
     @property
     def n_tet(self) -> int:
         return int(self.tet4.shape[0])
+
+    @property
+    def cells(self) -> np.ndarray:
+        return self.tet4
+
+    @property
+    def n_cells(self) -> int:
+        return int(self.tet4.shape[0])
+
+
+@dataclass
+class HexMesh:
+    """A hexahedral mesh as plain arrays (caller order).
+
+    Vertices of a hexahedron in the usual order: 0-3 one quadrilateral in cyclic
+    order, 4-7 the opposite one with vertex 4 + a joined to vertex a; positive
+    orientation ((x1 - x0) x (x3 - x0)) . (x4 - x0) > 0. Boundary quadrilaterals
+    list their four vertices in cyclic order."""
+    xyz: np.ndarray            # [n_vert, 3] float64
+    hex8: np.ndarray           # [n_hex, 8] int64
+    bface4: np.ndarray         # [n_bface, 4] int64
+    btag: np.ndarray           # [n_bface] int32
+    periodic_shift: np.ndarray | None = None
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def cells(self) -> np.ndarray:
+        return self.hex8
+
+    @property
+    def n_cells(self) -> int:
+        return int(self.hex8.shape[0])
 
 
 def _kuhn_tets(idx):
@@ -177,6 +210,159 @@ def periodic_cube_mesh(n: int = 6, jitter: float = 0.1, seed: int = BASE_SEED + 
                 name=f"periodic{n}", meta=dict(n=n, jitter=jitter, seed=seed, length=length))
 
 
+# corner (a, b, c) in {0,1}^3 of the usual hexahedron vertex order
+_HEX_CORNER = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0],
+                        [0, 0, 1], [1, 0, 1], [1, 1, 1], [0, 1, 1]])
+
+
+def _hex_rotations() -> np.ndarray:
+    """[24, 8] vertex relabellings of a hexahedron by the 24 rotations of a cube.
+
+    Row r gives, for new local vertex a, the old local vertex at the corner the
+    rotation moves a to: every row keeps the hexahedron positively oriented."""
+    corner_id = {tuple(c): k for k, c in enumerate(_HEX_CORNER)}
+    rows = []
+    for perm in [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]:
+        for sg in np.ndindex(2, 2, 2):
+            R = np.zeros((3, 3))
+            for r in range(3):
+                R[r, perm[r]] = 1.0 if sg[r] == 0 else -1.0
+            if np.linalg.det(R) < 0:
+                continue
+            s = 2 * _HEX_CORNER - 1
+            t = (s @ R.T + 1) // 2
+            rows.append([corner_id[tuple(int(x) for x in v)] for v in t])
+    return np.array(rows, dtype=np.int64)
+
+
+def _hex_grid(n: int, vid, reorient: bool, rng) -> np.ndarray:
+    hi, hj, hk = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    hi, hj, hk = hi.ravel(), hj.ravel(), hk.ravel()
+    hx = np.stack([vid(hi + c[0], hj + c[1], hk + c[2]) for c in _HEX_CORNER], axis=1)
+    if reorient:
+        rot = _hex_rotations()[rng.integers(0, 24, size=hx.shape[0])]
+        hx = np.take_along_axis(hx, rot, axis=1)
+    return hx
+
+
+def hex_cavity_mesh(n: int = 6, jitter: float = 0.1, seed: int = BASE_SEED + 500,
+                    permute: bool = True, reorient: bool = True, lid_tag: int = BC_WALL_LID,
+                    wall_tag: int = BC_WALL_ISO) -> HexMesh:
+    """Unit cube of n^3 hexahedra (Sec. 3.1's hexahedral cells), lid y = 1.
+
+    Interior vertices are moved by U(-jitter h, +jitter h) per axis, so the faces
+    are non-planar quadrilaterals; with `reorient` each hexahedron's vertices are
+    relabelled by a random one of the 24 rotations of a cube (its local faces,
+    and so its sub-stencils, then point along random axes); the order of the
+    cells is randomly permuted."""
+    rng = np.random.default_rng(seed)
+    h = 1.0 / n
+    g = np.arange(n + 1)
+    I, J, K = np.meshgrid(g, g, g, indexing="ij")
+    lat = np.stack([I, J, K], axis=-1).reshape(-1, 3)
+    xyz = lat.astype(np.float64) * h
+    interior = np.all((lat > 0) & (lat < n), axis=1)
+    d = rng.uniform(-jitter * h, jitter * h, size=xyz.shape)
+    xyz[interior] += d[interior]
+
+    def vid(i, j, k):
+        return (i * (n + 1) + j) * (n + 1) + k
+
+    hx = _hex_grid(n, vid, reorient, rng)
+    if permute:
+        hx = hx[rng.permutation(hx.shape[0])]
+    a, b = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    a, b = a.ravel(), b.ravel()
+    bf, bt = [], []
+    for axis in range(3):
+        o1, o2 = [x for x in range(3) if x != axis]
+        for side in (0, n):
+            def V(u, v):
+                c = [None, None, None]
+                c[axis] = np.full_like(u, side)
+                c[o1] = u
+                c[o2] = v
+                return vid(c[0], c[1], c[2])
+            bf.append(np.stack([V(a, b), V(a + 1, b), V(a + 1, b + 1), V(a, b + 1)], axis=1))
+            tag = lid_tag if (axis == 1 and side == n) else wall_tag
+            bt.append(np.full(a.shape[0], tag, dtype=np.int32))
+    return HexMesh(xyz, hx.astype(np.int64), np.concatenate(bf).astype(np.int64), np.concatenate(bt),
+                   None, name=f"hexcavity{n}", meta=dict(n=n, jitter=jitter, seed=seed))
+
+
+def hex_tilted_box_mesh(n: int = 6, tilt: float = 0.3, seed: int = BASE_SEED + 700,
+                        permute: bool = True, reorient: bool = True,
+                        tag: int = BC_FARFIELD) -> HexMesh:
+    """Hexahedra between three families of tilted planes: planar faces, cells
+    that are not parallelepipeds (their faces are general planar quadrilaterals).
+
+    Plane i of family x: x = i/n + a_i (y - 1/2) + b_i (z - 1/2), a_i, b_i drawn
+    from U(-tilt, tilt) / n (tilt < 1/2 keeps neighbouring planes from crossing
+    inside the box), likewise for y and z; vertex (i, j, k) is the meeting
+    point of planes i, j, k. Every boundary quadrilateral gets `tag`."""
+    rng = np.random.default_rng(seed)
+    g = np.arange(n + 1) / n
+    tl = rng.uniform(-tilt, tilt, size=(3, n + 1, 2)) / n   # family, plane, two slopes
+    I, J, K = np.meshgrid(np.arange(n + 1), np.arange(n + 1), np.arange(n + 1), indexing="ij")
+    idx = np.stack([I, J, K], axis=-1).reshape(-1, 3)
+    A = np.zeros((idx.shape[0], 3, 3))
+    rhs = np.zeros((idx.shape[0], 3))
+    for fam in range(3):
+        o1, o2 = [x for x in range(3) if x != fam]
+        sl = tl[fam, idx[:, fam]]
+        # x_fam - s1 x_o1 - s2 x_o2 = g - (s1 + s2) / 2
+        A[:, fam, fam] = 1.0
+        A[:, fam, o1] = -sl[:, 0]
+        A[:, fam, o2] = -sl[:, 1]
+        rhs[:, fam] = g[idx[:, fam]] - 0.5 * (sl[:, 0] + sl[:, 1])
+    xyz = np.linalg.solve(A, rhs[..., None])[..., 0]
+
+    def vid(i, j, k):
+        return (i * (n + 1) + j) * (n + 1) + k
+
+    hx = _hex_grid(n, vid, reorient, rng)
+    if permute:
+        hx = hx[rng.permutation(hx.shape[0])]
+    a, b = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    a, b = a.ravel(), b.ravel()
+    bf = []
+    for axis in range(3):
+        o1, o2 = [x for x in range(3) if x != axis]
+        for side in (0, n):
+            def V(u, v):
+                c = [None, None, None]
+                c[axis] = np.full_like(u, side)
+                c[o1] = u
+                c[o2] = v
+                return vid(c[0], c[1], c[2])
+            bf.append(np.stack([V(a, b), V(a + 1, b), V(a + 1, b + 1), V(a, b + 1)], axis=1))
+    bf = np.concatenate(bf).astype(np.int64)
+    return HexMesh(xyz, hx.astype(np.int64), bf, np.full(bf.shape[0], tag, np.int32), None,
+                   name=f"hextilted{n}", meta=dict(n=n, tilt=tilt, seed=seed))
+
+
+def hex_periodic_cube_mesh(n: int = 4, jitter: float = 0.1, seed: int = BASE_SEED + 600,
+                           permute: bool = True, reorient: bool = True, length: float = 1.0) -> HexMesh:
+    """Periodic cube [0,L]^3 of n^3 hexahedra, every vertex jittered (periodic
+    images of a vertex move together)."""
+    rng = np.random.default_rng(seed)
+    h = length / n
+    g = np.arange(n + 1)
+    I, J, K = np.meshgrid(g, g, g, indexing="ij")
+    lat = np.stack([I, J, K], axis=-1).reshape(-1, 3)
+    base = rng.uniform(-jitter * h, jitter * h, size=(n, n, n, 3))
+    xyz = lat.astype(np.float64) * h + base[lat[:, 0] % n, lat[:, 1] % n, lat[:, 2] % n]
+
+    def vid(i, j, k):
+        return (i * (n + 1) + j) * (n + 1) + k
+
+    hx = _hex_grid(n, vid, reorient, rng)
+    if permute:
+        hx = hx[rng.permutation(hx.shape[0])]
+    return HexMesh(xyz, hx.astype(np.int64), np.zeros((0, 4), np.int64), np.zeros(0, np.int32),
+                   np.eye(3) * length, name=f"hexperiodic{n}", meta=dict(n=n, jitter=jitter, seed=seed))
+
+
 def sphere_radii(layers: int, r_in: float, r_out: float, stretch: float) -> np.ndarray:
     """Radii of a geometric O-grid: first spacing dr1, ratio `stretch`, r_out reached."""
     if stretch == 1.0:
@@ -283,9 +469,9 @@ def conservative(rho, u, v, w, p, gamma=1.4):
     return np.stack(np.broadcast_arrays(rho, rho * u, rho * v, rho * w, E), axis=-1)
 
 
-def vertex_mean(mesh: Mesh) -> np.ndarray:
-    """Mean of the four vertices of every tetrahedron (a sampling point for states)."""
-    return mesh.xyz[mesh.tet4].mean(axis=1)
+def vertex_mean(mesh) -> np.ndarray:
+    """Mean of the vertices of every cell (a sampling point for states)."""
+    return mesh.xyz[mesh.cells].mean(axis=1)
 
 
 def uniform_state(n: int, rho=1.0, u=0.3, v=0.0, w=0.0, p=1.0 / 1.4, gamma=1.4) -> np.ndarray:

@@ -19,7 +19,8 @@ import pytest
 import oracle as O
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-PINS = [os.path.join(ROOT, "tests", f) for f in ("test_oracle_pins.py", "test_oracle_fd.py", "test_oracle_force.py")]
+PINS = [os.path.join(ROOT, "tests", f)
+        for f in ("test_oracle_pins.py", "test_oracle_fd.py", "test_oracle_force.py", "test_oracle_hex.py")]
 
 # (what the mistake is, file, text as written, text with the mistake)
 PLANTED = [
@@ -90,8 +91,8 @@ PLANTED = [
      "om[0] = gam0 * (1.0 + tz / (beta[0] + p->weno_eps));", "om[0] = gam0 * (1.0 + tz / (beta[1] + p->weno_eps));"),
     # compact HWENO (Sec. 3.3, Eq. (compact-big-1/2), Eq. (derivative))
     ("HWENO: neighbour gradients taken from the target", "orc_recon.c",
-     "for (int j = 0; j < 3; j++) data[4 + 3 * k + j] = G[15 * ck + 3 * c + j];",
-     "for (int j = 0; j < 3; j++) data[4 + 3 * k + j] = G[15 * i + 3 * c + j];"),
+     "for (int j = 0; j < 3; j++) data[nfc + 3 * k + j] = G[15 * ck + 3 * c + j];",
+     "for (int j = 0; j < 3; j++) data[nfc + 3 * k + j] = G[15 * i + 3 * c + j];"),
     ("HWENO sub-stencil: the neighbour's gradient dropped", "orc_recon.c",
      "if (jm >= 0) for (int j = 0; j < 3; j++) dm[4 + j] = G[15 * jm + 3 * c + j];", ""),
     ("HWENO fit: equality rows without the target's own average", "orc_mesh.c",
@@ -128,6 +129,32 @@ PLANTED = [
     ("sub-stencil without the neighbours of neighbour m", "orc_mesh.c",
      "for (int q = 0; q < 4; q++) { double s[3]; int64_t k = nb_of(m, &rm, q, s); add_ref(F->sub[mm], &F->n_sub[mm], ORC_MAXSUB, i, k, s); }",
      "for (int q = 0; q < 1; q++) { double s[3]; int64_t k = nb_of(m, &rm, q, s); add_ref(F->sub[mm], &F->n_sub[mm], ORC_MAXSUB, i, k, s); }"),
+    # hexahedral cells (Sec. 3.1)
+    ("hexahedron: a sub-stencil across an edge instead of a corner", "orc_mesh.c",
+     "{5, 3, 4}, {5, 4, 1}}", "{5, 3, 4}, {5, 4, 2}}"),
+    ("hexahedron: sub-stencils of the face-0 corners only", "orc_mesh.c",
+     "const int nsub = hex ? 8 : 4;", "const int nsub = hex ? 4 : 4;"),
+    ("hexahedron: big stencil from four of the six faces", "orc_mesh.c",
+     "for (int q = 0; q < nfc; q++) { double s[3]; int64_t k = nb_of(m, l1 + a, q, s);",
+     "for (int q = 0; q < 4; q++) { double s[3]; int64_t k = nb_of(m, l1 + a, q, s);"),
+    ("hexahedron: Gauss points of the quadrilateral at 1/2 -+ 1/(2 sqrt 2)", "orc_mesh.c",
+     "gl = 0.5 - 0.5 / sqrt(3.0), gh = 0.5 + 0.5 / sqrt(3.0);", "gl = 0.5 - 0.5 / sqrt(2.0), gh = 0.5 + 0.5 / sqrt(2.0);"),
+    ("hexahedron: equal Gauss weights on a quadrilateral", "orc_mesh.c",
+     "m->fgw[4 * f + g] = jac[g] / jsum;", "m->fgw[4 * f + g] = 0.25;"),
+    ("hexahedron: face area from one triangle of the quadrilateral", "orc_mesh.c",
+     "for (int d = 0; d < 3; d++) { d1[d] = c[d] - a[d]; d2[d] = e[d] - b[d];",
+     "for (int d = 0; d < 3; d++) { d1[d] = c[d] - a[d]; d2[d] = e[d] - a[d];"),
+    ("hexahedron: centroid = mean of the vertices", "orc_mesh.c",
+     "for (int d = 0; d < 3; d++) m->cen[3 * i + d] = cx[d] / vol;",
+     "for (int d = 0; d < 3; d++) { m->cen[3 * i + d] = 0.0; for (int a = 0; a < 8; a++) m->cen[3 * i + d] += 0.125 * xyz[3 * cells[8 * i + a] + d]; }"),
+    ("hexahedron: 4-point rule with a wrong outer node", "orc_mesh.c",
+     "b = sqrt(3.0 / 7.0 + 2.0 / 7.0 * sqrt(6.0 / 5.0));", "b = sqrt(3.0 / 7.0 + 2.0 / 7.0 * sqrt(5.0 / 6.0));"),
+    ("hexahedron: Jacobian determinant with a wrong cofactor sign", "orc_mesh.c",
+     "J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +", "J[0][1] * (J[1][0] * J[2][2] + J[1][2] * J[2][0]) +"),
+    ("quadrilateral faces weighted 1/3 like triangles", "orc_solver.c",
+     "const double wS = m->farea[f] * m->fgw[ngp * f + g];", "const double wS = m->farea[f] / 3.0;"),
+    ("hexahedron: compact fit without the gradients of the last two neighbours", "orc_mesh.c",
+     "for (int col = 0; col < nfc + 3 * (1 + nfc); col++) {", "for (int col = 0; col < nfc + 3 * (1 + nfc) - 6; col++) {"),
     # dense linear algebra (the library primitives the oracle's steps call)
     ("elimination without pivoting", "orc_linalg.c",
      "if (fabs(M[r * (n + 1) + c]) > best) { best = fabs(M[r * (n + 1) + c]); piv = r; }",
@@ -150,7 +177,8 @@ PLANTED = [
     ("A: off-diagonal block with the row cell's Jacobian", "orc_solver.c",
      "orc_euler_jacobian(Q + 5 * j, n, p->gamma, J);", "orc_euler_jacobian(Q + 5 * i, n, p->gamma, J);"),
     ("Jacobi sweep adds the off-diagonal product", "orc_solver.c",
-     "s -= off[100 * i + 25 * q + 5 * r + c] * prev[5 * j + c];", "s += off[100 * i + 25 * q + 5 * r + c] * prev[5 * j + c];"),
+     "s -= off[25 * m->nfc * i + 25 * q + 5 * r + c] * prev[5 * j + c];",
+     "s += off[25 * m->nfc * i + 25 * q + 5 * r + c] * prev[5 * j + c];"),
     ("Givens rotation: sign of s", "orc_solver.c",
      "H[(j + 1) * mk + k] = -s * h1 + c * h2;", "H[(j + 1) * mk + k] = s * h1 + c * h2;"),
     ("back substitution adds", "orc_solver.c", "s -= H[j * mk + k] * y[k];", "s += H[j * mk + k] * y[k];"),
