@@ -466,6 +466,81 @@ def run_precision(args, rank, world):
     return 0
 
 
+def run_hex(args, rank, world):
+    """Hexahedral cells (Sec. 3.1): the sphere workload's solver settings
+    (inviscid Ma 0.3, GMRES(20)x3, Jacobi 2, CFL 10, FP64) on n^3 hexahedra between
+    tilted planes (planar faces, cells that are not parallelepipeds), far field
+    all round, from a smooth perturbation of the free stream. For both schemes:
+    residual and implicit-step throughput, per-kernel times of one step, and the
+    flux kernel's fraction of the FP64 peak (its work per Gauss point is the
+    tetrahedral flux's: the same flux function)."""
+    import torch
+    import paper_2304_09485_gb300 as H
+    from paper_2304_09485_gb300 import inputs as I
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    fp64_peak = H.hgks_fp64_peak(local, 2.0)
+    cond = I.sphere_conditions(0.3)
+    m = I.hex_tilted_box_mesh(args.hex_n)
+    t0 = time.time()
+    hm = H.hgks_mesh_create(m, scheme_mask=3, device=local)
+    setup_s = time.time() - t0
+    F = H.hgks_mesh_info(hm).n_faces
+    u = cond["u_inf"]
+    Q0, G0 = I.smooth_state(m, amp=0.05, base=(cond["rho_inf"], u[0], u[1], u[2], cond["p_inf"]))
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {}
+    clocks = ClockSampler(local)
+    clocks.start()
+    for scheme in (0, 1):
+        p = H.hgks_default_params(scheme=scheme, krylov_dim=20, restarts=3, jacobi_sweeps=2, cfl=10.0, **cond)
+        Q, G = hm.to_internal(Q0, device=dev), hm.to_internal(G0, device=dev)
+        R, Gn = torch.empty_like(Q), torch.empty_like(G)
+        gargs = (G, R, Gn) if scheme else (None, R, None)
+        for _ in range(3):
+            H.hgks_residual(hm, p, Q, *gargs)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            H.hgks_residual(hm, p, Q, *gargs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res_ms = e0.elapsed_time(e1) / args.steps
+        for _ in range(max(3, args.warmup)):
+            H.hgks_gmres_step(hm, p, Q, G if scheme else None)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            H.hgks_gmres_step(hm, p, Q, G if scheme else None)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms = e0.elapsed_time(e1) / args.steps
+        H.hgks_profile_begin()
+        H.hgks_gmres_step(hm, p, Q, G if scheme else None)
+        prof = H.hgks_profile_end()
+        fl_ms, fl_n = prof["flux"][0], prof["flux"][1]
+        flux_gflops = KERNEL_FLOPS["flux"][0] * 4 * F / (fl_ms / fl_n * 1e-3) / 1e9
+        res[("weno", "hweno")[scheme]] = {
+            "residual_ms": res_ms, "residual_mcells_per_s": m.n_cells / res_ms / 1e3,
+            "step_ms": step_ms, "step_mcells_per_s": m.n_cells / step_ms / 1e3,
+            "kernels_ms_one_step": {k: round(v[0], 3) for k, v in prof.items()},
+            "flux_fp64_frac": flux_gflops / fp64_peak}
+    clk = clocks.stop()
+    if rank != 0:
+        return 0
+    line = {"metric": "hexahedral mesh: residual and implicit-step Mcells/s", "value": res["weno"]["step_mcells_per_s"],
+            "unit": "Mcells/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.hex_n}^3 = {m.n_cells:,} hexahedra between tilted planes, far field, "
+                                   "inviscid Ma 0.3, GMRES(20)x3, Jacobi 2, CFL 10, FP64", "n_faces": F,
+                       "mesh_setup_s": setup_s, "l2": "inputs larger than L2"},
+            "fp64_peak_gflops": fp64_peak, "clocks": clk, **res}
+    print(json.dumps(line))
+    return 0
+
+
 def run_serve(args, rank, world):
     """Steady-solve requests with Poisson arrivals served by the continuous-
     batching server (mixed precision) against the same requests solved one
@@ -596,7 +671,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="scaled-down mesh (profiling runs)")
     ap.add_argument("--sphere-n", type=int, default=0, help="sphere of n x n patches and 2n layers (profiling runs)")
-    ap.add_argument("--workload", default="sphere", choices=["sphere", "batch", "serve", "precision"],
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "batch", "serve", "precision", "hex"],
                     help="sphere: the 2.36M-tet sphere (default); batch: many problems in one batch; "
                          "serve: Poisson-arriving solves through the request server")
     ap.add_argument("--serve-requests", type=int, default=96)
@@ -611,6 +686,7 @@ def main():
     ap.add_argument("--batch-meshes", type=int, default=48)
     ap.add_argument("--batch-scheme", default="hweno", choices=["weno", "hweno"])
     ap.add_argument("--batch-precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--hex-n", type=int, default=72, help="hex workload: n^3 hexahedra")
     ap.add_argument("--grad-relax", type=float, default=1.0,
                     help="precision workload: relaxation of the compact gradient update (1: Algorithm 1's)")
     ap.add_argument("--batch-drop", type=float, default=0.0,
@@ -629,6 +705,8 @@ def main():
         return run_batch(args, rank, world)
     if args.workload == "serve":
         return run_serve(args, rank, world)
+    if args.workload == "hex":
+        return run_hex(args, rank, world)
     if args.workload == "precision":
         return run_precision(args, rank, world)
 

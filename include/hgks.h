@@ -134,6 +134,8 @@ typedef struct {
   int64_t device_bytes;      /* device memory held by the handle */
   int32_t device;
   int32_t schemes;           /* bit 0: WENO data present, bit 1: HWENO data present */
+  int32_t faces_per_cell;    /* 4: tetrahedra, 6: hexahedra */
+  int32_t reserved;
 } hgks_mesh_info_t;
 
 typedef struct {
@@ -169,6 +171,26 @@ hgks_status hgks_mesh_create(const double *xyz, int64_t n_vert, const int64_t *t
                              const int64_t *bface3, const int32_t *btag, int64_t n_bface,
                              const double *periodic_shift, int32_t n_periodic, int32_t scheme_mask,
                              int32_t device, hgks_mesh *out, int64_t *perm_out);
+/* The same for a hexahedral mesh (paper Sec. 3.1: six faces per cell, the
+ * eight non-compact sub-stencils of three face neighbours across each corner,
+ * one compact sub-stencil per face).
+ *  hex8[n_hex][8]      vertex indices: 0-3 one quadrilateral in cyclic order,
+ *                      4 + a the vertex joined to a; positively oriented
+ *                      ((x1 - x0) x (x3 - x0)) . (x4 - x0) > 0; local faces
+ *                      0 = 0123, 1 = 0154, 2 = 1265, 3 = 2376, 4 = 3047, 5 = 4567
+ *  bquad4[n_bface][4]  boundary quadrilaterals (any cyclic vertex order)
+ * A cell is the trilinear map of the unit cube; a face the bilinear surface
+ * through its vertices, with area and normal from its vector area and 2 x 2
+ * Gauss points weighted by the area element (exact for planar faces). Meshes
+ * of hexahedra run through the single-mesh calls (residual, Jacobian, GMRES
+ * step, solves, matrix-free products); hgks_residual_noalloc and batches take
+ * tetrahedra only and return HGKS_ERR_ARG. Errors as hgks_mesh_create, and
+ * HGKS_ERR_MESH for an inverted hexahedron (Jacobian determinant <= 0 at a
+ * Gauss point). */
+hgks_status hgks_mesh_create_hex(const double *xyz, int64_t n_vert, const int64_t *hex8, int64_t n_hex,
+                                 const int64_t *bquad4, const int32_t *btag, int64_t n_bface,
+                                 const double *periodic_shift, int32_t n_periodic, int32_t scheme_mask,
+                                 int32_t device, hgks_mesh *out, int64_t *perm_out);
 hgks_status hgks_mesh_destroy(hgks_mesh mesh);
 hgks_status hgks_mesh_info(hgks_mesh mesh, hgks_mesh_info_t *info);
 /* Cell volumes in internal order, into a host array of n_cells doubles. */
@@ -176,7 +198,8 @@ hgks_status hgks_mesh_volumes(hgks_mesh mesh, double *vol_host);
 
 /* Residual R = L(Q) (Eq. (finite) with the time-averaged flux of Sec. 4.1):
  * reconstruction (Sec. 3.2/3.3 in characteristic variables, Sec. 5), the BGK
- * flux of Eq. (flux) at 3 Gauss points per face, face-to-cell accumulation;
+ * flux of Eq. (flux) at the Gauss points of every face (3 on a triangle, 2 x 2
+ * on a quadrilateral), face-to-cell accumulation;
  * compact scheme: G_new = cell-averaged gradients from the point values of
  * Eq. (point) by Eq. (derivative). G and G_new are NULL for WENO.
  * All pointers are device pointers in internal order. */

@@ -41,7 +41,8 @@ class hgks_params(C.Structure):
 
 class hgks_mesh_info_t(C.Structure):
     _fields_ = [("n_cells", C.c_int64), ("n_faces", C.c_int64), ("n_boundary_faces", C.c_int64),
-                ("device_bytes", C.c_int64), ("device", C.c_int32), ("schemes", C.c_int32)]
+                ("device_bytes", C.c_int64), ("device", C.c_int32), ("schemes", C.c_int32),
+                ("faces_per_cell", C.c_int32), ("reserved", C.c_int32)]
 
 
 class hgks_step_info(C.Structure):
@@ -82,6 +83,7 @@ def lib():
         sig = {
             "hgks_default_params": [P],
             "hgks_mesh_create": [dp, i64, dp, i64, dp, dp, i64, dp, i32, i32, i32, C.POINTER(vp), dp],
+            "hgks_mesh_create_hex": [dp, i64, dp, i64, dp, dp, i64, dp, i32, i32, i32, C.POINTER(vp), dp],
             "hgks_mesh_destroy": [vp],
             "hgks_mesh_info": [vp, C.POINTER(hgks_mesh_info_t)],
             "hgks_mesh_volumes": [vp, dp],
@@ -199,19 +201,23 @@ class hgks_mesh:
 
 
 def hgks_mesh_create(mesh, scheme_mask=3, device=0) -> hgks_mesh:
-    """Build a library mesh from an inputs.Mesh (host arrays, caller order)."""
+    """Build a library mesh from an inputs.Mesh (tetrahedra: hgks_mesh_create) or
+    an inputs.HexMesh (hexahedra: hgks_mesh_create_hex); host arrays, caller order."""
+    hexa = hasattr(mesh, "hex8")
     xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
-    tet = np.ascontiguousarray(mesh.tet4, dtype=np.int64)
-    bf = np.ascontiguousarray(mesh.bface3, dtype=np.int64).reshape(-1, 3)
+    cells = np.ascontiguousarray(mesh.hex8 if hexa else mesh.tet4, dtype=np.int64)
+    nfv = 4 if hexa else 3
+    bf = np.ascontiguousarray(mesh.bface4 if hexa else mesh.bface3, dtype=np.int64).reshape(-1, nfv)
     bt = np.ascontiguousarray(mesh.btag, dtype=np.int32)
     ps = mesh.periodic_shift
     psa = np.ascontiguousarray(ps if ps is not None else np.zeros((0, 3)), dtype=np.float64)
-    perm = np.zeros(max(1, tet.shape[0]), dtype=np.int64)
+    perm = np.zeros(max(1, cells.shape[0]), dtype=np.int64)
     h = C.c_void_p()
-    _check(lib().hgks_mesh_create(_ptr(xyz), xyz.shape[0], _ptr(tet), tet.shape[0], _ptr(bf) if len(bf) else None,
-                                  _ptr(bt) if len(bt) else None, bf.shape[0], _ptr(psa) if len(psa) else None,
-                                  psa.shape[0], scheme_mask, device, C.byref(h), _ptr(perm)))
-    return hgks_mesh(h.value, perm[: tet.shape[0]], tet.shape[0])
+    fn = lib().hgks_mesh_create_hex if hexa else lib().hgks_mesh_create
+    _check(fn(_ptr(xyz), xyz.shape[0], _ptr(cells), cells.shape[0], _ptr(bf) if len(bf) else None,
+              _ptr(bt) if len(bt) else None, bf.shape[0], _ptr(psa) if len(psa) else None,
+              psa.shape[0], scheme_mask, device, C.byref(h), _ptr(perm)))
+    return hgks_mesh(h.value, perm[: cells.shape[0]], cells.shape[0])
 
 
 def hgks_mesh_info(mesh: hgks_mesh) -> hgks_mesh_info_t:

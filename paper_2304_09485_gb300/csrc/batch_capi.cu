@@ -500,6 +500,7 @@ hgks_status hgks_batch_create(const hgks_mesh *meshes, const hgks_params *params
     if (!meshes[k]) return fail_msg(HGKS_ERR_ARG, "a mesh handle is NULL");
     const Mesh &a = *mesh_of(meshes[k]);
     if (a.device != mesh_of(meshes[0])->device) return fail_msg(HGKS_ERR_ARG, "meshes of a batch must be on one device");
+    if (a.d.hex) return fail_msg(HGKS_ERR_ARG, "batches take tetrahedral meshes only");
     if ((st = take_params(a, &params[k], &P[k]))) return st;
     if (!same_shared(P[0], P[k]))
       return fail_msg(HGKS_ERR_ARG, "scheme, precision, jv_mode, krylov_dim, restarts, jacobi_sweeps must agree");
@@ -550,6 +551,7 @@ hgks_status hgks_batch_add(hgks_batch batch, hgks_mesh mesh, const hgks_params *
   *k_out = -1;
   const Mesh &a = *mesh_of(mesh);
   if (a.device != B.m.device) return fail_msg(HGKS_ERR_ARG, "mesh is on another device");
+  if (a.d.hex) return fail_msg(HGKS_ERR_ARG, "batches take tetrahedral meshes only");
   hgks_params P;
   hgks_status st = take_params(a, p, &P);
   if (st) return st;

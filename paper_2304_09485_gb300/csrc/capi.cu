@@ -141,24 +141,27 @@ hgks_status take_params(const Mesh &m, const hgks_params *p, hgks_params *out) {
 hgks_status ensure_scratch(Mesh &m, int kdim, bool implicit, bool mixed) {
   Scratch &s = m.s;
   const size_t N = m.N, F = m.F;
+  const bool hex = m.d.hex != 0;
+  const size_t NF = hex ? HexShape::NF : TetShape::NF, NG = hex ? HexShape::NG : TetShape::NG;
+  const size_t ncoef = hex ? ShapeOf<HexShape>::COEF : ShapeOf<TetShape>::COEF;
   hgks_status st;
   if (!s.coef) {
-    if ((st = dalloc(m, &s.coef, (size_t)kCoef * N))) return st;
+    if ((st = dalloc(m, &s.coef, ncoef * N))) return st;
     if ((st = dalloc(m, &s.dt, N))) return st;
-    if ((st = dalloc(m, &s.wface, (size_t)2 * 3 * kFaceState * F))) return st;
-    if ((st = dalloc(m, &s.fflux, (size_t)15 * F))) return st;
-    if ((st = dalloc(m, &s.fpt, (size_t)15 * F))) return st;
+    if ((st = dalloc(m, &s.wface, 2 * NG * kFaceState * F))) return st;
+    if ((st = dalloc(m, &s.fflux, 5 * NG * F))) return st;
+    if ((st = dalloc(m, &s.fpt, 5 * NG * F))) return st;
     if ((st = dalloc(m, &s.flags, 8))) return st;
     // one partial per block and sum (the MGS pass reduces 16 sums over 608 blocks)
     if ((st = dalloc(m, &s.red, std::max<size_t>(16 * 608 + 64, N / 64 + 64)))) return st;
     if ((st = dalloc(m, &s.red_count, 4))) return st;
     HGKS_CUDA(cudaMemset(s.flags, 0, 8 * sizeof(int)));
     HGKS_CUDA(cudaMemset(s.red_count, 0, 4 * sizeof(unsigned)));
-    HGKS_CUDA(cudaMemset(s.wface, 0, sizeof(double) * 2 * 3 * kFaceState * F));
+    HGKS_CUDA(cudaMemset(s.wface, 0, sizeof(double) * 2 * NG * kFaceState * F));
   }
   s.vstride = (int64_t)((5 * N + 63) / 64 * 64);
   if (implicit && !s.off) {
-    if ((st = dalloc(m, &s.off, (size_t)100 * N))) return st;
+    if ((st = dalloc(m, &s.off, 25 * NF * N))) return st;
     if ((st = dalloc(m, &s.dval, N))) return st;
     if ((st = dalloc(m, &s.dinv, N))) return st;
     if ((st = dalloc(m, &s.R, 5 * N))) return st;
@@ -169,10 +172,10 @@ hgks_status ensure_scratch(Mesh &m, int kdim, bool implicit, bool mixed) {
     if ((st = dalloc(m, &s.t2, 5 * N))) return st;
     if ((st = dalloc(m, &s.hs, 65 * 64 + 256))) return st;
     if ((st = dalloc(m, &s.gram, 65 * 65 + 2 * 65 + 64))) return st;
-    HGKS_CUDA(cudaMemset(s.off, 0, sizeof(double) * 100 * N));
+    HGKS_CUDA(cudaMemset(s.off, 0, sizeof(double) * 25 * NF * N));
   }
   if (implicit && mixed && !s.jv32) {
-    if ((st = dalloc(m, &s.jv32, (size_t)22 * N))) return st;
+    if ((st = dalloc(m, &s.jv32, (6 + 4 * NF) * N))) return st;
     if ((st = dalloc(m, &s.dval32, N))) return st;
     if ((st = dalloc(m, &s.dinv32, N))) return st;
     if ((st = dalloc(m, &s.w32, 5 * N))) return st;
@@ -294,10 +297,12 @@ hgks_status hgks_default_params(hgks_params *p) {
   return HGKS_OK;
 }
 
-hgks_status hgks_mesh_create(const double *xyz, int64_t n_vert, const int64_t *tet4, int64_t n_tet,
-                             const int64_t *bface3, const int32_t *btag, int64_t n_bface,
-                             const double *periodic_shift, int32_t n_periodic, int32_t scheme_mask,
-                             int32_t device, hgks_mesh *out, int64_t *perm_out) {
+}  // extern "C"
+
+namespace {
+hgks_status create_mesh(const double *xyz, int64_t n_vert, const int64_t *cells, int32_t nvc, int64_t n_cells,
+                        const int64_t *bface, const int32_t *btag, int64_t n_bface, const double *periodic_shift,
+                        int32_t n_periodic, int32_t scheme_mask, int32_t device, hgks_mesh *out, int64_t *perm_out) {
   HGKS_RANGE("hgks mesh create");
   if (!out) return fail(HGKS_ERR_ARG, "out is NULL");
   *out = nullptr;
@@ -307,8 +312,8 @@ hgks_status hgks_mesh_create(const double *xyz, int64_t n_vert, const int64_t *t
   if (device < 0 || device >= ndev) return fail(HGKS_ERR_ARG, "device index out of range");
   HostMesh hm;
   std::string err;
-  hgks_status st = build_host_mesh(xyz, n_vert, tet4, n_tet, bface3, btag, n_bface, periodic_shift, n_periodic,
-                                   scheme_mask & 3, hm, err);
+  hgks_status st = build_host_mesh(xyz, n_vert, cells, nvc, n_cells, bface, btag, n_bface, periodic_shift,
+                                   n_periodic, scheme_mask & 3, hm, err);
   if (st) return fail(st, err);
   hgks_mesh_s *h = new (std::nothrow) hgks_mesh_s;
   if (!h) return fail(HGKS_ERR_OOM, "host allocation");
@@ -319,7 +324,7 @@ hgks_status hgks_mesh_create(const double *xyz, int64_t n_vert, const int64_t *t
   DeviceScope dev_scope(device);
   if (dev_scope.error() != cudaSuccess) return bail(cuda_fail(dev_scope.error(), "cudaSetDevice"));
   DevMesh &d = m.d;
-  d.N = (int)hm.N; d.F = (int)hm.F;
+  d.N = (int)hm.N; d.F = (int)hm.F; d.hex = hm.hex;
   std::vector<double> inv_vol(hm.N);
   for (int64_t i = 0; i < hm.N; i++) inv_vol[i] = 1.0 / hm.vol[i];
   if ((st = upload(m, &d.vol, hm.vol)) || (st = upload(m, &d.inv_vol, inv_vol)) || (st = upload(m, &d.h, hm.h)) ||
@@ -328,13 +333,32 @@ hgks_status hgks_mesh_create(const double *xyz, int64_t n_vert, const int64_t *t
       (st = upload(m, &d.Xs, hm.Xs)) || (st = upload(m, &d.ssl, hm.ssl)) || (st = upload(m, &d.subvalid, hm.subvalid)) || (st = upload(m, &d.H0, hm.H0)) ||
       (st = upload(m, &d.Hm, hm.Hm)) || (st = upload(m, &d.fl, hm.fl)) || (st = upload(m, &d.fr, hm.fr)) ||
       (st = upload(m, &d.ftag, hm.ftag)) || (st = upload(m, &d.fT, hm.fT)) || (st = upload(m, &d.fS, hm.fS)) ||
-      (st = upload(m, &d.fdist, hm.fdist)))
+      (st = upload(m, &d.fdist, hm.fdist)) || (hm.hex && (st = upload(m, &d.fw, hm.fw))))
     return bail(st);
   if ((st = ensure_scratch(m, 0, false))) return bail(st);
   m.vol_host = hm.vol;
   if (perm_out) std::memcpy(perm_out, hm.perm.data(), sizeof(int64_t) * hm.N);
   *out = h;
   return HGKS_OK;
+}
+}  // namespace
+
+extern "C" {
+
+hgks_status hgks_mesh_create(const double *xyz, int64_t n_vert, const int64_t *tet4, int64_t n_tet,
+                             const int64_t *bface3, const int32_t *btag, int64_t n_bface,
+                             const double *periodic_shift, int32_t n_periodic, int32_t scheme_mask,
+                             int32_t device, hgks_mesh *out, int64_t *perm_out) {
+  return create_mesh(xyz, n_vert, tet4, 4, n_tet, bface3, btag, n_bface, periodic_shift, n_periodic, scheme_mask,
+                     device, out, perm_out);
+}
+
+hgks_status hgks_mesh_create_hex(const double *xyz, int64_t n_vert, const int64_t *hex8, int64_t n_hex,
+                                 const int64_t *bquad4, const int32_t *btag, int64_t n_bface,
+                                 const double *periodic_shift, int32_t n_periodic, int32_t scheme_mask,
+                                 int32_t device, hgks_mesh *out, int64_t *perm_out) {
+  return create_mesh(xyz, n_vert, hex8, 8, n_hex, bquad4, btag, n_bface, periodic_shift, n_periodic, scheme_mask,
+                     device, out, perm_out);
 }
 
 hgks_status hgks_mesh_destroy(hgks_mesh mesh) {
@@ -349,6 +373,7 @@ hgks_status hgks_mesh_info(hgks_mesh mesh, hgks_mesh_info_t *info) {
   if (!mesh || !info) return fail(HGKS_ERR_ARG, "NULL argument");
   info->n_cells = mesh->m.N; info->n_faces = mesh->m.F; info->n_boundary_faces = mesh->m.Fb;
   info->device_bytes = (int64_t)mesh->m.bytes; info->device = mesh->m.device; info->schemes = mesh->m.schemes;
+  info->faces_per_cell = mesh->m.d.hex ? 6 : 4;
   return HGKS_OK;
 }
 

@@ -24,28 +24,49 @@ constexpr int kCoefA = 45;      // quadratic coefficients: 9 x 5
 constexpr int kCoef = 105;      // + 4 linear sub-polynomials: 4 x 3 x 5
 constexpr int kFaceState = 20;  // W[5] + dW[3][5] at one Gauss point, face frame
 
+// Compile-time shape of a cell kind (Sec. 3.1). Tetrahedra: 4 triangular faces
+// with 3 Gauss points, big stencil <= 16 cells, 4 sub-stencils of up to 6 cells
+// (slots in 4 bits). Hexahedra: 6 quadrilateral faces with 2 x 2 Gauss points,
+// big stencil <= 24 cells, 8 sub-stencils of 3 face neighbours (slots in 8 bits).
+// The compact scheme has one sub-stencil per face.
+struct TetShape {
+  static constexpr int NF = 4, NG = 3, BIG = 16, NSUBW = 4, SUBK = 6, SLOTBITS = 4;
+};
+struct HexShape {
+  static constexpr int NF = 6, NG = 4, BIG = 24, NSUBW = 8, SUBK = 3, SLOTBITS = 8;
+};
+template <class S> struct ShapeOf {
+  static constexpr int NSUB = S::NSUBW > S::NF ? S::NSUBW : S::NF;   // sub-polynomials held per cell
+  static constexpr int COEF = kCoefA + 15 * NSUB;                  // coefficients per cell
+  static constexpr int HCOLS = S::NF + 3 * (1 + S::NF);            // data columns of the compact fit
+};
+
 struct DevMesh {
   int N = 0, F = 0;
+  int hex = 0;                   // 0: tetrahedra (TetShape), 1: hexahedra (HexShape)
   // cells
   double *vol = nullptr, *inv_vol = nullptr, *h = nullptr;
   double *m2 = nullptr;          // [6][N] avg over the cell of xh_a xh_b: xx,yy,zz,xy,xz,yz
-  int *cnb = nullptr;            // [4][N] neighbour across local face p, -1 on a boundary
-  int *cface = nullptr;          // [4][N] 2*face + side (side 0: the cell is the face's left)
-  double *xg = nullptr;          // [36][N] Gauss points of face slot p: (p*3+g)*3+d, scaled frame
+  // sizes below for tetrahedra; hexahedra: NF = 6 faces, NG = 4 Gauss points,
+  // BIG = 24, 8 sub-stencils of SUBK = 3 cells with 8-bit slots, 27 compact columns
+  int *cnb = nullptr;            // [NF][N] neighbour across local face p, -1 on a boundary
+  int *cface = nullptr;          // [NF][N] 2*face + side (side 0: the cell is the face's left)
+  double *xg = nullptr;          // [NF*NG*3][N] Gauss points of face slot p: (p*NG+g)*3+d, scaled frame
   // non-compact (WENO)
-  int *sten = nullptr;           // [16][N] big stencil, -1 padded
-  double *X0 = nullptr;          // [9*16][N] a_d = sum_k X0[d*16+k] (Q_k - Q_i)
-  double *Xs = nullptr;          // [4*3*6][N] b_j^m = sum_s Xs[(m*3+j)*6+s] (Q_k(s) - Q_i)
-  unsigned *ssl = nullptr;       // [4][N] k(s) of sub-stencil m: 4-bit big-stencil slots, s = 0..5, ascending
+  int *sten = nullptr;           // [BIG][N] big stencil, -1 padded
+  double *X0 = nullptr;          // [9*BIG][N] a_d = sum_k X0[d*BIG+k] (Q_k - Q_i)
+  double *Xs = nullptr;          // [NSUBW*3*SUBK][N] b_j^m = sum_s Xs[(m*3+j)*SUBK+s] (Q_k(s) - Q_i)
+  unsigned *ssl = nullptr;       // [NSUBW][N] k(s) of sub-stencil m: SLOTBITS-bit big-stencil slots, ascending
   unsigned char *subvalid = nullptr;  // [N] bit m: sub-stencil m used
   // compact (HWENO)
-  double *H0 = nullptr;          // [9*19][N] a_d from (dQ of slots 0..3, G_i, G of slots 0..3)
-  double *Hm = nullptr;          // [4*3*7][N] b^m from (dQ_m, G_i, G_m)
+  double *H0 = nullptr;          // [9*HCOLS][N] a_d from (dQ of slots 0..NF-1, G_i, G of slots 0..NF-1)
+  double *Hm = nullptr;          // [NF*3*7][N] b^m from (dQ_m, G_i, G_m)
   // faces
   int *fl = nullptr, *fr = nullptr;   // [F] left/right cell, fr = -1 on a boundary
   signed char *ftag = nullptr;        // [F] boundary tag, 0 inside
   double *fT = nullptr;          // [9][F] rows n, t1, t2 (n from left to right)
   double *fS = nullptr;          // [F] area
+  double *fw = nullptr;          // [NG][F] Gauss weights of the quadrilateral faces (sum 1); null for tetrahedra
   double *fdist = nullptr;       // [F] |x_L - x_R| (or twice the wall distance on a boundary)
   // batches of meshes (hgks_batch_*): per-mesh parameters and the mesh of every
   // cell (-1 for the padding cells that align each mesh to a 256-cell block) and face
@@ -88,15 +109,15 @@ struct BatchState {
 };
 
 struct Scratch {
-  double *coef = nullptr;        // [105][N]
+  double *coef = nullptr;        // [COEF][N] (105 tetrahedra, 165 hexahedra)
   double *dt = nullptr;          // [N]
-  double *wface = nullptr;       // [2][3][20][F] reconstructed states at Gauss points
-  double *fflux = nullptr;       // [3][5][F] global-frame flux * area / 3
-  double *fpt = nullptr;         // [3][5][F] global-frame point values * area / 3
+  double *wface = nullptr;       // [2][NG][20][F] reconstructed states at Gauss points
+  double *fflux = nullptr;       // [NG][5][F] global-frame flux * area * Gauss weight
+  double *fpt = nullptr;         // [NG][5][F] global-frame point values * area * Gauss weight
   // implicit
   double *dinv = nullptr, *dval = nullptr;  // [N] the diagonal block is (|Omega|/dt + sum lambda S/2) I
-  double *off = nullptr;         // [4*25][N]: block of local face p of the row cell (0 on a boundary)
-  float *jv32 = nullptr;         // [22][N] mixed precision: the off-diagonal blocks as products,
+  double *off = nullptr;         // [NF*25][N]: block of local face p of the row cell (0 on a boundary)
+  float *jv32 = nullptr;         // [6 + 4 NF][N] mixed precision: the off-diagonal blocks as products,
                                  // rows 0-5 per cell (u, v, w, H, (gamma-1)|u|^2/2, gamma-1),
                                  // rows 6 + 4p + k per (cell, local face p): n S/2 (k < 3), lambda S/2
   float *dinv32 = nullptr, *dval32 = nullptr;
@@ -146,15 +167,19 @@ struct Mesh {
 // ---- host mesh construction (mesh_setup.cpp) ----
 struct HostMesh {
   int64_t N = 0, F = 0, Fb = 0;
+  int hex = 0;                           // cell kind: 0 tetrahedra, 1 hexahedra
   std::vector<int64_t> perm;             // internal -> caller
   std::vector<double> vol, h, m2, xg;    // SoA-ready, internal order
   std::vector<int> cnb, cface, sten, fl, fr;
   std::vector<signed char> ftag;
   std::vector<unsigned char> subvalid;
-  std::vector<double> X0, Xs, H0, Hm, fT, fS, fdist;
+  std::vector<double> X0, Xs, H0, Hm, fT, fS, fw, fdist;
   std::vector<unsigned> ssl;
 };
-hgks_status build_host_mesh(const double *xyz, int64_t nv, const int64_t *tet, int64_t nt,
+// cells: [nt][nvc] vertex indices, nvc = 4 (tetrahedra) or 8 (hexahedra: 0-3 one
+// quadrilateral in cyclic order, 4 + a above a); bface: [nb][3] triangles or
+// [nb][4] quadrilaterals in cyclic order
+hgks_status build_host_mesh(const double *xyz, int64_t nv, const int64_t *cells, int32_t nvc, int64_t nt,
                             const int64_t *bface, const int32_t *btag, int64_t nb,
                             const double *pshift, int32_t nps, int scheme_mask, HostMesh &hm,
                             std::string &err);

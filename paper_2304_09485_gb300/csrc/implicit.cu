@@ -52,7 +52,7 @@ __device__ __forceinline__ void euler_jacobian(const double *Q, const double *n,
 
 // jv32 (may be null): FP32 operands of the product form of the off-diagonal
 // blocks (mixed precision), with dval32, dinv32
-template <bool BATCH>
+template <bool BATCH, int NF>
 __global__ void __launch_bounds__(kCellBlock) k_assemble(DevMesh m, hgks_params Pv, const double *__restrict__ Q,
                                                          const double *__restrict__ dt, double *__restrict__ dval,
                                                          double *__restrict__ dinv, double *__restrict__ off,
@@ -66,12 +66,12 @@ __global__ void __launch_bounds__(kCellBlock) k_assemble(DevMesh m, hgks_params 
     dval[i] = 1.0;
     dinv[i] = 1.0;
 #pragma unroll 4
-    for (int k = 0; k < 100; k++) off[(size_t)k * N + i] = 0.0;
+    for (int k = 0; k < 25 * NF; k++) off[(size_t)k * N + i] = 0.0;
     if (jv32) {
       dval32[i] = 1.0f;
       dinv32[i] = 1.0f;
 #pragma unroll 2
-      for (int k = 0; k < 22; k++) jv32[(size_t)k * N + i] = 0.0f;
+      for (int k = 0; k < 6 + 4 * NF; k++) jv32[(size_t)k * N + i] = 0.0f;
     }
     return;
   }
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kCellBlock) k_assemble(DevMesh m, hgks_params 
   }
   double d = m.vol[i] / dt[i];
 #pragma unroll 1
-  for (int p = 0; p < 4; p++) {
+  for (int p = 0; p < NF; p++) {
     const int cf = m.cface[(size_t)p * N + i], f = cf >> 1, side = cf & 1;
     const int j = m.cnb[(size_t)p * N + i];
     const double sg = side ? -1.0 : 1.0;
@@ -186,7 +186,7 @@ enum { kSpmv = 0, kJacobi = 1, kNeumann = 2, kE = 3, kNegE = 4 };
 
 // TM = float: the off-diagonal blocks come as products from jv (mixed precision);
 // TM = double: stored 5x5 blocks in off.
-template <typename TM, typename TV, typename TO, int Mode, bool FirstSweep>
+template <typename TM, typename TV, typename TO, int Mode, bool FirstSweep, int NF>
 __global__ void __launch_bounds__(kCellBlock) k_apply(DevMesh m, const TM *__restrict__ off, const TM *__restrict__ dval,
                                                       const TM *__restrict__ dinv, const TV *__restrict__ b,
                                                       const TV *__restrict__ x, TO *__restrict__ y,
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kCellBlock) k_apply(DevMesh m, const TM *__res
 #pragma unroll
     for (int r = 0; r < 5; r++) acc[r] = Mode == kSpmv ? di * x[(size_t)r * N + i] : TV(0);
 #pragma unroll
-    for (int p = 0; p < 4; p++) {
+    for (int p = 0; p < NF; p++) {
       const int j = m.cnb[(size_t)p * N + i];
       if (j < 0) continue;
       TV xj[5];
@@ -249,6 +249,18 @@ __global__ void __launch_bounds__(kCellBlock) k_apply(DevMesh m, const TM *__res
     }
   }
   if (dotv) grid_sum(part, partials, count, dot_out, 0);
+}
+
+// k_apply for the mesh's cell kind (4 or 6 off-diagonal blocks per row)
+template <typename TM, typename TV, typename TO, int Mode, bool FirstSweep>
+void apply_launch(unsigned grid, cudaStream_t st, const DevMesh &m, const TM *off, const TM *dval, const TM *dinv,
+                  const TV *b, const TV *x, TO *y, const TO *dotv, TO *partials, unsigned int *count, double *dot_out) {
+  if (m.hex)
+    k_apply<TM, TV, TO, Mode, FirstSweep, HexShape::NF><<<grid, kCellBlock, 0, st>>>(m, off, dval, dinv, b, x, y, dotv,
+                                                                                      partials, count, dot_out);
+  else
+    k_apply<TM, TV, TO, Mode, FirstSweep, TetShape::NF><<<grid, kCellBlock, 0, st>>>(m, off, dval, dinv, b, x, y, dotv,
+                                                                                      partials, count, dot_out);
 }
 
 template <typename T>
@@ -718,10 +730,10 @@ void precondition_t(const DevMesh &m, Scratch &s, const KBuf<T> &k, int sweeps, 
     const T *dv = (q == sweeps) ? dotv : nullptr;
     HGKS_PROF_BEGIN(K_JACOBI, st);
     if (q == 1)
-      k_apply<T, T, T, kJacobi, true><<<cg, kCellBlock, 0, st>>>(m, k.off, k.dval, k.dinv, b, nullptr, dst, dv, k.red,
+      apply_launch<T, T, T, kJacobi, true>(cg, st, m, k.off, k.dval, k.dinv, b, nullptr, dst, dv, k.red,
                                                                   s.red_count, dot_out);
     else
-      k_apply<T, T, T, kJacobi, false><<<cg, kCellBlock, 0, st>>>(m, k.off, k.dval, k.dinv, b, prev, dst, dv, k.red,
+      apply_launch<T, T, T, kJacobi, false>(cg, st, m, k.off, k.dval, k.dinv, b, prev, dst, dv, k.red,
                                                                    s.red_count, dot_out);
     HGKS_PROF_END(K_JACOBI, st);
     prev = dst;
@@ -745,16 +757,16 @@ void neumann_t(const DevMesh &m, Scratch &s, const KBuf<T> &k, int sweeps, const
     T *dst = (q % 2 == 0) ? k.t : k.t2;
     HGKS_PROF_BEGIN(K_JACOBI, st);
     if (q == 0 && sweeps % 2 == 1)
-      k_apply<T, T, T, kNegE, false><<<cg, kCellBlock, 0, st>>>(m, k.off, k.dval, k.dinv, nullptr, z, dst, nullptr,
+      apply_launch<T, T, T, kNegE, false>(cg, st, m, k.off, k.dval, k.dinv, nullptr, z, dst, nullptr,
                                                                  k.red, s.red_count, nullptr);
     else
-      k_apply<T, T, T, kE, false><<<cg, kCellBlock, 0, st>>>(m, k.off, k.dval, k.dinv, nullptr, z, dst, nullptr,
+      apply_launch<T, T, T, kE, false>(cg, st, m, k.off, k.dval, k.dinv, nullptr, z, dst, nullptr,
                                                               k.red, s.red_count, nullptr);
     HGKS_PROF_END(K_JACOBI, st);
     z = dst;
   }
   HGKS_PROF_BEGIN(K_SPMV, st);
-  k_apply<T, T, T, kNeumann, false><<<cg, kCellBlock, 0, st>>>(m, k.off, k.dval, k.dinv, v, z, w, dotv, k.red,
+  apply_launch<T, T, T, kNeumann, false>(cg, st, m, k.off, k.dval, k.dinv, v, z, w, dotv, k.red,
                                                                 s.red_count, dot_out);
   HGKS_PROF_END(K_SPMV, st);
 }
@@ -785,7 +797,7 @@ void gmres_t(const DevMesh &m, Scratch &s, const KBuf<T> &k, const hgks_params &
       HGKS_PROF_END(K_SPMV, st);
     } else {
       HGKS_PROF_BEGIN(K_SPMV, st);
-      k_apply<T, double, T, kSpmv, false><<<cg, kCellBlock, 0, st>>>(m, k.off, k.dval, k.dinv, rhs, dx, k.t, nullptr,
+      apply_launch<T, double, T, kSpmv, false>(cg, st, m, k.off, k.dval, k.dinv, rhs, dx, k.t, nullptr,
                                                                       nullptr, nullptr, nullptr);
       HGKS_PROF_END(K_SPMV, st);
     }
@@ -868,18 +880,22 @@ void launch_assemble(const DevMesh &m, Scratch &s, const hgks_params &p, const d
   HGKS_PROF_BEGIN(K_ASSEMBLE, st);
   batch = batch || m.ptab;
   if (batch)
-    k_assemble<true><<<grid_for(m.NL, kCellBlock), kCellBlock, 0, st>>>(m, p, Q, dt, s.dval, s.dinv, s.off, diag_out,
-                                                                         off_out, dv32, di32, jv);
+    k_assemble<true, TetShape::NF><<<grid_for(m.NL, kCellBlock), kCellBlock, 0, st>>>(m, p, Q, dt, s.dval, s.dinv, s.off,
+                                                                                       diag_out, off_out, dv32, di32, jv);
+  else if (m.hex)
+    k_assemble<false, HexShape::NF><<<grid_for(m.N, kCellBlock), kCellBlock, 0, st>>>(m, p, Q, dt, s.dval, s.dinv, s.off,
+                                                                                       diag_out, off_out, dv32, di32, jv);
   else
-    k_assemble<false><<<grid_for(m.N, kCellBlock), kCellBlock, 0, st>>>(m, p, Q, dt, s.dval, s.dinv, s.off, diag_out,
-                                                                          off_out, dv32, di32, jv);
+    k_assemble<false, TetShape::NF><<<grid_for(m.N, kCellBlock), kCellBlock, 0, st>>>(m, p, Q, dt, s.dval, s.dinv, s.off,
+                                                                                       diag_out, off_out, dv32, di32, jv);
   HGKS_PROF_END(K_ASSEMBLE, st);
 }
 
 void launch_apply_A(const DevMesh &m, const Scratch &s, const double *x, double *y, cudaStream_t st) {
   HGKS_PROF_BEGIN(K_SPMV, st);
-  k_apply<double, double, double, kSpmv, false><<<grid_for(m.N, kCellBlock), kCellBlock, 0, st>>>(
-      m, s.off, s.dval, s.dinv, nullptr, x, y, nullptr, nullptr, nullptr, nullptr);
+  apply_launch<double, double, double, kSpmv, false>(grid_for(m.N, kCellBlock), st, m, s.off, s.dval, s.dinv,
+                                                     (const double *)nullptr, x, y, (const double *)nullptr,
+                                                     (double *)nullptr, nullptr, nullptr);
   HGKS_PROF_END(K_SPMV, st);
 }
 

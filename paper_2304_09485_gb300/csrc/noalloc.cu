@@ -53,6 +53,7 @@ extern "C" hgks_status hgks_residual_noalloc(hgks_mesh mesh, const hgks_params *
   p = &P;
   if (!Q || !R) return fail_msg(HGKS_ERR_ARG, "Q or R is NULL");
   if (p->scheme == HGKS_HWENO && (!G || !G_new)) return fail_msg(HGKS_ERR_ARG, "compact scheme needs G and G_new");
+  if (m.d.hex) return fail_msg(HGKS_ERR_ARG, "this entry point takes tetrahedral meshes only");
   const size_t need = noalloc_need((size_t)m.N, (size_t)m.F);
   if (need > kNoallocDoubles)
     return fail_msg(HGKS_ERR_ARG,

@@ -108,9 +108,11 @@ __device__ __forceinline__ bool live(const DevMesh &m, int i) {
 // One thread per (component, cell): P0's 9 coefficients over the big stencil, then
 // the four sub-stencils' 3 each over their six cells, whose differences the thread
 // keeps in shared memory (its own column) from the first pass.
-template <bool BATCH>
+template <bool BATCH, class S>
 __global__ void __launch_bounds__(kBlock) k_coef_weno(DevMesh m, const double *__restrict__ Q, double *__restrict__ coef) {
-  __shared__ double sdq[kBig][kBlock];
+  constexpr int BIG = S::BIG, SUBK = S::SUBK;
+  constexpr unsigned SLOTMASK = (1u << S::SLOTBITS) - 1u;
+  __shared__ double sdq[BIG][kBlock];
   const int N = m.N;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int NL = BATCH ? m.NL : N;
@@ -122,34 +124,35 @@ __global__ void __launch_bounds__(kBlock) k_coef_weno(DevMesh m, const double *_
 #pragma unroll
   for (int d = 0; d < 9; d++) a[d] = 0.0;
 #pragma unroll
-  for (int k = 0; k < kBig; k++) {
+  for (int k = 0; k < BIG; k++) {
     int j = m.sten[(size_t)k * N + i];
     if (j < 0) break;
     const double dq = Q[(size_t)c * N + j] - qi;
     sdq[k][threadIdx.x] = dq;
 #pragma unroll
-    for (int d = 0; d < 9; d++) a[d] = fma(m.X0[(size_t)(d * kBig + k) * N + i], dq, a[d]);
+    for (int d = 0; d < 9; d++) a[d] = fma(m.X0[(size_t)(d * BIG + k) * N + i], dq, a[d]);
   }
 #pragma unroll
   for (int d = 0; d < 9; d++) coef[(size_t)(d * 5 + c) * N + i] = a[d];
 #pragma unroll
-  for (int mm = 0; mm < 4; mm++) {
+  for (int mm = 0; mm < S::NSUBW; mm++) {
     const unsigned sl = m.ssl[(size_t)mm * N + i];
     double b[3] = {0.0, 0.0, 0.0};
 #pragma unroll
-    for (int s = 0; s < kSubK; s++) {
-      const double dq = sdq[(sl >> (4 * s)) & 15u][threadIdx.x];
+    for (int s = 0; s < SUBK; s++) {
+      const double dq = sdq[(sl >> (S::SLOTBITS * s)) & SLOTMASK][threadIdx.x];
 #pragma unroll
-      for (int j = 0; j < 3; j++) b[j] = fma(m.Xs[(size_t)((mm * 3 + j) * kSubK + s) * N + i], dq, b[j]);
+      for (int j = 0; j < 3; j++) b[j] = fma(m.Xs[(size_t)((mm * 3 + j) * SUBK + s) * N + i], dq, b[j]);
     }
 #pragma unroll
     for (int j = 0; j < 3; j++) coef[(size_t)(kCoefA + (mm * 3 + j) * 5 + c) * N + i] = b[j];
   }
 }
 
-template <bool BATCH>
+template <bool BATCH, class S>
 __global__ void __launch_bounds__(kBlock) k_coef_hweno(DevMesh m, const double *__restrict__ Q, const double *__restrict__ G,
                                                         double *__restrict__ coef) {
+  constexpr int NF = S::NF, HC = ShapeOf<S>::HCOLS;
   const int N = m.N;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int NL = BATCH ? m.NL : N;
@@ -157,29 +160,30 @@ __global__ void __launch_bounds__(kBlock) k_coef_hweno(DevMesh m, const double *
   const int c = t / NL, i = t - c * NL;
   if (BATCH && !live(m, i)) return;
   const double qi = Q[(size_t)c * N + i];
-  double data[19];
-  int nb[4];
+  double data[HC];
+  int nb[NF];
 #pragma unroll
-  for (int p = 0; p < 4; p++) {
+  for (int p = 0; p < NF; p++) {
     nb[p] = m.cnb[(size_t)p * N + i];
     data[p] = nb[p] >= 0 ? Q[(size_t)c * N + nb[p]] - qi : 0.0;
   }
 #pragma unroll
-  for (int j = 0; j < 3; j++) data[4 + j] = G[(size_t)(3 * c + j) * N + i];
+  for (int j = 0; j < 3; j++) data[NF + j] = G[(size_t)(3 * c + j) * N + i];
 #pragma unroll
-  for (int p = 0; p < 4; p++)
+  for (int p = 0; p < NF; p++)
 #pragma unroll
-    for (int j = 0; j < 3; j++) data[7 + 3 * p + j] = nb[p] >= 0 ? G[(size_t)(3 * c + j) * N + nb[p]] : 0.0;
+    for (int j = 0; j < 3; j++) data[NF + 3 + 3 * p + j] = nb[p] >= 0 ? G[(size_t)(3 * c + j) * N + nb[p]] : 0.0;
 #pragma unroll
   for (int d = 0; d < 9; d++) {
     double s = 0.0;
 #pragma unroll
-    for (int col = 0; col < 19; col++) s = fma(m.H0[(size_t)(d * 19 + col) * N + i], data[col], s);
+    for (int col = 0; col < HC; col++) s = fma(m.H0[(size_t)(d * HC + col) * N + i], data[col], s);
     coef[(size_t)(d * 5 + c) * N + i] = s;
   }
 #pragma unroll
-  for (int mm = 0; mm < 4; mm++) {
-    double dm[7] = {data[mm], data[4], data[5], data[6], data[7 + 3 * mm], data[8 + 3 * mm], data[9 + 3 * mm]};
+  for (int mm = 0; mm < NF; mm++) {
+    double dm[7] = {data[mm], data[NF], data[NF + 1], data[NF + 2], data[NF + 3 + 3 * mm], data[NF + 4 + 3 * mm],
+                    data[NF + 5 + 3 * mm]};
 #pragma unroll
     for (int j = 0; j < 3; j++) {
       double s = 0.0;
@@ -193,14 +197,15 @@ __global__ void __launch_bounds__(kBlock) k_coef_hweno(DevMesh m, const double *
 // ------------------------------------------------------------------------
 // 2. reconstruction at the Gauss points of one face, one side
 // ------------------------------------------------------------------------
-template <bool BATCH>
+template <bool BATCH, class S>
 __global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const double *__restrict__ Q,
                                                const double *__restrict__ coef, double *__restrict__ wface) {
+  constexpr int NF = S::NF, NG = S::NG, NSUB = ShapeOf<S>::NSUB;
   const int N = m.N, F = m.F;
   const int NL = BATCH ? m.NL : N;
-  // block b covers local face (b mod 4) of cell range b / 4: the four blocks of a
+  // block b covers local face (b mod NF) of cell range b / NF: the blocks of a
   // range run together and read its coefficients from L2 after the first
-  const int slot = blockIdx.x & 3, i = (blockIdx.x >> 2) * blockDim.x + threadIdx.x;
+  const int slot = blockIdx.x % NF, i = (blockIdx.x / NF) * blockDim.x + threadIdx.x;
   if (i >= NL) return;
   if (BATCH && !live(m, i)) return;                     // padding cell, or a mesh that has stopped
   const hgks_params &P = BATCH ? m.ptab[m.cmesh[i]] : Pv;
@@ -219,20 +224,20 @@ __global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const 
   rot_in(T, Qs, Qsl);
   const Eig e = eig_of(Qsl, P.gamma);
   const double ih = 1.0 / m.h[i];
-  double m2[6], xg[9];
+  double m2[6], xg[3 * NG];
 #pragma unroll
   for (int k = 0; k < 6; k++) m2[k] = m.m2[(size_t)k * N + i];
 #pragma unroll
-  for (int k = 0; k < 9; k++) xg[k] = m.xg[(size_t)(slot * 9 + k) * N + i];
-  // weights of the sub-stencils
-  unsigned valid = P.scheme == HGKS_WENO ? m.subvalid[i] : 0xFu;
+  for (int k = 0; k < 3 * NG; k++) xg[k] = m.xg[(size_t)(slot * 3 * NG + k) * N + i];
+  // weights of the sub-stencils (compact: one per face)
+  unsigned valid = P.scheme == HGKS_WENO ? m.subvalid[i] : (1u << NF) - 1u;
   const int M = __popc(valid);
   const double gm = P.lin_weight, g0 = M ? 1.0 - gm * M : 1.0;
   const double ig0 = 1.0 / g0, iM = M ? 1.0 / M : 0.0;
   double Th[9];                                         // face frame rows / h: scaled derivatives
 #pragma unroll
   for (int k = 0; k < 9; k++) Th[k] = ih * T[k];
-  double *out = wface + (size_t)side * 3 * kFaceState * F + f;
+  double *out = wface + (size_t)side * NG * kFaceState * F + f;
   for (int c = 0; c < 5; c++) {
     double mr[5];
     if (P.characteristic) {
@@ -248,7 +253,7 @@ __global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const 
     double q0 = 0.0;
 #pragma unroll
     for (int k = 0; k < 5; k++) q0 = fma(mr[k], Qi[k], q0);
-    double ac[9], bc[12];
+    double ac[9], bc[3 * NSUB];
 #pragma unroll
     for (int d = 0; d < 9; d++) {
       double s = 0.0;
@@ -257,7 +262,7 @@ __global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const 
       ac[d] = s;
     }
 #pragma unroll
-    for (int d = 0; d < 12; d++) {
+    for (int d = 0; d < 3 * NSUB; d++) {
       double s = 0.0;
 #pragma unroll
       for (int k = 0; k < 5; k++) s = fma(mr[k], coef[(size_t)(kCoefA + d * 5 + k) * N + i], s);
@@ -275,34 +280,38 @@ __global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const 
                          2.0 * fma(m2[3], S01, fma(m2[4], S02, m2[5] * S12));
     const double beta0 = fma(ac[0], ac[0], fma(ac[1], ac[1], ac[2] * ac[2])) + trMH2 +
                          ((s00 + s11 + s22) + (s01 + s02 + s12));
-    double kap0, kap[4];
+    double kap0, kap[NSUB];
     if (P.weights == HGKS_LINEAR || M == 0) {
       kap0 = 1.0;
 #pragma unroll
-      for (int mm = 0; mm < 4; mm++) kap[mm] = 0.0;
+      for (int mm = 0; mm < NSUB; mm++) kap[mm] = 0.0;
     } else {
-      double beta[4], tz = 0.0;
+      double beta[NSUB], tz = 0.0;
 #pragma unroll
-      for (int mm = 0; mm < 4; mm++) {
+      for (int mm = 0; mm < NSUB; mm++) {
         beta[mm] = bc[3 * mm] * bc[3 * mm] + bc[3 * mm + 1] * bc[3 * mm + 1] + bc[3 * mm + 2] * bc[3 * mm + 2];
         if (valid >> mm & 1) tz += fabs(beta0 - beta[mm]);
       }
       tz *= iM;
-      // 1 / (beta + eps) of the five stencils from one division (prefix products)
+      // 1 / (beta + eps) of all stencils from one division (prefix products
+      // pre[k] = d0 dm[0] ... dm[k-1], then back through them)
       const double d0 = beta0 + P.weno_eps;
-      double dm[4];
+      double dm[NSUB], pre[NSUB + 1];
 #pragma unroll
-      for (int mm = 0; mm < 4; mm++) dm[mm] = (valid >> mm & 1) ? beta[mm] + P.weno_eps : 1.0;
-      const double p1 = d0 * dm[0], p2 = p1 * dm[1], p3 = p2 * dm[2];
-      double inv = 1.0 / (p3 * dm[3]), r[4];
-      r[3] = inv * p3; inv *= dm[3];
-      r[2] = inv * p2; inv *= dm[2];
-      r[1] = inv * p1; inv *= dm[1];
-      r[0] = inv * d0;
-      const double r0 = inv * dm[0];
-      double w0 = g0 * fma(tz, r0, 1.0), w[4], sum = w0;
+      for (int mm = 0; mm < NSUB; mm++) dm[mm] = (valid >> mm & 1) ? beta[mm] + P.weno_eps : 1.0;
+      pre[0] = d0;
 #pragma unroll
-      for (int mm = 0; mm < 4; mm++) {
+      for (int mm = 0; mm < NSUB; mm++) pre[mm + 1] = pre[mm] * dm[mm];
+      double inv = 1.0 / pre[NSUB], r[NSUB];
+#pragma unroll
+      for (int mm = NSUB - 1; mm >= 0; mm--) {
+        r[mm] = inv * pre[mm];
+        inv *= dm[mm];
+      }
+      const double r0 = inv;
+      double w0 = g0 * fma(tz, r0, 1.0), w[NSUB], sum = w0;
+#pragma unroll
+      for (int mm = 0; mm < NSUB; mm++) {
         w[mm] = (valid >> mm & 1) ? gm * fma(tz, r[mm], 1.0) : 0.0;
         sum += w[mm];
       }
@@ -310,7 +319,7 @@ __global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const 
       double wb0 = w0 * is;
       kap0 = wb0 * ig0;
 #pragma unroll
-      for (int mm = 0; mm < 4; mm++) kap[mm] = (valid >> mm & 1) ? w[mm] * is - wb0 * gm * ig0 : 0.0;
+      for (int mm = 0; mm < NSUB; mm++) kap[mm] = (valid >> mm & 1) ? w[mm] * is - wb0 * gm * ig0 : 0.0;
     }
     // combined polynomial: Q = kap0 P0 + sum kap_m P_m (kap0 + sum kap_m = 1)
     double lin[3];
@@ -318,7 +327,7 @@ __global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const 
     for (int j = 0; j < 3; j++) {
       double s = kap0 * ac[j];
 #pragma unroll
-      for (int mm = 0; mm < 4; mm++) s = fma(kap[mm], bc[3 * mm + j], s);
+      for (int mm = 0; mm < NSUB; mm++) s = fma(kap[mm], bc[3 * mm + j], s);
       lin[j] = s;
     }
     double qd[6];
@@ -328,7 +337,7 @@ __global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const 
     // and the gradient share their partial sums
     const double q0m = q0 - (qd[0] * m2[0] + qd[1] * m2[1] + qd[2] * m2[2] + qd[3] * m2[3] + qd[4] * m2[4] + qd[5] * m2[5]);
 #pragma unroll
-    for (int g = 0; g < 3; g++) {
+    for (int g = 0; g < NG; g++) {
       const double x = xg[3 * g], y = xg[3 * g + 1], z = xg[3 * g + 2];
       const double ax = fma(qd[0], x, fma(qd[3], y, fma(qd[4], z, lin[0])));   // lin0 + qd0 x + qd3 y + qd4 z
       const double by = fma(qd[1], y, fma(qd[5], z, lin[1]));                  // lin1 + qd1 y + qd5 z
@@ -701,15 +710,16 @@ __device__ __forceinline__ bool physical(const double *W, double gamma) {
   return W[0] > 0.0 && rp > 0.0;
 }
 
-template <bool BATCH>
+template <bool BATCH, class S>
 __global__ void __launch_bounds__(256) k_flux(DevMesh m, hgks_params Pv, const double *__restrict__ Q,
                                                   const double *__restrict__ dt, const double *__restrict__ wface,
                                                   double *__restrict__ fflux, double *__restrict__ fpt, int *__restrict__ flags) {
+  constexpr int NG = S::NG;
   const int N = m.N, F = m.F;
   const int FL = BATCH ? m.FL : F;
-  // block b covers Gauss point (b mod 3) of face range b / 3: the three blocks of a
+  // block b covers Gauss point (b mod NG) of face range b / NG: the blocks of a
   // range run together and share the face's frame and cell states in L2
-  const int g = blockIdx.x % 3, f = (blockIdx.x / 3) * blockDim.x + threadIdx.x;
+  const int g = blockIdx.x % NG, f = (blockIdx.x / NG) * blockDim.x + threadIdx.x;
   if (f >= FL) return;
   if (BATCH && !m.mact[m.fmesh[f]]) return;             // a mesh of a batch that has stopped
   const hgks_params &P = BATCH ? m.ptab[m.fmesh[f]] : Pv;
@@ -730,7 +740,7 @@ __global__ void __launch_bounds__(256) k_flux(DevMesh m, hgks_params Pv, const d
   int bad = 0;
 #pragma unroll 1
   for (int s = 0; s < (R >= 0 ? 2 : 1); s++) {
-    const double *in = wface + ((size_t)(s * 3 + g) * kFaceState) * F + f;
+    const double *in = wface + ((size_t)(s * NG + g) * kFaceState) * F + f;
     double q[5];
 #pragma unroll
     for (int c = 0; c < 5; c++) q[c] = in[(size_t)c * F];
@@ -760,7 +770,8 @@ __global__ void __launch_bounds__(256) k_flux(DevMesh m, hgks_params Pv, const d
   // walls are impermeable: their faces carry momentum and energy, no mass
   if (R < 0 && m.ftag[f] >= HGKS_BC_WALL_ISO && m.ftag[f] <= HGKS_BC_NOSLIP_ADIA) Fl[0] = 0.0;
   if (bad) atomicAdd(flags, bad);
-  const double w = m.fS[f] * (1.0 / 3.0);
+  // Gauss weight times area: 1/3 on a triangle, the area-element weight on a quadrilateral
+  const double w = NG == 3 ? m.fS[f] * (1.0 / 3.0) : m.fS[f] * m.fw[(size_t)g * F + f];
   double Fg[5];
   rot_out(T, Fl, Fg);
 #pragma unroll
@@ -775,10 +786,11 @@ __global__ void __launch_bounds__(256) k_flux(DevMesh m, hgks_params Pv, const d
 // ------------------------------------------------------------------------
 // 4. face -> cell
 // ------------------------------------------------------------------------
-template <bool BATCH>
+template <bool BATCH, class S>
 __global__ void __launch_bounds__(kBlock) k_gather(DevMesh m, int compact, const double *__restrict__ fflux,
                                                     const double *__restrict__ fpt, double *__restrict__ R,
                                                     double *__restrict__ Gnew) {
+  constexpr int NF = S::NF, NG = S::NG;
   const int N = m.N, F = m.F;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -795,13 +807,15 @@ __global__ void __launch_bounds__(kBlock) k_gather(DevMesh m, int compact, const
 #pragma unroll
   for (int k = 0; k < 15; k++) gr[k] = 0.0;
 #pragma unroll
-  for (int p = 0; p < 4; p++) {
+  for (int p = 0; p < NF; p++) {
     const int cf = m.cface[(size_t)p * N + i];
     const int f = cf >> 1;
     const double sg = (cf & 1) ? 1.0 : -1.0;   // the flux leaves the left cell
 #pragma unroll
     for (int c = 0; c < 5; c++) {
-      double s = fflux[(size_t)c * F + f] + fflux[(size_t)(5 + c) * F + f] + fflux[(size_t)(10 + c) * F + f];
+      double s = fflux[(size_t)c * F + f];
+#pragma unroll
+      for (int g = 1; g < NG; g++) s += fflux[(size_t)(5 * g + c) * F + f];
       r[c] = fma(sg, s, r[c]);
     }
     if (compact) {
@@ -810,7 +824,9 @@ __global__ void __launch_bounds__(kBlock) k_gather(DevMesh m, int compact, const
       for (int d = 0; d < 3; d++) n[d] = -sg * m.fT[(size_t)d * F + f];   // outward normal of this cell
 #pragma unroll
       for (int c = 0; c < 5; c++) {
-        double s = fpt[(size_t)c * F + f] + fpt[(size_t)(5 + c) * F + f] + fpt[(size_t)(10 + c) * F + f];
+        double s = fpt[(size_t)c * F + f];
+#pragma unroll
+        for (int g = 1; g < NG; g++) s += fpt[(size_t)(5 * g + c) * F + f];
 #pragma unroll
         for (int d = 0; d < 3; d++) gr[3 * c + d] = fma(s, n[d], gr[3 * c + d]);
       }
@@ -825,7 +841,7 @@ __global__ void __launch_bounds__(kBlock) k_gather(DevMesh m, int compact, const
   }
 }
 
-template <bool BATCH>
+template <bool BATCH, class S>
 __global__ void k_local_dt(DevMesh m, hgks_params Pv, const double *__restrict__ Q, double *__restrict__ dt) {
   const int N = m.N, F = m.F;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -842,7 +858,7 @@ __global__ void k_local_dt(DevMesh m, hgks_params Pv, const double *__restrict__
   const double nu = P.viscous ? 2.0 * P.gamma * P.mu / (P.Pr * q[0] * m.h[i]) : 0.0;
   double s = 0.0;
 #pragma unroll
-  for (int k = 0; k < 4; k++) {
+  for (int k = 0; k < S::NF; k++) {
     const int f = m.cface[(size_t)k * N + i] >> 1;
     const double un = u * m.fT[f] + v * m.fT[(size_t)F + f] + w * m.fT[(size_t)2 * F + f];
     s += m.fS[f] * (fabs(un) + a + nu);
@@ -854,15 +870,14 @@ __global__ void k_local_dt(DevMesh m, hgks_params Pv, const double *__restrict__
 
 // force[3] = sum over the faces tagged `tag` of the momentum part of fflux ([3][5][F],
 // global frame, area included); one block, fixed summation order
-__global__ void __launch_bounds__(1024) k_wall_force(DevMesh m, int tag, const double *__restrict__ fflux,
+__global__ void __launch_bounds__(1024) k_wall_force(DevMesh m, int tag, int ng, const double *__restrict__ fflux,
                                                      double *__restrict__ force) {
   __shared__ double sh[3][1024];
   const int F = m.F;
   double acc[3] = {0.0, 0.0, 0.0};
   for (int f = threadIdx.x; f < F; f += blockDim.x) {
     if (m.fr[f] >= 0 || m.ftag[f] != tag) continue;
-#pragma unroll
-    for (int g = 0; g < 3; g++)
+    for (int g = 0; g < ng; g++)
 #pragma unroll
       for (int d = 0; d < 3; d++) acc[d] += fflux[(size_t)(5 * g + 1 + d) * F + f];
   }
@@ -882,48 +897,50 @@ __global__ void __launch_bounds__(1024) k_wall_force(DevMesh m, int tag, const d
 
 void launch_wall_force(const DevMesh &m, const Scratch &s, int tag, double *force_dev, cudaStream_t st) {
   HGKS_PROF_BEGIN(K_NORM, st);
-  k_wall_force<<<1, 1024, 0, st>>>(m, tag, s.fflux, force_dev);
+  k_wall_force<<<1, 1024, 0, st>>>(m, tag, m.hex ? HexShape::NG : TetShape::NG, s.fflux, force_dev);
   HGKS_PROF_END(K_NORM, st);
 }
 
 void launch_local_dt(const DevMesh &m, const hgks_params &p, const double *Q, double *dt, cudaStream_t st) {
   HGKS_PROF_BEGIN(K_DT, st);
-  if (m.ptab) k_local_dt<true><<<grid_for(m.NL, kBlock), kBlock, 0, st>>>(m, p, Q, dt);
-  else k_local_dt<false><<<grid_for(m.N, kBlock), kBlock, 0, st>>>(m, p, Q, dt);
+  if (m.ptab) k_local_dt<true, TetShape><<<grid_for(m.NL, kBlock), kBlock, 0, st>>>(m, p, Q, dt);
+  else if (m.hex) k_local_dt<false, HexShape><<<grid_for(m.N, kBlock), kBlock, 0, st>>>(m, p, Q, dt);
+  else k_local_dt<false, TetShape><<<grid_for(m.N, kBlock), kBlock, 0, st>>>(m, p, Q, dt);
   HGKS_PROF_END(K_DT, st);
 }
+
+namespace {
+// the four residual kernels of one cell kind; batches are tetrahedra only
+template <bool BATCH, class S>
+void residual_kernels(const DevMesh &m, Scratch &s, const hgks_params &p, const double *Q, const double *G, double *R,
+                      double *Gnew, cudaStream_t st) {
+  const int64_t NL = BATCH ? m.NL : m.N, FL = BATCH ? m.FL : m.F;
+  HGKS_PROF_BEGIN(K_COEF, st);
+  const unsigned gc = grid_for(5 * NL, kBlock);
+  if (p.scheme == HGKS_WENO) k_coef_weno<BATCH, S><<<gc, kBlock, 0, st>>>(m, Q, s.coef);
+  else k_coef_hweno<BATCH, S><<<gc, kBlock, 0, st>>>(m, Q, G, s.coef);
+  HGKS_PROF_END(K_COEF, st);
+  HGKS_PROF_BEGIN(K_RECON, st);
+  k_recon<BATCH, S><<<S::NF * grid_for(NL, s.blk_recon), s.blk_recon, 0, st>>>(m, p, Q, s.coef, s.wface);
+  HGKS_PROF_END(K_RECON, st);
+  HGKS_PROF_BEGIN(K_FLUX, st);
+  k_flux<BATCH, S><<<S::NG * grid_for(FL, s.blk_flux), s.blk_flux, 0, st>>>(m, p, Q, s.dt, s.wface, s.fflux, s.fpt, s.flags);
+  HGKS_PROF_END(K_FLUX, st);
+  HGKS_PROF_BEGIN(K_GATHER, st);
+  const int grad = p.scheme == HGKS_HWENO && Gnew != nullptr;   // gradients wanted
+  k_gather<BATCH, S><<<grid_for(NL, kBlock), kBlock, 0, st>>>(m, grad, s.fflux, s.fpt, R, Gnew);
+  HGKS_PROF_END(K_GATHER, st);
+}
+}  // namespace
 
 void launch_residual(const DevMesh &m, Scratch &s, const hgks_params &p, const double *Q, const double *G, double *R,
                      double *Gnew, cudaStream_t st, bool batch, bool fresh_dt) {
   HGKS_RANGE("hgks residual");
   batch = batch || m.ptab != nullptr;
   if (fresh_dt) launch_local_dt(m, p, Q, s.dt, st);
-  HGKS_PROF_BEGIN(K_COEF, st);
-  const int64_t NL = batch ? m.NL : m.N, FL = batch ? m.FL : m.F;
-  const unsigned gc = grid_for(5 * NL, kBlock);
-  if (p.scheme == HGKS_WENO) {
-    if (batch) k_coef_weno<true><<<gc, kBlock, 0, st>>>(m, Q, s.coef);
-    else k_coef_weno<false><<<gc, kBlock, 0, st>>>(m, Q, s.coef);
-  } else {
-    if (batch) k_coef_hweno<true><<<gc, kBlock, 0, st>>>(m, Q, G, s.coef);
-    else k_coef_hweno<false><<<gc, kBlock, 0, st>>>(m, Q, G, s.coef);
-  }
-  HGKS_PROF_END(K_COEF, st);
-  HGKS_PROF_BEGIN(K_RECON, st);
-  if (batch) k_recon<true><<<4 * grid_for(NL, s.blk_recon), s.blk_recon, 0, st>>>(m, p, Q, s.coef, s.wface);
-  else k_recon<false><<<4 * grid_for(m.N, s.blk_recon), s.blk_recon, 0, st>>>(m, p, Q, s.coef, s.wface);
-  HGKS_PROF_END(K_RECON, st);
-  HGKS_PROF_BEGIN(K_FLUX, st);
-  if (batch)
-    k_flux<true><<<3 * grid_for(FL, s.blk_flux), s.blk_flux, 0, st>>>(m, p, Q, s.dt, s.wface, s.fflux, s.fpt, s.flags);
-  else
-    k_flux<false><<<3 * grid_for(m.F, s.blk_flux), s.blk_flux, 0, st>>>(m, p, Q, s.dt, s.wface, s.fflux, s.fpt, s.flags);
-  HGKS_PROF_END(K_FLUX, st);
-  HGKS_PROF_BEGIN(K_GATHER, st);
-  const int grad = p.scheme == HGKS_HWENO && Gnew != nullptr;   // gradients wanted
-  if (batch) k_gather<true><<<grid_for(NL, kBlock), kBlock, 0, st>>>(m, grad, s.fflux, s.fpt, R, Gnew);
-  else k_gather<false><<<grid_for(m.N, kBlock), kBlock, 0, st>>>(m, grad, s.fflux, s.fpt, R, Gnew);
-  HGKS_PROF_END(K_GATHER, st);
+  if (batch) residual_kernels<true, TetShape>(m, s, p, Q, G, R, Gnew, st);
+  else if (m.hex) residual_kernels<false, HexShape>(m, s, p, Q, G, R, Gnew, st);
+  else residual_kernels<false, TetShape>(m, s, p, Q, G, R, Gnew, st);
 }
 
 }  // namespace hgks

@@ -94,7 +94,7 @@ void builder_loop(hgks_server_s *S) {
     std::string err;
     hgks_status st;
     try {
-      st = build_host_mesh(r->xyz.data(), (int64_t)r->xyz.size() / 3, r->tet.data(), (int64_t)r->tet.size() / 4,
+      st = build_host_mesh(r->xyz.data(), (int64_t)r->xyz.size() / 3, r->tet.data(), 4, (int64_t)r->tet.size() / 4,
                            r->bface.empty() ? nullptr : r->bface.data(), r->btag.empty() ? nullptr : r->btag.data(),
                            (int64_t)r->btag.size(), r->pshift.empty() ? nullptr : r->pshift.data(), r->nps, mask, r->hm,
                            err);

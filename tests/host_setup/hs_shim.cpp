@@ -24,7 +24,19 @@ extern "C" int hs_build(const double *xyz, int64_t nv, const int64_t *tet, int64
                         const int32_t *btag, int64_t nb, const double *pshift, int32_t nps, int scheme_mask,
                         int64_t *sizes) {
   g_hm = HostMesh{};
-  hgks_status st = build_host_mesh(xyz, nv, tet, nt, bface, btag, nb, pshift, nps, scheme_mask, g_hm, g_err);
+  hgks_status st = build_host_mesh(xyz, nv, tet, 4, nt, bface, btag, nb, pshift, nps, scheme_mask, g_hm, g_err);
+  sizes[0] = g_hm.N;
+  sizes[1] = g_hm.F;
+  sizes[2] = g_hm.Fb;
+  return (int)st;
+}
+
+// cells of nvc = 4 or 8 vertices (hexahedra: boundary quadrilaterals [nb][4])
+extern "C" int hs_build_cells(const double *xyz, int64_t nv, const int64_t *cells, int32_t nvc, int64_t nt,
+                              const int64_t *bface, const int32_t *btag, int64_t nb, const double *pshift,
+                              int32_t nps, int scheme_mask, int64_t *sizes) {
+  g_hm = HostMesh{};
+  hgks_status st = build_host_mesh(xyz, nv, cells, nvc, nt, bface, btag, nb, pshift, nps, scheme_mask, g_hm, g_err);
   sizes[0] = g_hm.N;
   sizes[1] = g_hm.F;
   sizes[2] = g_hm.Fb;
@@ -54,5 +66,7 @@ extern "C" int hs_get(const char *name, void *out, int64_t bytes) {
   if (n == "fr") return copy_out(g_hm.fr, out, bytes);
   if (n == "ssl") return copy_out(g_hm.ssl, out, bytes);
   if (n == "subvalid") return copy_out(g_hm.subvalid, out, bytes);
+  if (n == "fw") return copy_out(g_hm.fw, out, bytes);
+  if (n == "m2") return copy_out(g_hm.m2, out, bytes);
   return -2;
 }

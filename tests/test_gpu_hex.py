@@ -1,0 +1,240 @@
+"""Parity of the CUDA path with the FP64 oracle on hexahedral meshes (Sec. 3.1:
+six faces per cell, the eight non-compact sub-stencils of three face
+neighbours, one compact sub-stencil per face, 2 x 2 Gauss points per face).
+
+Tolerances are those of the tetrahedral parity tests: residual components
+against their flux scale sum_p S_p |F_Euler(Q_i) . n_p|, gradients against
+|Q_i| sum_p S_p / |Omega_i|, a step's update in relative L2.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2304_09485_gb300 as H
+from paper_2304_09485_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+GAMMA = 1.4
+TOL_R = 1e-11
+TOL_R_FLUX = 2e-12
+MIXED_DQ = 1e-4
+
+
+def face_sums(om, Q):
+    """Per cell: sum over its faces of S |F_Euler(Q_i) . n| (flux scale) and of S."""
+    fg = om.face_geometry()
+    rho = Q[:, 0]
+    u = Q[:, 1:4] / rho[:, None]
+    p = (GAMMA - 1) * (Q[:, 4] - 0.5 * rho * np.einsum("ij,ij->i", u, u))
+    scale, area = np.zeros_like(Q), np.zeros(len(Q))
+    for side in ("left", "right"):
+        c = fg[side]
+        ok = c >= 0
+        ci, n, S = c[ok], fg["normal"][ok], fg["area"][ok]
+        un = np.einsum("ij,ij->i", u[ci], n)
+        F = np.stack([rho[ci] * un, rho[ci] * u[ci, 0] * un + p[ci] * n[:, 0], rho[ci] * u[ci, 1] * un + p[ci] * n[:, 1],
+                      rho[ci] * u[ci, 2] * un + p[ci] * n[:, 2], (Q[ci, 4] + p[ci]) * un], -1)
+        np.add.at(scale, ci, S[:, None] * np.abs(F))
+        np.add.at(area, ci, S)
+    return scale, area / om.vol
+
+
+MESHES = {
+    "hexcav5": lambda: (I.hex_cavity_mesh(5, jitter=0.15), I.cavity_conditions()),
+    "hexper4": lambda: (I.hex_periodic_cube_mesh(4, jitter=0.15), I.sphere_conditions(0.3)),
+    "hextilt6": lambda: (I.hex_tilted_box_mesh(6), I.sphere_conditions(0.3)),
+}
+_cache = {}
+
+
+def setup(name):
+    if name not in _cache:
+        m, cond = MESHES[name]()
+        hm = H.hgks_mesh_create(m, scheme_mask=3)
+        assert H.hgks_mesh_info(hm).faces_per_cell == 6
+        _cache[name] = (m, cond, O.OracleMesh(m), hm)
+    return _cache[name]
+
+
+def state(m, cond, seed=1):
+    base = (cond["rho_inf"], cond["u_inf"][0] + 0.1, cond["u_inf"][1] + 0.05, -0.03, cond["p_inf"])
+    return I.smooth_state(m, seed=I.BASE_SEED + seed, amp=0.05, base=base)
+
+
+CASES = [
+    ("hexcav5", dict(scheme=0)), ("hexcav5", dict(scheme=1)),
+    ("hexcav5", dict(scheme=1, Pr=0.72)), ("hexcav5", dict(scheme=0, weights=1, Pr=0.72)),
+    ("hexper4", dict(scheme=0)), ("hexper4", dict(scheme=1, characteristic=0)),
+    ("hextilt6", dict(scheme=0)), ("hextilt6", dict(scheme=1, weights=1)),
+    ("hextilt6", dict(scheme=1, flux_dt=1e-3)),
+]
+
+
+@pytest.mark.parametrize("name,kw", CASES, ids=[f"{n}-{'-'.join(f'{k}{v}' for k, v in kw.items())}" for n, kw in CASES])
+def test_hex_residual_parity(cuda, name, kw):
+    import torch
+    m, cond, om, hm = setup(name)
+    Q, G = state(m, cond)
+    po = O.make_params(**{**cond, **kw})
+    ph = H.hgks_default_params(**{**cond, **kw})
+    out = om.residual(po, Q, G)
+    Ro, Go = (out if kw.get("scheme") == 1 else (out, None))
+    Qd, Gd = hm.to_internal(Q), hm.to_internal(G)
+    Rd, Gn = torch.empty_like(Qd), torch.empty_like(Gd)
+    H.hgks_residual(hm, ph, Qd, Gd if kw.get("scheme") == 1 else None, Rd, Gn if kw.get("scheme") == 1 else None)
+    torch.cuda.synchronize()
+    scale, aov = face_sums(om, Q)
+    err = np.abs(hm.to_caller(Rd) - Ro) / scale
+    assert err.max() <= TOL_R_FLUX, f"max rel err {err.max():.3e}"
+    if kw.get("scheme") == 1:
+        gs = np.repeat(np.abs(Q), 3, axis=1) * aov[:, None]
+        gerr = np.abs(hm.to_caller(Gn) - Go) / gs
+        assert gerr.max() <= TOL_R, f"gradient max rel err {gerr.max():.3e}"
+
+
+def test_hex_free_stream_on_gpu(cuda):
+    """A uniform state on the jittered periodic hexahedra: R = 0 and G_new = 0 to rounding."""
+    import torch
+    m, cond, om, hm = setup("hexper4")
+    Q = I.uniform_state(m.n_cells, rho=1.1, u=0.3, v=-0.2, w=0.1, p=0.9)
+    Qd, Gd = hm.to_internal(Q), hm.to_internal(np.zeros((m.n_cells, 15)))
+    Rd, Gn = torch.empty_like(Qd), torch.empty_like(Gd)
+    H.hgks_residual(hm, H.hgks_default_params(scheme=1), Qd, Gd, Rd, Gn)
+    torch.cuda.synchronize()
+    assert Rd.abs().max().item() <= 1e-13 and Gn.abs().max().item() <= 1e-12
+
+
+def test_hex_local_dt_and_jacobian_parity(cuda):
+    import torch
+    for name, kw in [("hexcav5", dict(scheme=1, Pr=0.72)), ("hextilt6", dict(scheme=0))]:
+        m, cond, om, hm = setup(name)
+        Q, _ = state(m, cond, seed=5)
+        po = O.make_params(**{**cond, **kw}); ph = H.hgks_default_params(**{**cond, **kw})
+        Qd = hm.to_internal(Q)
+        dtd = torch.empty(hm.n_cells, dtype=torch.float64, device="cuda")
+        H.hgks_local_dt(hm, ph, Qd, dtd)
+        dto = om.local_dt(po, Q)
+        np.testing.assert_allclose(dtd.cpu().numpy()[hm.inv], dto, rtol=1e-13)
+        diag = torch.empty(25, hm.n_cells, dtype=torch.float64, device="cuda")
+        off = torch.empty(150, hm.n_cells, dtype=torch.float64, device="cuda")
+        H.hgks_assemble(hm, ph, Qd, dtd, diag, off)
+        torch.cuda.synchronize()
+        Do, Oo = om.jacobian(po, Q, dto)
+        Dg = diag.cpu().numpy().T[hm.inv].reshape(-1, 5, 5)
+        Og = off.cpu().numpy().T[hm.inv].reshape(-1, 6, 5, 5)
+        dscale = np.abs(Do).max(axis=(1, 2))[:, None, None]
+        assert (np.abs(Dg - Do) / dscale).max() <= 1e-12
+        assert (np.abs(Og - Oo) / dscale[:, None]).max() <= 1e-12
+        x = np.random.default_rng(7).normal(size=Q.shape)
+        xd = hm.to_internal(x)
+        yd, zd = torch.empty_like(xd), torch.empty_like(xd)
+        H.hgks_apply_jacobian(hm, xd, yd)
+        H.hgks_precondition(hm, 2, xd, zd)
+        torch.cuda.synchronize()
+        yo = np.einsum("nij,nj->ni", Do, x)
+        nb = om.neighbours
+        for q in range(6):
+            ok = nb[:, q] >= 0
+            yo[ok] += np.einsum("nij,nj->ni", Oo[ok, q], x[nb[ok, q]])
+        ysc = np.abs(Do).max(axis=(1, 2))[:, None] * np.abs(x).max()
+        assert (np.abs(hm.to_caller(yd) - yo) / ysc).max() <= 1e-12
+        zo = om.precondition(Do, Oo, 2, x)
+        np.testing.assert_allclose(hm.to_caller(zd), zo, rtol=1e-10, atol=1e-12 * np.abs(zo).max())
+
+
+@pytest.mark.parametrize("name,kw", [("hexcav5", dict(scheme=1, Pr=0.72)), ("hextilt6", dict(scheme=0, krylov_dim=20)),
+                                     ("hexcav5", dict(scheme=0, Pr=0.72, jacobi_sweeps=1)),
+                                     ("hexcav5", dict(scheme=1, Pr=0.72, grad_relax=0.5))])
+def test_hex_gmres_step_parity(cuda, name, kw):
+    import torch
+    m, cond, om, hm = setup(name)
+    Q, G = state(m, cond, seed=9)
+    po = O.make_params(**{**cond, **kw}); ph = H.hgks_default_params(**{**cond, **kw})
+    Qo, Go, reso, dQo = om.gmres_step(po, Q, G)
+    Qd, Gd = hm.to_internal(Q), hm.to_internal(G)
+    dQd = torch.empty_like(Qd)
+    info = H.hgks_gmres_step(hm, ph, Qd, Gd if kw["scheme"] == 1 else None, dQd)
+    assert info.res_l1 == pytest.approx(reso, rel=1e-11)
+    rel = np.linalg.norm(hm.to_caller(dQd) - dQo) / np.linalg.norm(dQo)
+    assert rel <= 1e-9, rel
+    if kw["scheme"] == 1:
+        assert np.linalg.norm(hm.to_caller(Gd) - Go) / np.linalg.norm(Go) <= 1e-11
+    # the FP32 Krylov part: the same step to the mixed-precision tolerance
+    Qd, Gd = hm.to_internal(Q), hm.to_internal(G)
+    H.hgks_gmres_step(hm, H.hgks_default_params(**{**cond, **kw, "precision": 1}), Qd,
+                      Gd if kw["scheme"] == 1 else None, dQd)
+    rel32 = np.linalg.norm(hm.to_caller(dQd) - dQo) / np.linalg.norm(dQo)
+    assert rel32 <= MIXED_DQ, rel32
+
+
+def test_hex_steps_track_oracle(cuda):
+    """Five consecutive implicit steps of the lid-driven hexahedral cavity (compact)."""
+    m, cond, om, hm = setup("hexcav5")
+    kw = dict(scheme=1, Pr=0.72)
+    po = O.make_params(**{**cond, **kw}); ph = H.hgks_default_params(**{**cond, **kw})
+    Q = I.state_from_conditions(m.n_cells, cond); G = np.zeros((m.n_cells, 15))
+    Qd, Gd = hm.to_internal(Q), hm.to_internal(G)
+    for k in range(5):
+        Q, G, res, _ = om.gmres_step(po, Q, G)
+        info = H.hgks_gmres_step(hm, ph, Qd, Gd)
+        # the cavity starts at rest: the first residual is rounding only
+        assert info.res_l1 == pytest.approx(res, rel=1e-9, abs=1e-12)
+    assert np.linalg.norm(hm.to_caller(Qd) - Q) / np.linalg.norm(Q) <= 1e-9
+
+
+def test_hex_matrix_free_product(cuda):
+    """Eq. (frechet) on hexahedra: the GPU's product against the oracle's."""
+    import torch
+    m, cond, om, hm = setup("hextilt6")
+    kw = dict(scheme=1, jv_mode=1)
+    Q, G = state(m, cond, seed=13)
+    x = np.random.default_rng(I.BASE_SEED + 82).normal(size=Q.shape) * np.abs(Q).mean(0)
+    ph = H.hgks_default_params(**{**cond, **kw}); po = O.make_params(**{**cond, **kw})
+    dt = om.local_dt(po, Q)
+    Qd, Gd, xd = hm.to_internal(Q), hm.to_internal(G), hm.to_internal(x)
+    dtd = hm.to_internal(dt[:, None])[0].contiguous()
+    yd = torch.empty_like(Qd)
+    H.hgks_apply_jacobian_fd(hm, ph, Qd, Gd, dtd, xd, yd)
+    torch.cuda.synchronize()
+    yo, so = om.apply_fd(po, Q, G, dt, x)
+    scale, _ = face_sums(om, Q)
+    err = np.abs(hm.to_caller(yd) - yo) / (scale / so)
+    assert err.max() <= 2 * TOL_R, err.max()
+
+
+def test_hex_meshes_rejected_where_tetrahedra_only(cuda):
+    """The no-allocation residual and the batches take tetrahedra only: a hexahedral
+    mesh is refused with HGKS_ERR_ARG before any work."""
+    import torch
+    m, cond, om, hm = setup("hexcav5")
+    ph = H.hgks_default_params(**cond)
+    Qd = hm.to_internal(I.state_from_conditions(m.n_cells, cond))
+    with pytest.raises(H.HGKSError) as e:
+        H.hgks_residual_noalloc(hm, ph, Qd, None, torch.empty_like(Qd))
+    assert e.value.status == 1
+    with pytest.raises(H.HGKSError) as e:
+        H.hgks_batch_create([hm], [ph])
+    assert e.value.status == 1
+
+
+@pytest.mark.parametrize("scheme", [1, 0])
+def test_hex_cavity_solve_to_1e8_parity(cuda, scheme):
+    """Algorithm 1 to a 1e-8 drop on the 64-hexahedron lid-driven cavity (Ma 0.15,
+    Re 100, CFL 10; the oracle converges in 742 (compact) and 754 (non-compact)
+    steps): the same step count on the GPU, histories within 1e-8, states within 1e-9."""
+    m = I.hex_cavity_mesh(4, jitter=0.1)
+    cond = I.cavity_conditions()
+    om, hm = O.OracleMesh(m), H.hgks_mesh_create(m, scheme_mask=3)
+    kw = dict(scheme=scheme, Pr=0.72)
+    Q0 = I.state_from_conditions(m.n_cells, cond)
+    G0 = np.zeros((m.n_cells, 15))
+    Qo, _, hist_o, conv_o = om.solve_steady(O.make_params(**{**cond, **kw}), Q0, G0 if scheme else None,
+                                            drop=1e-8, max_steps=1000)
+    Qd, Gd = hm.to_internal(Q0), hm.to_internal(G0)
+    info, hist_g, conv_g = H.hgks_solve_steady(hm, H.hgks_default_params(**{**cond, **kw}), Qd,
+                                               Gd if scheme else None, drop_tol=1e-8, max_steps=1000)
+    assert conv_o and conv_g and info.steps > 500
+    assert info.steps == len(hist_o) - 1
+    np.testing.assert_allclose(hist_g, hist_o, rtol=1e-8, atol=1e-12 * hist_o.max())
+    assert np.linalg.norm(hm.to_caller(Qd) - Qo) / np.linalg.norm(Qo) <= 1e-9

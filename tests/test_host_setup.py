@@ -266,3 +266,179 @@ def test_stencils_gauss_points_and_face_geometry(shim):
         p_ = int(np.where(cface[:, L] >> 1 == f)[0][0])
         fc = cen[L] + h[L] * xg[p_, :, :, L].mean(0)
         assert fdist[f] == pytest.approx(2 * abs((fc - cen[L]) @ fT[0:3, f]), rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# hexahedral meshes (Sec. 3.1: six faces, eight corner sub-stencils)
+# ---------------------------------------------------------------------------
+
+HEX_CORNER = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0], [0, 0, 1], [1, 0, 1], [1, 1, 1], [0, 1, 1]])
+HEX_FACES = [[0, 1, 2, 3], [0, 1, 5, 4], [1, 2, 6, 5], [2, 3, 7, 6], [3, 0, 4, 7], [4, 5, 6, 7]]
+
+
+class BuiltHex(Built):
+    def __init__(self, L, m, mask=3):
+        xyz = np.ascontiguousarray(m.xyz, dtype=np.float64)
+        hx = np.ascontiguousarray(m.hex8, dtype=np.int64)
+        bf = np.ascontiguousarray(m.bface4, dtype=np.int64).reshape(-1, 4)
+        bt = np.ascontiguousarray(m.btag, dtype=np.int32)
+        ps = m.periodic_shift
+        psa = np.ascontiguousarray(ps if ps is not None else np.zeros((0, 3)), dtype=np.float64)
+        sizes = np.zeros(3, dtype=np.int64)
+        p = lambda a: a.ctypes.data_as(C.c_void_p)
+        rc = L.hs_build_cells(p(xyz), C.c_int64(len(xyz)), p(hx), C.c_int32(8), C.c_int64(len(hx)), p(bf), p(bt),
+                              C.c_int64(len(bt)), p(psa), C.c_int32(len(psa)), C.c_int(mask), p(sizes))
+        assert rc == 0, L.hs_error()
+        self.L, self.N, self.F, self.Fb = L, int(sizes[0]), int(sizes[1]), int(sizes[2])
+
+
+def hex_average(V, f, order=5):
+    """Cell averages of f and volumes of hexahedra V [n, 8, 3] by a tensor Gauss rule of the trilinear map."""
+    t, w = np.polynomial.legendre.leggauss(order)
+    t, w = 0.5 * (t + 1), 0.5 * w
+    acc, vol = 0.0, 0.0
+    sg = np.where(HEX_CORNER == 1, 1.0, -1.0)
+    for a, wa in zip(t, w):
+        for b, wb in zip(t, w):
+            for c, wc in zip(t, w):
+                r = np.array([a, b, c])
+                fr = np.where(HEX_CORNER == 1, r, 1 - r)
+                N = fr.prod(1)
+                dN = np.stack([sg[:, e] * np.prod(np.delete(fr, e, axis=1), axis=1) for e in range(3)], 1)
+                X = np.einsum("a,nad->nd", N, V)
+                dj = np.linalg.det(np.einsum("ae,nad->nde", dN, V)) * wa * wb * wc
+                acc = acc + dj[:, None] * f(X)
+                vol = vol + dj
+    return acc / vol[:, None], vol
+
+
+def test_hex_cell_order_and_face_table(shim):
+    m = I.hex_cavity_mesh(4, jitter=0.15)
+    b = BuiltHex(shim, m)
+    N, F = b.N, b.F
+    perm = b.get("perm", np.int64)
+    assert N == m.n_cells and np.array_equal(np.sort(perm), np.arange(N))
+    cen, vol = hex_average(m.xyz[m.hex8], lambda X: X)
+    np.testing.assert_allclose(b.get("vol", np.float64), vol[perm], rtol=1e-13)
+    assert b.Fb == len(m.btag) and 2 * F == 6 * N + b.Fb
+    cnb, cface = b.get("cnb", np.int32, 6), b.get("cface", np.int32, 6)
+    fl, fr = b.get("fl", np.int32, per="F"), b.get("fr", np.int32, per="F")
+    fT, fS, fw = b.get("fT", np.float64, 9, per="F"), b.get("fS", np.float64, per="F"), b.get("fw", np.float64, 4, per="F")
+    area_vec = np.zeros((N, 3))
+    for p_ in range(6):
+        f, side = cface[p_] >> 1, cface[p_] & 1
+        assert np.array_equal(np.where(side == 0, fl[f], fr[f]), np.arange(N))
+        assert np.array_equal(cnb[p_], np.where(side == 0, fr[f], fl[f]))
+        area_vec += (np.where(side == 0, 1.0, -1.0) * fS[f])[:, None] * fT[0:3, f].T
+    assert np.abs(area_vec).max() <= 1e-15
+    np.testing.assert_allclose(fw.sum(0), 1.0, rtol=0, atol=1e-15)
+    assert fS[fr < 0].sum() == pytest.approx(6.0, rel=1e-12)
+    inner = fr >= 0
+    d = cen[perm][fr[inner]] - cen[perm][fl[inner]]
+    assert np.all(np.einsum("ij,ji->i", d, fT[0:3, inner]) > 0)
+
+
+def test_hex_stencils_and_gauss_points(shim):
+    """Undistorted grid: an interior cell's big stencil holds its face neighbours and
+    theirs (24 cells), and its eight sub-stencils are the face-neighbour triples
+    across the cell's eight corners; Gauss points lie at the 2 x 2 points of the
+    bilinear face with the slot's neighbour, the same points seen from both sides."""
+    n = 5
+    m = I.hex_cavity_mesh(n, jitter=0.0)
+    b = BuiltHex(shim, m, mask=1)
+    N = b.N
+    perm = b.get("perm", np.int64)
+    cen = hex_average(m.xyz[m.hex8], lambda X: X)[0][perm]
+    hh = 1.0 / n
+    sten, ssl, valid = b.get("sten", np.int32, 24), b.get("ssl", np.uint32, 8), b.get("subvalid", np.uint8)
+    c = int(np.where(np.all((cen > 2 * hh) & (cen < 1 - 2 * hh), axis=1))[0][0])
+    got = [int(k) for k in sten[:, c] if k >= 0]
+    assert len(got) == 24
+    off = {tuple(np.rint((cen[k] - cen[c]) / hh).astype(int)) for k in got}
+    assert all(sum(abs(x) for x in o) in (1, 2) for o in off) and len(off) == 24
+    assert valid[c] == 0xFF
+    signs = set()
+    for mm in range(8):
+        cells = [got[(int(ssl[mm, c]) >> (8 * s)) & 255] for s in range(3)]
+        o = np.rint((cen[cells] - cen[c]) / hh).astype(int)
+        assert sorted(np.abs(o).sum(1)) == [1, 1, 1] and np.abs(o.sum(0)).tolist() == [1, 1, 1]
+        signs.add(tuple(o.sum(0)))
+    assert len(signs) == 8
+    # Gauss points, jittered mesh
+    mj = I.hex_cavity_mesh(3, jitter=0.15)
+    bj = BuiltHex(shim, mj, mask=1)
+    permj = bj.get("perm", np.int64)
+    cenj = hex_average(mj.xyz[mj.hex8], lambda X: X)[0][permj]
+    hj = bj.get("h", np.float64)
+    xg = bj.get("xg", np.float64, 72).reshape(6, 4, 3, bj.N)
+    cnb, cface = bj.get("cnb", np.int32, 6), bj.get("cface", np.int32, 6)
+    hexes = mj.hex8[permj]
+    gl, gh = 0.5 - 0.5 / np.sqrt(3), 0.5 + 0.5 / np.sqrt(3)
+    for i in range(bj.N):
+        for p_ in range(6):
+            X = cenj[i] + hj[i] * xg[p_, :, :, i]                   # [4 points, 3]
+            # the face: the quadrilateral of this cell whose bilinear 2 x 2 points are X
+            hit = 0
+            for F_ in HEX_FACES:
+                P = mj.xyz[hexes[i][F_]]
+                pts = np.array([(1 - s) * (1 - t) * P[0] + s * (1 - t) * P[1] + s * t * P[2] + (1 - s) * t * P[3]
+                                for s, t in ((gl, gl), (gh, gl), (gh, gh), (gl, gh))])
+                dist = np.linalg.norm(pts[:, None, :] - X[None, :, :], axis=2)
+                if np.all(dist.min(0) < 1e-12) and np.all(dist.min(1) < 1e-12):
+                    hit += 1
+                    if cnb[p_, i] >= 0:                                # shared with the slot's neighbour
+                        assert set(hexes[i][F_]) <= set(hexes[cnb[p_, i]])
+            assert hit == 1, (i, p_)
+
+
+def test_hex_fits_reproduce_quadratics_and_linear_fields(shim):
+    """Non-compact and compact fits on jittered hexahedra: exact coefficients of a
+    quadratic (cells with >= 3 face neighbours for the compact one), exact gradients
+    of a linear field for every sub-stencil in use."""
+    m = I.hex_cavity_mesh(5, jitter=0.15)
+    b = BuiltHex(shim, m, mask=3)
+    N = b.N
+    perm = b.get("perm", np.int64)
+    h = b.get("h", np.float64)
+    rng = np.random.default_rng(7)
+    f, grad, Hq = _quadratic(rng)
+    Qc, _ = hex_average(m.xyz[m.hex8], lambda X: f(X)[..., None])
+    Q = Qc[:, 0][perm]
+    cen = hex_average(m.xyz[m.hex8], lambda X: X)[0][perm]
+    ref = _scaled_coefficients(grad(cen), Hq, h)
+    sten, X0 = b.get("sten", np.int32, 24), b.get("X0", np.float64, 9 * 24)
+    dQ = np.where(sten >= 0, Q[np.maximum(sten, 0)] - Q[None, :], 0.0)
+    a = np.einsum("dkn,kn->nd", X0.reshape(9, 24, N), dQ)
+    np.testing.assert_allclose(a, ref, rtol=1e-8, atol=1e-10 * np.abs(ref).max())
+    gl = rng.normal(size=3)
+    Ql = hex_average(m.xyz[m.hex8], lambda X: (0.7 + X @ gl)[..., None])[0][:, 0][perm]
+    Xs, ssl, valid = b.get("Xs", np.float64, 8 * 3 * 3).reshape(8, 3, 3, N), b.get("ssl", np.uint32, 8), b.get("subvalid", np.uint8)
+    used = 0
+    for mm in range(8):
+        slots = np.stack([(ssl[mm] >> (8 * s)) & 255 for s in range(3)]).astype(np.int64)
+        cells = sten[slots, np.arange(N)[None, :]]
+        d = np.where(cells >= 0, Ql[np.maximum(cells, 0)] - Ql[None, :], 0.0)
+        bm = np.einsum("jsn,sn->nj", Xs[mm], d)
+        ok = (valid >> mm) & 1 == 1
+        used += int(ok.sum())
+        np.testing.assert_allclose(bm[ok], (h[:, None] * gl[None, :])[ok], rtol=1e-10, atol=1e-12)
+    assert used >= 3 * N
+    # compact: data = (dQ of slots 0..5, G_i, G of slots 0..5)
+    cnb = b.get("cnb", np.int32, 6)
+    H0, Hm = b.get("H0", np.float64, 9 * 27).reshape(9, 27, N), b.get("Hm", np.float64, 6 * 3 * 7).reshape(6, 3, 7, N)
+    G = grad(cen)
+    has = cnb >= 0
+    data = np.zeros((27, N))
+    data[0:6] = np.where(has, Q[np.maximum(cnb, 0)] - Q[None, :], 0.0)
+    data[6:9] = G.T
+    for p_ in range(6):
+        data[9 + 3 * p_:12 + 3 * p_] = np.where(has[p_][None, :], G[np.maximum(cnb[p_], 0)].T, 0.0)
+    a = np.einsum("dcn,cn->nd", H0, data)
+    full = has.sum(0) >= 3
+    np.testing.assert_allclose(a[full], ref[full], rtol=1e-8, atol=1e-10 * np.abs(ref).max())
+    for mm in range(6):
+        d = np.zeros((7, N))
+        d[0] = np.where(has[mm], Ql[np.maximum(cnb[mm], 0)] - Ql, 0.0)
+        d[1:4] = gl[:, None]
+        d[4:7] = np.where(has[mm][None, :], gl[:, None], 0.0)
+        np.testing.assert_allclose(np.einsum("jcn,cn->nj", Hm[mm], d), h[:, None] * gl[None, :], rtol=1e-10, atol=1e-12)
