@@ -557,7 +557,8 @@ def run_serve(args, rank, world):
     torch.cuda.set_device(local)
     reqs = I.serving_requests(args.serve_requests, n_min=args.serve_min_tets, n_max=args.serve_max_tets,
                               rate=args.serve_rate, seed=I.BASE_SEED + 500 + 1000 * rank,
-                              viscous_fraction=args.serve_viscous_fraction)
+                              viscous_fraction=args.serve_viscous_fraction,
+                              cavity_fraction=args.serve_cavity_fraction)
     kw = dict(scheme=0, krylov_dim=10, restarts=3, jacobi_sweeps=2)
     drop, max_steps = args.serve_drop, args.serve_max_steps
     for r in reqs:
@@ -634,10 +635,13 @@ def run_serve(args, rank, world):
            "n_gpus": world, "steps": len(reqs), "warmup": 0, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
            "config": {"workload": f"{len(reqs)} steady-solve requests, Poisson arrivals at {args.serve_rate}/s, "
-                                  f"spheres of {min(r['n_cells'] for r in reqs)}-{max(r['n_cells'] for r in reqs)} tets, "
+                                  f"meshes of {min(r['n_cells'] for r in reqs)}-{max(r['n_cells'] for r in reqs)} tets: "
+                                  f"a fraction {args.serve_cavity_fraction} lid-driven cavities (lid Mach U(0.2,0.5), "
+                                  f"Re logU(50,1000)), the rest spheres, "
                                   f"inviscid (Mach U(0.2,0.5), AoA U(0,10)) and a fraction {args.serve_viscous_fraction} "
                                   f"viscous (Re logU(50,1000)), "
                                   f"WENO, GMRES(10)x3, Jacobi 2, CFL 10, drop {drop:g}, max {max_steps} steps",
+                      "kinds": {k: sum(r["kind"] == k for r in reqs) for k in sorted({r["kind"] for r in reqs})},
                       "hbm_budget_gb": args.serve_budget_gb, "arena_cells": int(info.n_cells),
                       "arena_gb": info.device_bytes / 1e9},
            "served_mixed": {"solves_per_hour": 3600.0 * len(conv_a) / span_a,
@@ -657,6 +661,9 @@ def run_serve(args, rank, world):
                                "p99_ttc_converged_s": pct(conv_b, 99), "span_s": span_b,
                                "mean_steps": float(np.mean([s["steps"] for s in seq if s["steps"] >= 0])),
                                "mean_service_s": float(np.mean([s["service"] for s in seq]))},
+           "requests": [{"kind": r["kind"], "n_cells": r["n_cells"], "served_steps": a["steps"],
+                         "served_converged": a["converged"], "sequential_steps": b["steps"],
+                         "sequential_converged": b["converged"]} for r, a, b in zip(reqs, served, seq)],
            "clocks": clk}
     print(json.dumps(res))
     return 0
@@ -680,6 +687,8 @@ def main():
     ap.add_argument("--serve-min-tets", type=float, default=30e3)
     ap.add_argument("--serve-max-tets", type=float, default=250e3)
     ap.add_argument("--serve-viscous-fraction", type=float, default=0.5)
+    ap.add_argument("--serve-cavity-fraction", type=float, default=0.0,
+                    help="serve workload: fraction of lid-driven cavity requests (the rest spheres)")
     ap.add_argument("--serve-drop", type=float, default=1e-2)
     ap.add_argument("--serve-max-steps", type=int, default=500)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)

@@ -580,20 +580,30 @@ def batch_problems(n_problems: int = 48, n_min: float = 20e3, n_max: float = 500
 
 
 def serving_requests(n_requests: int = 24, n_min: float = 30e3, n_max: float = 250e3, rate: float = 1.0,
-                     seed: int = BASE_SEED + 500, viscous_fraction: float = 0.5):
-    """Steady-solve requests with Poisson arrivals (exponential gaps of mean 1/rate s):
-    half inviscid spheres (Mach ~ U(0.2, 0.5), angle of attack ~ U(0, 10) deg), half
-    viscous spheres (Mach ~ U(0.2, 0.5), Re ~ log-uniform in [50, 1000]); N ~
-    log-uniform in [n_min, n_max] tets (patches n = (N/72)^(1/3), 2n layers).
-    Returns dicts: arrival (s), kind, mesh, cond, n_cells."""
+                     seed: int = BASE_SEED + 500, viscous_fraction: float = 0.5, cavity_fraction: float = 0.0):
+    """Steady-solve requests with Poisson arrivals (exponential gaps of mean 1/rate s).
+    A fraction `cavity_fraction` are lid-driven cavities (Mach ~ U(0.2, 0.5) of the
+    lid, Re ~ log-uniform in [50, 1000], n = (N/6)^(1/3) Kuhn-split hexahedra a
+    side); the rest are spheres, inviscid (Mach ~ U(0.2, 0.5), angle of attack ~
+    U(0, 10) deg) or, a fraction `viscous_fraction` of them, viscous (Mach ~ U(0.2,
+    0.5), Re ~ log-uniform in [50, 1000]); N ~ log-uniform in [n_min, n_max] tets
+    (sphere patches n = (N/72)^(1/3), 2n layers). With cavity_fraction 0 the draws
+    are those of the sphere-only stream. Returns dicts: arrival (s), kind, mesh,
+    cond, n_cells."""
     rng = np.random.default_rng(seed)
     t = 0.0
     out = []
     for k in range(n_requests):
         t += rng.exponential(1.0 / rate)
         N = math.exp(rng.uniform(math.log(n_min), math.log(n_max)))
-        n = max(2, int(round((N / 72.0) ** (1.0 / 3.0))))
         mach = rng.uniform(0.2, 0.5)
+        if cavity_fraction > 0.0 and rng.random() < cavity_fraction:
+            kind = "cavity"
+            cond = cavity_conditions(mach, math.exp(rng.uniform(math.log(50.0), math.log(1000.0))))
+            mesh = cavity_mesh(max(2, int(round((N / 6.0) ** (1.0 / 3.0)))), seed=seed + 1 + k)
+            out.append(dict(arrival=t, kind=kind, mesh=mesh, cond=cond, n_cells=mesh.n_tet))
+            continue
+        n = max(2, int(round((N / 72.0) ** (1.0 / 3.0))))
         if rng.random() < 1.0 - viscous_fraction:
             kind = "inviscid sphere"
             cond = sphere_conditions(mach, None, aoa_deg=rng.uniform(0.0, 10.0))
