@@ -98,3 +98,35 @@ def test_generators_are_deterministic():
     Q1, G1 = I.smooth_state(a)
     Q2, G2 = I.smooth_state(b)
     assert np.array_equal(Q1, Q2) and np.array_equal(G1, G2)
+
+
+def test_serving_stream_with_cavities():
+    """The cavity fraction adds lid-driven cavities to the request stream; with
+    fraction 0 the stream is the sphere-only one, draw for draw."""
+    a = I.serving_requests(12, n_min=50e3, n_max=150e3, rate=0.05)
+    b = I.serving_requests(12, n_min=50e3, n_max=150e3, rate=0.05, cavity_fraction=0.0)
+    assert [(r["kind"], r["n_cells"], r["arrival"]) for r in a] == [(r["kind"], r["n_cells"], r["arrival"]) for r in b]
+    c = I.serving_requests(40, n_min=50e3, n_max=150e3, rate=0.05, cavity_fraction=0.5)
+    kinds = [r["kind"] for r in c]
+    assert 10 <= kinds.count("cavity") <= 30
+    for r in c:
+        if r["kind"] == "cavity":
+            assert r["cond"]["lid_speed"] == 1.0 and r["cond"]["viscous"] == 1
+            assert 40e3 <= r["n_cells"] <= 190e3 and r["n_cells"] % 6 == 0
+            assert 50.0 <= 1.0 / r["cond"]["mu"] <= 1000.0
+
+
+def test_hex_generators():
+    """Hexahedra are positively oriented; boundary quadrilaterals cover the box
+    surface; the tilted-plane cells have planar faces."""
+    for m in (I.hex_cavity_mesh(4), I.hex_tilted_box_mesh(4), I.hex_periodic_cube_mesh(3)):
+        x = m.xyz[m.hex8]
+        assert np.all(np.einsum("ij,ij->i", np.cross(x[:, 1] - x[:, 0], x[:, 3] - x[:, 0]), x[:, 4] - x[:, 0]) > 0)
+        assert len(np.unique(m.hex8)) == len(m.xyz)
+    m = I.hex_cavity_mesh(4)
+    assert m.bface4.shape == (6 * 16, 4) and np.all(m.btag[m.btag != I.BC_WALL_LID] == I.BC_WALL_ISO)
+    t = I.hex_tilted_box_mesh(5)
+    for F in ([0, 1, 2, 3], [0, 1, 5, 4], [1, 2, 6, 5], [2, 3, 7, 6], [3, 0, 4, 7], [4, 5, 6, 7]):
+        P = t.xyz[t.hex8][:, F]
+        n = np.cross(P[:, 2] - P[:, 0], P[:, 3] - P[:, 1])
+        assert np.abs(np.einsum("ij,ij->i", n, P[:, 1] - P[:, 0])).max() <= 1e-14
