@@ -400,10 +400,11 @@ def run_precision(args, rank, world):
     ~995k tets, adiabatic no-slip wall), compact HWENO, CFL 20. The same steps
     in FP64 and with the FP32 Krylov part, from the free stream: density
     residual history, drag coefficient every few steps, state difference, time
-    per step. The compact scheme does not reach a steady state on these
-    tetrahedral sphere grids (its gradient update settles into a two-step cycle
-    in the wall layer), so C_D is reported over the last steps as the mean and
-    the spread of that cycle. The comparison with the oracle on a scaled-down
+    per step. With Algorithm 1's gradient update the compact solve settles into
+    a two-step cycle at the separation line on these tetrahedral sphere grids,
+    so C_D is reported over the last steps as the mean and the spread; with
+    --grad-relax 0.5 the cycle is damped and the solve keeps converging. The
+    comparison with the oracle on a scaled-down
     sphere of the same construction is a GPU test
     (tests/test_gpu_precision.py)."""
     import torch
