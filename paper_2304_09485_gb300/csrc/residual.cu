@@ -253,7 +253,12 @@ __global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const 
     double q0 = 0.0;
 #pragma unroll
     for (int k = 0; k < 5; k++) q0 = fma(mr[k], Qi[k], q0);
-    double ac[9], bc[3 * NSUB];
+    // Sub-stencil coefficients in characteristic variables: tetrahedra (4 sub-
+    // stencils) keep all of them in registers; with 8 the arrays would go to local
+    // memory, so hexahedra form them where they are used (twice) from the
+    // coefficients, which the thread has just read (L1).
+    constexpr bool kHold = NSUB <= 4;
+    double ac[9], bc[kHold ? 3 * NSUB : 1];
 #pragma unroll
     for (int d = 0; d < 9; d++) {
       double s = 0.0;
@@ -261,13 +266,29 @@ __global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const 
       for (int k = 0; k < 5; k++) s = fma(mr[k], coef[(size_t)(d * 5 + k) * N + i], s);
       ac[d] = s;
     }
+    if constexpr (kHold) {
 #pragma unroll
-    for (int d = 0; d < 3 * NSUB; d++) {
-      double s = 0.0;
+      for (int d = 0; d < 3 * NSUB; d++) {
+        double s = 0.0;
 #pragma unroll
-      for (int k = 0; k < 5; k++) s = fma(mr[k], coef[(size_t)(kCoefA + d * 5 + k) * N + i], s);
-      bc[d] = s;
+        for (int k = 0; k < 5; k++) s = fma(mr[k], coef[(size_t)(kCoefA + d * 5 + k) * N + i], s);
+        bc[d] = s;
+      }
     }
+    auto sub_coef = [&](int mm, double *b3) {
+      if constexpr (kHold) {
+#pragma unroll
+        for (int j = 0; j < 3; j++) b3[j] = bc[3 * mm + j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+          double s = 0.0;
+#pragma unroll
+          for (int k = 0; k < 5; k++) s = fma(mr[k], coef[(size_t)(kCoefA + (3 * mm + j) * 5 + k) * N + i], s);
+          b3[j] = s;
+        }
+      }
+    };
     // smoothness indicators in the scaled frame: beta_0 = avg |grad P0|^2 + sum of squared second derivatives
     const double H00 = 2.0 * ac[3], H11 = 2.0 * ac[4], H22 = 2.0 * ac[5], H01 = ac[6], H02 = ac[7], H12 = ac[8];
     // avg |grad P0|^2 = |a|^2 + tr(M2 H^2) (M2: second moments, H symmetric)
@@ -289,7 +310,9 @@ __global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const 
       double beta[NSUB], tz = 0.0;
 #pragma unroll
       for (int mm = 0; mm < NSUB; mm++) {
-        beta[mm] = bc[3 * mm] * bc[3 * mm] + bc[3 * mm + 1] * bc[3 * mm + 1] + bc[3 * mm + 2] * bc[3 * mm + 2];
+        double b3[3];
+        sub_coef(mm, b3);
+        beta[mm] = b3[0] * b3[0] + b3[1] * b3[1] + b3[2] * b3[2];
         if (valid >> mm & 1) tz += fabs(beta0 - beta[mm]);
       }
       tz *= iM;
@@ -323,12 +346,26 @@ __global__ void __launch_bounds__(256) k_recon(DevMesh m, hgks_params Pv, const 
     }
     // combined polynomial: Q = kap0 P0 + sum kap_m P_m (kap0 + sum kap_m = 1)
     double lin[3];
+    if constexpr (kHold) {
 #pragma unroll
-    for (int j = 0; j < 3; j++) {
-      double s = kap0 * ac[j];
+      for (int j = 0; j < 3; j++) {
+        double s = kap0 * ac[j];
 #pragma unroll
-      for (int mm = 0; mm < NSUB; mm++) s = fma(kap[mm], bc[3 * mm + j], s);
-      lin[j] = s;
+        for (int mm = 0; mm < NSUB; mm++) s = fma(kap[mm], bc[3 * mm + j], s);
+        lin[j] = s;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 3; j++) lin[j] = kap0 * ac[j];
+      if (kap0 != 1.0 || P.weights != HGKS_LINEAR) {
+#pragma unroll
+        for (int mm = 0; mm < NSUB; mm++) {
+          double b3[3];
+          sub_coef(mm, b3);
+#pragma unroll
+          for (int j = 0; j < 3; j++) lin[j] = fma(kap[mm], b3[j], lin[j]);
+        }
+      }
     }
     double qd[6];
 #pragma unroll
