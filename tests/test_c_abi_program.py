@@ -45,9 +45,10 @@ def test_c_program_compiles_against_the_header(tmp_path):
 
 
 @pytest.mark.gpu
-def test_c_program_matches_the_python_binding(cuda, tmp_path):
+@pytest.mark.parametrize("cells", ["tetrahedra", "hexahedra"])
+def test_c_program_matches_the_python_binding(cuda, tmp_path, cells):
     import torch
-    m = I.cavity_mesh(4)
+    m = I.cavity_mesh(4) if cells == "tetrahedra" else I.hex_cavity_mesh(5)
     cond = I.cavity_conditions(0.2, 100.0)
     p = H.hgks_default_params(scheme=0, Pr=0.72, krylov_dim=8, restarts=2, **cond)
     # the C caller states the problem as the paper does (Mach of the lid, Re) and
@@ -57,10 +58,11 @@ def test_c_program_matches_the_python_binding(cuda, tmp_path):
     Q, _ = I.smooth_state(m, seed=I.BASE_SEED + 99, amp=0.03, base=(1.0, 0.05, 0.02, -0.01, cond["p_inf"]))
     src = tmp_path / "in.bin"
     with open(src, "wb") as f:
-        np.array([m.xyz.shape[0], m.n_tet, m.bface3.shape[0]], dtype=np.int64).tofile(f)
+        bface = m.bface4 if cells == "hexahedra" else m.bface3
+        np.array([m.xyz.shape[0], m.n_cells, bface.shape[0], m.cells.shape[1]], dtype=np.int64).tofile(f)
         np.ascontiguousarray(m.xyz, dtype=np.float64).tofile(f)
-        np.ascontiguousarray(m.tet4, dtype=np.int64).tofile(f)
-        np.ascontiguousarray(m.bface3, dtype=np.int64).tofile(f)
+        np.ascontiguousarray(m.cells, dtype=np.int64).tofile(f)
+        np.ascontiguousarray(bface, dtype=np.int64).tofile(f)
         np.ascontiguousarray(m.btag, dtype=np.int32).tofile(f)
         f.write(bytes(pc))
         np.ascontiguousarray(Q, dtype=np.float64).tofile(f)
@@ -69,7 +71,7 @@ def test_c_program_matches_the_python_binding(cuda, tmp_path):
     r = subprocess.run([exe, str(src), str(dst)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     out = np.fromfile(dst, dtype=np.float64)
-    n5 = 5 * m.n_tet
+    n5 = 5 * m.n_cells
     Rc, Qc, res_c = out[:n5].reshape(-1, 5), out[n5:2 * n5].reshape(-1, 5), out[2 * n5]
     hm = H.hgks_mesh_create(m, scheme_mask=1)
     Qd = hm.to_internal(Q)
