@@ -135,6 +135,119 @@ __global__ void __launch_bounds__(kB) k_baxpy_dot(int N, BatchDev bd, T *__restr
   mesh_sum(s, bd, part, out, stride, self);
 }
 
+// ---- modified Gram-Schmidt from one pass over the basis (FP32 vectors) ----
+// As the single-mesh path: with a_k = (w, v_k) and the basis Gram matrix
+// G_ki = (v_k, v_i), Algorithm 1's MGS coefficients are h_i = a_i - sum_{k<i} h_k G_ki,
+// so per Arnoldi step the batch takes a and the new Gram row from one pass
+// (kBatchMdot basis vectors per launch, per-mesh sums), solves for h per mesh
+// and subtracts sum h_i v_i in MGS order in one more pass with ||w||.
+
+// a(mesh)[k] = (w, v_k) for k in [k0, k0 + nk), g(mesh)[k] = (v_j, v_k) for those k < j
+template <typename T>
+__global__ void __launch_bounds__(kB) k_bmdot(int N, BatchDev bd, const T *__restrict__ w, const T *__restrict__ V,
+                                              int64_t vs, int k0, int nk, int j, T *part, double *hs, int hz, int aoff,
+                                              int goff) {
+  const int i = blockIdx.x * kB + threadIdx.x;
+  const int mesh = bd.bmesh[blockIdx.x];
+  if (!bd.active[mesh]) return;
+  T sa[kBatchMdot], sg[kBatchMdot];
+#pragma unroll
+  for (int q = 0; q < kBatchMdot; q++) { sa[q] = T(0); sg[q] = T(0); }
+#pragma unroll
+  for (int c = 0; c < 5; c++) {
+    const size_t k = (size_t)c * N + i;
+    const T wk = w[k], vj = V[(size_t)j * vs + k];
+#pragma unroll
+    for (int q = 0; q < kBatchMdot; q++)
+      if (q < nk) {
+        const T vk = V[(size_t)(k0 + q) * vs + k];
+        sa[q] = fma(wk, vk, sa[q]);
+        if (k0 + q < j) sg[q] = fma(vj, vk, sg[q]);
+      }
+  }
+  // per block 2 kBatchMdot partials (each warp reduces all of its sums by shuffles,
+  // then one thread per sum adds the warps' values in warp order); the mesh's last
+  // block adds each slot's partials in block order
+  const int nb = gridDim.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ T wsum[2 * kBatchMdot][kB / 32];
+  __shared__ bool last;
+#pragma unroll
+  for (int q = 0; q < 2 * kBatchMdot; q++) {
+    T v = q < kBatchMdot ? sa[q] : sg[q - kBatchMdot];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) wsum[q][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * kBatchMdot) {
+    T v = T(0);
+#pragma unroll
+    for (int q = 0; q < kB / 32; q++) v += wsum[threadIdx.x][q];
+    part[(size_t)threadIdx.x * nb + blockIdx.x] = v;
+    __threadfence();                       // visible to the mesh's last block
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(bd.counters + mesh, 1u);
+    last = (prev == (unsigned)(bd.bcount[mesh] - 1));
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double *rec = hs + (size_t)mesh * hz;
+  const int b0 = bd.bstart[mesh], b1 = b0 + bd.bcount[mesh];
+  for (int q = 0; q < 2 * kBatchMdot; q++) {
+    const int kk = k0 + (q % kBatchMdot);
+    const bool want = (q % kBatchMdot) < nk && (q < kBatchMdot || kk < j);   // uniform over the block
+    if (!want) continue;
+    T sum = T(0);
+    for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x) sum += ((volatile T *)part)[(size_t)q * nb + b];
+    sum = bsum(sum);
+    if (threadIdx.x == 0) rec[(q < kBatchMdot ? aoff : goff) + kk] = (double)sum;
+  }
+  if (threadIdx.x == 0) bd.counters[mesh] = 0u;
+}
+
+// one thread per mesh: row j of the Gram matrix from g, then h_ij by forward substitution
+__global__ void k_bmgs_coef(BatchDev bd, int j, int mk, double *__restrict__ hs, int hz, int aoff, int goff,
+                            int gram_off) {
+  const int mesh = blockIdx.x * blockDim.x + threadIdx.x;
+  if (mesh >= bd.nmesh || !bd.active[mesh]) return;
+  double *rec = hs + (size_t)mesh * hz, *G = rec + gram_off;
+  const double *a = rec + aoff, *g = rec + goff;
+  const int ld = mk + 1;
+  for (int k = 0; k < j; k++) G[k * ld + j] = g[k];
+  for (int i = 0; i <= j; i++) {
+    double h = a[i];
+    for (int k = 0; k < i; k++) h -= rec[k * mk + j] * G[k * ld + i];
+    rec[i * mk + j] = h;
+  }
+}
+
+// w -= sum_{k <= j} h_kj(mesh) v_k in the order of k, then h_{j+1,j}(mesh) = ||w||
+template <typename T>
+__global__ void __launch_bounds__(kB) k_bmupdate(int N, BatchDev bd, T *__restrict__ w, const T *__restrict__ V,
+                                                 int64_t vs, int j, int mk, double *hs, int hz, T *part) {
+  const int i = blockIdx.x * kB + threadIdx.x;
+  const int mesh = bd.bmesh[blockIdx.x];
+  if (!bd.active[mesh]) return;
+  __shared__ T nh[65];
+  const double *rec = hs + (size_t)mesh * hz;
+  for (int k = threadIdx.x; k <= j; k += blockDim.x) nh[k] = (T)(-rec[k * mk + j]);
+  __syncthreads();
+  T s = T(0);
+#pragma unroll
+  for (int c = 0; c < 5; c++) {
+    const size_t k = (size_t)c * N + i;
+    T wk = w[k];
+    for (int q = 0; q <= j; q++) wk = fma(nh[q], V[(size_t)q * vs + k], wk);
+    w[k] = wk;
+    s = fma(wk, wk, s);
+  }
+  mesh_sum(s, bd, part, hs + (size_t)(j + 1) * mk + j, hz, 1);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kB) k_bscale(int N, BatchDev bd, const T *__restrict__ w, const double *__restrict__ h,
                                                int hstride, T *__restrict__ v) {
@@ -331,9 +444,27 @@ void bgmres_t(const DevMesh &m, Scratch &s, BatchState &bs, const BBuf<T> &k, co
     HGKS_PROF_BEGIN(K_SCALE, st);
     k_bscale<T><<<g, kB, 0, st>>>(N, bs.b, k.w, beta, hz, k.V);
     HGKS_PROF_END(K_SCALE, st);
+    // FP32 vectors: MGS from one pass over the basis (HBM bound, about half the
+    // bytes); FP64 vectors: one basis vector per pass (bound by the FP64 rate either way)
+    constexpr bool one_pass = std::is_same<T, float>::value;
     for (int j = 0; j < mk; j++) {
-      bneumann<T>(m, bs, k, p.jacobi_sweeps, k.V + (size_t)j * vs, k.w, k.V, H + j, st);
-      for (int i = 0; i <= j; i++) {
+      bneumann<T>(m, bs, k, p.jacobi_sweeps, k.V + (size_t)j * vs, k.w, one_pass ? nullptr : k.V,
+                  one_pass ? nullptr : H + j, st);
+      if constexpr (one_pass) {
+        for (int k0 = 0; k0 <= j; k0 += kBatchMdot) {
+          HGKS_PROF_BEGIN(K_DOT, st);
+          k_bmdot<T><<<g, kB, 0, st>>>(N, bs.b, k.w, k.V, vs, k0, std::min(kBatchMdot, j + 1 - k0), j, k.part, bs.hs,
+                                       hz, bs.a_off, bs.g_off);
+          HGKS_PROF_END(K_DOT, st);
+        }
+        HGKS_PROF_BEGIN(K_DOT, st);
+        k_bmgs_coef<<<(nm + 63) / 64, 64, 0, st>>>(bs.b, j, mk, bs.hs, hz, bs.a_off, bs.g_off, bs.gram_off);
+        HGKS_PROF_END(K_DOT, st);
+        HGKS_PROF_BEGIN(K_DOT, st);
+        k_bmupdate<T><<<g, kB, 0, st>>>(N, bs.b, k.w, k.V, vs, j, mk, bs.hs, hz, k.part);
+        HGKS_PROF_END(K_DOT, st);
+      }
+      for (int i = 0; !one_pass && i <= j; i++) {
         const bool last = (i == j);
         HGKS_PROF_BEGIN(K_DOT, st);
         k_baxpy_dot<T><<<g, kB, 0, st>>>(N, bs.b, k.w, k.V + (size_t)i * vs, H + i * mk + j, hz,

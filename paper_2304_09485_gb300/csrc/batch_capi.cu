@@ -156,7 +156,8 @@ int64_t arena_bytes(int64_t cells, int64_t faces, const hgks_params &p, int sche
   c += 8 * (kCoef + 1 + 100 + 2 + 5 + 15 + 5 + 15);             // coef, dt, off, dval/dinv, R, Gnew, dQ, w/t/t2
   c += mixed ? (4 * 22 + 4 * 2 + 4 * 15 + 4 * 5 * (p.krylov_dim + 1)) : 8 * 5 * (p.krylov_dim + 1);
   const int64_t f = 4 * 2 + 1 + 8 * (9 + 2) + 2 + 8 * (2 * 3 * kFaceState + 15 + 15);
-  return N * c + F * f + nb * (2 + 8 + 4) + 8 * std::max<int64_t>(4096, N / 64 + 64) + (64 << 10);
+  return N * c + F * f + nb * (2 + 8 + 4 + (mixed ? 4 * 2 * kBatchMdot : 0)) + 8 * std::max<int64_t>(4096, N / 64 + 64) +
+         (64 << 10);
 }
 
 void batch_delete(Batch *B) {
@@ -233,7 +234,10 @@ hgks_status batch_new(int device, int64_t cell_cap, int64_t face_cap, int nslot,
   const int mk = shared.krylov_dim;
   bs.kdim = mk;
   bs.l1_off = (mk + 1) * mk + 1 + mk + 2;
-  bs.hsz = (bs.l1_off + 1 + 7) / 8 * 8;
+  bs.a_off = bs.l1_off + 1;
+  bs.g_off = bs.a_off + mk + 1;
+  bs.gram_off = bs.g_off + mk + 1;
+  bs.hsz = (bs.gram_off + (mk + 1) * (mk + 1) + 7) / 8 * 8;
   if ((s = balloc(M, &B->ptab, nslot)) || (s = balloc(M, &B->cmesh, N)) || (s = balloc(M, &B->fmesh, F)) ||
       (s = balloc(M, &B->bmesh, nb)) || (s = balloc(M, &B->bstart, nslot)) || (s = balloc(M, &B->bcount, nslot)) ||
       (s = balloc(M, &B->ncell, nslot)) || (s = balloc(M, &B->active_base, nslot + 1)) ||
@@ -241,7 +245,7 @@ hgks_status batch_new(int device, int64_t cell_cap, int64_t face_cap, int nslot,
       (s = balloc(M, &bs.bad, nslot)) || (s = balloc(M, &bs.ref, nslot)) || (s = balloc(M, &bs.res, nslot)) ||
       (s = balloc(M, &bs.drop, nslot)) || (s = balloc(M, &bs.max_steps, nslot)) ||
       (s = balloc(M, &bs.hs, (size_t)nslot * bs.hsz)) || (s = balloc(M, &bs.part, nb)) ||
-      (mixed && (s = balloc(M, &bs.part32, nb))) || (s = balloc(M, &B->Q, 5 * N)) ||
+      (mixed && (s = balloc(M, &bs.part32, (size_t)kBatchMdot * 2 * nb))) || (s = balloc(M, &B->Q, 5 * N)) ||
       (compact(*B) && (s = balloc(M, &B->G, 15 * N))))
     return bail(s);
   // free cells: unit volume and size, no neighbours, zero matrices, mesh -1

@@ -83,6 +83,7 @@ struct DevMesh {
 // cells, have mesh -1; per-mesh arrays are indexed from -1 (entry -1 is a
 // permanently inactive slot), so "mesh of x" can always be looked up.
 constexpr int kBatchBlock = 256;
+constexpr int kBatchMdot = 8;    // basis vectors per batched multi-dot launch (FP32 one-pass MGS)
 struct BatchDev {
   int nmesh = 0, nblocks = 0;
   const short *bmesh = nullptr;    // [nblocks] mesh of each block of kBatchBlock cells (-1: free)
@@ -91,7 +92,8 @@ struct BatchDev {
   unsigned *counters = nullptr;    // [nmesh] arrival counters of the per-mesh reductions (0 between launches)
   int *active = nullptr;           // [-1 .. nmesh-1] 1 while the mesh iterates; active[-1] = 0
 };
-// Device scalars of a batch: per mesh hs[hsz] = H[(m+1) m] | beta | y[m] | lres[2] | density L1 | pad
+// Device scalars of a batch: per mesh hs[hsz] = H[(m+1) m] | beta | y[m] | lres[2] | density L1 |
+// a[m+1] | g[m+1] | Gram[(m+1)(m+1)] (the one-pass MGS of FP32 vectors) | pad
 struct BatchState {
   BatchDev b;
   int hsz = 0, kdim = 0;
@@ -106,6 +108,7 @@ struct BatchState {
   double *hist = nullptr;          // [nmesh][hist_len] density residual history (may be null)
   int hist_len = 0;
   int l1_off = 0;                  // offset of the density L1 in a mesh's hs record
+  int a_off = 0, g_off = 0, gram_off = 0;   // offsets of a, g and the basis Gram matrix (leading dimension m + 1)
 };
 
 struct Scratch {
