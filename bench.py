@@ -542,6 +542,109 @@ def run_hex(args, rank, world):
     return 0
 
 
+def wake_and_separation(m, Qc, radii):
+    """Closed wake length L (diameters, from the rear of the sphere to where u_x
+    changes sign on the downstream axis) and separation angle theta (degrees from
+    the front stagnation point, where the meridional velocity of the first cell
+    layer, averaged over the azimuth in 2-degree bins, changes sign) from the cell
+    states Qc [n, 5] (caller order) of a sphere of diameter 1 in a flow along +x."""
+    cen = m.xyz[m.cells].mean(1)
+    u = Qc[:, 1:4] / Qc[:, :1]
+    r = np.linalg.norm(cen, axis=1)
+    first = r < radii[1]
+    c, uf = cen[first], u[first]
+    cn = c / np.linalg.norm(c, axis=1)[:, None]
+    th = np.degrees(np.arccos(np.clip(-cn[:, 0], -1.0, 1.0)))
+    e = np.array([1.0, 0.0, 0.0])[None, :] - cn * cn[:, :1]
+    e_th = e / np.maximum(np.linalg.norm(e, axis=1), 1e-30)[:, None]
+    ut = np.einsum("ij,ij->i", uf, e_th)
+    bins = np.linspace(0.0, 180.0, 91)
+    idx = np.digitize(th, bins) - 1
+    prof = np.array([ut[idx == k].mean() if np.any(idx == k) else np.nan for k in range(90)])
+    mid = 0.5 * (bins[1:] + bins[:-1])
+    theta = None
+    for k in range(1, 90):
+        if mid[k] > 60.0 and np.isfinite(prof[k - 1]) and np.isfinite(prof[k]) and prof[k - 1] > 0.0 >= prof[k]:
+            theta = float(mid[k - 1] + (mid[k] - mid[k - 1]) * prof[k - 1] / (prof[k - 1] - prof[k]))
+            break
+    n = m.meta["n"]
+    ax = (cen[:, 0] > 0.5) & (np.linalg.norm(cen[:, 1:], axis=1) < 0.8 * cen[:, 0] * (math.pi / 2) / n)
+    xs, ux = cen[ax, 0], u[ax, 0]
+    o = np.argsort(xs)
+    xs, ux = xs[o], ux[o]
+    L = None
+    for k in range(1, len(xs)):
+        if ux[k - 1] < 0.0 <= ux[k]:
+            L = float(xs[k - 1] + (xs[k] - xs[k - 1]) * (-ux[k - 1]) / (ux[k] - ux[k - 1]) - 0.5)
+            break
+    return L, theta
+
+
+def run_hexsphere(args, rank, world):
+    """Sec. 5.2's viscous sphere on hexahedra: Re 118, Ma 0.2535, a cubed-sphere
+    O-grid of 6 x 32 x 32 x 31 = 190,464 hexahedra (the paper's cell count) with a
+    first layer 3e-2 thick, adiabatic no-slip wall, linear weights, CFL 20,
+    GMRES(10) x 3, Jacobi 2, from the free stream. Algorithm 1 to a 1e-10 drop
+    (or the step limit) with both schemes in FP64 and the compact one with the
+    FP32 Krylov part: steps, time, C_D, the closed wake length L and the
+    separation angle theta, beside the values the paper prints for its own
+    190,464-cell hexahedral grid (context: the grids differ)."""
+    import torch
+    import paper_2304_09485_gb300 as H
+    from paper_2304_09485_gb300 import inputs as I
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    layers = 31
+    stretch = I.sphere_stretch(layers, dr1=3e-2)
+    m = I.hex_sphere_mesh(32, layers, stretch=stretch)
+    radii = I.sphere_radii(layers, 0.5, 10.0, stretch)
+    hm = H.hgks_mesh_create(m, scheme_mask=3, device=local)
+    cond = I.sphere_conditions(0.2535, Re=118.0)
+    qinf = 0.5 * cond["rho_inf"] * cond["u_inf"][0] ** 2 * math.pi * 0.25
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    res = {}
+    for name, scheme, prec in (("GMRES-HWENO", 1, 0), ("GMRES-WENO", 0, 0), ("GMRES-HWENO, FP32 Krylov", 1, 1)):
+        p = H.hgks_default_params(scheme=scheme, weights=1, precision=prec, Pr=0.72, cfl=20.0, krylov_dim=10,
+                                  restarts=3, jacobi_sweeps=2, **cond)
+        Q = hm.to_internal(I.state_from_conditions(m.n_cells, cond), device=dev)
+        G = torch.zeros((15, m.n_cells), dtype=torch.float64, device=dev)
+        e0.record(stream)
+        info, hist, conv = H.hgks_solve_steady(hm, p, Q, G if scheme else None, drop_tol=args.hexsphere_drop,
+                                               max_steps=args.hexsphere_max_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        L, theta = wake_and_separation(m, hm.to_caller(Q), radii)
+        cd = float(H.hgks_wall_force(hm, p, Q, G if scheme else None, I.BC_NOSLIP_ADIA)[0] / qinf)
+        res[name] = {"converged": bool(conv), "steps": int(info.steps), "final_drop": float(hist[-1] / hist.max()),
+                     "seconds": sec, "mcells_per_s": m.n_cells * info.steps / sec / 1e6, "C_D": cd, "L": L,
+                     "theta_deg": theta, "state": Q}
+    clk = clocks.stop()
+    q64, q32 = res["GMRES-HWENO"].pop("state"), res["GMRES-HWENO, FP32 Krylov"].pop("state")
+    res["GMRES-WENO"].pop("state")
+    state_diff = float(torch.linalg.norm(q32 - q64) / torch.linalg.norm(q64))
+    if rank != 0:
+        return 0
+    line = {"metric": "viscous sphere on hexahedra: closed wake length and separation angle at a converged steady state",
+            "value": res["GMRES-HWENO"]["L"], "unit": "L (diameters), GMRES-HWENO", "n_gpus": world,
+            "steps": res["GMRES-HWENO"]["steps"], "warmup": 0, "higher_is_better": None, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "sphere Re 118, Ma 0.2535, cubed-sphere O-grid 6x32x32x31 = 190,464 hexahedra, "
+                                   "first layer 3e-2, adiabatic no-slip wall, linear weights, CFL 20, GMRES(10)x3, "
+                                   f"Jacobi 2, from the free stream, drop {args.hexsphere_drop:g}, "
+                                   f"max {args.hexsphere_max_steps} steps"},
+            "results": res, "fp32_vs_fp64_state_rel_l2": state_diff,
+            "paper_190464_hex": {"GMRES-HWENO": {"L": 0.95, "theta_deg": 128.1},
+                                 "GMRES-WENO": {"L": 0.91, "theta_deg": 124.5}},
+            "clocks": clk}
+    print(json.dumps(line))
+    return 0
+
+
 def run_serve(args, rank, world):
     """Steady-solve requests with Poisson arrivals served by the continuous-
     batching server (mixed precision) against the same requests solved one
@@ -679,7 +782,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="scaled-down mesh (profiling runs)")
     ap.add_argument("--sphere-n", type=int, default=0, help="sphere of n x n patches and 2n layers (profiling runs)")
-    ap.add_argument("--workload", default="sphere", choices=["sphere", "batch", "serve", "precision", "hex"],
+    ap.add_argument("--workload", default="sphere",
+                    choices=["sphere", "batch", "serve", "precision", "hex", "hexsphere"],
                     help="sphere: the 2.36M-tet sphere (default); batch: many problems in one batch; "
                          "serve: Poisson-arriving solves through the request server")
     ap.add_argument("--serve-requests", type=int, default=96)
@@ -697,6 +801,8 @@ def main():
     ap.add_argument("--batch-scheme", default="hweno", choices=["weno", "hweno"])
     ap.add_argument("--batch-precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--hex-n", type=int, default=72, help="hex workload: n^3 hexahedra")
+    ap.add_argument("--hexsphere-drop", type=float, default=1e-10)
+    ap.add_argument("--hexsphere-max-steps", type=int, default=4000)
     ap.add_argument("--grad-relax", type=float, default=1.0,
                     help="precision workload: relaxation of the compact gradient update (1: Algorithm 1's)")
     ap.add_argument("--batch-drop", type=float, default=0.0,
@@ -717,6 +823,8 @@ def main():
         return run_serve(args, rank, world)
     if args.workload == "hex":
         return run_hex(args, rank, world)
+    if args.workload == "hexsphere":
+        return run_hexsphere(args, rank, world)
     if args.workload == "precision":
         return run_precision(args, rank, world)
 

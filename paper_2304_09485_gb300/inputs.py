@@ -341,6 +341,60 @@ def hex_tilted_box_mesh(n: int = 6, tilt: float = 0.3, seed: int = BASE_SEED + 7
                    name=f"hextilted{n}", meta=dict(n=n, tilt=tilt, seed=seed))
 
 
+def hex_sphere_mesh(n: int = 32, layers: int = 31, r_in: float = 0.5, r_out: float = 10.0,
+                    stretch: float | None = None, wall_tag: int = BC_NOSLIP_ADIA, seed: int = BASE_SEED + 800,
+                    permute: bool = True) -> HexMesh:
+    """Cubed-sphere O-grid of hexahedra around a sphere (Sec. 5.2's hexahedral
+    sphere grids): six equiangular n x n patches on the sphere, `layers` radial
+    layers stretched geometrically from r_in to r_out (first layer of the wall
+    cells' tangential size times 0.36 unless `stretch` is given); inner faces
+    tagged `wall_tag`, outer faces far field. 6 n^2 layers cells (n = 32,
+    31 layers: 190,464, the cell count of the paper's hexahedral sphere)."""
+    rng = np.random.default_rng(seed)
+    g = np.arange(n + 1)
+    I_, J_, K_ = np.meshgrid(g, g, g, indexing="ij")
+    lat = np.stack([I_, J_, K_], axis=-1).reshape(-1, 3)
+    on_surf = np.any((lat == 0) | (lat == n), axis=1)
+    surf = lat[on_surf]
+    ns = surf.shape[0]
+    sid = -np.ones((n + 1) ** 3, dtype=np.int64)
+    sid[(surf[:, 0] * (n + 1) + surf[:, 1]) * (n + 1) + surf[:, 2]] = np.arange(ns)
+    t = np.tan((surf.astype(np.float64) / n - 0.5) * (math.pi / 2.0))
+    unit = t / np.linalg.norm(t, axis=1, keepdims=True)
+    a, b = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    a, b = a.ravel(), b.ravel()
+    quads = []
+    for axis in range(3):
+        for side in (0, n):
+            o1, o2 = [x for x in range(3) if x != axis]
+
+            def P(u, v):
+                c = [None, None, None]
+                c[axis] = np.full_like(u, side)
+                c[o1] = u
+                c[o2] = v
+                return sid[(c[0] * (n + 1) + c[1]) * (n + 1) + c[2]]
+            quads.append(np.stack([P(a, b), P(a + 1, b), P(a + 1, b + 1), P(a, b + 1)], axis=1))
+    quads = np.concatenate(quads, axis=0)
+    if stretch is None:
+        stretch = sphere_stretch(layers, r_in, r_out, dr1=0.36 * math.pi * r_in / (2 * n))
+    radii = sphere_radii(layers, r_in, r_out, stretch)
+    xyz = (unit[None, :, :] * radii[:, None, None]).reshape(-1, 3)
+    L = np.arange(layers)[:, None]
+    lower = (L[:, :, None] * ns + quads[None, :, :]).reshape(-1, 4)
+    hx = np.concatenate([lower, lower + ns], axis=1)
+    # orient every hexahedron positively (the quads' cyclic direction depends on the patch)
+    x = xyz[hx]
+    neg = np.einsum("ij,ij->i", np.cross(x[:, 1] - x[:, 0], x[:, 3] - x[:, 0]), x[:, 4] - x[:, 0]) < 0
+    hx[neg] = hx[neg][:, [0, 3, 2, 1, 4, 7, 6, 5]]
+    if permute:
+        hx = hx[rng.permutation(hx.shape[0])]
+    bface = np.concatenate([quads, quads + layers * ns], axis=0).astype(np.int64)
+    btag = np.concatenate([np.full(len(quads), wall_tag, np.int32), np.full(len(quads), BC_FARFIELD, np.int32)])
+    return HexMesh(xyz, hx.astype(np.int64), bface, btag, None, name=f"hexsphere{n}x{layers}",
+                   meta=dict(n=n, layers=layers, r_in=r_in, r_out=r_out, stretch=stretch))
+
+
 def hex_periodic_cube_mesh(n: int = 4, jitter: float = 0.1, seed: int = BASE_SEED + 600,
                            permute: bool = True, reorient: bool = True, length: float = 1.0) -> HexMesh:
     """Periodic cube [0,L]^3 of n^3 hexahedra, every vertex jittered (periodic
