@@ -238,3 +238,40 @@ def test_hex_cavity_solve_to_1e8_parity(cuda, scheme):
     assert info.steps == len(hist_o) - 1
     np.testing.assert_allclose(hist_g, hist_o, rtol=1e-8, atol=1e-12 * hist_o.max())
     assert np.linalg.norm(hm.to_caller(Qd) - Qo) / np.linalg.norm(Qo) <= 1e-9
+
+
+def test_hex_sphere_converged_steady_state_fp64_mixed_and_oracle(cuda):
+    """The viscous sphere of Sec. 5.2 (Re 118, Ma 0.2535, linear weights, CFL 20,
+    compact HWENO) on a scaled-down hexahedral O-grid of the same construction
+    (6 x 4 x 4 patches, 6 layers, 576 cells): Algorithm 1 to a 1e-8 drop in the
+    oracle (636 steps), on the GPU in FP64 (the same steps, histories within
+    1e-8, state within 1e-9, drag coefficient within 1e-10) and with the FP32
+    Krylov part (a converged state is fixed by the FP64 residual: state within
+    1e-8, drag within 1e-9)."""
+    import math
+    m = I.hex_sphere_mesh(4, 6, stretch=I.sphere_stretch(6, dr1=6e-2))
+    cond = I.sphere_conditions(0.2535, Re=118.0)
+    kw = dict(scheme=1, weights=1, Pr=0.72, cfl=20.0)
+    om, hm = O.OracleMesh(m), H.hgks_mesh_create(m, scheme_mask=2)
+    Q0, G0 = I.state_from_conditions(m.n_cells, cond), np.zeros((m.n_cells, 15))
+    po = O.make_params(**{**cond, **kw})
+    Qo, Go, hist_o, conv_o = om.solve_steady(po, Q0, G0, drop=1e-8, max_steps=1500)
+    assert conv_o
+    qinf = 0.5 * cond["u_inf"][0] ** 2 * math.pi * 0.25
+    cd_o = om.wall_force(po, Qo, Go, I.BC_NOSLIP_ADIA)[0] / qinf
+    out = {}
+    for prec in (0, 1):
+        ph = H.hgks_default_params(**{**cond, **kw, "precision": prec})
+        Qd, Gd = hm.to_internal(Q0), hm.to_internal(G0)
+        info, hist_g, conv_g = H.hgks_solve_steady(hm, ph, Qd, Gd, drop_tol=1e-8, max_steps=1500)
+        assert conv_g
+        cd_g = H.hgks_wall_force(hm, ph, Qd, Gd, I.BC_NOSLIP_ADIA)[0] / qinf
+        out[prec] = (info.steps, hist_g, hm.to_caller(Qd), cd_g)
+    steps, hist_g, Qg, cd_g = out[0]
+    assert steps == len(hist_o) - 1
+    np.testing.assert_allclose(hist_g, hist_o, rtol=1e-8, atol=1e-12 * hist_o.max())
+    assert np.linalg.norm(Qg - Qo) / np.linalg.norm(Qo) <= 1e-9
+    assert abs(cd_g - cd_o) <= 1e-10 * abs(cd_o)
+    _, _, Q32, cd32 = out[1]
+    assert np.linalg.norm(Q32 - Qo) / np.linalg.norm(Qo) <= 1e-8
+    assert abs(cd32 - cd_o) <= 1e-9 * abs(cd_o)
