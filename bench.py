@@ -581,10 +581,11 @@ def wake_and_separation(m, Qc, radii):
 
 
 def run_hexsphere(args, rank, world):
-    """Sec. 5.2's viscous sphere on hexahedra: Re 118, Ma 0.2535, a cubed-sphere
-    O-grid of 6 x 32 x 32 x 31 = 190,464 hexahedra (the paper's cell count) with a
-    first layer 3e-2 thick, adiabatic no-slip wall, linear weights, CFL 20,
-    GMRES(10) x 3, Jacobi 2, from the free stream. Algorithm 1 to a 1e-10 drop
+    """Sec. 5.2's viscous sphere on hexahedra: a cubed-sphere O-grid of 6 x 32 x
+    32 x 31 = 190,464 hexahedra (the paper's cell count) with a first layer 3e-2
+    thick, adiabatic no-slip wall, GMRES(10) x 3, Jacobi 2, from the free stream;
+    Re 118, Ma 0.2535 with linear weights at CFL 20, or Re 300, Ma 1.5 with
+    nonlinear weights at CFL 5 (the paper's two cases). Algorithm 1 to a 1e-10 drop
     (or the step limit) with both schemes in FP64 and the compact one with the
     FP32 Krylov part: steps, time, C_D, the closed wake length L and the
     separation angle theta, beside the values the paper prints for its own
@@ -600,7 +601,13 @@ def run_hexsphere(args, rank, world):
     m = I.hex_sphere_mesh(32, layers, stretch=stretch)
     radii = I.sphere_radii(layers, 0.5, 10.0, stretch)
     hm = H.hgks_mesh_create(m, scheme_mask=3, device=local)
-    cond = I.sphere_conditions(0.2535, Re=118.0)
+    # the paper's two cases on this grid: Re 118, Ma 0.2535, linear weights, CFL 20;
+    # Re 300, Ma 1.5, nonlinear weights, CFL 5
+    sub = args.hexsphere_case == "re118"
+    cond = I.sphere_conditions(0.2535, Re=118.0) if sub else I.sphere_conditions(1.5, Re=300.0)
+    weights, cfl = (1, 20.0) if sub else (0, 5.0)
+    paper = ({"GMRES-HWENO": {"L": 0.95, "theta_deg": 128.1}, "GMRES-WENO": {"L": 0.91, "theta_deg": 124.5}} if sub else
+             {"GMRES-HWENO": {"L": 1.16, "theta_deg": 135.9}, "GMRES-WENO": {"L": 1.17, "theta_deg": 135.4}})
     qinf = 0.5 * cond["rho_inf"] * cond["u_inf"][0] ** 2 * math.pi * 0.25
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -608,7 +615,7 @@ def run_hexsphere(args, rank, world):
     clocks.start()
     res = {}
     for name, scheme, prec in (("GMRES-HWENO", 1, 0), ("GMRES-WENO", 0, 0), ("GMRES-HWENO, FP32 Krylov", 1, 1)):
-        p = H.hgks_default_params(scheme=scheme, weights=1, precision=prec, Pr=0.72, cfl=20.0, krylov_dim=10,
+        p = H.hgks_default_params(scheme=scheme, weights=weights, precision=prec, Pr=0.72, cfl=cfl, krylov_dim=10,
                                   restarts=3, jacobi_sweeps=2, **cond)
         Q = hm.to_internal(I.state_from_conditions(m.n_cells, cond), device=dev)
         G = torch.zeros((15, m.n_cells), dtype=torch.float64, device=dev)
@@ -633,13 +640,12 @@ def run_hexsphere(args, rank, world):
             "value": res["GMRES-HWENO"]["L"], "unit": "L (diameters), GMRES-HWENO", "n_gpus": world,
             "steps": res["GMRES-HWENO"]["steps"], "warmup": 0, "higher_is_better": None, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "sphere Re 118, Ma 0.2535, cubed-sphere O-grid 6x32x32x31 = 190,464 hexahedra, "
-                                   "first layer 3e-2, adiabatic no-slip wall, linear weights, CFL 20, GMRES(10)x3, "
-                                   f"Jacobi 2, from the free stream, drop {args.hexsphere_drop:g}, "
+            "config": {"workload": ("sphere Re 118, Ma 0.2535, " if sub else "sphere Re 300, Ma 1.5, ") +
+                                   "cubed-sphere O-grid 6x32x32x31 = 190,464 hexahedra, first layer 3e-2, adiabatic "
+                                   "no-slip wall, " + ("linear weights, CFL 20" if sub else "nonlinear weights, CFL 5") +
+                                   f", GMRES(10)x3, Jacobi 2, from the free stream, drop {args.hexsphere_drop:g}, "
                                    f"max {args.hexsphere_max_steps} steps"},
-            "results": res, "fp32_vs_fp64_state_rel_l2": state_diff,
-            "paper_190464_hex": {"GMRES-HWENO": {"L": 0.95, "theta_deg": 128.1},
-                                 "GMRES-WENO": {"L": 0.91, "theta_deg": 124.5}},
+            "results": res, "fp32_vs_fp64_state_rel_l2": state_diff, "paper_190464_hex": paper,
             "clocks": clk}
     print(json.dumps(line))
     return 0
@@ -801,6 +807,9 @@ def main():
     ap.add_argument("--batch-scheme", default="hweno", choices=["weno", "hweno"])
     ap.add_argument("--batch-precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--hex-n", type=int, default=72, help="hex workload: n^3 hexahedra")
+    ap.add_argument("--hexsphere-case", default="re118", choices=["re118", "ma15"],
+                    help="hexsphere workload: Re 118, Ma 0.2535 (linear weights, CFL 20) or Re 300, Ma 1.5 "
+                         "(nonlinear weights, CFL 5)")
     ap.add_argument("--hexsphere-drop", type=float, default=1e-10)
     ap.add_argument("--hexsphere-max-steps", type=int, default=4000)
     ap.add_argument("--grad-relax", type=float, default=1.0,
