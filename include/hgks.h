@@ -324,7 +324,8 @@ typedef struct {
  * mu, viscous, cfl, free stream, walls, weights ...) may differ per mesh.
  * State starts at zero: set it with hgks_batch_set_state. Errors: HGKS_ERR_ARG
  * (n_meshes < 1 or > 32767, NULL, disagreeing parameters, a mesh built without
- * the scheme's data, meshes on different devices), HGKS_ERR_OOM, HGKS_ERR_CUDA. */
+ * the scheme's data, meshes on different devices, a hexahedral mesh: batches
+ * take tetrahedra), HGKS_ERR_OOM, HGKS_ERR_CUDA. */
 hgks_status hgks_batch_create(const hgks_mesh *meshes, const hgks_params *params, int32_t n_meshes,
                               hgks_batch *out);
 hgks_status hgks_batch_destroy(hgks_batch batch);
@@ -340,7 +341,7 @@ hgks_status hgks_batch_create_empty(int32_t device, int64_t cell_capacity, int64
 /* Place a mesh (copied; the handle stays the caller's) in a free slot and in
  * free cell and face ranges (first fit); *k_out receives the slot, the index
  * every other hgks_batch_* call takes. HGKS_ERR_OOM if no slot or range is
- * free (nothing changes then). */
+ * free (nothing changes then); HGKS_ERR_ARG for a hexahedral mesh. */
 hgks_status hgks_batch_add(hgks_batch batch, hgks_mesh mesh, const hgks_params *p, int32_t *k_out);
 /* Free slot k and its ranges; later launches skip them. */
 hgks_status hgks_batch_remove(hgks_batch batch, int32_t k);
