@@ -275,3 +275,42 @@ def test_hex_sphere_converged_steady_state_fp64_mixed_and_oracle(cuda):
     _, _, Q32, cd32 = out[1]
     assert np.linalg.norm(Q32 - Qo) / np.linalg.norm(Qo) <= 1e-8
     assert abs(cd32 - cd_o) <= 1e-9 * abs(cd_o)
+
+
+def test_hex_host_variants_resume_and_wall_force(cuda):
+    """The rest of the single-mesh API on hexahedra: the host-buffer residual and
+    step equal the device ones bit for bit, a solve resumed from a host snapshot
+    equals the uninterrupted one bit for bit, and the wall force matches the
+    oracle's (1e-11 of its size)."""
+    import torch
+    m, cond, om, hm = setup("hexcav5")
+    Q, G = state(m, cond, seed=17)
+    p = H.hgks_default_params(scheme=1, Pr=0.72, krylov_dim=6, restarts=2, **cond)
+    Qd, Gd = hm.to_internal(Q), hm.to_internal(G)
+    Rd, Gn = torch.empty_like(Qd), torch.empty_like(Gd)
+    H.hgks_residual(hm, p, Qd, Gd, Rd, Gn)
+    torch.cuda.synchronize()
+    Qh, Gh = np.ascontiguousarray(Qd.cpu().numpy()), np.ascontiguousarray(Gd.cpu().numpy())
+    Rh, Gnh = np.zeros_like(Qh), np.zeros_like(Gh)
+    H.hgks_residual_host(hm, p, Qh, Gh, Rh, Gnh)
+    assert np.array_equal(Rh, Rd.cpu().numpy()) and np.array_equal(Gnh, Gn.cpu().numpy())
+    info_d = H.hgks_gmres_step(hm, p, Qd, Gd)
+    info_h = H.hgks_gmres_step_host(hm, p, Qh, Gh)
+    torch.cuda.synchronize()
+    assert info_h.res_l1 == info_d.res_l1 and np.array_equal(Qh, Qd.cpu().numpy())
+    # checkpoint / resume
+    Qa, Ga = hm.to_internal(Q), hm.to_internal(G)
+    ia, ha, _ = H.hgks_solve_steady(hm, p, Qa, Ga, drop_tol=1e-12, max_steps=10)
+    Qb, Gb = hm.to_internal(Q), hm.to_internal(G)
+    i5, h5, _ = H.hgks_solve_steady(hm, p, Qb, Gb, drop_tol=1e-12, max_steps=5)
+    Qc, Gc = torch.from_numpy(Qb.cpu().numpy().copy()).cuda(), torch.from_numpy(Gb.cpu().numpy().copy()).cuda()
+    ib, hb, _ = H.hgks_solve_resume(hm, p, Qc, Gc, i5, drop_tol=1e-12, max_steps=10)
+    torch.cuda.synchronize()
+    assert ib.steps == ia.steps == 10 and torch.equal(Qc, Qa) and torch.equal(Gc, Ga)
+    np.testing.assert_array_equal(hb[5:], ha[5:])
+    # wall force on the lid and on the other walls
+    po = O.make_params(scheme=1, Pr=0.72, krylov_dim=6, restarts=2, **cond)
+    for tag in (I.BC_WALL_LID, I.BC_WALL_ISO):
+        fo = om.wall_force(po, Q, G, tag)
+        fg = H.hgks_wall_force(hm, p, hm.to_internal(Q), hm.to_internal(G), tag)
+        assert np.abs(fg - fo).max() <= 1e-11 * np.abs(fo).max()
