@@ -183,8 +183,9 @@ hgks_status hgks_mesh_create(const double *xyz, int64_t n_vert, const int64_t *t
  * through its vertices, with area and normal from its vector area and 2 x 2
  * Gauss points weighted by the area element (exact for planar faces). Meshes
  * of hexahedra run through the single-mesh calls (residual, Jacobian, GMRES
- * step, solves, matrix-free products); hgks_residual_noalloc and batches take
- * tetrahedra only and return HGKS_ERR_ARG. Errors as hgks_mesh_create, and
+ * step, solves, matrix-free products) and through batches made by
+ * hgks_batch_create from hexahedral meshes only; hgks_residual_noalloc, empty
+ * batches and the server take tetrahedra (HGKS_ERR_ARG otherwise). Errors as hgks_mesh_create, and
  * HGKS_ERR_MESH for an inverted hexahedron (Jacobian determinant <= 0 at a
  * Gauss point). */
 hgks_status hgks_mesh_create_hex(const double *xyz, int64_t n_vert, const int64_t *hex8, int64_t n_hex,
@@ -324,8 +325,8 @@ typedef struct {
  * mu, viscous, cfl, free stream, walls, weights ...) may differ per mesh.
  * State starts at zero: set it with hgks_batch_set_state. Errors: HGKS_ERR_ARG
  * (n_meshes < 1 or > 32767, NULL, disagreeing parameters, a mesh built without
- * the scheme's data, meshes on different devices, a hexahedral mesh: batches
- * take tetrahedra), HGKS_ERR_OOM, HGKS_ERR_CUDA. */
+ * the scheme's data, meshes on different devices, tetrahedral and hexahedral
+ * meshes mixed: a batch holds one cell kind), HGKS_ERR_OOM, HGKS_ERR_CUDA. */
 hgks_status hgks_batch_create(const hgks_mesh *meshes, const hgks_params *params, int32_t n_meshes,
                               hgks_batch *out);
 hgks_status hgks_batch_destroy(hgks_batch batch);
@@ -334,14 +335,15 @@ hgks_status hgks_batch_info(hgks_batch batch, hgks_batch_info_t *info);
 
 /* An empty batch: an arena of cell_capacity cells and face_capacity faces with
  * max_meshes slots, for meshes whose params agree with *shared in the fields
- * listed above (shared->scheme decides which reconstruction data it holds).
+ * listed above (shared->scheme decides which reconstruction data it holds);
+ * an empty batch holds tetrahedra (hexahedral batches come from hgks_batch_create).
  * Device memory: about 8 KB per cell and 1.3 KB per face (FP64, Krylov 10). */
 hgks_status hgks_batch_create_empty(int32_t device, int64_t cell_capacity, int64_t face_capacity,
                                     int32_t max_meshes, const hgks_params *shared, hgks_batch *out);
 /* Place a mesh (copied; the handle stays the caller's) in a free slot and in
  * free cell and face ranges (first fit); *k_out receives the slot, the index
  * every other hgks_batch_* call takes. HGKS_ERR_OOM if no slot or range is
- * free (nothing changes then); HGKS_ERR_ARG for a hexahedral mesh. */
+ * free (nothing changes then); HGKS_ERR_ARG for a mesh of the other cell kind. */
 hgks_status hgks_batch_add(hgks_batch batch, hgks_mesh mesh, const hgks_params *p, int32_t *k_out);
 /* Free slot k and its ranges; later launches skip them. */
 hgks_status hgks_batch_remove(hgks_batch batch, int32_t k);

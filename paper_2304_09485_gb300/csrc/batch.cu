@@ -66,7 +66,7 @@ __device__ __forceinline__ void mesh_sum(T v, const BatchDev &b, T *part, double
 
 enum { kSpmv = 0, kJacobi = 1, kNeumann = 2, kE = 3, kNegE = 4 };   // as k_apply of the single-mesh path
 // SpMV / Jacobi sweep over the merged cells with an optional per-mesh (y, dotv)
-template <typename TM, typename TV, typename TO, int Mode, bool First>
+template <typename TM, typename TV, typename TO, int Mode, bool First, int NF>
 __global__ void __launch_bounds__(kB) k_bapply(DevMesh m, BatchDev bd, const TM *__restrict__ off,
                                                const TM *__restrict__ dval, const TM *__restrict__ dinv,
                                                const TV *__restrict__ b, const TV *__restrict__ x, TO *__restrict__ y,
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(kB) k_bapply(DevMesh m, BatchDev bd, const TM 
 #pragma unroll
   for (int r = 0; r < 5; r++) acc[r] = Mode == kSpmv ? di * x[(size_t)r * N + i] : TV(0);
 #pragma unroll
-  for (int p = 0; p < 4; p++) {
+  for (int p = 0; p < NF; p++) {
     const int j = m.cnb[(size_t)p * N + i];
     if (j < 0) continue;
     TV xj[5];
@@ -113,6 +113,18 @@ __global__ void __launch_bounds__(kB) k_bapply(DevMesh m, BatchDev bd, const TM 
     if (dotv) part_v = fma(oo, dotv[(size_t)r * N + i], part_v);
   }
   if (dotv) mesh_sum(part_v, bd, part, dot_out, stride, 0);
+}
+
+// k_bapply for the batch's cell kind (4 or 6 off-diagonal blocks per row)
+template <typename TM, typename TV, typename TO, int Mode, bool First>
+void bapply(unsigned g, cudaStream_t st, const DevMesh &m, const BatchDev &bd, const TM *off, const TM *dval,
+            const TM *dinv, const TV *b, const TV *x, TO *y, const TO *dotv, TO *part, double *dot_out, int stride) {
+  if (m.hex)
+    k_bapply<TM, TV, TO, Mode, First, HexShape::NF><<<g, kB, 0, st>>>(m, bd, off, dval, dinv, b, x, y, dotv, part,
+                                                                      dot_out, stride);
+  else
+    k_bapply<TM, TV, TO, Mode, First, TetShape::NF><<<g, kB, 0, st>>>(m, bd, off, dval, dinv, b, x, y, dotv, part,
+                                                                      dot_out, stride);
 }
 
 // w -= h(mesh) v (if v); out(mesh) = (w, x) or ||w|| (self)
@@ -382,10 +394,10 @@ void bprecondition(const DevMesh &m, BatchState &bs, const BBuf<T> &k, int sweep
     const T *dv = (q == sweeps) ? dotv : nullptr;
     HGKS_PROF_BEGIN(K_JACOBI, st);
     if (q == 1)
-      k_bapply<T, T, T, kJacobi, true><<<g, kB, 0, st>>>(m, bs.b, k.off, k.dval, k.dinv, b, nullptr, dst, dv, k.part,
+      bapply<T, T, T, kJacobi, true>(g, st, m, bs.b, k.off, k.dval, k.dinv, b, nullptr, dst, dv, k.part,
                                                           dot_out, hz);
     else
-      k_bapply<T, T, T, kJacobi, false><<<g, kB, 0, st>>>(m, bs.b, k.off, k.dval, k.dinv, b, prev, dst, dv, k.part,
+      bapply<T, T, T, kJacobi, false>(g, st, m, bs.b, k.off, k.dval, k.dinv, b, prev, dst, dv, k.part,
                                                            dot_out, hz);
     HGKS_PROF_END(K_JACOBI, st);
     prev = dst;
@@ -405,16 +417,16 @@ void bneumann(const DevMesh &m, BatchState &bs, const BBuf<T> &k, int sweeps, co
     T *dst = (q % 2 == 0) ? k.t : k.t2;
     HGKS_PROF_BEGIN(K_JACOBI, st);
     if (q == 0 && sweeps % 2 == 1)
-      k_bapply<T, T, T, kNegE, false><<<g, kB, 0, st>>>(m, bs.b, k.off, k.dval, k.dinv, nullptr, z, dst, nullptr, k.part,
+      bapply<T, T, T, kNegE, false>(g, st, m, bs.b, k.off, k.dval, k.dinv, nullptr, z, dst, nullptr, k.part,
                                                          nullptr, hz);
     else
-      k_bapply<T, T, T, kE, false><<<g, kB, 0, st>>>(m, bs.b, k.off, k.dval, k.dinv, nullptr, z, dst, nullptr, k.part,
+      bapply<T, T, T, kE, false>(g, st, m, bs.b, k.off, k.dval, k.dinv, nullptr, z, dst, nullptr, k.part,
                                                       nullptr, hz);
     HGKS_PROF_END(K_JACOBI, st);
     z = dst;
   }
   HGKS_PROF_BEGIN(K_SPMV, st);
-  k_bapply<T, T, T, kNeumann, false><<<g, kB, 0, st>>>(m, bs.b, k.off, k.dval, k.dinv, v, z, w, dotv, k.part, dot_out,
+  bapply<T, T, T, kNeumann, false>(g, st, m, bs.b, k.off, k.dval, k.dinv, v, z, w, dotv, k.part, dot_out,
                                                         hz);
   HGKS_PROF_END(K_SPMV, st);
 }
@@ -432,7 +444,7 @@ void bgmres_t(const DevMesh &m, Scratch &s, BatchState &bs, const BBuf<T> &k, co
   for (int it = 0; it < p.restarts; it++) {
     cudaMemset2DAsync(H, sizeof(double) * hz, 0, sizeof(double) * (mk + 1) * mk, nm, st);
     HGKS_PROF_BEGIN(K_SPMV, st);
-    k_bapply<T, double, T, kSpmv, false><<<g, kB, 0, st>>>(m, bs.b, k.off, k.dval, k.dinv, rhs, dx, k.t, nullptr, nullptr,
+    bapply<T, double, T, kSpmv, false>(g, st, m, bs.b, k.off, k.dval, k.dinv, rhs, dx, k.t, nullptr, nullptr,
                                                             nullptr, hz);
     HGKS_PROF_END(K_SPMV, st);
     bprecondition<T>(m, bs, k, p.jacobi_sweeps, k.t, k.w, nullptr, nullptr, st);

@@ -69,6 +69,7 @@ MeshSource source_of(const Mesh &a) {
   s.vol = d.vol; s.inv_vol = d.inv_vol; s.h = d.h; s.m2 = d.m2; s.xg = d.xg;
   s.cnb = d.cnb; s.cface = d.cface; s.sten = d.sten; s.fl = d.fl; s.fr = d.fr; s.subvalid = d.subvalid;
   s.X0 = d.X0; s.Xs = d.Xs; s.ssl = d.ssl; s.H0 = d.H0; s.Hm = d.Hm; s.ftag = d.ftag; s.fT = d.fT; s.fS = d.fS; s.fdist = d.fdist;
+  s.fw = d.fw; s.hex = d.hex;
   return s;
 }
 MeshSource source_of(const HostMesh &hm, std::vector<double> &inv) {
@@ -82,6 +83,7 @@ MeshSource source_of(const HostMesh &hm, std::vector<double> &inv) {
   s.cnb = P(hm.cnb); s.cface = P(hm.cface); s.sten = P(hm.sten); s.fl = P(hm.fl); s.fr = P(hm.fr);
   s.subvalid = P(hm.subvalid); s.X0 = P(hm.X0); s.Xs = P(hm.Xs); s.ssl = P(hm.ssl); s.H0 = P(hm.H0); s.Hm = P(hm.Hm);
   s.ftag = P(hm.ftag); s.fT = P(hm.fT); s.fS = P(hm.fS); s.fdist = P(hm.fdist);
+  s.fw = P(hm.fw); s.hex = hm.hex;
   return s;
 }
 
@@ -190,8 +192,18 @@ hgks_status leave(Batch &B, cudaStream_t user) {
 namespace hgks {
 
 // An empty arena of cell_cap cells (rounded up to kBatchBlock) and face_cap faces.
+// rows of the per-cell and per-face arrays of a cell kind
+struct Rows {
+  int NF, NG, BIG, NSUBW, SUBK, HCOLS;
+  explicit Rows(bool hex)
+      : NF(hex ? HexShape::NF : TetShape::NF), NG(hex ? HexShape::NG : TetShape::NG),
+        BIG(hex ? HexShape::BIG : TetShape::BIG), NSUBW(hex ? HexShape::NSUBW : TetShape::NSUBW),
+        SUBK(hex ? HexShape::SUBK : TetShape::SUBK),
+        HCOLS(hex ? ShapeOf<HexShape>::HCOLS : ShapeOf<TetShape>::HCOLS) {}
+};
+
 hgks_status batch_new(int device, int64_t cell_cap, int64_t face_cap, int nslot, const hgks_params &shared,
-                      int schemes, Batch **out) {
+                      int schemes, Batch **out, bool hex) {
   *out = nullptr;
   const int64_t N = (cell_cap + kBatchBlock - 1) / kBatchBlock * kBatchBlock, F = std::max<int64_t>(face_cap, 1);
   if (N <= 0 || nslot < 1 || nslot > 32767) return fail_msg(HGKS_ERR_ARG, "batch capacity or slot count out of range");
@@ -210,7 +222,8 @@ hgks_status batch_new(int device, int64_t cell_cap, int64_t face_cap, int nslot,
   Mesh &M = B->m;
   M.device = device; M.N = N; M.F = F; M.schemes = schemes;
   DevMesh &d = M.d;
-  d.N = (int)N; d.F = (int)F;
+  d.N = (int)N; d.F = (int)F; d.hex = hex ? 1 : 0;
+  const Rows rw(hex);
   DeviceScope dev_scope(device);
   if (dev_scope.error() != cudaSuccess) return bail(fail_msg(HGKS_ERR_CUDA, "cudaSetDevice"));
   if (cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -222,13 +235,15 @@ hgks_status batch_new(int device, int64_t cell_cap, int64_t face_cap, int nslot,
   const int nb = (int)(N / kBatchBlock);
   hgks_status s;
   if ((s = balloc(M, &d.vol, N)) || (s = balloc(M, &d.inv_vol, N)) || (s = balloc(M, &d.h, N)) ||
-      (s = balloc(M, &d.m2, 6 * N)) || (s = balloc(M, &d.cnb, 4 * N)) || (s = balloc(M, &d.cface, 4 * N)) ||
-      (s = balloc(M, &d.xg, 36 * N)) || (s = balloc(M, &d.subvalid, N)) || (s = balloc(M, &d.fl, F)) ||
+      (s = balloc(M, &d.m2, 6 * N)) || (s = balloc(M, &d.cnb, (size_t)rw.NF * N)) ||
+      (s = balloc(M, &d.cface, (size_t)rw.NF * N)) || (s = balloc(M, &d.xg, (size_t)rw.NF * rw.NG * 3 * N)) ||
+      (s = balloc(M, &d.subvalid, N)) || (s = balloc(M, &d.fl, F)) ||
       (s = balloc(M, &d.fr, F)) || (s = balloc(M, &d.ftag, F)) || (s = balloc(M, &d.fT, 9 * F)) ||
-      (s = balloc(M, &d.fS, F)) || (s = balloc(M, &d.fdist, F)) ||
-      (weno && ((s = balloc(M, &d.sten, (size_t)kBig * N)) || (s = balloc(M, &d.X0, (size_t)9 * kBig * N)) ||
-                (s = balloc(M, &d.Xs, (size_t)12 * kSubK * N)) || (s = balloc(M, &d.ssl, (size_t)4 * N)))) ||
-      (hweno && ((s = balloc(M, &d.H0, (size_t)9 * 19 * N)) || (s = balloc(M, &d.Hm, (size_t)12 * 7 * N)))))
+      (s = balloc(M, &d.fS, F)) || (s = balloc(M, &d.fdist, F)) || (hex && (s = balloc(M, &d.fw, (size_t)rw.NG * F))) ||
+      (weno && ((s = balloc(M, &d.sten, (size_t)rw.BIG * N)) || (s = balloc(M, &d.X0, (size_t)9 * rw.BIG * N)) ||
+                (s = balloc(M, &d.Xs, (size_t)rw.NSUBW * 3 * rw.SUBK * N)) ||
+                (s = balloc(M, &d.ssl, (size_t)rw.NSUBW * N)))) ||
+      (hweno && ((s = balloc(M, &d.H0, (size_t)9 * rw.HCOLS * N)) || (s = balloc(M, &d.Hm, (size_t)rw.NF * 21 * N)))))
     return bail(s);
   BatchState &bs = B->bs;
   const int mk = shared.krylov_dim;
@@ -253,9 +268,10 @@ hgks_status batch_new(int device, int64_t cell_cap, int64_t face_cap, int nslot,
   launch_fill(d.inv_vol, N, 1.0, st);
   launch_fill(d.h, N, 1.0, st);
   cudaMemsetAsync(d.m2, 0, sizeof(double) * 6 * N, st);
-  cudaMemsetAsync(d.xg, 0, sizeof(double) * 36 * N, st);
-  cudaMemsetAsync(d.cnb, 0xff, sizeof(int) * 4 * N, st);
-  cudaMemsetAsync(d.cface, 0xff, sizeof(int) * 4 * N, st);
+  cudaMemsetAsync(d.xg, 0, sizeof(double) * rw.NF * rw.NG * 3 * N, st);
+  cudaMemsetAsync(d.cnb, 0xff, sizeof(int) * rw.NF * N, st);
+  cudaMemsetAsync(d.cface, 0xff, sizeof(int) * rw.NF * N, st);
+  if (hex) cudaMemsetAsync(d.fw, 0, sizeof(double) * rw.NG * F, st);
   cudaMemsetAsync(d.subvalid, 0, N, st);
   cudaMemsetAsync(d.fl, 0xff, sizeof(int) * F, st);
   cudaMemsetAsync(d.fr, 0xff, sizeof(int) * F, st);
@@ -264,14 +280,14 @@ hgks_status batch_new(int device, int64_t cell_cap, int64_t face_cap, int nslot,
   cudaMemsetAsync(d.fS, 0, sizeof(double) * F, st);
   cudaMemsetAsync(d.fdist, 0, sizeof(double) * F, st);
   if (weno) {
-    cudaMemsetAsync(d.sten, 0xff, sizeof(int) * kBig * N, st);
-    cudaMemsetAsync(d.X0, 0, sizeof(double) * 9 * kBig * N, st);
-    cudaMemsetAsync(d.Xs, 0, sizeof(double) * 12 * kSubK * N, st);
-    cudaMemsetAsync(d.ssl, 0, sizeof(unsigned) * 4 * N, st);
+    cudaMemsetAsync(d.sten, 0xff, sizeof(int) * rw.BIG * N, st);
+    cudaMemsetAsync(d.X0, 0, sizeof(double) * 9 * rw.BIG * N, st);
+    cudaMemsetAsync(d.Xs, 0, sizeof(double) * rw.NSUBW * 3 * rw.SUBK * N, st);
+    cudaMemsetAsync(d.ssl, 0, sizeof(unsigned) * rw.NSUBW * N, st);
   }
   if (hweno) {
-    cudaMemsetAsync(d.H0, 0, sizeof(double) * 9 * 19 * N, st);
-    cudaMemsetAsync(d.Hm, 0, sizeof(double) * 12 * 7 * N, st);
+    cudaMemsetAsync(d.H0, 0, sizeof(double) * 9 * rw.HCOLS * N, st);
+    cudaMemsetAsync(d.Hm, 0, sizeof(double) * rw.NF * 21 * N, st);
   }
   cudaMemsetAsync(B->ptab, 0, sizeof(hgks_params) * nslot, st);
   cudaMemsetAsync(B->cmesh, 0xff, sizeof(short) * N, st);
@@ -308,6 +324,8 @@ hgks_status batch_place(Batch &B, const MeshSource &src, const hgks_params &p, i
   *slot = -1;
   if (!same_shared(B.p0, p)) return fail_msg(HGKS_ERR_ARG, "scheme, precision, jv_mode, krylov_dim, restarts, jacobi_sweeps must agree");
   if ((src.schemes & B.m.schemes) != B.m.schemes) return fail_msg(HGKS_ERR_ARG, "mesh lacks data for the batch's scheme");
+  if (src.hex != B.m.d.hex) return fail_msg(HGKS_ERR_ARG, "the meshes of a batch are all tetrahedra or all hexahedra");
+  const Rows rw(B.m.d.hex != 0);
   int k = 0;
   while (k < B.nslot && B.slots[k].used) k++;
   if (k == B.nslot) return HGKS_OK;
@@ -325,25 +343,30 @@ hgks_status batch_place(Batch &B, const MeshSource &src, const hgks_params &p, i
   hgks_status s;
   if ((s = copy_in(d.vol, N, c0, src.vol, nk, 1, st)) || (s = copy_in(d.inv_vol, N, c0, src.inv_vol, nk, 1, st)) ||
       (s = copy_in(d.h, N, c0, src.h, nk, 1, st)) || (s = copy_in(d.m2, N, c0, src.m2, nk, 6, st)) ||
-      (s = copy_in(d.cnb, N, c0, src.cnb, nk, 4, st)) || (s = copy_in(d.cface, N, c0, src.cface, nk, 4, st)) ||
-      (s = copy_in(d.xg, N, c0, src.xg, nk, 36, st)) || (s = copy_in(d.subvalid, N, c0, src.subvalid, nk, 1, st)) ||
+      (s = copy_in(d.cnb, N, c0, src.cnb, nk, rw.NF, st)) || (s = copy_in(d.cface, N, c0, src.cface, nk, rw.NF, st)) ||
+      (s = copy_in(d.xg, N, c0, src.xg, nk, rw.NF * rw.NG * 3, st)) ||
+      (s = copy_in(d.subvalid, N, c0, src.subvalid, nk, 1, st)) ||
+      (d.fw && (s = copy_in(d.fw, F, f0, src.fw, fk, rw.NG, st))) ||
       (s = copy_in(d.fl, F, f0, src.fl, fk, 1, st)) || (s = copy_in(d.fr, F, f0, src.fr, fk, 1, st)) ||
       (s = copy_in(d.ftag, F, f0, src.ftag, fk, 1, st)) || (s = copy_in(d.fT, F, f0, src.fT, fk, 9, st)) ||
       (s = copy_in(d.fS, F, f0, src.fS, fk, 1, st)) || (s = copy_in(d.fdist, F, f0, src.fdist, fk, 1, st)) ||
-      (weno && ((s = copy_in(d.sten, N, c0, src.sten, nk, kBig, st)) || (s = copy_in(d.X0, N, c0, src.X0, nk, 9 * kBig, st)) ||
-                (s = copy_in(d.Xs, N, c0, src.Xs, nk, 12 * kSubK, st)) || (s = copy_in(d.ssl, N, c0, src.ssl, nk, 4, st)))) ||
-      (hweno && ((s = copy_in(d.H0, N, c0, src.H0, nk, 9 * 19, st)) || (s = copy_in(d.Hm, N, c0, src.Hm, nk, 12 * 7, st)))))
+      (weno && ((s = copy_in(d.sten, N, c0, src.sten, nk, rw.BIG, st)) ||
+                (s = copy_in(d.X0, N, c0, src.X0, nk, 9 * rw.BIG, st)) ||
+                (s = copy_in(d.Xs, N, c0, src.Xs, nk, rw.NSUBW * 3 * rw.SUBK, st)) ||
+                (s = copy_in(d.ssl, N, c0, src.ssl, nk, rw.NSUBW, st)))) ||
+      (hweno && ((s = copy_in(d.H0, N, c0, src.H0, nk, 9 * rw.HCOLS, st)) ||
+                 (s = copy_in(d.Hm, N, c0, src.Hm, nk, rw.NF * 21, st)))))
     return s;
   // padding cells of the range: no neighbours
   if (cpad > nk) {
-    BCUDA(cudaMemset2DAsync(d.cnb + c0 + nk, sizeof(int) * N, 0xff, sizeof(int) * (cpad - nk), 4, st));
-    BCUDA(cudaMemset2DAsync(d.cface + c0 + nk, sizeof(int) * N, 0xff, sizeof(int) * (cpad - nk), 4, st));
-    if (weno) BCUDA(cudaMemset2DAsync(d.sten + c0 + nk, sizeof(int) * N, 0xff, sizeof(int) * (cpad - nk), kBig, st));
+    BCUDA(cudaMemset2DAsync(d.cnb + c0 + nk, sizeof(int) * N, 0xff, sizeof(int) * (cpad - nk), rw.NF, st));
+    BCUDA(cudaMemset2DAsync(d.cface + c0 + nk, sizeof(int) * N, 0xff, sizeof(int) * (cpad - nk), rw.NF, st));
+    if (weno) BCUDA(cudaMemset2DAsync(d.sten + c0 + nk, sizeof(int) * N, 0xff, sizeof(int) * (cpad - nk), rw.BIG, st));
   }
   // cell indices move by the range's first cell, face indices (2 f + side) by twice its first face
-  launch_offset_index(d.cnb + c0, 4, nk, N, c0, st);
-  launch_offset_index(d.cface + c0, 4, nk, N, 2 * f0, st);
-  if (weno) launch_offset_index(d.sten + c0, kBig, nk, N, c0, st);
+  launch_offset_index(d.cnb + c0, rw.NF, nk, N, c0, st);
+  launch_offset_index(d.cface + c0, rw.NF, nk, N, 2 * f0, st);
+  if (weno) launch_offset_index(d.sten + c0, rw.BIG, nk, N, c0, st);
   launch_offset_index(d.fl + f0, 1, fk, F, c0, st);
   launch_offset_index(d.fr + f0, 1, fk, F, c0, st);
   launch_fill_short(B.cmesh + c0, nk, (short)k, st);
@@ -504,7 +527,8 @@ hgks_status hgks_batch_create(const hgks_mesh *meshes, const hgks_params *params
     if (!meshes[k]) return fail_msg(HGKS_ERR_ARG, "a mesh handle is NULL");
     const Mesh &a = *mesh_of(meshes[k]);
     if (a.device != mesh_of(meshes[0])->device) return fail_msg(HGKS_ERR_ARG, "meshes of a batch must be on one device");
-    if (a.d.hex) return fail_msg(HGKS_ERR_ARG, "batches take tetrahedral meshes only");
+    if (a.d.hex != mesh_of(meshes[0])->d.hex)
+      return fail_msg(HGKS_ERR_ARG, "the meshes of a batch are all tetrahedra or all hexahedra");
     if ((st = take_params(a, &params[k], &P[k]))) return st;
     if (!same_shared(P[0], P[k]))
       return fail_msg(HGKS_ERR_ARG, "scheme, precision, jv_mode, krylov_dim, restarts, jacobi_sweeps must agree");
@@ -516,7 +540,8 @@ hgks_status hgks_batch_create(const hgks_mesh *meshes, const hgks_params *params
   schemes &= P[0].scheme == HGKS_WENO ? 1 : 2;
   HGKS_ON_DEVICE(mesh_of(meshes[0])->device);
   Batch *B = nullptr;
-  if ((st = batch_new(mesh_of(meshes[0])->device, N, F, n_meshes, P[0], schemes, &B))) return st;
+  if ((st = batch_new(mesh_of(meshes[0])->device, N, F, n_meshes, P[0], schemes, &B, mesh_of(meshes[0])->d.hex != 0)))
+    return st;
   for (int k = 0; k < n_meshes; k++) {
     int slot = -1;
     if ((st = batch_place(*B, source_of(*mesh_of(meshes[k])), P[k], &slot)) || slot != k) {
@@ -555,7 +580,7 @@ hgks_status hgks_batch_add(hgks_batch batch, hgks_mesh mesh, const hgks_params *
   *k_out = -1;
   const Mesh &a = *mesh_of(mesh);
   if (a.device != B.m.device) return fail_msg(HGKS_ERR_ARG, "mesh is on another device");
-  if (a.d.hex) return fail_msg(HGKS_ERR_ARG, "batches take tetrahedral meshes only");
+  if (a.d.hex != B.m.d.hex) return fail_msg(HGKS_ERR_ARG, "the meshes of a batch are all tetrahedra or all hexahedra");
   hgks_params P;
   hgks_status st = take_params(a, p, &P);
   if (st) return st;

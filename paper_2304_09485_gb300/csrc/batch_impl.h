@@ -29,7 +29,9 @@ struct MeshSource {
   const unsigned *ssl = nullptr;
   const signed char *ftag = nullptr;
   const double *fT = nullptr, *fS = nullptr, *fdist = nullptr;
+  const double *fw = nullptr;            // hexahedra: Gauss weights [4][F]
   int schemes = 0;
+  int hex = 0;                           // cell kind: 0 tetrahedra, 1 hexahedra
 };
 MeshSource source_of(const Mesh &m);
 MeshSource source_of(const HostMesh &hm, std::vector<double> &inv_vol_scratch);
@@ -68,8 +70,9 @@ bool compact(const Batch &B);
 bool same_shared(const hgks_params &a, const hgks_params &b);
 // device bytes of an arena of `cells` cells and `faces` faces
 int64_t arena_bytes(int64_t cells, int64_t faces, const hgks_params &shared, int schemes);
+// hex: the arena holds hexahedral meshes (HexShape rows); a batch holds one cell kind
 hgks_status batch_new(int device, int64_t cell_cap, int64_t face_cap, int nslot, const hgks_params &shared,
-                      int schemes, Batch **out);
+                      int schemes, Batch **out, bool hex = false);
 void batch_delete(Batch *B);
 // place a mesh into a free slot and free ranges: *slot = -1 if it does not fit
 hgks_status batch_place(Batch &B, const MeshSource &src, const hgks_params &p, int *slot);

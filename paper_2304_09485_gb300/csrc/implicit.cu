@@ -879,7 +879,10 @@ void launch_assemble(const DevMesh &m, Scratch &s, const hgks_params &p, const d
   float *dv32 = mixed ? s.dval32 : nullptr, *di32 = mixed ? s.dinv32 : nullptr, *jv = mixed ? s.jv32 : nullptr;
   HGKS_PROF_BEGIN(K_ASSEMBLE, st);
   batch = batch || m.ptab;
-  if (batch)
+  if (batch && m.hex)
+    k_assemble<true, HexShape::NF><<<grid_for(m.NL, kCellBlock), kCellBlock, 0, st>>>(m, p, Q, dt, s.dval, s.dinv, s.off,
+                                                                                       diag_out, off_out, dv32, di32, jv);
+  else if (batch)
     k_assemble<true, TetShape::NF><<<grid_for(m.NL, kCellBlock), kCellBlock, 0, st>>>(m, p, Q, dt, s.dval, s.dinv, s.off,
                                                                                        diag_out, off_out, dv32, di32, jv);
   else if (m.hex)

@@ -940,14 +940,15 @@ void launch_wall_force(const DevMesh &m, const Scratch &s, int tag, double *forc
 
 void launch_local_dt(const DevMesh &m, const hgks_params &p, const double *Q, double *dt, cudaStream_t st) {
   HGKS_PROF_BEGIN(K_DT, st);
-  if (m.ptab) k_local_dt<true, TetShape><<<grid_for(m.NL, kBlock), kBlock, 0, st>>>(m, p, Q, dt);
+  if (m.ptab && m.hex) k_local_dt<true, HexShape><<<grid_for(m.NL, kBlock), kBlock, 0, st>>>(m, p, Q, dt);
+  else if (m.ptab) k_local_dt<true, TetShape><<<grid_for(m.NL, kBlock), kBlock, 0, st>>>(m, p, Q, dt);
   else if (m.hex) k_local_dt<false, HexShape><<<grid_for(m.N, kBlock), kBlock, 0, st>>>(m, p, Q, dt);
   else k_local_dt<false, TetShape><<<grid_for(m.N, kBlock), kBlock, 0, st>>>(m, p, Q, dt);
   HGKS_PROF_END(K_DT, st);
 }
 
 namespace {
-// the four residual kernels of one cell kind; batches are tetrahedra only
+// the four residual kernels of one cell kind
 template <bool BATCH, class S>
 void residual_kernels(const DevMesh &m, Scratch &s, const hgks_params &p, const double *Q, const double *G, double *R,
                       double *Gnew, cudaStream_t st) {
@@ -975,7 +976,8 @@ void launch_residual(const DevMesh &m, Scratch &s, const hgks_params &p, const d
   HGKS_RANGE("hgks residual");
   batch = batch || m.ptab != nullptr;
   if (fresh_dt) launch_local_dt(m, p, Q, s.dt, st);
-  if (batch) residual_kernels<true, TetShape>(m, s, p, Q, G, R, Gnew, st);
+  if (batch && m.hex) residual_kernels<true, HexShape>(m, s, p, Q, G, R, Gnew, st);
+  else if (batch) residual_kernels<true, TetShape>(m, s, p, Q, G, R, Gnew, st);
   else if (m.hex) residual_kernels<false, HexShape>(m, s, p, Q, G, R, Gnew, st);
   else residual_kernels<false, TetShape>(m, s, p, Q, G, R, Gnew, st);
 }

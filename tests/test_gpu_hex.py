@@ -204,8 +204,9 @@ def test_hex_matrix_free_product(cuda):
 
 
 def test_hex_meshes_rejected_where_tetrahedra_only(cuda):
-    """The no-allocation residual and the batches take tetrahedra only: a hexahedral
-    mesh is refused with HGKS_ERR_ARG before any work."""
+    """The no-allocation residual and the server take tetrahedra, and a batch holds
+    one cell kind: a hexahedral mesh there, or hexahedra mixed with tetrahedra in
+    a batch, is refused with HGKS_ERR_ARG before any work."""
     import torch
     m, cond, om, hm = setup("hexcav5")
     ph = H.hgks_default_params(**cond)
@@ -213,9 +214,90 @@ def test_hex_meshes_rejected_where_tetrahedra_only(cuda):
     with pytest.raises(H.HGKSError) as e:
         H.hgks_residual_noalloc(hm, ph, Qd, None, torch.empty_like(Qd))
     assert e.value.status == 1
+    tet = H.hgks_mesh_create(I.cavity_mesh(3), scheme_mask=3)
     with pytest.raises(H.HGKSError) as e:
-        H.hgks_batch_create([hm], [ph])
+        H.hgks_batch_create([tet, hm], [ph, ph])
     assert e.value.status == 1
+    b = H.hgks_batch_create([tet], [ph])
+    with pytest.raises(H.HGKSError) as e:
+        H.hgks_batch_add(b, hm, ph)
+    assert e.value.status == 1
+
+
+def _hex_batch(kw, seed):
+    """Three hexahedral problems of different size and kind in one batch, and
+    the same problems as single meshes (states and handles)."""
+    import torch
+    probs = [(I.hex_cavity_mesh(4, seed=I.BASE_SEED + seed), I.cavity_conditions(0.15, 100.0)),
+             (I.hex_cavity_mesh(5, seed=I.BASE_SEED + seed + 1), I.cavity_conditions(0.2, 100.0)),
+             (I.hex_sphere_mesh(4, 6, stretch=I.sphere_stretch(6, dr1=6e-2)), I.sphere_conditions(0.2535, Re=118.0))]
+    meshes, params, singles = [], [], []
+    for k, (m, cond) in enumerate(probs):
+        hm = H.hgks_mesh_create(m, scheme_mask=3)
+        p = H.hgks_default_params(Pr=0.72, **cond, **kw)
+        Q, G = state(m, cond, seed=seed + k)
+        meshes.append(hm); params.append(p); singles.append((hm, p, hm.to_internal(Q), hm.to_internal(G)))
+    b = H.hgks_batch_create(meshes, params)
+    for k, (hm, p, Qd, Gd) in enumerate(singles):
+        H.hgks_batch_set_state(b, k, Qd, Gd)
+    torch.cuda.synchronize()
+    return b, singles
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_hex_batch_step_equals_single(cuda, precision):
+    """One batched implicit step of three hexahedral meshes (compact scheme) equals
+    each mesh's step alone: the residual norm to 1e-13, the update to 1e-10 (FP64;
+    2e-4 with the FP32 Krylov part, whose sums run in another order); replayed
+    from the batch's CUDA graph it equals the eager step bit for bit."""
+    import torch
+    kw = dict(scheme=1, krylov_dim=8, restarts=2, precision=precision)
+    b, singles = _hex_batch(kw, seed=310)
+    Q0 = [Qd.clone() for _, _, Qd, _ in singles]
+    G0 = [Gd.clone() for _, _, _, Gd in singles]
+    infos = H.hgks_batch_gmres_step(b, use_graph=False)
+    tol = 1e-10 if precision == 0 else 2e-4
+    for k, (hm, p, Qd, Gd) in enumerate(singles):
+        si = H.hgks_gmres_step(hm, p, Qd, Gd)
+        Qb = torch.empty_like(Qd)
+        H.hgks_batch_get_state(b, k, Q=Qb)
+        torch.cuda.synchronize()
+        assert abs(infos[k].res_l1 - si.res_l1) <= 1e-13 * si.res_l1
+        rel = (torch.linalg.norm((Qb - Q0[k]) - (Qd - Q0[k])) / torch.linalg.norm(Qd - Q0[k])).item()
+        assert rel <= tol, (k, rel)
+    out = {}
+    for mode in (False, True):
+        for k in range(len(singles)):
+            H.hgks_batch_set_state(b, k, Q0[k], G0[k])
+        H.hgks_batch_gmres_step(b, use_graph=mode)
+        Qs = [torch.empty_like(q) for q in Q0]
+        for k in range(len(singles)):
+            H.hgks_batch_get_state(b, k, Q=Qs[k])
+        torch.cuda.synchronize()
+        out[mode] = Qs
+    assert all(torch.equal(a, c) for a, c in zip(out[False], out[True]))
+
+
+def test_hex_batch_solve_converges_like_alone(cuda):
+    """Three hexahedral problems solved together to a 1e-5 drop (FP64, compact):
+    each converges with the step count, history (1e-9 of its reference) and state
+    (1e-9) it has alone."""
+    import torch
+    kw = dict(scheme=1, krylov_dim=10, restarts=3)
+    b, singles = _hex_batch(kw, seed=320)
+    starts = [(Qd.clone(), Gd.clone()) for _, _, Qd, Gd in singles]
+    infos, hist, ok = H.hgks_batch_solve_steady(b, 1e-5, 2000)
+    assert ok
+    for k, (hm, p, Qd, Gd) in enumerate(singles):
+        Q, G = starts[k][0].clone(), starts[k][1].clone()
+        si, hs, conv = H.hgks_solve_steady(hm, p, Q, G, drop_tol=1e-5, max_steps=2000)
+        assert conv and infos[k].converged and infos[k].steps == si.steps, (k, infos[k].steps, si.steps)
+        np.testing.assert_allclose(hist[k][: si.steps + 1], hs, rtol=0, atol=1e-9 * hs.max())
+        Qb, Gb = torch.empty_like(Q), torch.empty_like(G)
+        H.hgks_batch_get_state(b, k, Q=Qb, G=Gb)
+        torch.cuda.synchronize()
+        assert (torch.linalg.norm(Qb - Q) / torch.linalg.norm(Q)).item() <= 1e-9
+        assert (torch.linalg.norm(Gb - G) / torch.linalg.norm(G)).item() <= 1e-9
 
 
 @pytest.mark.parametrize("scheme", [1, 0])
