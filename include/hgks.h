@@ -184,8 +184,9 @@ hgks_status hgks_mesh_create(const double *xyz, int64_t n_vert, const int64_t *t
  * Gauss points weighted by the area element (exact for planar faces). Meshes
  * of hexahedra run through the single-mesh calls (residual, Jacobian, GMRES
  * step, solves, matrix-free products) and through batches made by
- * hgks_batch_create from hexahedral meshes only; hgks_residual_noalloc, empty
- * batches and the server take tetrahedra (HGKS_ERR_ARG otherwise). Errors as hgks_mesh_create, and
+ * hgks_batch_create from hexahedral meshes only and servers made by
+ * hgks_server_create_hex; hgks_residual_noalloc and empty batches take
+ * tetrahedra (HGKS_ERR_ARG otherwise). Errors as hgks_mesh_create, and
  * HGKS_ERR_MESH for an inverted hexahedron (Jacobian determinant <= 0 at a
  * Gauss point). */
 hgks_status hgks_mesh_create_hex(const double *xyz, int64_t n_vert, const int64_t *hex8, int64_t n_hex,
@@ -411,6 +412,10 @@ typedef struct {
  * restarts and jacobi_sweeps. use_graph != 0 replays the step from a CUDA graph. */
 hgks_status hgks_server_create(int32_t device, int64_t hbm_budget_bytes, int32_t max_inflight,
                                const hgks_params *shared, int32_t use_graph, hgks_server *out);
+/* The same for hexahedral meshes (a server takes one cell kind; submit them
+ * with hgks_server_submit_hex). */
+hgks_status hgks_server_create_hex(int32_t device, int64_t hbm_budget_bytes, int32_t max_inflight,
+                                   const hgks_params *shared, int32_t use_graph, hgks_server *out);
 /* Stops the build thread and frees everything, finished or not. */
 hgks_status hgks_server_destroy(hgks_server server);
 /* Queue a steady solve. Mesh arrays as hgks_mesh_create (host, copied); Q0
@@ -424,6 +429,14 @@ hgks_status hgks_server_submit(hgks_server server, const double *xyz, int64_t n_
                                const double *periodic_shift, int32_t n_periodic, const hgks_params *p,
                                const double *Q0, const double *G0, double drop_tol, int32_t max_steps,
                                int64_t *id_out);
+/* A hexahedral request (mesh arrays as hgks_mesh_create_hex) to a server made by
+ * hgks_server_create_hex; HGKS_ERR_ARG on a tetrahedral server (and
+ * hgks_server_submit on a hexahedral one). */
+hgks_status hgks_server_submit_hex(hgks_server server, const double *xyz, int64_t n_vert, const int64_t *hex8,
+                                   int64_t n_hex, const int64_t *bquad4, const int32_t *btag, int64_t n_bface,
+                                   const double *periodic_shift, int32_t n_periodic, const hgks_params *p,
+                                   const double *Q0, const double *G0, double drop_tol, int32_t max_steps,
+                                   int64_t *id_out);
 /* One scheduling round (admit, one batched step, retire). Outputs (may be
  * NULL): solves finished in this round, solves running, requests waiting
  * (for their build, in it, or for admission: zero running and zero waiting

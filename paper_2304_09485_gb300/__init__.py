@@ -108,9 +108,12 @@ def lib():
             "hgks_batch_add": [vp, vp, P, C.POINTER(C.c_int32)],
             "hgks_batch_remove": [vp, i32],
             "hgks_server_create": [i32, i64, i32, P, i32, C.POINTER(vp)],
+            "hgks_server_create_hex": [i32, i64, i32, P, i32, C.POINTER(vp)],
             "hgks_server_destroy": [vp],
             "hgks_server_submit": [vp, dp, i64, dp, i64, dp, dp, i64, dp, i32, P, dp, dp, C.c_double, i32,
                                    C.POINTER(C.c_int64)],
+            "hgks_server_submit_hex": [vp, dp, i64, dp, i64, dp, dp, i64, dp, i32, P, dp, dp, C.c_double, i32,
+                                       C.POINTER(C.c_int64)],
             "hgks_server_step": [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
             "hgks_server_status": [vp, i64, C.POINTER(hgks_request_info)],
             "hgks_server_collect": [vp, i64, dp, dp],
@@ -401,12 +404,13 @@ def hgks_batch_autotune(batch, stream=None):
 
 
 class hgks_server:
-    """Continuous-batching request server (hgks_server_*)."""
+    """Continuous-batching request server (hgks_server_*); hexahedra=True makes a
+    server of hexahedral meshes (hgks_server_create_hex)."""
 
-    def __init__(self, shared, hbm_budget_bytes, max_inflight=64, use_graph=True, device=0):
+    def __init__(self, shared, hbm_budget_bytes, max_inflight=64, use_graph=True, device=0, hexahedra=False):
         h = C.c_void_p()
-        _check(lib().hgks_server_create(device, int(hbm_budget_bytes), max_inflight, C.byref(shared),
-                                        1 if use_graph else 0, C.byref(h)))
+        fn = lib().hgks_server_create_hex if hexahedra else lib().hgks_server_create
+        _check(fn(device, int(hbm_budget_bytes), max_inflight, C.byref(shared), 1 if use_graph else 0, C.byref(h)))
         self.handle = h
         self.n_cells = {}
 
@@ -419,20 +423,23 @@ class hgks_server:
             self.handle = C.c_void_p(0)
 
     def submit(self, mesh, params, Q0, G0=None, drop_tol=1e-8, max_steps=1000) -> int:
-        """Queue a solve of an inputs.Mesh from Q0 (caller order [n, 5]); returns its id."""
+        """Queue a solve of an inputs.Mesh (or inputs.HexMesh) from Q0 (caller order
+        [n, 5]); returns its id."""
+        hexa = hasattr(mesh, "hex8")
         xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
-        tet = np.ascontiguousarray(mesh.tet4, dtype=np.int64)
-        bf = np.ascontiguousarray(mesh.bface3, dtype=np.int64).reshape(-1, 3)
+        tet = np.ascontiguousarray(mesh.hex8 if hexa else mesh.tet4, dtype=np.int64)
+        bf = np.ascontiguousarray(mesh.bface4 if hexa else mesh.bface3, dtype=np.int64).reshape(-1, 4 if hexa else 3)
         bt = np.ascontiguousarray(mesh.btag, dtype=np.int32)
         ps = mesh.periodic_shift
         psa = np.ascontiguousarray(ps if ps is not None else np.zeros((0, 3)), dtype=np.float64)
         q = np.ascontiguousarray(Q0, dtype=np.float64)
         g = None if G0 is None else np.ascontiguousarray(G0, dtype=np.float64)
         rid = C.c_int64(0)
-        _check(lib().hgks_server_submit(self.handle, _ptr(xyz), xyz.shape[0], _ptr(tet), tet.shape[0],
-                                        _ptr(bf) if len(bf) else None, _ptr(bt) if len(bt) else None, bf.shape[0],
-                                        _ptr(psa) if len(psa) else None, psa.shape[0], C.byref(params), _ptr(q),
-                                        _ptr(g), drop_tol, max_steps, C.byref(rid)))
+        fn = lib().hgks_server_submit_hex if hexa else lib().hgks_server_submit
+        _check(fn(self.handle, _ptr(xyz), xyz.shape[0], _ptr(tet), tet.shape[0],
+                  _ptr(bf) if len(bf) else None, _ptr(bt) if len(bt) else None, bf.shape[0],
+                  _ptr(psa) if len(psa) else None, psa.shape[0], C.byref(params), _ptr(q),
+                  _ptr(g), drop_tol, max_steps, C.byref(rid)))
         self.n_cells[rid.value] = tet.shape[0]
         return rid.value
 

@@ -129,6 +129,16 @@ hgks_status launch_status() {
 
 }  // namespace
 
+// rows of the per-cell and per-face arrays of a cell kind
+struct Rows {
+  int NF, NG, BIG, NSUBW, SUBK, HCOLS;
+  explicit Rows(bool hex)
+      : NF(hex ? HexShape::NF : TetShape::NF), NG(hex ? HexShape::NG : TetShape::NG),
+        BIG(hex ? HexShape::BIG : TetShape::BIG), NSUBW(hex ? HexShape::NSUBW : TetShape::NSUBW),
+        SUBK(hex ? HexShape::SUBK : TetShape::SUBK),
+        HCOLS(hex ? ShapeOf<HexShape>::HCOLS : ShapeOf<TetShape>::HCOLS) {}
+};
+
 bool compact(const Batch &B) { return B.p0.scheme == HGKS_HWENO; }
 
 // the cells and faces the kernels of a batch cover: up to the end of the last range in use
@@ -147,17 +157,19 @@ bool same_shared(const hgks_params &a, const hgks_params &b) {
 }
 
 // Device bytes of an arena (the allocations of batch_new and ensure_scratch).
-int64_t arena_bytes(int64_t cells, int64_t faces, const hgks_params &p, int schemes) {
+int64_t arena_bytes(int64_t cells, int64_t faces, const hgks_params &p, int schemes, bool hex) {
   const int64_t N = cells, F = faces, nb = cells / kBatchBlock;
   const bool mixed = p.precision == HGKS_MIXED, hw = p.scheme == HGKS_HWENO;
+  const Rows rw(hex);
+  const int64_t ncoef = 45 + 15 * std::max(rw.NSUBW, rw.NF);
   int64_t c = 0;
-  c += 8 * (3 + 6 + 36) + 4 * 8 + 1 + 2;                       // geometry, neighbours, faces, mesh id
-  if (schemes & 1) c += 4 * kBig + 8 * 9 * kBig + 8 * 12 * kSubK + 4 * 4;   // big stencil, its matrices, sub-stencil slots
-  if (schemes & 2) c += 8 * (9 * 19 + 12 * 7);                  // compact matrices
+  c += 8 * (3 + 6 + rw.NF * rw.NG * 3) + 4 * 2 * rw.NF + 1 + 2;   // geometry, neighbours, faces, mesh id
+  if (schemes & 1) c += 4 * rw.BIG + 8 * 9 * rw.BIG + 8 * rw.NSUBW * 3 * rw.SUBK + 4 * rw.NSUBW;   // big stencil, matrices, slots
+  if (schemes & 2) c += 8 * (9 * rw.HCOLS + rw.NF * 21);       // compact matrices
   c += 8 * (5 + (hw ? 15 : 0));                                 // Q, G
-  c += 8 * (kCoef + 1 + 100 + 2 + 5 + 15 + 5 + 15);             // coef, dt, off, dval/dinv, R, Gnew, dQ, w/t/t2
-  c += mixed ? (4 * 22 + 4 * 2 + 4 * 15 + 4 * 5 * (p.krylov_dim + 1)) : 8 * 5 * (p.krylov_dim + 1);
-  const int64_t f = 4 * 2 + 1 + 8 * (9 + 2) + 2 + 8 * (2 * 3 * kFaceState + 15 + 15);
+  c += 8 * (ncoef + 1 + 25 * rw.NF + 2 + 5 + 15 + 5 + 15);      // coef, dt, off, dval/dinv, R, Gnew, dQ, w/t/t2
+  c += mixed ? (4 * (6 + 4 * rw.NF) + 4 * 2 + 4 * 15 + 4 * 5 * (p.krylov_dim + 1)) : 8 * 5 * (p.krylov_dim + 1);
+  const int64_t f = 4 * 2 + 1 + 8 * (9 + 2 + (hex ? rw.NG : 0)) + 2 + 8 * (2 * rw.NG * kFaceState + 10 * rw.NG);
   return N * c + F * f + nb * (2 + 8 + 4 + (mixed ? 4 * 2 * kBatchMdot : 0)) + 8 * std::max<int64_t>(4096, N / 64 + 64) +
          (64 << 10);
 }
@@ -192,16 +204,6 @@ hgks_status leave(Batch &B, cudaStream_t user) {
 namespace hgks {
 
 // An empty arena of cell_cap cells (rounded up to kBatchBlock) and face_cap faces.
-// rows of the per-cell and per-face arrays of a cell kind
-struct Rows {
-  int NF, NG, BIG, NSUBW, SUBK, HCOLS;
-  explicit Rows(bool hex)
-      : NF(hex ? HexShape::NF : TetShape::NF), NG(hex ? HexShape::NG : TetShape::NG),
-        BIG(hex ? HexShape::BIG : TetShape::BIG), NSUBW(hex ? HexShape::NSUBW : TetShape::NSUBW),
-        SUBK(hex ? HexShape::SUBK : TetShape::SUBK),
-        HCOLS(hex ? ShapeOf<HexShape>::HCOLS : ShapeOf<TetShape>::HCOLS) {}
-};
-
 hgks_status batch_new(int device, int64_t cell_cap, int64_t face_cap, int nslot, const hgks_params &shared,
                       int schemes, Batch **out, bool hex) {
   *out = nullptr;

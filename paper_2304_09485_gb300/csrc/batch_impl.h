@@ -69,7 +69,7 @@ struct Batch {
 bool compact(const Batch &B);
 bool same_shared(const hgks_params &a, const hgks_params &b);
 // device bytes of an arena of `cells` cells and `faces` faces
-int64_t arena_bytes(int64_t cells, int64_t faces, const hgks_params &shared, int schemes);
+int64_t arena_bytes(int64_t cells, int64_t faces, const hgks_params &shared, int schemes, bool hex = false);
 // hex: the arena holds hexahedral meshes (HexShape rows); a batch holds one cell kind
 hgks_status batch_new(int device, int64_t cell_cap, int64_t face_cap, int nslot, const hgks_params &shared,
                       int schemes, Batch **out, bool hex = false);

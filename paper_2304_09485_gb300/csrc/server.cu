@@ -35,7 +35,8 @@ enum { Q_WAIT = 0, Q_BUILT = 1, Q_RUN = 2, Q_DONE = 3, Q_FAIL = 4 };
 struct Request {
   int64_t id = 0;
   std::vector<double> xyz, pshift;
-  std::vector<int64_t> tet, bface;
+  std::vector<int64_t> tet, bface;     // cells [n][nvc] and boundary faces
+  int32_t nvc = 4;                     // vertices per cell: 4 tetrahedra, 8 hexahedra
   std::vector<int32_t> btag;
   int32_t nps = 0;
   hgks_params p{};
@@ -94,7 +95,8 @@ void builder_loop(hgks_server_s *S) {
     std::string err;
     hgks_status st;
     try {
-      st = build_host_mesh(r->xyz.data(), (int64_t)r->xyz.size() / 3, r->tet.data(), 4, (int64_t)r->tet.size() / 4,
+      st = build_host_mesh(r->xyz.data(), (int64_t)r->xyz.size() / 3, r->tet.data(), r->nvc,
+                           (int64_t)r->tet.size() / r->nvc,
                            r->bface.empty() ? nullptr : r->bface.data(), r->btag.empty() ? nullptr : r->btag.data(),
                            (int64_t)r->btag.size(), r->pshift.empty() ? nullptr : r->pshift.data(), r->nps, mask, r->hm,
                            err);
@@ -265,31 +267,28 @@ hgks_status retire(hgks_server_s &S, const std::vector<int> &act, int *n_finishe
   return HGKS_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-hgks_status hgks_server_create(int32_t device, int64_t hbm_budget_bytes, int32_t max_inflight, const hgks_params *shared,
-                               int32_t use_graph, hgks_server *out) {
+hgks_status server_create(int32_t device, int64_t hbm_budget_bytes, int32_t max_inflight, const hgks_params *shared,
+                          int32_t use_graph, bool hex, hgks_server *out) {
   if (!out || !shared) return fail_msg(HGKS_ERR_ARG, "NULL argument");
   *out = nullptr;
   if (max_inflight < 1 || max_inflight > 32767) return fail_msg(HGKS_ERR_ARG, "max_inflight must be in 1..32767");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return fail_msg(HGKS_ERR_ARG, "no such device");
   const int schemes = shared->scheme == HGKS_WENO ? 1 : 2;
-  // the largest arena (faces: 2.1 per cell, the tetrahedral ratio plus boundary) within the budget
-  auto faces_for = [](int64_t n) { return n * 21 / 10 + 4096; };
+  // the largest arena within the budget (faces: 2.1 per cell for tetrahedra, 3.1 for
+  // hexahedra, the interior ratios plus boundary)
+  auto faces_for = [hex](int64_t n) { return n * (hex ? 31 : 21) / 10 + 4096; };
   int64_t lo = 0, hi = (int64_t)(INT32_MAX / 14);
   while (hi - lo > kBatchBlock) {
     const int64_t mid = (lo + hi) / 2;
-    if (arena_bytes(mid, faces_for(mid), *shared, schemes) <= hbm_budget_bytes) lo = mid; else hi = mid;
+    if (arena_bytes(mid, faces_for(mid), *shared, schemes, hex) <= hbm_budget_bytes) lo = mid; else hi = mid;
   }
   const int64_t ncap = lo / kBatchBlock * kBatchBlock;
   if (ncap < kBatchBlock) return fail_msg(HGKS_ERR_ARG, "HBM budget too small for any mesh");
   HGKS_ON_DEVICE(device);
   hgks_server_s *S = new (std::nothrow) hgks_server_s;
   if (!S) return fail_msg(HGKS_ERR_OOM, "host allocation");
-  hgks_status st = batch_new(device, ncap, faces_for(ncap), max_inflight, *shared, schemes, &S->B);
+  hgks_status st = batch_new(device, ncap, faces_for(ncap), max_inflight, *shared, schemes, &S->B, hex);
   if (st) { delete S; return st; }
   S->t0 = std::chrono::steady_clock::now();
   S->running.assign(max_inflight, nullptr);
@@ -297,6 +296,19 @@ hgks_status hgks_server_create(int32_t device, int64_t hbm_budget_bytes, int32_t
   S->builder = std::thread(builder_loop, S);
   *out = S;
   return HGKS_OK;
+}
+}  // namespace
+
+extern "C" {
+
+hgks_status hgks_server_create(int32_t device, int64_t hbm_budget_bytes, int32_t max_inflight, const hgks_params *shared,
+                               int32_t use_graph, hgks_server *out) {
+  return server_create(device, hbm_budget_bytes, max_inflight, shared, use_graph, false, out);
+}
+
+hgks_status hgks_server_create_hex(int32_t device, int64_t hbm_budget_bytes, int32_t max_inflight,
+                                   const hgks_params *shared, int32_t use_graph, hgks_server *out) {
+  return server_create(device, hbm_budget_bytes, max_inflight, shared, use_graph, true, out);
 }
 
 hgks_status hgks_server_destroy(hgks_server S) {
@@ -312,14 +324,21 @@ hgks_status hgks_server_destroy(hgks_server S) {
   return HGKS_OK;
 }
 
-hgks_status hgks_server_submit(hgks_server S, const double *xyz, int64_t n_vert, const int64_t *tet4, int64_t n_tet,
-                               const int64_t *bface3, const int32_t *btag, int64_t n_bface, const double *periodic_shift,
-                               int32_t n_periodic, const hgks_params *p, const double *Q0, const double *G0,
-                               double drop_tol, int32_t max_steps, int64_t *id_out) {
+}  // extern "C"
+
+namespace {
+hgks_status server_submit(hgks_server S, const double *xyz, int64_t n_vert, const int64_t *tet4, int32_t nvc,
+                          int64_t n_tet, const int64_t *bface3, const int32_t *btag, int64_t n_bface,
+                          const double *periodic_shift, int32_t n_periodic, const hgks_params *p, const double *Q0,
+                          const double *G0, double drop_tol, int32_t max_steps, int64_t *id_out) {
   if (!S || !p || !xyz || !tet4 || !Q0 || !id_out) return fail_msg(HGKS_ERR_ARG, "NULL argument");
   if (n_tet <= 0 || n_vert <= 0 || n_bface < 0 || n_periodic < 0) return fail_msg(HGKS_ERR_ARG, "bad sizes");
   if (!(drop_tol > 0.0) || max_steps < 0) return fail_msg(HGKS_ERR_ARG, "drop_tol must be > 0 and max_steps >= 0");
   Batch &B = *S->B;
+  if ((nvc == 8) != (B.m.d.hex != 0))
+    return fail_msg(HGKS_ERR_ARG, "a server takes one cell kind: tetrahedra (hgks_server_create) or hexahedra "
+                                  "(hgks_server_create_hex)");
+  const int64_t nfv = nvc == 8 ? 4 : 3;
   Mesh probe;
   probe.schemes = B.m.schemes;
   hgks_params P;
@@ -332,10 +351,11 @@ hgks_status hgks_server_submit(hgks_server S, const double *xyz, int64_t n_vert,
     return fail_msg(HGKS_ERR_ARG, "mesh larger than the server's arena (HBM budget)");
   auto r = std::make_unique<Request>();
   r->xyz.assign(xyz, xyz + 3 * n_vert);
-  r->tet.assign(tet4, tet4 + 4 * n_tet);
+  r->nvc = nvc;
+  r->tet.assign(tet4, tet4 + (int64_t)nvc * n_tet);
   if (n_bface) {
     if (!bface3 || !btag) return fail_msg(HGKS_ERR_ARG, "boundary arrays are NULL");
-    r->bface.assign(bface3, bface3 + 3 * n_bface);
+    r->bface.assign(bface3, bface3 + nfv * n_bface);
     r->btag.assign(btag, btag + n_bface);
   }
   if (n_periodic) {
@@ -356,6 +376,26 @@ hgks_status hgks_server_submit(hgks_server S, const double *xyz, int64_t n_vert,
   S->all[r->id] = std::move(r);
   S->cv.notify_all();
   return HGKS_OK;
+}
+}  // namespace
+
+extern "C" {
+
+hgks_status hgks_server_submit(hgks_server S, const double *xyz, int64_t n_vert, const int64_t *tet4, int64_t n_tet,
+                               const int64_t *bface3, const int32_t *btag, int64_t n_bface, const double *periodic_shift,
+                               int32_t n_periodic, const hgks_params *p, const double *Q0, const double *G0,
+                               double drop_tol, int32_t max_steps, int64_t *id_out) {
+  return server_submit(S, xyz, n_vert, tet4, 4, n_tet, bface3, btag, n_bface, periodic_shift, n_periodic, p, Q0, G0,
+                       drop_tol, max_steps, id_out);
+}
+
+hgks_status hgks_server_submit_hex(hgks_server S, const double *xyz, int64_t n_vert, const int64_t *hex8, int64_t n_hex,
+                                   const int64_t *bquad4, const int32_t *btag, int64_t n_bface,
+                                   const double *periodic_shift, int32_t n_periodic, const hgks_params *p,
+                                   const double *Q0, const double *G0, double drop_tol, int32_t max_steps,
+                                   int64_t *id_out) {
+  return server_submit(S, xyz, n_vert, hex8, 8, n_hex, bquad4, btag, n_bface, periodic_shift, n_periodic, p, Q0, G0,
+                       drop_tol, max_steps, id_out);
 }
 
 hgks_status hgks_server_step(hgks_server S, int32_t *n_finished, int32_t *n_running, int32_t *n_waiting) {
@@ -413,7 +453,7 @@ hgks_status hgks_server_status(hgks_server S, int64_t id, hgks_request_info *inf
   std::memset(info, 0, sizeof(*info));
   info->state = r.state;
   info->status = r.status;
-  info->n_cells = (int64_t)(r.perm.empty() ? r.tet.size() / 4 : r.perm.size());
+  info->n_cells = (int64_t)(r.perm.empty() ? r.tet.size() / r.nvc : r.perm.size());
   info->solve = r.info;
   info->t_submit = r.t_submit;
   info->t_built = r.t_built;

@@ -396,3 +396,53 @@ def test_hex_host_variants_resume_and_wall_force(cuda):
         fo = om.wall_force(po, Q, G, tag)
         fg = H.hgks_wall_force(hm, p, hm.to_internal(Q), hm.to_internal(G), tag)
         assert np.abs(fg - fo).max() <= 1e-11 * np.abs(fo).max()
+
+
+def test_hex_server_results_equal_alone(cuda):
+    """A server of hexahedral meshes (hgks_server_create_hex): three requests of
+    different size and kind, each served result equals the same solve alone
+    (steps, convergence, state within 1e-9); a tetrahedral request to it, and a
+    hexahedral one to a tetrahedral server, are refused with HGKS_ERR_ARG."""
+    import time
+    import torch
+    kw = dict(scheme=0, krylov_dim=8, restarts=2, jacobi_sweeps=2)
+    probs = [(I.hex_cavity_mesh(4, seed=I.BASE_SEED + 330), I.cavity_conditions(0.2, 100.0)),
+             (I.hex_cavity_mesh(5, seed=I.BASE_SEED + 331), I.cavity_conditions(0.3, 200.0)),
+             (I.hex_sphere_mesh(4, 6, stretch=I.sphere_stretch(6, dr1=6e-2)), I.sphere_conditions(0.3))]
+    srv = H.hgks_server(H.hgks_default_params(**kw), hbm_budget_bytes=int(400e6), max_inflight=4, hexahedra=True)
+    ids, reqs = [], []
+    for k, (m, cond) in enumerate(probs):
+        p = H.hgks_default_params(**{**cond, "Pr": 0.72 if cond["viscous"] else 1.0, **kw})
+        Q0, _ = state(m, cond, seed=340 + k)
+        ids.append(srv.submit(m, p, Q0, drop_tol=1e-3, max_steps=60))
+        reqs.append((m, p, Q0))
+    rounds = 0
+    while True:
+        fin, run, wait = srv.step()
+        rounds += 1
+        if run == 0 and wait == 0:
+            break
+        if run == 0:
+            time.sleep(0.005)
+        assert rounds < 5000
+    for rid, (m, p, Q0) in zip(ids, reqs):
+        st = srv.status(rid)
+        assert st.state == 3
+        Qs, _ = srv.collect(rid)
+        hm = H.hgks_mesh_create(m, scheme_mask=1)
+        Qd = hm.to_internal(Q0)
+        info, _, conv = H.hgks_solve_steady(hm, p, Qd, None, drop_tol=1e-3, max_steps=60)
+        torch.cuda.synchronize()
+        assert st.solve.steps == info.steps and bool(st.solve.converged) == bool(conv)
+        Qa = hm.to_caller(Qd)
+        assert np.linalg.norm(Qs - Qa) / np.linalg.norm(Qa) <= 1e-9
+    tm, tc = I.cavity_mesh(3), I.cavity_conditions()
+    tp = H.hgks_default_params(**{**tc, "Pr": 0.72, **kw})
+    with pytest.raises(H.HGKSError) as e:
+        srv.submit(tm, tp, I.state_from_conditions(tm.n_tet, tc))
+    assert e.value.status == 1
+    tsrv = H.hgks_server(H.hgks_default_params(**kw), hbm_budget_bytes=int(200e6), max_inflight=2)
+    m, p, Q0 = reqs[0]
+    with pytest.raises(H.HGKSError) as e:
+        tsrv.submit(m, p, Q0)
+    assert e.value.status == 1
