@@ -183,10 +183,9 @@ hgks_status hgks_mesh_create(const double *xyz, int64_t n_vert, const int64_t *t
  * through its vertices, with area and normal from its vector area and 2 x 2
  * Gauss points weighted by the area element (exact for planar faces). Meshes
  * of hexahedra run through the single-mesh calls (residual, Jacobian, GMRES
- * step, solves, matrix-free products) and through batches made by
- * hgks_batch_create from hexahedral meshes only and servers made by
- * hgks_server_create_hex; hgks_residual_noalloc and empty batches take
- * tetrahedra (HGKS_ERR_ARG otherwise). Errors as hgks_mesh_create, and
+ * step, solves, matrix-free products, hgks_residual_noalloc), through batches
+ * made by hgks_batch_create from hexahedral meshes only and through servers made
+ * by hgks_server_create_hex; empty batches take tetrahedra (HGKS_ERR_ARG otherwise). Errors as hgks_mesh_create, and
  * HGKS_ERR_MESH for an inverted hexahedron (Jacobian determinant <= 0 at a
  * Gauss point). */
 hgks_status hgks_mesh_create_hex(const double *xyz, int64_t n_vert, const int64_t *hex8, int64_t n_hex,
@@ -283,8 +282,8 @@ hgks_status hgks_gmres_step_host(hgks_mesh mesh, const hgks_params *p, double *Q
  * it answers requests). The mesh is still created up front with
  * hgks_mesh_create; this call leaves the handle's own scratch untouched and uses
  * one fixed array of 32 MiB compiled into the library instead. Meshes larger
- * than that array allows (about 10,000 tetrahedra: 106 N + 150 F doubles) are
- * rejected with HGKS_ERR_ARG. Arguments, checks, layouts and results are those of
+ * than that array allows (about 10,000 tetrahedra: 106 N + 150 F doubles; about
+ * 5,000 hexahedra: 166 N + 200 F) are rejected with HGKS_ERR_ARG. Arguments, checks, layouts and results are those of
  * hgks_residual (the same kernels: the results are identical).
  * Set-up: under CUDA's lazy module loading (the default) the driver allocates
  * the array on a device when the first call of this entry point on that device

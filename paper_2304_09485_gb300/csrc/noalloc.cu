@@ -32,10 +32,17 @@ namespace {
 std::mutex g_noalloc_mu;
 double *g_noalloc_ptr[64] = {nullptr};   // device address of the array, per device
 
+// sizes of the regions, per cell and per face, of one cell kind
+struct NoallocRows {
+  size_t coef, face;      // coefficients per cell; Gauss points per face
+  explicit NoallocRows(bool hex)
+      : coef(hex ? ShapeOf<HexShape>::COEF : ShapeOf<TetShape>::COEF), face(hex ? HexShape::NG : TetShape::NG) {}
+};
 // doubles of scratch one residual evaluation needs on an (N cells, F faces) mesh
-size_t noalloc_need(size_t N, size_t F) {
+size_t noalloc_need(size_t N, size_t F, bool hex) {
   auto up = [](size_t n) { return (n + 31) / 32 * 32; };   // keep every region 256-byte aligned
-  return up((size_t)kCoef * N) + up(N) + up((size_t)2 * 3 * kFaceState * F) + 2 * up((size_t)15 * F) + 32;
+  const NoallocRows r(hex);
+  return up(r.coef * N) + up(N) + up(2 * r.face * kFaceState * F) + 2 * up(5 * r.face * F) + 32;
 }
 }  // namespace
 
@@ -53,11 +60,11 @@ extern "C" hgks_status hgks_residual_noalloc(hgks_mesh mesh, const hgks_params *
   p = &P;
   if (!Q || !R) return fail_msg(HGKS_ERR_ARG, "Q or R is NULL");
   if (p->scheme == HGKS_HWENO && (!G || !G_new)) return fail_msg(HGKS_ERR_ARG, "compact scheme needs G and G_new");
-  if (m.d.hex) return fail_msg(HGKS_ERR_ARG, "this entry point takes tetrahedral meshes only");
-  const size_t need = noalloc_need((size_t)m.N, (size_t)m.F);
+  const bool hex = m.d.hex != 0;
+  const size_t need = noalloc_need((size_t)m.N, (size_t)m.F, hex);
   if (need > kNoallocDoubles)
-    return fail_msg(HGKS_ERR_ARG,
-                    "mesh too large for the static scratch of hgks_residual_noalloc (32 MiB: about 10,000 tetrahedra)");
+    return fail_msg(HGKS_ERR_ARG, "mesh too large for the static scratch of hgks_residual_noalloc "
+                                  "(32 MiB: about 10,000 tetrahedra or 5,000 hexahedra)");
   if (m.device < 0 || m.device >= 64) return fail_msg(HGKS_ERR_ARG, "device index out of range");
   HGKS_ON_DEVICE(m.device);
   double *base;
@@ -74,13 +81,14 @@ extern "C" hgks_status hgks_residual_noalloc(hgks_mesh mesh, const hgks_params *
   }
   auto up = [](size_t n) { return (n + 31) / 32 * 32; };
   const size_t N = m.N, F = m.F;
+  const NoallocRows r(hex);
   Scratch s;
   s.coef = base;
-  s.dt = s.coef + up((size_t)kCoef * N);
+  s.dt = s.coef + up(r.coef * N);
   s.wface = s.dt + up(N);
-  s.fflux = s.wface + up((size_t)2 * 3 * kFaceState * F);
-  s.fpt = s.fflux + up((size_t)15 * F);
-  s.flags = (int *)(s.fpt + up((size_t)15 * F));
+  s.fflux = s.wface + up(2 * r.face * kFaceState * F);
+  s.fpt = s.fflux + up(5 * r.face * F);
+  s.flags = (int *)(s.fpt + up(5 * r.face * F));
   cudaStream_t st = (cudaStream_t)cuda_stream;
   // the positivity counter must start at zero; every other region is fully
   // written before it is read

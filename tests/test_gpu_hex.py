@@ -203,17 +203,22 @@ def test_hex_matrix_free_product(cuda):
     assert err.max() <= 2 * TOL_R, err.max()
 
 
-def test_hex_meshes_rejected_where_tetrahedra_only(cuda):
-    """The no-allocation residual and the server take tetrahedra, and a batch holds
-    one cell kind: a hexahedral mesh there, or hexahedra mixed with tetrahedra in
-    a batch, is refused with HGKS_ERR_ARG before any work."""
+def test_hex_noalloc_and_mixed_batches(cuda):
+    """The no-allocation residual of a hexahedral mesh equals hgks_residual bit for
+    bit; a batch holds one cell kind: hexahedra mixed with tetrahedra are refused
+    with HGKS_ERR_ARG before any work."""
     import torch
     m, cond, om, hm = setup("hexcav5")
+    ph = H.hgks_default_params(scheme=1, Pr=0.72, **cond)
+    Q, G = state(m, cond, seed=23)
+    Qd, Gd = hm.to_internal(Q), hm.to_internal(G)
+    R1, R2 = torch.empty_like(Qd), torch.empty_like(Qd)
+    G1, G2 = torch.empty_like(Gd), torch.empty_like(Gd)
+    H.hgks_residual(hm, ph, Qd, Gd, R1, G1)
+    H.hgks_residual_noalloc(hm, ph, Qd, Gd, R2, G2)
+    torch.cuda.synchronize()
+    assert torch.equal(R1, R2) and torch.equal(G1, G2)
     ph = H.hgks_default_params(**cond)
-    Qd = hm.to_internal(I.state_from_conditions(m.n_cells, cond))
-    with pytest.raises(H.HGKSError) as e:
-        H.hgks_residual_noalloc(hm, ph, Qd, None, torch.empty_like(Qd))
-    assert e.value.status == 1
     tet = H.hgks_mesh_create(I.cavity_mesh(3), scheme_mask=3)
     with pytest.raises(H.HGKSError) as e:
         H.hgks_batch_create([tet, hm], [ph, ph])
