@@ -184,8 +184,9 @@ hgks_status hgks_mesh_create(const double *xyz, int64_t n_vert, const int64_t *t
  * Gauss points weighted by the area element (exact for planar faces). Meshes
  * of hexahedra run through the single-mesh calls (residual, Jacobian, GMRES
  * step, solves, matrix-free products, hgks_residual_noalloc), through batches
- * made by hgks_batch_create from hexahedral meshes only and through servers made
- * by hgks_server_create_hex; empty batches take tetrahedra (HGKS_ERR_ARG otherwise). Errors as hgks_mesh_create, and
+ * of hexahedral meshes (hgks_batch_create, hgks_batch_create_empty_hex) and
+ * through servers made by hgks_server_create_hex: a batch or a server holds one
+ * cell kind (HGKS_ERR_ARG otherwise). Errors as hgks_mesh_create, and
  * HGKS_ERR_MESH for an inverted hexahedron (Jacobian determinant <= 0 at a
  * Gauss point). */
 hgks_status hgks_mesh_create_hex(const double *xyz, int64_t n_vert, const int64_t *hex8, int64_t n_hex,
@@ -336,10 +337,13 @@ hgks_status hgks_batch_info(hgks_batch batch, hgks_batch_info_t *info);
 /* An empty batch: an arena of cell_capacity cells and face_capacity faces with
  * max_meshes slots, for meshes whose params agree with *shared in the fields
  * listed above (shared->scheme decides which reconstruction data it holds);
- * an empty batch holds tetrahedra (hexahedral batches come from hgks_batch_create).
+ * it holds tetrahedra (hgks_batch_create_empty_hex below: hexahedra).
  * Device memory: about 8 KB per cell and 1.3 KB per face (FP64, Krylov 10). */
 hgks_status hgks_batch_create_empty(int32_t device, int64_t cell_capacity, int64_t face_capacity,
                                     int32_t max_meshes, const hgks_params *shared, hgks_batch *out);
+/* The same arena for hexahedral meshes (add them with hgks_batch_add). */
+hgks_status hgks_batch_create_empty_hex(int32_t device, int64_t cell_capacity, int64_t face_capacity,
+                                        int32_t max_meshes, const hgks_params *shared, hgks_batch *out);
 /* Place a mesh (copied; the handle stays the caller's) in a free slot and in
  * free cell and face ranges (first fit); *k_out receives the slot, the index
  * every other hgks_batch_* call takes. HGKS_ERR_OOM if no slot or range is

@@ -105,6 +105,7 @@ def lib():
             "hgks_batch_create": [dp, P, i32, C.POINTER(vp)],
             "hgks_batch_destroy": [vp],
             "hgks_batch_create_empty": [i32, i64, i64, i32, P, C.POINTER(vp)],
+            "hgks_batch_create_empty_hex": [i32, i64, i64, i32, P, C.POINTER(vp)],
             "hgks_batch_add": [vp, vp, P, C.POINTER(C.c_int32)],
             "hgks_batch_remove": [vp, i32],
             "hgks_server_create": [i32, i64, i32, P, i32, C.POINTER(vp)],
@@ -339,9 +340,10 @@ def hgks_batch_create(meshes, params) -> hgks_batch:
     return hgks_batch(h.value, meshes, params)
 
 
-def hgks_batch_create_empty(cell_capacity, face_capacity, max_meshes, shared, device=0) -> hgks_batch:
+def hgks_batch_create_empty(cell_capacity, face_capacity, max_meshes, shared, device=0, hexahedra=False) -> hgks_batch:
     h = C.c_void_p()
-    _check(lib().hgks_batch_create_empty(device, cell_capacity, face_capacity, max_meshes, C.byref(shared), C.byref(h)))
+    fn = lib().hgks_batch_create_empty_hex if hexahedra else lib().hgks_batch_create_empty
+    _check(fn(device, cell_capacity, face_capacity, max_meshes, C.byref(shared), C.byref(h)))
     b = hgks_batch(h.value, [None] * max_meshes, [None] * max_meshes)
     return b
 

@@ -558,8 +558,11 @@ hgks_status hgks_batch_create(const hgks_mesh *meshes, const hgks_params *params
   return HGKS_OK;
 }
 
-hgks_status hgks_batch_create_empty(int32_t device, int64_t cell_capacity, int64_t face_capacity, int32_t max_meshes,
-                                    const hgks_params *shared, hgks_batch *out) {
+}  // extern "C"
+
+namespace {
+hgks_status create_empty(int32_t device, int64_t cell_capacity, int64_t face_capacity, int32_t max_meshes,
+                         const hgks_params *shared, bool hex, hgks_batch *out) {
   if (!out || !shared) return fail_msg(HGKS_ERR_ARG, "NULL argument");
   *out = nullptr;
   int ndev = 0;
@@ -567,13 +570,26 @@ hgks_status hgks_batch_create_empty(int32_t device, int64_t cell_capacity, int64
   HGKS_ON_DEVICE(device);
   Batch *B = nullptr;
   hgks_status st = batch_new(device, cell_capacity, face_capacity, max_meshes, *shared,
-                             shared->scheme == HGKS_WENO ? 1 : 2, &B);
+                             shared->scheme == HGKS_WENO ? 1 : 2, &B, hex);
   if (st) return st;
   hgks_batch_s *h = new (std::nothrow) hgks_batch_s;
   if (!h) { batch_delete(B); return fail_msg(HGKS_ERR_OOM, "host allocation"); }
   h->B = B;
   *out = h;
   return HGKS_OK;
+}
+}  // namespace
+
+extern "C" {
+
+hgks_status hgks_batch_create_empty(int32_t device, int64_t cell_capacity, int64_t face_capacity, int32_t max_meshes,
+                                    const hgks_params *shared, hgks_batch *out) {
+  return create_empty(device, cell_capacity, face_capacity, max_meshes, shared, false, out);
+}
+
+hgks_status hgks_batch_create_empty_hex(int32_t device, int64_t cell_capacity, int64_t face_capacity,
+                                        int32_t max_meshes, const hgks_params *shared, hgks_batch *out) {
+  return create_empty(device, cell_capacity, face_capacity, max_meshes, shared, true, out);
 }
 
 hgks_status hgks_batch_add(hgks_batch batch, hgks_mesh mesh, const hgks_params *p, int32_t *k_out) {

@@ -451,3 +451,37 @@ def test_hex_server_results_equal_alone(cuda):
     with pytest.raises(H.HGKSError) as e:
         tsrv.submit(m, p, Q0)
     assert e.value.status == 1
+
+
+def test_hex_empty_batch_add_step_equals_single(cuda):
+    """An empty hexahedral batch (hgks_batch_create_empty_hex) filled with
+    hgks_batch_add: one batched step equals each mesh's step alone (FP64, 1e-10);
+    a tetrahedral mesh is refused."""
+    import torch
+    kw = dict(scheme=0, krylov_dim=8, restarts=2)
+    shared = H.hgks_default_params(**kw)
+    b = H.hgks_batch_create_empty(20000, 80000, 4, shared, hexahedra=True)
+    singles = []
+    for k, (m, cond) in enumerate([(I.hex_cavity_mesh(4, seed=I.BASE_SEED + 350), I.cavity_conditions(0.2, 100.0)),
+                                   (I.hex_tilted_box_mesh(5), I.sphere_conditions(0.3))]):
+        hm = H.hgks_mesh_create(m, scheme_mask=1)
+        p = H.hgks_default_params(Pr=0.72 if cond["viscous"] else 1.0, **cond, **kw)
+        slot = H.hgks_batch_add(b, hm, p)
+        Q, _ = state(m, cond, seed=360 + k)
+        Qd = hm.to_internal(Q)
+        H.hgks_batch_set_state(b, slot, Qd)
+        singles.append((slot, hm, p, Qd))
+    infos = H.hgks_batch_gmres_step(b, use_graph=False)
+    for slot, hm, p, Qd in singles:
+        Q0 = Qd.clone()
+        si = H.hgks_gmres_step(hm, p, Qd, None)
+        Qb = torch.empty_like(Qd)
+        H.hgks_batch_get_state(b, slot, Q=Qb)
+        torch.cuda.synchronize()
+        assert abs(infos[slot].res_l1 - si.res_l1) <= 1e-13 * si.res_l1
+        rel = (torch.linalg.norm((Qb - Q0) - (Qd - Q0)) / torch.linalg.norm(Qd - Q0)).item()
+        assert rel <= 1e-10, rel
+    tet = H.hgks_mesh_create(I.cavity_mesh(3), scheme_mask=1)
+    with pytest.raises(H.HGKSError) as e:
+        H.hgks_batch_add(b, tet, H.hgks_default_params(**kw, **I.cavity_conditions()))
+    assert e.value.status == 1
