@@ -9,6 +9,10 @@ paper_2304_09485_gb300.inputs, which holds none of the method's arithmetic.
 The C sources (orc_*.c) restate the paper step by step; this file loads them
 through ctypes and converts between numpy arrays and C pointers. Arrays are in
 the caller's cell order: Q [n,5], G [n,15] (component-major: 3*c + d).
+
+Parity unpinned: the local time step beyond its scaling invariants (the paper
+gives no formula) and the boundary states beyond their involution, rest-state,
+wall-symmetry and mass properties; every other routine has pins in tests/.
 """
 from __future__ import annotations
 

@@ -1,5 +1,6 @@
 /*
- * ORACLE for the implicit high-order gas-kinetic scheme (HGKS) on tetrahedra.
+ * ORACLE for the implicit high-order gas-kinetic scheme (HGKS) on tetrahedra
+ * and hexahedra.
  *
  * TEST INFRASTRUCTURE ONLY. This is a plain, slow, FP64 CPU restatement of the
  * paper's method, written to check the CUDA library against. Only tests/,
@@ -16,6 +17,12 @@
  * Data layout is the natural one for a reader: cell arrays are [cell][5] in the
  * caller's cell order, gradients [cell][5][3] (component, then direction).
  * Cells are tetrahedra or hexahedra (Sec. 3.1: four or six faces).
+ *
+ * Parity unpinned: the local time step (orc_local_dt) beyond its scaling
+ * invariants, since the paper gives no formula for it, and the boundary states
+ * (orc_boundary_state) beyond their involution, rest-state, wall-symmetry and
+ * mass properties. Every other routine is pinned by the tests against closed
+ * forms, library routines, invariants or brute force.
  */
 #ifndef HGKS_ORACLE_H
 #define HGKS_ORACLE_H
