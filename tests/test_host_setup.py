@@ -442,3 +442,66 @@ def test_hex_fits_reproduce_quadratics_and_linear_fields(shim):
         d[1:4] = gl[:, None]
         d[4:7] = np.where(has[mm][None, :], gl[:, None], 0.0)
         np.testing.assert_allclose(np.einsum("jcn,cn->nj", Hm[mm], d), h[:, None] * gl[None, :], rtol=1e-10, atol=1e-12)
+
+
+def _build_raw(L, xyz, cells, bface, btag, pshift=None, mask=3):
+    """hs_build_cells on raw arrays: (status, message)."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    cells = np.ascontiguousarray(cells, dtype=np.int64)
+    bface = np.ascontiguousarray(bface, dtype=np.int64)
+    btag = np.ascontiguousarray(btag, dtype=np.int32)
+    psa = np.ascontiguousarray(pshift if pshift is not None else np.zeros((0, 3)), dtype=np.float64)
+    sizes = np.zeros(3, dtype=np.int64)
+    p = lambda a: a.ctypes.data_as(C.c_void_p)
+    rc = L.hs_build_cells(p(xyz), C.c_int64(len(xyz)), p(cells), C.c_int32(cells.shape[1]), C.c_int64(len(cells)),
+                          p(bface), p(btag), C.c_int64(len(btag)), p(psa), C.c_int32(len(psa)), C.c_int(mask), p(sizes))
+    return rc, L.hs_error().decode()
+
+
+def test_invalid_meshes_are_refused(shim):
+    """Meshes the scheme cannot run on are refused by the host set-up with
+    HGKS_ERR_MESH (2) or HGKS_ERR_ARG (1) and a message naming the fault: an
+    inverted or flat cell, a vertex index out of range, a face of three cells, a
+    face that is neither shared, tagged nor periodic, an unknown tag, and a
+    non-compact stencil with fewer than the 9 cells the quadratic fit needs."""
+    ERR_ARG, ERR_MESH = 1, 2
+    hexm = I.hex_cavity_mesh(3, jitter=0.1)
+    good = (hexm.xyz, hexm.hex8, hexm.bface4, hexm.btag)
+    assert _build_raw(shim, *good)[0] == 0
+    # top and bottom quadrilaterals swapped: the trilinear map has detJ < 0
+    inv = hexm.hex8.copy()
+    inv[5] = inv[5][[4, 5, 6, 7, 0, 1, 2, 3]]
+    rc, msg = _build_raw(shim, hexm.xyz, inv, hexm.bface4, hexm.btag)
+    assert rc == ERR_MESH and "hexahedron 5" in msg
+    # a vertex index past the vertex array
+    bad = hexm.hex8.copy()
+    bad[2, 3] = len(hexm.xyz)
+    rc, msg = _build_raw(shim, hexm.xyz, bad, hexm.bface4, hexm.btag)
+    assert rc == ERR_MESH and "out of range" in msg
+    # cells of a kind the library does not have
+    rc, msg = _build_raw(shim, hexm.xyz, hexm.hex8[:, :5], hexm.bface4, hexm.btag)
+    assert rc == ERR_ARG and "4 or 8" in msg
+    # one boundary quadrilateral dropped, no periodic shifts
+    rc, msg = _build_raw(shim, hexm.xyz, hexm.hex8, hexm.bface4[1:], hexm.btag[1:])
+    assert rc == ERR_MESH and msg.startswith("1 faces")
+    # a boundary tag outside 1..5
+    tag = hexm.btag.copy()
+    tag[0] = 9
+    rc, msg = _build_raw(shim, hexm.xyz, hexm.hex8, hexm.bface4, tag)
+    assert rc == ERR_ARG and "tag" in msg
+    # a cell listed twice: its interior faces belong to three cells
+    rc, msg = _build_raw(shim, hexm.xyz, np.concatenate([hexm.hex8, hexm.hex8[13:14]]), hexm.bface4, hexm.btag)
+    assert rc == ERR_MESH and "more than two" in msg
+
+    tetm = I.cavity_mesh(2)
+    flat_xyz = tetm.xyz.copy()
+    t = tetm.tet4[0]
+    flat_xyz[t[3]] = flat_xyz[t[0]] + 0.5 * (flat_xyz[t[1]] - flat_xyz[t[0]]) + 0.25 * (flat_xyz[t[2]] - flat_xyz[t[0]])
+    rc, msg = _build_raw(shim, flat_xyz, tetm.tet4, tetm.bface3, tetm.btag)
+    assert rc == ERR_MESH and "degenerate tetrahedron" in msg
+    # one tetrahedron, all four faces walls: no non-compact stencil
+    one = np.array([[0, 1, 2, 3]])
+    xyz = np.array([[0.0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]])
+    bf = np.array([[1, 2, 3], [0, 2, 3], [0, 1, 3], [0, 1, 2]])
+    rc, msg = _build_raw(shim, xyz, one, bf, np.full(4, I.BC_WALL_ISO), mask=1)
+    assert rc == ERR_MESH and "fewer than 9" in msg
