@@ -216,9 +216,9 @@ hgks_status hgks_local_dt(hgks_mesh mesh, const hgks_params *p, const double *Q,
 
 /* Assemble A of Eq. (A-system-2) with Eq. (deri-matrix) at state Q and
  * time step dt (device arrays), into the handle. If diag_out / off_out are not
- * NULL they receive the blocks (device, double[25][N] and double[4][25][N],
- * row-major 5x5, off block p multiplies the neighbour across local face p;
- * zero on boundary faces). */
+ * NULL they receive the blocks (device, double[25][N] and double[F][25][N] with
+ * F = faces_per_cell of hgks_mesh_info (4 or 6), row-major 5x5, off block p
+ * multiplies the neighbour across local face p; zero on boundary faces). */
 hgks_status hgks_assemble(hgks_mesh mesh, const hgks_params *p, const double *Q, const double *dt,
                           double *diag_out, double *off_out, void *cuda_stream);
 /* y = A x with the assembled A (device double[5][N]). */

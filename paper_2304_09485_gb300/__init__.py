@@ -18,6 +18,7 @@ import numpy as np
 from . import _native
 
 HGKS_OK = 0
+HGKS_ERR_ARG = 1
 HGKS_ERR_NONPHYSICAL = 5
 HGKS_ERR_NOT_CONVERGED = 7
 HGKS_ERR_CANCELLED = 9
@@ -157,6 +158,45 @@ def _ptr(t):
     return t.data_ptr()
 
 
+def _dev(t, rows, n, name):
+    """Data pointer of a device-array argument, or None for NULL. The C entry
+    points take raw double pointers and their kernels touch rows x n values, so
+    anything but a contiguous float64 CUDA tensor of at least that many values (a
+    host array, another dtype, a strided view, a short buffer) is refused here
+    with HGKS_ERR_ARG instead of being read or written out of bounds on the GPU."""
+    if t is None:
+        return None
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+            and t.numel() >= rows * n):
+        raise HGKSError(HGKS_ERR_ARG, f"{name}: expected a contiguous float64 CUDA tensor of at least "
+                                      f"{rows} x {n} values, got {_describe(t)}")
+    return t.data_ptr()
+
+
+def _host(a, rows, n, name):
+    """Data pointer of a host-array argument (a C-contiguous float64 numpy array
+    or CPU tensor of at least rows x n values), or None; otherwise HGKS_ERR_ARG."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype == np.float64 and a.flags.c_contiguous and a.size >= rows * n:
+            return a.ctypes.data
+    else:
+        import torch
+        if (isinstance(a, torch.Tensor) and not a.is_cuda and a.device.type == "cpu" and a.dtype == torch.float64
+                and a.is_contiguous() and a.numel() >= rows * n):
+            return a.data_ptr()
+    raise HGKSError(HGKS_ERR_ARG, f"{name}: expected a C-contiguous float64 host array of at least "
+                                  f"{rows} x {n} values, got {_describe(a)}")
+
+
+def _describe(t):
+    what = f"{type(t).__name__} {getattr(t, 'dtype', '')} {tuple(getattr(t, 'shape', ()))}"
+    dev = getattr(t, "device", None)
+    return what + (f" on {dev}" if dev is not None else "")
+
+
 def _stream(stream):
     if stream is None:
         import torch
@@ -178,8 +218,9 @@ def hgks_default_params(**overrides) -> hgks_params:
 class hgks_mesh:
     """A mesh handle; .perm[internal] = caller cell index."""
 
-    def __init__(self, handle, perm, n_cells):
+    def __init__(self, handle, perm, n_cells, faces_per_cell=4):
         self.handle = C.c_void_p(handle)
+        self.faces_per_cell = faces_per_cell
         self.perm = perm
         self.inv = np.empty_like(perm)
         self.inv[perm] = np.arange(len(perm))
@@ -221,7 +262,7 @@ def hgks_mesh_create(mesh, scheme_mask=3, device=0) -> hgks_mesh:
     _check(fn(_ptr(xyz), xyz.shape[0], _ptr(cells), cells.shape[0], _ptr(bf) if len(bf) else None,
               _ptr(bt) if len(bt) else None, bf.shape[0], _ptr(psa) if len(psa) else None,
               psa.shape[0], scheme_mask, device, C.byref(h), _ptr(perm)))
-    return hgks_mesh(h.value, perm[: cells.shape[0]], cells.shape[0])
+    return hgks_mesh(h.value, perm[: cells.shape[0]], cells.shape[0], 6 if hexa else 4)
 
 
 def hgks_mesh_info(mesh: hgks_mesh) -> hgks_mesh_info_t:
@@ -237,54 +278,70 @@ def hgks_mesh_volumes(mesh: hgks_mesh) -> np.ndarray:
 
 
 def hgks_residual(mesh, params, Q, G, R, G_new=None, stream=None):
-    _check(lib().hgks_residual(mesh.handle, C.byref(params), _ptr(Q), _ptr(G), _ptr(R), _ptr(G_new), _stream(stream)))
+    n = mesh.n_cells
+    _check(lib().hgks_residual(mesh.handle, C.byref(params), _dev(Q, 5, n, "Q"), _dev(G, 15, n, "G"),
+                               _dev(R, 5, n, "R"), _dev(G_new, 15, n, "G_new"), _stream(stream)))
 
 
 def hgks_residual_noalloc(mesh, params, Q, G, R, G_new=None, stream=None):
     """hgks_residual with its scratch in the library's fixed static array (no allocation)."""
-    _check(lib().hgks_residual_noalloc(mesh.handle, C.byref(params), _ptr(Q), _ptr(G), _ptr(R), _ptr(G_new),
-                                       _stream(stream)))
+    n = mesh.n_cells
+    _check(lib().hgks_residual_noalloc(mesh.handle, C.byref(params), _dev(Q, 5, n, "Q"), _dev(G, 15, n, "G"),
+                                       _dev(R, 5, n, "R"), _dev(G_new, 15, n, "G_new"), _stream(stream)))
 
 
 def hgks_local_dt(mesh, params, Q, dt, stream=None):
-    _check(lib().hgks_local_dt(mesh.handle, C.byref(params), _ptr(Q), _ptr(dt), _stream(stream)))
-
-
-def hgks_assemble(mesh, params, Q, dt, diag_out=None, off_out=None, stream=None):
-    _check(lib().hgks_assemble(mesh.handle, C.byref(params), _ptr(Q), _ptr(dt), _ptr(diag_out), _ptr(off_out),
+    n = mesh.n_cells
+    _check(lib().hgks_local_dt(mesh.handle, C.byref(params), _dev(Q, 5, n, "Q"), _dev(dt, 1, n, "dt"),
                                _stream(stream)))
 
 
+def hgks_assemble(mesh, params, Q, dt, diag_out=None, off_out=None, stream=None):
+    n = mesh.n_cells
+    _check(lib().hgks_assemble(mesh.handle, C.byref(params), _dev(Q, 5, n, "Q"), _dev(dt, 1, n, "dt"),
+                               _dev(diag_out, 25, n, "diag_out"),
+                               _dev(off_out, 25 * mesh.faces_per_cell, n, "off_out"), _stream(stream)))
+
+
 def hgks_apply_jacobian(mesh, x, y, stream=None):
-    _check(lib().hgks_apply_jacobian(mesh.handle, _ptr(x), _ptr(y), _stream(stream)))
+    n = mesh.n_cells
+    _check(lib().hgks_apply_jacobian(mesh.handle, _dev(x, 5, n, "x"), _dev(y, 5, n, "y"), _stream(stream)))
 
 
 def hgks_apply_jacobian_fd(mesh, params, Q, G, dt, x, y, stream=None):
-    _check(lib().hgks_apply_jacobian_fd(mesh.handle, C.byref(params), _ptr(Q), _ptr(G), _ptr(dt), _ptr(x), _ptr(y),
+    n = mesh.n_cells
+    _check(lib().hgks_apply_jacobian_fd(mesh.handle, C.byref(params), _dev(Q, 5, n, "Q"), _dev(G, 15, n, "G"),
+                                        _dev(dt, 1, n, "dt"), _dev(x, 5, n, "x"), _dev(y, 5, n, "y"),
                                         _stream(stream)))
 
 
 def hgks_wall_force(mesh, params, Q, G, tag, stream=None) -> np.ndarray:
     f = np.zeros(3)
-    _check(lib().hgks_wall_force(mesh.handle, C.byref(params), _ptr(Q), _ptr(G), tag, _ptr(f), _stream(stream)))
+    n = mesh.n_cells
+    _check(lib().hgks_wall_force(mesh.handle, C.byref(params), _dev(Q, 5, n, "Q"), _dev(G, 15, n, "G"), tag,
+                                 _ptr(f), _stream(stream)))
     return f
 
 
 def hgks_precondition(mesh, sweeps, b, x, stream=None):
-    _check(lib().hgks_precondition(mesh.handle, sweeps, _ptr(b), _ptr(x), _stream(stream)))
+    n = mesh.n_cells
+    _check(lib().hgks_precondition(mesh.handle, sweeps, _dev(b, 5, n, "b"), _dev(x, 5, n, "x"), _stream(stream)))
 
 
 def hgks_gmres_step(mesh, params, Q, G=None, dQ_out=None, stream=None) -> hgks_step_info:
     info = hgks_step_info()
-    _check(lib().hgks_gmres_step(mesh.handle, C.byref(params), _ptr(Q), _ptr(G), _ptr(dQ_out), C.byref(info),
-                                 _stream(stream)))
+    n = mesh.n_cells
+    _check(lib().hgks_gmres_step(mesh.handle, C.byref(params), _dev(Q, 5, n, "Q"), _dev(G, 15, n, "G"),
+                                 _dev(dQ_out, 5, n, "dQ_out"), C.byref(info), _stream(stream)))
     return info
 
 
 def hgks_solve_steady(mesh, params, Q, G=None, drop_tol=1e-8, max_steps=1000, stream=None):
     hist = np.zeros(max_steps + 1)
     info = hgks_solve_info()
-    st = _check(lib().hgks_solve_steady(mesh.handle, C.byref(params), _ptr(Q), _ptr(G), drop_tol, max_steps,
+    n = mesh.n_cells
+    st = _check(lib().hgks_solve_steady(mesh.handle, C.byref(params), _dev(Q, 5, n, "Q"), _dev(G, 15, n, "G"),
+                                        drop_tol, max_steps,
                                         _ptr(hist), C.byref(info), _stream(stream)), allow=(HGKS_ERR_NOT_CONVERGED,))
     return info, hist[: info.steps + 1], st == HGKS_OK
 
@@ -293,21 +350,26 @@ def hgks_solve_resume(mesh, params, Q, G, frm, drop_tol=1e-8, max_steps=1000, st
     """Continue a solve from its state and hgks_solve_info: (info, hist [absolute steps], converged)."""
     hist = np.zeros(max_steps + 1)
     info = hgks_solve_info()
-    st = _check(lib().hgks_solve_resume(mesh.handle, C.byref(params), _ptr(Q), _ptr(G), drop_tol, max_steps,
+    n = mesh.n_cells
+    st = _check(lib().hgks_solve_resume(mesh.handle, C.byref(params), _dev(Q, 5, n, "Q"), _dev(G, 15, n, "G"),
+                                        drop_tol, max_steps,
                                         C.byref(frm), _ptr(hist), C.byref(info), _stream(stream)),
                 allow=(HGKS_ERR_NOT_CONVERGED,))
     return info, hist[: info.steps + 1], st == HGKS_OK
 
 
 def hgks_residual_host(mesh, params, Q_host, G_host, R_host, G_new_host, stream=None):
-    _check(lib().hgks_residual_host(mesh.handle, C.byref(params), _ptr(Q_host), _ptr(G_host), _ptr(R_host),
-                                    _ptr(G_new_host), _stream(stream)))
+    n = mesh.n_cells
+    _check(lib().hgks_residual_host(mesh.handle, C.byref(params), _host(Q_host, 5, n, "Q_host"),
+                                    _host(G_host, 15, n, "G_host"), _host(R_host, 5, n, "R_host"),
+                                    _host(G_new_host, 15, n, "G_new_host"), _stream(stream)))
 
 
 def hgks_gmres_step_host(mesh, params, Q_host, G_host=None, stream=None) -> hgks_step_info:
     info = hgks_step_info()
-    _check(lib().hgks_gmres_step_host(mesh.handle, C.byref(params), _ptr(Q_host), _ptr(G_host), C.byref(info),
-                                      _stream(stream)))
+    n = mesh.n_cells
+    _check(lib().hgks_gmres_step_host(mesh.handle, C.byref(params), _host(Q_host, 5, n, "Q_host"),
+                                      _host(G_host, 15, n, "G_host"), C.byref(info), _stream(stream)))
     return info
 
 
@@ -368,12 +430,22 @@ def hgks_batch_info(batch) -> hgks_batch_info_t:
     return info
 
 
+def _slot_cells(batch, k):
+    """Cells of the mesh in slot k (HGKS_ERR_ARG for a slot out of range or empty)."""
+    if not (0 <= k < len(batch.meshes)) or batch.meshes[k] is None:
+        raise HGKSError(HGKS_ERR_ARG, f"batch slot {k} holds no mesh")
+    return batch.meshes[k].n_cells
+
+
 def hgks_batch_set_state(batch, k, Q, G=None, stream=None):
-    _check(lib().hgks_batch_set_state(batch.handle, k, _ptr(Q), _ptr(G), _stream(stream)))
+    n = _slot_cells(batch, k)
+    _check(lib().hgks_batch_set_state(batch.handle, k, _dev(Q, 5, n, "Q"), _dev(G, 15, n, "G"), _stream(stream)))
 
 
 def hgks_batch_get_state(batch, k, Q=None, G=None, R=None, G_new=None, stream=None):
-    _check(lib().hgks_batch_get_state(batch.handle, k, _ptr(Q), _ptr(G), _ptr(R), _ptr(G_new), _stream(stream)))
+    n = _slot_cells(batch, k)
+    _check(lib().hgks_batch_get_state(batch.handle, k, _dev(Q, 5, n, "Q"), _dev(G, 15, n, "G"), _dev(R, 5, n, "R"),
+                                      _dev(G_new, 15, n, "G_new"), _stream(stream)))
 
 
 def hgks_batch_residual(batch, stream=None):
@@ -436,6 +508,10 @@ class hgks_server:
         psa = np.ascontiguousarray(ps if ps is not None else np.zeros((0, 3)), dtype=np.float64)
         q = np.ascontiguousarray(Q0, dtype=np.float64)
         g = None if G0 is None else np.ascontiguousarray(G0, dtype=np.float64)
+        n = tet.shape[0]
+        if q.size < 5 * n or (g is not None and g.size < 15 * n):
+            raise HGKSError(HGKS_ERR_ARG, f"Q0 / G0 hold {q.size} / {0 if g is None else g.size} values, "
+                                          f"the mesh's {n} cells need {5 * n} / {15 * n}")
         rid = C.c_int64(0)
         fn = lib().hgks_server_submit_hex if hexa else lib().hgks_server_submit
         _check(fn(self.handle, _ptr(xyz), xyz.shape[0], _ptr(tet), tet.shape[0],
