@@ -45,9 +45,9 @@ def gauss_hermite_moment(U, lam, k):
 def half_moment(U, lam, k, sign):
     f = lambda u: u ** k * math.sqrt(lam / math.pi) * math.exp(-lam * (u - U) ** 2)
     if sign > 0:
-        v, _ = integrate.quad(f, 0, np.inf, epsabs=1e-15, epsrel=1e-14, limit=200)
+        v, _ = integrate.quad(f, 0, np.inf, epsabs=1e-14, epsrel=1e-12, limit=200)
     else:
-        v, _ = integrate.quad(f, -np.inf, 0, epsabs=1e-15, epsrel=1e-14, limit=200)
+        v, _ = integrate.quad(f, -np.inf, 0, epsabs=1e-14, epsrel=1e-12, limit=200)
     return v
 
 
