@@ -461,9 +461,10 @@ def _build_raw(L, xyz, cells, bface, btag, pshift=None, mask=3):
 def test_invalid_meshes_are_refused(shim):
     """Meshes the scheme cannot run on are refused by the host set-up with
     HGKS_ERR_MESH (2) or HGKS_ERR_ARG (1) and a message naming the fault: an
-    inverted or flat cell, a vertex index out of range, a face of three cells, a
-    face that is neither shared, tagged nor periodic, an unknown tag, and a
-    non-compact stencil with fewer than the 9 cells the quadratic fit needs."""
+    empty mesh, an inverted or flat cell, a vertex index out of range, a face
+    of three cells, a face that is neither shared, tagged nor periodic, an
+    unknown tag, and a non-compact stencil with fewer than the 9 cells the
+    quadratic fit needs."""
     ERR_ARG, ERR_MESH = 1, 2
     hexm = I.hex_cavity_mesh(3, jitter=0.1)
     good = (hexm.xyz, hexm.hex8, hexm.bface4, hexm.btag)
@@ -499,6 +500,9 @@ def test_invalid_meshes_are_refused(shim):
     flat_xyz[t[3]] = flat_xyz[t[0]] + 0.5 * (flat_xyz[t[1]] - flat_xyz[t[0]]) + 0.25 * (flat_xyz[t[2]] - flat_xyz[t[0]])
     rc, msg = _build_raw(shim, flat_xyz, tetm.tet4, tetm.bface3, tetm.btag)
     assert rc == ERR_MESH and "degenerate tetrahedron" in msg
+    # no cells at all
+    rc, msg = _build_raw(shim, tetm.xyz, np.zeros((0, 4), dtype=np.int64), np.zeros((0, 3)), np.zeros(0))
+    assert rc == ERR_ARG and "empty" in msg
     # one tetrahedron, all four faces walls: no non-compact stencil
     one = np.array([[0, 1, 2, 3]])
     xyz = np.array([[0.0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]])
