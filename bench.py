@@ -166,7 +166,7 @@ def cpu_baseline(steps=1, max_seconds=30.0):
     t1 = time.perf_counter()
     om.residual(p, Q)                  # the residual alone (fits already built)
     res_s = time.perf_counter() - t1
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = O.set_threads(0)           # the OpenMP threads the timed steps ran on (0: query only)
     # the residual of the compact cavity (3,072 tets, HWENO, viscous) on one core and on all
     mc = I.cavity_mesh(8)
     cc = I.cavity_conditions(0.15, 100.0)
@@ -218,7 +218,7 @@ def run_reference(args, rank, world):
     t_all = time.perf_counter() - t0
     value = m.n_tet * args.steps / t_all / 1e6 if args.steps else 0.0
     _, _, _, name = workload(small=True)
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = O.set_threads(0)           # the OpenMP threads the timed steps ran on (0: query only)
     cb = {"value": value, "unit": "Mcells/s", "cores": cores, "kind": "oracle",
           "sample": f"{args.steps} implicit step(s) on {m.n_tet} tets (6x12x12x24 sphere, same scheme and "
                     f"parameters) after {max(1, args.warmup)} untimed"}

@@ -400,5 +400,5 @@ def primitive(Q, gamma=1.4):
 
 
 def set_threads(n: int) -> int:
-    """OpenMP threads of the oracle's loops (n > 0); returns the previous maximum."""
+    """OpenMP threads of the oracle's loops (n > 0; n = 0 leaves them); returns the previous maximum."""
     return int(lib().orc_set_threads(int(n)))
