@@ -47,6 +47,10 @@ FP64_NOMINAL_GFLOPS = 1258.6
 # count. DRAM bytes per unit of work from the same ncu captures
 # (dram__bytes_read.sum + dram__bytes_write.sum divided by the units of the
 # 124,416-tet launch); the traffic of a full launch is this times its units.
+# Since those captures the kernels were templated on the cell shape; their
+# tetrahedral instances are the same loops with the face count as a template
+# argument, compile to the same registers, stack frame and spills (-Xptxas -v)
+# and take the same time per launch, so the counters still describe them.
 KERNEL_TRAFFIC = {"flux": 395.6, "recon": 957.6, "jacobi": 858.0, "spmv": 935.0}
 KERNEL_FLOPS = {
     "flux": (2242.5, lambda N, F: 3 * F),        # per face Gauss point
