@@ -17,11 +17,7 @@
 
 namespace hgks {
 
-constexpr int kBig = 16;        // non-compact big stencil size (excluding the target)
-constexpr int kSubK = 6;        // cells of a non-compact sub-stencil (three face neighbours + three)
-constexpr int kSub = 4;         // sub-stencils per tetrahedron
-constexpr int kCoefA = 45;      // quadratic coefficients: 9 x 5
-constexpr int kCoef = 105;      // + 4 linear sub-polynomials: 4 x 3 x 5
+constexpr int kCoefA = 45;      // quadratic coefficients: 9 x 5 (then 15 per sub-polynomial, ShapeOf::COEF)
 constexpr int kFaceState = 20;  // W[5] + dW[3][5] at one Gauss point, face frame
 
 // Compile-time shape of a cell kind (Sec. 3.1). Tetrahedra: 4 triangular faces
