@@ -432,7 +432,6 @@ hgks_status hgks_apply_jacobian(hgks_mesh mesh, const double *x, double *y, void
   if (!mesh || !x || !y) return fail(HGKS_ERR_ARG, "NULL argument");
   Mesh &m = mesh->m;
   if (!m.s.off) return fail(HGKS_ERR_ARG, "hgks_assemble has not been called");
-  hgks_status st;
   HGKS_ON_DEVICE(m.device);
   launch_apply_A(m.d, m.s, x, y, (cudaStream_t)cuda_stream);
   return last_launch();
@@ -483,7 +482,6 @@ hgks_status hgks_precondition(hgks_mesh mesh, int32_t sweeps, const double *b, d
   if (sweeps < 0) return fail(HGKS_ERR_ARG, "negative sweeps");
   Mesh &m = mesh->m;
   if (!m.s.off) return fail(HGKS_ERR_ARG, "hgks_assemble has not been called");
-  hgks_status st;
   HGKS_ON_DEVICE(m.device);
   launch_precondition(m.d, m.s, sweeps, b, x, (cudaStream_t)cuda_stream);
   return last_launch();
