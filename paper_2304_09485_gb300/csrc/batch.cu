@@ -127,7 +127,8 @@ void bapply(unsigned g, cudaStream_t st, const DevMesh &m, const BatchDev &bd, c
                                                                       dot_out, stride);
 }
 
-// w -= h(mesh) v (if v); out(mesh) = (w, x) or ||w|| (self)
+// w -= h(mesh) v (if v); out(mesh) = (w, x) or ||w|| (self; x is not read then,
+// so callers may pass w for it)
 template <typename T>
 __global__ void __launch_bounds__(kB) k_baxpy_dot(int N, BatchDev bd, T *__restrict__ w, const T *__restrict__ v,
                                                   const double *__restrict__ h, int hstride, const T *__restrict__ x,

@@ -278,6 +278,8 @@ template <> struct Vec16<double> { typedef double2 type; static constexpr int n 
 template <> struct Vec16<float> { typedef float4 type; static constexpr int n = 4; };
 
 // w -= h v (if v != nullptr); *out = (w, x) (mode 0) or ||w|| (x == w, mode 1).
+// In mode 1 nothing is read through x, so callers may pass w itself for it
+// without breaking the restrict qualifiers.
 // 16 bytes per vector per thread and step, four steps in flight; n need not be
 // a multiple of the vector width.
 template <typename T>
