@@ -462,14 +462,27 @@ int orc_fit_cell(orc_mesh *m, int64_t i, int scheme) {
         for (int q = 0; q < nfc && F->n_big < 12; q++) { double s[3]; int64_t k = nb_of(m, F->big + a, q, s); add_ref(F->big, &F->n_big, 12, i, k, s); }
       fs = ns; fe = F->n_big;
     }
-    if (F->n_big < 9) return -1;
-    double A[ORC_MAXSTEN * 9], av[9];
-    for (int r = 0; r < F->n_big; r++) {
-      avg_monomials(m, i, F->big[r].cell, F->big[r].shift, av);
-      for (int d = 0; d < 9; d++) A[r * 9 + d] = av[d] - avg_i[d];
+    /* the quadratic fit needs cells that determine it: while it is singular
+     * over the cells found (on a regular grid the 12 cells of a boundary cell
+     * are), add the neighbours of every stencil cell, in stencil and local-face
+     * order, up to 16 cells around a tetrahedron or 24 around a hexahedron */
+    const int cap = hex ? 24 : 16;
+    double A[ORC_MAXSTEN * 9], av[9], X[9 * ORC_MAXSTEN];
+    for (;;) {
+      int ok = 0;
+      if (F->n_big >= 9) {
+        for (int r = 0; r < F->n_big; r++) {
+          avg_monomials(m, i, F->big[r].cell, F->big[r].shift, av);
+          for (int d = 0; d < 9; d++) A[r * 9 + d] = av[d] - avg_i[d];
+        }
+        ok = orc_lsq_pinv(F->n_big, 9, A, X) == 0;
+      }
+      if (ok) break;
+      const int before = F->n_big;
+      for (int a = 0; a < before && F->n_big < cap; a++)
+        for (int q = 0; q < nfc && F->n_big < cap; q++) { double s[3]; int64_t k = nb_of(m, F->big + a, q, s); add_ref(F->big, &F->n_big, cap, i, k, s); }
+      if (F->n_big == before) return before < 9 ? -1 : -2;
     }
-    double X[9 * ORC_MAXSTEN];
-    if (orc_lsq_pinv(F->n_big, 9, A, X)) return -2;
     memset(F->X0, 0, sizeof(F->X0));
     for (int d = 0; d < 9; d++) for (int r = 0; r < F->n_big; r++) F->X0[d][r] = X[d * F->n_big + r];
     /* sub-stencils: tetrahedron, three face neighbours plus the neighbours of

@@ -517,16 +517,33 @@ hgks_status build_host_mesh(const double *xyz, int64_t nv, const int64_t *cells,
               for (int q = 0; q < NF && big.size() < 12; q++) { Ref r; if (nb_of(big[a], q, r)) add(big, r, 12); }
             fs = ns; fe = big.size();
           }
-          int K = (int)big.size();
-          if (K < 9) { fail = 1; return; }
-          A.assign(K * 9, 0.0); X.assign(9 * K, 0.0);
+          // the quadratic fit needs cells that determine it: while it is singular
+          // over the cells found (on a regular grid the 12 cells of a boundary
+          // cell are), add the neighbours of every stencil cell, in stencil and
+          // local-face order, up to BIG cells
+          int K = 0;
           double av[9];
-          for (int k = 0; k < K; k++) {
-            g.avg_mono(i, big[k].cell, big[k].shift, av);
-            for (int d = 0; d < 9; d++) A[k * 9 + d] = av[d] - own[d];
-            hm.sten[(size_t)k * N + i] = big[k].cell;
+          for (;;) {
+            K = (int)big.size();
+            bool ok = false;
+            if (K >= 9) {
+              A.assign(K * 9, 0.0); X.assign(9 * K, 0.0);
+              for (int k = 0; k < K; k++) {
+                g.avg_mono(i, big[k].cell, big[k].shift, av);
+                for (int d = 0; d < 9; d++) A[k * 9 + d] = av[d] - own[d];
+              }
+              ok = lsq_map(K, 9, A.data(), X.data());
+            }
+            if (ok) break;
+            const size_t before = big.size();
+            for (size_t a = 0; a < before && big.size() < (size_t)BIG; a++)
+              for (int q = 0; q < NF && big.size() < (size_t)BIG; q++) {
+                Ref r;
+                if (nb_of(big[a], q, r)) add(big, r, BIG);
+              }
+            if (big.size() == before) { fail = K < 9 ? 1 : 2; return; }
           }
-          if (!lsq_map(K, 9, A.data(), X.data())) { fail = 2; return; }
+          for (int k = 0; k < K; k++) hm.sten[(size_t)k * N + i] = big[k].cell;
           for (int d = 0; d < 9; d++)
             for (int k = 0; k < K; k++) hm.X0[(size_t)(d * BIG + k) * N + i] = X[d * K + k];
           unsigned char valid = 0;

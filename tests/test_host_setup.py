@@ -128,10 +128,13 @@ def _scaled_coefficients(grad_c, Hq, h):
     return a
 
 
-def test_non_compact_fits_reproduce_quadratics_and_linear_fields(shim):
+@pytest.mark.parametrize("jitter", [0.1, 0.0])
+def test_non_compact_fits_reproduce_quadratics_and_linear_fields(shim, jitter):
     """Eq. (polys): the big-stencil least squares returns a quadratic's coefficients
-    exactly; every sub-stencil fit in use returns a linear field's gradient."""
-    m = I.cavity_mesh(4)
+    exactly; every sub-stencil fit in use returns a linear field's gradient. Also on
+    the regular grid (no jitter), whose boundary cells need more than two rings
+    for a determined quadratic fit."""
+    m = I.cavity_mesh(4, jitter=jitter)
     b = Built(shim, m, mask=1)
     N = b.N
     perm = b.get("perm", np.int64)

@@ -448,6 +448,40 @@ def test_quadratic_fields_reproduced_linear_weights(scheme):
             np.testing.assert_allclose(gg, grad, rtol=1e-9, atol=1e-10)
 
 
+def test_regular_grid_stencils_grow_until_the_fit_is_determined():
+    """On a regular grid (cubes split into six tetrahedra, no jitter) the 12 cells
+    of a boundary cell's first rings leave the quadratic fit of Eq. (polys)
+    singular; the stencil grows by the neighbours of its cells until the fit is
+    determined, and P0 (linear weights) then reproduces any quadratic exactly."""
+    m = I.cavity_mesh(4, jitter=0.0)
+    om = O.OracleMesh(m)
+    rng = np.random.default_rng(31)
+    Hq = rng.normal(size=(5, 3, 3)) * 0.2
+    Hq = Hq + Hq.transpose(0, 2, 1)
+    A = rng.normal(size=(5, 3)) * 0.3
+    b = np.array([1.0, 0.2, -0.1, 0.05, 2.5])
+
+    def f(X):
+        return X @ A.T + 0.5 * np.einsum("...i,cij,...j->...c", X, Hq, X) + b
+    Q = tet_average_quadratic(m.xyz, m.tet4, f)
+    p = O.make_params(scheme=0, weights=1)
+    om.residual(p, Q)
+    sizes = np.array([len(om.stencil(c)[0]) for c in range(m.n_tet)])
+    # the jittered grid has the same cells and neighbours, and no singular fit
+    mj = I.cavity_mesh(4)
+    assert np.array_equal(mj.tet4, m.tet4)
+    oj = O.OracleMesh(mj)
+    oj.residual(p, tet_average_quadratic(mj.xyz, mj.tet4, f))
+    sizes_j = np.array([len(oj.stencil(c)[0]) for c in range(mj.n_tet)])
+    grown = np.where(sizes > sizes_j)[0]
+    assert len(grown) > 0 and np.all(sizes_j[grown] == 12) and np.all(sizes[grown] <= 16)
+    assert np.array_equal(sizes[sizes == sizes_j], sizes_j[sizes == sizes_j])
+    for cell in grown[:12]:
+        for slot in range(4):
+            _, _, Wg, _ = om.recon_side(p, Q, None, int(cell), slot)
+            np.testing.assert_allclose(Wg, f(om.face_gauss_points(int(cell), slot)), rtol=1e-10, atol=1e-11)
+
+
 def test_gauss_points_on_faces():
     m = I.cavity_mesh(3)
     om = O.OracleMesh(m)

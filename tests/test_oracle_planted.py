@@ -95,6 +95,8 @@ PLANTED = [
      "for (int j = 0; j < 3; j++) data[nfc + 3 * k + j] = G[15 * i + 3 * c + j];"),
     ("HWENO sub-stencil: the neighbour's gradient dropped", "orc_recon.c",
      "if (jm >= 0) for (int j = 0; j < 3; j++) dm[4 + j] = G[15 * jm + 3 * c + j];", ""),
+    ("singular quadratic fits: the stencil stops growing at 12 cells", "orc_mesh.c",
+     "const int cap = hex ? 24 : 16;", "const int cap = 12;"),
     ("HWENO fit: equality rows without the target's own average", "orc_mesh.c",
      "for (int d = 0; d < 9; d++) C[r][d] = av[d] - avg_i[d];", "for (int d = 0; d < 9; d++) C[r][d] = av[d];"),
     ("HWENO fit: gradient data not scaled by h", "orc_mesh.c",
