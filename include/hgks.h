@@ -165,8 +165,14 @@ hgks_status hgks_default_params(hgks_params *p);
  *                      (NULL / 0 if none)
  *  scheme_mask         bit 0: build WENO data, bit 1: build HWENO data
  *  perm_out[n_tet]     (host, may be NULL) internal index -> caller index
+ * The non-compact big stencil is the face neighbours and their neighbours,
+ * widened ring by ring to 12 cells near boundaries and then, while its
+ * quadratic fit is singular (a regular grid's wall cells), by the neighbours
+ * of its cells up to 16 (24 around a hexahedron).
  * Errors: HGKS_ERR_ARG (n_tet <= 0, NULL arrays), HGKS_ERR_MESH (degenerate or
- * non-conforming mesh, singular stencil), HGKS_ERR_CUDA/OOM. */
+ * non-conforming mesh, a stencil whose fit stays singular, or fewer than 9
+ * other cells reachable for the non-compact fit, e.g. a mesh of under 10
+ * cells), HGKS_ERR_CUDA/OOM. */
 hgks_status hgks_mesh_create(const double *xyz, int64_t n_vert, const int64_t *tet4, int64_t n_tet,
                              const int64_t *bface3, const int32_t *btag, int64_t n_bface,
                              const double *periodic_shift, int32_t n_periodic, int32_t scheme_mask,
