@@ -55,6 +55,9 @@ PLANTED = [
     ("point value: t* term of the left side dropped", "orc_gks.c",
      "+ es * (ml[a] - (tau + ts) * mal[a] - tau * mAl[a])", "+ es * (ml[a] - tau * mal[a] - tau * mAl[a])"),
     # boundary images (Sec. 5.1, 5.2)
+    ("far field: free stream rotated by the transposed face frame", "orc_gks.c",
+     "u[i] = T3[3 * i] * p->u_inf[0] + T3[3 * i + 1] * p->u_inf[1] + T3[3 * i + 2] * p->u_inf[2];",
+     "u[i] = T3[i] * p->u_inf[0] + T3[i + 3] * p->u_inf[1] + T3[i + 6] * p->u_inf[2];"),
     ("slip wall reflects a tangential velocity", "orc_gks.c",
      "if (tag == 3) { vel_odd[0] = 1; vel_odd[1] = 0; vel_odd[2] = 0; }",
      "if (tag == 3) { vel_odd[0] = 1; vel_odd[1] = 1; vel_odd[2] = 0; }"),
