@@ -532,6 +532,28 @@ def test_free_stream_through_far_field_boundaries(scheme):
         assert np.abs(out[1]).max() <= 1e-12
 
 
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_flow_along_slip_walls_is_steady(scheme):
+    """Uniform flow along the walls y = 0, 1 (slip) of a box whose other faces
+    are far-field boundaries is an exact steady solution: R = 0. The flow has
+    components along both tangents of the walls; a slip image that reflected
+    either of them, or dropped the pressure, would not leave this state at rest."""
+    m = I.cavity_mesh(4, wall_tag=I.BC_SLIP, lid_tag=I.BC_SLIP)
+    cy = m.xyz[m.bface3][:, :, 1].mean(1)
+    m.btag = np.where(np.isclose(cy, 0.0) | np.isclose(cy, 1.0), I.BC_SLIP, I.BC_FARFIELD).astype(m.btag.dtype)
+    assert (m.btag == I.BC_SLIP).sum() == 2 * 2 * 16 and (m.btag == I.BC_FARFIELD).sum() == 4 * 2 * 16
+    om = O.OracleMesh(m)
+    u = (0.35, 0.0, -0.25)
+    Q = I.uniform_state(m.n_tet, rho=1.2, u=u[0], v=u[1], w=u[2], p=0.85)
+    G = np.zeros((m.n_tet, 15))
+    p = O.make_params(scheme=scheme, rho_inf=1.2, u_inf=u, p_inf=0.85)
+    out = om.residual(p, Q, G)
+    R = out[0] if scheme == 1 else out
+    assert np.abs(R).max() <= 1e-13
+    if scheme == 1:
+        assert np.abs(out[1]).max() <= 1e-12
+
+
 def test_rest_state_in_closed_cavity():
     """Fluid at rest at the wall temperature inside isothermal walls at rest: R = 0."""
     m = I.cavity_mesh(4, lid_tag=I.BC_WALL_ISO)
