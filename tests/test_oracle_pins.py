@@ -554,6 +554,28 @@ def test_flow_along_slip_walls_is_steady(scheme):
         assert np.abs(out[1]).max() <= 1e-12
 
 
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_flow_moving_with_isothermal_lids_is_steady(scheme):
+    """Viscous flow moving with two lids (y = 0, 1, isothermal walls sliding
+    along x) at the wall temperature, between far-field faces, is an exact steady
+    solution: R = 0. This pins the moving wall's image velocity (2 u_w - u): an
+    image that did not double the wall's velocity would stop the flow."""
+    U, Tw, rho = 0.4, 0.75, 1.3
+    m = I.cavity_mesh(4, wall_tag=I.BC_WALL_LID, lid_tag=I.BC_WALL_LID)
+    cy = m.xyz[m.bface3][:, :, 1].mean(1)
+    m.btag = np.where(np.isclose(cy, 0.0) | np.isclose(cy, 1.0), I.BC_WALL_LID, I.BC_FARFIELD).astype(m.btag.dtype)
+    om = O.OracleMesh(m)
+    Q = I.uniform_state(m.n_tet, rho=rho, u=U, v=0.0, w=0.0, p=rho * Tw)
+    G = np.zeros((m.n_tet, 15))
+    p = O.make_params(scheme=scheme, viscous=1, mu=2e-3, Pr=0.72, lid_speed=U, wall_T=Tw,
+                      rho_inf=rho, u_inf=(U, 0.0, 0.0), p_inf=rho * Tw)
+    out = om.residual(p, Q, G)
+    R = out[0] if scheme == 1 else out
+    assert np.abs(R).max() <= 1e-13
+    if scheme == 1:
+        assert np.abs(out[1]).max() <= 1e-12
+
+
 def test_rest_state_in_closed_cavity():
     """Fluid at rest at the wall temperature inside isothermal walls at rest: R = 0."""
     m = I.cavity_mesh(4, lid_tag=I.BC_WALL_ISO)

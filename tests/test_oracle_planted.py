@@ -58,6 +58,8 @@ PLANTED = [
     ("far field: free stream rotated by the transposed face frame", "orc_gks.c",
      "u[i] = T3[3 * i] * p->u_inf[0] + T3[3 * i + 1] * p->u_inf[1] + T3[3 * i + 2] * p->u_inf[2];",
      "u[i] = T3[i] * p->u_inf[0] + T3[i + 3] * p->u_inf[1] + T3[i + 6] * p->u_inf[2];"),
+    ("moving wall: image velocity u_w - u instead of 2 u_w - u", "orc_gks.c",
+     "ug[i] = vel_odd[i] ? 2.0 * uw[i] - u[i] : u[i];", "ug[i] = vel_odd[i] ? uw[i] - u[i] : u[i];"),
     ("slip wall reflects a tangential velocity", "orc_gks.c",
      "if (tag == 3) { vel_odd[0] = 1; vel_odd[1] = 0; vel_odd[2] = 0; }",
      "if (tag == 3) { vel_odd[0] = 1; vel_odd[1] = 1; vel_odd[2] = 0; }"),
