@@ -12,7 +12,8 @@ the caller's cell order: Q [n,5], G [n,15] (component-major: 3*c + d).
 
 Parity unpinned: the local time step beyond its scaling invariants (the paper
 gives no formula) and the boundary states beyond their involution, rest-state,
-wall-symmetry and mass properties; every other routine has pins in tests/.
+wall-symmetry and mass properties and the uniform flows they leave steady;
+every other routine has pins in tests/.
 """
 from __future__ import annotations
 

@@ -21,7 +21,8 @@
  * Parity unpinned: the local time step (orc_local_dt) beyond its scaling
  * invariants, since the paper gives no formula for it, and the boundary states
  * (orc_boundary_state) beyond their involution, rest-state, wall-symmetry and
- * mass properties. Every other routine is pinned by the tests against closed
+ * mass properties and the uniform flows they leave steady (far field, slip
+ * walls, moving isothermal walls). Every other routine is pinned by the tests against closed
  * forms, library routines, invariants or brute force.
  */
 #ifndef HGKS_ORACLE_H
